@@ -1,0 +1,957 @@
+/*
+ * ddlr_oracle.c -- plain, slow, FP64 CPU oracle of the DDLR preconditioner
+ * (Li & Saad, "Low-rank correction methods for algebraic domain decomposition
+ * preconditioners").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA library is checked against.  Only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark load it; the product path never does.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Every routine follows the paper's statement of the method step by step, in
+ * the paper's notation, with no blocking, fusion or reordering:
+ *   - Sec. 2.1-2.2 (eq. locsys2, Bmat): interior / interface classification and
+ *     the global reordering (all interiors by subdomain, then all interfaces);
+ *   - Sec. 3.1 (eq. EF, split): E = [a^-1 Ehat ; -a I],
+ *     A0 = blkdiag(B + a^-2 Ehat Ehat^T, C + a^2 I), A = A0 - E E^T;
+ *   - Sec. 4.1, 5: local solvers = incomplete Cholesky IC(0) on the pattern
+ *     (or exact Cholesky, dense), one factor per B_{i,a} and one for C_a;
+ *   - Sec. 4.4 (eq. converge): Lanczos on H = E^T A0^-1 E (DDLR-1) or on
+ *     E^T A0^-2 E (DDLR-2), with full reorthogonalisation (two classical
+ *     Gram-Schmidt passes), convergence checked every `check` steps;
+ *   - Sec. 3.2 (prop. gkt, Algorithm 1): DDLR-1 apply with
+ *     G_{k,theta}^-1 = (1-theta)^-1 I + U_k [(I-L_k)^-1 - (1-theta)^-1 I] U_k^T;
+ *   - Sec. 3.3 (eq. Form2a, lemma 1): DDLR-2 apply A0^-1 + U_k H_k U_k^T with
+ *     U_k = A0^-1 E V_k and H_k = (I - U_k^T E V_k)^-1;
+ *   - Sec. 5: preconditioned CG from x0 = 0.
+ *
+ * Readings where the paper is silent are the same as the CUDA library's and are
+ * listed with the design notes: natural (ascending original index) elimination
+ * order inside interior blocks; C_a factored like a local block, in ascending
+ * original index (c_order 0) or greedy multicolour order (c_order 1); Lanczos
+ * start vector from SplitMix64; breakdown restarts; theta = Ritz_{k+1}.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_OK = 0, OR_INVALID = 1, OR_NOMEM = 2, OR_BREAKDOWN = 3,
+       OR_NOT_SPD = 4, OR_NOCONV = 5 };
+
+/* ---------------------------------------------------------------- sparse */
+typedef struct {
+  int nr;       /* rows */
+  int *rp;      /* nr+1 */
+  int *ci;      /* column indices, ascending in each row */
+  double *va;
+} sp;
+
+static void sp_free(sp *a) {
+  free(a->rp); free(a->ci); free(a->va);
+  a->rp = NULL; a->ci = NULL; a->va = NULL; a->nr = 0;
+}
+
+/* coordinate entry used to assemble matrices; duplicates are summed */
+typedef struct { int r, c; double v; } trip;
+
+static int trip_cmp(const void *a, const void *b) {
+  const trip *x = (const trip *)a, *y = (const trip *)b;
+  if (x->r != y->r) return x->r < y->r ? -1 : 1;
+  if (x->c != y->c) return x->c < y->c ? -1 : 1;
+  return 0;
+}
+
+/* builds CSR from triplets (sorted, duplicates summed) */
+static int sp_from_trips(sp *out, int nr, trip *t, long nt) {
+  qsort(t, (size_t)nt, sizeof(trip), trip_cmp);
+  long nu = 0;
+  for (long q = 0; q < nt; q++) {
+    if (nu > 0 && t[nu - 1].r == t[q].r && t[nu - 1].c == t[q].c)
+      t[nu - 1].v += t[q].v;
+    else
+      t[nu++] = t[q];
+  }
+  out->nr = nr;
+  out->rp = (int *)calloc((size_t)nr + 1, sizeof(int));
+  out->ci = (int *)malloc(sizeof(int) * (size_t)(nu > 0 ? nu : 1));
+  out->va = (double *)malloc(sizeof(double) * (size_t)(nu > 0 ? nu : 1));
+  if (!out->rp || !out->ci || !out->va) return OR_NOMEM;
+  for (long q = 0; q < nu; q++) out->rp[t[q].r + 1]++;
+  for (int i = 0; i < nr; i++) out->rp[i + 1] += out->rp[i];
+  for (long q = 0; q < nu; q++) { out->ci[q] = t[q].c; out->va[q] = t[q].v; }
+  return OR_OK;
+}
+
+/* y = M x for an nr-row CSR */
+static void sp_mv(const sp *M, const double *x, double *y) {
+  for (int i = 0; i < M->nr; i++) {
+    double acc = 0.0;
+    for (int q = M->rp[i]; q < M->rp[i + 1]; q++) acc += M->va[q] * x[M->ci[q]];
+    y[i] = acc;
+  }
+}
+
+static double dot(int n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int i = 0; i < n; i++) s += a[i] * b[i];
+  return s;
+}
+
+/* ---------------------------------------------------- SplitMix64 (Steele et
+ * al. 2014): output i of stream `seed` is mix(seed + (i+1)*gamma). */
+static uint64_t sm64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+static double sm64_pm1(uint64_t seed, uint64_t i) {
+  return 2.0 * ((double)(sm64(seed, i) >> 11) * 0x1.0p-53) - 1.0;
+}
+
+/* ------------------------------------------------------------ block factor */
+typedef struct {
+  int nb;        /* block size */
+  int *ord;      /* ord[e] = block-local row (eq. Bmat order) eliminated e-th */
+  int exact;     /* 1: dense Cholesky, 0: IC(0) */
+  sp L;          /* IC(0): rows in elimination order, lower part incl. diagonal */
+  double *D;     /* exact: dense nb x nb lower factor, row-major */
+} blockfac;
+
+/* IC(0) of the symmetric matrix S (elimination-ordered, full storage):
+ *   l_ij = (s_ij - sum_{t<j, t in P_i and P_j} l_it l_jt) / l_jj   (j < i)
+ *   l_ii = sqrt(s_ii - sum_{t<i} l_it^2)
+ * over the lower pattern P_i of S; a pivot <= 0 is a breakdown. */
+static int ic0(const sp *S, sp *L) {
+  int n = S->nr;
+  long nnz = 0;
+  for (int i = 0; i < n; i++)
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
+      if (S->ci[q] <= i) nnz++;
+  L->nr = n;
+  L->rp = (int *)calloc((size_t)n + 1, sizeof(int));
+  L->ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  L->va = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!L->rp || !L->ci || !L->va) return OR_NOMEM;
+  long w = 0;
+  for (int i = 0; i < n; i++) {
+    int has_diag = 0;
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
+      if (S->ci[q] <= i) {
+        L->ci[w] = S->ci[q]; L->va[w] = S->va[q]; w++;
+        if (S->ci[q] == i) has_diag = 1;
+      }
+    if (!has_diag) return OR_BREAKDOWN;
+    L->rp[i + 1] = (int)w;
+  }
+  for (int i = 0; i < n; i++) {
+    int b = L->rp[i], e = L->rp[i + 1];   /* diagonal is the last entry */
+    for (int q = b; q < e - 1; q++) {
+      int j = L->ci[q];
+      double s = L->va[q];
+      /* merge row i (entries before q) with row j (entries before its diag) */
+      int qa = b, qb = L->rp[j], eb = L->rp[j + 1] - 1;
+      while (qa < q && qb < eb) {
+        if (L->ci[qa] == L->ci[qb]) { s -= L->va[qa] * L->va[qb]; qa++; qb++; }
+        else if (L->ci[qa] < L->ci[qb]) qa++;
+        else qb++;
+      }
+      L->va[q] = s / L->va[L->rp[j + 1] - 1];
+    }
+    double d = L->va[e - 1];
+    for (int q = b; q < e - 1; q++) d -= L->va[q] * L->va[q];
+    if (!(d > 0.0)) return OR_BREAKDOWN;
+    L->va[e - 1] = sqrt(d);
+  }
+  return OR_OK;
+}
+
+/* dense Cholesky S = L L^T (row-major lower); pivot <= 0 is a breakdown */
+static int chol_dense(int n, double *a) {
+  for (int j = 0; j < n; j++) {
+    double d = a[(size_t)j * n + j];
+    for (int t = 0; t < j; t++) d -= a[(size_t)j * n + t] * a[(size_t)j * n + t];
+    if (!(d > 0.0)) return OR_BREAKDOWN;
+    d = sqrt(d);
+    a[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; i++) {
+      double s = a[(size_t)i * n + j];
+      for (int t = 0; t < j; t++) s -= a[(size_t)i * n + t] * a[(size_t)j * n + t];
+      a[(size_t)i * n + j] = s / d;
+    }
+  }
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) a[(size_t)i * n + j] = 0.0;
+  return OR_OK;
+}
+
+/* solve (L L^T) x = b in place, b in elimination order */
+static void fac_solve(const blockfac *f, double *b) {
+  int n = f->nb;
+  if (f->exact) {
+    const double *D = f->D;
+    for (int i = 0; i < n; i++) {
+      double s = b[i];
+      for (int t = 0; t < i; t++) s -= D[(size_t)i * n + t] * b[t];
+      b[i] = s / D[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double s = b[i];
+      for (int t = i + 1; t < n; t++) s -= D[(size_t)t * n + i] * b[t];
+      b[i] = s / D[(size_t)i * n + i];
+    }
+  } else {
+    const sp *L = &f->L;
+    for (int i = 0; i < n; i++) {          /* forward: L y = b */
+      double s = b[i];
+      int e = L->rp[i + 1] - 1;
+      for (int q = L->rp[i]; q < e; q++) s -= L->va[q] * b[L->ci[q]];
+      b[i] = s / L->va[e];
+    }
+    for (int i = n - 1; i >= 0; i--) {     /* backward: L^T x = y (column form) */
+      int e = L->rp[i + 1] - 1;
+      b[i] = b[i] / L->va[e];
+      for (int q = L->rp[i]; q < e; q++) b[L->ci[q]] -= L->va[q] * b[i];
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ oracle */
+typedef struct {
+  int n, p, s, m;
+  int variant, k, theta_mode, factor, c_order, scale_diag;
+  double alpha;
+  int *perm;       /* new index (eq. Bmat order) -> original index */
+  int *iperm;      /* original -> new */
+  int *boff;       /* p+2 offsets; block p (interface) = [m, n) */
+  double *dsc;     /* D^-1/2 by original index (scale_diag), else NULL */
+  sp A;            /* original A (unscaled), for PCG */
+  sp Ap;           /* (scaled) A in new order */
+  sp Eh;           /* Ehat: m rows, columns 0..s-1 (= new index - m) */
+  sp EhT;          /* Ehat^T: s rows, columns 0..m-1 */
+  blockfac *bf;    /* p+1 local factors of A0 */
+  int urows;       /* s (DDLR-1) or n (DDLR-2) */
+  double *U;       /* urows x k, row-major, new order */
+  double *lam;     /* k Ritz values (DDLR-1) */
+  double theta;
+  double *Hk;      /* k x k (DDLR-2) */
+  int msteps;      /* Lanczos steps */
+  double *ritz;    /* all Ritz values of T_m, descending */
+  int ncolors;     /* colours of C_a (c_order 1) */
+  double *work;    /* n scratch */
+  double *work2;   /* n scratch */
+} oracle;
+
+void or_free(oracle *o);
+
+/* A0 solve in new order: p local solves with B_{i,a} and one with C_a */
+static void a0_solve(oracle *o, const double *x, double *z) {
+  for (int b = 0; b <= o->p; b++) {
+    blockfac *f = &o->bf[b];
+    int off = o->boff[b];
+    double *t = o->work2;
+    for (int e = 0; e < f->nb; e++) t[e] = x[off + f->ord[e]];
+    fac_solve(f, t);
+    for (int e = 0; e < f->nb; e++) z[off + f->ord[e]] = t[e];
+  }
+}
+
+/* v = E w = [a^-1 Ehat w ; -a w]  (eq. EF), w of length s, v of length n */
+static void e_mult(oracle *o, const double *w, double *v) {
+  sp_mv(&o->Eh, w, v);
+  for (int i = 0; i < o->m; i++) v[i] /= o->alpha;
+  for (int j = 0; j < o->s; j++) v[o->m + j] = -o->alpha * w[j];
+}
+
+/* y = E^T z = a^-1 Ehat^T z_B - a z_C */
+static void et_mult(oracle *o, const double *z, double *y) {
+  sp_mv(&o->EhT, z, y);
+  for (int j = 0; j < o->s; j++) y[j] = y[j] / o->alpha - o->alpha * z[o->m + j];
+}
+
+/* Lanczos operator: DDLR-1 H q = E^T A0^-1 E q; DDLR-2 E^T A0^-2 E q */
+static void lanczos_op(oracle *o, const double *q, double *w) {
+  double *v = (double *)malloc(sizeof(double) * (size_t)o->n);
+  double *z = (double *)malloc(sizeof(double) * (size_t)o->n);
+  e_mult(o, q, v);
+  a0_solve(o, v, z);
+  if (o->variant == 2) { a0_solve(o, z, v); memcpy(z, v, sizeof(double) * (size_t)o->n); }
+  et_mult(o, z, w);
+  free(v); free(z);
+}
+
+/* cyclic-by-row Jacobi eigen-decomposition of the dense symmetric m x m T:
+ * on return diag(T) holds eigenvalues and the columns of V the vectors. */
+static void jacobi_eig(int m, double *T, double *V) {
+  for (int i = 0; i < m * m; i++) V[i] = 0.0;
+  for (int i = 0; i < m; i++) V[i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; sweep++) {
+    double fro = 0.0;
+    for (int i = 0; i < m * m; i++) fro += T[i] * T[i];
+    fro = sqrt(fro);
+    int rotated = 0;
+    for (int p = 0; p < m - 1; p++)
+      for (int q = p + 1; q < m; q++) {
+        double apq = T[p * m + q];
+        /* an entry below 1e-18 ||T||_F is already zero in double precision */
+        if (fabs(apq) <= 1e-18 * fro) continue;
+        rotated = 1;
+        /* rotation zeroing T[p][q]: tau = (a_qq - a_pp)/(2 a_pq) */
+        double tau = (T[q * m + q] - T[p * m + p]) / (2.0 * apq);
+        double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int r = 0; r < m; r++) {          /* T <- T J */
+          double tp = T[r * m + p], tq = T[r * m + q];
+          T[r * m + p] = c * tp - s * tq;
+          T[r * m + q] = s * tp + c * tq;
+        }
+        for (int r = 0; r < m; r++) {          /* T <- J^T T */
+          double tp = T[p * m + r], tq = T[q * m + r];
+          T[p * m + r] = c * tp - s * tq;
+          T[q * m + r] = s * tp + c * tq;
+        }
+        for (int r = 0; r < m; r++) {          /* V <- V J */
+          double vp = V[r * m + p], vq = V[r * m + q];
+          V[r * m + p] = c * vp - s * vq;
+          V[r * m + q] = s * vp + c * vq;
+        }
+        T[p * m + q] = 0.0;   /* annihilated by construction */
+        T[q * m + p] = 0.0;
+      }
+    if (!rotated) break;
+  }
+}
+
+/* eigen-pairs of the tridiagonal T_m (alpha_1..m, beta_1..m-1), sorted
+ * descending; ties keep the eigensolver's index order. vals[m], vecs m x m
+ * (column c = c-th largest) when vecs != NULL. */
+static void tri_eig(int m, const double *al, const double *be, double *vals, double *vecs) {
+  double *T = (double *)calloc((size_t)m * m, sizeof(double));
+  double *V = (double *)calloc((size_t)m * m, sizeof(double));
+  int *idx = (int *)malloc(sizeof(int) * (size_t)m);
+  for (int i = 0; i < m; i++) {
+    T[i * m + i] = al[i];
+    if (i + 1 < m) { T[i * m + i + 1] = be[i]; T[(i + 1) * m + i] = be[i]; }
+  }
+  jacobi_eig(m, T, V);
+  for (int i = 0; i < m; i++) idx[i] = i;
+  for (int i = 1; i < m; i++) {          /* stable insertion sort, descending */
+    int v = idx[i], j = i - 1;
+    while (j >= 0 && T[idx[j] * m + idx[j]] < T[v * m + v]) { idx[j + 1] = idx[j]; j--; }
+    idx[j + 1] = v;
+  }
+  for (int c = 0; c < m; c++) {
+    vals[c] = T[idx[c] * m + idx[c]];
+    if (vecs)
+      for (int r = 0; r < m; r++) vecs[r * m + c] = V[r * m + idx[c]];
+  }
+  free(T); free(V); free(idx);
+}
+
+static double topk_sum(int m, const double *al, const double *be, int k) {
+  double *v = (double *)malloc(sizeof(double) * (size_t)m);
+  tri_eig(m, al, be, v, NULL);
+  double s = 0.0;
+  for (int i = 0; i < k && i < m; i++) s += v[i];
+  free(v);
+  return s;
+}
+
+/* w -= Q_j (Q_j^T w), twice (classical Gram-Schmidt, two passes) */
+static void cgs2(int s, int j, const double *Q, double *w, double *c) {
+  for (int pass = 0; pass < 2; pass++) {
+    for (int i = 0; i < j; i++) c[i] = dot(s, Q + (size_t)i * s, w);
+    for (int i = 0; i < j; i++)
+      for (int r = 0; r < s; r++) w[r] -= c[i] * Q[(size_t)i * s + r];
+  }
+}
+
+/* Lanczos with full reorthogonalisation (Sec. 4.4).  Q is s x mmax, column-
+ * major.  Returns the number of steps m and the tridiagonal (al, be). */
+static int lanczos(oracle *o, int k, int mmax, int check, double eps, uint64_t seed,
+                   double *Q, double *al, double *be) {
+  int s = o->s;
+  double *w = (double *)malloc(sizeof(double) * (size_t)s);
+  double *c = (double *)malloc(sizeof(double) * (size_t)(mmax + 1));
+  uint64_t restart = 0;
+  for (int r = 0; r < s; r++) Q[r] = sm64_pm1(seed + restart, (uint64_t)r);
+  double nq = sqrt(dot(s, Q, Q));
+  for (int r = 0; r < s; r++) Q[r] /= nq;
+  double scale = 0.0;
+  int m = 0;
+  double sig_prev = 0.0;
+  int have_prev = 0;
+  for (int j = 0; j < mmax; j++) {       /* step j+1 in the paper's 1-based count */
+    double *q = Q + (size_t)j * s;
+    lanczos_op(o, q, w);
+    al[j] = dot(s, q, w);
+    for (int r = 0; r < s; r++) w[r] -= al[j] * q[r];
+    if (j > 0)
+      for (int r = 0; r < s; r++) w[r] -= be[j - 1] * Q[(size_t)(j - 1) * s + r];
+    cgs2(s, j + 1, Q, w, c);
+    double b = sqrt(dot(s, w, w));
+    if (fabs(al[j]) > scale) scale = fabs(al[j]);
+    m = j + 1;
+    /* convergence test of eq. (converge) every `check` steps once m > k */
+    if (check > 0 && m % check == 0 && m >= k + 1) {
+      double sig = topk_sum(m, al, be, k);
+      double sp_ = topk_sum(m - 1, al, be, k);
+      (void)have_prev; (void)sig_prev;
+      if (fabs(sig - sp_) < eps * fabs(sp_)) { be[j] = b; break; }
+    }
+    if (m == mmax) { be[j] = b; break; }
+    if (b <= 1e-12 * (scale > 0 ? scale : 1.0)) {
+      /* breakdown: invariant subspace found; continue from a fresh random
+       * vector orthogonalised against Q_j, with beta_j = 0 */
+      be[j] = 0.0;
+      restart++;
+      for (int r = 0; r < s; r++) w[r] = sm64_pm1(seed + restart, (uint64_t)r);
+      cgs2(s, j + 1, Q, w, c);
+      b = sqrt(dot(s, w, w));
+      double *qn = Q + (size_t)(j + 1) * s;
+      for (int r = 0; r < s; r++) qn[r] = w[r] / b;
+    } else {
+      be[j] = b;
+      if (b > scale) scale = b;
+      double *qn = Q + (size_t)(j + 1) * s;
+      for (int r = 0; r < s; r++) qn[r] = w[r] / b;
+    }
+  }
+  free(w); free(c);
+  return m;
+}
+
+/* ------------------------------------------------------------ public API */
+int or_setup(int n, const int *rowptr, const int *colind, const double *val,
+             const int *part, int p, int variant, int k, double alpha,
+             int theta_mode, int factor, int c_order, int scale_diag,
+             int lanczos_max, int lanczos_check, double lanczos_eps,
+             unsigned long long seed, void **out) {
+  *out = NULL;
+  if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
+    return OR_INVALID;
+  for (int i = 0; i < n; i++) {
+    if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
+    if (part[i] < 0 || part[i] >= p) return OR_INVALID;
+    for (int q = rowptr[i]; q < rowptr[i + 1]; q++) {
+      if (colind[q] < 0 || colind[q] >= n) return OR_INVALID;
+      if (q > rowptr[i] && colind[q] <= colind[q - 1]) return OR_INVALID;
+    }
+  }
+  /* symmetry of pattern and values */
+  for (int i = 0; i < n; i++)
+    for (int q = rowptr[i]; q < rowptr[i + 1]; q++) {
+      int j = colind[q], found = 0;
+      for (int t = rowptr[j]; t < rowptr[j + 1]; t++)
+        if (colind[t] == i) { found = (val[t] == val[q]); break; }
+      if (!found) return OR_INVALID;
+    }
+  oracle *o = (oracle *)calloc(1, sizeof(oracle));
+  if (!o) return OR_NOMEM;
+  o->n = n; o->p = p; o->variant = variant; o->k = k; o->alpha = alpha;
+  o->theta_mode = theta_mode; o->factor = factor; o->c_order = c_order;
+  o->scale_diag = scale_diag;
+  int st = OR_OK;
+  long nnz = rowptr[n];
+
+  /* original A (for PCG) */
+  o->A.nr = n;
+  o->A.rp = (int *)malloc(sizeof(int) * (size_t)(n + 1));
+  o->A.ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  o->A.va = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  memcpy(o->A.rp, rowptr, sizeof(int) * (size_t)(n + 1));
+  memcpy(o->A.ci, colind, sizeof(int) * (size_t)nnz);
+  memcpy(o->A.va, val, sizeof(double) * (size_t)nnz);
+
+  /* optional symmetric diagonal scaling D^-1/2 A D^-1/2 */
+  double *As = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  memcpy(As, val, sizeof(double) * (size_t)nnz);
+  if (scale_diag) {
+    o->dsc = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; i++) {
+      double d = 0.0;
+      for (int q = rowptr[i]; q < rowptr[i + 1]; q++) if (colind[q] == i) d = val[q];
+      if (!(d > 0)) { free(As); or_free(o); return OR_INVALID; }
+      o->dsc[i] = 1.0 / sqrt(d);
+    }
+    for (int i = 0; i < n; i++)
+      for (int q = rowptr[i]; q < rowptr[i + 1]; q++)
+        As[q] = val[q] * o->dsc[i] * o->dsc[colind[q]];
+  }
+
+  /* Sec. 2.1: node i is an interface node iff it couples to another part */
+  int *iface = (int *)calloc((size_t)n, sizeof(int));
+  for (int i = 0; i < n; i++)
+    for (int q = rowptr[i]; q < rowptr[i + 1]; q++)
+      if (part[colind[q]] != part[i]) iface[i] = 1;
+
+  /* eq. (Bmat): interiors of subdomain 0..p-1 (ascending index), then all
+   * interface nodes (ascending index) */
+  o->perm = (int *)malloc(sizeof(int) * (size_t)n);
+  o->iperm = (int *)malloc(sizeof(int) * (size_t)n);
+  o->boff = (int *)malloc(sizeof(int) * (size_t)(p + 2));
+  int w = 0;
+  for (int b = 0; b < p; b++) {
+    o->boff[b] = w;
+    for (int i = 0; i < n; i++) if (part[i] == b && !iface[i]) o->perm[w++] = i;
+  }
+  o->boff[p] = w;
+  o->m = w;
+  for (int i = 0; i < n; i++) if (iface[i]) o->perm[w++] = i;
+  o->boff[p + 1] = w;
+  o->s = n - o->m;
+  for (int g = 0; g < n; g++) o->iperm[o->perm[g]] = g;
+  int m = o->m, s = o->s;
+  if (s == 0) { free(As); free(iface); or_free(o); return OR_INVALID; }
+  if (k > s) { free(As); free(iface); or_free(o); return OR_INVALID; }
+
+  /* permuted (scaled) A */
+  {
+    trip *t = (trip *)malloc(sizeof(trip) * (size_t)(nnz > 0 ? nnz : 1));
+    long nt = 0;
+    for (int i = 0; i < n; i++)
+      for (int q = rowptr[i]; q < rowptr[i + 1]; q++) {
+        t[nt].r = o->iperm[i]; t[nt].c = o->iperm[colind[q]]; t[nt].v = As[q]; nt++;
+      }
+    sp_from_trips(&o->Ap, n, t, nt);
+    free(t);
+  }
+  free(As);
+
+  /* Ehat (m x s) and its transpose */
+  {
+    long ne = 0;
+    for (int g = 0; g < m; g++)
+      for (int q = o->Ap.rp[g]; q < o->Ap.rp[g + 1]; q++) if (o->Ap.ci[q] >= m) ne++;
+    trip *t1 = (trip *)malloc(sizeof(trip) * (size_t)(ne > 0 ? ne : 1));
+    trip *t2 = (trip *)malloc(sizeof(trip) * (size_t)(ne > 0 ? ne : 1));
+    long nt = 0;
+    for (int g = 0; g < m; g++)
+      for (int q = o->Ap.rp[g]; q < o->Ap.rp[g + 1]; q++)
+        if (o->Ap.ci[q] >= m) {
+          t1[nt].r = g; t1[nt].c = o->Ap.ci[q] - m; t1[nt].v = o->Ap.va[q];
+          t2[nt].r = o->Ap.ci[q] - m; t2[nt].c = g; t2[nt].v = o->Ap.va[q];
+          nt++;
+        }
+    sp_from_trips(&o->Eh, m, t1, nt);
+    sp_from_trips(&o->EhT, s, t2, nt);
+    free(t1); free(t2);
+  }
+
+  /* local blocks of A0 (eq. split): B_{i,a} = B_i + a^-2 E_i E_i^T and
+   * C_a = C + a^2 I.  Proposition (locality): Ehat Ehat^T has no coupling
+   * between different subdomains; a violation is reported as INVALID. */
+  o->bf = (blockfac *)calloc((size_t)(p + 1), sizeof(blockfac));
+  o->work = (double *)malloc(sizeof(double) * (size_t)n);
+  o->work2 = (double *)malloc(sizeof(double) * (size_t)n);
+  int *blk = (int *)malloc(sizeof(int) * (size_t)n);
+  for (int b = 0; b <= p; b++)
+    for (int g = o->boff[b]; g < o->boff[b + 1]; g++) blk[g] = b;
+  for (int b = 0; b <= p && st == OR_OK; b++) {
+    int off = o->boff[b], nb = o->boff[b + 1] - off;
+    blockfac *f = &o->bf[b];
+    f->nb = nb;
+    f->ord = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
+    /* assemble the block in eq. Bmat (local) order */
+    long cap = 16 + nb;
+    for (int g = off; g < off + nb; g++) cap += o->Ap.rp[g + 1] - o->Ap.rp[g];
+    if (b < p)
+      for (int g = off; g < off + nb; g++)
+        for (int q = o->Eh.rp[g]; q < o->Eh.rp[g + 1]; q++) {
+          int j = o->Eh.ci[q];
+          cap += o->EhT.rp[j + 1] - o->EhT.rp[j];
+        }
+    trip *t = (trip *)malloc(sizeof(trip) * (size_t)cap);
+    long nt = 0;
+    for (int g = off; g < off + nb; g++)
+      for (int q = o->Ap.rp[g]; q < o->Ap.rp[g + 1]; q++) {
+        int c = o->Ap.ci[q];
+        if (c >= off && c < off + nb) { t[nt].r = g - off; t[nt].c = c - off; t[nt].v = o->Ap.va[q]; nt++; }
+      }
+    if (b < p) {
+      double ia2 = 1.0 / (alpha * alpha);
+      for (int g = off; g < off + nb; g++)
+        for (int q = o->Eh.rp[g]; q < o->Eh.rp[g + 1]; q++) {
+          int j = o->Eh.ci[q];
+          for (int t2 = o->EhT.rp[j]; t2 < o->EhT.rp[j + 1]; t2++) {
+            int g2 = o->EhT.ci[t2];
+            if (blk[g2] != b) { st = OR_INVALID; break; }
+            t[nt].r = g - off; t[nt].c = g2 - off; t[nt].v = ia2 * o->Eh.va[q] * o->EhT.va[t2]; nt++;
+          }
+        }
+    } else {
+      for (int r = 0; r < nb; r++) { t[nt].r = r; t[nt].c = r; t[nt].v = alpha * alpha; nt++; }
+    }
+    sp B;
+    memset(&B, 0, sizeof B);
+    if (st == OR_OK) st = sp_from_trips(&B, nb, t, nt);
+    free(t);
+    if (st != OR_OK) { sp_free(&B); break; }
+
+    /* elimination order: ascending index, or greedy multicolour for C_a */
+    for (int e = 0; e < nb; e++) f->ord[e] = e;
+    if (b == p && c_order == 1) {
+      int *col = (int *)malloc(sizeof(int) * (size_t)nb);
+      int *used = (int *)calloc((size_t)nb + 2, sizeof(int));
+      int nc = 0;
+      for (int r = 0; r < nb; r++) {
+        for (int q = B.rp[r]; q < B.rp[r + 1]; q++)
+          if (B.ci[q] < r) used[col[B.ci[q]]] = r + 1;
+        int c = 0;
+        while (used[c] == r + 1) c++;
+        col[r] = c;
+        if (c + 1 > nc) nc = c + 1;
+      }
+      o->ncolors = nc;
+      int e = 0;
+      for (int c = 0; c < nc; c++)
+        for (int r = 0; r < nb; r++) if (col[r] == c) f->ord[e++] = r;
+      free(col); free(used);
+    }
+    int *pos = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
+    for (int e = 0; e < nb; e++) pos[f->ord[e]] = e;
+    /* the block in elimination order */
+    long bn = B.rp[nb];
+    trip *t3 = (trip *)malloc(sizeof(trip) * (size_t)(bn > 0 ? bn : 1));
+    long n3 = 0;
+    for (int r = 0; r < nb; r++)
+      for (int q = B.rp[r]; q < B.rp[r + 1]; q++) {
+        t3[n3].r = pos[r]; t3[n3].c = pos[B.ci[q]]; t3[n3].v = B.va[q]; n3++;
+      }
+    sp S;
+    memset(&S, 0, sizeof S);
+    sp_from_trips(&S, nb, t3, n3);
+    free(t3); free(pos); sp_free(&B);
+    if (factor == 1) {
+      f->exact = 1;
+      f->D = (double *)calloc((size_t)nb * nb + 1, sizeof(double));
+      if (!f->D) { st = OR_NOMEM; sp_free(&S); break; }
+      for (int r = 0; r < nb; r++)
+        for (int q = S.rp[r]; q < S.rp[r + 1]; q++) f->D[(size_t)r * nb + S.ci[q]] = S.va[q];
+      st = chol_dense(nb, f->D);
+    } else {
+      st = ic0(&S, &f->L);
+    }
+    sp_free(&S);
+  }
+  free(blk);
+  free(iface);
+  if (st != OR_OK) { or_free(o); return st; }
+
+  /* low-rank part (Sec. 4.4) */
+  int mmax = lanczos_max > 0 ? lanczos_max : 5 * k;
+  if (mmax > s) mmax = s;
+  if (mmax < k) mmax = k;
+  double *Q = (double *)malloc(sizeof(double) * (size_t)s * (size_t)(mmax + 1));
+  double *al = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  double *be = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  if (!Q || !al || !be) { free(Q); free(al); free(be); or_free(o); return OR_NOMEM; }
+  int mm = lanczos(o, k, mmax, lanczos_check, lanczos_eps, (uint64_t)seed, Q, al, be);
+  o->msteps = mm;
+  o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
+  double *Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+  tri_eig(mm, al, be, o->ritz, Y);
+  /* Ritz vectors: (Q_m Y)_k, s x k row-major */
+  double *V = (double *)calloc((size_t)s * k, sizeof(double));
+  for (int r = 0; r < s; r++)
+    for (int c = 0; c < k; c++) {
+      double acc = 0.0;
+      for (int j = 0; j < mm; j++) acc += Q[(size_t)j * s + r] * Y[j * mm + c];
+      V[(size_t)r * k + c] = acc;
+    }
+  free(Q); free(al); free(be); free(Y);
+
+  if (variant == 1) {
+    o->urows = s;
+    o->U = V;
+    o->lam = (double *)malloc(sizeof(double) * (size_t)k);
+    for (int c = 0; c < k; c++) o->lam[c] = o->ritz[c];
+    o->theta = (theta_mode == 1 && k < mm) ? o->ritz[k] : 0.0;
+    /* prop. spd-1: M is SPD when theta < 1 and every lambda_i < 1 */
+    if (!(o->lam[0] < 1.0) || !(o->theta < 1.0)) { or_free(o); return OR_NOT_SPD; }
+  } else {
+    /* U_k = A0^-1 E V_k (n x k); K = U_k^T (E V_k); H_k = (I - K)^-1 */
+    o->urows = n;
+    o->U = (double *)calloc((size_t)n * k, sizeof(double));
+    double *EV = (double *)calloc((size_t)n * k, sizeof(double));
+    double *vc = (double *)malloc(sizeof(double) * (size_t)s);
+    double *ev = (double *)malloc(sizeof(double) * (size_t)n);
+    double *uc = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int c = 0; c < k; c++) {
+      for (int r = 0; r < s; r++) vc[r] = V[(size_t)r * k + c];
+      e_mult(o, vc, ev);
+      a0_solve(o, ev, uc);
+      for (int r = 0; r < n; r++) { EV[(size_t)r * k + c] = ev[r]; o->U[(size_t)r * k + c] = uc[r]; }
+    }
+    double *K = (double *)calloc((size_t)k * k, sizeof(double));
+    for (int a = 0; a < k; a++)
+      for (int b = 0; b < k; b++) {
+        double acc = 0.0;
+        for (int r = 0; r < n; r++) acc += o->U[(size_t)r * k + a] * EV[(size_t)r * k + b];
+        K[a * k + b] = acc;
+      }
+    /* I - K, symmetrised, Cholesky (failure: not SPD, prop. spd-2), inverse */
+    double *IK = (double *)calloc((size_t)k * k, sizeof(double));
+    for (int a = 0; a < k; a++)
+      for (int b = 0; b < k; b++)
+        IK[a * k + b] = (a == b ? 1.0 : 0.0) - 0.5 * (K[a * k + b] + K[b * k + a]);
+    int cst = chol_dense(k, IK);
+    if (cst == OR_OK) {
+      o->Hk = (double *)calloc((size_t)k * k, sizeof(double));
+      double *e = (double *)malloc(sizeof(double) * (size_t)k);
+      for (int c = 0; c < k; c++) {
+        for (int r = 0; r < k; r++) e[r] = (r == c) ? 1.0 : 0.0;
+        for (int i = 0; i < k; i++) {
+          double sm = e[i];
+          for (int t = 0; t < i; t++) sm -= IK[i * k + t] * e[t];
+          e[i] = sm / IK[i * k + i];
+        }
+        for (int i = k - 1; i >= 0; i--) {
+          double sm = e[i];
+          for (int t = i + 1; t < k; t++) sm -= IK[t * k + i] * e[t];
+          e[i] = sm / IK[i * k + i];
+        }
+        for (int r = 0; r < k; r++) o->Hk[r * k + c] = e[r];
+      }
+      free(e);
+    }
+    free(EV); free(vc); free(ev); free(uc); free(K); free(IK); free(V);
+    if (cst != OR_OK) { or_free(o); return OR_NOT_SPD; }
+  }
+  *out = o;
+  return OR_OK;
+}
+
+void or_free(oracle *o) {
+  if (!o) return;
+  free(o->perm); free(o->iperm); free(o->boff); free(o->dsc);
+  sp_free(&o->A); sp_free(&o->Ap); sp_free(&o->Eh); sp_free(&o->EhT);
+  if (o->bf) {
+    for (int b = 0; b <= o->p; b++) {
+      free(o->bf[b].ord); free(o->bf[b].D); sp_free(&o->bf[b].L);
+    }
+    free(o->bf);
+  }
+  free(o->U); free(o->lam); free(o->Hk); free(o->ritz);
+  free(o->work); free(o->work2);
+  free(o);
+}
+
+void or_destroy(void *h) { or_free((oracle *)h); }
+
+/* M^-1 applied in new order (scaled system) */
+static void apply_new(oracle *o, const double *x, double *u) {
+  int n = o->n, s = o->s, k = o->k;
+  double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *t = (double *)malloc(sizeof(double) * (size_t)k);
+  if (o->variant == 1) {
+    /* Algorithm 1 */
+    double *y = (double *)malloc(sizeof(double) * (size_t)s);
+    double *wv = (double *)malloc(sizeof(double) * (size_t)s);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    a0_solve(o, x, z);                                  /* 1: A0 z = x */
+    et_mult(o, z, y);                                   /* 2: y = E^T z */
+    double it = 1.0 / (1.0 - o->theta);                 /* 3: w = G_{k,theta}^-1 y */
+    for (int c = 0; c < k; c++) {
+      double acc = 0.0;
+      for (int r = 0; r < s; r++) acc += o->U[(size_t)r * k + c] * y[r];
+      t[c] = acc * (1.0 / (1.0 - o->lam[c]) - it);
+    }
+    for (int r = 0; r < s; r++) {
+      double acc = 0.0;
+      for (int c = 0; c < k; c++) acc += o->U[(size_t)r * k + c] * t[c];
+      wv[r] = it * y[r] + acc;
+    }
+    e_mult(o, wv, v);                                   /* 4: v = E w */
+    for (int i = 0; i < n; i++) v[i] += x[i];
+    a0_solve(o, v, u);                                  /* 5: A0 u = x + v */
+    free(y); free(wv); free(v);
+  } else {
+    /* eq. (Form2a): u = A0^-1 x + U_k H_k U_k^T x */
+    double *h = (double *)malloc(sizeof(double) * (size_t)k);
+    a0_solve(o, x, u);
+    for (int c = 0; c < k; c++) {
+      double acc = 0.0;
+      for (int r = 0; r < n; r++) acc += o->U[(size_t)r * k + c] * x[r];
+      t[c] = acc;
+    }
+    for (int a = 0; a < k; a++) {
+      double acc = 0.0;
+      for (int b = 0; b < k; b++) acc += o->Hk[a * k + b] * t[b];
+      h[a] = acc;
+    }
+    for (int r = 0; r < n; r++) {
+      double acc = 0.0;
+      for (int c = 0; c < k; c++) acc += o->U[(size_t)r * k + c] * h[c];
+      u[r] += acc;
+    }
+    free(h);
+  }
+  free(z); free(t);
+}
+
+/* y = M^-1 x in the original ordering; with diagonal scaling
+ * M^-1 = D^-1/2 Mhat^-1 D^-1/2 */
+int or_apply(void *h, const double *x, double *y) {
+  oracle *o = (oracle *)h;
+  int n = o->n;
+  double *xn = (double *)malloc(sizeof(double) * (size_t)n);
+  double *yn = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int g = 0; g < n; g++) {
+    int i = o->perm[g];
+    xn[g] = o->dsc ? x[i] * o->dsc[i] : x[i];
+  }
+  apply_new(o, xn, yn);
+  for (int g = 0; g < n; g++) {
+    int i = o->perm[g];
+    y[i] = o->dsc ? yn[g] * o->dsc[i] : yn[g];
+  }
+  free(xn); free(yn);
+  return OR_OK;
+}
+
+/* z = A0^-1 x in the original ordering (scaled system when scale_diag) */
+int or_a0_solve(void *h, const double *x, double *y) {
+  oracle *o = (oracle *)h;
+  int n = o->n;
+  double *xn = (double *)malloc(sizeof(double) * (size_t)n);
+  double *yn = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int g = 0; g < n; g++) xn[g] = x[o->perm[g]];
+  a0_solve(o, xn, yn);
+  for (int g = 0; g < n; g++) y[o->perm[g]] = yn[g];
+  free(xn); free(yn);
+  return OR_OK;
+}
+
+/* Preconditioned CG (Hestenes-Stiefel; flexible=1: Polak-Ribiere beta) from
+ * x0 = 0.  Converged when ||r|| <= tol ||b||, confirmed on the true residual
+ * b - A x; if that check fails, r is replaced by the true residual and CG
+ * restarts from the current x.  its = number of x updates. */
+int or_pcg(void *h, const double *b, double *x, double tol, int maxit, int flexible,
+           int *its_out, double *relres_out) {
+  oracle *o = (oracle *)h;
+  int n = o->n;
+  double *r = (double *)malloc(sizeof(double) * (size_t)n);
+  double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *zo = (double *)malloc(sizeof(double) * (size_t)n);
+  double *p = (double *)malloc(sizeof(double) * (size_t)n);
+  double *q = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+  double bn = sqrt(dot(n, b, b));
+  int its = 0, st = OR_NOCONV;
+  double rel = 0.0;
+  if (bn == 0.0) { st = OR_OK; goto done; }
+  or_apply(o, r, z);
+  memcpy(p, z, sizeof(double) * (size_t)n);
+  double rz = dot(n, r, z);
+  while (its < maxit) {
+    sp_mv(&o->A, p, q);
+    double a = rz / dot(n, p, q);
+    for (int i = 0; i < n; i++) { x[i] += a * p[i]; r[i] -= a * q[i]; }
+    its++;
+    if (sqrt(dot(n, r, r)) <= tol * bn) {
+      sp_mv(&o->A, x, q);
+      for (int i = 0; i < n; i++) q[i] = b[i] - q[i];
+      if (sqrt(dot(n, q, q)) <= tol * bn) { st = OR_OK; break; }
+      memcpy(r, q, sizeof(double) * (size_t)n);
+      or_apply(o, r, z);
+      memcpy(p, z, sizeof(double) * (size_t)n);
+      rz = dot(n, r, z);
+      continue;
+    }
+    memcpy(zo, z, sizeof(double) * (size_t)n);
+    or_apply(o, r, z);
+    double rzn = dot(n, r, z), beta;
+    if (flexible) {
+      double t = 0.0;
+      for (int i = 0; i < n; i++) t += r[i] * (z[i] - zo[i]);
+      beta = t / rz;
+    } else {
+      beta = rzn / rz;
+    }
+    rz = rzn;
+    for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+  }
+done:
+  sp_mv(&o->A, x, q);
+  for (int i = 0; i < n; i++) q[i] = b[i] - q[i];
+  rel = bn > 0 ? sqrt(dot(n, q, q)) / bn : 0.0;
+  *its_out = its;
+  *relres_out = rel;
+  free(r); free(z); free(zo); free(p); free(q);
+  return st;
+}
+
+/* sizes and scalars: out[0..8] = n, p, s, m, k, msteps, ncolors, variant, urows */
+void or_info(void *h, int *out, double *theta) {
+  oracle *o = (oracle *)h;
+  out[0] = o->n; out[1] = o->p; out[2] = o->s; out[3] = o->m; out[4] = o->k;
+  out[5] = o->msteps; out[6] = o->ncolors; out[7] = o->variant; out[8] = o->urows;
+  *theta = o->theta;
+}
+
+void or_ritz(void *h, double *out) {
+  oracle *o = (oracle *)h;
+  memcpy(out, o->ritz, sizeof(double) * (size_t)o->msteps);
+}
+
+void or_perm(void *h, int *perm) {
+  oracle *o = (oracle *)h;
+  memcpy(perm, o->perm, sizeof(int) * (size_t)o->n);
+}
+
+/* low-rank data: U (urows x k, rows in new order), lam (k), Hk (k x k) */
+void or_lowrank(void *h, double *U, double *lam, double *Hk) {
+  oracle *o = (oracle *)h;
+  memcpy(U, o->U, sizeof(double) * (size_t)o->urows * o->k);
+  if (lam && o->lam) memcpy(lam, o->lam, sizeof(double) * (size_t)o->k);
+  if (Hk && o->Hk) memcpy(Hk, o->Hk, sizeof(double) * (size_t)o->k * o->k);
+}
+
+/* number of stored factor entries (lower incl. diagonal) over all blocks */
+long or_factor_nnz(void *h) {
+  oracle *o = (oracle *)h;
+  long t = 0;
+  for (int b = 0; b <= o->p; b++) {
+    blockfac *f = &o->bf[b];
+    if (f->exact) {
+      for (long i = 0; i < (long)f->nb * f->nb; i++) if (f->D[i] != 0.0) t++;
+    } else {
+      t += f->L.rp[f->nb];
+    }
+  }
+  return t;
+}
+
+/* factor entries as (row, col, value) with ORIGINAL indices: entry L(e_i, e_j)
+ * of a block's factor in its elimination order is reported at the original
+ * indices of the rows eliminated at e_i and e_j. */
+void or_factor_coo(void *h, int *ri, int *cj, double *v) {
+  oracle *o = (oracle *)h;
+  long w = 0;
+  for (int b = 0; b <= o->p; b++) {
+    blockfac *f = &o->bf[b];
+    int off = o->boff[b];
+    for (int i = 0; i < f->nb; i++) {
+      if (f->exact) {
+        for (int j = 0; j <= i; j++) {
+          double d = f->D[(size_t)i * f->nb + j];
+          if (d == 0.0) continue;
+          ri[w] = o->perm[off + f->ord[i]]; cj[w] = o->perm[off + f->ord[j]]; v[w] = d; w++;
+        }
+      } else {
+        for (int q = f->L.rp[i]; q < f->L.rp[i + 1]; q++) {
+          ri[w] = o->perm[off + f->ord[i]];
+          cj[w] = o->perm[off + f->ord[f->L.ci[q]]];
+          v[w] = f->L.va[q]; w++;
+        }
+      }
+    }
+  }
+}
+
+/* SplitMix64 value in [-1, 1): exposed so the tests can pin the generator */
+double or_sm64_pm1(unsigned long long seed, unsigned long long i) {
+  return sm64_pm1((uint64_t)seed, (uint64_t)i);
+}

@@ -1,0 +1,352 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+No expected value here comes from the oracle itself or from the CUDA path:
+each is a hand-derived closed form (tests/golden), a published generator
+output, a dense LAPACK computation written from the paper's definitions
+(tests/dense_ddlr.py), or an invariant proved in the paper.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from dense_ddlr import DenseDDLR, oracle_matrix
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out.setdefault(key, []).append(vals)
+    return out
+
+
+def test_splitmix64_published_outputs():
+    vals = []
+    with open(os.path.join(GOLD, "splitmix64_seed0.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                vals.append(int(line, 16))
+    z = W.splitmix64(0, 3)
+    assert [int(v) for v in z] == vals
+    # the oracle's own implementation of the same generator
+    for i, v in enumerate(vals):
+        assert O.sm64_pm1(0, i) == 2.0 * ((v >> 11) * 2.0 ** -53) - 1.0
+
+
+def test_closed_form_1d_n4():
+    """Sec. 3.1-3.2 by hand: H eigenvalues 5/6, 7/12; k=1, theta=7/12 gives
+    M^-1 = A^-1 exactly."""
+    g = _read_golden("ddlr_1d_n4.txt")
+    A = W.laplacian((4,))
+    part = np.array([0, 0, 1, 1], dtype=np.int32)
+    Ainv = np.array([[float(v) for v in row] for row in g["Ainv"]])
+    lam = np.array([float(v) for v in g["lambda"][0]])
+    orc = O.Oracle(A, part, 2, variant=1, k=1, factor=0)
+    assert (orc.s, orc.m) == (2, 2)
+    assert list(orc.perm) == [0, 3, 1, 2]
+    np.testing.assert_allclose(orc.ritz, lam, rtol=0, atol=1e-15)
+    assert abs(orc.theta - float(g["theta_k1"][0][0])) < 1e-15
+    M = oracle_matrix(orc, 4)
+    np.testing.assert_allclose(M, Ainv, rtol=0, atol=1e-14)
+    # k = s (= 2): theta = 0 and again M^-1 = A^-1
+    orc2 = O.Oracle(A, part, 2, variant=1, k=2, factor=0)
+    np.testing.assert_allclose(oracle_matrix(orc2, 4), Ainv, rtol=0, atol=1e-14)
+    # DDLR-2 with k = s is exact too
+    orc3 = O.Oracle(A, part, 2, variant=2, k=2, factor=0)
+    np.testing.assert_allclose(oracle_matrix(orc3, 4), Ainv, rtol=0, atol=1e-14)
+
+
+SMALL = [
+    ("2d_12x12_2x2", lambda: (W.laplacian((12, 12)),) + W.box_partition((12, 12), (2, 2))),
+    ("3d_6x6x6_2x2x2", lambda: (W.laplacian((6, 6, 6)),) + W.box_partition((6, 6, 6), (2, 2, 2))),
+    ("2d_13x11_3x2", lambda: (W.laplacian((13, 11)),) + W.box_partition((13, 11), (3, 2))),
+]
+
+
+@pytest.fixture(scope="module", params=SMALL, ids=[s[0] for s in SMALL])
+def small(request):
+    A, part, p = request.param[1]()
+    return A, part, p, DenseDDLR(A, part, p)
+
+
+def _gap_k(lam, k0, tol=1e-6):
+    """Smallest k >= k0 with lambda_k > lambda_{k+1} (a unique top-k space)."""
+    k = k0
+    while lam[k - 1] - lam[k] <= tol:
+        k += 1
+    return k
+
+
+def test_splitting_identity(small):
+    """eq. (split): A = A0 - E E^T; Proposition: Ehat Ehat^T block-local;
+    Lemma eigH: 0 <= lambda(H) < 1 and E^T A^-1 E = H (I - H)^-1."""
+    A, part, p, D = small
+    np.testing.assert_allclose(D.A0 - D.E @ D.E.T, D.Ap, atol=1e-14)
+    assert D.lam.min() >= -1e-14 and D.lam.max() < 1.0
+    EtAinvE = D.E.T @ np.linalg.solve(D.Ap, D.E)
+    HH = D.H @ np.linalg.inv(np.eye(D.s) - D.H)
+    np.testing.assert_allclose(EtAinvE, HH, atol=1e-10)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_full_rank_is_exact(small, variant):
+    """SMW (eq. split3): exact local factors and k = s give M^-1 = A^-1, and
+    PCG converges in one iteration."""
+    A, part, p, D = small
+    orc = O.Oracle(A, part, p, variant=variant, k=D.s, factor=1)
+    assert orc.s == D.s and orc.m == D.m
+    assert np.array_equal(orc.perm, D.perm)
+    Ad = W.to_dense(A)
+    Ainv = np.linalg.inv(Ad)
+    M = oracle_matrix(orc, D.n)
+    assert np.abs(M - Ainv).max() / np.abs(Ainv).max() < 1e-12
+    b = W.rhs(D.n, 3)
+    x, its, rel, st = orc.pcg(b, 1e-10)
+    assert st == "OK" and its == 1 and rel < 1e-10
+
+
+def test_ddlr1_theta_k_eq_s_minus_1_exact(small):
+    """eq. (eigDiffG): with theta = lambda_s and k = s-1 all eigenvalues of
+    G^-1 - G_{k,theta}^-1 vanish, so M^-1 = A^-1."""
+    A, part, p, D = small
+    orc = O.Oracle(A, part, p, variant=1, k=D.s - 1, factor=1, lanczos_max=D.s,
+                   lanczos_eps=0.0, lanczos_check=0)
+    Ainv = np.linalg.inv(W.to_dense(A))
+    M = oracle_matrix(orc, D.n)
+    assert np.abs(M - Ainv).max() / np.abs(Ainv).max() < 1e-11
+
+
+@pytest.mark.parametrize("theta_mode", [1, 0])
+def test_ddlr1_matches_dense_eigenbasis(small, theta_mode):
+    """Oracle DDLR-1 (prop. gkt form, Lanczos Ritz pairs at m = s) equals the
+    dense eq. (UDU)/(Mprec) form built from eigh(H) with the full basis."""
+    A, part, p, D = small
+    k = _gap_k(D.lam, 5)
+    orc = O.Oracle(A, part, p, variant=1, k=k, factor=1, theta_mode=theta_mode,
+                   lanczos_max=D.s, lanczos_eps=0.0, lanczos_check=0)
+    np.testing.assert_allclose(orc.ritz, D.lam, atol=1e-12)
+    Mp, theta = D.minv_ddlr1(k, theta_mode)
+    assert abs(orc.theta - theta) < 1e-12
+    M = oracle_matrix(orc, D.n)
+    Md = D.to_original(Mp)
+    assert np.abs(M - Md).max() / np.abs(Md).max() < 1e-10
+    U, lam, _ = orc.lowrank()
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-10)
+
+
+def test_ddlr2_matches_dense_svd(small):
+    """Oracle DDLR-2 equals the dense eq. (LR)/(Form2a) built from the top-k
+    right singular vectors of A0^-1 E."""
+    A, part, p, D = small
+    X = D.A0inv @ D.E
+    mu = np.sort(np.linalg.eigvalsh(X.T @ X))[::-1]
+    k = _gap_k(mu, 6, 1e-9 * mu[0])
+    orc = O.Oracle(A, part, p, variant=2, k=k, factor=1, lanczos_max=D.s,
+                   lanczos_eps=0.0, lanczos_check=0)
+    M = oracle_matrix(orc, D.n)
+    Md = D.to_original(D.minv_ddlr2(k))
+    assert np.abs(M - Md).max() / np.abs(Md).max() < 1e-10
+    U, _, Hk = orc.lowrank()
+    np.testing.assert_allclose(Hk, Hk.T, atol=1e-12)
+
+
+def test_eigenvalue_windows(small):
+    """Sec. 3.2: theta = 0 -> m+k eigenvalues of AM^-1 equal 1, the rest in
+    (0,1); thm. eigs: theta = lambda_{k+1} -> eigenvalues in
+    [1, 1 + ||A^1/2 A0^-1 E||^2/(1-theta)] with the norm <= 1/4;
+    thm. eigs2: DDLR-2 eigenvalues in (0, 1], n-s+k of them equal to 1."""
+    A, part, p, D = small
+    k = _gap_k(D.lam, 4)
+    Ad = W.to_dense(A)
+    n, m = D.n, D.m
+    orc0 = O.Oracle(A, part, p, variant=1, k=k, factor=1, theta_mode=0,
+                    lanczos_max=D.s, lanczos_eps=0.0, lanczos_check=0)
+    ev = np.sort(np.linalg.eigvals(Ad @ oracle_matrix(orc0, n)).real)
+    assert np.sum(np.abs(ev - 1) < 1e-8) == m + k
+    assert ev.min() > 0 and ev.max() < 1 + 1e-8
+    orc1 = O.Oracle(A, part, p, variant=1, k=k, factor=1, theta_mode=1,
+                    lanczos_max=D.s, lanczos_eps=0.0, lanczos_check=0)
+    ev = np.linalg.eigvals(Ad @ oracle_matrix(orc1, n)).real
+    w, V = np.linalg.eigh(Ad)
+    Ahalf = V @ np.diag(np.sqrt(w)) @ V.T
+    Y = Ahalf[np.ix_(D.perm, D.perm)] @ D.A0inv @ D.E
+    nrm2 = np.linalg.norm(Y, 2) ** 2
+    assert nrm2 <= 0.25 + 1e-12
+    bound = 1 + nrm2 / (1 - orc1.theta)
+    assert ev.min() > 1 - 1e-8 and ev.max() <= bound + 1e-8
+    orc2 = O.Oracle(A, part, p, variant=2, k=k, factor=1, lanczos_max=D.s,
+                    lanczos_eps=0.0, lanczos_check=0)
+    ev = np.linalg.eigvals(Ad @ oracle_matrix(orc2, n)).real
+    assert ev.min() > 0 and ev.max() <= 1 + 1e-8
+    assert np.sum(np.abs(ev - 1) < 1e-8) == n - D.s + k
+
+
+def test_ic0_defining_property(small):
+    """IC(0): (L L^T)_ij = (A0)_ij on the lower pattern of each block, L
+    lower-triangular in the block's elimination order, positive diagonal;
+    exact mode: L L^T = A0 everywhere."""
+    A, part, p, D = small
+    for factor, c_order in ((0, 0), (0, 1), (1, 0)):
+        orc = O.Oracle(A, part, p, variant=1, k=2, factor=factor, c_order=c_order)
+        r, c, v = orc.factor_coo()
+        n = D.n
+        L = np.zeros((n, n))
+        L[r, c] = v
+        A0 = D.to_original(D.A0)
+        LLt = L @ L.T
+        if factor == 1:
+            np.testing.assert_allclose(LLt, A0, atol=1e-12)
+        else:
+            mask = A0 != 0
+            np.testing.assert_allclose(LLt[mask], A0[mask], atol=1e-12)
+            # the pattern of L is the lower pattern of A0 in elimination order
+            assert np.all((L != 0) <= (mask | np.eye(n, dtype=bool)))
+            assert np.sum(L != 0) == (np.sum(mask) + n) // 2
+        assert np.all(np.diag(L) > 0)
+
+
+def test_ic0_equals_cholesky_in_1d():
+    """Tridiagonal blocks have no fill, so IC(0) is exact Cholesky and the
+    full-rank DDLR with IC(0) reproduces A^-1 (1-D problem)."""
+    A = W.laplacian((40,))
+    part, p = W.box_partition((40,), (4,))
+    orc = O.Oracle(A, part, p, variant=1, k=6, factor=0)
+    assert orc.s == 6
+    Ainv = np.linalg.inv(W.to_dense(A))
+    M = oracle_matrix(orc, 40)
+    assert np.abs(M - Ainv).max() / np.abs(Ainv).max() < 1e-12
+
+
+def test_worked_example_relations():
+    """Fig. SpEgs (30x30 Laplacian, 4 subdomains, k = 5): the printed bound is
+    1 + ||A^1/2 A0^-1 E||^2/(1-theta), the norm is close to 1/4 for every
+    alpha, the bound holds, and alpha = 1 gives the smallest largest
+    eigenvalue.  The printed theta values came from a METIS partition (119
+    interface nodes); box partitions give 116, so only relations are pinned."""
+    paper = [(1.0, 0.93492, 0.24996, 4.8413), (2.0, 0.93987, 0.25000, 5.1575),
+             (0.5, 0.96945, 0.24999, 9.1840)]
+    for _a, th, nr, bnd in paper:
+        assert abs(1 + nr / (1 - th) - bnd) < 2e-3 * bnd
+    A = W.laplacian((30, 30))
+    part, p = W.box_partition((30, 30), (2, 2))
+    Ad = W.to_dense(A)
+    w, V = np.linalg.eigh(Ad)
+    Ahalf = V @ np.diag(np.sqrt(w)) @ V.T
+    lmax = {}
+    for alpha in (1.0, 2.0, 0.5):
+        D = DenseDDLR(A, part, p, alpha=alpha)
+        assert D.s == 116
+        Y = Ahalf[np.ix_(D.perm, D.perm)] @ D.A0inv @ D.E
+        nrm2 = np.linalg.norm(Y, 2) ** 2
+        assert 0.24 < nrm2 <= 0.25 + 1e-12
+        orc = O.Oracle(A, part, p, variant=1, k=5, factor=1, alpha=alpha,
+                       lanczos_max=D.s, lanczos_eps=0.0, lanczos_check=0)
+        assert abs(orc.theta - D.lam[5]) < 1e-10
+        ev = np.linalg.eigvals(Ad @ oracle_matrix(orc, 900)).real
+        lmax[alpha] = ev.max()
+        assert ev.max() <= 1 + nrm2 / (1 - orc.theta) + 1e-8
+    assert lmax[1.0] < lmax[2.0] and lmax[1.0] < lmax[0.5]
+
+
+def test_pcg_matches_dense_cg():
+    """Oracle PCG vs a dense preconditioned CG written here with the dense
+    DDLR-1 M^-1 (IC(0) is replaced by exact factors on both sides)."""
+    A = W.laplacian((20, 20))
+    part, p = W.box_partition((20, 20), (2, 2))
+    D = DenseDDLR(A, part, p)
+    k = 4
+    orc = O.Oracle(A, part, p, variant=1, k=k, factor=1, lanczos_max=D.s,
+                   lanczos_eps=0.0, lanczos_check=0)
+    Mp, _ = D.minv_ddlr1(k, 1)
+    M = D.to_original(Mp)
+    Ad = W.to_dense(A)
+    b = W.rhs(D.n, 0)
+    x = np.zeros(D.n)
+    r = b.copy()
+    z = M @ r
+    pp = z.copy()
+    rz = r @ z
+    its = 0
+    while its < 500:
+        q = Ad @ pp
+        a = rz / (pp @ q)
+        x += a * pp
+        r -= a * q
+        its += 1
+        if np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b):
+            break
+        z = M @ r
+        rzn = r @ z
+        pp = z + (rzn / rz) * pp
+        rz = rzn
+    xo, its_o, rel, st = orc.pcg(b, 1e-8)
+    assert st == "OK" and abs(its_o - its) <= 1 and rel <= 1e-8
+    np.testing.assert_allclose(xo, np.linalg.solve(Ad, b), rtol=0, atol=1e-6)
+
+
+def test_scale_diag_jump_coefficients():
+    """Diagonal scaling reading: DDLR built on D^-1/2 A D^-1/2 and
+    M^-1 = D^-1/2 Mhat^-1 D^-1/2; full rank + exact factors is still A^-1."""
+    A = W.jump_coefficient_fv(8, 4, 1)
+    part, p = W.box_partition((8, 8, 8), (2, 2, 2))
+    D = DenseDDLR(A, part, p, scale_diag=True)
+    orc = O.Oracle(A, part, p, variant=1, k=D.s, factor=1, scale_diag=1)
+    Ainv = np.linalg.inv(W.to_dense(A))
+    M = oracle_matrix(orc, D.n)
+    assert np.abs(M - Ainv).max() / np.abs(Ainv).max() < 1e-11
+    orc2 = O.Oracle(A, part, p, variant=1, k=5, factor=1, scale_diag=1,
+                    lanczos_max=D.s, lanczos_eps=0.0, lanczos_check=0)
+    Md = D.to_original(D.minv_ddlr1(5, 1)[0])
+    M2 = oracle_matrix(orc2, D.n)
+    assert np.abs(M2 - Md).max() / np.abs(Md).max() < 1e-10
+
+
+def test_invalid_inputs():
+    A = W.laplacian((6, 6))
+    part, p = W.box_partition((6, 6), (2, 2))
+    n, rp, ci, va = A
+    va2 = va.copy()
+    va2[1] += 1.0     # breaks symmetry
+    with pytest.raises(O.OracleError) as e:
+        O.Oracle((n, rp, ci, va2), part, p)
+    assert e.value.status == "INVALID"
+    bad = part.copy()
+    bad[0] = p        # part out of range
+    with pytest.raises(O.OracleError):
+        O.Oracle(A, bad, p)
+    # an indefinite matrix breaks the factorisation
+    va3 = va.copy()
+    va3[rp[0]] = -10.0
+    with pytest.raises(O.OracleError) as e:
+        O.Oracle((n, rp, ci, va3), part, p)
+    assert e.value.status == "BREAKDOWN"
+
+
+def test_lanczos_convergence_rule():
+    """eq. (converge): with the default check (every 10 steps, eps 1e-4,
+    at most 5k steps) Lanczos stops at a multiple of 10 once the sum of the
+    top-k Ritz values settles; the Ritz values interlace the eigenvalues of H
+    (theta_i <= lambda_i) and the leading ones are close to eigh(H).  The 3x2
+    partition of a 25x19 grid has no repeated eigenvalues, which a
+    single-vector Lanczos run would see only once."""
+    A = W.laplacian((25, 19))
+    part, p = W.box_partition((25, 19), (3, 2))
+    D = DenseDDLR(A, part, p)
+    orc = O.Oracle(A, part, p, variant=1, k=4, factor=1)
+    assert orc.msteps % 10 == 0 and orc.msteps <= 20
+    r = orc.ritz
+    assert np.all(r[:4] <= D.lam[:4] + 1e-12)
+    np.testing.assert_allclose(r[:2], D.lam[:2], rtol=1e-4)
+    assert abs(r[:4].sum() - D.lam[:4].sum()) < 1e-2 * D.lam[:4].sum()
+    # each Ritz value lies within the spectrum of H (Cauchy interlacing)
+    assert orc.ritz.max() <= D.lam.max() + 1e-12
+    assert orc.ritz.min() >= D.lam.min() - 1e-12
