@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""DDLR-PCG benchmark on one GB300 (N replicas under torchrun).
+
+A step is one pass of the whole hot path on the 3-D 7-point Laplacian, 64^3
+grid (n = 262,144), 4x4x4 box subdomains, IC(0) local factors, DDLR-1 with
+k = 16, FP64: the device-side preconditioner build (scaling, block forming,
+batched factorisation, Lanczos with full reorthogonalisation, low-rank data)
+from values resident in HBM, then PCG from x0 = 0 to a 1e-8 true relative
+residual.  `value` is the time to solution per solve (ms, lower is better),
+over all ranks.  `e2e` repeats the step through the C ABI from host buffers
+(host CSR and b in, x out, symbolic setup included).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "lap3d_64_b4"
+OPTS = dict(variant=1, rank_k=16, factor=0, c_order=1, precision=0)
+TOL = 1e-8
+METRIC = "DDLR-PCG time to 1e-8 rel. residual (setup + solve)"
+UNIT = "ms/solve"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _config(extra=None):
+    c = {"workload": WORKLOAD, "grid": "64^3 7-point Laplacian, Dirichlet",
+         "n": 262144, "subdomains": "4x4x4 boxes (64)", "variant": "DDLR-1",
+         "rank_k": OPTS["rank_k"], "local_solver": "IC(0), natural order",
+         "c_alpha_order": "greedy multicolour", "alpha": 1.0,
+         "theta": "lambda_{k+1}", "lanczos": "<=5k steps, check every 10, eps 1e-4",
+         "tol": TOL, "rhs": "SplitMix64 seed 0, U[-1,1)",
+         "l2": "flushed (256 MiB write) before every timed step"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = os.path.join(ROOT, "paper_1505_04341_gb300", "csrc", "ddlr_kernels.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("kernels_sha") != sha:
+        return None
+    return d
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1505_04341_gb300 as pkg
+    import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.build()
+    w = W.workload(WORKLOAD)
+    A, part, p = w["A"], w["part"], w["p"]
+    n = A[0]
+    stream = torch.cuda.current_stream()
+    b_host = W.rhs(n, 0)
+    b = torch.tensor(b_host, device="cuda")
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    h = pkg.DDLR(A, part, p, **OPTS)
+
+    def step(hh, xb):
+        hh.refactor()
+        _, info = hh.pcg(b, xb, tol=TOL)
+        return info[0]
+
+    def timed_steps(hh, K):
+        ms, infos = [], []
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(hh, x))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, infos
+
+    for _ in range(args.warmup):
+        step(h, x)
+    barrier()
+    clocks = Clocks(local)
+    h.reset_counters()
+    barrier()
+    t0 = time.perf_counter()
+    ms, infos = timed_steps(h, args.steps)
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = h.counters()["launches"]
+    tot = sum(ms)
+    if ws > 1:
+        t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = float(t.item())
+    value = tot / (args.steps * ws)
+    relres = max(i["relres"] for i in infos)
+    its = [i["its"] for i in infos]
+    assert all(i["status"] == "OK" for i in infos), infos
+
+    # split of one step: setup vs solve (CUDA events on the same stream)
+    def split_once(hh):
+        flush.fill_(1.0)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        hh.refactor()
+        e1.record(stream)
+        hh.pcg(b, x, tol=TOL)
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    setup_ms, solve_ms = split_once(h)
+
+    # roofline: per-kernel-family CUDA-event timing over a second timed pass
+    h.reset_counters()
+    h.set_timing(True)
+    ms_prof, _ = timed_steps(h, max(1, min(args.steps, 3)))
+    h.set_timing(False)
+    cnt = h.counters()
+    tr = h.traffic()
+    fams = cnt["families"]
+    dom = max((f for f in fams if fams[f]["launches"] > 0), key=lambda f: fams[f]["ms"])
+    dom_ms = fams[dom]["ms"] / fams[dom]["launches"]
+    dom_bytes = tr["family_bytes"].get(dom, 0.0)
+    peak, peak_kind = _peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes > 0 else None
+    prof = _traffic_from_profile()
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind + " HBM copy bandwidth", "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "algorithmic_bytes_per_launch": dom_bytes,
+            "avg_launch_us": dom_ms * 1e3,
+            "traffic": (prof.get("dram_bytes_per_launch", {}).get(dom) if prof else None)}
+    families = {f: dict(ms=round(v["ms"], 4), launches=v["launches"],
+                        share=round(v["ms"] / max(1e-9, sum(u["ms"] for u in fams.values())), 4),
+                        gbs=(round(tr["family_bytes"].get(f, 0) * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
+                             if v["ms"] > 0 and tr["family_bytes"].get(f, 0) > 0 else None))
+                for f, v in sorted(fams.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # M^-1 apply throughput (device vectors, K back-to-back applies)
+    def apply_rate(hh, reps=20):
+        y = torch.empty_like(b)
+        for _ in range(3):
+            hh.apply(b, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hh.apply(b, y)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        return t, hh.traffic()["apply_bytes"] / (t * 1e-3) / 1e9
+
+    apply_ms, apply_gbs = apply_rate(h)
+
+    # mixed precision form of the same step (FP32 factors/solves, BF16 U_k,
+    # FP64 flexible CG outer loop)
+    hm = pkg.DDLR(A, part, p, **dict(OPTS, precision=1, uk_bf16=1))
+    for _ in range(2):
+        step(hm, x)
+    ms_mixed, inf_mixed = timed_steps(hm, args.steps)
+    x_mixed = x.clone()
+    mixed_apply_ms, mixed_apply_gbs = apply_rate(hm)
+    hm.close()
+    # DDLR-2 on the same problem
+    h2 = pkg.DDLR(A, part, p, **dict(OPTS, variant=2))
+    step(h2, x)
+    ms_v2, inf_v2 = timed_steps(h2, 1)
+    v2_apply_ms, v2_apply_gbs = apply_rate(h2)
+    h2.close()
+
+    # end to end through the C ABI from host buffers
+    e2e_ms = []
+    for i in range(args.steps + 1):
+        t0 = time.perf_counter()
+        he = pkg.DDLR(A, part, p, **OPTS)
+        xh, _ = he.pcg(b_host, tol=TOL)
+        dt = (time.perf_counter() - t0) * 1e3
+        he.close()
+        if i > 0:
+            e2e_ms.append(dt)
+    e2e = statistics.mean(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e = float(t.item()) / ws
+    h2d = (A[1].nbytes + A[2].nbytes + A[3].nbytes + part.nbytes + b_host.nbytes)
+    d2h = b_host.nbytes
+    info = h.info()
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generators, no dataset)",
+        "config": _config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk,
+        "detail": {
+            "iterations": its, "true_relres_max": relres,
+            "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
+            "lanczos_steps": info["lanczos_steps"], "theta": info["theta"],
+            "fill_ratio": round(info["fill_ratio"], 3), "levels_interior": info["levels_interior"],
+            "levels_c": info["levels_c"], "wall_s": round(wall, 3),
+            "apply_fp64": {"ms": round(apply_ms, 4), "algorithmic_GBps": round(apply_gbs, 1),
+                           "bytes": tr["apply_bytes"]},
+            "kernel_families": families,
+            "mixed_fp32_bf16": {"ms_per_solve": round(statistics.mean(ms_mixed), 3),
+                                "iterations": [i["its"] for i in inf_mixed],
+                                "true_relres_max": max(i["relres"] for i in inf_mixed),
+                                "speedup_vs_fp64": round(value / statistics.mean(ms_mixed), 3),
+                                "apply_ms": round(mixed_apply_ms, 4),
+                                "apply_algorithmic_GBps": round(mixed_apply_gbs, 1)},
+            "ddlr2_fp64": {"ms_per_solve": round(statistics.mean(ms_v2), 3),
+                           "iterations": [i["its"] for i in inf_v2],
+                           "apply_ms": round(v2_apply_ms, 4),
+                           "apply_algorithmic_GBps": round(v2_apply_gbs, 1)},
+        },
+    }
+    del x_mixed
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    h.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_step():
+    import oracle
+    import workloads as W
+    w = W.workload(WORKLOAD)
+    A, part, p = w["A"], w["part"], w["p"]
+    b = W.rhs(A[0], 0)
+    t0 = time.perf_counter()
+    orc = oracle.Oracle(A, part, p, variant=1, k=OPTS["rank_k"], factor=0, c_order=1)
+    x, its, rel, st = orc.pcg(b, TOL)
+    dt = (time.perf_counter() - t0) * 1e3
+    assert st == "OK"
+    return dt, its, rel
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands (single-threaded C) on the host cores: one
+    full setup + PCG solve of the same workload (about 5-15 s)."""
+    dt, its, rel = _oracle_step()
+    return {"value": round(dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 full DDLR-1 setup + PCG solve of {WORKLOAD} (its={its})",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        _oracle_step()
+    ms = []
+    for _ in range(args.steps):
+        dt, its, rel = _oracle_step()
+        ms.append(dt)
+    v = statistics.mean(ms)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT,
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators, no dataset)",
+           "config": _config({"impl": "FP64 CPU oracle (plain C, single thread)"}),
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"full DDLR-1 setup + PCG solve of {WORKLOAD} per step"},
+           "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

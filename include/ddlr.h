@@ -1,0 +1,202 @@
+/*
+ * ddlr.h -- C ABI of the GB300 (sm_103a) DDLR preconditioner library.
+ *
+ * DDLR (Li & Saad, "Low-rank correction methods for algebraic domain
+ * decomposition preconditioners") splits a sparse SPD matrix, reordered with
+ * all interior unknowns first and all interface unknowns last (Sec. 2.2,
+ * eq. Bmat), as A = A0 - E E^T with E = [a^-1 Ehat ; -a I] and
+ * A0 = blkdiag(B_{1,a}, ..., B_{p,a}, C_a) (Sec. 3.1, eq. EF and eq. split),
+ * and preconditions CG with the Sherman-Morrison-Woodbury based
+ *   DDLR-1: M^-1 = A0^-1 + (A0^-1 E) G_{k,theta}^-1 (E^T A0^-1)
+ *           (Sec. 3.2, eq. Mprec with prop. gkt, applied by Algorithm 1), or
+ *   DDLR-2: M^-1 = A0^-1 + U_k H_k U_k^T   (Sec. 3.3, eq. Form2a),
+ * where the rank-k data come from Lanczos with full reorthogonalisation
+ * (Sec. 4.4).
+ *
+ * Conventions for every call:
+ *  - Matrices are passed as full symmetric CSR (both triangles), int32 row
+ *    pointers and column indices, strictly ascending columns in each row,
+ *    float64 values, in the caller's ORIGINAL ordering.  The library copies what
+ *    it needs; the caller keeps ownership of every array it passes.
+ *  - Vectors are float64, original ordering, column-major n x nrhs with leading
+ *    dimension ld >= n.  A vector pointer may be device memory (then the call is
+ *    asynchronous on the handle's stream, except where noted) or host memory
+ *    (pageable or pinned; detected with cudaPointerGetAttributes, staged through
+ *    device buffers, and the call returns when the result is in host memory).
+ *  - The handle owns all of its device memory until ddlr_destroy.  A handle is
+ *    not thread-safe: use one handle per thread or serving slot.
+ *  - No C++ exception crosses the ABI.  Every call returns a ddlr_status; the
+ *    text of the last error is available from ddlr_last_error.
+ */
+#ifndef DDLR_H
+#define DDLR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddlr_ctx *ddlr_handle;
+
+typedef enum {
+  DDLR_OK = 0,
+  DDLR_ERR_INVALID = 1,    /* bad argument, malformed or non-symmetric CSR   */
+  DDLR_ERR_OOM = 2,        /* device or host allocation failed                */
+  DDLR_ERR_BREAKDOWN = 3,  /* non-positive pivot in a local factorisation     */
+  DDLR_ERR_NOT_SPD = 4,    /* prop. spd-1 / spd-2 check failed (Sec. 5)       */
+  DDLR_ERR_NOCONV = 5,     /* PCG did not reach tol within maxit ('F', Sec. 5) */
+  DDLR_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up              */
+  DDLR_ERR_NAN = 7,        /* NaN or Inf met in a residual or a Lanczos step  */
+  DDLR_ERR_CUDA = 8        /* a CUDA runtime call failed                      */
+} ddlr_status;
+
+typedef struct {
+  int variant;             /* 1 = DDLR-1 (Sec. 3.2), 2 = DDLR-2 (Sec. 3.3)         */
+  int rank_k;              /* k >= 1, k <= s (k = s gives M^-1 = A^-1 with exact
+                              local factors, eq. split3)                          */
+  double alpha;            /* splitting parameter a of eq. EF; default 1 (Sec. 5) */
+  int theta_mode;          /* DDLR-1: 1 = theta = lambda_{k+1} (default, Sec. 5),
+                              0 = theta = 0 (eq. Lambda-1)                         */
+  int factor;              /* local solver: 0 = IC(0) on the block pattern,
+                              1 = exact Cholesky (IC on the symbolic fill pattern) */
+  int c_order;             /* elimination order of C_a: 0 = ascending original
+                              index, 1 = greedy multicolour (2 colours on grids)   */
+  int precision;           /* 0 = FP64 throughout; 1 = mixed: FP32 factors and
+                              triangular solves, FP32/BF16 U_k, inside an FP64
+                              flexible CG                                          */
+  int uk_bf16;             /* precision 1 only: 1 = U_k stored in BF16            */
+  int scale_diag;          /* 1 = build DDLR on D^-1/2 A D^-1/2, D = diag(A)      */
+  int lanczos_max;         /* maximum Lanczos steps; 0 = 5k (Sec. 5)              */
+  int lanczos_check;       /* convergence check period; default 10 (Sec. 5)       */
+  double lanczos_eps;      /* tolerance of eq. converge; default 1e-4 (Sec. 5)    */
+  unsigned long long seed; /* SplitMix64 stream of the Lanczos start vector       */
+  int max_nrhs;            /* largest nrhs used with this handle (workspace)      */
+} ddlr_options;
+
+typedef struct {
+  int n, p, s, m, k, variant, precision;
+  int lanczos_steps;       /* m of Sec. 4.4 (steps actually taken)                */
+  int ncolors;             /* colours of C_a (c_order 1), else 0                  */
+  int levels_interior;     /* max dependency levels of an interior block factor   */
+  int levels_c;            /* dependency levels of the C_a factor                 */
+  double theta;            /* theta used in G_{k,theta}^-1 (DDLR-1)               */
+  double lambda_max;       /* largest Ritz value (DDLR-1; must be < 1)            */
+  long long nnz_a;         /* nnz(A)                                              */
+  long long nnz_factor;    /* stored factor entries incl. diagonals, all blocks   */
+  long long nnz_ehat;      /* nnz(Ehat)                                           */
+  double fill_ratio;       /* nnz(preconditioner)/nnz(A) as in Sec. 5             */
+  long long device_bytes;  /* device memory held by the handle                    */
+  double setup_ms;         /* wall time of the last (re)setup                     */
+} ddlr_info;
+
+typedef struct {
+  int its;                 /* iterations (x updates)                              */
+  double relres;           /* true relative residual ||b - A x|| / ||b||          */
+  int status;              /* DDLR_OK, DDLR_ERR_NOCONV or DDLR_ERR_NAN            */
+} ddlr_solve_info;
+
+/* Fills *opt with the defaults named above (variant 1, k 16, alpha 1,
+ * theta_mode 1, IC(0), c_order 0, FP64, lanczos 5k/10/1e-4, seed 0, max_nrhs 1).
+ * Returns DDLR_ERR_INVALID for a NULL pointer. */
+ddlr_status ddlr_options_default(ddlr_options *opt);
+
+/* Build the preconditioner (Sec. 4.1): classify nodes (Sec. 2.1), reorder
+ * (eq. Bmat), form B_{i,a} = B_i + a^-2 E_i E_i^T and C_a = C + a^2 I
+ * (eq. split), factor all p+1 blocks on the GPU, run Lanczos on the GPU
+ * (Sec. 4.4) and form the low-rank data.
+ *   n, rowptr[n+1], colind[nnz], val[nnz]: A, host memory, original order.
+ *   part[n]: subdomain of each node, values in [0, p), host memory.
+ *   opt: options (NULL = defaults).  cuda_stream: cudaStream_t or NULL for the
+ *   legacy default stream.  *out receives the handle (NULL on failure).
+ * Synchronous.  Errors: INVALID (malformed input, k > s, no interface nodes),
+ * OOM, BREAKDOWN, NOT_SPD, NAN, CUDA. */
+ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind,
+                       const double *val, const int *part, int p,
+                       const ddlr_options *opt, void *cuda_stream,
+                       ddlr_handle *out);
+
+/* Numeric re-setup with the same sparsity pattern and partition: optional new
+ * values val[nnz] (host or device memory, original CSR order; NULL keeps the
+ * resident values), then the device-side part of ddlr_setup (scaling, block
+ * forming, factorisation, Lanczos, low-rank data).  Synchronous. */
+ddlr_status ddlr_refactor(ddlr_handle h, const double *val);
+
+/* y = M^-1 x (Algorithm 1 for DDLR-1, eq. Form2a for DDLR-2) for nrhs vectors.
+ * x and y must not overlap.  Errors: INVALID (nrhs < 1, ld < n, NULL). */
+ddlr_status ddlr_apply(ddlr_handle h, const double *x, double *y, int nrhs,
+                       int ld);
+
+/* y = A0^-1 x: the p local solves with B_{i,a} and the solve with C_a that
+ * Algorithm 1 performs twice per application (Sec. 4.2). */
+ddlr_status ddlr_a0_solve(ddlr_handle h, const double *x, double *y, int nrhs,
+                          int ld);
+
+/* Preconditioned CG from x0 = 0 (Sec. 5) for each of nrhs right-hand sides,
+ * stopping when ||r|| <= tol ||b|| and the true residual confirms it (else r is
+ * replaced by b - A x and CG restarts), or after maxit iterations (maxit <= 0:
+ * 500, Sec. 5).  With precision 1 the outer loop is flexible CG in FP64 around
+ * the FP32 preconditioner.  info[nrhs] (host memory, may be NULL) receives the
+ * per-RHS result.  Synchronous.  Returns DDLR_OK when every RHS converged,
+ * else DDLR_ERR_NOCONV or DDLR_ERR_NAN. */
+ddlr_status ddlr_pcg(ddlr_handle h, const double *b, double *x, int nrhs,
+                     int ld, double tol, int maxit, ddlr_solve_info *info);
+
+/* Sizes, counts and scalars of the handle (host struct). */
+ddlr_status ddlr_get_info(ddlr_handle h, ddlr_info *info);
+
+/* The Lanczos Ritz values (all m of T_m, descending) into out[cap] (host);
+ * *count receives m. */
+ddlr_status ddlr_get_ritz(ddlr_handle h, double *out, int cap, int *count);
+
+/* The local factor entries (lower triangle incl. diagonal, every block) as
+ * (row, col, value) in ORIGINAL indices.  With rows == NULL only *nnz is set.
+ * Host arrays of length *nnz.  Synchronous. */
+ddlr_status ddlr_get_factor_coo(ddlr_handle h, long long *nnz, int *rows,
+                                int *cols, double *vals);
+
+/* Low-rank data, host memory.  U is urows x k row-major with rows in ascending
+ * original index of the nodes it covers (the s interface nodes for DDLR-1, all
+ * n nodes for DDLR-2); lam[k] = Lambda_k (DDLR-1), theta (DDLR-1), Hk[k*k]
+ * (DDLR-2).  Any output pointer may be NULL.  Synchronous. */
+ddlr_status ddlr_get_lowrank(ddlr_handle h, double *U, double *lam,
+                             double *theta, double *Hk);
+
+/* Replace the low-rank data (same layout as ddlr_get_lowrank, host memory):
+ * checkpoint restore, or injection of reference data for parity checks.
+ * lam/theta are used by DDLR-1, Hk by DDLR-2.  Synchronous. */
+ddlr_status ddlr_set_lowrank(ddlr_handle h, const double *U, const double *lam,
+                             double theta, const double *Hk);
+
+/* Kernel accounting: number of library kernel launches since the last reset,
+ * and per-family device time accumulated with CUDA events recorded on the
+ * launching stream while timing is enabled (ddlr_set_timing).  names receives
+ * a comma-separated list of families (cap bytes), ms[cap_f] and launches[cap_f]
+ * their totals.  Host memory. */
+ddlr_status ddlr_set_timing(ddlr_handle h, int enable);
+ddlr_status ddlr_get_counters(ddlr_handle h, long long *launches, char *names,
+                              int cap, double *ms, long long *family_launches,
+                              int cap_f, int *nfamilies);
+ddlr_status ddlr_reset_counters(ddlr_handle h);
+
+/* Algorithmic bytes (single RHS, int32 indices, each factor value and index
+ * read once per sweep, vectors read and written once, gathered vector reads
+ * counted as cache hits) of one M^-1 apply and of one A0 solve, and, per kernel
+ * family of ddlr_get_counters (same order, cap_f entries), the bytes one launch
+ * of that family moves on average (0 where not accounted).  Host memory. */
+ddlr_status ddlr_get_traffic(ddlr_handle h, double *apply_bytes,
+                             double *a0_solve_bytes, double *family_bytes,
+                             int cap_f);
+
+/* Use another stream (cudaStream_t) for later calls. */
+ddlr_status ddlr_set_stream(ddlr_handle h, void *cuda_stream);
+
+/* Text of the last error on this handle; with h == NULL, of the last failed
+ * ddlr_setup on this thread.  Never NULL. */
+const char *ddlr_last_error(ddlr_handle h);
+
+/* Frees every device and host resource of the handle (NULL is a no-op). */
+ddlr_status ddlr_destroy(ddlr_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDLR_H */

@@ -750,9 +750,9 @@ static void apply_new(oracle *o, const double *x, double *u) {
     double *y = (double *)malloc(sizeof(double) * (size_t)s);
     double *wv = (double *)malloc(sizeof(double) * (size_t)s);
     double *v = (double *)malloc(sizeof(double) * (size_t)n);
-    a0_solve(o, x, z);                                  /* 1: A0 z = x */
-    et_mult(o, z, y);                                   /* 2: y = E^T z */
-    double it = 1.0 / (1.0 - o->theta);                 /* 3: w = G_{k,theta}^-1 y */
+    a0_solve(o, x, z);                                  /* A0 z = x */
+    et_mult(o, z, y);                                   /* y = E^T z */
+    double it = 1.0 / (1.0 - o->theta);                 /* w = G_{k,theta}^-1 y */
     for (int c = 0; c < k; c++) {
       double acc = 0.0;
       for (int r = 0; r < s; r++) acc += o->U[(size_t)r * k + c] * y[r];
@@ -763,9 +763,9 @@ static void apply_new(oracle *o, const double *x, double *u) {
       for (int c = 0; c < k; c++) acc += o->U[(size_t)r * k + c] * t[c];
       wv[r] = it * y[r] + acc;
     }
-    e_mult(o, wv, v);                                   /* 4: v = E w */
+    e_mult(o, wv, v);                                   /* v = E w */
     for (int i = 0; i < n; i++) v[i] += x[i];
-    a0_solve(o, v, u);                                  /* 5: A0 u = x + v */
+    a0_solve(o, v, u);                                  /* A0 u = x + v */
     free(y); free(wv); free(v);
   } else {
     /* eq. (Form2a): u = A0^-1 x + U_k H_k U_k^T x */

@@ -1,0 +1,1102 @@
+// ddlr_api.cu -- C ABI of the DDLR library: setup, A0 solve, M^-1 apply,
+// Lanczos and PCG orchestration on one GB300 (sm_103a).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "ddlr.h"
+#include "ddlr_kernels.cuh"
+#include "ddlr_plan.h"
+
+using namespace ddlr;
+
+namespace {
+
+struct Fail {
+  ddlr_status st;
+  std::string msg;
+};
+
+inline void ck(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) throw Fail{DDLR_ERR_OOM, std::string(what) + ": out of device memory"};
+    throw Fail{DDLR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+inline unsigned nblk(long long n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// SplitMix64 (Steele, Lea & Flood 2014): output i of the stream `seed`
+inline double sm64_pm1(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return 2.0 * (double(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+thread_local std::string g_setup_error;
+
+}  // namespace
+
+struct ddlr_ctx {
+  ddlr_options opt{};
+  cudaStream_t stream = nullptr;   // caller's stream
+  cudaStream_t stream2 = nullptr;  // C_a solve branch (forked with events)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  Plan P;
+  std::string err;
+  std::vector<void *> allocs;
+  long long dev_bytes = 0;
+
+  // plan arrays on the device
+  int *perm = nullptr;
+  int *a_soff = nullptr, *a_sw = nullptr, *a_col = nullptr, *a_src = nullptr;
+  int *eh_rp = nullptr, *eh_ci = nullptr, *eh_src = nullptr;
+  int *eht_rp = nullptr, *eht_ci = nullptr, *eht_src = nullptr;
+  int *f_rp = nullptr, *f_ci = nullptr, *f_row = nullptr, *f_src = nullptr;
+  int *f_prp = nullptr, *f_pa = nullptr, *f_pb = nullptr;
+  unsigned char *f_cdiag = nullptr;
+  int *fl_rows = nullptr;
+  int *map_l = nullptr, *map_u = nullptr;
+  int *orow = nullptr, *ocol = nullptr, *diag_pos = nullptr;
+  SolveLayout S{};
+  // numeric data
+  double *val = nullptr;      // caller's values (original CSR order)
+  double *vals = nullptr;     // scaled values (alias of val without scaling)
+  double *dsc = nullptr;      // D^-1/2 in ORIGINAL order (scale_diag)
+  double *dsc_dev = nullptr;  // D^-1/2 in device order
+  double *a_val = nullptr;    // A (unscaled) in sliced ELL, device order
+  double *fval = nullptr;     // factor values (CSR)
+  double *l64 = nullptr, *u64 = nullptr, *dinv64 = nullptr, *eh64 = nullptr, *eht64 = nullptr;
+  float *l32 = nullptr, *u32 = nullptr, *dinv32 = nullptr, *eh32 = nullptr, *eht32 = nullptr;
+  // low-rank data (device order)
+  int urows = 0;
+  double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
+  float *U32 = nullptr, *coef32 = nullptr, *Hk32 = nullptr, *inv1mt32 = nullptr;
+  __nv_bfloat16 *Ub16 = nullptr;
+  std::vector<double> ritz;
+  int msteps = 0;
+  double theta = 0.0;
+  int *dflag = nullptr;       // device error flags [0]=breakdown [1]=notspd [2]=eig fail
+  // workspaces
+  double *w64[8] = {nullptr};
+  float *w32[8] = {nullptr};
+  double *part64 = nullptr;
+  float *part32 = nullptr;
+  PcgState *pcg = nullptr;
+  double *pv[8] = {nullptr};
+  double *stg_in = nullptr, *stg_out = nullptr;  // staging of host vector arguments
+  double *h_pin = nullptr;    // pinned host scratch
+  // accounting
+  long long launches = 0;
+  bool timing = false;
+  struct Rec { int fam; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::string> fam_names;
+  std::map<std::string, int> fam_idx;
+  std::vector<double> fam_ms;
+  std::vector<long long> fam_cnt;
+  double setup_ms = 0;
+
+  template <typename T>
+  T *alloc(size_t n) {
+    if (n == 0) n = 1;
+    void *p = nullptr;
+    ck(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
+    allocs.push_back(p);
+    dev_bytes += (long long)(n * sizeof(T));
+    return (T *)p;
+  }
+  template <typename T>
+  T *upload(const std::vector<T> &v) {
+    T *d = alloc<T>(v.size());
+    if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream), "upload");
+    return d;
+  }
+  void release() {
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    dev_bytes = 0;
+  }
+
+  // ---- launch accounting
+  int fam(const char *name) {
+    auto it = fam_idx.find(name);
+    if (it != fam_idx.end()) return it->second;
+    int id = int(fam_names.size());
+    fam_names.push_back(name);
+    fam_ms.push_back(0.0);
+    fam_cnt.push_back(0);
+    fam_idx[name] = id;
+    return id;
+  }
+  cudaEvent_t get_ev() {
+    if (evpool.empty()) resolve();
+    if (evpool.empty()) {
+      cudaEvent_t e;
+      ck(cudaEventCreate(&e), "cudaEventCreate");
+      return e;
+    }
+    cudaEvent_t e = evpool.back();
+    evpool.pop_back();
+    return e;
+  }
+  void resolve() {
+    if (pending.empty()) return;
+    for (auto &r : pending) {
+      cudaEventSynchronize(r.b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      fam_ms[r.fam] += ms;
+      evpool.push_back(r.a);
+      evpool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  struct Scope {
+    ddlr_ctx *c; int f; cudaStream_t s; cudaEvent_t a = nullptr;
+    Scope(ddlr_ctx *c_, const char *name, cudaStream_t s_) : c(c_), f(c_->fam(name)), s(s_) {
+      c->launches++;
+      c->fam_cnt[f]++;
+      if (c->timing) { a = c->get_ev(); cudaEventRecord(a, s); }
+    }
+    ~Scope() {
+      if (c->timing) {
+        cudaEvent_t b = c->get_ev();
+        cudaEventRecord(b, s);
+        c->pending.push_back({f, a, b});
+        if (c->pending.size() > 4096) c->resolve();
+      }
+    }
+  };
+};
+
+#define KL(ctx, name, strm, kern, grid, block, smem, ...)                      \
+  do {                                                                          \
+    ddlr_ctx::Scope _sc((ctx), (name), (strm));                                 \
+    kern<<<(grid), (block), (smem), (strm)>>>(__VA_ARGS__);                     \
+  } while (0)
+
+namespace {
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const double *l(ddlr_ctx *c) { return c->l64; }
+  static const double *u(ddlr_ctx *c) { return c->u64; }
+  static const double *dinv(ddlr_ctx *c) { return c->dinv64; }
+  static const double *eh(ddlr_ctx *c) { return c->eh64; }
+  static const double *eht(ddlr_ctx *c) { return c->eht64; }
+  static double *w(ddlr_ctx *c, int i) { return c->w64[i]; }
+  static double *part(ddlr_ctx *c) { return c->part64; }
+  static const double *coef(ddlr_ctx *c) { return c->coef64; }
+  static const double *inv1mt(ddlr_ctx *c) { return c->inv1mt64; }
+  static const double *Hk(ddlr_ctx *c) { return c->Hk64; }
+};
+template <> struct Prec<float> {
+  static const float *l(ddlr_ctx *c) { return c->l32; }
+  static const float *u(ddlr_ctx *c) { return c->u32; }
+  static const float *dinv(ddlr_ctx *c) { return c->dinv32; }
+  static const float *eh(ddlr_ctx *c) { return c->eh32; }
+  static const float *eht(ddlr_ctx *c) { return c->eht32; }
+  static float *w(ddlr_ctx *c, int i) { return c->w32[i]; }
+  static float *part(ddlr_ctx *c) { return c->part32; }
+  static const float *coef(ddlr_ctx *c) { return c->coef32; }
+  static const float *inv1mt(ddlr_ctx *c) { return c->inv1mt32; }
+  static const float *Hk(ddlr_ctx *c) { return c->Hk32; }
+};
+
+// ----------------------------------------------------------- A0 solve
+// z = A0^-1 x in device order: all interior blocks in one launch (CTA per
+// block) on the main stream, the C_a levels on the second stream.
+template <typename T>
+void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
+  const Plan &P = c->P;
+  const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  ck(cudaEventRecord(c->ev_fork, c->stream), "event");
+  ck(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0), "wait");
+  if (P.p > 0)
+    KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks<T, 256>), P.p, 256, 0,
+       c->S, lv, uv, di, x, z, gate);
+  const int l0 = P.blk_lvl0[P.p], l1 = P.blk_lvl0[P.p + 1];
+  for (int l = l0; l < l1; l++) {
+    const int mode = (l == l1 - 1) ? 2 : 0;
+    KL(c, "sptrsv_c", c->stream2, k_sptrsv_level<T>, nblk(P.lvl_nrows[l]), kThreads, 0,
+       c->S, l, mode, lv, uv, di, x, z, gate);
+  }
+  for (int l = l1 - 2; l >= l0; l--)
+    KL(c, "sptrsv_c", c->stream2, k_sptrsv_level<T>, nblk(P.lvl_nrows[l]), kThreads, 0,
+       c->S, l, 1, lv, uv, di, x, z, gate);
+  ck(cudaEventRecord(c->ev_join, c->stream2), "event");
+  ck(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "wait");
+}
+
+// ----------------------------------------------------------- M^-1 apply
+// u = M^-1 x in device order.  DDLR-1: Algorithm 1 with prop. gkt;
+// DDLR-2: eq. Form2a.  Uses workspaces 0..3 of precision T.
+template <typename T, typename TU>
+void apply_dev(ddlr_ctx *c, const TU *U, const T *x, T *u, const int *gate) {
+  const Plan &P = c->P;
+  const int n = P.n, m = P.m, s = P.s, k = c->opt.rank_k;
+  const T a = T(c->opt.alpha), ia = T(1.0 / c->opt.alpha);
+  T *part = Prec<T>::part(c);
+  if (c->opt.variant == 1) {
+    T *z = Prec<T>::w(c, 0), *y = Prec<T>::w(c, 1), *w = Prec<T>::w(c, 2), *rhs = Prec<T>::w(c, 3);
+    T *t = Prec<T>::w(c, 4);
+    a0_solve<T>(c, x, z, gate);                                      // A0 z = x
+    KL(c, "et", c->stream, k_et<T>, nblk(s), kThreads, 0,            // y = E^T z
+       s, m, c->eht_rp, c->eht_ci, Prec<T>::eht(c), ia, a, z, y, gate);
+    KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0,
+       s, k, U, y, part, gate);                                      // t = D U^T y
+    KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
+       kRedGrid, k, part, Prec<T>::coef(c), (const T *)nullptr, t, gate);
+    KL(c, "w_rhs", c->stream, (k_w_rhs<T, TU>), nblk(s), kThreads, k * sizeof(T),
+       s, m, k, U, t, y, Prec<T>::inv1mt(c), a, x, w, rhs, gate);    // w, x_C - a w
+    KL(c, "e_int", c->stream, k_e_interior<T>, nblk(m), kThreads, 0,
+       m, c->eh_rp, c->eh_ci, Prec<T>::eh(c), ia, w, x, rhs, gate);   // x_B + a^-1 Ehat w
+    a0_solve<T>(c, rhs, u, gate);                                    // A0 u = x + v
+  } else {
+    T *t = Prec<T>::w(c, 4);
+    a0_solve<T>(c, x, u, gate);
+    KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0,
+       n, k, U, x, part, gate);
+    KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
+       kRedGrid, k, part, (const T *)nullptr, Prec<T>::Hk(c), t, gate);
+    KL(c, "u_add", c->stream, (k_u_add<T, TU>), nblk(n), kThreads, k * sizeof(T),
+       n, k, U, t, u, gate);
+  }
+}
+
+// preconditioner on FP64 vectors in device order (scaled system handled here)
+void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
+  const int n = c->P.n;
+  const double *rin = r;
+  if (c->dsc_dev) {
+    KL(c, "vec", c->stream, k_mulv_t<double>, nblk(n), kThreads, 0, (long long)n, c->dsc_dev, r, c->w64[6], gate);
+    rin = c->w64[6];
+  }
+  if (c->opt.precision == 0) {
+    apply_dev<double, double>(c, c->U64, rin, z, gate);
+  } else {
+    float *r32 = c->w32[6], *z32 = c->w32[7];
+    KL(c, "vec", c->stream, (k_cast<float, double>), nblk(n), kThreads, 0, (long long)n, rin, r32, gate);
+    if (c->opt.uk_bf16) apply_dev<float, __nv_bfloat16>(c, c->Ub16, r32, z32, gate);
+    else apply_dev<float, float>(c, c->U32, r32, z32, gate);
+    KL(c, "vec", c->stream, (k_cast<double, float>), nblk(n), kThreads, 0, (long long)n, z32, z, gate);
+  }
+  if (c->dsc_dev)
+    KL(c, "vec", c->stream, k_mulv_t<double>, nblk(n), kThreads, 0, (long long)n, c->dsc_dev, z, z, gate);
+}
+
+// ------------------------------------------------------------- Lanczos
+// Lanczos operator (Sec. 4.4): DDLR-1 w = E^T A0^-1 E q; DDLR-2 E^T A0^-2 E q.
+void lanczos_op(ddlr_ctx *c, const double *q, double *w) {
+  const Plan &P = c->P;
+  const int n = P.n, m = P.m, s = P.s;
+  const double a = c->opt.alpha, ia = 1.0 / a;
+  double *v = c->w64[0], *z = c->w64[1];
+  KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0,
+     m, s, c->eh_rp, c->eh_ci, c->eh64, ia, a, q, (const double *)nullptr, v, (const int *)nullptr);
+  a0_solve<double>(c, v, z, nullptr);
+  if (c->opt.variant == 2) {
+    a0_solve<double>(c, z, v, nullptr);
+    std::swap(v, z);
+  }
+  KL(c, "et", c->stream, k_et<double>, nblk(s), kThreads, 0,
+     s, m, c->eht_rp, c->eht_ci, c->eht64, ia, a, z, w, (const int *)nullptr);
+}
+
+void cgs2(ddlr_ctx *c, int s, int ncol, const double *Q, double *w, double *cvec) {
+  for (int pass = 0; pass < 2; pass++) {
+    KL(c, "lanczos", c->stream, k_gemvT_partial<256>, kRedGrid, 256, 0,
+       s, ncol, Q, (long long)s, w, c->part64);
+    KL(c, "lanczos", c->stream, k_reduce_cols<double>, 1, 256, ncol * sizeof(double),
+       kRedGrid, ncol, c->part64, (const double *)nullptr, (const double *)nullptr, cvec,
+       (const int *)nullptr);
+    KL(c, "lanczos", c->stream, k_gemvN_sub, nblk(s), kThreads, ncol * sizeof(double),
+       s, ncol, Q, (long long)s, cvec, w);
+  }
+}
+
+void dot_to(ddlr_ctx *c, long long n, const double *a, const double *b, double *out, int do_sqrt) {
+  KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, n, a, b, c->part64,
+     (const int *)nullptr);
+  KL(c, "dot", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, out, do_sqrt,
+     (const int *)nullptr);
+}
+
+void sync(ddlr_ctx *c) { ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"); }
+
+void read_dev(ddlr_ctx *c, void *h, const void *d, size_t bytes) {
+  ck(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H");
+  sync(c);
+}
+
+ddlr_status run_lanczos(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int s = P.s, n = P.n, m0 = P.m, k = c->opt.rank_k;
+  int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
+  mmax = std::min(mmax, s);
+  mmax = std::max(mmax, k);
+  const int check = c->opt.lanczos_check;
+  const double eps = c->opt.lanczos_eps;
+  std::vector<void *> tmp;
+  auto talloc = [&](size_t bytes) {
+    void *p = nullptr;
+    ck(cudaMalloc(&p, bytes), "cudaMalloc");
+    tmp.push_back(p);
+    return p;
+  };
+  ddlr_status st = DDLR_OK;
+  try {
+    double *Q = (double *)talloc(sizeof(double) * size_t(s) * size_t(mmax + 1));
+    double *al = (double *)talloc(sizeof(double) * (mmax + 1));
+    double *be = (double *)talloc(sizeof(double) * (mmax + 1));
+    double *cvec = (double *)talloc(sizeof(double) * (mmax + 2));
+    double *w = (double *)talloc(sizeof(double) * s);
+    double *nrm = (double *)talloc(sizeof(double) * 4);
+    double *ed = (double *)talloc(sizeof(double) * mmax);
+    double *ee = (double *)talloc(sizeof(double) * mmax);
+    double *eZ = (double *)talloc(sizeof(double) * size_t(mmax) * mmax);
+    double *erot = (double *)talloc(sizeof(double) * 2 * mmax);
+    double *evals = (double *)talloc(sizeof(double) * mmax);
+    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * mmax);
+    double *esum = (double *)talloc(sizeof(double) * 2);
+    ck(cudaMemsetAsync(be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
+    // start vector: SplitMix64 stream `seed + restart`, drawn for the interface
+    // nodes in ascending original index, normalised
+    std::vector<int> rank(s);
+    {
+      std::vector<std::pair<int, int>> o(s);
+      for (int j = 0; j < s; j++) o[j] = {P.perm[m0 + j], j};
+      std::sort(o.begin(), o.end());
+      for (int r = 0; r < s; r++) rank[o[r].second] = r;
+    }
+    auto rand_vec = [&](uint64_t stream_id, std::vector<double> &v, bool normalise) {
+      std::vector<double> byrank(s);
+      for (int r = 0; r < s; r++) byrank[r] = sm64_pm1(stream_id, (uint64_t)r);
+      double nn = 0;
+      for (int r = 0; r < s; r++) nn += byrank[r] * byrank[r];
+      nn = std::sqrt(nn);
+      v.resize(s);
+      for (int j = 0; j < s; j++) v[j] = normalise ? byrank[rank[j]] / nn : byrank[rank[j]];
+    };
+    uint64_t restart = 0;
+    std::vector<double> hv;
+    rand_vec(c->opt.seed + restart, hv, true);
+    ck(cudaMemcpyAsync(Q, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+    double scale = 0.0;
+    int mm = 0;
+    double ab[2];
+    for (int j = 0; j < mmax; j++) {
+      double *q = Q + size_t(j) * s;
+      lanczos_op(c, q, w);
+      dot_to(c, s, q, w, al + j, 0);
+      KL(c, "lanczos", c->stream, k_lz_three_term, nblk(s), kThreads, 0,
+         s, al, be, j, q, j > 0 ? Q + size_t(j - 1) * s : (const double *)nullptr, w);
+      cgs2(c, s, j + 1, Q, w, cvec);
+      dot_to(c, s, w, w, be + j, 1);
+      ck(cudaMemcpyAsync(c->h_pin, al + j, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+      ck(cudaMemcpyAsync(c->h_pin + 1, be + j, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+      sync(c);
+      ab[0] = c->h_pin[0];
+      ab[1] = c->h_pin[1];
+      if (!std::isfinite(ab[0]) || !std::isfinite(ab[1])) { st = DDLR_ERR_NAN; break; }
+      scale = std::max(scale, std::fabs(ab[0]));
+      mm = j + 1;
+      if (check > 0 && mm % check == 0 && mm >= k + 1) {
+        KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm, al, be, ed, ee, (double *)nullptr,
+           erot, evals, (double *)nullptr, k, esum, c->dflag + 2);
+        KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm - 1, al, be, ed, ee, (double *)nullptr,
+           erot, evals, (double *)nullptr, k, esum + 1, c->dflag + 2);
+        read_dev(c, c->h_pin, esum, 2 * sizeof(double));
+        if (std::fabs(c->h_pin[0] - c->h_pin[1]) < eps * std::fabs(c->h_pin[1])) break;
+      }
+      if (mm == mmax) break;
+      double *qn = Q + size_t(j + 1) * s;
+      if (ab[1] <= 1e-12 * (scale > 0 ? scale : 1.0)) {
+        // breakdown: an invariant subspace was found; continue from a fresh
+        // random vector orthogonalised against Q_j, with beta_j = 0
+        restart++;
+        rand_vec(c->opt.seed + restart, hv, false);
+        ck(cudaMemcpyAsync(w, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+        cgs2(c, s, j + 1, Q, w, cvec);
+        dot_to(c, s, w, w, nrm, 1);
+        KL(c, "lanczos", c->stream, k_scale_into, nblk(s), kThreads, 0, s, w, nrm, qn);
+        ck(cudaMemsetAsync(be + j, 0, sizeof(double), c->stream), "memset");
+      } else {
+        scale = std::max(scale, ab[1]);
+        KL(c, "lanczos", c->stream, k_scale_into, nblk(s), kThreads, 0, s, w, be + j, qn);
+      }
+    }
+    if (st == DDLR_OK) {
+      c->msteps = mm;
+      KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm, al, be, ed, ee, eZ, erot, evals, eY, k,
+         (double *)nullptr, c->dflag + 2);
+      c->ritz.assign(mm, 0.0);
+      read_dev(c, c->ritz.data(), evals, sizeof(double) * mm);
+      if (c->opt.variant == 1) {
+        KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, Q, (long long)s, eY, c->U64);
+        KL(c, "ritz", c->stream, k_ddlr1_coef, 1, 32, 0, mm, k, c->opt.theta_mode, evals,
+           c->theta_d, c->inv1mt64, c->coef64, c->dflag + 1);
+        read_dev(c, &c->theta, c->theta_d, sizeof(double));
+      } else {
+        // V_k = Q_m Y_k; U_k = A0^-1 E V_k; H_k = (I - U_k^T E V_k)^-1
+        double *V = (double *)talloc(sizeof(double) * size_t(s) * k);
+        double *EV = (double *)talloc(sizeof(double) * size_t(n) * k);
+        double *vc = (double *)talloc(sizeof(double) * s);
+        double *ev = (double *)talloc(sizeof(double) * n);
+        double *uc = (double *)talloc(sizeof(double) * n);
+        double *kp = (double *)talloc(sizeof(double) * size_t(kRedGrid) * k * k);
+        double *hw = (double *)talloc(sizeof(double) * (k * k + k));
+        KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, Q, (long long)s, eY, V);
+        const double a = c->opt.alpha;
+        for (int cc = 0; cc < k; cc++) {
+          KL(c, "ritz", c->stream, k_get_col, nblk(s), kThreads, 0, (long long)s, k, cc, V, vc);
+          KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0, m0, s, c->eh_rp, c->eh_ci,
+             c->eh64, 1.0 / a, a, vc, (const double *)nullptr, ev, (const int *)nullptr);
+          KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, ev, EV);
+          a0_solve<double>(c, ev, uc, nullptr);
+          KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, uc, c->U64);
+        }
+        KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, EV, kp);
+        KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, kp, hw, c->Hk64, c->dflag + 1);
+        c->theta = 0.0;
+      }
+      int fl[3];
+      read_dev(c, fl, c->dflag, sizeof(fl));
+      if (fl[2]) st = DDLR_ERR_NAN;
+      else if (fl[1]) st = DDLR_ERR_NOT_SPD;
+    }
+    sync(c);
+  } catch (...) {
+    cudaStreamSynchronize(c->stream);
+    for (void *p : tmp) cudaFree(p);
+    throw;
+  }
+  for (void *p : tmp) cudaFree(p);
+  return st;
+}
+
+void lowrank_to_low_precision(ddlr_ctx *c) {
+  if (c->opt.precision == 0) return;
+  const int k = c->opt.rank_k;
+  const long long nu = (long long)c->urows * k;
+  if (c->opt.uk_bf16)
+    KL(c, "setup", c->stream, k_to_bf16, nblk(nu), kThreads, 0, nu, c->U64, c->Ub16);
+  else
+    KL(c, "setup", c->stream, (k_cast<float, double>), nblk(nu), kThreads, 0, nu, c->U64, c->U32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), 1, kThreads, 0, (long long)k, c->coef64, c->coef32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), 1, kThreads, 0, 1LL, c->inv1mt64, c->inv1mt32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk((long long)k * k), kThreads, 0, (long long)k * k, c->Hk64, c->Hk32, (const int *)nullptr);
+}
+
+// FP32 / BF16 copies used by the mixed-precision preconditioner
+void make_low_precision(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  if (c->opt.precision == 0) return;
+  const long long ll = (long long)P.l_col.size(), lu = (long long)P.u_col.size();
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ll), kThreads, 0, ll, c->l64, c->l32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(lu), kThreads, 0, lu, c->u64, c->u32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(P.n), kThreads, 0, (long long)P.n, c->dinv64, c->dinv32, (const int *)nullptr);
+  const long long ne = (long long)P.eh_ci.size();
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ne), kThreads, 0, ne, c->eh64, c->eh32, (const int *)nullptr);
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ne), kThreads, 0, ne, c->eht64, c->eht32, (const int *)nullptr);
+  lowrank_to_low_precision(c);
+}
+
+}  // namespace
+
+namespace {
+
+const int *pcg_gate(ddlr_ctx *c) {
+  return reinterpret_cast<const int *>(reinterpret_cast<const char *>(c->pcg) +
+                                       offsetof(PcgState, done));
+}
+
+// device-side numeric setup from the resident values (Sec. 4.1: local factors, low-rank data)
+ddlr_status numeric_setup(ddlr_ctx *c) {
+  auto t0 = std::chrono::steady_clock::now();
+  const Plan &P = c->P;
+  const int n = P.n;
+  const long long nnz = P.nnz, nf = P.nnz_factor;
+  const double a = c->opt.alpha;
+  ck(cudaMemsetAsync(c->dflag, 0, 4 * sizeof(int), c->stream), "memset");
+  if (c->opt.scale_diag) {
+    KL(c, "setup", c->stream, k_diag_scale, nblk(n), kThreads, 0, n, c->diag_pos, c->val, c->dsc);
+    KL(c, "setup", c->stream, k_scale_vals, nblk(nnz), kThreads, 0, nnz, c->orow, c->ocol, c->val, c->dsc, c->vals);
+    KL(c, "setup", c->stream, k_permute_in<double>, nblk(n), kThreads, 0, n, c->perm, c->dsc, c->dsc_dev);
+  }
+  const long long na = (long long)P.a_col.size(), ne = (long long)P.eh_ci.size();
+  KL(c, "setup", c->stream, k_gather<double>, nblk(na), kThreads, 0, na, c->a_src, c->val, c->a_val);
+  KL(c, "setup", c->stream, k_gather<double>, nblk(ne), kThreads, 0, ne, c->eh_src, c->vals, c->eh64);
+  KL(c, "setup", c->stream, k_gather<double>, nblk(ne), kThreads, 0, ne, c->eht_src, c->vals, c->eht64);
+  KL(c, "setup", c->stream, k_factor_init, nblk(nf), kThreads, 0, (int)nf, c->f_src, c->f_prp, c->f_pa,
+     c->f_pb, c->f_cdiag, c->vals, 1.0 / (a * a), a * a, c->fval);
+  const int nL = int(P.fl_ptr.size()) - 1;
+  for (int L = 0; L < nL; L++) {
+    const int cnt = P.fl_ptr[L + 1] - P.fl_ptr[L];
+    if (cnt == 0) continue;
+    KL(c, "factor", c->stream, k_ic_level, nblk(cnt), kThreads, 0, cnt, c->fl_rows + P.fl_ptr[L],
+       c->f_rp, c->f_ci, c->fval, c->dflag);
+  }
+  ck(cudaMemsetAsync(c->l64, 0, sizeof(double) * P.l_col.size(), c->stream), "memset");
+  ck(cudaMemsetAsync(c->u64, 0, sizeof(double) * P.u_col.size(), c->stream), "memset");
+  KL(c, "setup", c->stream, k_solve_layout<double>, nblk(nf), kThreads, 0, (int)nf, c->f_row, c->f_rp,
+     c->map_l, c->map_u, c->fval, c->l64, c->u64, c->dinv64);
+  int fl[4];
+  read_dev(c, fl, c->dflag, sizeof(fl));
+  if (fl[0]) {
+    c->err = "non-positive pivot in a local factorisation";
+    return DDLR_ERR_BREAKDOWN;
+  }
+  ddlr_status st = run_lanczos(c);
+  if (st != DDLR_OK) {
+    c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
+                                    : "NaN/Inf in the Lanczos process";
+    return st;
+  }
+  make_low_precision(c);
+  ck(cudaPeekAtLastError(), "kernel launch");
+  sync(c);
+  c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return DDLR_OK;
+}
+
+void allocate(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int n = P.n, k = c->opt.rank_k;
+  c->perm = c->upload(P.perm);
+  c->a_soff = c->upload(P.a_soff); c->a_sw = c->upload(P.a_sw);
+  c->a_col = c->upload(P.a_col); c->a_src = c->upload(P.a_src);
+  c->eh_rp = c->upload(P.eh_rp); c->eh_ci = c->upload(P.eh_ci); c->eh_src = c->upload(P.eh_src);
+  c->eht_rp = c->upload(P.eht_rp); c->eht_ci = c->upload(P.eht_ci); c->eht_src = c->upload(P.eht_src);
+  c->f_rp = c->upload(P.f_rp); c->f_ci = c->upload(P.f_ci); c->f_row = c->upload(P.f_row);
+  c->f_src = c->upload(P.f_src); c->f_prp = c->upload(P.f_prp);
+  c->f_pa = c->upload(P.f_pa); c->f_pb = c->upload(P.f_pb); c->f_cdiag = c->upload(P.f_cdiag);
+  c->fl_rows = c->upload(P.fl_rows);
+  c->map_l = c->upload(P.map_l); c->map_u = c->upload(P.map_u);
+  c->orow = c->upload(P.orig_row); c->ocol = c->upload(P.orig_col); c->diag_pos = c->upload(P.diag_pos);
+  c->S.blk_lvl0 = c->upload(P.blk_lvl0);
+  c->S.lvl_row0 = c->upload(P.lvl_row0);
+  c->S.lvl_nrows = c->upload(P.lvl_nrows);
+  c->S.lvl_slice0 = c->upload(P.lvl_slice0);
+  c->S.l_soff = c->upload(P.l_soff); c->S.l_sw = c->upload(P.l_sw); c->S.l_col = c->upload(P.l_col);
+  c->S.u_soff = c->upload(P.u_soff); c->S.u_sw = c->upload(P.u_sw); c->S.u_col = c->upload(P.u_col);
+  c->val = c->alloc<double>(P.nnz);
+  if (c->opt.scale_diag) {
+    c->vals = c->alloc<double>(P.nnz);
+    c->dsc = c->alloc<double>(n);
+    c->dsc_dev = c->alloc<double>(n);
+  } else {
+    c->vals = c->val;
+  }
+  c->a_val = c->alloc<double>(P.a_col.size());
+  c->fval = c->alloc<double>(P.nnz_factor);
+  c->l64 = c->alloc<double>(P.l_col.size());
+  c->u64 = c->alloc<double>(P.u_col.size());
+  c->dinv64 = c->alloc<double>(n);
+  c->eh64 = c->alloc<double>(P.eh_ci.size());
+  c->eht64 = c->alloc<double>(P.eht_ci.size());
+  c->urows = c->opt.variant == 1 ? P.s : n;
+  c->U64 = c->alloc<double>(size_t(c->urows) * k);
+  c->coef64 = c->alloc<double>(k);
+  c->Hk64 = c->alloc<double>(size_t(k) * k);
+  c->theta_d = c->alloc<double>(1);
+  c->inv1mt64 = c->alloc<double>(1);
+  ck(cudaMemsetAsync(c->coef64, 0, sizeof(double) * k, c->stream), "memset");
+  ck(cudaMemsetAsync(c->Hk64, 0, sizeof(double) * k * k, c->stream), "memset");
+  ck(cudaMemsetAsync(c->inv1mt64, 0, sizeof(double), c->stream), "memset");
+  c->dflag = c->alloc<int>(4);
+  for (int i = 0; i < 8; i++) c->w64[i] = c->alloc<double>(n);
+  int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
+  mmax = std::max(std::min(mmax, P.s), k);
+  c->part64 = c->alloc<double>(size_t(kRedGrid) * std::max(k + 2, mmax + 2) + 2 * kRedGrid);
+  if (c->opt.precision == 1) {
+    c->l32 = c->alloc<float>(P.l_col.size());
+    c->u32 = c->alloc<float>(P.u_col.size());
+    c->dinv32 = c->alloc<float>(n);
+    c->eh32 = c->alloc<float>(P.eh_ci.size());
+    c->eht32 = c->alloc<float>(P.eht_ci.size());
+    if (c->opt.uk_bf16) c->Ub16 = c->alloc<__nv_bfloat16>(size_t(c->urows) * k);
+    else c->U32 = c->alloc<float>(size_t(c->urows) * k);
+    c->coef32 = c->alloc<float>(k);
+    c->Hk32 = c->alloc<float>(size_t(k) * k);
+    c->inv1mt32 = c->alloc<float>(1);
+    for (int i = 0; i < 8; i++) c->w32[i] = c->alloc<float>(n);
+    c->part32 = c->alloc<float>(size_t(kRedGrid) * (k + 2));
+  }
+  c->pcg = c->alloc<PcgState>(1);
+  for (int i = 0; i < 8; i++) c->pv[i] = c->alloc<double>(n);
+  c->stg_in = c->alloc<double>(n);
+  c->stg_out = c->alloc<double>(n);
+  ck(cudaMallocHost(&c->h_pin, 64 * sizeof(double)), "cudaMallocHost");
+}
+
+// PCG on device-order vectors b -> x (Sec. 5), device-side control flow; the
+// host only polls the `done` word every few iterations.
+void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
+             ddlr_solve_info *info) {
+  const Plan &P = c->P;
+  const int n = P.n;
+  const int flexible = c->opt.precision == 1 ? 1 : 0;
+  double *r = c->pv[1], *z = c->pv[2], *p = c->pv[3], *q = c->pv[4], *t = c->pv[5], *zo = c->pv[6];
+  double *part = c->part64;
+  const int *gate = pcg_gate(c);
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream), "memset");
+  ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, b, b, part, (const int *)nullptr);
+  KL(c, "pcg", c->stream, k_pcg_init, 1, 32, 0, c->pcg, part, kRedGrid, tol, maxit, flexible);
+  precond(c, r, z, gate);
+  KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, part, gate);
+  KL(c, "pcg", c->stream, k_pcg_rz0, 1, 32, 0, c->pcg, part, kRedGrid);
+  ck(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  ck(cudaMemcpyAsync(zo, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  const int batch = 4;
+  for (int it = 0; it < maxit + batch; it += batch) {
+    for (int bi = 0; bi < batch; bi++) {
+      KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, p, q, gate);
+      KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, p, q, part, gate);
+      KL(c, "pcg", c->stream, k_pcg_alpha, 1, 32, 0, c->pcg, part, kRedGrid);
+      KL(c, "pcg", c->stream, k_pcg_update<256>, kRedGrid, 256, 0, (long long)n, c->pcg, p, q, x, r, part);
+      KL(c, "pcg", c->stream, k_pcg_rr, 1, 32, 0, c->pcg, part, kRedGrid);
+      KL(c, "pcg", c->stream, k_pcg_true_res<256>, kRedGrid, 256, 0, n, c->pcg, c->a_soff, c->a_sw, c->a_col, c->a_val, b, x, t, part);
+      KL(c, "pcg", c->stream, k_pcg_true_dec, 1, 32, 0, c->pcg, part, kRedGrid);
+      KL(c, "pcg", c->stream, k_pcg_copy_r, nblk(n), kThreads, 0, (long long)n, c->pcg, t, r);
+      precond(c, r, z, gate);
+      KL(c, "pcg", c->stream, (k_dot2_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part, gate);
+      KL(c, "pcg", c->stream, k_pcg_beta, 1, 32, 0, c->pcg, part, kRedGrid);
+      KL(c, "pcg", c->stream, k_pcg_p, nblk(n), kThreads, 0, (long long)n, c->pcg, z, p, flexible ? zo : (double *)nullptr);
+    }
+    int done = 0;
+    ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    sync(c);
+    std::memcpy(&done, c->h_pin, sizeof(int));
+    if (done) break;
+  }
+  // final true residual
+  KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, x, q, (const int *)nullptr);
+  KL(c, "pcg", c->stream, k_resid2_partial<256>, kRedGrid, 256, 0, (long long)n, b, q, part);
+  KL(c, "pcg", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, part, c->w64[7], 0, (const int *)nullptr);
+  PcgState hs;
+  ck(cudaMemcpyAsync(c->h_pin, c->w64[7], sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  ck(cudaMemcpyAsync(&hs, c->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  sync(c);
+  if (info) {
+    info->its = hs.its;
+    info->relres = hs.bb > 0 ? std::sqrt(c->h_pin[0] / hs.bb) : 0.0;
+    info->status = hs.status == 0 ? DDLR_OK : (hs.status == 5 ? DDLR_ERR_NOCONV : DDLR_ERR_NAN);
+    if (hs.done == 0) info->status = DDLR_ERR_NOCONV;
+  }
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+namespace {
+ddlr_status run_guarded(ddlr_ctx *c, const std::function<ddlr_status()> &f) {
+  try {
+    ddlr_status st = f();
+    if (st == DDLR_OK) {
+      cudaError_t e = cudaPeekAtLastError();
+      if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return DDLR_ERR_CUDA; }
+    }
+    return st;
+  } catch (const Fail &f2) {
+    c->err = f2.msg;
+    return f2.st;
+  } catch (const std::bad_alloc &) {
+    c->err = "host allocation failed";
+    return DDLR_ERR_OOM;
+  } catch (const std::exception &e) {
+    c->err = e.what();
+    return DDLR_ERR_INVALID;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ddlr_status ddlr_options_default(ddlr_options *o) {
+  if (!o) return DDLR_ERR_INVALID;
+  std::memset(o, 0, sizeof(*o));
+  o->variant = 1;
+  o->rank_k = 16;
+  o->alpha = 1.0;
+  o->theta_mode = 1;
+  o->factor = 0;
+  o->c_order = 0;
+  o->precision = 0;
+  o->uk_bf16 = 0;
+  o->scale_diag = 0;
+  o->lanczos_max = 0;
+  o->lanczos_check = 10;
+  o->lanczos_eps = 1e-4;
+  o->seed = 0;
+  o->max_nrhs = 1;
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double *val,
+                       const int *part, int p, const ddlr_options *opt, void *cuda_stream,
+                       ddlr_handle *out) {
+  if (!out) return DDLR_ERR_INVALID;
+  *out = nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  ddlr_options o;
+  if (opt) o = *opt; else ddlr_options_default(&o);
+  if ((o.variant != 1 && o.variant != 2) || !(o.alpha > 0) || (o.precision != 0 && o.precision != 1) ||
+      (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) || o.rank_k < 1 ||
+      o.rank_k > 256) {
+    g_setup_error = "invalid options";
+    return DDLR_ERR_INVALID;
+  }
+  if (o.lanczos_check < 0) o.lanczos_check = 0;
+  ddlr_ctx *c = new (std::nothrow) ddlr_ctx();
+  if (!c) { g_setup_error = "host allocation failed"; return DDLR_ERR_OOM; }
+  c->opt = o;
+  c->stream = (cudaStream_t)cuda_stream;
+  ddlr_status st = run_guarded(c, [&]() -> ddlr_status {
+    std::string err;
+    ddlr_status s1 = build_plan(n, rowptr, colind, val, part, p, c->opt, c->P, err);
+    if (s1 != DDLR_OK) { c->err = err; return s1; }
+    ck(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    allocate(c);
+    ck(cudaMemcpyAsync(c->val, val, sizeof(double) * c->P.nnz, cudaMemcpyHostToDevice, c->stream), "H2D");
+    return numeric_setup(c);
+  });
+  if (st != DDLR_OK) {
+    g_setup_error = c->err;
+    ddlr_destroy(c);
+    return st;
+  }
+  c->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = c;
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_refactor(ddlr_handle c, const double *val) {
+  if (!c) return DDLR_ERR_INVALID;
+  return run_guarded(c, [&]() -> ddlr_status {
+    if (val)
+      ck(cudaMemcpyAsync(c->val, val, sizeof(double) * c->P.nnz, cudaMemcpyDefault, c->stream), "copy values");
+    return numeric_setup(c);
+  });
+}
+
+static ddlr_status vec_call(ddlr_ctx *c, const double *x, double *y, int nrhs, int ld,
+                            const std::function<void(const double *, double *)> &body) {
+  if (!c) return DDLR_ERR_INVALID;
+  const int n = c->P.n;
+  if (!x || !y || nrhs < 1 || ld < n) { c->err = "invalid vector arguments"; return DDLR_ERR_INVALID; }
+  return run_guarded(c, [&]() -> ddlr_status {
+    const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
+    for (int j = 0; j < nrhs; j++) {
+      const double *xj = x + size_t(j) * ld;
+      double *yj = y + size_t(j) * ld;
+      const double *xd = xj;
+      double *yd = yj;
+      if (hx) {
+        ck(cudaMemcpyAsync(c->stg_in, xj, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "H2D");
+        xd = c->stg_in;
+      }
+      if (hy) yd = c->stg_out;
+      body(xd, yd);
+      if (hy) {
+        ck(cudaMemcpyAsync(yj, yd, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "D2H");
+        sync(c);
+      }
+    }
+    return DDLR_OK;
+  });
+}
+
+ddlr_status ddlr_apply(ddlr_handle c, const double *x, double *y, int nrhs, int ld) {
+  return vec_call(c, x, y, nrhs, ld, [c](const double *xd, double *yd) {
+    const int n = c->P.n;
+    double *xi = c->pv[1], *yo = c->pv[2];
+    KL(c, "perm", c->stream, k_permute_in<double>, nblk(n), kThreads, 0, n, c->perm, xd, xi);
+    precond(c, xi, yo, nullptr);
+    KL(c, "perm", c->stream, k_permute_out<double>, nblk(n), kThreads, 0, n, c->perm, yo, yd);
+  });
+}
+
+ddlr_status ddlr_a0_solve(ddlr_handle c, const double *x, double *y, int nrhs, int ld) {
+  return vec_call(c, x, y, nrhs, ld, [c](const double *xd, double *yd) {
+    const int n = c->P.n;
+    double *xi = c->pv[1], *yo = c->pv[2];
+    KL(c, "perm", c->stream, k_permute_in<double>, nblk(n), kThreads, 0, n, c->perm, xd, xi);
+    if (c->opt.precision == 0) {
+      a0_solve<double>(c, xi, yo, nullptr);
+    } else {
+      KL(c, "vec", c->stream, (k_cast<float, double>), nblk(n), kThreads, 0, (long long)n, xi, c->w32[6], (const int *)nullptr);
+      a0_solve<float>(c, c->w32[6], c->w32[7], nullptr);
+      KL(c, "vec", c->stream, (k_cast<double, float>), nblk(n), kThreads, 0, (long long)n, c->w32[7], yo, (const int *)nullptr);
+    }
+    KL(c, "perm", c->stream, k_permute_out<double>, nblk(n), kThreads, 0, n, c->perm, yo, yd);
+  });
+}
+
+ddlr_status ddlr_pcg(ddlr_handle c, const double *b, double *x, int nrhs, int ld, double tol,
+                     int maxit, ddlr_solve_info *info) {
+  if (!c) return DDLR_ERR_INVALID;
+  if (maxit <= 0) maxit = 500;
+  if (!(tol > 0)) { c->err = "tol must be positive"; return DDLR_ERR_INVALID; }
+  std::vector<ddlr_solve_info> inf(nrhs > 0 ? nrhs : 1);
+  int j = 0;
+  ddlr_status st = vec_call(c, b, x, nrhs, ld, [&](const double *bd, double *xd) {
+    const int n = c->P.n;
+    // b in device order -> pv[0]; solution in device order -> w64[5]
+    KL(c, "perm", c->stream, k_permute_in<double>, nblk(n), kThreads, 0, n, c->perm, bd, c->pv[0]);
+    pcg_dev(c, c->pv[0], c->w64[5], tol, maxit, &inf[j]);
+    KL(c, "perm", c->stream, k_permute_out<double>, nblk(n), kThreads, 0, n, c->perm, c->w64[5], xd);
+    j++;
+  });
+  if (st != DDLR_OK) return st;
+  ddlr_status agg = DDLR_OK;
+  for (int r = 0; r < nrhs; r++) {
+    if (info) info[r] = inf[r];
+    if (inf[r].status != DDLR_OK && agg == DDLR_OK) agg = (ddlr_status)inf[r].status;
+  }
+  if (agg != DDLR_OK) c->err = agg == DDLR_ERR_NOCONV ? "PCG did not converge" : "NaN/Inf in PCG";
+  return agg;
+}
+
+ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
+  if (!c || !info) return DDLR_ERR_INVALID;
+  const Plan &P = c->P;
+  std::memset(info, 0, sizeof(*info));
+  info->n = P.n; info->p = P.p; info->s = P.s; info->m = P.m; info->k = c->opt.rank_k;
+  info->variant = c->opt.variant; info->precision = c->opt.precision;
+  info->lanczos_steps = c->msteps; info->ncolors = P.ncolors;
+  info->levels_interior = P.levels_interior; info->levels_c = P.levels_c;
+  info->theta = c->theta;
+  info->lambda_max = c->ritz.empty() ? 0.0 : c->ritz[0];
+  info->nnz_a = P.nnz; info->nnz_factor = P.nnz_factor; info->nnz_ehat = P.nnz_ehat;
+  // fill ratio (Sec. 5): factors + Ehat + low-rank data over nnz(A)
+  const double lr = double(c->urows) * c->opt.rank_k + (c->opt.variant == 2 ? double(c->opt.rank_k) * c->opt.rank_k : 0);
+  info->fill_ratio = (double(P.nnz_factor) + double(P.nnz_ehat) + lr) / double(P.nnz);
+  info->device_bytes = c->dev_bytes;
+  info->setup_ms = c->setup_ms;
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_get_ritz(ddlr_handle c, double *out, int cap, int *count) {
+  if (!c) return DDLR_ERR_INVALID;
+  if (count) *count = int(c->ritz.size());
+  if (out)
+    for (int i = 0; i < cap && i < int(c->ritz.size()); i++) out[i] = c->ritz[i];
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_get_factor_coo(ddlr_handle c, long long *nnz, int *rows, int *cols, double *vals) {
+  if (!c || !nnz) return DDLR_ERR_INVALID;
+  *nnz = c->P.nnz_factor;
+  if (!rows) return DDLR_OK;
+  return run_guarded(c, [&]() -> ddlr_status {
+    std::vector<double> h(c->P.nnz_factor);
+    read_dev(c, h.data(), c->fval, sizeof(double) * h.size());
+    for (long long q = 0; q < c->P.nnz_factor; q++) {
+      rows[q] = c->P.perm[c->P.f_row[q]];
+      cols[q] = c->P.perm[c->P.f_ci[q]];
+      if (vals) vals[q] = h[q];
+    }
+    return DDLR_OK;
+  });
+}
+
+// rows of U in ascending original index: order[r] = device row of rank r
+static std::vector<int> lowrank_order(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int off = c->opt.variant == 1 ? P.m : 0;
+  std::vector<std::pair<int, int>> o(c->urows);
+  for (int r = 0; r < c->urows; r++) o[r] = {P.perm[off + r], r};
+  std::sort(o.begin(), o.end());
+  std::vector<int> ord(c->urows);
+  for (int r = 0; r < c->urows; r++) ord[r] = o[r].second;
+  return ord;
+}
+
+ddlr_status ddlr_get_lowrank(ddlr_handle c, double *U, double *lam, double *theta, double *Hk) {
+  if (!c) return DDLR_ERR_INVALID;
+  return run_guarded(c, [&]() -> ddlr_status {
+    const int k = c->opt.rank_k;
+    if (U) {
+      std::vector<double> h(size_t(c->urows) * k);
+      read_dev(c, h.data(), c->U64, sizeof(double) * h.size());
+      std::vector<int> ord = lowrank_order(c);
+      for (int r = 0; r < c->urows; r++)
+        std::memcpy(U + size_t(r) * k, h.data() + size_t(ord[r]) * k, sizeof(double) * k);
+    }
+    if (lam) for (int i = 0; i < k; i++) lam[i] = i < int(c->ritz.size()) ? c->ritz[i] : 0.0;
+    if (theta) *theta = c->theta;
+    if (Hk) read_dev(c, Hk, c->Hk64, sizeof(double) * k * k);
+    return DDLR_OK;
+  });
+}
+
+ddlr_status ddlr_set_lowrank(ddlr_handle c, const double *U, const double *lam, double theta,
+                             const double *Hk) {
+  if (!c || !U) return DDLR_ERR_INVALID;
+  if (c->opt.variant == 1 && !lam) return DDLR_ERR_INVALID;
+  if (c->opt.variant == 2 && !Hk) return DDLR_ERR_INVALID;
+  return run_guarded(c, [&]() -> ddlr_status {
+    const int k = c->opt.rank_k;
+    std::vector<int> ord = lowrank_order(c);
+    std::vector<double> h(size_t(c->urows) * k);
+    for (int r = 0; r < c->urows; r++)
+      std::memcpy(h.data() + size_t(ord[r]) * k, U + size_t(r) * k, sizeof(double) * k);
+    ck(cudaMemcpyAsync(c->U64, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream), "H2D");
+    if (c->opt.variant == 1) {
+      std::vector<double> v(lam, lam + k);
+      v.push_back(theta);
+      double *dv = c->w64[7];
+      ck(cudaMemcpyAsync(dv, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, c->stream), "H2D");
+      ck(cudaMemsetAsync(c->dflag, 0, 4 * sizeof(int), c->stream), "memset");
+      KL(c, "setup", c->stream, k_ddlr1_coef, 1, 32, 0, k + 1, k, 1, dv, c->theta_d, c->inv1mt64,
+         c->coef64, c->dflag + 1);
+      c->theta = theta;
+      for (int i = 0; i < k && i < int(c->ritz.size()); i++) c->ritz[i] = lam[i];
+    } else {
+      ck(cudaMemcpyAsync(c->Hk64, Hk, sizeof(double) * k * k, cudaMemcpyHostToDevice, c->stream), "H2D");
+    }
+    lowrank_to_low_precision(c);
+    sync(c);
+    return DDLR_OK;
+  });
+}
+
+ddlr_status ddlr_set_timing(ddlr_handle c, int enable) {
+  if (!c) return DDLR_ERR_INVALID;
+  c->timing = enable != 0;
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_get_counters(ddlr_handle c, long long *launches, char *names, int cap, double *ms,
+                              long long *family_launches, int cap_f, int *nfamilies) {
+  if (!c) return DDLR_ERR_INVALID;
+  return run_guarded(c, [&]() -> ddlr_status {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream2);
+    c->resolve();
+    if (launches) *launches = c->launches;
+    if (nfamilies) *nfamilies = int(c->fam_names.size());
+    if (names && cap > 0) {
+      std::string all;
+      for (size_t i = 0; i < c->fam_names.size(); i++) { if (i) all += ","; all += c->fam_names[i]; }
+      std::strncpy(names, all.c_str(), size_t(cap) - 1);
+      names[cap - 1] = 0;
+    }
+    for (int i = 0; i < cap_f && i < int(c->fam_names.size()); i++) {
+      if (ms) ms[i] = c->fam_ms[i];
+      if (family_launches) family_launches[i] = c->fam_cnt[i];
+    }
+    return DDLR_OK;
+  });
+}
+
+ddlr_status ddlr_reset_counters(ddlr_handle c) {
+  if (!c) return DDLR_ERR_INVALID;
+  cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream2);
+  c->resolve();
+  c->launches = 0;
+  for (auto &v : c->fam_ms) v = 0;
+  for (auto &v : c->fam_cnt) v = 0;
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_bytes,
+                             double *family_bytes, int cap_f) {
+  if (!c) return DDLR_ERR_INVALID;
+  const Plan &P = c->P;
+  const double v = c->opt.precision == 1 ? 4.0 : 8.0;
+  const double ub = c->opt.precision == 1 ? (c->opt.uk_bf16 ? 2.0 : 4.0) : 8.0;
+  const double n = P.n, s = P.s, m = P.m, k = c->opt.rank_k;
+  // off-diagonal factor entries of the interior blocks and of C_a
+  double off_c = 0.0;
+  for (int g = P.blk_row0[P.p]; g < P.n; g++) off_c += P.f_rp[g + 1] - P.f_rp[g] - 1;
+  const double off_int = double(P.nnz_factor) - n - off_c;
+  const double ne = double(P.nnz_ehat);
+  // one forward + one backward sweep: off-diagonal values and indices once per
+  // sweep, the inverse diagonal, the right-hand side read and the result written
+  const double blocks = 2.0 * (off_int * (v + 4.0) + 3.0 * m * v);
+  const double cblk = 2.0 * (off_c * (v + 4.0) + 3.0 * s * v);
+  const double a0 = blocks + cblk;
+  const double et = ne * (v + 4.0) + 4.0 * s + 2.0 * s * v;
+  const double urows = c->urows;
+  const double utx = urows * k * ub + urows * v;
+  const double wr = s * k * ub + 4.0 * s * v;
+  const double ei = ne * (v + 4.0) + 4.0 * m + 2.0 * m * v;
+  const double uadd = n * k * ub + 2.0 * n * v;
+  const double apply = c->opt.variant == 1 ? 2.0 * a0 + et + utx + wr + ei : a0 + utx + uadd;
+  if (apply_bytes) *apply_bytes = apply;
+  if (a0_bytes) *a0_bytes = a0;
+  if (family_bytes) {
+    const double clev = std::max(1, 2 * P.levels_c - 1);
+    const double nnz_a = double(P.nnz);
+    for (int i = 0; i < cap_f && i < int(c->fam_names.size()); i++) {
+      const std::string &f = c->fam_names[i];
+      double b = 0.0;
+      if (f == "sptrsv_blocks") b = blocks;
+      else if (f == "sptrsv_c") b = cblk / clev;
+      else if (f == "et") b = et;
+      else if (f == "utx") b = utx;
+      else if (f == "w_rhs") b = wr;
+      else if (f == "e_int") b = ei;
+      else if (f == "u_add") b = uadd;
+      else if (f == "spmv") b = nnz_a * 12.0 + 2.0 * n * 8.0;
+      family_bytes[i] = b;
+    }
+  }
+  return DDLR_OK;
+}
+
+ddlr_status ddlr_set_stream(ddlr_handle c, void *s) {
+  if (!c) return DDLR_ERR_INVALID;
+  c->stream = (cudaStream_t)s;
+  return DDLR_OK;
+}
+
+const char *ddlr_last_error(ddlr_handle c) {
+  if (!c) return g_setup_error.c_str();
+  return c->err.c_str();
+}
+
+ddlr_status ddlr_destroy(ddlr_handle c) {
+  if (!c) return DDLR_OK;
+  if (c->stream2) cudaStreamSynchronize(c->stream2);
+  cudaStreamSynchronize(c->stream);
+  c->resolve();
+  for (auto e : c->evpool) cudaEventDestroy(e);
+  c->release();
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
+  delete c;
+  return DDLR_OK;
+}
+
+}  // extern "C"

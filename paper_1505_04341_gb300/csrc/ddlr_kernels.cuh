@@ -1,0 +1,849 @@
+// ddlr_kernels.cuh -- CUDA kernels of the DDLR library (sm_103a).
+//
+// Vectors live in the device order of the plan: interior rows of block
+// 0..p-1, then the interface rows; inside each block rows are sorted by
+// dependency level.  All floating-point reductions are two-stage with a fixed
+// grid and a fixed summation order (no floating-point atomics), so results do
+// not depend on scheduling.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ddlr {
+
+constexpr int kRedGrid = 304;   // CTAs of every two-stage reduction (2 x 152 SMs)
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- helpers
+template <typename T> __device__ __forceinline__ T ld_u(const T *p) { return *p; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+
+template <typename T> struct AccOf { using type = T; };
+template <> struct AccOf<__nv_bfloat16> { using type = float; };
+
+// deterministic block sum of one value per thread (result valid in thread 0)
+template <typename T, int NT>
+__device__ __forceinline__ T block_sum(T v, T *sm) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; i++) r += sm[i];
+  __syncthreads();
+  return r;
+}
+
+// =================================================================== setup
+__global__ void k_diag_scale(int n, const int *diag_pos, const double *val,
+                             double *dsc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dsc[i] = 1.0 / sqrt(val[diag_pos[i]]);
+}
+
+__global__ void k_scale_vals(long long nnz, const int *orow, const int *ocol,
+                             const double *val, const double *dsc, double *out) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nnz) out[q] = val[q] * dsc[orow[q]] * dsc[ocol[q]];
+}
+
+template <typename T>
+__global__ void k_gather(long long cnt, const int *src, const double *in, T *out) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < cnt) { int s = src[q]; out[q] = s >= 0 ? T(in[s]) : T(0); }
+}
+
+// initial values of the factor pattern: entries of B_{i,a} = B_i + a^-2 E_i E_i^T
+// and C_a = C + a^2 I (eq. split)
+__global__ void k_factor_init(int nf, const int *f_src, const int *f_prp,
+                              const int *pa, const int *pb,
+                              const unsigned char *cdiag, const double *as,
+                              double ia2, double a2, double *fval) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nf) return;
+  double v = f_src[q] >= 0 ? as[f_src[q]] : 0.0;
+  double e = 0.0;
+  for (int t = f_prp[q]; t < f_prp[q + 1]; t++) e += as[pa[t]] * as[pb[t]];
+  v += ia2 * e;
+  if (cdiag[q]) v += a2;
+  fval[q] = v;
+}
+
+// One dependency level of the up-looking incomplete Cholesky on the given
+// pattern (IC(0), or exact Cholesky on the symbolic fill pattern):
+//   l_ij = (a_ij - sum_{t in P_i, P_j} l_it l_jt) / l_jj,
+//   l_ii = sqrt(a_ii - sum_t l_it^2).
+// Rows of one level only read rows of lower levels; columns ascend in device
+// order, which is a topological order of the factor, so l_it is final before
+// l_ij is formed.  A non-positive pivot sets *err = 1 (BREAKDOWN).
+__global__ void k_ic_level(int cnt, const int *rows, const int *f_rp,
+                           const int *f_ci, double *fval, int *err) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int i = rows[t];
+  const int b = f_rp[i], e = f_rp[i + 1];
+  for (int q = b; q < e - 1; q++) {
+    const int j = f_ci[q];
+    double s = fval[q];
+    int qa = b, qb = f_rp[j];
+    const int eb = f_rp[j + 1] - 1;
+    while (qa < q && qb < eb) {
+      const int ca = f_ci[qa], cb = f_ci[qb];
+      if (ca == cb) { s -= fval[qa] * fval[qb]; qa++; qb++; }
+      else if (ca < cb) qa++;
+      else qb++;
+    }
+    fval[q] = s / fval[eb];
+  }
+  double d = fval[e - 1];
+  for (int q = b; q < e - 1; q++) d -= fval[q] * fval[q];
+  if (!(d > 0.0)) { *err = 1; d = 1.0; }
+  fval[e - 1] = sqrt(d);
+}
+
+// scatter the factor into the sliced-ELL solve layouts (L rows and L^T rows)
+template <typename T>
+__global__ void k_solve_layout(int nf, const int *f_row, const int *f_rp,
+                               const int *map_l, const int *map_u,
+                               const double *fval, T *lval, T *uval, T *dinv) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nf) return;
+  const int g = f_row[q];
+  if (q == f_rp[g + 1] - 1) {
+    dinv[g] = T(1.0 / fval[q]);
+  } else {
+    lval[map_l[q]] = T(fval[q]);
+    uval[map_u[q]] = T(fval[q]);
+  }
+}
+
+// ====================================================== triangular solves
+struct SolveLayout {
+  const int *blk_lvl0, *lvl_row0, *lvl_nrows, *lvl_slice0;
+  const int *l_soff, *l_sw, *l_col;
+  const int *u_soff, *u_sw, *u_col;
+};
+
+// forward row:  z_r = (x_r - sum_c L_rc z_c) / L_rr
+// backward row: z_r = (z_r - sum_c (L^T)_rc z_c) / L_rr
+template <typename T, bool FWD>
+__device__ __forceinline__ void solve_row(const SolveLayout &S, const T *val,
+                                          const T *dinv, const T *x, T *z,
+                                          int slice, int lane, int r) {
+  const int *soff = FWD ? S.l_soff : S.u_soff;
+  const int *sw = FWD ? S.l_sw : S.u_sw;
+  const int *col = FWD ? S.l_col : S.u_col;
+  const int off = soff[slice] + lane, w = sw[slice];
+  T acc = FWD ? x[r] : z[r];
+  for (int kk = 0; kk < w; kk++) {
+    const int c = col[off + kk * 32];
+    acc -= val[off + kk * 32] * z[c];
+  }
+  z[r] = acc * dinv[r];
+}
+
+// All interior blocks B_{i,a} of A0 in one launch, one CTA per block: forward
+// sweep over the block's levels, then backward sweep, with a CTA barrier
+// between levels (Sec. 4.2: the p local solves are independent).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+k_sptrsv_blocks(SolveLayout S, const T *lval, const T *uval, const T *dinv,
+                const T *x, T *z, const int *gate) {
+  if (gate && *gate) return;
+  const int b = blockIdx.x;
+  const int l0 = S.blk_lvl0[b], l1 = S.blk_lvl0[b + 1];
+  for (int l = l0; l < l1; l++) {
+    const int r0 = S.lvl_row0[l], nr = S.lvl_nrows[l], s0 = S.lvl_slice0[l];
+    for (int i = threadIdx.x; i < nr; i += NT)
+      solve_row<T, true>(S, lval, dinv, x, z, s0 + (i >> 5), i & 31, r0 + i);
+    __syncthreads();
+  }
+  for (int l = l1 - 1; l >= l0; l--) {
+    const int r0 = S.lvl_row0[l], nr = S.lvl_nrows[l], s0 = S.lvl_slice0[l];
+    for (int i = threadIdx.x; i < nr; i += NT)
+      solve_row<T, false>(S, uval, dinv, x, z, s0 + (i >> 5), i & 31, r0 + i);
+    __syncthreads();
+  }
+}
+
+// One level of one block (used for C_a, whose levels span the whole GPU):
+// mode 0 forward, 1 backward, 2 forward then backward on the same (top) level.
+template <typename T>
+__global__ void k_sptrsv_level(SolveLayout S, int lvl, int mode, const T *lval,
+                               const T *uval, const T *dinv, const T *x, T *z,
+                               const int *gate) {
+  if (gate && *gate) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = S.lvl_nrows[lvl];
+  if (i >= nr) return;
+  const int r = S.lvl_row0[lvl] + i, sl = S.lvl_slice0[lvl] + (i >> 5), ln = i & 31;
+  if (mode == 1) {
+    solve_row<T, false>(S, uval, dinv, x, z, sl, ln, r);
+  } else {
+    solve_row<T, true>(S, lval, dinv, x, z, sl, ln, r);
+    if (mode == 2) z[r] = z[r] * dinv[r];
+  }
+}
+
+// ======================================================= E, E^T products
+// v = E w + xadd = [a^-1 Ehat w ; -a w] + xadd   (eq. EF), rows [0, n)
+template <typename T>
+__global__ void k_e_vec(int m, int s, const int *eh_rp, const int *eh_ci,
+                        const T *eh_val, T ia, T a, const T *w, const T *xadd,
+                        T *v, const int *gate) {
+  if (gate && *gate) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m + s) return;
+  T acc;
+  if (r < m) {
+    acc = 0;
+    for (int q = eh_rp[r]; q < eh_rp[r + 1]; q++) acc += eh_val[q] * w[eh_ci[q]];
+    acc *= ia;
+  } else {
+    acc = -a * w[r - m];
+  }
+  v[r] = xadd ? xadd[r] + acc : acc;
+}
+
+// interior rows only: v_r = xadd_r + a^-1 (Ehat w)_r
+template <typename T>
+__global__ void k_e_interior(int m, const int *eh_rp, const int *eh_ci,
+                             const T *eh_val, T ia, const T *w, const T *xadd,
+                             T *v, const int *gate) {
+  if (gate && *gate) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  T acc = 0;
+  for (int q = eh_rp[r]; q < eh_rp[r + 1]; q++) acc += eh_val[q] * w[eh_ci[q]];
+  v[r] = xadd[r] + ia * acc;
+}
+
+// y = E^T z = a^-1 Ehat^T z_B - a z_C  (interface rows j in [0, s))
+template <typename T>
+__global__ void k_et(int s, int m, const int *eht_rp, const int *eht_ci,
+                     const T *eht_val, T ia, T a, const T *z, T *y,
+                     const int *gate) {
+  if (gate && *gate) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  T acc = 0;
+  for (int q = eht_rp[j]; q < eht_rp[j + 1]; q++) acc += eht_val[q] * z[eht_ci[q]];
+  y[j] = ia * acc - a * z[m + j];
+}
+
+// ================================================ tall-skinny U products
+// partials[blk][c] = sum over this CTA's rows r of U[r][c] * x[r]
+// (U row-major nrows x k; k <= NT).  Stage 1 of t = U^T x.
+template <typename T, typename TU, int NT>
+__global__ void __launch_bounds__(NT)
+k_utx_partial(int nrows, int k, const TU *U, const T *x, T *partials,
+              const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T xs[NT];
+  __shared__ T red[NT];
+  const int G = NT / k;
+  const int c = threadIdx.x % k, g = threadIdx.x / k;
+  T acc = 0;
+  for (long long base = (long long)blockIdx.x * NT; base < nrows;
+       base += (long long)gridDim.x * NT) {
+    const long long r = base + threadIdx.x;
+    xs[threadIdx.x] = r < nrows ? x[r] : T(0);
+    __syncthreads();
+    if (g < G) {
+      const int lim = (int)min((long long)NT, nrows - base);
+      for (int rr = g; rr < lim; rr += G)
+        acc += T(to_acc(U[(base + rr) * k + c])) * xs[rr];
+    }
+    __syncthreads();
+  }
+  red[threadIdx.x] = (g < G) ? acc : T(0);
+  __syncthreads();
+  if (threadIdx.x < k) {
+    T s = 0;
+    for (int gg = 0; gg < G; gg++) s += red[gg * k + threadIdx.x];
+    partials[(long long)blockIdx.x * k + threadIdx.x] = s;
+  }
+}
+
+// out[c] = coef[c] * sum_g partials[g][c]  (warp per column, fixed order);
+// if H != null: out = H * (that k-vector) with H k x k row-major.
+template <typename T>
+__global__ void k_reduce_cols(int G, int k, const T *partials, const T *coef,
+                              const T *H, T *out, const int *gate) {
+  if (gate && *gate) return;
+  extern __shared__ unsigned char smraw[];
+  T *tmp = reinterpret_cast<T *>(smraw);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = w; c < k; c += nw) {
+    T s = 0;
+    for (int g = l; g < G; g += 32) s += partials[(long long)g * k + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) tmp[c] = coef ? coef[c] * s : s;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    if (H) {
+      T s = 0;
+      for (int b = 0; b < k; b++) s += H[c * k + b] * tmp[b];
+      out[c] = s;
+    } else {
+      out[c] = tmp[c];
+    }
+  }
+}
+
+// DDLR-1 (Algorithm 1): G_{k,theta}^-1 y and the interface half of x + E w:
+//   w_j = y_j / (1 - theta) + sum_c U[j][c] t_c   (prop. gkt, t = D U^T y)
+//   rhs_{m+j} = x_{m+j} - a w_j
+template <typename T, typename TU>
+__global__ void k_w_rhs(int s, int m, int k, const TU *U, const T *t,
+                        const T *y, const T *inv1mt, T a, const T *x, T *w,
+                        T *rhs, const int *gate) {
+  if (gate && *gate) return;
+  extern __shared__ unsigned char smraw[];
+  T *ts = reinterpret_cast<T *>(smraw);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) ts[c] = t[c];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  T acc = 0;
+  const TU *u = U + (long long)j * k;
+  for (int c = 0; c < k; c++) acc += T(to_acc(u[c])) * ts[c];
+  const T wj = (*inv1mt) * y[j] + acc;
+  w[j] = wj;
+  rhs[m + j] = x[m + j] - a * wj;
+}
+
+// u_r += sum_c U[r][c] h_c   (DDLR-2, eq. Form2a)
+template <typename T, typename TU>
+__global__ void k_u_add(int nrows, int k, const TU *U, const T *h, T *u,
+                        const int *gate) {
+  if (gate && *gate) return;
+  extern __shared__ unsigned char smraw[];
+  T *hs = reinterpret_cast<T *>(smraw);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  T acc = 0;
+  const TU *row = U + r * k;
+  for (int c = 0; c < k; c++) acc += T(to_acc(row[c])) * hs[c];
+  u[r] += acc;
+}
+
+// ===================================================== vectors and PCG
+// y = A x with A in sliced ELL (device order)
+template <typename T>
+__global__ void k_spmv(int n, const int *soff, const int *sw, const int *col,
+                       const T *val, const T *x, T *y, const int *gate) {
+  if (gate && *gate) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int g = r >> 5, l = r & 31;
+  const int off = soff[g] + l, w = sw[g];
+  T acc = 0;
+  for (int kk = 0; kk < w; kk++) acc += val[off + kk * 32] * x[col[off + kk * 32]];
+  y[r] = acc;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+k_dot_partial(long long n, const T *a, const T *b, T *partials, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T sm[NT / 32];
+  T acc = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
+       i += (long long)gridDim.x * NT)
+    acc += a[i] * b[i];
+  acc = block_sum<T, NT>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// partial sums of two dot products a.b and a.c
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+k_dot2_partial(long long n, const T *a, const T *b, const T *c, T *partials,
+               const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T sm[NT / 32];
+  T acc = 0, acc2 = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
+       i += (long long)gridDim.x * NT) {
+    acc += a[i] * b[i];
+    acc2 += a[i] * c[i];
+  }
+  acc = block_sum<T, NT>(acc, sm);
+  acc2 = block_sum<T, NT>(acc2, sm);
+  if (threadIdx.x == 0) { partials[blockIdx.x] = acc; partials[gridDim.x + blockIdx.x] = acc2; }
+}
+
+// sum of G partials in a fixed order (one warp)
+__device__ __forceinline__ double warp_sum_partials(const double *p, int G) {
+  const int l = threadIdx.x & 31;
+  double s = 0;
+  for (int g = l; g < G; g += 32) s += p[g];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+__global__ void k_reduce_scalar(int G, const double *partials, double *out,
+                                int do_sqrt, const int *gate) {
+  if (gate && *gate) return;
+  double s = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) *out = do_sqrt ? sqrt(s) : s;
+}
+
+template <typename T, typename S>
+__global__ void k_cast(long long n, const S *in, T *out, const int *gate) {
+  if (gate && *gate) return;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = T(in[i]);
+}
+
+// out = a .* b
+template <typename T>
+__global__ void k_mulv_t(long long n, const T *a, const T *b, T *out, const int *gate) {
+  if (gate && *gate) return;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] * b[i];
+}
+
+__global__ void k_to_bf16(long long n, const double *in, __nv_bfloat16 *out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __float2bfloat16_rn(float(in[i]));
+}
+
+// out[g] = in[perm[g]] (original -> device order)
+template <typename T>
+__global__ void k_permute_in(int n, const int *perm, const T *in, T *out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[g] = in[perm[g]];
+}
+template <typename T>
+__global__ void k_permute_out(int n, const int *perm, const T *in, T *out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[perm[g]] = in[g];
+}
+// with diagonal scaling: out = dsc .* (permuted in)
+__global__ void k_permute_in_scaled(int n, const int *perm, const double *dsc,
+                                    const double *in, double *out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) { int i = perm[g]; out[g] = in[i] * (dsc ? dsc[i] : 1.0); }
+}
+
+// partial sums of ||b - q||^2
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_resid2_partial(long long n, const double *b, const double *q, double *partials) {
+  __shared__ double sm[NT / 32];
+  double acc = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
+       i += (long long)gridDim.x * NT) {
+    const double d = b[i] - q[i];
+    acc += d * d;
+  }
+  acc = block_sum<double, NT>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// --------------------------------------------------------- PCG control
+struct PcgState {
+  double rz, rz_new, pq, alpha, beta, rr, bb, tol2, rt2, rzold;
+  int its, maxit, done, status, check_true, restart, flexible, pad;
+};
+
+__global__ void k_pcg_init(PcgState *st, const double *partials, int G,
+                           double tol, int maxit, int flexible) {
+  double bb = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) {
+    st->bb = bb;
+    st->tol2 = tol * tol * bb;
+    st->its = 0; st->maxit = maxit; st->status = 0; st->check_true = 0;
+    st->restart = 0; st->flexible = flexible;
+    st->done = (bb == 0.0) ? 1 : 0;
+    st->rz = 0; st->rr = bb;
+  }
+}
+
+// rz = r.z after the first preconditioning
+__global__ void k_pcg_rz0(PcgState *st, const double *partials, int G) {
+  if (st->done) return;
+  double s = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) {
+    st->rz = s;
+    if (!(s == s) || isinf(s)) { st->status = 7; st->done = 1; }
+  }
+}
+
+// alpha = rz / (p.q)
+__global__ void k_pcg_alpha(PcgState *st, const double *partials, int G) {
+  if (st->done) return;
+  double pq = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) {
+    st->pq = pq;
+    st->alpha = st->rz / pq;
+    if (!(st->alpha == st->alpha) || isinf(st->alpha)) { st->status = 7; st->done = 1; }
+  }
+}
+
+// x += alpha p; r -= alpha q; partial r.r
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_pcg_update(long long n, PcgState *st, const double *p, const double *q,
+             double *x, double *r, double *partials) {
+  if (st->done) return;
+  __shared__ double sm[NT / 32];
+  const double a = st->alpha;
+  double acc = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
+       i += (long long)gridDim.x * NT) {
+    x[i] += a * p[i];
+    const double ri = r[i] - a * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  acc = block_sum<double, NT>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// recursive residual test; a pass schedules the true-residual check
+__global__ void k_pcg_rr(PcgState *st, const double *partials, int G) {
+  if (st->done) return;
+  double rr = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) {
+    st->rr = rr;
+    st->its += 1;
+    if (!(rr == rr) || isinf(rr)) { st->status = 7; st->done = 1; return; }
+    st->check_true = (rr <= st->tol2) ? 1 : 0;
+    if (!st->check_true && st->its >= st->maxit) { st->status = 5; st->done = 1; }
+  }
+}
+
+// t = b - A x for the true-residual check, partial t.t
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_pcg_true_res(int n, const PcgState *st, const int *soff, const int *sw,
+               const int *col, const double *val, const double *b,
+               const double *x, double *t, double *partials) {
+  if (st->done || !st->check_true) return;
+  __shared__ double sm[NT / 32];
+  double acc = 0;
+  for (int r = blockIdx.x * NT + threadIdx.x; r < n; r += gridDim.x * NT) {
+    const int g = r >> 5, l = r & 31;
+    const int off = soff[g] + l, w = sw[g];
+    double ax = 0;
+    for (int kk = 0; kk < w; kk++) ax += val[off + kk * 32] * x[col[off + kk * 32]];
+    const double tr = b[r] - ax;
+    t[r] = tr;
+    acc += tr * tr;
+  }
+  acc = block_sum<double, NT>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void k_pcg_true_dec(PcgState *st, const double *partials, int G) {
+  if (st->done || !st->check_true) return;
+  double rt2 = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) {
+    st->rt2 = rt2;
+    st->check_true = 0;
+    if (rt2 <= st->tol2) { st->status = 0; st->done = 1; return; }
+    st->restart = 1;     // continue from the true residual
+    if (st->its >= st->maxit) { st->status = 5; st->done = 1; }
+  }
+}
+
+__global__ void k_pcg_copy_r(long long n, const PcgState *st, const double *t,
+                             double *r) {
+  if (st->done || !st->restart) return;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = t[i];
+}
+
+// beta = rz_new / rz (Hestenes-Stiefel) or (rz_new - r.z_old) / rz (flexible)
+__global__ void k_pcg_beta(PcgState *st, const double *partials, int G) {
+  if (st->done) return;
+  double rzn = warp_sum_partials(partials, G);
+  double rzo = warp_sum_partials(partials + G, G);
+  if (threadIdx.x == 0) {
+    double beta = st->flexible ? (rzn - rzo) / st->rz : rzn / st->rz;
+    if (st->restart) beta = 0.0;
+    st->beta = beta;
+    st->rz = rzn;
+    st->restart = 0;
+    if (!(rzn == rzn) || isinf(rzn)) { st->status = 7; st->done = 1; }
+  }
+}
+
+// p = z + beta p (and z_old = z for flexible CG)
+__global__ void k_pcg_p(long long n, const PcgState *st, const double *z,
+                        double *p, double *zold) {
+  if (st->done) return;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double zi = z[i];
+  p[i] = zi + st->beta * p[i];
+  if (zold) zold[i] = zi;
+}
+
+// ================================================================ Lanczos
+// c[j] partials of Q^T w over a CTA's row range, warp per column
+// (Q column-major, ld rows).  partials[blk * ncol + j].
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_gemvT_partial(int s, int ncol, const double *Q, long long ld, const double *w,
+                double *partials) {
+  const int nw = NT / 32, wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const long long chunk = ((long long)s + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * chunk;
+  const long long r1 = min((long long)s, r0 + chunk);
+  for (int j = wi; j < ncol; j += nw) {
+    const double *q = Q + (long long)j * ld;
+    double acc = 0;
+    for (long long r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (l == 0) partials[(long long)blockIdx.x * ncol + j] = acc;
+  }
+}
+
+// w -= Q c (c of length ncol)
+__global__ void k_gemvN_sub(int s, int ncol, const double *Q, long long ld,
+                            const double *c, double *w) {
+  extern __shared__ unsigned char smraw[];
+  double *cs = reinterpret_cast<double *>(smraw);
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  double acc = 0;
+  for (int j = 0; j < ncol; j++) acc += Q[(long long)j * ld + r] * cs[j];
+  w[r] -= acc;
+}
+
+// w -= alpha_j q_j + beta_{j-1} q_{j-1}
+__global__ void k_lz_three_term(int s, const double *al, const double *be, int j,
+                                const double *qj, const double *qjm1, double *w) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  double v = w[r] - al[j] * qj[r];
+  if (qjm1) v -= be[j - 1] * qjm1[r];
+  w[r] = v;
+}
+
+__global__ void k_scale_into(int s, const double *num, const double *den,
+                             double *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < s) out[r] = num[r] / (*den);
+}
+
+// Eigen-decomposition of the symmetric tridiagonal T_m (diagonal al, off-
+// diagonal be) by the implicit symmetric QR algorithm with Wilkinson shifts
+// (Golub & Van Loan, Sec. 8.3), in one CTA.  Thread 0 chases the bulge and
+// records the Givens rotations of a sweep; every thread then applies them to
+// its own row of Z.  Outputs: vals[m] descending; with Z != null, the
+// eigenvector columns (column-major m x m, ld m) sorted the same way into Y;
+// sum_topk (if non-null) = sum of the k largest values.
+// Work arrays (global): d[m], e[m], Z[m*m], cs[2m].
+__global__ void k_tridiag_eig(int m, const double *al, const double *be,
+                              double *d, double *e, double *Z, double *rot,
+                              double *vals, double *Y, int k, double *sum_topk,
+                              int *fail) {
+  __shared__ int s_lo, s_hi, s_cont, s_nrot;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) {
+    d[i] = al[i];
+    e[i] = (i + 1 < m) ? be[i] : 0.0;
+  }
+  if (Z)
+    for (long long i = tid; i < (long long)m * m; i += blockDim.x)
+      Z[i] = ((i % m) == (i / m)) ? 1.0 : 0.0;
+  if (tid == 0) { s_hi = m - 1; s_cont = 1; }
+  __syncthreads();
+  const double eps = 2.220446049250313e-16;
+  int guard = 0;
+  while (true) {
+    if (tid == 0) {
+      s_nrot = 0;
+      int hi = s_hi;
+      // deflate converged trailing eigenvalues
+      while (hi > 0 && fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+        e[hi - 1] = 0.0;
+        hi--;
+      }
+      s_hi = hi;
+      if (hi == 0 || guard > 60 * m) {
+        s_cont = 0;
+        if (hi != 0 && fail) *fail = 1;
+      } else {
+        int lo = hi - 1;
+        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) lo--;
+        if (lo > 0) e[lo - 1] = 0.0;
+        s_lo = lo;
+        // Wilkinson shift from the trailing 2 x 2 of the active block
+        const double dd = 0.5 * (d[hi - 1] - d[hi]);
+        const double bb = e[hi - 1];
+        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * hypot(dd, bb);
+        const double mu = d[hi] - (den != 0.0 ? bb * bb / den : 0.0);
+        double x = d[lo] - mu, z = e[lo], g = 0.0;
+        for (int kk = lo; kk < hi; kk++) {
+          double c, sn;
+          if (z == 0.0) { c = 1.0; sn = 0.0; }
+          else if (fabs(z) > fabs(x)) { double tau = -x / z; sn = 1.0 / sqrt(1.0 + tau * tau); c = sn * tau; }
+          else { double tau = -z / x; c = 1.0 / sqrt(1.0 + tau * tau); sn = c * tau; }
+          if (kk > lo) e[kk - 1] = c * e[kk - 1] - sn * g;
+          const double a0 = d[kk], a1 = d[kk + 1], b0 = e[kk];
+          d[kk] = c * c * a0 - 2.0 * c * sn * b0 + sn * sn * a1;
+          d[kk + 1] = sn * sn * a0 + 2.0 * c * sn * b0 + c * c * a1;
+          e[kk] = c * sn * (a0 - a1) + (c * c - sn * sn) * b0;
+          if (kk + 1 < hi) { g = -sn * e[kk + 1]; e[kk + 1] = c * e[kk + 1]; }
+          rot[2 * kk] = c;
+          rot[2 * kk + 1] = sn;
+          if (kk < hi - 1) { x = e[kk]; z = g; }
+        }
+        s_nrot = 1;
+      }
+    }
+    __syncthreads();
+    if (!s_cont) break;
+    if (Z && s_nrot) {
+      const int lo = s_lo, hi = s_hi;
+      for (int r = tid; r < m; r += blockDim.x)
+        for (int kk = lo; kk < hi; kk++) {
+          const double c = rot[2 * kk], sn = rot[2 * kk + 1];
+          const double zk = Z[(long long)kk * m + r], zk1 = Z[(long long)(kk + 1) * m + r];
+          Z[(long long)kk * m + r] = c * zk - sn * zk1;
+          Z[(long long)(kk + 1) * m + r] = sn * zk + c * zk1;
+        }
+    }
+    guard++;
+    __syncthreads();
+  }
+  __syncthreads();
+  // sort descending by rank; ties by index
+  for (int i = tid; i < m; i += blockDim.x) {
+    const double di = d[i];
+    int rank = 0;
+    for (int j = 0; j < m; j++) {
+      const double dj = d[j];
+      if (dj > di || (dj == di && j < i)) rank++;
+    }
+    vals[rank] = di;
+    if (Z && Y)
+      for (int r = 0; r < m; r++) Y[(long long)rank * m + r] = Z[(long long)i * m + r];
+  }
+  __syncthreads();
+  if (tid == 0 && sum_topk) {
+    double s = 0;
+    for (int i = 0; i < k && i < m; i++) s += vals[i];
+    *sum_topk = s;
+  }
+}
+
+// U (s x k row-major) = Q_m Y_k   (Ritz vectors; Q column-major ld, Y
+// column-major m x m with the wanted vectors in its first k columns)
+template <int CH>
+__global__ void k_ritz_gemm(int s, int m, int k, const double *Q, long long ld,
+                            const double *Y, double *U) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  for (int c0 = 0; c0 < k; c0 += CH) {
+    double acc[CH];
+#pragma unroll
+    for (int t = 0; t < CH; t++) acc[t] = 0;
+    for (int j = 0; j < m; j++) {
+      const double q = Q[(long long)j * ld + r];
+#pragma unroll
+      for (int t = 0; t < CH; t++)
+        if (c0 + t < k) acc[t] += q * Y[(long long)(c0 + t) * m + j];
+    }
+#pragma unroll
+    for (int t = 0; t < CH; t++)
+      if (c0 + t < k) U[r * k + c0 + t] = acc[t];
+  }
+}
+
+// DDLR-1 scalars: theta, 1/(1-theta) and D_c = (1-lambda_c)^-1 - (1-theta)^-1
+// (prop. gkt); flags NOT_SPD when lambda_max >= 1 or theta >= 1.
+__global__ void k_ddlr1_coef(int m, int k, int theta_mode, const double *vals,
+                             double *theta, double *inv1mt, double *coef,
+                             int *notspd) {
+  if (threadIdx.x != 0) return;
+  const double th = (theta_mode == 1 && k < m) ? vals[k] : 0.0;
+  *theta = th;
+  *inv1mt = 1.0 / (1.0 - th);
+  for (int c = 0; c < k; c++) coef[c] = 1.0 / (1.0 - vals[c]) - 1.0 / (1.0 - th);
+  if (!(vals[0] < 1.0) || !(th < 1.0)) *notspd = 1;
+}
+
+// column c of a row-major n x k matrix <-> contiguous vector
+__global__ void k_get_col(long long n, int k, int c, const double *M, double *v) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) v[r] = M[r * k + c];
+}
+__global__ void k_set_col(long long n, int k, int c, const double *v, double *M) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) M[r * k + c] = v[r];
+}
+
+// partials of K = U^T EV over row chunks (U, EV row-major n x k)
+__global__ void k_utv_partial(long long n, int k, const double *U,
+                              const double *EV, double *partials) {
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  for (int pr = threadIdx.x; pr < k * k; pr += blockDim.x) {
+    const int a = pr / k, b = pr % k;
+    double acc = 0;
+    for (long long r = r0; r < r1; r++) acc += U[r * k + a] * EV[r * k + b];
+    partials[(long long)blockIdx.x * k * k + pr] = acc;
+  }
+}
+
+// H_k = (I - (K + K^T)/2)^-1 by Cholesky (lemma 1 / prop. spd-2); failure of
+// the Cholesky flags NOT_SPD.  One thread; k is small.
+__global__ void k_hk_finalize(int G, int k, const double *partials, double *work,
+                              double *Hk, int *notspd) {
+  if (threadIdx.x != 0) return;
+  double *M = work;            // k x k
+  double *e = work + k * k;    // k
+  for (int a = 0; a < k; a++)
+    for (int b = 0; b < k; b++) {
+      double s1 = 0, s2 = 0;
+      for (int g = 0; g < G; g++) {
+        s1 += partials[(long long)g * k * k + a * k + b];
+        s2 += partials[(long long)g * k * k + b * k + a];
+      }
+      M[a * k + b] = (a == b ? 1.0 : 0.0) - 0.5 * (s1 + s2);
+    }
+  for (int j = 0; j < k; j++) {
+    double dj = M[j * k + j];
+    for (int t = 0; t < j; t++) dj -= M[j * k + t] * M[j * k + t];
+    if (!(dj > 0.0)) { *notspd = 1; return; }
+    dj = sqrt(dj);
+    M[j * k + j] = dj;
+    for (int i = j + 1; i < k; i++) {
+      double sm = M[i * k + j];
+      for (int t = 0; t < j; t++) sm -= M[i * k + t] * M[j * k + t];
+      M[i * k + j] = sm / dj;
+    }
+  }
+  for (int c = 0; c < k; c++) {
+    for (int r = 0; r < k; r++) e[r] = (r == c) ? 1.0 : 0.0;
+    for (int i = 0; i < k; i++) {
+      double sm = e[i];
+      for (int t = 0; t < i; t++) sm -= M[i * k + t] * e[t];
+      e[i] = sm / M[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; i--) {
+      double sm = e[i];
+      for (int t = i + 1; t < k; t++) sm -= M[t * k + i] * e[t];
+      e[i] = sm / M[i * k + i];
+    }
+    for (int r = 0; r < k; r++) Hk[r * k + c] = e[r];
+  }
+}
+
+}  // namespace ddlr
