@@ -175,7 +175,9 @@ def run_ours(args):
     h.reset_counters()
     barrier()
     t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("ddlr_timed")
     ms, infos = timed_steps(h, args.steps)
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()

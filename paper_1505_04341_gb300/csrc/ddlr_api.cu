@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -86,6 +87,11 @@ struct ddlr_ctx {
   double *fval = nullptr;     // factor values (CSR)
   double *l64 = nullptr, *u64 = nullptr, *dinv64 = nullptr, *eh64 = nullptr, *eht64 = nullptr;
   float *l32 = nullptr, *u32 = nullptr, *dinv32 = nullptr, *eh32 = nullptr, *eht32 = nullptr;
+  double *dinvs64 = nullptr;  // inverse diagonal in slice layout (TMA solve)
+  float *dinvs32 = nullptr;
+  int *row_slot = nullptr;
+  TmaCfg tma{};
+  bool use_tma = false;
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -197,11 +203,15 @@ struct ddlr_ctx {
 
 namespace {
 
+constexpr int kTmaStages = 3;          // depth of the TMA ring of the interior solve
+constexpr size_t kTmaSmemMax = 100 << 10;
+
 template <typename T> struct Prec;
 template <> struct Prec<double> {
   static const double *l(ddlr_ctx *c) { return c->l64; }
   static const double *u(ddlr_ctx *c) { return c->u64; }
   static const double *dinv(ddlr_ctx *c) { return c->dinv64; }
+  static const double *dinvs(ddlr_ctx *c) { return c->dinvs64; }
   static const double *eh(ddlr_ctx *c) { return c->eh64; }
   static const double *eht(ddlr_ctx *c) { return c->eht64; }
   static double *w(ddlr_ctx *c, int i) { return c->w64[i]; }
@@ -214,6 +224,7 @@ template <> struct Prec<float> {
   static const float *l(ddlr_ctx *c) { return c->l32; }
   static const float *u(ddlr_ctx *c) { return c->u32; }
   static const float *dinv(ddlr_ctx *c) { return c->dinv32; }
+  static const float *dinvs(ddlr_ctx *c) { return c->dinvs32; }
   static const float *eh(ddlr_ctx *c) { return c->eh32; }
   static const float *eht(ddlr_ctx *c) { return c->eht32; }
   static float *w(ddlr_ctx *c, int i) { return c->w32[i]; }
@@ -232,9 +243,16 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
   ck(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0), "wait");
-  if (P.p > 0)
-    KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks<T, 256>), P.p, 256, 0,
-       c->S, lv, uv, di, x, z, gate);
+  if (P.p > 0) {
+    if (c->use_tma) {
+      const size_t sm = tma_smem_bytes<T, kTmaStages>(c->tma);
+      KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_tma<T, 256, kTmaStages>), P.p, 256, sm,
+         c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, c->tma, c->dflag + 3);
+    } else {
+      KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks<T, 256>), P.p, 256, 0,
+         c->S, lv, uv, di, x, z, gate);
+    }
+  }
   const int l0 = P.blk_lvl0[P.p], l1 = P.blk_lvl0[P.p + 1];
   for (int l = l0; l < l1; l++) {
     const int mode = (l == l1 - 1) ? 2 : 0;
@@ -372,12 +390,10 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     double *cvec = (double *)talloc(sizeof(double) * (mmax + 2));
     double *w = (double *)talloc(sizeof(double) * s);
     double *nrm = (double *)talloc(sizeof(double) * 4);
-    double *ed = (double *)talloc(sizeof(double) * mmax);
-    double *ee = (double *)talloc(sizeof(double) * mmax);
-    double *eZ = (double *)talloc(sizeof(double) * size_t(mmax) * mmax);
-    double *erot = (double *)talloc(sizeof(double) * 2 * mmax);
+    double *ework = (double *)talloc(sizeof(double) * 5 * size_t(mmax) * k);
+    double *etop = (double *)talloc(sizeof(double) * (k + 1));
     double *evals = (double *)talloc(sizeof(double) * mmax);
-    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * mmax);
+    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * k);
     double *esum = (double *)talloc(sizeof(double) * 2);
     ck(cudaMemsetAsync(be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
     // start vector: SplitMix64 stream `seed + restart`, drawn for the interface
@@ -422,10 +438,9 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       scale = std::max(scale, std::fabs(ab[0]));
       mm = j + 1;
       if (check > 0 && mm % check == 0 && mm >= k + 1) {
-        KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm, al, be, ed, ee, (double *)nullptr,
-           erot, evals, (double *)nullptr, k, esum, c->dflag + 2);
-        KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm - 1, al, be, ed, ee, (double *)nullptr,
-           erot, evals, (double *)nullptr, k, esum + 1, c->dflag + 2);
+        const size_t smk = 2 * mm * sizeof(double) + 1024 * sizeof(int);
+        KL(c, "eig_check", c->stream, k_tridiag_values, 1, 1024, smk, mm, al, be, k, etop, esum);
+        KL(c, "eig_check", c->stream, k_tridiag_values, 1, 1024, smk, mm - 1, al, be, k, etop, esum + 1);
         read_dev(c, c->h_pin, esum, 2 * sizeof(double));
         if (std::fabs(c->h_pin[0] - c->h_pin[1]) < eps * std::fabs(c->h_pin[1])) break;
       }
@@ -448,10 +463,12 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     if (st == DDLR_OK) {
       c->msteps = mm;
-      KL(c, "eig", c->stream, k_tridiag_eig, 1, 256, 0, mm, al, be, ed, ee, eZ, erot, evals, eY, k,
-         (double *)nullptr, c->dflag + 2);
-      c->ritz.assign(mm, 0.0);
-      read_dev(c, c->ritz.data(), evals, sizeof(double) * mm);
+      const int nvals = std::min(mm, 1024);
+      KL(c, "eig", c->stream, k_tridiag_values, 1, 1024, 2 * mm * sizeof(double) + 1024 * sizeof(int),
+         mm, al, be, nvals, evals, (double *)nullptr);
+      KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, al, be, k, evals, eY, ework);
+      c->ritz.assign(nvals, 0.0);
+      read_dev(c, c->ritz.data(), evals, sizeof(double) * nvals);
       if (c->opt.variant == 1) {
         KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, Q, (long long)s, eY, c->U64);
         KL(c, "ritz", c->stream, k_ddlr1_coef, 1, 32, 0, mm, k, c->opt.theta_mode, evals,
@@ -480,9 +497,10 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
         KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, kp, hw, c->Hk64, c->dflag + 1);
         c->theta = 0.0;
       }
-      int fl[3];
+      int fl[4];
       read_dev(c, fl, c->dflag, sizeof(fl));
-      if (fl[2]) st = DDLR_ERR_NAN;
+      if (fl[3]) st = DDLR_ERR_TIMEOUT;
+      else if (fl[2]) st = DDLR_ERR_NAN;
       else if (fl[1]) st = DDLR_ERR_NOT_SPD;
     }
     sync(c);
@@ -516,6 +534,8 @@ void make_low_precision(ddlr_ctx *c) {
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ll), kThreads, 0, ll, c->l64, c->l32, (const int *)nullptr);
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(lu), kThreads, 0, lu, c->u64, c->u32, (const int *)nullptr);
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(P.n), kThreads, 0, (long long)P.n, c->dinv64, c->dinv32, (const int *)nullptr);
+  const long long nds = (long long)P.nslice * kSlice;
+  KL(c, "setup", c->stream, (k_cast<float, double>), nblk(nds), kThreads, 0, nds, c->dinvs64, c->dinvs32, (const int *)nullptr);
   const long long ne = (long long)P.eh_ci.size();
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ne), kThreads, 0, ne, c->eh64, c->eh32, (const int *)nullptr);
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ne), kThreads, 0, ne, c->eht64, c->eht32, (const int *)nullptr);
@@ -560,9 +580,10 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   ck(cudaMemsetAsync(c->l64, 0, sizeof(double) * P.l_col.size(), c->stream), "memset");
   ck(cudaMemsetAsync(c->u64, 0, sizeof(double) * P.u_col.size(), c->stream), "memset");
   KL(c, "setup", c->stream, k_solve_layout<double>, nblk(nf), kThreads, 0, (int)nf, c->f_row, c->f_rp,
-     c->map_l, c->map_u, c->fval, c->l64, c->u64, c->dinv64);
+     c->map_l, c->map_u, c->row_slot, c->fval, c->l64, c->u64, c->dinv64, c->dinvs64);
   int fl[4];
   read_dev(c, fl, c->dflag, sizeof(fl));
+  if (fl[3]) { c->err = "a bounded device wait timed out"; return DDLR_ERR_TIMEOUT; }
   if (fl[0]) {
     c->err = "non-positive pivot in a local factorisation";
     return DDLR_ERR_BREAKDOWN;
@@ -613,6 +634,24 @@ void allocate(ddlr_ctx *c) {
   c->l64 = c->alloc<double>(P.l_col.size());
   c->u64 = c->alloc<double>(P.u_col.size());
   c->dinv64 = c->alloc<double>(n);
+  c->dinvs64 = c->alloc<double>(size_t(P.nslice) * kSlice);
+  ck(cudaMemsetAsync(c->dinvs64, 0, sizeof(double) * size_t(P.nslice) * kSlice, c->stream), "memset");
+  c->row_slot = c->upload(P.row_slot);
+  c->tma = TmaCfg{P.tma_zs, P.tma_nl, P.tma_ns, P.tma_e, P.tma_s};
+  {
+    const char *env = getenv("DDLR_NO_TMA");
+    const bool off = env && env[0] == '1';
+    const size_t need = c->opt.precision == 1 ? tma_smem_bytes<float, kTmaStages>(c->tma)
+                                               : tma_smem_bytes<double, kTmaStages>(c->tma);
+    c->use_tma = !off && P.tma_zs > 0 && need <= kTmaSmemMax;
+    ck(cudaFuncSetAttribute(k_tridiag_values, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10), "attr");
+    if (c->use_tma) {
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256, kTmaStages>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax)), "attr");
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<float, 256, kTmaStages>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax)), "attr");
+    }
+  }
   c->eh64 = c->alloc<double>(P.eh_ci.size());
   c->eht64 = c->alloc<double>(P.eht_ci.size());
   c->urows = c->opt.variant == 1 ? P.s : n;
@@ -633,6 +672,7 @@ void allocate(ddlr_ctx *c) {
     c->l32 = c->alloc<float>(P.l_col.size());
     c->u32 = c->alloc<float>(P.u_col.size());
     c->dinv32 = c->alloc<float>(n);
+    c->dinvs32 = c->alloc<float>(size_t(P.nslice) * kSlice);
     c->eh32 = c->alloc<float>(P.eh_ci.size());
     c->eht32 = c->alloc<float>(P.eht_ci.size());
     if (c->opt.uk_bf16) c->Ub16 = c->alloc<__nv_bfloat16>(size_t(c->urows) * k);
@@ -696,9 +736,12 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   KL(c, "pcg", c->stream, k_resid2_partial<256>, kRedGrid, 256, 0, (long long)n, b, q, part);
   KL(c, "pcg", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, part, c->w64[7], 0, (const int *)nullptr);
   PcgState hs;
+  int dfl[4];
   ck(cudaMemcpyAsync(c->h_pin, c->w64[7], sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
   ck(cudaMemcpyAsync(&hs, c->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  ck(cudaMemcpyAsync(dfl, c->dflag, sizeof(dfl), cudaMemcpyDeviceToHost, c->stream), "D2H");
   sync(c);
+  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
   if (info) {
     info->its = hs.its;
     info->relres = hs.bb > 0 ? std::sqrt(c->h_pin[0] / hs.bb) : 0.0;

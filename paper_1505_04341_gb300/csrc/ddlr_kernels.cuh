@@ -109,12 +109,14 @@ __global__ void k_ic_level(int cnt, const int *rows, const int *f_rp,
 template <typename T>
 __global__ void k_solve_layout(int nf, const int *f_row, const int *f_rp,
                                const int *map_l, const int *map_u,
-                               const double *fval, T *lval, T *uval, T *dinv) {
+                               const int *row_slot, const double *fval, T *lval,
+                               T *uval, T *dinv, T *dinv_s) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nf) return;
   const int g = f_row[q];
   if (q == f_rp[g + 1] - 1) {
     dinv[g] = T(1.0 / fval[q]);
+    dinv_s[row_slot[g]] = T(1.0 / fval[q]);
   } else {
     lval[map_l[q]] = T(fval[q]);
     uval[map_u[q]] = T(fval[q]);
@@ -168,6 +170,160 @@ k_sptrsv_blocks(SolveLayout S, const T *lval, const T *uval, const T *dinv,
       solve_row<T, false>(S, uval, dinv, x, z, s0 + (i >> 5), i & 31, r0 + i);
     __syncthreads();
   }
+}
+
+// ----------------------------------------- TMA-pipelined interior solves
+// Shared-memory capacities (elements) of k_sptrsv_blocks_tma, computed on the
+// host over all interior blocks.
+struct TmaCfg {
+  int zs_cap;   // rows of the largest block
+  int nl_cap;   // levels of the deepest block
+  int ns_cap;   // slices of the largest block + 1
+  int e_cap;    // sliced-ELL entries of the largest level (L or L^T)
+  int s_cap;    // slices of the widest level
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared (TMA), completion counted on `bar`
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ size_t al128(size_t b) { return (b + 127) & ~size_t(127); }
+
+template <typename T>
+__host__ __device__ inline size_t tma_slot_bytes(const TmaCfg &c) {
+  return ((size_t(c.e_cap) * sizeof(T) + 127) & ~size_t(127)) +
+         ((size_t(c.e_cap) * 4 + 127) & ~size_t(127)) +
+         ((size_t(c.s_cap) * 32 * sizeof(T) + 127) & ~size_t(127));
+}
+template <typename T, int D>
+__host__ __device__ inline size_t tma_smem_bytes(const TmaCfg &c) {
+  return 128 + D * tma_slot_bytes<T>(c) + ((size_t(c.zs_cap) * sizeof(T) + 127) & ~size_t(127)) +
+         ((size_t(3 * c.nl_cap) * 4 + 127) & ~size_t(127)) + size_t(4 * c.ns_cap) * 4;
+}
+
+// All interior blocks of A0 in one launch, one CTA per block (Sec. 4.2: the p
+// local solves are independent).  The block's solution lives in shared
+// memory; the sliced-ELL data of each level (values, column indices and the
+// inverse diagonal in slice layout, all 128-byte aligned) is brought in by
+// 1-D TMA bulk copies into a ring of D stages issued D levels ahead, so the
+// level chain only waits on shared memory.  Forward sweep with L, backward
+// sweep with L^T, one CTA barrier per level.  Waits are bounded: on timeout
+// *err is set and the CTA returns.
+template <typename T, int NT, int D>
+__global__ void __launch_bounds__(NT)
+k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s,
+                    const T *x, T *z, const int *gate, TmaCfg cfg, int *err) {
+  if (gate && *gate) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
+  const size_t slot_bytes = tma_slot_bytes<T>(cfg);
+  const size_t o_col = al128(size_t(cfg.e_cap) * sizeof(T));
+  const size_t o_din = o_col + al128(size_t(cfg.e_cap) * 4);
+  unsigned char *ring = smraw + 128;
+  T *zs = reinterpret_cast<T *>(ring + D * slot_bytes);
+  int *lt = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(zs) + al128(size_t(cfg.zs_cap) * sizeof(T)));
+  int *st = lt + ((3 * cfg.nl_cap + 31) & ~31);
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int l0 = S.blk_lvl0[b], l1 = S.blk_lvl0[b + 1], NL = l1 - l0;
+  if (NL == 0) return;
+  const int rb0 = S.lvl_row0[l0], sb0 = S.lvl_slice0[l0];
+  const int NS = S.lvl_slice0[l1] - sb0;
+  const int nb = S.lvl_row0[l1 - 1] + S.lvl_nrows[l1 - 1] - rb0;
+  for (int i = tid; i < NL; i += NT) {
+    lt[3 * i] = S.lvl_row0[l0 + i] - rb0;
+    lt[3 * i + 1] = S.lvl_nrows[l0 + i];
+    lt[3 * i + 2] = S.lvl_slice0[l0 + i] - sb0;
+  }
+  for (int i = tid; i <= NS; i += NT) {
+    st[4 * i] = S.l_soff[sb0 + i];
+    st[4 * i + 1] = i < NS ? S.l_sw[sb0 + i] : 0;
+    st[4 * i + 2] = S.u_soff[sb0 + i];
+    st[4 * i + 3] = i < NS ? S.u_sw[sb0 + i] : 0;
+  }
+  for (int i = tid; i < nb; i += NT) zs[i] = x[rb0 + i];
+  if (tid == 0) {
+    for (int q = 0; q < D; q++) mbar_init(bar + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const int nstage = 2 * NL;
+  // stage j: forward level j (j < NL) or backward level 2NL-1-j
+  auto issue = [&](int j) {
+    const bool fwd = j < NL;
+    const int li = fwd ? j : nstage - 1 - j;
+    const int sa = lt[3 * li + 2];
+    const int sbn = (li + 1 < NL) ? lt[3 * (li + 1) + 2] : NS;
+    const int oa = st[4 * sa + (fwd ? 0 : 2)], ob = st[4 * sbn + (fwd ? 0 : 2)];
+    const int ne = ob - oa, nsl = sbn - sa;
+    unsigned char *slot = ring + size_t(j % D) * slot_bytes;
+    const unsigned bytes = unsigned(ne) * (unsigned)(sizeof(T) + 4) + unsigned(nsl) * 32u * (unsigned)sizeof(T);
+    mbar_expect_tx(bar + (j % D), bytes);
+    if (ne > 0) {
+      tma_load_1d(slot, (fwd ? lval : uval) + oa, unsigned(ne) * (unsigned)sizeof(T), bar + (j % D));
+      tma_load_1d(slot + o_col, (fwd ? S.l_col : S.u_col) + oa, unsigned(ne) * 4u, bar + (j % D));
+    }
+    tma_load_1d(slot + o_din, dinv_s + size_t(sb0 + sa) * 32, unsigned(nsl) * 32u * (unsigned)sizeof(T),
+                bar + (j % D));
+  };
+  if (tid == 0)
+    for (int j = 0; j < D && j < nstage; j++) issue(j);
+  for (int j = 0; j < nstage; j++) {
+    const unsigned par = unsigned(j / D) & 1u;
+    if (!mbar_try_wait(bar + (j % D), par)) {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(bar + (j % D), par)) {
+        if (clock64() - t0 > (1LL << 32)) { *err = 1; return; }
+      }
+    }
+    const bool fwd = j < NL;
+    const int li = fwd ? j : nstage - 1 - j;
+    const int r0 = lt[3 * li], nr = lt[3 * li + 1], sa = lt[3 * li + 2];
+    const int oa = st[4 * sa + (fwd ? 0 : 2)];
+    const unsigned char *slot = ring + size_t(j % D) * slot_bytes;
+    const T *sv = reinterpret_cast<const T *>(slot);
+    const int *sc = reinterpret_cast<const int *>(slot + o_col);
+    const T *sd = reinterpret_cast<const T *>(slot + o_din);
+    for (int i = tid; i < nr; i += NT) {
+      const int sl = sa + (i >> 5), ln = i & 31;
+      const int o = st[4 * sl + (fwd ? 0 : 2)] - oa + ln, w = st[4 * sl + (fwd ? 1 : 3)];
+      T acc = zs[r0 + i];
+      for (int kk = 0; kk < w; kk++) acc -= sv[o + 32 * kk] * zs[sc[o + 32 * kk] - rb0];
+      zs[r0 + i] = acc * sd[i];
+    }
+    __syncthreads();
+    if (tid == 0 && j + D < nstage) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j + D);
+    }
+  }
+  for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
 }
 
 // One level of one block (used for C_a, whose levels span the whole GPU):
@@ -640,106 +796,202 @@ __global__ void k_scale_into(int s, const double *num, const double *den,
   if (r < s) out[r] = num[r] / (*den);
 }
 
-// Eigen-decomposition of the symmetric tridiagonal T_m (diagonal al, off-
-// diagonal be) by the implicit symmetric QR algorithm with Wilkinson shifts
-// (Golub & Van Loan, Sec. 8.3), in one CTA.  Thread 0 chases the bulge and
-// records the Givens rotations of a sweep; every thread then applies them to
-// its own row of Z.  Outputs: vals[m] descending; with Z != null, the
-// eigenvector columns (column-major m x m, ld m) sorted the same way into Y;
-// sum_topk (if non-null) = sum of the k largest values.
-// Work arrays (global): d[m], e[m], Z[m*m], cs[2m].
-__global__ void k_tridiag_eig(int m, const double *al, const double *be,
-                              double *d, double *e, double *Z, double *rot,
-                              double *vals, double *Y, int k, double *sum_topk,
-                              int *fail) {
-  __shared__ int s_lo, s_hi, s_cont, s_nrot;
+// ------------------------------------------------ tridiagonal eigensolver
+// Eigenvalues of the symmetric tridiagonal T_m (diagonal al, off-diagonal be)
+// by Sturm-sequence multisection, eigenvectors by inverse iteration
+// (Wilkinson; Golub & Van Loan Sec. 8.4-8.5).  Everything is parallel and
+// uses fused multiply-adds only in the inner loops: FP64 division and square
+// root are slow on this part, and one-thread QR sweeps were the bottleneck.
+
+// number of eigenvalues of T smaller than x: sign changes of the three-term
+// Sturm recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, rescaled by
+// powers of two (exact) to stay in range; a zero term counts as a change
+__device__ __forceinline__ int sturm_count(int m, const double *a, const double *b2, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int cnt = 0;
+  if (p == 0.0) p = -1e-300;
+  if (p < 0.0) cnt++;
+  for (int i = 1; i < m; i++) {
+    double q = fma(a[i] - x, p, -b2[i - 1] * pm);
+    if (q == 0.0) q = (p > 0.0) ? -1e-300 * fabs(p) : 1e-300 * fabs(p);
+    if ((q < 0.0) != (p < 0.0)) cnt++;
+    pm = p;
+    p = q;
+    const double ap = fabs(p);
+    if (ap > 0x1.0p+500) { p *= 0x1.0p-500; pm *= 0x1.0p-500; }
+    else if (ap < 0x1.0p-500) { p *= 0x1.0p+500; pm *= 0x1.0p+500; }
+  }
+  return cnt;
+}
+
+// The nv largest eigenvalues of T_m, descending, into vals (and their sum
+// into *sum when non-null).  G = blockDim/nv threads share one eigenvalue and
+// evaluate G interior points of its bracket per round (nv <= blockDim).
+// Dynamic shared memory: 2m doubles + blockDim ints.
+__global__ void k_tridiag_values(int m, const double *al, const double *be,
+                                 int nv, double *vals, double *sum) {
+  extern __shared__ double shm[];
+  double *a = shm, *b2 = shm + m;
+  int *cnts = reinterpret_cast<int *>(shm + 2 * m);
   const int tid = threadIdx.x;
   for (int i = tid; i < m; i += blockDim.x) {
-    d[i] = al[i];
-    e[i] = (i + 1 < m) ? be[i] : 0.0;
+    a[i] = al[i];
+    b2[i] = (i + 1 < m) ? be[i] * be[i] : 0.0;
   }
-  if (Z)
-    for (long long i = tid; i < (long long)m * m; i += blockDim.x)
-      Z[i] = ((i % m) == (i / m)) ? 1.0 : 0.0;
-  if (tid == 0) { s_hi = m - 1; s_cont = 1; }
   __syncthreads();
-  const double eps = 2.220446049250313e-16;
-  int guard = 0;
-  while (true) {
-    if (tid == 0) {
-      s_nrot = 0;
-      int hi = s_hi;
-      // deflate converged trailing eigenvalues
-      while (hi > 0 && fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-        e[hi - 1] = 0.0;
-        hi--;
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; i++) {
+    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  const double span = fmax(hi - lo, 1e-300);
+  lo -= 1e-9 * span;
+  hi += 1e-9 * span;
+  const int G = max(1, (int)blockDim.x / max(nv, 1));
+  const int gi = tid / G, gt = tid % G;
+  const bool active = gi < nv;
+  const int target = m - 1 - gi;     // eigenvalue gi (0 = largest)
+  double blo = lo, bhi = hi;
+  const int rounds = (int)ceil(60.0 / log2((double)G + 1.0));
+  for (int round = 0; round < rounds; round++) {
+    if (active) cnts[tid] = sturm_count(m, a, b2, blo + (bhi - blo) * double(gt + 1) / double(G + 1));
+    __syncthreads();
+    if (active) {
+      double nlo = blo, nhi = bhi;
+      for (int t = 0; t < G; t++) {
+        const double xt = blo + (bhi - blo) * double(t + 1) / double(G + 1);
+        if (cnts[gi * G + t] <= target) nlo = xt;
+        else { nhi = xt; break; }
       }
-      s_hi = hi;
-      if (hi == 0 || guard > 60 * m) {
-        s_cont = 0;
-        if (hi != 0 && fail) *fail = 1;
+      blo = nlo;
+      bhi = nhi;
+    }
+    __syncthreads();
+  }
+  if (active && gt == 0) vals[gi] = 0.5 * (blo + bhi);
+  __syncthreads();
+  if (sum && tid == 0) {
+    double sacc = 0;
+    for (int i = 0; i < nv; i++) sacc += vals[i];
+    *sum = sacc;
+  }
+}
+
+// Eigenvectors of T_m for the nv given eigenvalues (descending) by inverse
+// iteration: one thread per vector factors T - lambda I by Gaussian
+// elimination with partial pivoting (tridiagonal, second superdiagonal from
+// the row swaps) and solves three times from a fixed start vector,
+// normalising each time.  Vectors whose eigenvalues lie within 1e-3 ||T|| of
+// each other (a cluster) are then re-orthogonalised by modified Gram-Schmidt
+// in order.  Y is column-major m x nv; work holds 5m doubles per vector.
+__global__ void k_tridiag_vectors(int m, const double *al, const double *be,
+                                  int nv, const double *vals, double *Y,
+                                  double *work) {
+  __shared__ double red[32];
+  __shared__ double s_tn;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double tn = 0;
+    for (int i = 0; i < m; i++)
+      tn = fmax(tn, fabs(al[i]) + (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0));
+    s_tn = fmax(tn, 1e-300);
+  }
+  __syncthreads();
+  const double tnorm = s_tn;
+  for (int v = tid; v < nv; v += blockDim.x) {
+    double *d = work + size_t(v) * 5 * m, *du = d + m, *du2 = du + m, *dl = du2 + m, *y = dl + m;
+    const double lam = vals[v];
+    for (int i = 0; i < m; i++) {
+      d[i] = al[i] - lam;
+      du[i] = (i + 1 < m) ? be[i] : 0.0;
+      du2[i] = 0.0;
+    }
+    double *flags = y;   // flags[i] = 1 when rows i and i+1 were swapped
+    for (int i = 0; i + 1 < m; i++) {
+      const double sub = be[i];
+      if (fabs(d[i]) >= fabs(sub)) {
+        const double piv_d = (d[i] != 0.0) ? d[i] : 1e-15 * tnorm;
+        d[i] = piv_d;
+        const double l = sub / piv_d;
+        dl[i] = l;
+        d[i + 1] -= l * du[i];
+        flags[i] = 0.0;
       } else {
-        int lo = hi - 1;
-        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) lo--;
-        if (lo > 0) e[lo - 1] = 0.0;
-        s_lo = lo;
-        // Wilkinson shift from the trailing 2 x 2 of the active block
-        const double dd = 0.5 * (d[hi - 1] - d[hi]);
-        const double bb = e[hi - 1];
-        const double den = dd + (dd >= 0 ? 1.0 : -1.0) * hypot(dd, bb);
-        const double mu = d[hi] - (den != 0.0 ? bb * bb / den : 0.0);
-        double x = d[lo] - mu, z = e[lo], g = 0.0;
-        for (int kk = lo; kk < hi; kk++) {
-          double c, sn;
-          if (z == 0.0) { c = 1.0; sn = 0.0; }
-          else if (fabs(z) > fabs(x)) { double tau = -x / z; sn = 1.0 / sqrt(1.0 + tau * tau); c = sn * tau; }
-          else { double tau = -z / x; c = 1.0 / sqrt(1.0 + tau * tau); sn = c * tau; }
-          if (kk > lo) e[kk - 1] = c * e[kk - 1] - sn * g;
-          const double a0 = d[kk], a1 = d[kk + 1], b0 = e[kk];
-          d[kk] = c * c * a0 - 2.0 * c * sn * b0 + sn * sn * a1;
-          d[kk + 1] = sn * sn * a0 + 2.0 * c * sn * b0 + c * c * a1;
-          e[kk] = c * sn * (a0 - a1) + (c * c - sn * sn) * b0;
-          if (kk + 1 < hi) { g = -sn * e[kk + 1]; e[kk + 1] = c * e[kk + 1]; }
-          rot[2 * kk] = c;
-          rot[2 * kk + 1] = sn;
-          if (kk < hi - 1) { x = e[kk]; z = g; }
-        }
-        s_nrot = 1;
+        const double l = d[i] / sub;
+        dl[i] = l;
+        const double old_du = du[i];
+        d[i] = sub;
+        du[i] = d[i + 1];
+        const double nxt = (i + 1 < m - 1) ? du[i + 1] : 0.0;
+        du2[i] = nxt;
+        d[i + 1] = old_du - l * du[i];
+        if (i + 1 < m - 1) du[i + 1] = -l * nxt;
+        flags[i] = 1.0;
       }
     }
-    __syncthreads();
-    if (!s_cont) break;
-    if (Z && s_nrot) {
-      const int lo = s_lo, hi = s_hi;
-      for (int r = tid; r < m; r += blockDim.x)
-        for (int kk = lo; kk < hi; kk++) {
-          const double c = rot[2 * kk], sn = rot[2 * kk + 1];
-          const double zk = Z[(long long)kk * m + r], zk1 = Z[(long long)(kk + 1) * m + r];
-          Z[(long long)kk * m + r] = c * zk - sn * zk1;
-          Z[(long long)(kk + 1) * m + r] = sn * zk + c * zk1;
-        }
+    if (d[m - 1] == 0.0) d[m - 1] = 1e-15 * tnorm;
+    double *b = Y + size_t(v) * m;
+    for (int r = 0; r < m; r++) {
+      // start vector: 1 + small deterministic perturbation per (v, r)
+      unsigned int h = (unsigned)(r * 2654435761u) ^ (unsigned)(v * 40503u + 12345u);
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      b[r] = 1.0 + 0.5 * (double(h & 0xffff) / 65536.0 - 0.5);
     }
-    guard++;
-    __syncthreads();
+    for (int it = 0; it < 3; it++) {
+      // forward: apply the row swaps and multipliers
+      for (int i = 0; i + 1 < m; i++) {
+        if (flags[i] != 0.0) { const double t = b[i]; b[i] = b[i + 1]; b[i + 1] = t; }
+        b[i + 1] -= dl[i] * b[i];
+      }
+      // back substitution with U (diag d, super du, second super du2)
+      b[m - 1] = b[m - 1] / d[m - 1];
+      if (m > 1) b[m - 2] = (b[m - 2] - du[m - 2] * b[m - 1]) / d[m - 2];
+      for (int i = m - 3; i >= 0; i--) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / d[i];
+      double nn = 0;
+      for (int r = 0; r < m; r++) nn = fma(b[r], b[r], nn);
+      const double inv = 1.0 / sqrt(nn);
+      for (int r = 0; r < m; r++) b[r] *= inv;
+    }
   }
   __syncthreads();
-  // sort descending by rank; ties by index
-  for (int i = tid; i < m; i += blockDim.x) {
-    const double di = d[i];
-    int rank = 0;
-    for (int j = 0; j < m; j++) {
-      const double dj = d[j];
-      if (dj > di || (dj == di && j < i)) rank++;
+  // modified Gram-Schmidt inside clusters, in order of decreasing eigenvalue
+  for (int v = 1; v < nv; v++) {
+    double *yv = Y + size_t(v) * m;
+    int first = v;
+    while (first > 0 && fabs(vals[first - 1] - vals[first]) <= 1e-3 * tnorm) first--;
+    if (first == v) continue;
+    for (int j = first; j < v; j++) {
+      const double *yj = Y + size_t(j) * m;
+      double part = 0;
+      for (int r = tid; r < m; r += blockDim.x) part = fma(yv[r], yj[r], part);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      if ((tid & 31) == 0) red[tid >> 5] = part;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        red[0] = t;
+      }
+      __syncthreads();
+      const double dt = red[0];
+      for (int r = tid; r < m; r += blockDim.x) yv[r] -= dt * yj[r];
+      __syncthreads();
     }
-    vals[rank] = di;
-    if (Z && Y)
-      for (int r = 0; r < m; r++) Y[(long long)rank * m + r] = Z[(long long)i * m + r];
-  }
-  __syncthreads();
-  if (tid == 0 && sum_topk) {
-    double s = 0;
-    for (int i = 0; i < k && i < m; i++) s += vals[i];
-    *sum_topk = s;
+    double part = 0;
+    for (int r = tid; r < m; r += blockDim.x) part = fma(yv[r], yv[r], part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+      red[0] = 1.0 / sqrt(t);
+    }
+    __syncthreads();
+    const double sc = red[0];
+    for (int r = tid; r < m; r += blockDim.x) yv[r] *= sc;
+    __syncthreads();
   }
 }
 

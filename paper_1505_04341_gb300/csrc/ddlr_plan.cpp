@@ -371,6 +371,23 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       }
     }
   }
+  // inverse diagonal in slice layout, and the capacities of the TMA solve
+  P.row_slot.assign(n, 0);
+  for (int l = 0; l < nlev; l++)
+    for (int i = 0; i < P.lvl_nrows[l]; i++)
+      P.row_slot[P.lvl_row0[l] + i] = (P.lvl_slice0[l] + i / kSlice) * kSlice + i % kSlice;
+  for (int b = 0; b < p; b++) {
+    const int l0 = P.blk_lvl0[b], l1 = P.blk_lvl0[b + 1];
+    if (l1 == l0) continue;
+    P.tma_zs = std::max(P.tma_zs, P.blk_row0[b + 1] - P.blk_row0[b]);
+    P.tma_nl = std::max(P.tma_nl, l1 - l0);
+    P.tma_ns = std::max(P.tma_ns, P.lvl_slice0[l1] - P.lvl_slice0[l0] + 1);
+    for (int l = l0; l < l1; l++) {
+      const int s0 = P.lvl_slice0[l], s1 = P.lvl_slice0[l + 1];
+      P.tma_e = std::max(P.tma_e, std::max(P.l_soff[s1] - P.l_soff[s0], P.u_soff[s1] - P.u_soff[s0]));
+      P.tma_s = std::max(P.tma_s, s1 - s0);
+    }
+  }
   return DDLR_OK;
 }
 

@@ -50,6 +50,9 @@ struct Plan {
   std::vector<int> l_soff, l_sw, l_col;   // strictly lower part of L
   std::vector<int> u_soff, u_sw, u_col;   // strictly upper part of L^T
   std::vector<int> map_l, map_u;          // factor entry -> slot (-1 for diagonal)
+  std::vector<int> row_slot;              // row -> slice*32 + lane (inverse diagonal in slice layout)
+  // shared-memory capacities of the TMA-pipelined interior solve
+  int tma_zs = 0, tma_nl = 0, tma_ns = 0, tma_e = 0, tma_s = 0;
   // statistics
   int levels_interior = 0, levels_c = 0, ncolors = 0;
   long long nnz_ehat = 0, nnz_factor = 0;

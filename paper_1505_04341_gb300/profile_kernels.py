@@ -1,0 +1,84 @@
+"""Kernel driver for profiling and timing one operation of the library.
+
+Builds the preconditioner for a named workload and repeats one operation --
+an A0 solve, an M^-1 apply or a PCG solve -- with device-resident vectors,
+printing the CUDA-event time per repetition and the algorithmic bytes.  Used
+as the command under ncu for the kernel summaries in profiles/:
+
+    python -m paper_1505_04341_gb300.profile_kernels --workload lap3d_128_b8 \
+        --op a0 --reps 5 [--variant 1] [--k 16] [--precision 0]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="lap3d_64_b4")
+    ap.add_argument("--op", default="a0", choices=["a0", "apply", "pcg"])
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--variant", type=int, default=1)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--bf16", type=int, default=1)
+    ap.add_argument("--c-order", type=int, default=1)
+    ap.add_argument("--lanczos-max", type=int, default=0)
+    args = ap.parse_args(argv)
+
+    import torch
+
+    import workloads as W
+    from paper_1505_04341_gb300 import DDLR, build
+
+    build()
+    w = W.workload(args.workload)
+    A, part, p = w["A"], w["part"], w["p"]
+    n = A[0]
+    h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=0,
+             c_order=args.c_order, precision=args.precision, uk_bf16=args.bf16,
+             lanczos_max=args.lanczos_max)
+    b = torch.tensor(W.rhs(n, 0), device="cuda")
+    y = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+
+    def once():
+        if args.op == "a0":
+            h.a0_solve(b, y)
+        elif args.op == "apply":
+            h.apply(b, y)
+        else:
+            h.pcg(b, y, tol=1e-8)
+
+    once()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    tr = h.traffic()
+    byts = tr["a0_bytes"] if args.op == "a0" else tr["apply_bytes"]
+    best = min(times)
+    print(json.dumps({"workload": args.workload, "op": args.op, "ms": times,
+                      "best_ms": best, "algorithmic_bytes": byts,
+                      "GBps_best": byts / (best * 1e-3) / 1e9 if args.op != "pcg" else None,
+                      "info": {k: v for k, v in h.info().items()
+                               if k in ("n", "s", "p", "k", "levels_interior", "levels_c",
+                                        "nnz_factor", "lanczos_steps")}}))
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -39,10 +39,14 @@ def _built():
     O.build()
 
 
+@pytest.mark.parametrize("tma", [1, 0], ids=["tma", "plain"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
-def test_a0_solve_and_factor_parity(name):
+def test_a0_solve_and_factor_parity(name, tma, monkeypatch):
+    """Both interior-solve kernels (TMA-pipelined and plain) against the oracle."""
     A, part, p, factor, c_order = PROBLEMS[name]()
     k = 4
+    if not tma:
+        monkeypatch.setenv("DDLR_NO_TMA", "1")
     h = pkg.DDLR(A, part, p, rank_k=k, factor=factor, c_order=c_order)
     orc = O.Oracle(A, part, p, k=k, factor=factor, c_order=c_order)
     n = A[0]
