@@ -191,6 +191,15 @@ def run_ours(args):
     relres = max(i["relres"] for i in infos)
     its = [i["its"] for i in infos]
     assert all(i["status"] == "OK" for i in infos), infos
+    if args.timed_only:
+        # the pass used for the ncu launch list: warm-up and timed steps only
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 4), "unit": UNIT,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "gpu_launches": int(launches), "iterations": its,
+                              "note": "timed-only pass (launch-list capture)"}))
+        h.close()
+        return
 
     # split of one step: setup vs solve (CUDA events on the same stream)
     def split_once(hh):
@@ -379,6 +388,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="run only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

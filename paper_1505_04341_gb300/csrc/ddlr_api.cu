@@ -90,8 +90,8 @@ struct ddlr_ctx {
   double *dinvs64 = nullptr;  // inverse diagonal in slice layout (TMA solve)
   float *dinvs32 = nullptr;
   int *row_slot = nullptr;
-  TmaCfg tma{};
-  bool use_tma = false;
+  TmaCfg tma64{}, tma32{};
+  bool use_tma64 = false, use_tma32 = false;
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -203,8 +203,32 @@ struct ddlr_ctx {
 
 namespace {
 
-constexpr int kTmaStages = 3;          // depth of the TMA ring of the interior solve
-constexpr size_t kTmaSmemMax = 100 << 10;
+// geometry of the TMA-pipelined interior solve for element type T: the ring
+// takes what the shared memory of one SM leaves for each co-resident CTA
+// (enough CTAs per SM to hold every interior block in one wave, up to 4),
+// capped at one block's total staged bytes; false if a stage does not fit
+template <typename T>
+bool tma_config(const Plan &P, TmaCfg &cfg) {
+  int dev = 0, sms = 0, per_sm = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (P.tma_zs <= 0 || sms <= 0) return false;
+  const int cps = std::max(1, std::min(4, (P.p + sms - 1) / sms));
+  const long long budget = std::min<long long>(optin, per_sm / cps - 1024);
+  cfg = TmaCfg{P.tma_zs, P.tma_nl, P.tma_ns, 0};
+  const long long fixed = (long long)tma_smem_bytes<T>(cfg);
+  const long long stage_max = (long long)P.tma_e * (long long)(sizeof(T) + 4) +
+                              (long long)P.tma_s * 32 * (long long)sizeof(T);
+  const long long block_total = P.tma_blk_e * (long long)(sizeof(T) + 4) +
+                                P.tma_blk_s * 32 * (long long)sizeof(T);
+  long long ring = std::min(budget - fixed, block_total + stage_max);
+  ring &= ~127LL;
+  if (ring < stage_max || ring <= 0) return false;
+  cfg.ring_bytes = int(ring);
+  return true;
+}
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
@@ -244,10 +268,11 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
   ck(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0), "wait");
   if (P.p > 0) {
-    if (c->use_tma) {
-      const size_t sm = tma_smem_bytes<T, kTmaStages>(c->tma);
-      KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_tma<T, 256, kTmaStages>), P.p, 256, sm,
-         c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, c->tma, c->dflag + 3);
+    const bool use = sizeof(T) == 8 ? c->use_tma64 : c->use_tma32;
+    const TmaCfg &cfg = sizeof(T) == 8 ? c->tma64 : c->tma32;
+    if (use) {
+      KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_tma<T, 256>), P.p, 256, tma_smem_bytes<T>(cfg),
+         c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, cfg, c->dflag + 3);
     } else {
       KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks<T, 256>), P.p, 256, 0,
          c->S, lv, uv, di, x, z, gate);
@@ -438,9 +463,11 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       scale = std::max(scale, std::fabs(ab[0]));
       mm = j + 1;
       if (check > 0 && mm % check == 0 && mm >= k + 1) {
-        const size_t smk = 2 * mm * sizeof(double) + 1024 * sizeof(int);
-        KL(c, "eig_check", c->stream, k_tridiag_values, 1, 1024, smk, mm, al, be, k, etop, esum);
-        KL(c, "eig_check", c->stream, k_tridiag_values, 1, 1024, smk, mm - 1, al, be, k, etop, esum + 1);
+        const size_t smk = 2 * mm * sizeof(double);
+        KL(c, "eig_check", c->stream, k_tridiag_values, (k + 3) / 4, 128, smk, mm, al, be, k, etop);
+        KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum);
+        KL(c, "eig_check", c->stream, k_tridiag_values, (k + 3) / 4, 128, smk, mm - 1, al, be, k, etop);
+        KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum + 1);
         read_dev(c, c->h_pin, esum, 2 * sizeof(double));
         if (std::fabs(c->h_pin[0] - c->h_pin[1]) < eps * std::fabs(c->h_pin[1])) break;
       }
@@ -463,9 +490,9 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     if (st == DDLR_OK) {
       c->msteps = mm;
-      const int nvals = std::min(mm, 1024);
-      KL(c, "eig", c->stream, k_tridiag_values, 1, 1024, 2 * mm * sizeof(double) + 1024 * sizeof(int),
-         mm, al, be, nvals, evals, (double *)nullptr);
+      const int nvals = mm;
+      KL(c, "eig", c->stream, k_tridiag_values, (nvals + 3) / 4, 128, 2 * mm * sizeof(double),
+         mm, al, be, nvals, evals);
       KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, al, be, k, evals, eY, ework);
       c->ritz.assign(nvals, 0.0);
       read_dev(c, c->ritz.data(), evals, sizeof(double) * nvals);
@@ -637,20 +664,18 @@ void allocate(ddlr_ctx *c) {
   c->dinvs64 = c->alloc<double>(size_t(P.nslice) * kSlice);
   ck(cudaMemsetAsync(c->dinvs64, 0, sizeof(double) * size_t(P.nslice) * kSlice, c->stream), "memset");
   c->row_slot = c->upload(P.row_slot);
-  c->tma = TmaCfg{P.tma_zs, P.tma_nl, P.tma_ns, P.tma_e, P.tma_s};
   {
     const char *env = getenv("DDLR_NO_TMA");
     const bool off = env && env[0] == '1';
-    const size_t need = c->opt.precision == 1 ? tma_smem_bytes<float, kTmaStages>(c->tma)
-                                               : tma_smem_bytes<double, kTmaStages>(c->tma);
-    c->use_tma = !off && P.tma_zs > 0 && need <= kTmaSmemMax;
+    c->use_tma64 = !off && tma_config<double>(P, c->tma64);
+    c->use_tma32 = !off && tma_config<float>(P, c->tma32);
     ck(cudaFuncSetAttribute(k_tridiag_values, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10), "attr");
-    if (c->use_tma) {
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256, kTmaStages>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax)), "attr");
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<float, 256, kTmaStages>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax)), "attr");
-    }
+    if (c->use_tma64)
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(tma_smem_bytes<double>(c->tma64))), "attr");
+    if (c->use_tma32)
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(tma_smem_bytes<float>(c->tma32))), "attr");
   }
   c->eh64 = c->alloc<double>(P.eh_ci.size());
   c->eht64 = c->alloc<double>(P.eht_ci.size());

@@ -173,15 +173,14 @@ k_sptrsv_blocks(SolveLayout S, const T *lval, const T *uval, const T *dinv,
 }
 
 // ----------------------------------------- TMA-pipelined interior solves
-// Shared-memory capacities (elements) of k_sptrsv_blocks_tma, computed on the
-// host over all interior blocks.
+// Shared-memory geometry of k_sptrsv_blocks_tma, chosen on the host.
 struct TmaCfg {
-  int zs_cap;   // rows of the largest block
-  int nl_cap;   // levels of the deepest block
-  int ns_cap;   // slices of the largest block + 1
-  int e_cap;    // sliced-ELL entries of the largest level (L or L^T)
-  int s_cap;    // slices of the widest level
+  int zs_cap;      // rows of the largest interior block
+  int nl_cap;      // levels of the deepest block
+  int ns_cap;      // slices of the largest block + 1
+  int ring_bytes;  // staging ring (multiple of 128, >= the largest stage)
 };
+constexpr int kNBar = 64;       // mbarriers = stages in flight at most
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -213,40 +212,35 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ size_t al128(size_t b) { return (b + 127) & ~size_t(127); }
+__host__ __device__ inline size_t al128(size_t b) { return (b + 127) & ~size_t(127); }
 
 template <typename T>
-__host__ __device__ inline size_t tma_slot_bytes(const TmaCfg &c) {
-  return ((size_t(c.e_cap) * sizeof(T) + 127) & ~size_t(127)) +
-         ((size_t(c.e_cap) * 4 + 127) & ~size_t(127)) +
-         ((size_t(c.s_cap) * 32 * sizeof(T) + 127) & ~size_t(127));
-}
-template <typename T, int D>
 __host__ __device__ inline size_t tma_smem_bytes(const TmaCfg &c) {
-  return 128 + D * tma_slot_bytes<T>(c) + ((size_t(c.zs_cap) * sizeof(T) + 127) & ~size_t(127)) +
-         ((size_t(3 * c.nl_cap) * 4 + 127) & ~size_t(127)) + size_t(4 * c.ns_cap) * 4;
+  return 8 * kNBar + size_t(c.ring_bytes) + al128(size_t(c.zs_cap) * sizeof(T)) +
+         al128(size_t(3 * c.nl_cap) * 4) + size_t(4 * c.ns_cap) * 4;
 }
 
 // All interior blocks of A0 in one launch, one CTA per block (Sec. 4.2: the p
 // local solves are independent).  The block's solution lives in shared
-// memory; the sliced-ELL data of each level (values, column indices and the
-// inverse diagonal in slice layout, all 128-byte aligned) is brought in by
-// 1-D TMA bulk copies into a ring of D stages issued D levels ahead, so the
-// level chain only waits on shared memory.  Forward sweep with L, backward
-// sweep with L^T, one CTA barrier per level.  Waits are bounded: on timeout
-// *err is set and the CTA returns.
-template <typename T, int NT, int D>
+// memory.  The sliced-ELL data of each level (values, column indices and the
+// inverse diagonal in slice layout; every piece a multiple of 128 bytes) is a
+// "stage"; stages are brought in by 1-D TMA bulk copies into a byte ring,
+// placed one after the other (wrapping to the ring start when a stage does
+// not fit before the end), as far ahead as the ring allows.  Placement is a
+// pure function of the stage sizes, so every thread computes where its next
+// stage lies; only thread 0 issues copies, after the barrier that ends a
+// level.  Forward sweep with L, backward sweep with L^T.  Waits are bounded:
+// on timeout *err is set and the CTA returns.
+template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s,
                     const T *x, T *z, const int *gate, TmaCfg cfg, int *err) {
   if (gate && *gate) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
-  const size_t slot_bytes = tma_slot_bytes<T>(cfg);
-  const size_t o_col = al128(size_t(cfg.e_cap) * sizeof(T));
-  const size_t o_din = o_col + al128(size_t(cfg.e_cap) * 4);
-  unsigned char *ring = smraw + 128;
-  T *zs = reinterpret_cast<T *>(ring + D * slot_bytes);
+  unsigned char *ring = smraw + 8 * kNBar;
+  const long long R = cfg.ring_bytes;
+  T *zs = reinterpret_cast<T *>(ring + R);
   int *lt = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(zs) + al128(size_t(cfg.zs_cap) * sizeof(T)));
   int *st = lt + ((3 * cfg.nl_cap + 31) & ~31);
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -268,59 +262,85 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
   }
   for (int i = tid; i < nb; i += NT) zs[i] = x[rb0 + i];
   if (tid == 0) {
-    for (int q = 0; q < D; q++) mbar_init(bar + q, 1);
+    for (int q = 0; q < kNBar; q++) mbar_init(bar + q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
   const int nstage = 2 * NL;
   // stage j: forward level j (j < NL) or backward level 2NL-1-j
-  auto issue = [&](int j) {
-    const bool fwd = j < NL;
-    const int li = fwd ? j : nstage - 1 - j;
-    const int sa = lt[3 * li + 2];
-    const int sbn = (li + 1 < NL) ? lt[3 * (li + 1) + 2] : NS;
-    const int oa = st[4 * sa + (fwd ? 0 : 2)], ob = st[4 * sbn + (fwd ? 0 : 2)];
-    const int ne = ob - oa, nsl = sbn - sa;
-    unsigned char *slot = ring + size_t(j % D) * slot_bytes;
-    const unsigned bytes = unsigned(ne) * (unsigned)(sizeof(T) + 4) + unsigned(nsl) * 32u * (unsigned)sizeof(T);
-    mbar_expect_tx(bar + (j % D), bytes);
-    if (ne > 0) {
-      tma_load_1d(slot, (fwd ? lval : uval) + oa, unsigned(ne) * (unsigned)sizeof(T), bar + (j % D));
-      tma_load_1d(slot + o_col, (fwd ? S.l_col : S.u_col) + oa, unsigned(ne) * 4u, bar + (j % D));
-    }
-    tma_load_1d(slot + o_din, dinv_s + size_t(sb0 + sa) * 32, unsigned(nsl) * 32u * (unsigned)sizeof(T),
-                bar + (j % D));
+  struct Geo { int li, sa, oa, ne, nsl; bool fwd; long long bytes; };
+  auto geo = [&](int j) {
+    Geo g;
+    g.fwd = j < NL;
+    g.li = g.fwd ? j : nstage - 1 - j;
+    g.sa = lt[3 * g.li + 2];
+    const int sbn = (g.li + 1 < NL) ? lt[3 * (g.li + 1) + 2] : NS;
+    g.oa = st[4 * g.sa + (g.fwd ? 0 : 2)];
+    g.ne = st[4 * sbn + (g.fwd ? 0 : 2)] - g.oa;
+    g.nsl = sbn - g.sa;
+    g.bytes = (long long)g.ne * (long long)(sizeof(T) + 4) + (long long)g.nsl * 32 * (long long)sizeof(T);
+    return g;
   };
-  if (tid == 0)
-    for (int j = 0; j < D && j < nstage; j++) issue(j);
+  // linear (unwrapped) start of a stage of `bytes` placed after position lin
+  auto place = [&](long long lin, long long bytes) {
+    const long long p = lin % R;
+    return (p + bytes > R) ? lin + (R - p) : lin;
+  };
+  // producer (thread 0): next stage to issue and the end of the last placed one
+  int jn = 0;
+  long long lin_end = 0;
+  auto produce = [&](int jc, long long lin_c) {
+    while (jn < nstage && jn - jc < kNBar) {
+      const Geo g = geo(jn);
+      const long long at = place(lin_end, g.bytes);
+      if (at + g.bytes - lin_c > R) break;     // would reach the oldest live stage
+      unsigned char *dst = ring + (at % R);
+      uint64_t *bj = bar + (jn % kNBar);
+      mbar_expect_tx(bj, unsigned(g.bytes));
+      if (g.ne > 0) {
+        tma_load_1d(dst, (g.fwd ? lval : uval) + g.oa, unsigned(g.ne) * (unsigned)sizeof(T), bj);
+        tma_load_1d(dst + size_t(g.ne) * sizeof(T), (g.fwd ? S.l_col : S.u_col) + g.oa,
+                    unsigned(g.ne) * 4u, bj);
+      }
+      tma_load_1d(dst + size_t(g.ne) * (sizeof(T) + 4), dinv_s + size_t(sb0 + g.sa) * 32,
+                  unsigned(g.nsl) * 32u * (unsigned)sizeof(T), bj);
+      lin_end = at + g.bytes;
+      jn++;
+    }
+  };
+  Geo g = geo(0);
+  long long lin_c = 0;          // placed linear start of the stage being consumed
+  if (tid == 0) produce(0, lin_c);
   for (int j = 0; j < nstage; j++) {
-    const unsigned par = unsigned(j / D) & 1u;
-    if (!mbar_try_wait(bar + (j % D), par)) {
+    const unsigned par = unsigned(j / kNBar) & 1u;
+    if (!mbar_try_wait(bar + (j % kNBar), par)) {
       const long long t0 = clock64();
-      while (!mbar_try_wait(bar + (j % D), par)) {
+      while (!mbar_try_wait(bar + (j % kNBar), par)) {
         if (clock64() - t0 > (1LL << 32)) { *err = 1; return; }
       }
     }
-    const bool fwd = j < NL;
-    const int li = fwd ? j : nstage - 1 - j;
-    const int r0 = lt[3 * li], nr = lt[3 * li + 1], sa = lt[3 * li + 2];
-    const int oa = st[4 * sa + (fwd ? 0 : 2)];
-    const unsigned char *slot = ring + size_t(j % D) * slot_bytes;
+    const int r0 = lt[3 * g.li], nr = lt[3 * g.li + 1];
+    const unsigned char *slot = ring + (lin_c % R);
     const T *sv = reinterpret_cast<const T *>(slot);
-    const int *sc = reinterpret_cast<const int *>(slot + o_col);
-    const T *sd = reinterpret_cast<const T *>(slot + o_din);
+    const int *sc = reinterpret_cast<const int *>(slot + size_t(g.ne) * sizeof(T));
+    const T *sd = reinterpret_cast<const T *>(slot + size_t(g.ne) * (sizeof(T) + 4));
     for (int i = tid; i < nr; i += NT) {
-      const int sl = sa + (i >> 5), ln = i & 31;
-      const int o = st[4 * sl + (fwd ? 0 : 2)] - oa + ln, w = st[4 * sl + (fwd ? 1 : 3)];
+      const int sl = g.sa + (i >> 5), ln = i & 31;
+      const int o = st[4 * sl + (g.fwd ? 0 : 2)] - g.oa + ln, w = st[4 * sl + (g.fwd ? 1 : 3)];
       T acc = zs[r0 + i];
       for (int kk = 0; kk < w; kk++) acc -= sv[o + 32 * kk] * zs[sc[o + 32 * kk] - rb0];
       zs[r0 + i] = acc * sd[i];
     }
     __syncthreads();
-    if (tid == 0 && j + D < nstage) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(j + D);
+    if (j + 1 < nstage) {
+      const long long endj = lin_c + g.bytes;
+      g = geo(j + 1);
+      lin_c = place(endj, g.bytes);
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        produce(j + 1, lin_c);
+      }
     }
   }
   for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
@@ -824,57 +844,56 @@ __device__ __forceinline__ int sturm_count(int m, const double *a, const double 
   return cnt;
 }
 
-// The nv largest eigenvalues of T_m, descending, into vals (and their sum
-// into *sum when non-null).  G = blockDim/nv threads share one eigenvalue and
-// evaluate G interior points of its bracket per round (nv <= blockDim).
-// Dynamic shared memory: 2m doubles + blockDim ints.
+// The nv largest eigenvalues of T_m, descending, into vals.  One warp per
+// eigenvalue (CTA = 4 warps, grid covers nv): the 32 lanes evaluate 32
+// interior points of the eigenvalue's bracket per round (multisection, 5 bits
+// per round).  Spreading the eigenvalues over many SMs matters because the
+// FP64 pipe of one SM is narrow.  Dynamic shared memory: 2m doubles.
 __global__ void k_tridiag_values(int m, const double *al, const double *be,
-                                 int nv, double *vals, double *sum) {
+                                 int nv, double *vals) {
   extern __shared__ double shm[];
   double *a = shm, *b2 = shm + m;
-  int *cnts = reinterpret_cast<int *>(shm + 2 * m);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < m; i += blockDim.x) {
     a[i] = al[i];
     b2[i] = (i + 1 < m) ? be[i] * be[i] : 0.0;
   }
   __syncthreads();
+  const int gi = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);   // eigenvalue index
+  if (gi >= nv) return;
   double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < m; i++) {
+  for (int i = lane; i < m; i += 32) {
     const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
     lo = fmin(lo, a[i] - r);
     hi = fmax(hi, a[i] + r);
   }
-  const double span = fmax(hi - lo, 1e-300);
-  lo -= 1e-9 * span;
-  hi += 1e-9 * span;
-  const int G = max(1, (int)blockDim.x / max(nv, 1));
-  const int gi = tid / G, gt = tid % G;
-  const bool active = gi < nv;
-  const int target = m - 1 - gi;     // eigenvalue gi (0 = largest)
-  double blo = lo, bhi = hi;
-  const int rounds = (int)ceil(60.0 / log2((double)G + 1.0));
-  for (int round = 0; round < rounds; round++) {
-    if (active) cnts[tid] = sturm_count(m, a, b2, blo + (bhi - blo) * double(gt + 1) / double(G + 1));
-    __syncthreads();
-    if (active) {
-      double nlo = blo, nhi = bhi;
-      for (int t = 0; t < G; t++) {
-        const double xt = blo + (bhi - blo) * double(t + 1) / double(G + 1);
-        if (cnts[gi * G + t] <= target) nlo = xt;
-        else { nhi = xt; break; }
-      }
-      blo = nlo;
-      bhi = nhi;
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
-  if (active && gt == 0) vals[gi] = 0.5 * (blo + bhi);
-  __syncthreads();
-  if (sum && tid == 0) {
-    double sacc = 0;
-    for (int i = 0; i < nv; i++) sacc += vals[i];
-    *sum = sacc;
+  const double span = fmax(hi - lo, 1e-300);
+  double blo = lo - 1e-9 * span, bhi = hi + 1e-9 * span;
+  const int target = m - 1 - gi;     // eigenvalue gi (0 = largest)
+  for (int round = 0; round < 12; round++) {
+    const double x = blo + (bhi - blo) * double(lane + 1) * (1.0 / 33.0);
+    const int c = sturm_count(m, a, b2, x);
+    // lanes whose point has count <= target lie below the eigenvalue
+    const unsigned below = __ballot_sync(0xffffffffu, c <= target);
+    const int nb = __popc(below);            // counts are monotone in x
+    const double nlo = nb > 0 ? blo + (bhi - blo) * double(nb) * (1.0 / 33.0) : blo;
+    const double nhi = nb < 32 ? blo + (bhi - blo) * double(nb + 1) * (1.0 / 33.0) : bhi;
+    blo = nlo;
+    bhi = nhi;
+  }
+  if (lane == 0) vals[gi] = 0.5 * (blo + bhi);
+}
+
+// *out = sum of the first k entries of v (fixed order)
+__global__ void k_sum_first(int k, const double *v, double *out) {
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int i = 0; i < k; i++) s += v[i];
+    *out = s;
   }
 }
 

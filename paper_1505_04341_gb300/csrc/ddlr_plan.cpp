@@ -382,11 +382,16 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     P.tma_zs = std::max(P.tma_zs, P.blk_row0[b + 1] - P.blk_row0[b]);
     P.tma_nl = std::max(P.tma_nl, l1 - l0);
     P.tma_ns = std::max(P.tma_ns, P.lvl_slice0[l1] - P.lvl_slice0[l0] + 1);
+    long long be = 0, bs = 0;
     for (int l = l0; l < l1; l++) {
       const int s0 = P.lvl_slice0[l], s1 = P.lvl_slice0[l + 1];
       P.tma_e = std::max(P.tma_e, std::max(P.l_soff[s1] - P.l_soff[s0], P.u_soff[s1] - P.u_soff[s0]));
       P.tma_s = std::max(P.tma_s, s1 - s0);
+      be += (P.l_soff[s1] - P.l_soff[s0]) + (P.u_soff[s1] - P.u_soff[s0]);
+      bs += 2 * (s1 - s0);
     }
+    P.tma_blk_e = std::max(P.tma_blk_e, be);
+    P.tma_blk_s = std::max(P.tma_blk_s, bs);
   }
   return DDLR_OK;
 }

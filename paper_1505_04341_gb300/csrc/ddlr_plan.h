@@ -53,6 +53,7 @@ struct Plan {
   std::vector<int> row_slot;              // row -> slice*32 + lane (inverse diagonal in slice layout)
   // shared-memory capacities of the TMA-pipelined interior solve
   int tma_zs = 0, tma_nl = 0, tma_ns = 0, tma_e = 0, tma_s = 0;
+  long long tma_blk_e = 0, tma_blk_s = 0;   // largest per-block totals over all stages
   // statistics
   int levels_interior = 0, levels_c = 0, ncolors = 0;
   long long nnz_ehat = 0, nnz_factor = 0;
