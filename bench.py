@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "lap3d_64_b4"
-OPTS = dict(variant=1, rank_k=16, factor=0, c_order=1, precision=0)
+OPTS = dict(variant=1, rank_k=16, factor=0, c_order=1, b_order=1, precision=0)
 TOL = 1e-8
 METRIC = "DDLR-PCG time to 1e-8 rel. residual (setup + solve)"
 UNIT = "ms/solve"
@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 def _config(extra=None):
     c = {"workload": WORKLOAD, "grid": "64^3 7-point Laplacian, Dirichlet",
          "n": 262144, "subdomains": "4x4x4 boxes (64)", "variant": "DDLR-1",
-         "rank_k": OPTS["rank_k"], "local_solver": "IC(0), natural order",
-         "c_alpha_order": "greedy multicolour", "alpha": 1.0,
+         "rank_k": OPTS["rank_k"], "local_solver": "IC(0)",
+         "interior_order": "greedy multicolour", "c_alpha_order": "greedy multicolour", "alpha": 1.0,
          "theta": "lambda_{k+1}", "lanczos": "<=5k steps, check every 10, eps 1e-4",
          "tol": TOL, "rhs": "SplitMix64 seed 0, U[-1,1)",
          "l2": "flushed (256 MiB write) before every timed step"}
@@ -267,6 +267,12 @@ def run_ours(args):
     x_mixed = x.clone()
     mixed_apply_ms, mixed_apply_gbs = apply_rate(hm)
     hm.close()
+    # natural (ascending index) order inside the interior blocks: deeper
+    # factors, fewer iterations
+    hn = pkg.DDLR(A, part, p, **dict(OPTS, b_order=0))
+    step(hn, x)
+    ms_nat, inf_nat = timed_steps(hn, 1)
+    hn.close()
     # DDLR-2 on the same problem
     h2 = pkg.DDLR(A, part, p, **dict(OPTS, variant=2))
     step(h2, x)
@@ -319,6 +325,8 @@ def run_ours(args):
                                 "speedup_vs_fp64": round(value / statistics.mean(ms_mixed), 3),
                                 "apply_ms": round(mixed_apply_ms, 4),
                                 "apply_algorithmic_GBps": round(mixed_apply_gbs, 1)},
+            "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
+                                            "iterations": [i["its"] for i in inf_nat]},
             "ddlr2_fp64": {"ms_per_solve": round(statistics.mean(ms_v2), 3),
                            "iterations": [i["its"] for i in inf_v2],
                            "apply_ms": round(v2_apply_ms, 4),
@@ -342,7 +350,8 @@ def _oracle_step():
     A, part, p = w["A"], w["part"], w["p"]
     b = W.rhs(A[0], 0)
     t0 = time.perf_counter()
-    orc = oracle.Oracle(A, part, p, variant=1, k=OPTS["rank_k"], factor=0, c_order=1)
+    orc = oracle.Oracle(A, part, p, variant=1, k=OPTS["rank_k"], factor=0,
+                        c_order=OPTS["c_order"], b_order=OPTS["b_order"])
     x, its, rel, st = orc.pcg(b, TOL)
     dt = (time.perf_counter() - t0) * 1e3
     assert st == "OK"

@@ -60,6 +60,8 @@ typedef struct {
                               1 = exact Cholesky (IC on the symbolic fill pattern) */
   int c_order;             /* elimination order of C_a: 0 = ascending original
                               index, 1 = greedy multicolour (2 colours on grids)   */
+  int b_order;             /* elimination order inside the interior blocks B_{i,a}:
+                              0 = ascending original index, 1 = greedy multicolour */
   int precision;           /* 0 = FP64 throughout; 1 = mixed: FP32 factors and
                               triangular solves, FP32/BF16 U_k, inside an FP64
                               flexible CG                                          */
@@ -95,7 +97,8 @@ typedef struct {
 } ddlr_solve_info;
 
 /* Fills *opt with the defaults named above (variant 1, k 16, alpha 1,
- * theta_mode 1, IC(0), c_order 0, FP64, lanczos 5k/10/1e-4, seed 0, max_nrhs 1).
+ * theta_mode 1, IC(0), c_order 0, b_order 0, FP64, lanczos 5k/10/1e-4, seed 0,
+ * max_nrhs 1).
  * Returns DDLR_ERR_INVALID for a NULL pointer. */
 ddlr_status ddlr_options_default(ddlr_options *opt);
 

@@ -54,7 +54,7 @@ def _load():
         P = ctypes.c_void_p
         I = ctypes.c_int
         D = ctypes.c_double
-        lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, D,
+        lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
                                  ctypes.c_ulonglong, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
@@ -92,12 +92,13 @@ class Oracle:
     ``A = (n, rowptr, colind, val)`` full symmetric CSR, ``part[i]`` in [0, p).
     Options follow the library's: variant 1/2, rank k, alpha, theta_mode
     (1: theta = Ritz_{k+1}, 0: theta = 0), factor (0: IC(0), 1: exact),
-    c_order (0: ascending index, 1: greedy multicolour), scale_diag,
+    c_order (0: ascending index, 1: greedy multicolour) of C_a, b_order (the
+    same choice for the interior blocks), scale_diag,
     lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed.
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
-                 factor=0, c_order=0, scale_diag=0, lanczos_max=0,
+                 factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0):
         lib = _load()
         n, rp, ci, va = A
@@ -108,7 +109,7 @@ class Oracle:
         h = ctypes.c_void_p()
         st = lib.or_setup(int(n), *[_ptr(a) for a in self._keep], int(p),
                           int(variant), int(k), float(alpha), int(theta_mode),
-                          int(factor), int(c_order), int(scale_diag),
+                          int(factor), int(c_order), int(b_order), int(scale_diag),
                           int(lanczos_max), int(lanczos_check),
                           float(lanczos_eps), int(seed), ctypes.byref(h))
         if st != 0:

@@ -15,7 +15,8 @@
  *   - Sec. 3.1 (eq. EF, split): E = [a^-1 Ehat ; -a I],
  *     A0 = blkdiag(B + a^-2 Ehat Ehat^T, C + a^2 I), A = A0 - E E^T;
  *   - Sec. 4.1, 5: local solvers = incomplete Cholesky IC(0) on the pattern
- *     (or exact Cholesky, dense), one factor per B_{i,a} and one for C_a;
+ *     (or exact Cholesky, dense), one factor per B_{i,a} and one for C_a, each
+ *     in its elimination order (ascending index, or greedy multicolour);
  *   - Sec. 4.4 (eq. converge): Lanczos on H = E^T A0^-1 E (DDLR-1) or on
  *     E^T A0^-2 E (DDLR-2), with full reorthogonalisation (two classical
  *     Gram-Schmidt passes), convergence checked every `check` steps;
@@ -27,8 +28,9 @@
  *
  * Readings where the paper is silent are the same as the CUDA library's and are
  * listed with the design notes: natural (ascending original index) elimination
- * order inside interior blocks; C_a factored like a local block, in ascending
- * original index (c_order 0) or greedy multicolour order (c_order 1); Lanczos
+ * order inside interior blocks (b_order 0) or greedy multicolour (b_order 1);
+ * C_a factored like a local block, in ascending original index (c_order 0) or
+ * greedy multicolour order (c_order 1); Lanczos
  * start vector from SplitMix64; breakdown restarts; theta = Ritz_{k+1}.
  */
 #include <math.h>
@@ -425,7 +427,7 @@ static int lanczos(oracle *o, int k, int mmax, int check, double eps, uint64_t s
 /* ------------------------------------------------------------ public API */
 int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              const int *part, int p, int variant, int k, double alpha,
-             int theta_mode, int factor, int c_order, int scale_diag,
+             int theta_mode, int factor, int c_order, int b_order, int scale_diag,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, void **out) {
   *out = NULL;
@@ -591,7 +593,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
 
     /* elimination order: ascending index, or greedy multicolour for C_a */
     for (int e = 0; e < nb; e++) f->ord[e] = e;
-    if (b == p && c_order == 1) {
+    if ((b == p && c_order == 1) || (b < p && b_order == 1)) {
       int *col = (int *)malloc(sizeof(int) * (size_t)nb);
       int *used = (int *)calloc((size_t)nb + 2, sizeof(int));
       int nc = 0;
@@ -603,7 +605,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
         col[r] = c;
         if (c + 1 > nc) nc = c + 1;
       }
-      o->ncolors = nc;
+      if (b == p) o->ncolors = nc;
       int e = 0;
       for (int c = 0; c < nc; c++)
         for (int r = 0; r < nb; r++) if (col[r] == c) f->ord[e++] = r;

@@ -92,6 +92,10 @@ struct ddlr_ctx {
   int *row_slot = nullptr;
   TmaCfg tma64{}, tma32{};
   bool use_tma64 = false, use_tma32 = false;
+  bool use_sf64 = false, use_sf32 = false;   // synchronisation-free interior solve
+  int2 *l_span = nullptr, *u_span = nullptr;
+  int *blk_row0 = nullptr;
+  int *chunks = nullptr;
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -203,6 +207,11 @@ struct ddlr_ctx {
 
 namespace {
 
+template <typename T>
+size_t sf_smem_bytes(const Plan &P) {
+  return ((size_t(P.tma_zs) * sizeof(T) + 15) & ~size_t(15)) + size_t(P.tma_zs) * 4;
+}
+
 // geometry of the TMA-pipelined interior solve for element type T: the ring
 // takes what the shared memory of one SM leaves for each co-resident CTA
 // (enough CTAs per SM to hold every interior block in one wave, up to 4),
@@ -261,16 +270,47 @@ template <> struct Prec<float> {
 // ----------------------------------------------------------- A0 solve
 // z = A0^-1 x in device order: all interior blocks in one launch (CTA per
 // block) on the main stream, the C_a levels on the second stream.
+constexpr int kShallowLevels = 8;   // at most this deep: solve level by level over all blocks
+
+// levels [L0, L1) of the chunk lists ptr: forward up to the top, the top
+// level forward and backward in one pass, then backward down
+template <typename T>
+void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, const char *fam,
+                  const T *lv, const T *uv, const T *di, const T *x, T *z, const int *gate) {
+  const int nL = int(ptr.size()) - 1;
+  auto launch = [&](int L, int mode) {
+    const int nch = ptr[L + 1] - ptr[L];
+    if (nch > 0)
+      KL(c, fam, st, k_sptrsv_chunks<T>, nch, kThreads, 0, c->S,
+         reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, x, z, gate);
+  };
+  for (int L = 0; L + 1 < nL; L++) launch(L, 0);
+  if (nL > 0) launch(nL - 1, 2);
+  for (int L = nL - 2; L >= 0; L--) launch(L, 1);
+}
+
+// z = A0^-1 x in device order (Sec. 4.2: the p local solves with B_{i,a} and
+// the solve with C_a).  Shallow factors (multicolour orders): every level of
+// all blocks in one launch.  Deep factors: all interior blocks in one launch
+// (CTA per block) on the main stream, the C_a levels on a forked stream.
 template <typename T>
 void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   const Plan &P = c->P;
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  if (std::max(P.levels_interior, P.levels_c) <= kShallowLevels) {
+    chunk_sweeps<T>(c, c->stream, P.ch_all_ptr, "sptrsv_levels", lv, uv, di, x, z, gate);
+    return;
+  }
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
   ck(cudaStreamWaitEvent(c->stream2, c->ev_fork, 0), "wait");
   if (P.p > 0) {
     const bool use = sizeof(T) == 8 ? c->use_tma64 : c->use_tma32;
     const TmaCfg &cfg = sizeof(T) == 8 ? c->tma64 : c->tma32;
-    if (use) {
+    if (sizeof(T) == 8 ? c->use_sf64 : c->use_sf32) {
+      KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_sf<T, 256, 4>), P.p, 256, sf_smem_bytes<T>(P),
+         c->blk_row0, RowSpan{c->l_span, c->u_span}, c->S.l_col, lv, c->S.u_col, uv, di, x, z, gate,
+         c->dflag + 3);
+    } else if (use) {
       KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_tma<T, 256>), P.p, 256, tma_smem_bytes<T>(cfg),
          c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, cfg, c->dflag + 3);
     } else {
@@ -278,15 +318,7 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
          c->S, lv, uv, di, x, z, gate);
     }
   }
-  const int l0 = P.blk_lvl0[P.p], l1 = P.blk_lvl0[P.p + 1];
-  for (int l = l0; l < l1; l++) {
-    const int mode = (l == l1 - 1) ? 2 : 0;
-    KL(c, "sptrsv_c", c->stream2, k_sptrsv_level<T>, nblk(P.lvl_nrows[l]), kThreads, 0,
-       c->S, l, mode, lv, uv, di, x, z, gate);
-  }
-  for (int l = l1 - 2; l >= l0; l--)
-    KL(c, "sptrsv_c", c->stream2, k_sptrsv_level<T>, nblk(P.lvl_nrows[l]), kThreads, 0,
-       c->S, l, 1, lv, uv, di, x, z, gate);
+  chunk_sweeps<T>(c, c->stream2, P.ch_c_ptr, "sptrsv_c", lv, uv, di, x, z, gate);
   ck(cudaEventRecord(c->ev_join, c->stream2), "event");
   ck(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "wait");
 }
@@ -464,9 +496,9 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       mm = j + 1;
       if (check > 0 && mm % check == 0 && mm >= k + 1) {
         const size_t smk = 2 * mm * sizeof(double);
-        KL(c, "eig_check", c->stream, k_tridiag_values, (k + 3) / 4, 128, smk, mm, al, be, k, etop);
+        KL(c, "eig_check", c->stream, k_tridiag_values, k, 32, smk, mm, al, be, k, etop);
         KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum);
-        KL(c, "eig_check", c->stream, k_tridiag_values, (k + 3) / 4, 128, smk, mm - 1, al, be, k, etop);
+        KL(c, "eig_check", c->stream, k_tridiag_values, k, 32, smk, mm - 1, al, be, k, etop);
         KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum + 1);
         read_dev(c, c->h_pin, esum, 2 * sizeof(double));
         if (std::fabs(c->h_pin[0] - c->h_pin[1]) < eps * std::fabs(c->h_pin[1])) break;
@@ -491,7 +523,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     if (st == DDLR_OK) {
       c->msteps = mm;
       const int nvals = mm;
-      KL(c, "eig", c->stream, k_tridiag_values, (nvals + 3) / 4, 128, 2 * mm * sizeof(double),
+      KL(c, "eig", c->stream, k_tridiag_values, nvals, 32, 2 * mm * sizeof(double),
          mm, al, be, nvals, evals);
       KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, al, be, k, evals, eY, ework);
       c->ritz.assign(nvals, 0.0);
@@ -664,11 +696,31 @@ void allocate(ddlr_ctx *c) {
   c->dinvs64 = c->alloc<double>(size_t(P.nslice) * kSlice);
   ck(cudaMemsetAsync(c->dinvs64, 0, sizeof(double) * size_t(P.nslice) * kSlice, c->stream), "memset");
   c->row_slot = c->upload(P.row_slot);
+  c->l_span = reinterpret_cast<int2 *>(c->upload(P.l_span));
+  c->u_span = reinterpret_cast<int2 *>(c->upload(P.u_span));
+  c->blk_row0 = c->upload(P.blk_row0);
+  c->chunks = c->upload(P.chunks);
   {
-    const char *env = getenv("DDLR_NO_TMA");
-    const bool off = env && env[0] == '1';
-    c->use_tma64 = !off && tma_config<double>(P, c->tma64);
-    c->use_tma32 = !off && tma_config<float>(P, c->tma32);
+    // interior-solve kernel for deep factors: TMA-pipelined level schedule
+    // (default), synchronisation-free, or plain level schedule
+    // (DDLR_SOLVE=tma|sf|plain)
+    const char *env = getenv("DDLR_SOLVE");
+    const std::string kind = env ? env : "tma";
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool sf_ok = P.tma_zs > 0 && kind == "sf";
+    c->use_sf64 = sf_ok && sf_smem_bytes<double>(P) <= size_t(optin);
+    c->use_sf32 = sf_ok && sf_smem_bytes<float>(P) <= size_t(optin);
+    const bool off = kind == "plain";
+    c->use_tma64 = !off && !c->use_sf64 && tma_config<double>(P, c->tma64);
+    c->use_tma32 = !off && !c->use_sf32 && tma_config<float>(P, c->tma32);
+    if (c->use_sf64)
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_sf<double, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(sf_smem_bytes<double>(P))), "attr");
+    if (c->use_sf32)
+      ck(cudaFuncSetAttribute(k_sptrsv_blocks_sf<float, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(sf_smem_bytes<float>(P))), "attr");
     ck(cudaFuncSetAttribute(k_tridiag_values, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10), "attr");
     if (c->use_tma64)
       ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -813,6 +865,7 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->theta_mode = 1;
   o->factor = 0;
   o->c_order = 0;
+  o->b_order = 0;
   o->precision = 0;
   o->uk_bf16 = 0;
   o->scale_diag = 0;
@@ -833,7 +886,8 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
   ddlr_options o;
   if (opt) o = *opt; else ddlr_options_default(&o);
   if ((o.variant != 1 && o.variant != 2) || !(o.alpha > 0) || (o.precision != 0 && o.precision != 1) ||
-      (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) || o.rank_k < 1 ||
+      (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) ||
+      (o.b_order != 0 && o.b_order != 1) || o.rank_k < 1 ||
       o.rank_k > 256) {
     g_setup_error = "invalid options";
     return DDLR_ERR_INVALID;
@@ -1128,6 +1182,7 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       const std::string &f = c->fam_names[i];
       double b = 0.0;
       if (f == "sptrsv_blocks") b = blocks;
+      else if (f == "sptrsv_levels") b = a0 / std::max(1, 2 * std::max(P.levels_interior, P.levels_c) - 1);
       else if (f == "sptrsv_c") b = cblk / clev;
       else if (f == "et") b = et;
       else if (f == "utx") b = utx;

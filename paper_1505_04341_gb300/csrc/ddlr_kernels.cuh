@@ -6,6 +6,7 @@
 // grid and a fixed summation order (no floating-point atomics), so results do
 // not depend on scheduling.
 #pragma once
+#include <cuda/atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -216,8 +217,9 @@ __host__ __device__ inline size_t al128(size_t b) { return (b + 127) & ~size_t(1
 
 template <typename T>
 __host__ __device__ inline size_t tma_smem_bytes(const TmaCfg &c) {
+  // barriers | ring | block solution | stage table (2 int4 + 1 int64 per stage) | slice table
   return 8 * kNBar + size_t(c.ring_bytes) + al128(size_t(c.zs_cap) * sizeof(T)) +
-         al128(size_t(3 * c.nl_cap) * 4) + size_t(4 * c.ns_cap) * 4;
+         al128(size_t(2 * c.nl_cap) * 40) + size_t(4 * c.ns_cap) * 4;
 }
 
 // All interior blocks of A0 in one launch, one CTA per block (Sec. 4.2: the p
@@ -226,11 +228,12 @@ __host__ __device__ inline size_t tma_smem_bytes(const TmaCfg &c) {
 // inverse diagonal in slice layout; every piece a multiple of 128 bytes) is a
 // "stage"; stages are brought in by 1-D TMA bulk copies into a byte ring,
 // placed one after the other (wrapping to the ring start when a stage does
-// not fit before the end), as far ahead as the ring allows.  Placement is a
-// pure function of the stage sizes, so every thread computes where its next
-// stage lies; only thread 0 issues copies, after the barrier that ends a
-// level.  Forward sweep with L, backward sweep with L^T.  Waits are bounded:
-// on timeout *err is set and the CTA returns.
+// not fit before the end), as far ahead as the ring and the 64 mbarriers
+// allow.  Placement is a pure function of the stage sizes and is tabulated in
+// the prologue.  The last thread of the CTA issues the copies after the
+// barrier that ends a level (it has no row in levels narrower than NT-32, so
+// this stays off the level chain).  Forward sweep with L, backward sweep with
+// L^T.  Waits are bounded: on timeout *err is set and the CTA returns.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s,
@@ -239,20 +242,30 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
   unsigned char *ring = smraw + 8 * kNBar;
-  const long long R = cfg.ring_bytes;
+  const int R = cfg.ring_bytes;
   T *zs = reinterpret_cast<T *>(ring + R);
-  int *lt = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(zs) + al128(size_t(cfg.zs_cap) * sizeof(T)));
-  int *st = lt + ((3 * cfg.nl_cap + 31) & ~31);
+  unsigned char *tab = reinterpret_cast<unsigned char *>(zs) + al128(size_t(cfg.zs_cap) * sizeof(T));
+  int4 *sg0 = reinterpret_cast<int4 *>(tab);                  // {r0, nr, sa, oa}
+  int4 *sg1 = sg0 + 2 * cfg.nl_cap;                           // {ne, nsl, pos, bytes}
+  long long *slin = reinterpret_cast<long long *>(sg1 + 2 * cfg.nl_cap);  // linear start
+  int *st = reinterpret_cast<int *>(tab + al128(size_t(2 * cfg.nl_cap) * 40));
   const int b = blockIdx.x, tid = threadIdx.x;
   const int l0 = S.blk_lvl0[b], l1 = S.blk_lvl0[b + 1], NL = l1 - l0;
   if (NL == 0) return;
   const int rb0 = S.lvl_row0[l0], sb0 = S.lvl_slice0[l0];
   const int NS = S.lvl_slice0[l1] - sb0;
   const int nb = S.lvl_row0[l1 - 1] + S.lvl_nrows[l1 - 1] - rb0;
-  for (int i = tid; i < NL; i += NT) {
-    lt[3 * i] = S.lvl_row0[l0 + i] - rb0;
-    lt[3 * i + 1] = S.lvl_nrows[l0 + i];
-    lt[3 * i + 2] = S.lvl_slice0[l0 + i] - sb0;
+  const int nstage = 2 * NL;
+  constexpr int PROD = NT - 1;
+  // stage j: forward level j (j < NL) or backward level 2NL-1-j
+  for (int j = tid; j < nstage; j += NT) {
+    const bool fwd = j < NL;
+    const int li = fwd ? j : nstage - 1 - j;
+    const int sa = S.lvl_slice0[l0 + li] - sb0, sbn = S.lvl_slice0[l0 + li + 1] - sb0;
+    const int *soff = fwd ? S.l_soff : S.u_soff;
+    const int oa = soff[sb0 + sa], ne = soff[sb0 + sbn] - oa;
+    sg0[j] = make_int4(S.lvl_row0[l0 + li] - rb0, S.lvl_nrows[l0 + li], sa, oa);
+    sg1[j] = make_int4(ne, sbn - sa, 0, ne * int(sizeof(T) + 4) + (sbn - sa) * 32 * int(sizeof(T)));
   }
   for (int i = tid; i <= NS; i += NT) {
     st[4 * i] = S.l_soff[sb0 + i];
@@ -261,57 +274,44 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
     st[4 * i + 3] = i < NS ? S.u_sw[sb0 + i] : 0;
   }
   for (int i = tid; i < nb; i += NT) zs[i] = x[rb0 + i];
-  if (tid == 0) {
+  __syncthreads();
+  if (tid == PROD) {
+    // ring placement: consecutive, wrapping to 0 when a stage does not fit
+    long long lin = 0;
+    int pos = 0;
+    for (int j = 0; j < nstage; j++) {
+      const int by = sg1[j].w;
+      if (pos + by > R) { lin += R - pos; pos = 0; }
+      sg1[j].z = pos;
+      slin[j] = lin;
+      lin += by;
+      pos += by;
+    }
     for (int q = 0; q < kNBar; q++) mbar_init(bar + q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  __syncthreads();
-  const int nstage = 2 * NL;
-  // stage j: forward level j (j < NL) or backward level 2NL-1-j
-  struct Geo { int li, sa, oa, ne, nsl; bool fwd; long long bytes; };
-  auto geo = [&](int j) {
-    Geo g;
-    g.fwd = j < NL;
-    g.li = g.fwd ? j : nstage - 1 - j;
-    g.sa = lt[3 * g.li + 2];
-    const int sbn = (g.li + 1 < NL) ? lt[3 * (g.li + 1) + 2] : NS;
-    g.oa = st[4 * g.sa + (g.fwd ? 0 : 2)];
-    g.ne = st[4 * sbn + (g.fwd ? 0 : 2)] - g.oa;
-    g.nsl = sbn - g.sa;
-    g.bytes = (long long)g.ne * (long long)(sizeof(T) + 4) + (long long)g.nsl * 32 * (long long)sizeof(T);
-    return g;
-  };
-  // linear (unwrapped) start of a stage of `bytes` placed after position lin
-  auto place = [&](long long lin, long long bytes) {
-    const long long p = lin % R;
-    return (p + bytes > R) ? lin + (R - p) : lin;
-  };
-  // producer (thread 0): next stage to issue and the end of the last placed one
-  int jn = 0;
-  long long lin_end = 0;
-  auto produce = [&](int jc, long long lin_c) {
+  int jn = 0;   // producer: next stage to issue
+  auto produce = [&](int jc) {
+    const long long lim = slin[jc] + R;
     while (jn < nstage && jn - jc < kNBar) {
-      const Geo g = geo(jn);
-      const long long at = place(lin_end, g.bytes);
-      if (at + g.bytes - lin_c > R) break;     // would reach the oldest live stage
-      unsigned char *dst = ring + (at % R);
+      const int4 g0 = sg0[jn], g1 = sg1[jn];
+      if (slin[jn] + g1.w > lim) break;          // would reach the oldest live stage
+      const bool fwd = jn < NL;
+      unsigned char *dst = ring + g1.z;
       uint64_t *bj = bar + (jn % kNBar);
-      mbar_expect_tx(bj, unsigned(g.bytes));
-      if (g.ne > 0) {
-        tma_load_1d(dst, (g.fwd ? lval : uval) + g.oa, unsigned(g.ne) * (unsigned)sizeof(T), bj);
-        tma_load_1d(dst + size_t(g.ne) * sizeof(T), (g.fwd ? S.l_col : S.u_col) + g.oa,
-                    unsigned(g.ne) * 4u, bj);
+      mbar_expect_tx(bj, unsigned(g1.w));
+      if (g1.x > 0) {
+        tma_load_1d(dst, (fwd ? lval : uval) + g0.w, unsigned(g1.x) * (unsigned)sizeof(T), bj);
+        tma_load_1d(dst + size_t(g1.x) * sizeof(T), (fwd ? S.l_col : S.u_col) + g0.w, unsigned(g1.x) * 4u, bj);
       }
-      tma_load_1d(dst + size_t(g.ne) * (sizeof(T) + 4), dinv_s + size_t(sb0 + g.sa) * 32,
-                  unsigned(g.nsl) * 32u * (unsigned)sizeof(T), bj);
-      lin_end = at + g.bytes;
+      tma_load_1d(dst + size_t(g1.x) * (sizeof(T) + 4), dinv_s + size_t(sb0 + g0.z) * 32,
+                  unsigned(g1.y) * 32u * (unsigned)sizeof(T), bj);
       jn++;
     }
   };
-  Geo g = geo(0);
-  long long lin_c = 0;          // placed linear start of the stage being consumed
-  if (tid == 0) produce(0, lin_c);
+  if (tid == PROD) produce(0);
+  __syncthreads();
   for (int j = 0; j < nstage; j++) {
     const unsigned par = unsigned(j / kNBar) & 1u;
     if (!mbar_try_wait(bar + (j % kNBar), par)) {
@@ -320,30 +320,142 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
         if (clock64() - t0 > (1LL << 32)) { *err = 1; return; }
       }
     }
-    const int r0 = lt[3 * g.li], nr = lt[3 * g.li + 1];
-    const unsigned char *slot = ring + (lin_c % R);
+    const int4 g0 = sg0[j], g1 = sg1[j];
+    const bool fwd = j < NL;
+    const unsigned char *slot = ring + g1.z;
     const T *sv = reinterpret_cast<const T *>(slot);
-    const int *sc = reinterpret_cast<const int *>(slot + size_t(g.ne) * sizeof(T));
-    const T *sd = reinterpret_cast<const T *>(slot + size_t(g.ne) * (sizeof(T) + 4));
+    const int *sc = reinterpret_cast<const int *>(slot + size_t(g1.x) * sizeof(T));
+    const T *sd = reinterpret_cast<const T *>(slot + size_t(g1.x) * (sizeof(T) + 4));
+    const int r0 = g0.x, nr = g0.y, sa = g0.z, oa = g0.w;
     for (int i = tid; i < nr; i += NT) {
-      const int sl = g.sa + (i >> 5), ln = i & 31;
-      const int o = st[4 * sl + (g.fwd ? 0 : 2)] - g.oa + ln, w = st[4 * sl + (g.fwd ? 1 : 3)];
+      const int sl = sa + (i >> 5), ln = i & 31;
+      const int2 so = *reinterpret_cast<const int2 *>(st + 4 * sl + (fwd ? 0 : 2));
+      const int o = so.x - oa + ln, w = so.y;
       T acc = zs[r0 + i];
       for (int kk = 0; kk < w; kk++) acc -= sv[o + 32 * kk] * zs[sc[o + 32 * kk] - rb0];
       zs[r0 + i] = acc * sd[i];
     }
     __syncthreads();
-    if (j + 1 < nstage) {
-      const long long endj = lin_c + g.bytes;
-      g = geo(j + 1);
-      lin_c = place(endj, g.bytes);
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        produce(j + 1, lin_c);
-      }
+    if (tid == PROD && jn < nstage) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      produce(j + 1);
     }
   }
   for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
+}
+
+// --------------------------------------- synchronisation-free interior solve
+// Row r of the factor (device order) keeps {first slot, number of entries} of
+// its strictly-lower L row and of its strictly-upper L^T row in the sliced-ELL
+// arrays (entries kk at first + 32 kk).
+struct RowSpan { const int2 *l, *u; };
+
+template <typename T>
+__device__ __forceinline__ void sf_wait(int *flag, int target, int *err, bool &late) {
+  cuda::atomic_ref<int, cuda::thread_scope_block> f(*flag);
+  if (f.load(cuda::memory_order_acquire) >= target) return;
+  const long long t0 = clock64();
+  while (f.load(cuda::memory_order_acquire) < target) {
+    __nanosleep(32);
+    if (!late && clock64() - t0 > (1LL << 31)) { late = true; *err = 1; }
+    if (late) return;                 // give up waiting; the result is flagged invalid
+  }
+}
+
+// All interior blocks of A0 in one launch, one CTA per block (Sec. 4.2), with
+// no barrier per level: thread t solves rows t, t+NT, ... of its block in
+// topological order (ascending for L, descending for L^T), waiting only on the
+// rows each row depends on through a ready flag per row in shared memory
+// (release/acquire at block scope).  The block's solution lives in shared
+// memory; every thread loads the factor data of its next row before it waits
+// on the current one.  Dependencies point to rows earlier in the thread's
+// order or to rows of other threads at earlier positions, so every wait
+// ends; waits are bounded all the same (on timeout *err is set).
+template <typename T, int NT, int WR>
+__global__ void __launch_bounds__(NT)
+k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l_val,
+                   const int *u_col, const T *u_val, const T *dinv, const T *x, T *z,
+                   const int *gate, int *err) {
+  if (gate && *gate) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int rb0 = blk_row0[b], nb = blk_row0[b + 1] - rb0;
+  T *zs = reinterpret_cast<T *>(smraw);
+  int *flag = reinterpret_cast<int *>(smraw + ((size_t(nb) * sizeof(T) + 15) & ~size_t(15)));
+  for (int i = tid; i < nb; i += NT) { zs[i] = x[rb0 + i]; flag[i] = 0; }
+  __syncthreads();
+  bool late = false;
+  for (int sweep = 0; sweep < 2; sweep++) {
+    const bool fwd = sweep == 0;
+    const int2 *span = fwd ? rs.l : rs.u;
+    const int *col = fwd ? l_col : u_col;
+    const T *val = fwd ? l_val : u_val;
+    const int target = fwd ? 1 : 2;
+    // this thread's rows in dependency order
+    const int count = tid < nb ? (nb - 1 - tid) / NT + 1 : 0;
+    const int first = fwd ? tid : tid + (count - 1) * NT;
+    const int step = fwd ? NT : -NT;
+    // prefetched data of the next row
+    int2 nsp = make_int2(0, 0);
+    T nv[WR]; int nc[WR]; T nd = T(0);
+    auto fetch = [&](int i) {
+      const int r = rb0 + i;
+      nsp = span[r];
+      nd = dinv[r];
+#pragma unroll
+      for (int kk = 0; kk < WR; kk++)
+        if (kk < nsp.y) { nv[kk] = val[nsp.x + 32 * kk]; nc[kk] = col[nsp.x + 32 * kk] - rb0; }
+    };
+    if (count > 0) fetch(first);
+    for (int t = 0, i = first; t < count; t++, i += step) {
+      const int2 sp = nsp;
+      T cv[WR]; int cc[WR];
+#pragma unroll
+      for (int kk = 0; kk < WR; kk++) { cv[kk] = nv[kk]; cc[kk] = nc[kk]; }
+      const T dd = nd;
+      if (t + 1 < count) fetch(i + step);
+      T acc = zs[i];
+#pragma unroll
+      for (int kk = 0; kk < WR; kk++) {
+        if (kk < sp.y) {
+          sf_wait<T>(flag + cc[kk], target, err, late);
+          acc -= cv[kk] * zs[cc[kk]];
+        }
+      }
+      for (int kk = WR; kk < sp.y; kk++) {          // rows wider than WR
+        const int c = col[sp.x + 32 * kk] - rb0;
+        sf_wait<T>(flag + c, target, err, late);
+        acc -= val[sp.x + 32 * kk] * zs[c];
+      }
+      zs[i] = acc * dd;
+      cuda::atomic_ref<int, cuda::thread_scope_block> fi(flag[i]);
+      fi.store(target, cuda::memory_order_release);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
+}
+
+// One dependency level of many blocks in one launch: CTA q solves chunk q
+// = (level record, first row, rows) of that level; mode 0 forward, 1
+// backward, 2 forward then backward (a level that is the top level of every
+// block it contains).
+template <typename T>
+__global__ void k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode,
+                                const T *lval, const T *uval, const T *dinv,
+                                const T *x, T *z, const int *gate) {
+  if (gate && *gate) return;
+  const int4 ch = chunks[blockIdx.x];
+  const int lvl = ch.x, r0 = S.lvl_row0[lvl], s0 = S.lvl_slice0[lvl];
+  for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += blockDim.x) {
+    const int r = r0 + i, sl = s0 + (i >> 5), ln = i & 31;
+    if (mode == 1) {
+      solve_row<T, false>(S, uval, dinv, x, z, sl, ln, r);
+    } else {
+      solve_row<T, true>(S, lval, dinv, x, z, sl, ln, r);
+      if (mode == 2) z[r] = z[r] * dinv[r];
+    }
+  }
 }
 
 // One level of one block (used for C_a, whose levels span the whole GPU):

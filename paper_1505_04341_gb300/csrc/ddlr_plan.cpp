@@ -8,8 +8,8 @@
 //    B_{b,a} = B_b + a^-2 E_b E_b^T, block p is C_a = C + a^2 I.
 //  * Local solvers (Sec. 5): incomplete Cholesky with zero fill on the block
 //    pattern, or exact Cholesky on the symbolic fill pattern.  The elimination
-//    order is ascending original index for interior blocks; for C_a ascending
-//    index (c_order 0) or greedy multicolour (c_order 1).
+//    order is ascending original index (b_order 0) or greedy multicolour
+//    (b_order 1) for interior blocks, and likewise (c_order) for C_a.
 //  * Device order: inside every block the rows are sorted by (dependency
 //    level, elimination position).  This is a topological order of the
 //    factor's dependency graph, so it leaves the factor unchanged and lets
@@ -120,7 +120,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     // elimination order
     std::vector<int> ord(nb), epos(nb);
     std::iota(ord.begin(), ord.end(), 0);
-    if (b == p && opt.c_order == 1) {
+    if ((b == p && opt.c_order == 1) || (b < p && opt.b_order == 1)) {
       std::vector<int> col(nb, -1), used(nb + 2, -1);
       int nc = 0;
       for (int t = 0; t < nb; t++) {
@@ -130,7 +130,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         col[t] = c;
         nc = std::max(nc, c + 1);
       }
-      P.ncolors = nc;
+      if (b == p) P.ncolors = nc;
       std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return col[a] < col[c]; });
     }
     for (int e = 0; e < nb; e++) epos[ord[e]] = e;
@@ -371,11 +371,44 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       }
     }
   }
+  // level chunks: all blocks by level number, and C_a alone
+  {
+    const int maxL = int(P.fl_ptr.size()) - 1;
+    auto add = [&](int rec) {
+      for (int i0 = 0; i0 < P.lvl_nrows[rec]; i0 += kChunk) {
+        P.chunks.push_back(rec);
+        P.chunks.push_back(i0);
+        P.chunks.push_back(std::min(kChunk, P.lvl_nrows[rec] - i0));
+        P.chunks.push_back(0);
+      }
+    };
+    P.ch_all_ptr.assign(maxL + 1, 0);
+    for (int L = 0; L < maxL; L++) {
+      for (int b = 0; b <= p; b++)
+        if (P.blk_lvl0[b] + L < P.blk_lvl0[b + 1]) add(P.blk_lvl0[b] + L);
+      P.ch_all_ptr[L + 1] = int(P.chunks.size() / 4);
+    }
+    const int Lc = P.blk_lvl0[p + 1] - P.blk_lvl0[p];
+    P.ch_c_ptr.assign(Lc + 1, P.ch_all_ptr[maxL]);
+    for (int L = 0; L < Lc; L++) {
+      add(P.blk_lvl0[p] + L);
+      P.ch_c_ptr[L + 1] = int(P.chunks.size() / 4);
+    }
+  }
   // inverse diagonal in slice layout, and the capacities of the TMA solve
   P.row_slot.assign(n, 0);
   for (int l = 0; l < nlev; l++)
     for (int i = 0; i < P.lvl_nrows[l]; i++)
       P.row_slot[P.lvl_row0[l] + i] = (P.lvl_slice0[l] + i / kSlice) * kSlice + i % kSlice;
+  P.l_span.assign(2 * size_t(n), 0);
+  P.u_span.assign(2 * size_t(n), 0);
+  for (int g = 0; g < n; g++) {
+    const int sl = P.row_slot[g] / kSlice, ln = P.row_slot[g] % kSlice;
+    P.l_span[2 * g] = P.l_soff[sl] + ln;
+    P.l_span[2 * g + 1] = P.f_rp[g + 1] - P.f_rp[g] - 1;
+    P.u_span[2 * g] = P.u_soff[sl] + ln;
+    P.u_span[2 * g + 1] = int(upper[g].size());
+  }
   for (int b = 0; b < p; b++) {
     const int l0 = P.blk_lvl0[b], l1 = P.blk_lvl0[b + 1];
     if (l1 == l0) continue;

@@ -16,6 +16,7 @@
 namespace ddlr {
 
 constexpr int kSlice = 32;  // rows per sliced-ELL slice (one warp)
+constexpr int kChunk = 256;  // rows per CTA of the level-chunk solve (one per thread)
 
 struct Plan {
   int n = 0, p = 0, s = 0, m = 0;
@@ -51,9 +52,15 @@ struct Plan {
   std::vector<int> u_soff, u_sw, u_col;   // strictly upper part of L^T
   std::vector<int> map_l, map_u;          // factor entry -> slot (-1 for diagonal)
   std::vector<int> row_slot;              // row -> slice*32 + lane (inverse diagonal in slice layout)
+  std::vector<int> l_span, u_span;        // per row: {first slot, entries} of its L and L^T rows
   // shared-memory capacities of the TMA-pipelined interior solve
   int tma_zs = 0, tma_nl = 0, tma_ns = 0, tma_e = 0, tma_s = 0;
   long long tma_blk_e = 0, tma_blk_s = 0;   // largest per-block totals over all stages
+  // level chunks (record, first row, rows) of at most kChunk rows: level L of
+  // every block = chunks [ch_all_ptr[L], ch_all_ptr[L+1]); level L of C_a alone
+  // = [ch_c_ptr[L], ch_c_ptr[L+1])
+  std::vector<int> chunks;                // 4 ints per chunk
+  std::vector<int> ch_all_ptr, ch_c_ptr;
   // statistics
   int levels_interior = 0, levels_c = 0, ncolors = 0;
   long long nnz_ehat = 0, nnz_factor = 0;

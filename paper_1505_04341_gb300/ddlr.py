@@ -30,6 +30,7 @@ class ddlr_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("rank_k", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("theta_mode", ctypes.c_int),
                 ("factor", ctypes.c_int), ("c_order", ctypes.c_int),
+                ("b_order", ctypes.c_int),
                 ("precision", ctypes.c_int), ("uk_bf16", ctypes.c_int),
                 ("scale_diag", ctypes.c_int), ("lanczos_max", ctypes.c_int),
                 ("lanczos_check", ctypes.c_int), ("lanczos_eps", ctypes.c_double),

@@ -30,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--bf16", type=int, default=1)
     ap.add_argument("--c-order", type=int, default=1)
+    ap.add_argument("--b-order", type=int, default=1)
     ap.add_argument("--lanczos-max", type=int, default=0)
     args = ap.parse_args(argv)
 
@@ -43,7 +44,8 @@ def main(argv=None):
     A, part, p = w["A"], w["part"], w["p"]
     n = A[0]
     h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=0,
-             c_order=args.c_order, precision=args.precision, uk_bf16=args.bf16,
+             c_order=args.c_order, b_order=args.b_order, precision=args.precision,
+             uk_bf16=args.bf16,
              lanczos_max=args.lanczos_max)
     b = torch.tensor(W.rhs(n, 0), device="cuda")
     y = torch.empty_like(b)

@@ -33,7 +33,7 @@ def test_option_defaults(lib):
     o = pkg.options()
     assert (o.variant, o.rank_k, o.alpha, o.theta_mode) == (1, 16, 1.0, 1)
     assert (o.lanczos_max, o.lanczos_check, o.lanczos_eps) == (0, 10, 1e-4)
-    assert (o.factor, o.c_order, o.precision, o.max_nrhs) == (0, 0, 0, 1)
+    assert (o.factor, o.c_order, o.b_order, o.precision, o.max_nrhs) == (0, 0, 0, 0, 1)
 
 
 def _setup_status(lib, A, part, p, **kw):

@@ -26,7 +26,14 @@ PROBLEMS = {
     "3d_20_ic0_multicolour": lambda: (W.laplacian((20, 20, 20)),) + W.box_partition((20, 20, 20), (2, 2, 2)) + (0, 1),
     "3d_33x17x21_ragged": lambda: (W.laplacian((33, 17, 21)),) + W.box_partition((33, 17, 21), (3, 2, 2)) + (0, 0),
     "jump_32_cuts": lambda: (W.jump_coefficient_fv(32, 8, 0),) + W.random_cut_partition(32, 3, 0, 6, 16) + (0, 1),
+    "3d_24_ic0_multicolour_all": lambda: (W.laplacian((24, 24, 24)),) + W.box_partition((24, 24, 24), (3, 2, 2)) + (0, 3),
+    "jump_32_multicolour_all": lambda: (W.jump_coefficient_fv(32, 8, 0),) + W.random_cut_partition(32, 3, 0, 6, 16) + (0, 3),
 }
+
+
+def _orders(c_order):
+    """c_order bit 0: C_a multicolour; bit 1: interior blocks multicolour"""
+    return dict(c_order=c_order & 1, b_order=c_order >> 1)
 
 
 def _rel(a, b):
@@ -39,16 +46,16 @@ def _built():
     O.build()
 
 
-@pytest.mark.parametrize("tma", [1, 0], ids=["tma", "plain"])
+@pytest.mark.parametrize("kind", ["sf", "tma", "plain"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
-def test_a0_solve_and_factor_parity(name, tma, monkeypatch):
-    """Both interior-solve kernels (TMA-pipelined and plain) against the oracle."""
+def test_a0_solve_and_factor_parity(name, kind, monkeypatch):
+    """Every interior-solve kernel (synchronisation-free, TMA-pipelined level
+    schedule, plain level schedule) against the oracle."""
     A, part, p, factor, c_order = PROBLEMS[name]()
     k = 4
-    if not tma:
-        monkeypatch.setenv("DDLR_NO_TMA", "1")
-    h = pkg.DDLR(A, part, p, rank_k=k, factor=factor, c_order=c_order)
-    orc = O.Oracle(A, part, p, k=k, factor=factor, c_order=c_order)
+    monkeypatch.setenv("DDLR_SOLVE", kind)
+    h = pkg.DDLR(A, part, p, rank_k=k, factor=factor, **_orders(c_order))
+    orc = O.Oracle(A, part, p, k=k, factor=factor, **_orders(c_order))
     n = A[0]
     for seed in (1, 2):
         x = W.rhs(n, seed)
@@ -71,15 +78,15 @@ def test_a0_solve_and_factor_parity(name, tma, monkeypatch):
 
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("name", ["2d_64x64_C1_exact", "3d_24_ic0_natural", "3d_20_ic0_multicolour",
-                                  "jump_32_cuts"])
+                                  "jump_32_cuts", "3d_24_ic0_multicolour_all"])
 def test_apply_parity_injected_lowrank(name, variant):
     A, part, p, factor, c_order = PROBLEMS[name]()
     k = 8
     scale = 1 if name.startswith("jump") else 0
-    h = pkg.DDLR(A, part, p, variant=variant, rank_k=k, factor=factor, c_order=c_order,
-                 scale_diag=scale)
-    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=factor, c_order=c_order,
-                   scale_diag=scale)
+    h = pkg.DDLR(A, part, p, variant=variant, rank_k=k, factor=factor, scale_diag=scale,
+                 **_orders(c_order))
+    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=factor, scale_diag=scale,
+                   **_orders(c_order))
     U, lam, Hk, rows = orc.lowrank_original_order()
     h.set_lowrank(U, lam, orc.theta, Hk)
     n = A[0]
@@ -141,12 +148,14 @@ def test_full_rank_exact_one_iteration(variant):
 
 
 CONFIGS = [
-    # (workload, variant, k, factor, c_order)
+    # (workload, variant, k, factor, orders: bit 0 C_a, bit 1 interior multicolour)
     ("lap2d_64_b2x2", 1, 8, 1, 0),
     ("lap3d_64_b4", 1, 16, 0, 0),
     ("lap3d_64_b4", 1, 16, 0, 1),
     ("lap3d_64_b4", 2, 16, 0, 1),
     ("lap3d_64_b4", 1, 32, 0, 1),
+    ("lap3d_64_b4", 1, 16, 0, 3),
+    ("lap3d_64_b4", 2, 16, 0, 3),
 ]
 
 
@@ -154,8 +163,8 @@ CONFIGS = [
 def test_pcg_parity(wl, variant, k, factor, c_order):
     w = W.workload(wl)
     A, part, p = w["A"], w["part"], w["p"]
-    h = pkg.DDLR(A, part, p, variant=variant, rank_k=k, factor=factor, c_order=c_order)
-    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=factor, c_order=c_order)
+    h = pkg.DDLR(A, part, p, variant=variant, rank_k=k, factor=factor, **_orders(c_order))
+    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=factor, **_orders(c_order))
     b = W.rhs(A[0], 0)
     x, info = h.pcg(torch.tensor(b, device="cuda"), tol=1e-8)
     xo, its_o, rel_o, st = orc.pcg(b, 1e-8)
