@@ -223,7 +223,10 @@ def run_ours(args):
     cnt = h.counters()
     tr = h.traffic()
     fams = cnt["families"]
-    dom = max((f for f in fams if fams[f]["launches"] > 0), key=lambda f: fams[f]["ms"])
+    # dominant kernel: the family with the most device time among the kernels
+    # whose algorithmic bytes are accounted (the data-moving hot-path kernels)
+    dom = max((f for f in fams if fams[f]["launches"] > 0 and tr["family_bytes"].get(f, 0) > 0),
+              key=lambda f: fams[f]["ms"])
     dom_ms = fams[dom]["ms"] / fams[dom]["launches"]
     dom_bytes = tr["family_bytes"].get(dom, 0.0)
     peak, peak_kind = _peaks()

@@ -60,6 +60,11 @@ struct ddlr_ctx {
   ddlr_options opt{};
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t stream2 = nullptr;  // C_a solve branch (forked with events)
+  cudaStream_t gstream = nullptr;  // internal stream of the PCG graph
+  cudaGraphExec_t pcg_exec = nullptr;
+  int pcg_exec_flexible = -1;
+  long long pcg_nodes = 0;
+  std::vector<long long> pcg_fam_nodes;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Plan P;
   std::string err;
@@ -767,16 +772,51 @@ void allocate(ddlr_ctx *c) {
   ck(cudaMallocHost(&c->h_pin, 64 * sizeof(double)), "cudaMallocHost");
 }
 
+// one PCG iteration (Sec. 5) on device-order vectors; every kernel reads its
+// scalars from the device state and returns at once after convergence
+void pcg_iteration(ddlr_ctx *c, const double *b, double *x, int flexible) {
+  const int n = c->P.n;
+  double *r = c->pv[1], *z = c->pv[2], *p = c->pv[3], *q = c->pv[4], *t = c->pv[5], *zo = c->pv[6];
+  double *part = c->part64;
+  const int *gate = pcg_gate(c);
+  KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, p, q, gate);
+  KL(c, "pcg_dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, p, q, part, gate);
+  KL(c, "pcg_scalar", c->stream, k_pcg_alpha, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_axpy", c->stream, k_pcg_update<256>, kRedGrid, 256, 0, (long long)n, c->pcg, p, q, x, r, part);
+  KL(c, "pcg_scalar", c->stream, k_pcg_rr, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_check", c->stream, k_pcg_true_res<256>, kRedGrid, 256, 0, n, c->pcg, c->a_soff, c->a_sw, c->a_col, c->a_val, b, x, t, part);
+  KL(c, "pcg_scalar", c->stream, k_pcg_true_dec, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_check", c->stream, k_pcg_copy_r, nblk(n), kThreads, 0, (long long)n, c->pcg, t, r);
+  precond(c, r, z, gate);
+  KL(c, "pcg_dot2", c->stream, (k_dot2_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part, gate);
+  KL(c, "pcg_scalar", c->stream, k_pcg_beta, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_p", c->stream, k_pcg_p, nblk(n), kThreads, 0, (long long)n, c->pcg, z, p, flexible ? zo : (double *)nullptr);
+}
+
 // PCG on device-order vectors b -> x (Sec. 5), device-side control flow; the
-// host only polls the `done` word every few iterations.
+// host only polls the `done` word every few iterations.  Unless per-kernel
+// timing is on, one iteration is captured once into a CUDA graph (on an
+// internal stream ordered after the caller's) and replayed.
 void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
              ddlr_solve_info *info) {
   const Plan &P = c->P;
   const int n = P.n;
   const int flexible = c->opt.precision == 1 ? 1 : 0;
-  double *r = c->pv[1], *z = c->pv[2], *p = c->pv[3], *q = c->pv[4], *t = c->pv[5], *zo = c->pv[6];
+  double *r = c->pv[1], *z = c->pv[2], *p = c->pv[3], *q = c->pv[4], *zo = c->pv[6];
   double *part = c->part64;
   const int *gate = pcg_gate(c);
+  const char *ng = getenv("DDLR_NO_GRAPH");
+  const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+  cudaStream_t user = c->stream;
+  struct Restore {
+    ddlr_ctx *c; cudaStream_t s;
+    ~Restore() { c->stream = s; }
+  } restore{c, user};
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_fork, user), "event");
+    ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+    c->stream = c->gstream;
+  }
   ck(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream), "memset");
   ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
   KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, b, b, part, (const int *)nullptr);
@@ -786,25 +826,40 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   KL(c, "pcg", c->stream, k_pcg_rz0, 1, 32, 0, c->pcg, part, kRedGrid);
   ck(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
   ck(cudaMemcpyAsync(zo, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  if (use_graph && (c->pcg_exec == nullptr || c->pcg_exec_flexible != flexible)) {
+    if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+    const long long l0 = c->launches;
+    const std::vector<long long> f0 = c->fam_cnt;
+    ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+    pcg_iteration(c, b, x, flexible);
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamEndCapture(c->stream, &g), "capture");
+    cudaError_t e = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+    cudaGraphDestroy(g);
+    ck(e, "cudaGraphInstantiate");
+    c->pcg_exec_flexible = flexible;
+    c->pcg_nodes = c->launches - l0;
+    c->pcg_fam_nodes.assign(c->fam_cnt.size(), 0);
+    for (size_t i = 0; i < c->fam_cnt.size(); i++)
+      c->pcg_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+    c->launches = l0;                    // captured, not yet executed
+    for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+    for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+  }
   const int batch = 4;
   for (int it = 0; it < maxit + batch; it += batch) {
     for (int bi = 0; bi < batch; bi++) {
-      KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, p, q, gate);
-      KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, p, q, part, gate);
-      KL(c, "pcg", c->stream, k_pcg_alpha, 1, 32, 0, c->pcg, part, kRedGrid);
-      KL(c, "pcg", c->stream, k_pcg_update<256>, kRedGrid, 256, 0, (long long)n, c->pcg, p, q, x, r, part);
-      KL(c, "pcg", c->stream, k_pcg_rr, 1, 32, 0, c->pcg, part, kRedGrid);
-      KL(c, "pcg", c->stream, k_pcg_true_res<256>, kRedGrid, 256, 0, n, c->pcg, c->a_soff, c->a_sw, c->a_col, c->a_val, b, x, t, part);
-      KL(c, "pcg", c->stream, k_pcg_true_dec, 1, 32, 0, c->pcg, part, kRedGrid);
-      KL(c, "pcg", c->stream, k_pcg_copy_r, nblk(n), kThreads, 0, (long long)n, c->pcg, t, r);
-      precond(c, r, z, gate);
-      KL(c, "pcg", c->stream, (k_dot2_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part, gate);
-      KL(c, "pcg", c->stream, k_pcg_beta, 1, 32, 0, c->pcg, part, kRedGrid);
-      KL(c, "pcg", c->stream, k_pcg_p, nblk(n), kThreads, 0, (long long)n, c->pcg, z, p, flexible ? zo : (double *)nullptr);
+      if (use_graph) {
+        ck(cudaGraphLaunch(c->pcg_exec, c->stream), "cudaGraphLaunch");
+        c->launches += c->pcg_nodes;
+        for (size_t i = 0; i < c->pcg_fam_nodes.size(); i++) c->fam_cnt[i] += c->pcg_fam_nodes[i];
+      } else {
+        pcg_iteration(c, b, x, flexible);
+      }
     }
     int done = 0;
     ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
-    sync(c);
+    ck(cudaStreamSynchronize(c->stream), "sync");
     std::memcpy(&done, c->h_pin, sizeof(int));
     if (done) break;
   }
@@ -817,7 +872,11 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   ck(cudaMemcpyAsync(c->h_pin, c->w64[7], sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
   ck(cudaMemcpyAsync(&hs, c->pcg, sizeof(PcgState), cudaMemcpyDeviceToHost, c->stream), "D2H");
   ck(cudaMemcpyAsync(dfl, c->dflag, sizeof(dfl), cudaMemcpyDeviceToHost, c->stream), "D2H");
-  sync(c);
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_join, c->stream), "event");
+    ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
+  }
   if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
   if (info) {
     info->its = hs.its;
@@ -902,6 +961,7 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
     ddlr_status s1 = build_plan(n, rowptr, colind, val, part, p, c->opt, c->P, err);
     if (s1 != DDLR_OK) { c->err = err; return s1; }
     ck(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     allocate(c);
@@ -1190,6 +1250,10 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "e_int") b = ei;
       else if (f == "u_add") b = uadd;
       else if (f == "spmv") b = nnz_a * 12.0 + 2.0 * n * 8.0;
+      else if (f == "pcg_dot") b = 2.0 * n * 8.0;
+      else if (f == "pcg_axpy") b = 6.0 * n * 8.0;
+      else if (f == "pcg_dot2") b = 3.0 * n * 8.0;
+      else if (f == "pcg_p") b = (c->opt.precision == 1 ? 4.0 : 3.0) * n * 8.0;
       family_bytes[i] = b;
     }
   }
@@ -1217,6 +1281,8 @@ ddlr_status ddlr_destroy(ddlr_handle c) {
   if (c->h_pin) cudaFreeHost(c->h_pin);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->gstream) { cudaStreamSynchronize(c->gstream); cudaStreamDestroy(c->gstream); }
   if (c->stream2) cudaStreamDestroy(c->stream2);
   delete c;
   return DDLR_OK;
