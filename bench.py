@@ -283,6 +283,100 @@ def run_ours(args):
     v2_apply_ms, v2_apply_gbs = apply_rate(h2)
     h2.close()
 
+    # precision line: 128^3 Laplacian, 512 boxes, k = 32 -- FP64 against mixed
+    # (FP32 factors and solves, BF16 or FP32 U_k, FP64 flexible CG)
+    prec = {}
+    if not args.skip_large:
+        w3 = W.workload("lap3d_128_b8")
+        A3, part3, p3 = w3["A"], w3["part"], w3["p"]
+        b3 = torch.tensor(W.rhs(A3[0], 0), device="cuda")
+        x3 = torch.zeros_like(b3)
+        sol = {}
+        for name, extra in (("fp64", dict(precision=0)), ("mixed_bf16", dict(precision=1, uk_bf16=1)),
+                            ("mixed_fp32", dict(precision=1, uk_bf16=0))):
+            h3 = pkg.DDLR(A3, part3, p3, **dict(OPTS, rank_k=32, **extra))
+            h3.refactor()
+            h3.pcg(b3, x3, tol=TOL)
+            flush.fill_(1.0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            h3.refactor()
+            e1.record(stream)
+            _, inf3 = h3.pcg(b3, x3, tol=TOL)
+            e2.record(stream)
+            e2.synchronize()
+            sol[name] = x3.clone()
+            prec[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
+                          "total_ms": round(e0.elapsed_time(e2), 3), "iterations": inf3[0]["its"],
+                          "true_relres": inf3[0]["relres"]}
+            h3.close()
+        for name in ("mixed_bf16", "mixed_fp32"):
+            prec[name]["rel_err_vs_fp64_solution"] = float(
+                (sol[name] - sol["fp64"]).norm() / sol["fp64"].norm())
+            prec[name]["speedup_vs_fp64"] = round(prec["fp64"]["total_ms"] / prec[name]["total_ms"], 3)
+        del sol
+    # batching line: 96^3 jump coefficients, 125 uneven boxes, k = 24, 32
+    # right-hand sides in one batched solve (FP32 inner / FP64 outer)
+    batch = {}
+    if not args.skip_large:
+        w4 = W.workload("jump3d_96_cut5")
+        A4, part4, p4 = w4["A"], w4["part"], w4["p"]
+        n4 = A4[0]
+        B4 = torch.tensor(np.stack([W.rhs(n4, s_) for s_ in range(32)], axis=1), device="cuda")
+        B4 = B4.T.contiguous().T
+        X4 = torch.zeros_like(B4)
+        h4 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
+                      scale_diag=1, precision=1, uk_bf16=0, max_nrhs=32)
+        # 10^{+-3} jump coefficients need ~1,000-1,300 iterations at k = 24
+        # (the FP64 oracle: 1,297 with multicolour, 986 with natural orders),
+        # beyond the paper's 500-iteration cap
+        MAXIT4 = 3000
+        h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
+        flush.fill_(1.0)
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        e0.record(stream)
+        h4.refactor()
+        e1.record(stream)
+        _, inf4 = h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
+        e2.record(stream)
+        b1 = B4[:, 0].contiguous()
+        x1 = torch.zeros_like(b1)
+        _, inf1 = h4.pcg(b1, x1, tol=TOL, maxit=MAXIT4)
+        e3.record(stream)
+        e3.synchronize()
+        its4 = [i["its"] for i in inf4]
+        info4 = h4.info()
+        batch = {"workload": "jump3d_96_cut5", "n": n4, "subdomains": p4, "rank_k": 24, "nrhs": 32,
+                 "setup_ms": round(e0.elapsed_time(e1), 3),
+                 "batched_solve_ms": round(e1.elapsed_time(e2), 3),
+                 "ms_per_rhs": round(e1.elapsed_time(e2) / 32, 3),
+                 "single_rhs_solve_ms": round(e2.elapsed_time(e3), 3),
+                 "throughput_gain_vs_single": round(32 * e2.elapsed_time(e3) / e1.elapsed_time(e2), 2),
+                 "iterations_min_max": [min(its4), max(its4)],
+                 "true_relres_max": max(i["relres"] for i in inf4),
+                 "all_ok": all(i["status"] == "OK" for i in inf4),
+                 "single_rhs_iterations": inf1[0]["its"], "maxit": MAXIT4,
+                 "autotuned_block": [info4["batch_block_chunks"], info4["batch_block_elem"]]}
+        h4.close()
+        del B4, X4
+
+    # serving line: 512 requests over grid edges {32, 48, 64, 96, 128}
+    # ((edge/16)^3 boxes, k = 16, one RHS each), Poisson arrivals; first
+    # saturated (all submitted at once), then at 50 % and 90 % of that rate
+    serving = {}
+    if not args.skip_large:
+        from paper_1505_04341_gb300 import serve
+        srv, models = serve.setup_server([32, 48, 64, 96, 128], k=16, max_batch=16, max_concurrent=4)
+        recs, mk = serve.run_stream(srv, models, 512, 0.0, seed=0)
+        serving["saturated"] = serve.summarize(recs, mk)
+        sat = serving["saturated"]["solves_per_s"]
+        for frac in (0.5, 0.9):
+            recs, mk = serve.run_stream(srv, models, 512, frac * sat, seed=1)
+            serving[f"load_{frac}"] = serve.summarize(recs, mk)
+        serving["stats"] = srv.stats()
+        serving["setup_s"] = {str(e): round(models[e][2], 3) for e in models}
+        srv.close()
+
     # end to end through the C ABI from host buffers
     e2e_ms = []
     for i in range(args.steps + 1):
@@ -330,6 +424,9 @@ def run_ours(args):
                                 "apply_algorithmic_GBps": round(mixed_apply_gbs, 1)},
             "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
                                             "iterations": [i["its"] for i in inf_nat]},
+            "precision_lap3d_128_b8_k32": prec,
+            "batching_jump3d_96_cut5_32rhs": batch,
+            "serving_lap3d_32_to_128_512req": serving,
             "ddlr2_fp64": {"ms_per_solve": round(statistics.mean(ms_v2), 3),
                            "iterations": [i["its"] for i in inf_v2],
                            "apply_ms": round(v2_apply_ms, 4),
@@ -400,6 +497,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-large", action="store_true",
+                    help="skip the 128^3 precision and 96^3 batching legs")
     ap.add_argument("--timed-only", action="store_true",
                     help="run only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()

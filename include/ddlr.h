@@ -88,6 +88,9 @@ typedef struct {
   double fill_ratio;       /* nnz(preconditioner)/nnz(A) as in Sec. 5             */
   long long device_bytes;  /* device memory held by the handle                    */
   double setup_ms;         /* wall time of the last (re)setup                     */
+  int batch_block_chunks;  /* rows per pass picked by the autotuner for the batched
+                              level solve (0 before the first batched call)       */
+  int batch_block_elem;    /* block size picked for the batched row kernels      */
 } ddlr_info;
 
 typedef struct {
@@ -124,7 +127,10 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind,
 ddlr_status ddlr_refactor(ddlr_handle h, const double *val);
 
 /* y = M^-1 x (Algorithm 1 for DDLR-1, eq. Form2a for DDLR-2) for nrhs vectors.
- * x and y must not overlap.  Errors: INVALID (nrhs < 1, ld < n, NULL). */
+ * With nrhs > 1 the vectors are processed in batches of up to 64 in one set of
+ * launches (row-major blocks, one lane per vector); a column's result does not
+ * depend on the other columns of its batch.  x and y must not overlap.
+ * Errors: INVALID (nrhs < 1, ld < n, NULL). */
 ddlr_status ddlr_apply(ddlr_handle h, const double *x, double *y, int nrhs,
                        int ld);
 
@@ -137,7 +143,10 @@ ddlr_status ddlr_a0_solve(ddlr_handle h, const double *x, double *y, int nrhs,
  * stopping when ||r|| <= tol ||b|| and the true residual confirms it (else r is
  * replaced by b - A x and CG restarts), or after maxit iterations (maxit <= 0:
  * 500, Sec. 5).  With precision 1 the outer loop is flexible CG in FP64 around
- * the FP32 preconditioner.  info[nrhs] (host memory, may be NULL) receives the
+ * the FP32 preconditioner.  With nrhs > 1 the right-hand sides are solved
+ * together (batches of up to 64, one CUDA-graph iteration for the batch, a
+ * converged column is frozen while the others continue); a column's iterates
+ * do not depend on which other columns share its batch.  info[nrhs] (host memory, may be NULL) receives the
  * per-RHS result.  Synchronous.  Returns DDLR_OK when every RHS converged,
  * else DDLR_ERR_NOCONV or DDLR_ERR_NAN. */
 ddlr_status ddlr_pcg(ddlr_handle h, const double *b, double *x, int nrhs,
@@ -198,6 +207,65 @@ const char *ddlr_last_error(ddlr_handle h);
 
 /* Frees every device and host resource of the handle (NULL is a no-op). */
 ddlr_status ddlr_destroy(ddlr_handle h);
+
+/* ------------------------------------------------------------- serving
+ * A solve service on one GPU (no counterpart in the paper; it serves many
+ * solves with resident preconditioners, the amortisation the paper's
+ * conclusion points to).  Every model (a matrix with its DDLR setup) stays
+ * resident and has a worker thread with its own CUDA streams.  Requests are
+ * queued per model; a free worker takes all waiting requests of its model (up
+ * to max_batch) into one batched PCG, so requests arriving while others run
+ * join the next batch (continuous batching), and at most max_concurrent
+ * batches run on the GPU at once, overlapping across models.  A batch is
+ * admitted only if its workspace fits in memory_fraction of the free device
+ * memory (narrowed otherwise).  A request's result does not depend on the other
+ * requests of its batch. */
+typedef struct ddlr_server_ctx *ddlr_server;
+
+typedef struct {
+  int max_concurrent;      /* batches on the GPU at the same time (default 4)   */
+  int max_batch;           /* right-hand sides per batched solve, 1..64 (16)    */
+  double tol;              /* relative residual target (1e-8)                   */
+  int maxit;               /* iteration cap (500)                               */
+  double memory_fraction;  /* share of free device memory usable (0.9)          */
+} ddlr_server_options;
+
+ddlr_status ddlr_server_options_default(ddlr_server_options *opt);
+
+/* Creates a server on the current device.  Errors: INVALID (bad options). */
+ddlr_status ddlr_server_create(const ddlr_server_options *opt, ddlr_server *out);
+
+/* Sets up and keeps resident the preconditioner of one matrix (arguments as
+ * ddlr_setup); *model receives its index.  Synchronous.  OOM if its estimated
+ * footprint does not fit in the memory the server may use. */
+ddlr_status ddlr_server_add_model(ddlr_server s, int n, const int *rowptr,
+                                  const int *colind, const double *val,
+                                  const int *part, int p,
+                                  const ddlr_options *opt, int *model);
+
+/* Queues the solve A x = b for a model; b (host, original order, n values) is
+ * copied.  *request receives the request id.  Returns at once. */
+ddlr_status ddlr_server_submit(ddlr_server s, int model, const double *b,
+                               long long *request);
+
+/* Waits for a request (timeout_s <= 0: no limit; TIMEOUT when it expires),
+ * copies x (host, n values; may be NULL), its solve info, the latency from
+ * submit to completion in seconds and the width of the batch it ran in, then
+ * forgets the request.  Returns the request's solve status. */
+ddlr_status ddlr_server_wait(ddlr_server s, long long request, double timeout_s,
+                             double *x, ddlr_solve_info *info,
+                             double *latency_s, int *batch);
+
+/* Completed requests, widest batch and most batches in flight seen, models. */
+ddlr_status ddlr_server_stats(ddlr_server s, long long *completed,
+                              int *max_batch_seen, int *max_inflight_seen,
+                              int *nmodels);
+
+/* Text of the server's last error (never NULL). */
+const char *ddlr_server_last_error(ddlr_server s);
+
+/* Stops the workers (queued requests are dropped) and frees every model. */
+ddlr_status ddlr_server_destroy(ddlr_server s);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libddlr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ddlr_api.cu", "ddlr_plan.cpp"]
+SOURCES = ["ddlr_api.cu", "ddlr_plan.cpp", "ddlr_serve.cpp"]
 
 
 def _nvcc():

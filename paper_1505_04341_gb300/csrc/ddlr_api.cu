@@ -16,6 +16,8 @@
 #include <vector>
 
 #include "ddlr.h"
+#include "ddlr_batch.cuh"
+#include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
 
@@ -65,6 +67,27 @@ struct ddlr_ctx {
   int pcg_exec_flexible = -1;
   long long pcg_nodes = 0;
   std::vector<long long> pcg_fam_nodes;
+  // batched (multi right-hand side) path
+  struct Batch {
+    int R = 0;
+    std::vector<void *> mem;
+    double *B = nullptr, *X = nullptr, *Rr = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr,
+           *T = nullptr, *Zo = nullptr, *S = nullptr;
+    double *w64[5] = {nullptr};
+    float *w32[7] = {nullptr};
+    double *part64 = nullptr;
+    float *part32 = nullptr;
+    PcgStateMR *st = nullptr;
+    struct G {
+      cudaGraphExec_t exec = nullptr;
+      int flex = -1;
+      long long nodes = 0;
+      std::vector<long long> fam_nodes;
+    };
+    std::map<int, G> graphs;            // one captured PCG iteration per width R
+    int chunk_per = 0, bd_elem = 256;   // autotuned: rows per pass of the level solve, row-kernel block
+    bool tuned = false;
+  } bt;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Plan P;
   std::string err;
@@ -886,6 +909,351 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   }
 }
 
+// ============================================================ batched path
+void batch_free(ddlr_ctx *c) {
+  auto &B = c->bt;
+  for (auto &kv : B.graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  for (void *p : B.mem) cudaFree(p);
+  B = ddlr_ctx::Batch();
+}
+
+// workspaces for batches of up to R right-hand sides; they only grow (a
+// narrower batch reuses them), so steady-state serving never frees memory
+void batch_alloc(ddlr_ctx *c, int R) {
+  auto &B = c->bt;
+  if (B.R >= R) return;
+  const int per_c = B.chunk_per, bd_e = B.bd_elem;
+  const bool tuned = B.tuned;
+  batch_free(c);
+  const Plan &P = c->P;
+  const size_t nR = size_t(P.n) * R, sR = size_t(P.s) * R, k = c->opt.rank_k;
+  auto al = [&](size_t bytes) {
+    void *p = nullptr;
+    ck(cudaMalloc(&p, bytes < 16 ? 16 : bytes), "cudaMalloc");
+    B.mem.push_back(p);
+    return p;
+  };
+  double **v[] = {&B.B, &B.X, &B.Rr, &B.Z, &B.P, &B.Q, &B.T, &B.Zo, &B.S};
+  for (double **pp : v) *pp = (double *)al(nR * 8);
+  B.w64[0] = (double *)al(nR * 8);   // A0 solve result
+  B.w64[1] = (double *)al(sR * 8);   // Y
+  B.w64[2] = (double *)al(sR * 8);   // W
+  B.w64[3] = (double *)al(nR * 8);   // RHS
+  B.w64[4] = (double *)al(k * R * 8);
+  if (c->opt.precision == 1) {
+    B.w32[0] = (float *)al(nR * 4);
+    B.w32[1] = (float *)al(sR * 4);
+    B.w32[2] = (float *)al(sR * 4);
+    B.w32[3] = (float *)al(nR * 4);
+    B.w32[4] = (float *)al(k * R * 4);
+    B.w32[5] = (float *)al(nR * 4);   // cast input
+    B.w32[6] = (float *)al(nR * 4);   // cast output
+    B.part32 = (float *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 4);
+  }
+  B.part64 = (double *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 8);
+  B.st = (PcgStateMR *)al(sizeof(PcgStateMR));
+  B.R = R;
+  B.chunk_per = tuned ? per_c : std::max(1, 256 / R);
+  B.bd_elem = tuned ? bd_e : 256;
+  B.tuned = tuned;
+}
+
+// block of the batched level solve: the autotuned rows-per-pass times R
+inline int chunk_block(const ddlr_ctx *c, int R) {
+  return std::max(R, std::min(1024 / R, std::max(1, c->bt.chunk_per)) * R);
+}
+
+template <typename T> struct BPrec;
+template <> struct BPrec<double> {
+  static double *w(ddlr_ctx *c, int i) { return c->bt.w64[i]; }
+  static double *part(ddlr_ctx *c) { return c->bt.part64; }
+};
+template <> struct BPrec<float> {
+  static float *w(ddlr_ctx *c, int i) { return c->bt.w32[i]; }
+  static float *part(ddlr_ctx *c) { return c->bt.part32; }
+};
+
+inline unsigned eblk(long long cnt, int bd) { return (unsigned)((cnt + bd - 1) / bd); }
+
+// widest batch the shared-memory tiles allow (k*R <= 1024, k <= 64); < 2 means
+// "solve column by column"
+inline int batch_width(const ddlr_ctx *c) {
+  const int k = c->opt.rank_k;
+  return k <= 64 ? std::min(kMaxR, 1024 / k) : 0;
+}
+
+// Z = A0^-1 X for a block of R vectors: every level of all blocks per launch
+template <typename T>
+void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
+  const Plan &P = c->P;
+  const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  const std::vector<int> &ptr = P.ch_all_ptr;
+  const int nL = int(ptr.size()) - 1;
+  auto launch = [&](int L, int mode) {
+    const int nch = ptr[L + 1] - ptr[L];
+    if (nch > 0)
+      KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,
+         reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, X, Z, R, gate);
+  };
+  for (int L = 0; L + 1 < nL; L++) launch(L, 0);
+  if (nL > 0) launch(nL - 1, 2);
+  for (int L = nL - 2; L >= 0; L--) launch(L, 1);
+}
+
+// Out = M^-1 X for a block of R vectors (device order, row-major)
+template <typename T, typename TU>
+void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *gate) {
+  const Plan &P = c->P;
+  const int n = P.n, m = P.m, s = P.s, k = c->opt.rank_k;
+  const int bd = c->bt.bd_elem;
+  const T a = T(c->opt.alpha), ia = T(1.0 / c->opt.alpha);
+  T *part = BPrec<T>::part(c), *Tm = BPrec<T>::w(c, 4);
+  if (c->opt.variant == 1) {
+    T *Z = BPrec<T>::w(c, 0), *Y = BPrec<T>::w(c, 1), *W = BPrec<T>::w(c, 2), *RHS = BPrec<T>::w(c, 3);
+    a0_solve_mr<T>(c, X, Z, R, gate);
+    KL(c, "et_mr", c->stream, k_et_mr<T>, eblk((long long)s * R, bd), bd, 0, s, m, c->eht_rp, c->eht_ci,
+       Prec<T>::eht(c), ia, a, Z, Y, R, gate);
+    KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+    KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, Prec<T>::coef(c),
+       (const T *)nullptr, Tm, gate);
+    KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr<T, TU>), eblk((long long)s * R, bd), bd, 0, s, m, k, U, Tm, Y,
+       Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
+    KL(c, "e_int_mr", c->stream, k_e_interior_mr<T>, eblk((long long)m * R, bd), bd, 0, m, c->eh_rp, c->eh_ci,
+       Prec<T>::eh(c), ia, W, X, RHS, R, gate);
+    a0_solve_mr<T>(c, RHS, Out, R, gate);
+  } else {
+    a0_solve_mr<T>(c, X, Out, R, gate);
+    KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
+    KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, (const T *)nullptr,
+       Prec<T>::Hk(c), Tm, gate);
+    KL(c, "u_add_mr", c->stream, (k_u_add_mr<T, TU>), eblk((long long)n * R, bd), bd, 0, (long long)n, k, U, Tm,
+       Out, R, gate);
+  }
+}
+
+// Z = M^-1 Rr on FP64 blocks (scaling and precision handled here)
+void precond_mr(ddlr_ctx *c, const double *Rr, double *Z, int R, const int *gate) {
+  const int n = c->P.n;
+  const long long nR = (long long)n * R;
+  const int bd = c->bt.bd_elem;
+  const double *in = Rr;
+  if (c->dsc_dev) {
+    KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Rr, c->bt.S, gate);
+    in = c->bt.S;
+  }
+  if (c->opt.precision == 0) {
+    apply_mr<double, double>(c, c->U64, in, Z, R, gate);
+  } else {
+    float *i32 = c->bt.w32[5], *o32 = c->bt.w32[6];
+    KL(c, "vec_mr", c->stream, (k_cast<float, double>), eblk(nR, bd), bd, 0, nR, in, i32, gate);
+    if (c->opt.uk_bf16) apply_mr<float, __nv_bfloat16>(c, c->Ub16, i32, o32, R, gate);
+    else apply_mr<float, float>(c, c->U32, i32, o32, R, gate);
+    KL(c, "vec_mr", c->stream, (k_cast<double, float>), eblk(nR, bd), bd, 0, nR, o32, Z, gate);
+  }
+  if (c->dsc_dev)
+    KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Z, Z, gate);
+}
+
+// Autotuner: block shapes of the batched solve kernels, picked by timing the
+// candidates on the handle's own data (three preconditioner applications each,
+// CUDA events) the first time a batch of this width is used.
+void batch_autotune(ddlr_ctx *c, int R) {
+  auto &B = c->bt;
+  if (B.tuned) return;
+  const bool timing = c->timing;
+  c->timing = false;
+  const long long l0 = c->launches;
+  const std::vector<long long> f0 = c->fam_cnt;
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaMemsetAsync(B.Rr, 0, sizeof(double) * size_t(c->P.n) * R, c->stream), "memset");
+  auto time_apply = [&]() {
+    precond_mr(c, B.Rr, B.Z, R, nullptr);     // warm
+    ck(cudaEventRecord(e0, c->stream), "event");
+    for (int i = 0; i < 3; i++) precond_mr(c, B.Rr, B.Z, R, nullptr);
+    ck(cudaEventRecord(e1, c->stream), "event");
+    ck(cudaEventSynchronize(e1), "event");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  int best_c = B.chunk_per;
+  float best = 1e30f;
+  for (int mult : {1, 2, 4, 8, 16, 32}) {
+    const int bd = R * mult;
+    if (bd < 32 || bd > 1024) continue;
+    B.chunk_per = mult;
+    const float t = time_apply();
+    if (t < best) { best = t; best_c = mult; }
+  }
+  B.chunk_per = best_c;
+  int best_e = B.bd_elem;
+  best = 1e30f;
+  for (int bd : {128, 256, 512, 1024}) {
+    B.bd_elem = bd;
+    const float t = time_apply();
+    if (t < best) { best = t; best_e = bd; }
+  }
+  B.bd_elem = best_e;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->launches = l0;                      // tuning launches are not the caller's work
+  c->fam_cnt = f0;
+  c->fam_cnt.resize(c->fam_names.size(), 0);
+  c->timing = timing;
+  B.tuned = true;
+}
+
+void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
+  auto &B = c->bt;
+  const int n = c->P.n;
+  const long long nR = (long long)n * R;
+  const int bd = B.bd_elem;
+  const int *gate = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
+                                                  offsetof(PcgStateMR, all_done));
+  double *part = B.part64;
+  KL(c, "spmv_mr", c->stream, k_spmv_mr<double>, eblk(nR, bd), bd, 0, n, c->a_soff, c->a_sw, c->a_col,
+     c->a_val, B.P, B.Q, R, gate);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.P, B.Q, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_alpha, 1, 64, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_update, eblk(nR, bd), bd, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Rr, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_rr, 1, 64, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_true_res, eblk(nR, bd), bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
+     B.B, B.X, B.T);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_true_dec, 1, 64, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_copy_r, eblk(nR, bd), bd, 0, (long long)n, B.st, B.T, B.Rr);
+  precond_mr(c, B.Rr, B.Z, R, gate);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, flexible ? B.Zo : B.Z, part, gate);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_beta, 1, 64, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_p, eblk(nR, bd), bd, 0, (long long)n, B.st, B.Z, B.P, flexible ? B.Zo : (double *)nullptr);
+}
+
+// block PCG on B.B (device order, row-major, R columns) -> B.X
+void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info) {
+  auto &B = c->bt;
+  const int n = c->P.n;
+  const long long nR = (long long)n * R;
+  const int flexible = c->opt.precision == 1 ? 1 : 0;
+  const int *gate = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
+                                                  offsetof(PcgStateMR, all_done));
+  const char *ng = getenv("DDLR_NO_GRAPH");
+  const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+  cudaStream_t user = c->stream;
+  struct Restore {
+    ddlr_ctx *c; cudaStream_t s;
+    ~Restore() { c->stream = s; }
+  } restore{c, user};
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_fork, user), "event");
+    ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+    c->stream = c->gstream;
+  }
+  batch_autotune(c, R);
+  double *part = B.part64;
+  const int bd = B.bd_elem;
+  ck(cudaMemsetAsync(B.X, 0, sizeof(double) * nR, c->stream), "memset");
+  ck(cudaMemcpyAsync(B.Rr, B.B, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.B, B.B, (const double *)nullptr, part, (const int *)nullptr);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_init, 1, 64, 0, B.st, part, kRedGrid, R, tol, maxit, flexible);
+  precond_mr(c, B.Rr, B.Z, R, gate);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_rz0, 1, 64, 0, B.st, part, kRedGrid);
+  ck(cudaMemcpyAsync(B.P, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  ck(cudaMemcpyAsync(B.Zo, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  auto &GR = B.graphs[R];
+  if (use_graph && (GR.exec == nullptr || GR.flex != flexible)) {
+    if (GR.exec) { cudaGraphExecDestroy(GR.exec); GR.exec = nullptr; }
+    const long long l0 = c->launches;
+    const std::vector<long long> f0 = c->fam_cnt;
+    ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+    pcg_mr_iteration(c, R, flexible);
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamEndCapture(c->stream, &g), "capture");
+    cudaError_t e = cudaGraphInstantiate(&GR.exec, g, 0);
+    cudaGraphDestroy(g);
+    ck(e, "cudaGraphInstantiate");
+    GR.flex = flexible;
+    GR.nodes = c->launches - l0;
+    GR.fam_nodes.assign(c->fam_cnt.size(), 0);
+    for (size_t i = 0; i < c->fam_cnt.size(); i++)
+      GR.fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+    c->launches = l0;
+    for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+    for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+  }
+  const int batch = 4;
+  for (int it = 0; it < maxit + batch; it += batch) {
+    for (int bi = 0; bi < batch; bi++) {
+      if (use_graph) {
+        ck(cudaGraphLaunch(GR.exec, c->stream), "cudaGraphLaunch");
+        c->launches += GR.nodes;
+        for (size_t i = 0; i < GR.fam_nodes.size(); i++) c->fam_cnt[i] += GR.fam_nodes[i];
+      } else {
+        pcg_mr_iteration(c, R, flexible);
+      }
+    }
+    int done = 0;
+    ck(cudaMemcpyAsync(c->h_pin, gate, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    std::memcpy(&done, c->h_pin, sizeof(int));
+    if (done) break;
+  }
+  // true residuals
+  KL(c, "spmv_mr", c->stream, k_spmv_mr<double>, eblk(nR, bd), bd, 0, n, c->a_soff, c->a_sw, c->a_col,
+     c->a_val, B.X, B.Q, R, (const int *)nullptr);
+  KL(c, "pcg_mr", c->stream, k_sub_mr, eblk(nR, bd), bd, 0, nR, B.B, B.Q, B.T);
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part, (const int *)nullptr);
+  std::vector<double> hp(size_t(kRedGrid) * 2 * R);
+  PcgStateMR hs;
+  int dfl[4];
+  ck(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  ck(cudaMemcpyAsync(&hs, B.st, sizeof(PcgStateMR), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  ck(cudaMemcpyAsync(dfl, c->dflag, sizeof(dfl), cudaMemcpyDeviceToHost, c->stream), "D2H");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_join, c->stream), "event");
+    ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
+  }
+  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  for (int q = 0; q < R; q++) {
+    double rt2 = 0;
+    for (int g = 0; g < kRedGrid; g++) rt2 += hp[size_t(g) * 2 * R + q];   // fixed order
+    info[q].its = hs.its[q];
+    info[q].relres = hs.bb[q] > 0 ? std::sqrt(rt2 / hs.bb[q]) : 0.0;
+    info[q].status = hs.status[q] == 0 ? DDLR_OK : (hs.status[q] == 5 ? DDLR_ERR_NOCONV : DDLR_ERR_NAN);
+    if (!hs.done[q]) info[q].status = DDLR_ERR_NOCONV;
+  }
+}
+
+// a group of R columns of the caller's vectors (host or device, column-major,
+// original order) in and out of the batch layout
+void batch_load(ddlr_ctx *c, const double *x, int ld, int R, bool host, double *dst) {
+  const int n = c->P.n;
+  const double *src = x;
+  if (host) {
+    ck(cudaMemcpy2DAsync(c->bt.S, sizeof(double) * n, x, sizeof(double) * size_t(ld), sizeof(double) * n, R,
+                         cudaMemcpyHostToDevice, c->stream), "H2D");
+    src = c->bt.S;
+  }
+  KL(c, "perm", c->stream, k_batch_in, eblk((long long)n * R, 256), 256, 0, n, R, c->perm, src,
+     host ? (long long)n : (long long)ld, dst);
+}
+void batch_store(ddlr_ctx *c, const double *srcb, double *y, int ld, int R, bool host) {
+  const int n = c->P.n;
+  double *dst = host ? c->bt.S : y;
+  KL(c, "perm", c->stream, k_batch_out, eblk((long long)n * R, 256), 256, 0, n, R, c->perm, srcb, dst,
+     host ? (long long)n : (long long)ld);
+  if (host) {
+    ck(cudaMemcpy2DAsync(y, sizeof(double) * size_t(ld), c->bt.S, sizeof(double) * n, sizeof(double) * n, R,
+                         cudaMemcpyDeviceToHost, c->stream), "D2H");
+    sync(c);
+  }
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -912,6 +1280,20 @@ ddlr_status run_guarded(ddlr_ctx *c, const std::function<ddlr_status()> &f) {
 }
 
 }  // namespace
+
+// batched PCG of R host right-hand sides (column-major n x R, ld n) into host
+// x through the batched kernels (also for R = 1): the serving runtime's solve
+ddlr_status pcg_batched_host(ddlr_ctx *c, const double *b, double *x, int R, double tol, int maxit,
+                             ddlr_solve_info *info) {
+  return run_guarded(c, [&]() -> ddlr_status {
+    const int n = c->P.n;
+    batch_alloc(c, R);
+    batch_load(c, b, n, R, true, c->bt.B);
+    pcg_mr_dev(c, R, tol, maxit, info);
+    batch_store(c, c->bt.X, x, n, R, true);
+    return DDLR_OK;
+  });
+}
 
 extern "C" {
 
@@ -1015,6 +1397,23 @@ static ddlr_status vec_call(ddlr_ctx *c, const double *x, double *y, int nrhs, i
 }
 
 ddlr_status ddlr_apply(ddlr_handle c, const double *x, double *y, int nrhs, int ld) {
+  if (c && nrhs > 1 && batch_width(c) >= 2) {
+    const int n = c->P.n;
+    if (!x || !y || ld < n) { c->err = "invalid vector arguments"; return DDLR_ERR_INVALID; }
+    return run_guarded(c, [&]() -> ddlr_status {
+      const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
+      const int W = batch_width(c);
+      for (int j0 = 0; j0 < nrhs; j0 += W) {
+        const int R = std::min(W, nrhs - j0);
+        batch_alloc(c, R);
+        batch_autotune(c, R);
+        batch_load(c, x + size_t(j0) * ld, ld, R, hx, c->bt.Rr);
+        precond_mr(c, c->bt.Rr, c->bt.Z, R, nullptr);
+        batch_store(c, c->bt.Z, y + size_t(j0) * ld, ld, R, hy);
+      }
+      return DDLR_OK;
+    });
+  }
   return vec_call(c, x, y, nrhs, ld, [c](const double *xd, double *yd) {
     const int n = c->P.n;
     double *xi = c->pv[1], *yo = c->pv[2];
@@ -1046,6 +1445,30 @@ ddlr_status ddlr_pcg(ddlr_handle c, const double *b, double *x, int nrhs, int ld
   if (maxit <= 0) maxit = 500;
   if (!(tol > 0)) { c->err = "tol must be positive"; return DDLR_ERR_INVALID; }
   std::vector<ddlr_solve_info> inf(nrhs > 0 ? nrhs : 1);
+  if (nrhs > 1 && batch_width(c) >= 2) {
+    const int n = c->P.n;
+    if (!b || !x || ld < n) { c->err = "invalid vector arguments"; return DDLR_ERR_INVALID; }
+    ddlr_status st = run_guarded(c, [&]() -> ddlr_status {
+      const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
+      const int W = batch_width(c);
+      for (int j0 = 0; j0 < nrhs; j0 += W) {
+        const int R = std::min(W, nrhs - j0);
+        batch_alloc(c, R);
+        batch_load(c, b + size_t(j0) * ld, ld, R, hb, c->bt.B);
+        pcg_mr_dev(c, R, tol, maxit, inf.data() + j0);
+        batch_store(c, c->bt.X, x + size_t(j0) * ld, ld, R, hx);
+      }
+      return DDLR_OK;
+    });
+    if (st != DDLR_OK) return st;
+    ddlr_status agg = DDLR_OK;
+    for (int r = 0; r < nrhs; r++) {
+      if (info) info[r] = inf[r];
+      if (inf[r].status != DDLR_OK && agg == DDLR_OK) agg = (ddlr_status)inf[r].status;
+    }
+    if (agg != DDLR_OK) c->err = agg == DDLR_ERR_NOCONV ? "PCG did not converge" : "NaN/Inf in PCG";
+    return agg;
+  }
   int j = 0;
   ddlr_status st = vec_call(c, b, x, nrhs, ld, [&](const double *bd, double *xd) {
     const int n = c->P.n;
@@ -1080,6 +1503,8 @@ ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
   const double lr = double(c->urows) * c->opt.rank_k + (c->opt.variant == 2 ? double(c->opt.rank_k) * c->opt.rank_k : 0);
   info->fill_ratio = (double(P.nnz_factor) + double(P.nnz_ehat) + lr) / double(P.nnz);
   info->device_bytes = c->dev_bytes;
+  info->batch_block_chunks = c->bt.chunk_per;
+  info->batch_block_elem = c->bt.bd_elem;
   info->setup_ms = c->setup_ms;
   return DDLR_OK;
 }
@@ -1277,6 +1702,7 @@ ddlr_status ddlr_destroy(ddlr_handle c) {
   cudaStreamSynchronize(c->stream);
   c->resolve();
   for (auto e : c->evpool) cudaEventDestroy(e);
+  batch_free(c);
   c->release();
   if (c->h_pin) cudaFreeHost(c->h_pin);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);

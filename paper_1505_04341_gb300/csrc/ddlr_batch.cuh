@@ -1,0 +1,452 @@
+// ddlr_batch.cuh -- kernels of the batched (multi right-hand side) path.
+//
+// A block of R vectors is stored row-major in device order: X[r*R + q] is
+// row r of right-hand side q, so the R values of one row are contiguous and a
+// warp reads a row of 32 right-hand sides in one 128/256-byte transaction.
+// Every per-column quantity is computed with the same arithmetic whatever R is
+// and whichever other columns share the block: row-local work is identical,
+// and every reduction splits the rows into the same kRedGrid contiguous ranges,
+// sums each range in row order (eight interleaved partial sums combined in a
+// fixed tree), then sums the ranges in order.  A solve therefore gives the same
+// bits alone and inside a batch.
+#pragma once
+#include "ddlr_kernels.cuh"
+
+namespace ddlr {
+
+constexpr int kMaxR = 64;   // right-hand sides per batched launch
+
+// rows [r0, r1) of reduction range g out of G over nrows rows
+__device__ __forceinline__ void red_range(long long nrows, int g, int G, long long &r0, long long &r1) {
+  const long long chunk = (nrows + G - 1) / G;
+  r0 = (long long)g * chunk;
+  r1 = r0 + chunk < nrows ? r0 + chunk : nrows;
+  if (r0 > nrows) r0 = nrows;
+}
+
+// one dependency level of many blocks, R right-hand sides: CTA q solves chunk q;
+// thread -> (row sub-index, column); mode as k_sptrsv_chunks
+template <typename T>
+__global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
+                                   const T *lval, const T *uval, const T *dinv,
+                                   const T *X, T *Z, int R, const int *gate) {
+  if (gate && *gate) return;
+  const int4 ch = chunks[blockIdx.x];
+  const int lvl = ch.x, r0 = S.lvl_row0[lvl], s0 = S.lvl_slice0[lvl];
+  const int per = blockDim.x / R;
+  const int q = threadIdx.x % R, sub = threadIdx.x / R;
+  if (sub >= per) return;
+  const bool bwd = mode == 1;
+  const int *soff = bwd ? S.u_soff : S.l_soff;
+  const int *sw = bwd ? S.u_sw : S.l_sw;
+  const int *col = bwd ? S.u_col : S.l_col;
+  const T *val = bwd ? uval : lval;
+  for (int i = ch.y + sub; i < ch.y + ch.z; i += per) {
+    const int r = r0 + i, sl = s0 + (i >> 5), ln = i & 31;
+    const int off = soff[sl] + ln, w = sw[sl];
+    T acc = (bwd ? Z : X)[(long long)r * R + q];
+    for (int kk = 0; kk < w; kk++)
+      acc -= val[off + kk * 32] * Z[(long long)col[off + kk * 32] * R + q];
+    const T d = dinv[r];
+    acc *= d;
+    if (mode == 2) acc *= d;
+    Z[(long long)r * R + q] = acc;
+  }
+}
+
+// Y = E^T Z = a^-1 Ehat^T Z_B - a Z_C   (interface rows j, columns q)
+template <typename T>
+__global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,
+                        const T *eht_val, T ia, T a, const T *Z, T *Y, int R,
+                        const int *gate) {
+  if (gate && *gate) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long j = idx / R;
+  const int q = int(idx % R);
+  if (j >= s) return;
+  T acc = 0;
+  for (int p = eht_rp[j]; p < eht_rp[j + 1]; p++) acc += eht_val[p] * Z[(long long)eht_ci[p] * R + q];
+  Y[j * R + q] = ia * acc - a * Z[(m + j) * R + q];
+}
+
+// RHS_B = X_B + a^-1 Ehat W   (interior rows)
+template <typename T>
+__global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
+                                const T *eh_val, T ia, const T *W, const T *X, T *RHS,
+                                int R, const int *gate) {
+  if (gate && *gate) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r = idx / R;
+  const int q = int(idx % R);
+  if (r >= m) return;
+  T acc = 0;
+  for (int p = eh_rp[r]; p < eh_rp[r + 1]; p++) acc += eh_val[p] * W[(long long)eh_ci[p] * R + q];
+  RHS[r * R + q] = X[r * R + q] + ia * acc;
+}
+
+// partials[g][c*R + q] = sum over rows of range g (in order) of U[row][c] Y[row][q]
+// (stage 1 of U_k^T Y, k x R).  Needs k*R <= 4 * blockDim.
+template <typename T, typename TU>
+__global__ void __launch_bounds__(256)
+k_utx_mr_partial(long long nrows, int k, const TU *U, const T *Y, int R, T *partials,
+                 const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T us[32 * 64];
+  __shared__ T ys[32 * kMaxR];
+  long long r0, r1;
+  red_range(nrows, blockIdx.x, gridDim.x, r0, r1);
+  const int no = k * R;
+  T acc[4] = {0, 0, 0, 0};
+  for (long long base = r0; base < r1; base += 32) {
+    const int nt = int(min(32LL, r1 - base));
+    for (int t = threadIdx.x; t < nt * k; t += blockDim.x)
+      us[t] = T(to_acc(U[(base + t / k) * k + t % k]));
+    for (int t = threadIdx.x; t < nt * R; t += blockDim.x) ys[t] = Y[base * R + t];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int o = threadIdx.x + u * blockDim.x;
+      if (o < no) {
+        const int c = o / R, q = o % R;
+        T a = acc[u];
+        for (int rr = 0; rr < nt; rr++) a += us[rr * k + c] * ys[rr * R + q];
+        acc[u] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int o = threadIdx.x + u * blockDim.x;
+    if (o < no) partials[(long long)blockIdx.x * no + o] = acc[u];
+  }
+}
+
+// T[o] = coef[o / R] * sum_g partials[g][o] (o = c*R + q), fixed order; with H:
+// T = H * (that k x R block).  One CTA; k*R <= 1024.
+template <typename T>
+__global__ void k_reduce_mr(int G, int k, int R, const T *partials, const T *coef,
+                            const T *H, T *out, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T tmp[1024];
+  const int no = k * R;
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    T s = 0;
+    for (int g = 0; g < G; g++) s += partials[(long long)g * no + o];
+    tmp[o] = coef ? coef[o / R] * s : s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    if (H) {
+      const int c = o / R, q = o % R;
+      T s = 0;
+      for (int b = 0; b < k; b++) s += H[c * k + b] * tmp[b * R + q];
+      out[o] = s;
+    } else {
+      out[o] = tmp[o];
+    }
+  }
+}
+
+// W = Y/(1-theta) + U_k Tm ; RHS_C = X_C - a W   (interface rows, DDLR-1)
+template <typename T, typename TU>
+__global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const T *Y,
+                           const T *inv1mt, T a, const T *X, T *W, T *RHS, int R,
+                           const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T ts[1024];
+  for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = Tm[o];
+  __syncthreads();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long j = idx / R;
+  const int q = int(idx % R);
+  if (j >= s) return;
+  const TU *u = U + j * k;
+  T acc = 0;
+  for (int c = 0; c < k; c++) acc += T(to_acc(u[c])) * ts[c * R + q];
+  const T wj = (*inv1mt) * Y[j * R + q] + acc;
+  W[j * R + q] = wj;
+  RHS[(m + j) * R + q] = X[(m + j) * R + q] - a * wj;
+}
+
+// Uo += U_k HT   (DDLR-2, all rows)
+template <typename T, typename TU>
+__global__ void k_u_add_mr(long long nrows, int k, const TU *U, const T *HT, T *Uo, int R,
+                           const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T ts[1024];
+  for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = HT[o];
+  __syncthreads();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r = idx / R;
+  const int q = int(idx % R);
+  if (r >= nrows) return;
+  const TU *u = U + r * k;
+  T acc = 0;
+  for (int c = 0; c < k; c++) acc += T(to_acc(u[c])) * ts[c * R + q];
+  Uo[r * R + q] += acc;
+}
+
+// Q = A P (sliced ELL, device order), R columns
+template <typename T>
+__global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
+                          const T *val, const T *P, T *Q, int R, const int *gate) {
+  if (gate && *gate) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r = idx / R;
+  const int q = int(idx % R);
+  if (r >= n) return;
+  const int g = int(r >> 5), l = int(r & 31);
+  const int off = soff[g] + l, w = sw[g];
+  T acc = 0;
+  for (int kk = 0; kk < w; kk++) acc += val[off + kk * 32] * P[(long long)col[off + kk * 32] * R + q];
+  Q[r * R + q] = acc;
+}
+
+// partials[g][q] (and [g][R+q]) = column dot products of A.B (and A.C) over
+// range g of the rows.  The range is cut into 8 equal sub-ranges, one warp
+// each; a lane sums its column over the sub-range in row order with eight
+// interleaved partial sums (fixed tree), and the 8 sub-range sums are added in
+// order.  Launch with 256 threads; lanes q >= R idle.
+__global__ void __launch_bounds__(256)
+k_dot_mr_partial(long long n, int R, const double *A, const double *B,
+                 const double *C, double *partials, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ double red[8][2 * kMaxR];
+  const int w = threadIdx.x >> 5, q = threadIdx.x & 31;
+  long long g0, g1;
+  red_range(n, blockIdx.x, gridDim.x, g0, g1);
+  const long long sub = (g1 - g0 + 7) / 8;
+  for (int qq = q; qq < R; qq += 32) {
+    long long r0 = g0 + w * sub, r1 = r0 + sub;
+    if (r0 > g1) r0 = g1;
+    if (r1 > g1) r1 = g1;
+    double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long r = r0;
+    for (; r + 8 <= r1; r += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const double a = A[(r + u) * R + qq];
+        s8[u] = fma(a, B[(r + u) * R + qq], s8[u]);
+        if (C) t8[u] = fma(a, C[(r + u) * R + qq], t8[u]);
+      }
+    }
+    for (int u = 0; r < r1; r++, u++) {
+      const double a = A[r * R + qq];
+      s8[u] = fma(a, B[r * R + qq], s8[u]);
+      if (C) t8[u] = fma(a, C[r * R + qq], t8[u]);
+    }
+    red[w][qq] = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+    red[w][R + qq] = ((t8[0] + t8[1]) + (t8[2] + t8[3])) + ((t8[4] + t8[5]) + (t8[6] + t8[7]));
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < (C ? 2 * R : R); o += blockDim.x) {
+    double sm = 0;
+    for (int ww = 0; ww < 8; ww++) sm += red[ww][o];
+    partials[(long long)blockIdx.x * 2 * R + o] = sm;
+  }
+}
+
+// ------------------------------------------------------- block PCG control
+struct PcgStateMR {
+  double rz[kMaxR], pq[kMaxR], alpha[kMaxR], beta[kMaxR], rr[kMaxR], bb[kMaxR];
+  double tol2[kMaxR], rt2[kMaxR];
+  int its[kMaxR], done[kMaxR], status[kMaxR], check[kMaxR], restart[kMaxR];
+  int R, maxit, flexible, all_done, any_check, pad[3];
+};
+
+__device__ __forceinline__ double col_sum(const double *partials, int G, int R, int off) {
+  double s = 0;
+  for (int g = 0; g < G; g++) s += partials[(long long)g * 2 * R + off];
+  return s;
+}
+
+__global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int R,
+                             double tol, int maxit, int flexible) {
+  const int q = threadIdx.x;
+  if (q == 0) {
+    st->R = R; st->maxit = maxit; st->flexible = flexible; st->any_check = 0;
+  }
+  if (q < R) {
+    const double bb = col_sum(partials, G, R, q);
+    st->bb[q] = bb;
+    st->tol2[q] = tol * tol * bb;
+    st->its[q] = 0; st->status[q] = 0; st->check[q] = 0; st->restart[q] = 0;
+    st->done[q] = (bb == 0.0) ? 1 : 0;
+    st->rz[q] = 0;
+  }
+  __syncthreads();
+  if (q == 0) {
+    int all = 1;
+    for (int c = 0; c < R; c++) all &= st->done[c];
+    st->all_done = all;
+  }
+}
+
+__global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
+  if (st->all_done) return;
+  const int q = threadIdx.x, R = st->R;
+  if (q < R && !st->done[q]) {
+    const double s = col_sum(partials, G, R, q);
+    st->rz[q] = s;
+    if (!(s == s) || isinf(s)) { st->status[q] = 7; st->done[q] = 1; }
+  }
+}
+
+__global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
+  if (st->all_done) return;
+  const int q = threadIdx.x, R = st->R;
+  if (q < R) {
+    double a = 0.0;
+    if (!st->done[q]) {
+      const double pq = col_sum(partials, G, R, q);
+      st->pq[q] = pq;
+      a = st->rz[q] / pq;
+      if (!(a == a) || isinf(a)) { st->status[q] = 7; st->done[q] = 1; a = 0.0; }
+    }
+    st->alpha[q] = a;
+  }
+}
+
+// X += alpha P; Rr -= alpha Q for the columns still running
+__global__ void k_pcgmr_update(long long n, const PcgStateMR *st, const double *P,
+                               const double *Q, double *X, double *Rr) {
+  if (st->all_done) return;
+  const int R = st->R;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R) return;
+  const int q = int(idx % R);
+  if (st->done[q]) return;
+  const double a = st->alpha[q];
+  X[idx] += a * P[idx];
+  Rr[idx] -= a * Q[idx];
+}
+
+__global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
+  if (st->all_done) return;
+  const int q = threadIdx.x, R = st->R;
+  __shared__ int anyc;
+  if (q == 0) anyc = 0;
+  __syncthreads();
+  if (q < R && !st->done[q]) {
+    const double rr = col_sum(partials, G, R, q);
+    st->rr[q] = rr;
+    st->its[q] += 1;
+    if (!(rr == rr) || isinf(rr)) { st->status[q] = 7; st->done[q] = 1; }
+    else {
+      st->check[q] = (rr <= st->tol2[q]) ? 1 : 0;
+      if (st->check[q]) atomicOr(&anyc, 1);
+      else if (st->its[q] >= st->maxit) { st->status[q] = 5; st->done[q] = 1; }
+    }
+  }
+  __syncthreads();
+  if (q == 0) st->any_check = anyc;
+}
+
+// T = B - A X for the columns whose true residual is to be checked
+__global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, const int *sw,
+                                 const int *col, const double *val, const double *B,
+                                 const double *X, double *Tt) {
+  if (st->all_done || !st->any_check) return;
+  const int R = st->R;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r = idx / R;
+  const int q = int(idx % R);
+  if (r >= n || !st->check[q]) return;
+  const int g = int(r >> 5), l = int(r & 31);
+  const int off = soff[g] + l, w = sw[g];
+  double ax = 0;
+  for (int kk = 0; kk < w; kk++) ax += val[off + kk * 32] * X[(long long)col[off + kk * 32] * R + q];
+  Tt[idx] = B[idx] - ax;
+}
+
+__global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) {
+  if (st->all_done || !st->any_check) return;
+  const int q = threadIdx.x, R = st->R;
+  if (q < R && st->check[q] && !st->done[q]) {
+    const double rt2 = col_sum(partials, G, R, q);
+    st->rt2[q] = rt2;
+    if (rt2 <= st->tol2[q]) { st->status[q] = 0; st->done[q] = 1; }
+    else {
+      st->restart[q] = 1;
+      if (st->its[q] >= st->maxit) { st->status[q] = 5; st->done[q] = 1; }
+    }
+  }
+  if (q < R) st->check[q] = 0;
+}
+
+__global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *Tt, double *Rr) {
+  if (st->all_done) return;
+  const int R = st->R;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R) return;
+  const int q = int(idx % R);
+  if (st->restart[q] && !st->done[q]) Rr[idx] = Tt[idx];
+}
+
+__global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
+  if (st->all_done) return;
+  const int q = threadIdx.x, R = st->R;
+  if (q < R && !st->done[q]) {
+    const double rzn = col_sum(partials, G, R, q);
+    const double rzo = col_sum(partials, G, R, R + q);
+    double beta = st->flexible ? (rzn - rzo) / st->rz[q] : rzn / st->rz[q];
+    if (st->restart[q]) beta = 0.0;
+    st->beta[q] = beta;
+    st->rz[q] = rzn;
+    st->restart[q] = 0;
+    if (!(rzn == rzn) || isinf(rzn)) { st->status[q] = 7; st->done[q] = 1; }
+  }
+  __syncthreads();
+  if (q == 0) {
+    int all = 1;
+    for (int c = 0; c < R; c++) all &= st->done[c];
+    st->all_done = all;
+  }
+}
+
+// P = Z + beta P (and Zold = Z) for the columns still running
+__global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, double *P,
+                          double *Zold) {
+  const int R = st->R;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R) return;
+  const int q = int(idx % R);
+  if (st->done[q]) return;
+  const double z = Z[idx];
+  P[idx] = z + st->beta[q] * P[idx];
+  if (Zold) Zold[idx] = z;
+}
+
+// Tt = B - Q (all columns)
+__global__ void k_sub_mr(long long cnt, const double *B, const double *Q, double *Tt) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < cnt) Tt[idx] = B[idx] - Q[idx];
+}
+
+// gather/scatter between caller layout (column-major, original order, ld) and
+// the batch layout (row-major, device order); optional row scaling
+__global__ void k_batch_in(int n, int R, const int *perm, const double *in, long long ld,
+                           double *out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * R) return;
+  const long long g = idx / R;
+  const int q = int(idx % R);
+  out[idx] = in[q * ld + perm[g]];
+}
+__global__ void k_batch_out(int n, int R, const int *perm, const double *in, double *out,
+                            long long ld) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * R) return;
+  const long long g = idx / R;
+  const int q = int(idx % R);
+  out[q * ld + perm[g]] = in[idx];
+}
+__global__ void k_scale_rows_mr(long long n, int R, const double *d, const double *in,
+                                double *out, const int *gate) {
+  if (gate && *gate) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * R) out[idx] = in[idx] * d[idx / R];
+}
+
+}  // namespace ddlr

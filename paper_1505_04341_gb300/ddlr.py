@@ -46,12 +46,19 @@ class ddlr_info(ctypes.Structure):
                 ("lambda_max", ctypes.c_double), ("nnz_a", ctypes.c_longlong),
                 ("nnz_factor", ctypes.c_longlong), ("nnz_ehat", ctypes.c_longlong),
                 ("fill_ratio", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
-                ("setup_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("batch_block_chunks", ctypes.c_int),
+                ("batch_block_elem", ctypes.c_int)]
 
 
 class ddlr_solve_info(ctypes.Structure):
     _fields_ = [("its", ctypes.c_int), ("relres", ctypes.c_double),
                 ("status", ctypes.c_int)]
+
+
+class ddlr_server_options(ctypes.Structure):
+    _fields_ = [("max_concurrent", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("memory_fraction", ctypes.c_double)]
 
 
 # every entry point declared in include/ddlr.h
@@ -60,7 +67,9 @@ EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
            "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
-           "ddlr_destroy"]
+           "ddlr_destroy", "ddlr_server_options_default", "ddlr_server_create",
+           "ddlr_server_add_model", "ddlr_server_submit", "ddlr_server_wait",
+           "ddlr_server_stats", "ddlr_server_last_error", "ddlr_server_destroy"]
 
 _lib = None
 
@@ -98,6 +107,17 @@ def load(path: str | None = None):
         "ddlr_set_stream": ([P, P], I),
         "ddlr_last_error": ([P], ctypes.c_char_p),
         "ddlr_destroy": ([P], I),
+        "ddlr_server_options_default": ([ctypes.POINTER(ddlr_server_options)], I),
+        "ddlr_server_create": ([ctypes.POINTER(ddlr_server_options), ctypes.POINTER(P)], I),
+        "ddlr_server_add_model": ([P, I, P, P, P, P, I, ctypes.POINTER(ddlr_options),
+                                   ctypes.POINTER(I)], I),
+        "ddlr_server_submit": ([P, I, P, ctypes.POINTER(LL)], I),
+        "ddlr_server_wait": ([P, LL, D, P, ctypes.POINTER(ddlr_solve_info),
+                              ctypes.POINTER(D), ctypes.POINTER(I)], I),
+        "ddlr_server_stats": ([P, ctypes.POINTER(LL), ctypes.POINTER(I), ctypes.POINTER(I),
+                               ctypes.POINTER(I)], I),
+        "ddlr_server_last_error": ([P], ctypes.c_char_p),
+        "ddlr_server_destroy": ([P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -301,3 +321,70 @@ class DDLR:
         names = list(self.counters()["families"].keys())
         return dict(apply_bytes=a.value, a0_bytes=b.value,
                     family_bytes={nm: float(fam[i]) for i, nm in enumerate(names)})
+
+
+class Server:
+    """Solve service (include/ddlr.h, serving section): resident models,
+    continuous batching across requests, admission by device memory."""
+
+    def __init__(self, max_concurrent=4, max_batch=16, tol=1e-8, maxit=500,
+                 memory_fraction=0.9):
+        lib = load()
+        o = ddlr_server_options()
+        lib.ddlr_server_options_default(ctypes.byref(o))
+        o.max_concurrent, o.max_batch, o.tol, o.maxit, o.memory_fraction = (
+            max_concurrent, max_batch, tol, maxit, memory_fraction)
+        h = ctypes.c_void_p()
+        st = lib.ddlr_server_create(ctypes.byref(o), ctypes.byref(h))
+        if st != 0:
+            raise DdlrError(st, "server_create")
+        self._h = h
+        self._n = []
+
+    def _err(self, st):
+        if st != 0:
+            raise DdlrError(st, _lib.ddlr_server_last_error(self._h).decode())
+
+    def add_model(self, A, part, p, **opts) -> int:
+        n, rp, ci, va = A
+        arrs = [np.ascontiguousarray(rp, dtype=np.int32), np.ascontiguousarray(ci, dtype=np.int32),
+                np.ascontiguousarray(va, dtype=np.float64), np.ascontiguousarray(part, dtype=np.int32)]
+        o = options(**opts)
+        m = ctypes.c_int()
+        self._err(_lib.ddlr_server_add_model(self._h, int(n), *[_np_ptr(a) for a in arrs], int(p),
+                                             ctypes.byref(o), ctypes.byref(m)))
+        self._n.append(int(n))
+        return m.value
+
+    def submit(self, model, b) -> int:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        rid = ctypes.c_longlong()
+        self._err(_lib.ddlr_server_submit(self._h, int(model), _np_ptr(b), ctypes.byref(rid)))
+        return rid.value
+
+    def wait(self, request, n, timeout=0.0):
+        """Returns (x, info dict, latency seconds, batch width)."""
+        x = np.empty(n)
+        info = ddlr_solve_info()
+        lat = ctypes.c_double()
+        bw = ctypes.c_int()
+        st = _lib.ddlr_server_wait(self._h, int(request), float(timeout), _np_ptr(x),
+                                   ctypes.byref(info), ctypes.byref(lat), ctypes.byref(bw))
+        if st not in (0, 5, 7):
+            self._err(st)
+        return x, dict(its=info.its, relres=info.relres, status=STATUS[info.status]), lat.value, bw.value
+
+    def stats(self) -> dict:
+        c = ctypes.c_longlong()
+        mb, mi, nm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._err(_lib.ddlr_server_stats(self._h, ctypes.byref(c), ctypes.byref(mb), ctypes.byref(mi),
+                                         ctypes.byref(nm)))
+        return dict(completed=c.value, max_batch_seen=mb.value, max_inflight_seen=mi.value,
+                    models=nm.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.ddlr_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
