@@ -17,8 +17,8 @@
 #include "ddlr_plan.h"
 
 #include <algorithm>
+#include <array>
 #include <numeric>
-#include <unordered_map>
 
 namespace ddlr {
 
@@ -84,68 +84,82 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   const bool exact = opt.factor == 1;
   P.perm.resize(n); P.iperm.resize(n);
   P.blk_row0.assign(p + 2, 0);
-  // per block: device-ordered list of original rows, and each row's level
+  // per node: level in its block's factor; lower factor pattern per device
+  // row as device-order columns (flat CSR, filled block by block)
   std::vector<int> level_of(n, 0);
-  // lower factor pattern per original row, as original column indices
-  std::vector<std::vector<int>> lower(n);
+  std::vector<int> low_rp(n + 1, 0), low_ci;
+  low_ci.reserve(size_t(nnz));
   int row_w = 0;
+  std::vector<int> loc(n, -1);   // index of a node inside its own block
+  for (int b = 0; b <= p; b++)
+    for (int t = 0; t < int(members[b].size()); t++) loc[members[b][t]] = t;
+  std::vector<int> arp, aci, ord, epos, lrp, lci, lev, dev, col, used, cnt;
   for (int b = 0; b <= p; b++) {
     const std::vector<int> &mem = members[b];
     const int nb = int(mem.size());
     P.blk_row0[b] = row_w;
-    std::unordered_map<int, int> loc;
-    loc.reserve(size_t(nb) * 2 + 1);
-    for (int t = 0; t < nb; t++) loc[mem[t]] = t;
-    // block graph (local indices): A restricted to the block, plus, for
-    // interior blocks, the pattern of Ehat Ehat^T
-    std::vector<std::vector<int>> adj(nb);
+    // block graph (local indices, flat CSR): A restricted to the block, plus,
+    // for interior blocks, the pattern of Ehat Ehat^T
+    arp.assign(nb + 1, 0);
+    aci.clear();
     for (int t = 0; t < nb; t++) {
-      int i = mem[t];
+      const int i = mem[t];
+      const size_t a0 = aci.size();
       for (int q = rp[i]; q < rp[i + 1]; q++) {
-        int j = ci[q];
-        if (j != i && blk_of[j] == b) adj[t].push_back(loc[j]);
+        const int j = ci[q];
+        if (j != i && blk_of[j] == b) aci.push_back(loc[j]);
         if (b < p && iface[j]) {
           for (int q2 = rp[j]; q2 < rp[j + 1]; q2++) {
-            int r = ci[q2];
+            const int r = ci[q2];
             if (r != i && !iface[r]) {
               if (blk_of[r] != b) { err = "Ehat Ehat^T couples two subdomains"; return DDLR_ERR_INVALID; }
-              adj[t].push_back(loc[r]);
+              aci.push_back(loc[r]);
             }
           }
         }
       }
-      std::sort(adj[t].begin(), adj[t].end());
-      adj[t].erase(std::unique(adj[t].begin(), adj[t].end()), adj[t].end());
+      std::sort(aci.begin() + a0, aci.end());
+      aci.erase(std::unique(aci.begin() + a0, aci.end()), aci.end());
+      arp[t + 1] = int(aci.size());
     }
     // elimination order
-    std::vector<int> ord(nb), epos(nb);
+    ord.resize(nb);
+    epos.resize(nb);
     std::iota(ord.begin(), ord.end(), 0);
     if ((b == p && opt.c_order == 1) || (b < p && opt.b_order == 1)) {
-      std::vector<int> col(nb, -1), used(nb + 2, -1);
+      col.assign(nb, -1);
+      used.assign(nb + 2, -1);
       int nc = 0;
       for (int t = 0; t < nb; t++) {
-        for (int u : adj[t]) if (u < t) used[col[u]] = t;
+        for (int q = arp[t]; q < arp[t + 1]; q++) if (aci[q] < t) used[col[aci[q]]] = t;
         int c = 0;
         while (used[c] == t) c++;
         col[t] = c;
         nc = std::max(nc, c + 1);
       }
       if (b == p) P.ncolors = nc;
-      std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return col[a] < col[c]; });
+      // stable counting sort by colour
+      cnt.assign(nc + 1, 0);
+      for (int t = 0; t < nb; t++) cnt[col[t] + 1]++;
+      for (int c = 0; c < nc; c++) cnt[c + 1] += cnt[c];
+      for (int t = 0; t < nb; t++) ord[cnt[col[t]]++] = t;
     }
     for (int e = 0; e < nb; e++) epos[ord[e]] = e;
-    // lower pattern in elimination positions
-    std::vector<std::vector<int>> low(nb);
+    // lower pattern in elimination positions (flat CSR lrp/lci)
+    lrp.assign(nb + 1, 0);
+    lci.clear();
     for (int e = 0; e < nb; e++) {
-      int t = ord[e];
-      for (int u : adj[t]) if (epos[u] < e) low[e].push_back(epos[u]);
-      std::sort(low[e].begin(), low[e].end());
+      const int t = ord[e];
+      const size_t l0 = lci.size();
+      for (int q = arp[t]; q < arp[t + 1]; q++) if (epos[aci[q]] < e) lci.push_back(epos[aci[q]]);
+      std::sort(lci.begin() + l0, lci.end());
+      lrp[e + 1] = int(lci.size());
     }
     if (exact) {
       // symbolic Cholesky: struct(L_{*j}) = struct(A_{*j}) U struct of the
       // children of j in the elimination tree, minus j
       std::vector<std::vector<int>> cols(nb);
-      for (int e = 0; e < nb; e++) for (int f : low[e]) cols[f].push_back(e);
+      for (int e = 0; e < nb; e++) for (int q = lrp[e]; q < lrp[e + 1]; q++) cols[lci[q]].push_back(e);
       long long total = 0;
       for (int j = 0; j < nb; j++) {
         std::vector<int> &c = cols[j];
@@ -158,31 +172,39 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
           for (size_t t = 1; t < c.size(); t++) cols[par].push_back(c[t]);
         }
       }
-      for (int e = 0; e < nb; e++) low[e].clear();
-      for (int j = 0; j < nb; j++) for (int e : cols[j]) low[e].push_back(j);
+      std::vector<int> rc(nb + 1, 0);
+      for (int j = 0; j < nb; j++) for (int e : cols[j]) rc[e + 1]++;
+      for (int e = 0; e < nb; e++) rc[e + 1] += rc[e];
+      lrp = rc;
+      lci.assign(rc[nb], 0);
+      for (int j = 0; j < nb; j++) for (int e : cols[j]) lci[rc[e]++] = j;   // ascending j per row
     }
     // levels
-    std::vector<int> lev(nb, 0);
+    lev.assign(nb, 0);
     int maxlev = 0;
     for (int e = 0; e < nb; e++) {
       int l = 0;
-      for (int f : low[e]) l = std::max(l, lev[f] + 1);
+      for (int q = lrp[e]; q < lrp[e + 1]; q++) l = std::max(l, lev[lci[q]] + 1);
       lev[e] = l;
       maxlev = std::max(maxlev, l);
     }
     if (b < p) P.levels_interior = std::max(P.levels_interior, nb ? maxlev + 1 : 0);
     else P.levels_c = maxlev + 1;
-    // device order: (level, elimination position)
-    std::vector<int> dev(nb);
-    std::iota(dev.begin(), dev.end(), 0);
-    std::stable_sort(dev.begin(), dev.end(), [&](int a, int c) { return lev[a] < lev[c]; });
+    // device order: (level, elimination position), stable counting sort
+    cnt.assign(maxlev + 2, 0);
+    for (int e = 0; e < nb; e++) cnt[lev[e] + 1]++;
+    for (int l = 0; l <= maxlev; l++) cnt[l + 1] += cnt[l];
+    dev.resize(nb);
+    for (int e = 0; e < nb; e++) dev[cnt[lev[e]]++] = e;
+    std::vector<int> drow(nb);   // elimination position -> device row
+    for (int d = 0; d < nb; d++) drow[dev[d]] = row_w + d;
     for (int d = 0; d < nb; d++) {
-      int e = dev[d];
-      int i = mem[ord[e]];
+      const int e = dev[d];
+      const int i = mem[ord[e]];
       P.perm[row_w + d] = i;
       level_of[i] = lev[e];
-      lower[i].clear();
-      for (int f : low[e]) lower[i].push_back(mem[ord[f]]);
+      for (int q = lrp[e]; q < lrp[e + 1]; q++) low_ci.push_back(drow[lci[q]]);
+      low_rp[row_w + d + 1] = int(low_ci.size());
     }
     row_w += nb;
   }
@@ -207,11 +229,12 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     }
     P.a_col.assign(P.a_soff[ns], 0);
     P.a_src.assign(P.a_soff[ns], -1);
+    std::vector<std::pair<int, int>> ent;
     for (int g = 0; g < ns; g++)
       for (int l = 0; l < kSlice; l++) {
         int r = g * kSlice + l;
         int rr = r < n ? r : n - 1;
-        std::vector<std::pair<int, int>> ent;
+        ent.clear();
         if (r < n) {
           int i = P.perm[r];
           for (int q = rp[i]; q < rp[i + 1]; q++) ent.push_back({P.iperm[ci[q]], q});
@@ -250,37 +273,40 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
 
   // ---- factor pattern in device order with value sources
   P.f_rp.assign(n + 1, 0);
+  {
+    const size_t nf_est = low_ci.size() + size_t(n);
+    P.f_ci.reserve(nf_est); P.f_row.reserve(nf_est); P.f_src.reserve(nf_est);
+    P.f_prp.reserve(nf_est + 1); P.f_cdiag.reserve(nf_est);
+  }
   P.f_prp.push_back(0);
-  const double a2unused = 0.0; (void)a2unused;
+  std::vector<std::array<int, 3>> pairs;
+  std::vector<int> cols;
   for (int g = 0; g < n; g++) {
-    int i = P.perm[g];
-    int b = blk_of[i];
-    std::vector<int> cols;
-    for (int j : lower[i]) cols.push_back(P.iperm[j]);
+    const int i = P.perm[g];
+    const int b = blk_of[i];
+    cols.assign(low_ci.begin() + low_rp[g], low_ci.begin() + low_rp[g + 1]);
     cols.push_back(g);
     std::sort(cols.begin(), cols.end());
-    // Ehat Ehat^T contributions of row i: map original column -> pairs
-    std::unordered_map<int, std::vector<std::pair<int, int>>> pairs;
+    // Ehat Ehat^T contributions of row i: (original column, pa, pb)
+    pairs.clear();
     if (b < p) {
       for (int q = rp[i]; q < rp[i + 1]; q++) {
-        int j = ci[q];
+        const int j = ci[q];
         if (!iface[j]) continue;
         for (int q2 = rp[j]; q2 < rp[j + 1]; q2++) {
-          int r = ci[q2];
+          const int r = ci[q2];
           if (iface[r]) continue;
-          int pr = find_pos(rp, ci, r, j);
-          pairs[r].push_back({q, pr});
+          pairs.push_back({r, q, find_pos(rp, ci, r, j)});
         }
       }
     }
     for (int c : cols) {
-      int j = P.perm[c];
+      const int j = P.perm[c];
       P.f_ci.push_back(c);
       P.f_row.push_back(g);
       P.f_src.push_back(find_pos(rp, ci, i, j));
-      auto it = pairs.find(j);
-      if (it != pairs.end())
-        for (auto &pr : it->second) { P.f_pa.push_back(pr.first); P.f_pb.push_back(pr.second); }
+      for (const auto &pr : pairs)
+        if (pr[0] == j) { P.f_pa.push_back(pr[1]); P.f_pb.push_back(pr[2]); }
       P.f_prp.push_back(int(P.f_pa.size()));
       P.f_cdiag.push_back((b == p && c == g) ? 1 : 0);
     }
@@ -321,10 +347,20 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       P.fl_ptr[L + 1] = int(P.fl_rows.size());
     }
   }
-  // upper (L^T) rows: for device row c, the factor entries (g, c), g != c
-  std::vector<std::vector<int>> upper(n);   // factor entry indices
+  // upper (L^T) rows: for device row c, the factor entries (g, c), g != c,
+  // in ascending g (flat CSR up_rp / up_q)
+  std::vector<int> up_rp(n + 1, 0), up_q;
   for (int g = 0; g < n; g++)
-    for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) upper[P.f_ci[q]].push_back(q);
+    for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_rp[P.f_ci[q] + 1]++;
+  for (int c = 0; c < n; c++) up_rp[c + 1] += up_rp[c];
+  up_q.assign(up_rp[n], 0);
+  {
+    std::vector<int> fill(up_rp.begin(), up_rp.end() - 1);
+    for (int g = 0; g < n; g++)
+      for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_q[fill[P.f_ci[q]]++] = q;
+  }
+  auto upper_size = [&](int r) { return up_rp[r + 1] - up_rp[r]; };
+  auto upper_at = [&](int r, int kk) { return up_q[up_rp[r] + kk]; };
   P.l_soff.assign(P.nslice + 1, 0); P.l_sw.assign(P.nslice, 0);
   P.u_soff.assign(P.nslice + 1, 0); P.u_sw.assign(P.nslice, 0);
   std::vector<int> slice_row0(P.nslice), slice_rows(P.nslice), slice_blk(P.nslice);
@@ -341,7 +377,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     for (int t = 0; t < slice_rows[g]; t++) {
       int r = slice_row0[g] + t;
       wl = std::max(wl, P.f_rp[r + 1] - P.f_rp[r] - 1);
-      wu = std::max(wu, int(upper[r].size()));
+      wu = std::max(wu, upper_size(r));
     }
     P.l_sw[g] = wl; P.u_sw[g] = wu;
     P.l_soff[g + 1] = P.l_soff[g] + wl * kSlice;
@@ -363,10 +399,10 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         if (kk < nl) { int q = P.f_rp[r] + kk; P.l_col[slot] = P.f_ci[q]; P.map_l[q] = slot; }
         else P.l_col[slot] = first;   // level-0 row: final before any use
       }
-      int nu = live ? int(upper[r].size()) : 0;
+      int nu = live ? upper_size(r) : 0;
       for (int kk = 0; kk < P.u_sw[g]; kk++) {
         int slot = P.u_soff[g] + kk * kSlice + t;
-        if (kk < nu) { int q = upper[r][kk]; P.u_col[slot] = P.f_row[q]; P.map_u[q] = slot; }
+        if (kk < nu) { int q = upper_at(r, kk); P.u_col[slot] = P.f_row[q]; P.map_u[q] = slot; }
         else P.u_col[slot] = last;    // top-level row: final before any use
       }
     }
@@ -407,7 +443,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     P.l_span[2 * g] = P.l_soff[sl] + ln;
     P.l_span[2 * g + 1] = P.f_rp[g + 1] - P.f_rp[g] - 1;
     P.u_span[2 * g] = P.u_soff[sl] + ln;
-    P.u_span[2 * g + 1] = int(upper[g].size());
+    P.u_span[2 * g + 1] = upper_size(g);
   }
   for (int b = 0; b < p; b++) {
     const int l0 = P.blk_lvl0[b], l1 = P.blk_lvl0[b + 1];
