@@ -67,6 +67,8 @@ struct ddlr_ctx {
   int pcg_exec_flexible = -1;
   long long pcg_nodes = 0;
   std::vector<long long> pcg_fam_nodes;
+  long long lz_nodes = 0;
+  std::vector<long long> lz_fam_nodes;
   // batched (multi right-hand side) path
   struct Batch {
     int R = 0;
@@ -409,42 +411,6 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
 }
 
 // ------------------------------------------------------------- Lanczos
-// Lanczos operator (Sec. 4.4): DDLR-1 w = E^T A0^-1 E q; DDLR-2 E^T A0^-2 E q.
-void lanczos_op(ddlr_ctx *c, const double *q, double *w) {
-  const Plan &P = c->P;
-  const int n = P.n, m = P.m, s = P.s;
-  const double a = c->opt.alpha, ia = 1.0 / a;
-  double *v = c->w64[0], *z = c->w64[1];
-  KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0,
-     m, s, c->eh_rp, c->eh_ci, c->eh64, ia, a, q, (const double *)nullptr, v, (const int *)nullptr);
-  a0_solve<double>(c, v, z, nullptr);
-  if (c->opt.variant == 2) {
-    a0_solve<double>(c, z, v, nullptr);
-    std::swap(v, z);
-  }
-  KL(c, "et", c->stream, k_et<double>, nblk(s), kThreads, 0,
-     s, m, c->eht_rp, c->eht_ci, c->eht64, ia, a, z, w, (const int *)nullptr);
-}
-
-void cgs2(ddlr_ctx *c, int s, int ncol, const double *Q, double *w, double *cvec) {
-  for (int pass = 0; pass < 2; pass++) {
-    KL(c, "lanczos", c->stream, k_gemvT_partial<256>, kRedGrid, 256, 0,
-       s, ncol, Q, (long long)s, w, c->part64);
-    KL(c, "lanczos", c->stream, k_reduce_cols<double>, 1, 256, ncol * sizeof(double),
-       kRedGrid, ncol, c->part64, (const double *)nullptr, (const double *)nullptr, cvec,
-       (const int *)nullptr);
-    KL(c, "lanczos", c->stream, k_gemvN_sub, nblk(s), kThreads, ncol * sizeof(double),
-       s, ncol, Q, (long long)s, cvec, w);
-  }
-}
-
-void dot_to(ddlr_ctx *c, long long n, const double *a, const double *b, double *out, int do_sqrt) {
-  KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, n, a, b, c->part64,
-     (const int *)nullptr);
-  KL(c, "dot", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, out, do_sqrt,
-     (const int *)nullptr);
-}
-
 void sync(ddlr_ctx *c) { ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"); }
 
 void read_dev(ddlr_ctx *c, void *h, const void *d, size_t bytes) {
@@ -452,6 +418,70 @@ void read_dev(ddlr_ctx *c, void *h, const void *d, size_t bytes) {
   sync(c);
 }
 
+// one Lanczos step j (Sec. 4.4) with every scalar and index on the device:
+// w = Op q_j; alpha_j; three-term update; two classical Gram-Schmidt passes
+// against Q_{j+1}; beta_j; breakdown decision; q_{j+1} (or a restart vector
+// orthogonalised against Q_{j+1}); j += 1.  Kernels return at once once the
+// stop flag is set.
+struct LzBufs {
+  double *Q, *al, *be, *cvec, *w, *qcur, *qprev, *nrm;
+  int *rank;
+  LzState *st;
+  long long ld;
+  int mmax;
+};
+
+void lanczos_step(ddlr_ctx *c, const LzBufs &L) {
+  const Plan &P = c->P;
+  const int n = P.n, m = P.m, s = P.s;
+  const double a = c->opt.alpha, ia = 1.0 / a;
+  const int *stop = reinterpret_cast<const int *>(reinterpret_cast<const char *>(L.st) + offsetof(LzState, stop));
+  const int *nobrk = reinterpret_cast<const int *>(reinterpret_cast<const char *>(L.st) + offsetof(LzState, no_break));
+  double *v = c->w64[0], *z = c->w64[1];
+  const size_t csm = size_t(L.mmax + 2) * sizeof(double);
+  KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0,
+     m, s, c->eh_rp, c->eh_ci, c->eh64, ia, a, L.qcur, (const double *)nullptr, v, stop);
+  a0_solve<double>(c, v, z, stop);
+  if (c->opt.variant == 2) {
+    a0_solve<double>(c, z, v, stop);
+    std::swap(v, z);
+  }
+  KL(c, "et", c->stream, k_et<double>, nblk(s), kThreads, 0, s, m, c->eht_rp, c->eht_ci, c->eht64, ia, a, z,
+     L.w, stop);
+  KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.qcur, L.w,
+     c->part64, stop);
+  KL(c, "dot", c->stream, k_lz_reduce_at, 1, 32, 0, kRedGrid, c->part64, L.al, L.st, 0, stop);
+  KL(c, "lanczos", c->stream, k_lz_three_term_d, nblk(s), kThreads, 0, s, L.al, L.be, L.st, L.qcur, L.qprev, L.w);
+  auto cgs2 = [&](const int *gate) {
+    for (int pass = 0; pass < 2; pass++) {
+      KL(c, "cgs2", c->stream, k_gemvT_partial_d<256>, kRedGrid, 256, 0, s, L.Q, L.ld, L.w, c->part64, L.st,
+         gate, (const int *)nullptr);
+      KL(c, "cgs2", c->stream, k_reduce_cols_d, (L.mmax + 8) / 8, 256, 0, kRedGrid, c->part64, L.cvec, L.st, gate,
+         (const int *)nullptr);
+      KL(c, "cgs2", c->stream, k_gemvN_sub_d, nblk(s), kThreads, csm, s, L.Q, L.ld, L.cvec, L.w, L.st, gate,
+         (const int *)nullptr);
+    }
+  };
+  cgs2(stop);
+  KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.w, L.w, c->part64, stop);
+  KL(c, "dot", c->stream, k_lz_reduce_at, 1, 32, 0, kRedGrid, c->part64, L.be, L.st, 1, stop);
+  KL(c, "lanczos", c->stream, k_lz_decide, 1, 32, 0, L.st, L.al, L.be);
+  KL(c, "lanczos", c->stream, k_lz_normalize, nblk(s), kThreads, 0, s, L.w, L.be, L.Q, L.ld, L.qcur, L.qprev, L.st);
+  // breakdown: restart from a fresh vector orthogonalised against Q_{j+1}
+  KL(c, "lanczos", c->stream, k_lz_randvec, nblk(s), kThreads, 0, s, L.rank, L.st, L.w);
+  cgs2(nobrk);
+  KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.w, L.w, c->part64, nobrk);
+  KL(c, "dot", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, L.nrm, 1, nobrk);
+  KL(c, "lanczos", c->stream, k_lz_restart_norm, nblk(s), kThreads, 0, s, L.w, L.nrm, L.Q, L.ld, L.qcur, L.qprev,
+     L.be, L.st);
+  KL(c, "lanczos", c->stream, k_lz_advance, 1, 32, 0, L.st);
+}
+
+// Lanczos with full reorthogonalisation and the convergence test of
+// eq. converge every `check` steps (Sec. 4.4, Sec. 5).  The host enqueues the
+// steps (one CUDA graph each) without waiting; each test runs on the second
+// stream while later steps proceed, and sets the device stop flag when met;
+// the host reads that flag once per test, one test later.
 ddlr_status run_lanczos(ddlr_ctx *c) {
   const Plan &P = c->P;
   const int s = P.s, n = P.n, m0 = P.m, k = c->opt.rank_k;
@@ -467,22 +497,35 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     tmp.push_back(p);
     return p;
   };
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_chk = nullptr, ev_done = nullptr;
+  cudaStream_t user = c->stream;
   ddlr_status st = DDLR_OK;
   try {
-    double *Q = (double *)talloc(sizeof(double) * size_t(s) * size_t(mmax + 1));
-    double *al = (double *)talloc(sizeof(double) * (mmax + 1));
-    double *be = (double *)talloc(sizeof(double) * (mmax + 1));
-    double *cvec = (double *)talloc(sizeof(double) * (mmax + 2));
-    double *w = (double *)talloc(sizeof(double) * s);
-    double *nrm = (double *)talloc(sizeof(double) * 4);
+    LzBufs L;
+    L.mmax = mmax;
+    L.ld = s;
+    L.Q = (double *)talloc(sizeof(double) * size_t(s) * size_t(mmax + 1));
+    L.al = (double *)talloc(sizeof(double) * (mmax + 1));
+    L.be = (double *)talloc(sizeof(double) * (mmax + 1));
+    L.cvec = (double *)talloc(sizeof(double) * (mmax + 2));
+    L.w = (double *)talloc(sizeof(double) * s);
+    L.qcur = (double *)talloc(sizeof(double) * s);
+    L.qprev = (double *)talloc(sizeof(double) * s);
+    L.nrm = (double *)talloc(sizeof(double) * 4);
+    L.rank = (int *)talloc(sizeof(int) * s);
+    L.st = (LzState *)talloc(sizeof(LzState));
     double *ework = (double *)talloc(sizeof(double) * 5 * size_t(mmax) * k);
     double *etop = (double *)talloc(sizeof(double) * (k + 1));
     double *evals = (double *)talloc(sizeof(double) * mmax);
-    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * k);
     double *esum = (double *)talloc(sizeof(double) * 2);
-    ck(cudaMemsetAsync(be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
-    // start vector: SplitMix64 stream `seed + restart`, drawn for the interface
-    // nodes in ascending original index, normalised
+    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * k);
+    ck(cudaEventCreateWithFlags(&ev_chk, cudaEventDisableTiming), "event");
+    ck(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming), "event");
+    ck(cudaMemsetAsync(L.be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
+    ck(cudaMemsetAsync(L.qprev, 0, sizeof(double) * s, c->stream), "memset");
+    // start vector: SplitMix64 stream `seed`, drawn for the interface nodes in
+    // ascending original index, normalised
     std::vector<int> rank(s);
     {
       std::vector<std::pair<int, int>> o(s);
@@ -490,72 +533,91 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       std::sort(o.begin(), o.end());
       for (int r = 0; r < s; r++) rank[o[r].second] = r;
     }
-    auto rand_vec = [&](uint64_t stream_id, std::vector<double> &v, bool normalise) {
-      std::vector<double> byrank(s);
-      for (int r = 0; r < s; r++) byrank[r] = sm64_pm1(stream_id, (uint64_t)r);
-      double nn = 0;
-      for (int r = 0; r < s; r++) nn += byrank[r] * byrank[r];
-      nn = std::sqrt(nn);
-      v.resize(s);
-      for (int j = 0; j < s; j++) v[j] = normalise ? byrank[rank[j]] / nn : byrank[rank[j]];
-    };
-    uint64_t restart = 0;
-    std::vector<double> hv;
-    rand_vec(c->opt.seed + restart, hv, true);
-    ck(cudaMemcpyAsync(Q, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
-    double scale = 0.0;
-    int mm = 0;
-    double ab[2];
+    std::vector<double> byrank(s), hv(s);
+    double nn = 0;
+    for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }
+    nn = std::sqrt(nn);
+    for (int j = 0; j < s; j++) hv[j] = byrank[rank[j]] / nn;
+    ck(cudaMemcpyAsync(L.Q, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+    ck(cudaMemcpyAsync(L.qcur, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+    ck(cudaMemcpyAsync(L.rank, rank.data(), sizeof(int) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+    LzState h0{};
+    h0.j = 0; h0.stop = 0; h0.no_break = 1; h0.restarts = 0; h0.conv_m = 0; h0.nan_step = -1;
+    h0.mmax = mmax; h0.scale = 0.0; h0.seed = c->opt.seed;
+    ck(cudaMemcpyAsync(L.st, &h0, sizeof(h0), cudaMemcpyHostToDevice, c->stream), "H2D");
+    ck(cudaStreamSynchronize(c->stream), "sync");       // host buffers above are locals
+
+    const char *ng = getenv("DDLR_NO_GRAPH");
+    const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+    if (use_graph) {
+      ck(cudaEventRecord(c->ev_fork, user), "event");
+      ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+      c->stream = c->gstream;
+      const long long l0 = c->launches;
+      const std::vector<long long> f0 = c->fam_cnt;
+      ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+      lanczos_step(c, L);
+      cudaGraph_t g = nullptr;
+      ck(cudaStreamEndCapture(c->stream, &g), "capture");
+      cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      ck(e, "cudaGraphInstantiate");
+      c->lz_nodes = c->launches - l0;
+      c->lz_fam_nodes.assign(c->fam_cnt.size(), 0);
+      for (size_t i = 0; i < c->fam_cnt.size(); i++) c->lz_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+      c->launches = l0;
+      for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+      for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+    }
+    int *hstop = reinterpret_cast<int *>(c->h_pin + 8);
+    bool pending = false;
     for (int j = 0; j < mmax; j++) {
-      double *q = Q + size_t(j) * s;
-      lanczos_op(c, q, w);
-      dot_to(c, s, q, w, al + j, 0);
-      KL(c, "lanczos", c->stream, k_lz_three_term, nblk(s), kThreads, 0,
-         s, al, be, j, q, j > 0 ? Q + size_t(j - 1) * s : (const double *)nullptr, w);
-      cgs2(c, s, j + 1, Q, w, cvec);
-      dot_to(c, s, w, w, be + j, 1);
-      ck(cudaMemcpyAsync(c->h_pin, al + j, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
-      ck(cudaMemcpyAsync(c->h_pin + 1, be + j, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
-      sync(c);
-      ab[0] = c->h_pin[0];
-      ab[1] = c->h_pin[1];
-      if (!std::isfinite(ab[0]) || !std::isfinite(ab[1])) { st = DDLR_ERR_NAN; break; }
-      scale = std::max(scale, std::fabs(ab[0]));
-      mm = j + 1;
-      if (check > 0 && mm % check == 0 && mm >= k + 1) {
-        const size_t smk = 2 * mm * sizeof(double);
-        KL(c, "eig_check", c->stream, k_tridiag_values, k, 32, smk, mm, al, be, k, etop);
-        KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum);
-        KL(c, "eig_check", c->stream, k_tridiag_values, k, 32, smk, mm - 1, al, be, k, etop);
-        KL(c, "eig_check", c->stream, k_sum_first, 1, 32, 0, k, etop, esum + 1);
-        read_dev(c, c->h_pin, esum, 2 * sizeof(double));
-        if (std::fabs(c->h_pin[0] - c->h_pin[1]) < eps * std::fabs(c->h_pin[1])) break;
-      }
-      if (mm == mmax) break;
-      double *qn = Q + size_t(j + 1) * s;
-      if (ab[1] <= 1e-12 * (scale > 0 ? scale : 1.0)) {
-        // breakdown: an invariant subspace was found; continue from a fresh
-        // random vector orthogonalised against Q_j, with beta_j = 0
-        restart++;
-        rand_vec(c->opt.seed + restart, hv, false);
-        ck(cudaMemcpyAsync(w, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
-        cgs2(c, s, j + 1, Q, w, cvec);
-        dot_to(c, s, w, w, nrm, 1);
-        KL(c, "lanczos", c->stream, k_scale_into, nblk(s), kThreads, 0, s, w, nrm, qn);
-        ck(cudaMemsetAsync(be + j, 0, sizeof(double), c->stream), "memset");
+      if (use_graph) {
+        ck(cudaGraphLaunch(exec, c->stream), "cudaGraphLaunch");
+        c->launches += c->lz_nodes;
+        for (size_t i = 0; i < c->lz_fam_nodes.size(); i++) c->fam_cnt[i] += c->lz_fam_nodes[i];
       } else {
-        scale = std::max(scale, ab[1]);
-        KL(c, "lanczos", c->stream, k_scale_into, nblk(s), kThreads, 0, s, w, be + j, qn);
+        lanczos_step(c, L);
+      }
+      const int mm = j + 1;
+      if (check > 0 && mm % check == 0 && mm >= k + 1 && mm < mmax) {
+        if (pending) {
+          ck(cudaEventSynchronize(ev_done), "event");
+          if (*hstop) break;                 // converged at an earlier test
+        }
+        ck(cudaEventRecord(ev_chk, c->stream), "event");
+        ck(cudaStreamWaitEvent(c->stream2, ev_chk, 0), "wait");
+        const size_t smk = 2 * mm * sizeof(double);
+        KL(c, "eig_check", c->stream2, k_tridiag_values, k, 32, smk, mm, L.al, L.be, k, etop);
+        KL(c, "eig_check", c->stream2, k_sum_first, 1, 32, 0, k, etop, esum);
+        KL(c, "eig_check", c->stream2, k_tridiag_values, k, 32, smk, mm - 1, L.al, L.be, k, etop);
+        KL(c, "eig_check", c->stream2, k_sum_first, 1, 32, 0, k, etop, esum + 1);
+        KL(c, "eig_check", c->stream2, k_lz_converged, 1, 32, 0, esum, eps, mm, L.st);
+        ck(cudaMemcpyAsync(hstop, reinterpret_cast<const char *>(L.st) + offsetof(LzState, stop), sizeof(int),
+                           cudaMemcpyDeviceToHost, c->stream2), "D2H");
+        ck(cudaEventRecord(ev_done, c->stream2), "event");
+        pending = true;
       }
     }
+    ck(cudaStreamSynchronize(c->stream2), "sync");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    if (use_graph) {
+      ck(cudaEventRecord(c->ev_join, c->stream), "event");
+      ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
+      c->stream = user;
+    }
+    LzState hs;
+    ck(cudaMemcpy(&hs, L.st, sizeof(hs), cudaMemcpyDeviceToHost), "D2H");
+    const int mm = hs.conv_m > 0 ? hs.conv_m : std::min(hs.j, mmax);
+    if (hs.nan_step >= 0 && hs.nan_step < mm) st = DDLR_ERR_NAN;
     if (st == DDLR_OK) {
       c->msteps = mm;
       const int nvals = mm;
-      KL(c, "eig", c->stream, k_tridiag_values, nvals, 32, 2 * mm * sizeof(double),
-         mm, al, be, nvals, evals);
-      KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, al, be, k, evals, eY, ework);
+      KL(c, "eig", c->stream, k_tridiag_values, nvals, 32, 2 * mm * sizeof(double), mm, L.al, L.be, nvals, evals);
+      KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, L.al, L.be, k, evals, eY, ework);
       c->ritz.assign(nvals, 0.0);
       read_dev(c, c->ritz.data(), evals, sizeof(double) * nvals);
+      const double *Q = L.Q;
       if (c->opt.variant == 1) {
         KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, Q, (long long)s, eY, c->U64);
         KL(c, "ritz", c->stream, k_ddlr1_coef, 1, 32, 0, mm, k, c->opt.theta_mode, evals,
@@ -592,10 +654,19 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     sync(c);
   } catch (...) {
+    c->stream = user;
     cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream2);
+    cudaStreamSynchronize(c->gstream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev_chk) cudaEventDestroy(ev_chk);
+    if (ev_done) cudaEventDestroy(ev_done);
     for (void *p : tmp) cudaFree(p);
     throw;
   }
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaEventDestroy(ev_chk);
+  cudaEventDestroy(ev_done);
   for (void *p : tmp) cudaFree(p);
   return st;
 }

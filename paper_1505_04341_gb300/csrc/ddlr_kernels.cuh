@@ -928,6 +928,171 @@ __global__ void k_scale_into(int s, const double *num, const double *den,
   if (r < s) out[r] = num[r] / (*den);
 }
 
+// ------------------------------------------------ device-driven Lanczos step
+// Control state of the Lanczos recurrence kept on the device, so a step needs
+// no host round trip and can be replayed as one CUDA graph: the step index,
+// the stop flag (set at m = m_max, by the convergence test of eq. converge,
+// or on NaN), the breakdown decision and the running scale of the tridiagonal.
+struct LzState {
+  int j;            // current step (0-based)
+  int stop;         // nonzero: later step kernels return at once
+  int no_break;     // 1: normal step; 0: breakdown -> restart kernels run
+  int restarts;     // restarts so far (SplitMix64 stream seed + restarts)
+  int conv_m;       // m at which eq. converge was met (0: not met)
+  int nan_step;     // first step with a non-finite alpha or beta (-1: none)
+  int mmax, pad;
+  double scale;     // max |alpha_i|, beta_i seen (breakdown threshold)
+  unsigned long long seed;
+};
+
+// SplitMix64 (Steele, Lea & Flood 2014): output i of stream `seed`, mapped to
+// [-1, 1) as 2 (z >> 11) 2^-53 - 1
+__device__ __forceinline__ double d_sm64_pm1(unsigned long long seed, unsigned long long i) {
+  unsigned long long z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return 2.0 * (double(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// arr[st->j] = sum of G partials (sqrt when asked)
+__global__ void k_lz_reduce_at(int G, const double *partials, double *arr, const LzState *st,
+                               int do_sqrt, const int *gate) {
+  if (gate && *gate) return;
+  double s = warp_sum_partials(partials, G);
+  if (threadIdx.x == 0) arr[st->j] = do_sqrt ? sqrt(s) : s;
+}
+
+// w -= alpha_j q_j + beta_{j-1} q_{j-1}
+__global__ void k_lz_three_term_d(int s, const double *al, const double *be, const LzState *st,
+                                  const double *qcur, const double *qprev, double *w) {
+  if (st->stop) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  const int j = st->j;
+  double v = w[r] - al[j] * qcur[r];
+  if (j > 0) v -= be[j - 1] * qprev[r];
+  w[r] = v;
+}
+
+// partials of Q_{j+1}^T w (columns 0..j), warp per column; gate: return when
+// *gate != 0 (gate_inv: return when *gate_inv == 0)
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_gemvT_partial_d(int s, const double *Q, long long ld, const double *w, double *partials,
+                  const LzState *st, const int *gate, const int *gate_inv) {
+  if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
+  const int ncol = st->j + 1;
+  const int nw = NT / 32, wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const long long chunk = ((long long)s + gridDim.x - 1) / gridDim.x;
+  const long long r0 = (long long)blockIdx.x * chunk;
+  const long long r1 = min((long long)s, r0 + chunk);
+  for (int j = wi; j < ncol; j += nw) {
+    const double *q = Q + (long long)j * ld;
+    double acc = 0;
+    for (long long r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (l == 0) partials[(long long)blockIdx.x * ncol + j] = acc;
+  }
+}
+
+// c[j] = sum_g partials[g][j], j <= st->j (warp per column, fixed order)
+__global__ void k_reduce_cols_d(int G, const double *partials, double *c, const LzState *st,
+                                const int *gate, const int *gate_inv) {
+  if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
+  const int ncol = st->j + 1;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int col = blockIdx.x * nw + w; col < ncol; col += gridDim.x * nw) {
+    double s = 0;
+    for (int g = l; g < G; g += 32) s += partials[(long long)g * ncol + col];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) c[col] = s;
+  }
+}
+
+// w -= Q_{j+1} c
+__global__ void k_gemvN_sub_d(int s, const double *Q, long long ld, const double *c, double *w,
+                              const LzState *st, const int *gate, const int *gate_inv) {
+  if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
+  extern __shared__ unsigned char smraw[];
+  double *cs = reinterpret_cast<double *>(smraw);
+  const int ncol = st->j + 1;
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  double acc = 0;
+  for (int j = 0; j < ncol; j++) acc += Q[(long long)j * ld + r] * cs[j];
+  w[r] -= acc;
+}
+
+// breakdown decision of step j (beta_j <= 1e-12 max(|alpha_i|, beta_i))
+__global__ void k_lz_decide(LzState *st, const double *al, const double *be) {
+  if (st->stop || threadIdx.x != 0) return;
+  const int j = st->j;
+  const double a = al[j], b = be[j];
+  if (!(a == a) || isinf(a) || !(b == b) || isinf(b)) {
+    if (st->nan_step < 0) st->nan_step = j;
+    st->stop = 1;
+    return;
+  }
+  st->scale = fmax(st->scale, fabs(a));
+  const bool brk = b <= 1e-12 * (st->scale > 0 ? st->scale : 1.0);
+  st->no_break = brk ? 0 : 1;
+  if (brk) st->restarts += 1;
+  else st->scale = fmax(st->scale, b);
+}
+
+// normal step: q_{j+1} = w / beta_j into Q, qprev <- qcur, qcur <- q_{j+1}
+__global__ void k_lz_normalize(int s, const double *w, const double *be, double *Q, long long ld,
+                               double *qcur, double *qprev, const LzState *st) {
+  if (st->stop || !st->no_break) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  const int j = st->j;
+  const double v = w[r] / be[j];
+  Q[(long long)(j + 1) * ld + r] = v;
+  qprev[r] = qcur[r];
+  qcur[r] = v;
+}
+
+// breakdown: w = SplitMix64 stream (seed + restarts), drawn in the order of
+// rank[] (ascending original index of the interface nodes)
+__global__ void k_lz_randvec(int s, const int *rank, const LzState *st, double *w) {
+  if (st->stop || st->no_break) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  w[r] = d_sm64_pm1(st->seed + (unsigned long long)st->restarts, (unsigned long long)rank[r]);
+}
+
+// breakdown: q_{j+1} = w / ||w|| (w orthogonalised), beta_j = 0
+__global__ void k_lz_restart_norm(int s, const double *w, const double *nrm, double *Q, long long ld,
+                                  double *qcur, double *qprev, double *be, const LzState *st) {
+  if (st->stop || st->no_break) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= s) return;
+  const int j = st->j;
+  const double v = w[r] / (*nrm);
+  Q[(long long)(j + 1) * ld + r] = v;
+  qprev[r] = qcur[r];
+  qcur[r] = v;
+  if (r == 0) be[j] = 0.0;
+}
+
+// end of step j: j += 1; stop at m_max
+__global__ void k_lz_advance(LzState *st) {
+  if (st->stop || threadIdx.x != 0) return;
+  st->j += 1;
+  st->no_break = 1;
+  if (st->j >= st->mmax) st->stop = 1;
+}
+
+// eq. converge on the sums of the k largest Ritz values of T_m and T_{m-1}
+__global__ void k_lz_converged(const double *esum, double eps, int m, LzState *st) {
+  if (threadIdx.x != 0 || st->conv_m > 0) return;
+  if (fabs(esum[0] - esum[1]) < eps * fabs(esum[1])) { st->conv_m = m; st->stop = 1; }
+}
+
 // ------------------------------------------------ tridiagonal eigensolver
 // Eigenvalues of the symmetric tridiagonal T_m (diagonal al, off-diagonal be)
 // by Sturm-sequence multisection, eigenvectors by inverse iteration
