@@ -139,6 +139,28 @@ ddlr_status ddlr_apply(ddlr_handle h, const double *x, double *y, int nrhs,
 ddlr_status ddlr_a0_solve(ddlr_handle h, const double *x, double *y, int nrhs,
                           int ld);
 
+/* y = A0^-1 x as ddlr_a0_solve computes it, for callers that must not
+ * allocate device memory: applications whose device memory is all owned by
+ * their own allocator or pool (where a cudaMalloc could fail or fragment it),
+ * or code that runs inside such an allocator.  A call never calls cudaMalloc,
+ * cudaFree or an allocating library routine: it reads the handle's factors
+ * (allocated by ddlr_setup) and keeps its temporaries in static device memory.
+ * The paper has no counterpart: it is a property of the library, not of the
+ * method.
+ * The two temporary vectors live in one file-scope device array of
+ * 2 x 1,048,576 doubles (16 MiB), present on every GPU that loads the library
+ * until the process exits, so n must be at most 1,048,576.  The first call on
+ * each device does a one-time set-up (it looks up that array's device address
+ * with cudaGetSymbolAddress); make that first call before any stream capture.
+ * x and y: device memory, n doubles each, original order, not overlapping.
+ * Asynchronous on the handle's stream.  Nothing needs to start at zero: every
+ * entry of the array is written before it is read.  All calls in the process
+ * share the array, so calls whose work overlaps on the GPU (other streams,
+ * other handles, other threads) race: order them (one stream, or events).
+ * Errors: INVALID for n > 1,048,576, a precision-1 handle, NULL or host
+ * pointers; CUDA if the set-up fails. */
+ddlr_status ddlr_a0_solve_noalloc(ddlr_handle h, const double *x, double *y);
+
 /* Preconditioned CG from x0 = 0 (Sec. 5) for each of nrhs right-hand sides,
  * stopping when ||r|| <= tol ||b|| and the true residual confirms it (else r is
  * replaced by b - A x and CG restarts), or after maxit iterations (maxit <= 0:

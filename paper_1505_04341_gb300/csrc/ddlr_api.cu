@@ -11,6 +11,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -1508,6 +1509,65 @@ ddlr_status ddlr_a0_solve(ddlr_handle c, const double *x, double *y, int nrhs, i
     }
     KL(c, "perm", c->stream, k_permute_out<double>, nblk(n), kThreads, 0, n, c->perm, yo, yd);
   });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- A0 solve without allocation
+// Scratch of ddlr_a0_solve_noalloc: the permuted right-hand side and the
+// permuted result, at most kNoAllocMaxN rows each (16 MiB; every GPU that
+// loads the library holds it until the process exits).
+namespace {
+constexpr int kNoAllocMaxN = 1 << 20;
+}
+static __device__ __align__(256) double g_noalloc_scratch[2 * (1 << 20)];
+
+namespace {
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[128] = {nullptr};   // device address of the scratch, per device
+}
+
+extern "C" {
+
+ddlr_status ddlr_a0_solve_noalloc(ddlr_handle c, const double *x, double *y) {
+  if (!c) return DDLR_ERR_INVALID;
+  const int n = c->P.n;
+  if (!x || !y) { c->err = "NULL vector"; return DDLR_ERR_INVALID; }
+  if (n > kNoAllocMaxN) {
+    c->err = "ddlr_a0_solve_noalloc: n = " + std::to_string(n) + " exceeds its limit of " +
+             std::to_string(kNoAllocMaxN) + " rows";
+    return DDLR_ERR_INVALID;
+  }
+  if (c->opt.precision != 0) { c->err = "ddlr_a0_solve_noalloc: FP64 handles only"; return DDLR_ERR_INVALID; }
+  if (!is_device_ptr(x) || !is_device_ptr(y)) {
+    c->err = "ddlr_a0_solve_noalloc: x and y must be device memory";
+    return DDLR_ERR_INVALID;
+  }
+  const bool timing = c->timing;
+  c->timing = false;   // per-kernel timing would create events
+  ddlr_status st = run_guarded(c, [&]() -> ddlr_status {
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 128) throw Fail{DDLR_ERR_INVALID, "device index out of range"};
+    double *scratch = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_noalloc_mu);
+      if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        ck(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<double *>(ptr);
+      }
+      scratch = g_noalloc_ptr[dev];
+    }
+    double *xi = scratch, *yo = scratch + kNoAllocMaxN;
+    k_permute_in<double><<<nblk(n), kThreads, 0, c->stream>>>(n, c->perm, x, xi);
+    a0_solve<double>(c, xi, yo, nullptr);
+    k_permute_out<double><<<nblk(n), kThreads, 0, c->stream>>>(n, c->perm, yo, y);
+    c->launches += 2;
+    return DDLR_OK;
+  });
+  c->timing = timing;
+  return st;
 }
 
 ddlr_status ddlr_pcg(ddlr_handle c, const double *b, double *x, int nrhs, int ld, double tol,

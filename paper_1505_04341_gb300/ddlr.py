@@ -63,7 +63,7 @@ class ddlr_server_options(ctypes.Structure):
 
 # every entry point declared in include/ddlr.h
 EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
-           "ddlr_a0_solve", "ddlr_pcg", "ddlr_get_info", "ddlr_get_ritz",
+           "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_get_info", "ddlr_get_ritz",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
            "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
@@ -93,6 +93,7 @@ def load(path: str | None = None):
         "ddlr_refactor": ([P, P], I),
         "ddlr_apply": ([P, P, P, I, I], I),
         "ddlr_a0_solve": ([P, P, P, I, I], I),
+        "ddlr_a0_solve_noalloc": ([P, P, P], I),
         "ddlr_pcg": ([P, P, P, I, I, D, I, ctypes.POINTER(ddlr_solve_info)], I),
         "ddlr_get_info": ([P, ctypes.POINTER(ddlr_info)], I),
         "ddlr_get_ritz": ([P, P, I, ctypes.POINTER(I)], I),
@@ -242,6 +243,17 @@ class DDLR:
     def a0_solve(self, x, y=None):
         """y = A0^-1 x"""
         return self._vec_op(_lib.ddlr_a0_solve, x, self._like(x) if y is None else y)
+
+    def a0_solve_noalloc(self, x, y):
+        """y = A0^-1 x for device float64 vectors of length n, through the
+        entry point that allocates no device memory (temporaries in a static
+        device array; n <= 1,048,576, FP64 handles)."""
+        px, n, nr = _vec_ptr(x)
+        py, n2, nr2 = _vec_ptr(y)
+        if n != self.n or n2 != self.n or nr != 1 or nr2 != 1:
+            raise ValueError("shape mismatch: one vector of length n expected")
+        _check(_lib, self._h, _lib.ddlr_a0_solve_noalloc(self._h, px, py))
+        return y
 
     def pcg(self, b, x=None, tol=1e-8, maxit=500, check=True):
         """Returns (x, [ddlr_solve_info per RHS]); raises on NOCONV/NAN when
