@@ -21,6 +21,7 @@
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
+#include "ddlr_persist.cuh"
 
 using namespace ddlr;
 
@@ -136,6 +137,11 @@ struct ddlr_ctx {
   int msteps = 0;
   double theta = 0.0;
   int *dflag = nullptr;       // device error flags [0]=breakdown [1]=notspd [2]=eig fail
+  // persistent cooperative kernels (shallow factors): one CTA per SM
+  double *pz_part = nullptr;  // 3 x pz_grid x pz_pstride partial sums
+  unsigned *pz_bar = nullptr; // grid-barrier arrival counter
+  int pz_grid = 0, pz_pstride = 0, pz_mmax = 0;
+  bool pz_pcg = false, pz_lz = false;
   // workspaces
   double *w64[8] = {nullptr};
   float *w32[8] = {nullptr};
@@ -411,6 +417,11 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
     KL(c, "vec", c->stream, k_mulv_t<double>, nblk(n), kThreads, 0, (long long)n, c->dsc_dev, z, z, gate);
 }
 
+// persistent-kernel helpers (defined with the allocation code)
+PzOp make_pzop(ddlr_ctx *c);
+void pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
+size_t pz_lz_smem(int mmax);
+
 // ------------------------------------------------------------- Lanczos
 void sync(ddlr_ctx *c) { ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"); }
 
@@ -517,7 +528,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     L.rank = (int *)talloc(sizeof(int) * s);
     L.st = (LzState *)talloc(sizeof(LzState));
     double *ework = (double *)talloc(sizeof(double) * 5 * size_t(mmax) * k);
-    double *etop = (double *)talloc(sizeof(double) * (k + 1));
+    double *etop = (double *)talloc(sizeof(double) * (2 * k + 1));
     double *evals = (double *)talloc(sizeof(double) * mmax);
     double *esum = (double *)talloc(sizeof(double) * 2);
     double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * k);
@@ -549,7 +560,17 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     ck(cudaStreamSynchronize(c->stream), "sync");       // host buffers above are locals
 
     const char *ng = getenv("DDLR_NO_GRAPH");
-    const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+    // every step and test in one persistent kernel when the factors are shallow
+    const int nLz = int(P.ch_all_ptr.size()) - 1;
+    const bool persist = c->pz_lz && mmax <= c->pz_mmax &&
+                         (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
+    const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
+    if (persist) {
+      PzOp O = make_pzop(c);
+      PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps};
+      void *args[] = {&O, &Lz};
+      pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax), args);
+    }
     if (use_graph) {
       ck(cudaEventRecord(c->ev_fork, user), "event");
       ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
@@ -572,7 +593,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     int *hstop = reinterpret_cast<int *>(c->h_pin + 8);
     bool pending = false;
-    for (int j = 0; j < mmax; j++) {
+    for (int j = 0; j < (persist ? 0 : mmax); j++) {
       if (use_graph) {
         ck(cudaGraphLaunch(exec, c->stream), "cudaGraphLaunch");
         c->launches += c->lz_nodes;
@@ -760,6 +781,79 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   return DDLR_OK;
 }
 
+// ------------------------------------------------ persistent kernels
+size_t pz_pcg_smem(int k) { return size_t(kPzThreads + 32 + k + 2) * sizeof(double); }
+size_t pz_lz_smem(int mmax) { return size_t(kPzThreads + 32 + 3 * mmax + 2) * sizeof(double); }
+
+// Whole-solve persistent kernels serve shallow factors (every block at most
+// kPzMaxLevels levels deep) on devices with cooperative launch; one CTA per
+// SM.  DDLR_PERSIST=0 keeps the kernel-per-phase path.
+void pz_setup(ddlr_ctx *c, int mmax) {
+  const Plan &P = c->P;
+  const char *env = getenv("DDLR_PERSIST");
+  if (env && env[0] == '0') return;
+  const int nL = int(P.ch_all_ptr.size()) - 1;
+  if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
+  const int k = c->opt.rank_k;
+  int dev = 0, sms = 0, coop = 0, optin = 0;
+  ck(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (!coop || sms <= 0 || k > kPzThreads) return;
+  const size_t sp = pz_pcg_smem(k), sl = pz_lz_smem(mmax);
+  int occ_p = 0, occ_l = 0;
+  ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_pcg_persist<kPzThreads>, kPzThreads, sp), "occupancy");
+  if (sl <= size_t(optin)) {
+    ck(cudaFuncSetAttribute(k_lz_persist<kPzThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sl)), "attr");
+    ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, k_lz_persist<kPzThreads>, kPzThreads, sl), "occupancy");
+  }
+  c->pz_grid = sms;
+  c->pz_pstride = std::max(k, mmax + 2);
+  c->pz_mmax = mmax;
+  c->pz_pcg = c->opt.precision == 0 && occ_p >= 1;
+  c->pz_lz = occ_l >= 1;
+  if (!c->pz_pcg && !c->pz_lz) return;
+  c->pz_part = c->alloc<double>(size_t(3) * c->pz_grid * c->pz_pstride);
+  c->pz_bar = c->alloc<unsigned>(1);
+}
+
+PzOp make_pzop(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  PzOp O{};
+  O.n = P.n; O.m = P.m; O.s = P.s; O.k = c->opt.rank_k; O.variant = c->opt.variant;
+  O.nL = int(P.ch_all_ptr.size()) - 1;
+  O.pstride = c->pz_pstride;
+  O.a = c->opt.alpha; O.ia = 1.0 / c->opt.alpha;
+  for (int i = 0; i <= O.nL; i++) O.lvl_ptr[i] = P.ch_all_ptr[i];
+  O.S = c->S;
+  O.chunks = reinterpret_cast<const int4 *>(c->chunks);
+  O.lval = c->l64; O.uval = c->u64; O.dinv = c->dinv64;
+  O.eh_rp = c->eh_rp; O.eh_ci = c->eh_ci; O.eh = c->eh64;
+  O.eht_rp = c->eht_rp; O.eht_ci = c->eht_ci; O.eht = c->eht64;
+  O.U = c->U64; O.coef = c->coef64; O.inv1mt = c->inv1mt64; O.Hk = c->Hk64;
+  O.a_soff = c->a_soff; O.a_sw = c->a_sw; O.a_col = c->a_col; O.a_val = c->a_val;
+  O.dsc = c->dsc_dev;
+  O.part = c->pz_part;
+  O.gs.count = c->pz_bar;
+  O.gs.err = c->dflag + 3;
+  return O;
+}
+
+// one cooperative launch of a persistent kernel on the handle's stream
+void pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args) {
+  ck(cudaMemsetAsync(c->pz_bar, 0, sizeof(unsigned), c->stream), "memset");
+  ddlr_ctx::Scope sc(c, fam, c->stream);
+  ck(cudaLaunchCooperativeKernel(fn, dim3(c->pz_grid), dim3(kPzThreads), args, smem, c->stream),
+     "cudaLaunchCooperativeKernel");
+}
+
+// grid barriers of one PCG iteration and of one Lanczos step, upper bounds
+int pz_barriers_per_iteration(const ddlr_ctx *c) {
+  const int nL = int(c->P.ch_all_ptr.size()) - 1;
+  return 2 * (2 * nL - 1) + 8;
+}
+
 void allocate(ddlr_ctx *c) {
   const Plan &P = c->P;
   const int n = P.n, k = c->opt.rank_k;
@@ -845,6 +939,7 @@ void allocate(ddlr_ctx *c) {
   int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
   mmax = std::max(std::min(mmax, P.s), k);
   c->part64 = c->alloc<double>(size_t(kRedGrid) * std::max(k + 2, mmax + 2) + 2 * kRedGrid);
+  pz_setup(c, mmax);
   if (c->opt.precision == 1) {
     c->l32 = c->alloc<float>(P.l_col.size());
     c->u32 = c->alloc<float>(P.u_col.size());
@@ -901,62 +996,72 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   double *part = c->part64;
   const int *gate = pcg_gate(c);
   const char *ng = getenv("DDLR_NO_GRAPH");
-  const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+  // the whole solve in one persistent kernel when the factors are shallow
+  const bool persist = c->pz_pcg && !flexible &&
+                       (long long)(maxit + 2) * pz_barriers_per_iteration(c) * c->pz_grid < (1LL << 31);
+  const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
   cudaStream_t user = c->stream;
   struct Restore {
     ddlr_ctx *c; cudaStream_t s;
     ~Restore() { c->stream = s; }
   } restore{c, user};
-  if (use_graph) {
-    ck(cudaEventRecord(c->ev_fork, user), "event");
-    ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
-    c->stream = c->gstream;
-  }
-  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream), "memset");
-  ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, b, b, part, (const int *)nullptr);
-  KL(c, "pcg", c->stream, k_pcg_init, 1, 32, 0, c->pcg, part, kRedGrid, tol, maxit, flexible);
-  precond(c, r, z, gate);
-  KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, part, gate);
-  KL(c, "pcg", c->stream, k_pcg_rz0, 1, 32, 0, c->pcg, part, kRedGrid);
-  ck(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  ck(cudaMemcpyAsync(zo, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  if (use_graph && (c->pcg_exec == nullptr || c->pcg_exec_flexible != flexible)) {
-    if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
-    const long long l0 = c->launches;
-    const std::vector<long long> f0 = c->fam_cnt;
-    ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
-    pcg_iteration(c, b, x, flexible);
-    cudaGraph_t g = nullptr;
-    ck(cudaStreamEndCapture(c->stream, &g), "capture");
-    cudaError_t e = cudaGraphInstantiate(&c->pcg_exec, g, 0);
-    cudaGraphDestroy(g);
-    ck(e, "cudaGraphInstantiate");
-    c->pcg_exec_flexible = flexible;
-    c->pcg_nodes = c->launches - l0;
-    c->pcg_fam_nodes.assign(c->fam_cnt.size(), 0);
-    for (size_t i = 0; i < c->fam_cnt.size(); i++)
-      c->pcg_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
-    c->launches = l0;                    // captured, not yet executed
-    for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
-    for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
-  }
-  const int batch = 4;
-  for (int it = 0; it < maxit + batch; it += batch) {
-    for (int bi = 0; bi < batch; bi++) {
-      if (use_graph) {
-        ck(cudaGraphLaunch(c->pcg_exec, c->stream), "cudaGraphLaunch");
-        c->launches += c->pcg_nodes;
-        for (size_t i = 0; i < c->pcg_fam_nodes.size(); i++) c->fam_cnt[i] += c->pcg_fam_nodes[i];
-      } else {
-        pcg_iteration(c, b, x, flexible);
-      }
+  if (persist) {
+    PzOp O = make_pzop(c);
+    PzPcg Pp{b, x, r, z, p, zo, q, c->pv[5], c->w64[0], c->w64[1], c->w64[2], c->w64[3], c->pcg, tol, maxit};
+    void *args[] = {&O, &Pp};
+    pz_launch(c, "pcg_persist", (const void *)k_pcg_persist<kPzThreads>, pz_pcg_smem(c->opt.rank_k), args);
+  } else {
+    if (use_graph) {
+      ck(cudaEventRecord(c->ev_fork, user), "event");
+      ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+      c->stream = c->gstream;
     }
-    int done = 0;
-    ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
-    ck(cudaStreamSynchronize(c->stream), "sync");
-    std::memcpy(&done, c->h_pin, sizeof(int));
-    if (done) break;
+    ck(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream), "memset");
+    ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, b, b, part, (const int *)nullptr);
+    KL(c, "pcg", c->stream, k_pcg_init, 1, 32, 0, c->pcg, part, kRedGrid, tol, maxit, flexible);
+    precond(c, r, z, gate);
+    KL(c, "pcg", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, part, gate);
+    KL(c, "pcg", c->stream, k_pcg_rz0, 1, 32, 0, c->pcg, part, kRedGrid);
+    ck(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    ck(cudaMemcpyAsync(zo, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    if (use_graph && (c->pcg_exec == nullptr || c->pcg_exec_flexible != flexible)) {
+      if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+      const long long l0 = c->launches;
+      const std::vector<long long> f0 = c->fam_cnt;
+      ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+      pcg_iteration(c, b, x, flexible);
+      cudaGraph_t g = nullptr;
+      ck(cudaStreamEndCapture(c->stream, &g), "capture");
+      cudaError_t e = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+      cudaGraphDestroy(g);
+      ck(e, "cudaGraphInstantiate");
+      c->pcg_exec_flexible = flexible;
+      c->pcg_nodes = c->launches - l0;
+      c->pcg_fam_nodes.assign(c->fam_cnt.size(), 0);
+      for (size_t i = 0; i < c->fam_cnt.size(); i++)
+        c->pcg_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+      c->launches = l0;                    // captured, not yet executed
+      for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+      for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+    }
+    const int batch = 4;
+    for (int it = 0; it < maxit + batch; it += batch) {
+      for (int bi = 0; bi < batch; bi++) {
+        if (use_graph) {
+          ck(cudaGraphLaunch(c->pcg_exec, c->stream), "cudaGraphLaunch");
+          c->launches += c->pcg_nodes;
+          for (size_t i = 0; i < c->pcg_fam_nodes.size(); i++) c->fam_cnt[i] += c->pcg_fam_nodes[i];
+        } else {
+          pcg_iteration(c, b, x, flexible);
+        }
+      }
+      int done = 0;
+      ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+      ck(cudaStreamSynchronize(c->stream), "sync");
+      std::memcpy(&done, c->h_pin, sizeof(int));
+      if (done) break;
+    }
   }
   // final true residual
   KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, x, q, (const int *)nullptr);

@@ -1121,23 +1121,14 @@ __device__ __forceinline__ int sturm_count(int m, const double *a, const double 
   return cnt;
 }
 
-// The nv largest eigenvalues of T_m, descending, into vals.  One warp per
-// eigenvalue (CTA = 4 warps, grid covers nv): the 32 lanes evaluate 32
-// interior points of the eigenvalue's bracket per round (multisection, 5 bits
-// per round).  Spreading the eigenvalues over many SMs matters because the
-// FP64 pipe of one SM is narrow.  Dynamic shared memory: 2m doubles.
-__global__ void k_tridiag_values(int m, const double *al, const double *be,
-                                 int nv, double *vals) {
-  extern __shared__ double shm[];
-  double *a = shm, *b2 = shm + m;
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int i = tid; i < m; i += blockDim.x) {
-    a[i] = al[i];
-    b2[i] = (i + 1 < m) ? be[i] * be[i] : 0.0;
-  }
-  __syncthreads();
-  const int gi = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);   // eigenvalue index
-  if (gi >= nv) return;
+// Eigenvalue gi (0 = largest) of T_m by Sturm-sequence multisection, computed
+// by the 32 lanes of the calling warp (all get the value): each round the
+// lanes evaluate 32 interior points of the current bracket (5 bits per round),
+// starting from the Gershgorin interval.  a, b2: diagonal and squared
+// off-diagonal (b2[i] = be[i]^2, i + 1 < m); be: off-diagonal.
+__device__ __forceinline__ double tridiag_eig_warp(int m, const double *a, const double *b2,
+                                                   const double *be, int gi) {
+  const int lane = threadIdx.x & 31;
   double lo = 1e300, hi = -1e300;
   for (int i = lane; i < m; i += 32) {
     const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
@@ -1150,7 +1141,7 @@ __global__ void k_tridiag_values(int m, const double *al, const double *be,
   }
   const double span = fmax(hi - lo, 1e-300);
   double blo = lo - 1e-9 * span, bhi = hi + 1e-9 * span;
-  const int target = m - 1 - gi;     // eigenvalue gi (0 = largest)
+  const int target = m - 1 - gi;
   for (int round = 0; round < 12; round++) {
     const double x = blo + (bhi - blo) * double(lane + 1) * (1.0 / 33.0);
     const int c = sturm_count(m, a, b2, x);
@@ -1162,7 +1153,27 @@ __global__ void k_tridiag_values(int m, const double *al, const double *be,
     blo = nlo;
     bhi = nhi;
   }
-  if (lane == 0) vals[gi] = 0.5 * (blo + bhi);
+  return 0.5 * (blo + bhi);
+}
+
+// The nv largest eigenvalues of T_m, descending, into vals.  One warp per
+// eigenvalue (CTA = 4 warps, grid covers nv).  Spreading the eigenvalues over
+// many SMs matters because the FP64 pipe of one SM is narrow.  Dynamic shared
+// memory: 2m doubles.
+__global__ void k_tridiag_values(int m, const double *al, const double *be,
+                                 int nv, double *vals) {
+  extern __shared__ double shm[];
+  double *a = shm, *b2 = shm + m;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) {
+    a[i] = al[i];
+    b2[i] = (i + 1 < m) ? be[i] * be[i] : 0.0;
+  }
+  __syncthreads();
+  const int gi = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);   // eigenvalue index
+  if (gi >= nv) return;
+  const double v = tridiag_eig_warp(m, a, b2, be, gi);
+  if ((tid & 31) == 0) vals[gi] = v;
 }
 
 // *out = sum of the first k entries of v (fixed order)

@@ -1,0 +1,635 @@
+// ddlr_persist.cuh -- persistent cooperative kernels: a whole PCG solve
+// (Sec. 5) and the whole Lanczos process (Sec. 4.4) in one launch each.
+//
+// On the shallow factors of multicolour orders every phase of a PCG iteration
+// or of a Lanczos step touches a few hundred thousand rows once; launched as
+// separate kernels, the dependent launch gaps cost more than the work.  Here
+// one CTA per SM stays resident for the whole solve and the phases are
+// separated by a grid-wide barrier.  Scalars (alpha, beta, the convergence
+// and breakdown decisions) are reduced by every CTA from the same per-CTA
+// partials in the same fixed order, so all CTAs take the same branch without
+// a broadcast.  Elementwise work runs on a contiguous row range per CTA
+// (a multiple of 32 rows, one SELL slice per warp); the level solves walk the
+// level-chunk lists of all blocks exactly as the level-by-level kernels do.
+#pragma once
+#include "ddlr_kernels.cuh"
+#include "ddlr_plan.h"
+
+namespace ddlr {
+
+constexpr int kPzThreads = 512;          // threads per CTA of the persistent kernels
+constexpr int kPzMaxLevels = 8;          // deepest factor served (levels per block)
+constexpr unsigned long long kPzWaitNs = 2000000000ull;   // barrier wait limit (2 s)
+
+// arrival counter of the grid barrier (zeroed before each launch) and the
+// shared timeout flag
+struct GridSync {
+  unsigned *count;
+  int *err;
+};
+
+__device__ __forceinline__ unsigned pz_ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long pz_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of a cooperative launch (every CTA resident).  The counter only
+// grows: barrier number e is passed once e * gridDim.x arrivals are visible.
+// Thread 0 waits at most kPzWaitNs, or until another CTA has reported a
+// timeout; then the flag is set and every thread gets false (the kernel
+// returns).  Writes before the barrier are visible to every CTA after it.
+__device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    const unsigned target = epoch * gridDim.x;
+    __threadfence();
+    atomicAdd(g.count, 1u);
+    int ok = 1;
+    unsigned long long t0 = 0;
+    unsigned it = 0;
+    while (pz_ld_acquire(g.count) < target) {
+      if ((++it & 63u) == 0) {
+        if (*(volatile int *)g.err) { ok = 0; break; }
+        const unsigned long long t = pz_clock_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > kPzWaitNs) {
+          atomicExch(g.err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Operator data of the preconditioner in device order (FP64).
+struct PzOp {
+  int n, m, s, k, variant, nL, pstride;
+  double a, ia;
+  int lvl_ptr[kPzMaxLevels + 1];       // level-chunk list offsets, levels of all blocks
+  SolveLayout S;
+  const int4 *chunks;
+  const double *lval, *uval, *dinv;
+  const int *eh_rp, *eh_ci;
+  const double *eh;
+  const int *eht_rp, *eht_ci;
+  const double *eht;
+  const double *U, *coef, *inv1mt, *Hk;
+  const int *a_soff, *a_sw, *a_col;
+  const double *a_val;
+  const double *dsc;                   // D^-1/2 (scaled systems) or null
+  double *part;                        // 3 x gridDim.x x pstride partial sums
+  GridSync gs;
+};
+
+// this CTA's rows [r0, r1) of a vector of N rows
+__device__ __forceinline__ void pz_range(int N, int &r0, int &r1) {
+  const int per = (((N + (int)gridDim.x - 1) / (int)gridDim.x) + 31) & ~31;
+  r0 = min(N, (int)blockIdx.x * per);
+  r1 = min(N, r0 + per);
+}
+
+__device__ __forceinline__ double *pz_buf(const PzOp &O, int slot) {
+  return O.part + (size_t)(slot % 3) * gridDim.x * O.pstride;
+}
+
+// CTA sum of v written to pt[blockIdx.x * pstride] (sm: NT/32 doubles)
+template <int NT>
+__device__ __forceinline__ void pz_put(double v, double *pt, int pstride, double *sm) {
+  v = block_sum<double, NT>(v, sm);
+  if (threadIdx.x == 0) pt[(size_t)blockIdx.x * pstride] = v;
+}
+
+// sum over CTAs of pt[g * pstride] in a fixed order, returned to every thread
+__device__ __forceinline__ double pz_get(const double *pt, int pstride, double *bc) {
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    double s = 0;
+    for (int g = l; g < (int)gridDim.x; g += 32) s += pt[(size_t)g * pstride];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) bc[0] = s;
+  }
+  __syncthreads();
+  const double r = bc[0];
+  __syncthreads();
+  return r;
+}
+
+// out[c] = (coef ? coef[c] : 1) * sum_g pt[g * pstride + c], c < ncol, in shared
+// memory; with H (ncol x ncol row-major): out = H * (those sums)
+template <int NT>
+__device__ __forceinline__ void pz_get_cols(const double *pt, int pstride, int ncol, const double *coef,
+                                            const double *H, double *out, double *tmp) {
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  double *dst = H ? tmp : out;
+  for (int c = wi; c < ncol; c += NT / 32) {
+    double s = 0;
+    for (int g = l; g < (int)gridDim.x; g += 32) s += pt[(size_t)g * pstride + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (l == 0) dst[c] = coef ? coef[c] * s : s;
+  }
+  __syncthreads();
+  if (H) {
+    for (int c = threadIdx.x; c < ncol; c += NT) {
+      double s = 0;
+      for (int b = 0; b < ncol; b++) s += H[c * ncol + b] * tmp[b];
+      out[c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// this CTA's partials pt[blockIdx.x * pstride + c] = sum_{r in [r0,r1)} U[r][c] x_r
+// (U row-major, k columns, x optionally scaled by xsc); red: NT doubles
+template <int NT>
+__device__ __forceinline__ void pz_utx(int k, const double *U, const double *x, const double *xsc, int r0,
+                                       int r1, double *pt, int pstride, double *red) {
+  const int G = NT / k;
+  const int c = threadIdx.x % k, g = threadIdx.x / k;
+  double acc = 0;
+  if (g < G)
+    for (int r = r0 + g; r < r1; r += G) acc += U[(size_t)r * k + c] * (xsc ? x[r] * xsc[r] : x[r]);
+  red[threadIdx.x] = (g < G) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0;
+    for (int gg = 0; gg < G; gg++) s += red[gg * k + threadIdx.x];
+    pt[(size_t)blockIdx.x * pstride + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// One level L of every block: mode 0 forward, 1 backward, 2 forward then
+// backward (the top level).  x is read as xsc .* x when xsc is given.  Rows
+// finalised here (modes 1, 2) add racc_r * (zsc_r) z_r to acc when racc is
+// given.
+template <int NT>
+__device__ __forceinline__ void pz_level(const PzOp &O, int L, int mode, const double *x, const double *xsc,
+                                         double *z, const double *racc, const double *zsc, double &acc) {
+  const int c0 = O.lvl_ptr[L];
+  const unsigned nv = (unsigned)(O.lvl_ptr[L + 1] - c0) * (unsigned)kChunk;
+  for (unsigned v = blockIdx.x * NT + threadIdx.x; v < nv; v += gridDim.x * NT) {
+    const int4 ch = O.chunks[c0 + (int)(v / kChunk)];
+    const int i = (int)(v % kChunk);
+    if (i >= ch.z) continue;
+    const int ii = ch.y + i;
+    const int r = O.S.lvl_row0[ch.x] + ii, sl = O.S.lvl_slice0[ch.x] + (ii >> 5), ln = ii & 31;
+    double zr;
+    if (mode == 1) {
+      const int off = O.S.u_soff[sl] + ln, w = O.S.u_sw[sl];
+      double t = z[r];
+      for (int kk = 0; kk < w; kk++) t -= O.uval[off + kk * 32] * z[O.S.u_col[off + kk * 32]];
+      zr = t * O.dinv[r];
+    } else {
+      const int off = O.S.l_soff[sl] + ln, w = O.S.l_sw[sl];
+      double t = xsc ? x[r] * xsc[r] : x[r];
+      for (int kk = 0; kk < w; kk++) t -= O.lval[off + kk * 32] * z[O.S.l_col[off + kk * 32]];
+      zr = t * O.dinv[r];
+      if (mode == 2) zr = zr * O.dinv[r];
+    }
+    z[r] = zr;
+    if (racc && mode != 0) acc += racc[r] * (zsc ? zsc[r] * zr : zr);
+  }
+}
+
+// z = A0^-1 (xsc .* x) (Sec. 4.2), phases separated by grid barriers; the last
+// phase is left open (the caller adds its own work and barrier)
+template <int NT>
+__device__ __forceinline__ bool pz_a0(const PzOp &O, const double *x, const double *xsc, double *z,
+                                      const double *racc, const double *zsc, double &acc, unsigned &ep) {
+  const int nL = O.nL;
+  for (int L = 0; L + 1 < nL; L++) {
+    pz_level<NT>(O, L, 0, x, xsc, z, nullptr, nullptr, acc);
+    if (!pz_sync(O.gs, ep)) return false;
+  }
+  pz_level<NT>(O, nL - 1, 2, x, xsc, z, racc, zsc, acc);
+  for (int L = nL - 2; L >= 0; L--) {
+    if (!pz_sync(O.gs, ep)) return false;
+    pz_level<NT>(O, L, 1, x, xsc, z, racc, zsc, acc);
+  }
+  return true;
+}
+
+// u = M^-1 (dsc .* x) without the final dsc scaling, DDLR-1 (Algorithm 1,
+// prop. gkt) or DDLR-2 (eq. Form2a).  acc collects sum_r racc_r (dsc_r u_r)
+// over the rows this CTA finalises.  Scratch: z (n), y, w (s), rhs (n).  The
+// last phase is left open.  `slot` is the next partial-sum buffer.
+template <int NT>
+__device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double *u, double *z, double *y,
+                                         double *w, double *rhs, const double *racc, double &acc, unsigned &ep,
+                                         int &slot, double *red, double *vec) {
+  const double *xsc = O.dsc;
+  const int n = O.n, m = O.m, s = O.s, k = O.k;
+  if (O.variant == 2) {
+    int i0, i1;
+    pz_range(n, i0, i1);
+    double *pt = pz_buf(O, slot++);
+    pz_utx<NT>(k, O.U, x, xsc, i0, i1, pt, O.pstride, red);     // t = U^T x, this CTA's rows
+    double dummy = 0;
+    if (!pz_a0<NT>(O, x, xsc, u, nullptr, nullptr, dummy, ep)) return false;
+    if (!pz_sync(O.gs, ep)) return false;
+    pz_get_cols<NT>(pt, O.pstride, k, nullptr, O.Hk, vec, red);   // H_k t
+    for (int r = i0 + threadIdx.x; r < i1; r += NT) {
+      double t = 0;
+      const double *row = O.U + (size_t)r * k;
+      for (int c = 0; c < k; c++) t += row[c] * vec[c];
+      const double ur = u[r] + t;
+      u[r] = ur;
+      if (racc) acc += racc[r] * (O.dsc ? O.dsc[r] * ur : ur);
+    }
+    return true;
+  }
+  double dummy = 0;
+  if (!pz_a0<NT>(O, x, xsc, z, nullptr, nullptr, dummy, ep)) return false;
+  if (!pz_sync(O.gs, ep)) return false;
+  int j0, j1;
+  pz_range(s, j0, j1);
+  for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // y = E^T z
+    double t = 0;
+    for (int q = O.eht_rp[j]; q < O.eht_rp[j + 1]; q++) t += O.eht[q] * z[O.eht_ci[q]];
+    y[j] = O.ia * t - O.a * z[m + j];
+  }
+  __syncthreads();
+  double *pt = pz_buf(O, slot++);
+  pz_utx<NT>(k, O.U, y, nullptr, j0, j1, pt, O.pstride, red);     // D U^T y, this CTA's rows
+  if (!pz_sync(O.gs, ep)) return false;
+  pz_get_cols<NT>(pt, O.pstride, k, O.coef, nullptr, vec, red);
+  const double i1mt = *O.inv1mt;
+  for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // w = G^-1 y; x_C - a w
+    double t = 0;
+    const double *row = O.U + (size_t)j * k;
+    for (int c = 0; c < k; c++) t += row[c] * vec[c];
+    const double wj = i1mt * y[j] + t;
+    w[j] = wj;
+    rhs[m + j] = (xsc ? x[m + j] * xsc[m + j] : x[m + j]) - O.a * wj;
+  }
+  if (!pz_sync(O.gs, ep)) return false;
+  int i0, i1;
+  pz_range(m, i0, i1);
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) {                // x_B + a^-1 Ehat w
+    double t = 0;
+    for (int q = O.eh_rp[i]; q < O.eh_rp[i + 1]; q++) t += O.eh[q] * w[O.eh_ci[q]];
+    rhs[i] = (xsc ? x[i] * xsc[i] : x[i]) + O.ia * t;
+  }
+  if (!pz_sync(O.gs, ep)) return false;
+  return pz_a0<NT>(O, rhs, nullptr, u, racc, O.dsc, acc, ep);
+}
+
+// ------------------------------------------------------------------- PCG
+struct PzPcg {
+  const double *b;
+  double *x, *r, *u, *p0, *p1, *q, *t;
+  double *z, *y, *w, *rhs;
+  PcgState *st;
+  double tol;
+  int maxit;
+};
+
+// z_i of the preconditioned residual (u scaled back on scaled systems)
+__device__ __forceinline__ double pz_zval(const PzOp &O, const double *u, int i) {
+  return O.dsc ? O.dsc[i] * u[i] : u[i];
+}
+
+// PCG from x0 = 0 (Sec. 5) with the stopping rule, true-residual confirmation
+// and restart of the level-by-level path; the final state goes to P.st.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
+  extern __shared__ double pz_sm[];
+  double *red = pz_sm, *bc = pz_sm + NT, *vec = pz_sm + NT + 32;
+  unsigned ep = 0;
+  int slot = 0;
+  const int n = O.n;
+  int i0, i1;
+  pz_range(n, i0, i1);
+  double acc = 0;
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+    const double bi = P.b[i];
+    P.x[i] = 0.0;
+    P.r[i] = bi;
+    P.p0[i] = 0.0;
+    acc += bi * bi;
+  }
+  double *pt = pz_buf(O, slot++);
+  pz_put<NT>(acc, pt, O.pstride, red);
+  if (!pz_sync(O.gs, ep)) return;
+  const double bb = pz_get(pt, O.pstride, bc);
+  const double tol2 = P.tol * P.tol * bb;
+  int its = 0, status = 0;
+  bool done = (bb == 0.0);
+  double rz = 0, beta = 0, rr = bb, rt2 = 0, pq = 0, alpha = 0;
+  if (!done) {
+    acc = 0;
+    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec)) return;
+    pt = pz_buf(O, slot++);
+    pz_put<NT>(acc, pt, O.pstride, red);
+    if (!pz_sync(O.gs, ep)) return;
+    rz = pz_get(pt, O.pstride, bc);
+    if (!(rz == rz) || isinf(rz)) { status = 7; done = true; }
+  }
+  double *pold = P.p0, *pnew = P.p1;
+  bool restart = false;
+  while (!done) {
+    // p = z + beta p_old (into the other buffer), q = A p, p.q
+    acc = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+      const double pi = fma(beta, pold[i], pz_zval(O, P.u, i));
+      pnew[i] = pi;
+      const int g = i >> 5, l = i & 31;
+      const int off = O.a_soff[g] + l, wd = O.a_sw[g];
+      double qi = 0;
+      for (int kk = 0; kk < wd; kk++) {
+        const int cc = O.a_col[off + kk * 32];
+        qi += O.a_val[off + kk * 32] * fma(beta, pold[cc], pz_zval(O, P.u, cc));
+      }
+      P.q[i] = qi;
+      acc += pi * qi;
+    }
+    pt = pz_buf(O, slot++);
+    pz_put<NT>(acc, pt, O.pstride, red);
+    if (!pz_sync(O.gs, ep)) return;
+    pq = pz_get(pt, O.pstride, bc);
+    alpha = rz / pq;
+    if (!(alpha == alpha) || isinf(alpha)) { status = 7; break; }
+    // x += alpha p; r -= alpha q; r.r
+    acc = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+      P.x[i] += alpha * pnew[i];
+      const double ri = P.r[i] - alpha * P.q[i];
+      P.r[i] = ri;
+      acc += ri * ri;
+    }
+    pt = pz_buf(O, slot++);
+    pz_put<NT>(acc, pt, O.pstride, red);
+    if (!pz_sync(O.gs, ep)) return;
+    rr = pz_get(pt, O.pstride, bc);
+    its += 1;
+    if (!(rr == rr) || isinf(rr)) { status = 7; break; }
+    if (rr <= tol2) {
+      // confirm with the true residual t = b - A x
+      acc = 0;
+      for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+        const int g = i >> 5, l = i & 31;
+        const int off = O.a_soff[g] + l, wd = O.a_sw[g];
+        double ax = 0;
+        for (int kk = 0; kk < wd; kk++) ax += O.a_val[off + kk * 32] * P.x[O.a_col[off + kk * 32]];
+        const double tr = P.b[i] - ax;
+        P.t[i] = tr;
+        acc += tr * tr;
+      }
+      pt = pz_buf(O, slot++);
+      pz_put<NT>(acc, pt, O.pstride, red);
+      if (!pz_sync(O.gs, ep)) return;
+      rt2 = pz_get(pt, O.pstride, bc);
+      if (rt2 <= tol2) { status = 0; done = true; break; }
+      restart = true;                       // continue from the true residual
+      if (its >= P.maxit) { status = 5; break; }
+      for (int i = i0 + threadIdx.x; i < i1; i += NT) P.r[i] = P.t[i];
+      if (!pz_sync(O.gs, ep)) return;
+    } else if (its >= P.maxit) {
+      status = 5;
+      break;
+    }
+    acc = 0;
+    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec)) return;
+    pt = pz_buf(O, slot++);
+    pz_put<NT>(acc, pt, O.pstride, red);
+    if (!pz_sync(O.gs, ep)) return;
+    const double rzn = pz_get(pt, O.pstride, bc);
+    beta = restart ? 0.0 : rzn / rz;
+    rz = rzn;
+    restart = false;
+    if (!(rzn == rzn) || isinf(rzn)) { status = 7; break; }
+    double *tp = pold;
+    pold = pnew;
+    pnew = tp;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    PcgState *st = P.st;
+    st->rz = rz; st->pq = pq; st->alpha = alpha; st->beta = beta; st->rr = rr; st->bb = bb;
+    st->tol2 = tol2; st->rt2 = rt2; st->its = its; st->maxit = P.maxit; st->done = 1; st->status = status;
+    st->check_true = 0; st->restart = 0; st->flexible = 0;
+  }
+}
+
+// --------------------------------------------------------------- Lanczos
+struct PzLz {
+  double *Q;
+  long long ld;
+  double *al, *be, *w, *qcur, *qprev, *v, *z, *etop;
+  const int *rank;
+  LzState *st;
+  int check, k;
+  double eps;
+};
+
+// partials of Q_{ncol}^T w over this CTA's rows [r0, r1), warp per column
+template <int NT>
+__device__ __forceinline__ void pz_gemvT(const double *Q, long long ld, int ncol, const double *w, int r0,
+                                         int r1, double *pt, int pstride) {
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int j = wi; j < ncol; j += NT / 32) {
+    const double *q = Q + (long long)j * ld;
+    double acc = 0;
+    for (int r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (l == 0) pt[(size_t)blockIdx.x * pstride + j] = acc;
+  }
+}
+
+// w_r -= sum_j Q[j][r] c_j on this CTA's rows; returns this thread's sum of w_r^2
+template <int NT>
+__device__ __forceinline__ double pz_gemvN(const double *Q, long long ld, int ncol, const double *cs, double *w,
+                                           int r0, int r1) {
+  double ww = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += NT) {
+    double acc = 0;
+    for (int j = 0; j < ncol; j++) acc += Q[(long long)j * ld + r] * cs[j];
+    const double v = w[r] - acc;
+    w[r] = v;
+    ww += v * v;
+  }
+  return ww;
+}
+
+// Two classical Gram-Schmidt passes of w against Q_{ncol} (rows [j0, j1) of
+// this CTA), then ||w||^2 over all rows, returned to every thread.
+template <int NT>
+__device__ __forceinline__ bool pz_cgs2(const PzOp &O, const PzLz &L, int ncol, int j0, int j1, unsigned &ep,
+                                        int &slot, double *red, double *bc, double *cs, double &ww_out) {
+  double *pt = pz_buf(O, slot++);
+  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
+  if (!pz_sync(O.gs, ep)) return false;
+  pz_get_cols<NT>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
+  pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  __syncthreads();
+  pt = pz_buf(O, slot++);
+  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
+  if (!pz_sync(O.gs, ep)) return false;
+  pz_get_cols<NT>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
+  const double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  pt = pz_buf(O, slot++);
+  pz_put<NT>(ww, pt, O.pstride, red);
+  if (!pz_sync(O.gs, ep)) return false;
+  ww_out = pz_get(pt, O.pstride, bc);
+  return true;
+}
+
+// Lanczos with full reorthogonalisation on the operator of DDLR-1 (E^T A0^-1 E)
+// or DDLR-2 (E^T A0^-2 E), from the state in L.st (step j, start vector in
+// qcur and Q column j) until m_max steps, a NaN, or the convergence test of
+// eq. converge every `check` steps (sums of the k largest eigenvalues of T_m
+// and T_{m-1}); breakdown restarts as the level-by-level path does them.
+// Shared memory: NT + 32 + (m_max + 2) + 2 m_max doubles.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
+  extern __shared__ double pz_sm[];
+  double *red = pz_sm, *bc = pz_sm + NT;
+  LzState S0 = *L.st;
+  double *cs = pz_sm + NT + 32, *ea = cs + S0.mmax + 2, *eb2 = ea + S0.mmax;
+  unsigned ep = 0;
+  int slot = 0;
+  const int n = O.n, m = O.m, s = O.s, k = L.k;
+  int j = S0.j, restarts = S0.restarts, conv_m = S0.conv_m, nan_step = S0.nan_step;
+  bool stop = S0.stop != 0;
+  double scale = S0.scale;
+  const int mmax = S0.mmax;
+  int i0, i1, j0, j1;
+  pz_range(n, i0, i1);
+  pz_range(s, j0, j1);
+  double bprev = j > 0 ? L.be[j - 1] : 0.0;
+  double *v = L.v, *z = L.z;
+  while (!stop) {
+    // v = E q_j (eq. EF)
+    for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+      double t;
+      if (i < m) {
+        t = 0;
+        for (int q = O.eh_rp[i]; q < O.eh_rp[i + 1]; q++) t += O.eh[q] * L.qcur[O.eh_ci[q]];
+        t *= O.ia;
+      } else {
+        t = -O.a * L.qcur[i - m];
+      }
+      v[i] = t;
+    }
+    if (!pz_sync(O.gs, ep)) return;
+    double dummy = 0;
+    if (!pz_a0<NT>(O, v, nullptr, z, nullptr, nullptr, dummy, ep)) return;
+    if (!pz_sync(O.gs, ep)) return;
+    double *res = z;
+    if (O.variant == 2) {
+      if (!pz_a0<NT>(O, z, nullptr, v, nullptr, nullptr, dummy, ep)) return;
+      if (!pz_sync(O.gs, ep)) return;
+      res = v;
+    }
+    // w = E^T res, alpha_j = q_j . w
+    double acc = 0;
+    for (int r = j0 + threadIdx.x; r < j1; r += NT) {
+      double t = 0;
+      for (int q = O.eht_rp[r]; q < O.eht_rp[r + 1]; q++) t += O.eht[q] * res[O.eht_ci[q]];
+      const double wr = O.ia * t - O.a * res[m + r];
+      L.w[r] = wr;
+      acc += L.qcur[r] * wr;
+    }
+    double *pt = pz_buf(O, slot++);
+    pz_put<NT>(acc, pt, O.pstride, red);
+    if (!pz_sync(O.gs, ep)) return;
+    const double alpha = pz_get(pt, O.pstride, bc);
+    if (blockIdx.x == 0 && threadIdx.x == 0) L.al[j] = alpha;
+    // three-term recurrence, then two CGS passes against Q_{j+1}
+    for (int r = j0 + threadIdx.x; r < j1; r += NT) {
+      double t = L.w[r] - alpha * L.qcur[r];
+      if (j > 0) t -= bprev * L.qprev[r];
+      L.w[r] = t;
+    }
+    __syncthreads();
+    double ww = 0;
+    if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, ww)) return;
+    const double beta = sqrt(ww);
+    if (blockIdx.x == 0 && threadIdx.x == 0) L.be[j] = beta;
+    if (!(alpha == alpha) || isinf(alpha) || !(beta == beta) || isinf(beta)) {
+      if (nan_step < 0) nan_step = j;
+      stop = true;
+      break;
+    }
+    scale = fmax(scale, fabs(alpha));
+    const bool brk = beta <= 1e-12 * (scale > 0 ? scale : 1.0);
+    if (!brk) {
+      scale = fmax(scale, beta);
+      for (int r = j0 + threadIdx.x; r < j1; r += NT) {
+        const double q1 = L.w[r] / beta;
+        L.Q[(long long)(j + 1) * L.ld + r] = q1;
+        L.qprev[r] = L.qcur[r];
+        L.qcur[r] = q1;
+      }
+      bprev = beta;
+    } else {
+      // restart from SplitMix64 stream seed + restarts (interface nodes in
+      // ascending original index), orthogonalised against Q_{j+1}
+      restarts += 1;
+      for (int r = j0 + threadIdx.x; r < j1; r += NT)
+        L.w[r] = d_sm64_pm1(S0.seed + (unsigned long long)restarts, (unsigned long long)L.rank[r]);
+      __syncthreads();
+      double nn = 0;
+      if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, nn)) return;
+      const double nrm = sqrt(nn);
+      for (int r = j0 + threadIdx.x; r < j1; r += NT) {
+        const double q1 = L.w[r] / nrm;
+        L.Q[(long long)(j + 1) * L.ld + r] = q1;
+        L.qprev[r] = L.qcur[r];
+        L.qcur[r] = q1;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) L.be[j] = 0.0;
+      bprev = 0.0;
+    }
+    j += 1;
+    if (j >= mmax) stop = true;
+    if (!pz_sync(O.gs, ep)) return;
+    if (!stop && L.check > 0 && j % L.check == 0 && j >= k + 1 && j < mmax) {
+      // eq. converge: k largest eigenvalues of T_j and T_{j-1}, warp 0 of
+      // CTA e computes eigenvalue e % k of T_{j - e / k}
+      for (int e = blockIdx.x; e < 2 * k; e += gridDim.x) {
+        if (threadIdx.x < 32) {
+          const int mm = j - e / k;
+          for (int i = threadIdx.x; i < mm; i += 32) {
+            ea[i] = L.al[i];
+            eb2[i] = (i + 1 < mm) ? L.be[i] * L.be[i] : 0.0;
+          }
+          __syncwarp();
+          const double ev = tridiag_eig_warp(mm, ea, eb2, L.be, e % k);
+          if (threadIdx.x == 0) L.etop[e] = ev;
+          __syncwarp();
+        }
+      }
+      if (!pz_sync(O.gs, ep)) return;
+      double s0 = 0, s1 = 0;
+      for (int i = 0; i < k; i++) s0 += L.etop[i];
+      for (int i = 0; i < k; i++) s1 += L.etop[k + i];
+      if (fabs(s0 - s1) < L.eps * fabs(s1)) {
+        conv_m = j;
+        stop = true;
+      }
+      // every CTA has read etop before the next test writes it (barriers of
+      // the next step come first)
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    LzState *st = L.st;
+    st->j = j; st->stop = 1; st->no_break = 1; st->restarts = restarts; st->conv_m = conv_m;
+    st->nan_step = nan_step; st->scale = scale;
+  }
+}
+
+}  // namespace ddlr
