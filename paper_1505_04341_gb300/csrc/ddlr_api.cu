@@ -137,9 +137,23 @@ struct ddlr_ctx {
   int msteps = 0;
   double theta = 0.0;
   int *dflag = nullptr;       // device error flags [0]=breakdown [1]=notspd [2]=eig fail
+  // Lanczos workspace, start vector and step graph, kept for refactors
+  struct LzWork {
+    bool ready = false;
+    double *Q = nullptr, *al = nullptr, *be = nullptr, *cvec = nullptr, *w = nullptr, *qcur = nullptr,
+           *qprev = nullptr, *nrm = nullptr, *ework = nullptr, *etop = nullptr, *evals = nullptr,
+           *esum = nullptr, *eY = nullptr, *q0 = nullptr;
+    double *V = nullptr, *EV = nullptr, *vc = nullptr, *ev = nullptr, *uc = nullptr, *kp = nullptr, *hw = nullptr;
+    int *rank = nullptr;
+    LzState *st = nullptr;
+    LzState *h_st = nullptr;          // pinned
+    cudaEvent_t ev_chk = nullptr, ev_done = nullptr;
+    cudaGraphExec_t exec = nullptr;   // one captured step (kernel-per-phase path)
+  } lw;
   // persistent cooperative kernels (shallow factors): one CTA per SM
   double *pz_part = nullptr;  // 3 x pz_grid x pz_pstride partial sums
   unsigned *pz_bar = nullptr; // grid-barrier arrival counter
+  unsigned char *pz_lvl0 = nullptr;  // rows on the first level of their block
   int pz_grid = 0, pz_pstride = 0, pz_mmax = 0;
   bool pz_pcg = false, pz_lz = false;
   // workspaces
@@ -502,62 +516,75 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
   mmax = std::max(mmax, k);
   const int check = c->opt.lanczos_check;
   const double eps = c->opt.lanczos_eps;
-  std::vector<void *> tmp;
-  auto talloc = [&](size_t bytes) {
-    void *p = nullptr;
-    ck(cudaMalloc(&p, bytes), "cudaMalloc");
-    tmp.push_back(p);
-    return p;
-  };
-  cudaGraphExec_t exec = nullptr;
-  cudaEvent_t ev_chk = nullptr, ev_done = nullptr;
+  auto &W = c->lw;
   cudaStream_t user = c->stream;
   ddlr_status st = DDLR_OK;
   try {
+    if (!W.ready) {
+      // first run: workspace for m_max steps, the rank of every interface node
+      // in ascending original index and the start vector (SplitMix64 stream
+      // `seed` drawn in that order, normalised); refactors reuse them
+      W.Q = c->alloc<double>(size_t(s) * size_t(mmax + 1));
+      W.al = c->alloc<double>(mmax + 1);
+      W.be = c->alloc<double>(mmax + 1);
+      W.cvec = c->alloc<double>(mmax + 2);
+      W.w = c->alloc<double>(s);
+      W.qcur = c->alloc<double>(s);
+      W.qprev = c->alloc<double>(s);
+      W.q0 = c->alloc<double>(s);
+      W.nrm = c->alloc<double>(4);
+      W.rank = c->alloc<int>(s);
+      W.st = c->alloc<LzState>(1);
+      W.ework = c->alloc<double>(5 * size_t(mmax) * k);
+      W.etop = c->alloc<double>(2 * k + 1);
+      W.evals = c->alloc<double>(mmax);
+      W.esum = c->alloc<double>(2);
+      W.eY = c->alloc<double>(size_t(mmax) * k);
+      if (c->opt.variant == 2) {
+        W.V = c->alloc<double>(size_t(s) * k);
+        W.EV = c->alloc<double>(size_t(n) * k);
+        W.vc = c->alloc<double>(s);
+        W.ev = c->alloc<double>(n);
+        W.uc = c->alloc<double>(n);
+        W.kp = c->alloc<double>(size_t(kRedGrid) * k * k);
+        W.hw = c->alloc<double>(size_t(k) * k + k);
+      }
+      ck(cudaMallocHost(&W.h_st, sizeof(LzState)), "cudaMallocHost");
+      ck(cudaEventCreateWithFlags(&W.ev_chk, cudaEventDisableTiming), "event");
+      ck(cudaEventCreateWithFlags(&W.ev_done, cudaEventDisableTiming), "event");
+      std::vector<int> rank(s);
+      {
+        std::vector<std::pair<int, int>> o(s);
+        for (int j = 0; j < s; j++) o[j] = {P.perm[m0 + j], j};
+        std::sort(o.begin(), o.end());
+        for (int r = 0; r < s; r++) rank[o[r].second] = r;
+      }
+      std::vector<double> byrank(s), hv(s);
+      double nn = 0;
+      for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }
+      nn = std::sqrt(nn);
+      for (int j = 0; j < s; j++) hv[j] = byrank[rank[j]] / nn;
+      ck(cudaMemcpyAsync(W.q0, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+      ck(cudaMemcpyAsync(W.rank, rank.data(), sizeof(int) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
+      ck(cudaStreamSynchronize(c->stream), "sync");     // host vectors above are locals
+      W.ready = true;
+    }
     LzBufs L;
     L.mmax = mmax;
     L.ld = s;
-    L.Q = (double *)talloc(sizeof(double) * size_t(s) * size_t(mmax + 1));
-    L.al = (double *)talloc(sizeof(double) * (mmax + 1));
-    L.be = (double *)talloc(sizeof(double) * (mmax + 1));
-    L.cvec = (double *)talloc(sizeof(double) * (mmax + 2));
-    L.w = (double *)talloc(sizeof(double) * s);
-    L.qcur = (double *)talloc(sizeof(double) * s);
-    L.qprev = (double *)talloc(sizeof(double) * s);
-    L.nrm = (double *)talloc(sizeof(double) * 4);
-    L.rank = (int *)talloc(sizeof(int) * s);
-    L.st = (LzState *)talloc(sizeof(LzState));
-    double *ework = (double *)talloc(sizeof(double) * 5 * size_t(mmax) * k);
-    double *etop = (double *)talloc(sizeof(double) * (2 * k + 1));
-    double *evals = (double *)talloc(sizeof(double) * mmax);
-    double *esum = (double *)talloc(sizeof(double) * 2);
-    double *eY = (double *)talloc(sizeof(double) * size_t(mmax) * k);
-    ck(cudaEventCreateWithFlags(&ev_chk, cudaEventDisableTiming), "event");
-    ck(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming), "event");
+    L.Q = W.Q; L.al = W.al; L.be = W.be; L.cvec = W.cvec; L.w = W.w; L.qcur = W.qcur; L.qprev = W.qprev;
+    L.nrm = W.nrm; L.rank = W.rank; L.st = W.st;
+    double *ework = W.ework, *etop = W.etop, *evals = W.evals, *esum = W.esum, *eY = W.eY;
+    cudaEvent_t ev_chk = W.ev_chk, ev_done = W.ev_done;
     ck(cudaMemsetAsync(L.be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
     ck(cudaMemsetAsync(L.qprev, 0, sizeof(double) * s, c->stream), "memset");
-    // start vector: SplitMix64 stream `seed`, drawn for the interface nodes in
-    // ascending original index, normalised
-    std::vector<int> rank(s);
-    {
-      std::vector<std::pair<int, int>> o(s);
-      for (int j = 0; j < s; j++) o[j] = {P.perm[m0 + j], j};
-      std::sort(o.begin(), o.end());
-      for (int r = 0; r < s; r++) rank[o[r].second] = r;
-    }
-    std::vector<double> byrank(s), hv(s);
-    double nn = 0;
-    for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }
-    nn = std::sqrt(nn);
-    for (int j = 0; j < s; j++) hv[j] = byrank[rank[j]] / nn;
-    ck(cudaMemcpyAsync(L.Q, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
-    ck(cudaMemcpyAsync(L.qcur, hv.data(), sizeof(double) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
-    ck(cudaMemcpyAsync(L.rank, rank.data(), sizeof(int) * s, cudaMemcpyHostToDevice, c->stream), "H2D");
-    LzState h0{};
+    ck(cudaMemcpyAsync(L.Q, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    ck(cudaMemcpyAsync(L.qcur, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    LzState &h0 = *W.h_st;
+    h0 = LzState{};
     h0.j = 0; h0.stop = 0; h0.no_break = 1; h0.restarts = 0; h0.conv_m = 0; h0.nan_step = -1;
     h0.mmax = mmax; h0.scale = 0.0; h0.seed = c->opt.seed;
     ck(cudaMemcpyAsync(L.st, &h0, sizeof(h0), cudaMemcpyHostToDevice, c->stream), "H2D");
-    ck(cudaStreamSynchronize(c->stream), "sync");       // host buffers above are locals
 
     const char *ng = getenv("DDLR_NO_GRAPH");
     // every step and test in one persistent kernel when the factors are shallow
@@ -575,27 +602,29 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       ck(cudaEventRecord(c->ev_fork, user), "event");
       ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
       c->stream = c->gstream;
-      const long long l0 = c->launches;
-      const std::vector<long long> f0 = c->fam_cnt;
-      ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
-      lanczos_step(c, L);
-      cudaGraph_t g = nullptr;
-      ck(cudaStreamEndCapture(c->stream, &g), "capture");
-      cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      ck(e, "cudaGraphInstantiate");
-      c->lz_nodes = c->launches - l0;
-      c->lz_fam_nodes.assign(c->fam_cnt.size(), 0);
-      for (size_t i = 0; i < c->fam_cnt.size(); i++) c->lz_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
-      c->launches = l0;
-      for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
-      for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+      if (!W.exec) {
+        const long long l0 = c->launches;
+        const std::vector<long long> f0 = c->fam_cnt;
+        ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+        lanczos_step(c, L);
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamEndCapture(c->stream, &g), "capture");
+        cudaError_t e = cudaGraphInstantiate(&W.exec, g, 0);
+        cudaGraphDestroy(g);
+        ck(e, "cudaGraphInstantiate");
+        c->lz_nodes = c->launches - l0;
+        c->lz_fam_nodes.assign(c->fam_cnt.size(), 0);
+        for (size_t i = 0; i < c->fam_cnt.size(); i++) c->lz_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+        c->launches = l0;
+        for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+        for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+      }
     }
     int *hstop = reinterpret_cast<int *>(c->h_pin + 8);
     bool pending = false;
     for (int j = 0; j < (persist ? 0 : mmax); j++) {
       if (use_graph) {
-        ck(cudaGraphLaunch(exec, c->stream), "cudaGraphLaunch");
+        ck(cudaGraphLaunch(W.exec, c->stream), "cudaGraphLaunch");
         c->launches += c->lz_nodes;
         for (size_t i = 0; i < c->lz_fam_nodes.size(); i++) c->fam_cnt[i] += c->lz_fam_nodes[i];
       } else {
@@ -609,10 +638,10 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
         }
         ck(cudaEventRecord(ev_chk, c->stream), "event");
         ck(cudaStreamWaitEvent(c->stream2, ev_chk, 0), "wait");
-        const size_t smk = 2 * mm * sizeof(double);
-        KL(c, "eig_check", c->stream2, k_tridiag_values, k, 32, smk, mm, L.al, L.be, k, etop);
+        const size_t smk = (2 * mm + 2) * sizeof(double);
+        KL(c, "eig_check", c->stream2, k_tridiag_values, k, kEigPoints, smk, mm, L.al, L.be, k, etop);
         KL(c, "eig_check", c->stream2, k_sum_first, 1, 32, 0, k, etop, esum);
-        KL(c, "eig_check", c->stream2, k_tridiag_values, k, 32, smk, mm - 1, L.al, L.be, k, etop);
+        KL(c, "eig_check", c->stream2, k_tridiag_values, k, kEigPoints, smk, mm - 1, L.al, L.be, k, etop);
         KL(c, "eig_check", c->stream2, k_sum_first, 1, 32, 0, k, etop, esum + 1);
         KL(c, "eig_check", c->stream2, k_lz_converged, 1, 32, 0, esum, eps, mm, L.st);
         ck(cudaMemcpyAsync(hstop, reinterpret_cast<const char *>(L.st) + offsetof(LzState, stop), sizeof(int),
@@ -635,7 +664,8 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     if (st == DDLR_OK) {
       c->msteps = mm;
       const int nvals = mm;
-      KL(c, "eig", c->stream, k_tridiag_values, nvals, 32, 2 * mm * sizeof(double), mm, L.al, L.be, nvals, evals);
+      KL(c, "eig", c->stream, k_tridiag_values, nvals, kEigPoints, (2 * mm + 2) * sizeof(double), mm, L.al, L.be,
+         nvals, evals);
       KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, L.al, L.be, k, evals, eY, ework);
       c->ritz.assign(nvals, 0.0);
       read_dev(c, c->ritz.data(), evals, sizeof(double) * nvals);
@@ -647,13 +677,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
         read_dev(c, &c->theta, c->theta_d, sizeof(double));
       } else {
         // V_k = Q_m Y_k; U_k = A0^-1 E V_k; H_k = (I - U_k^T E V_k)^-1
-        double *V = (double *)talloc(sizeof(double) * size_t(s) * k);
-        double *EV = (double *)talloc(sizeof(double) * size_t(n) * k);
-        double *vc = (double *)talloc(sizeof(double) * s);
-        double *ev = (double *)talloc(sizeof(double) * n);
-        double *uc = (double *)talloc(sizeof(double) * n);
-        double *kp = (double *)talloc(sizeof(double) * size_t(kRedGrid) * k * k);
-        double *hw = (double *)talloc(sizeof(double) * (k * k + k));
+        double *V = W.V, *EV = W.EV, *vc = W.vc, *ev = W.ev, *uc = W.uc, *kp = W.kp, *hw = W.hw;
         KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, Q, (long long)s, eY, V);
         const double a = c->opt.alpha;
         for (int cc = 0; cc < k; cc++) {
@@ -680,16 +704,8 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     cudaStreamSynchronize(c->stream);
     cudaStreamSynchronize(c->stream2);
     cudaStreamSynchronize(c->gstream);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (ev_chk) cudaEventDestroy(ev_chk);
-    if (ev_done) cudaEventDestroy(ev_done);
-    for (void *p : tmp) cudaFree(p);
     throw;
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  cudaEventDestroy(ev_chk);
-  cudaEventDestroy(ev_done);
-  for (void *p : tmp) cudaFree(p);
   return st;
 }
 
@@ -816,6 +832,13 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   if (!c->pz_pcg && !c->pz_lz) return;
   c->pz_part = c->alloc<double>(size_t(3) * c->pz_grid * c->pz_pstride);
   c->pz_bar = c->alloc<unsigned>(1);
+  std::vector<unsigned char> f0(P.n, 0);
+  for (int b = 0; b + 1 < int(P.blk_lvl0.size()); b++) {
+    const int l0 = P.blk_lvl0[b];
+    if (l0 >= P.blk_lvl0[b + 1]) continue;
+    for (int r = P.lvl_row0[l0]; r < P.lvl_row0[l0] + P.lvl_nrows[l0]; r++) f0[r] = 1;
+  }
+  c->pz_lvl0 = c->upload(f0);
 }
 
 PzOp make_pzop(ddlr_ctx *c) {
@@ -834,6 +857,8 @@ PzOp make_pzop(ddlr_ctx *c) {
   O.U = c->U64; O.coef = c->coef64; O.inv1mt = c->inv1mt64; O.Hk = c->Hk64;
   O.a_soff = c->a_soff; O.a_sw = c->a_sw; O.a_col = c->a_col; O.a_val = c->a_val;
   O.dsc = c->dsc_dev;
+  O.lvl0 = c->pz_lvl0;
+  O.fuse0 = O.nL >= 2 ? 1 : 0;
   O.part = c->pz_part;
   O.gs.count = c->pz_bar;
   O.gs.err = c->dflag + 3;
@@ -1944,6 +1969,10 @@ ddlr_status ddlr_destroy(ddlr_handle c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  if (c->lw.exec) cudaGraphExecDestroy(c->lw.exec);
+  if (c->lw.ev_chk) cudaEventDestroy(c->lw.ev_chk);
+  if (c->lw.ev_done) cudaEventDestroy(c->lw.ev_done);
+  if (c->lw.h_st) cudaFreeHost(c->lw.h_st);
   if (c->gstream) { cudaStreamSynchronize(c->gstream); cudaStreamDestroy(c->gstream); }
   if (c->stream2) cudaStreamDestroy(c->stream2);
   delete c;

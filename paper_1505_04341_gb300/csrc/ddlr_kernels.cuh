@@ -1101,79 +1101,106 @@ __global__ void k_lz_converged(const double *esum, double eps, int m, LzState *s
 // root are slow on this part, and one-thread QR sweeps were the bottleneck.
 
 // number of eigenvalues of T smaller than x: sign changes of the three-term
-// Sturm recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, rescaled by
-// powers of two (exact) to stay in range; a zero term counts as a change
+// Sturm recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}; a zero term is
+// replaced by a tiny value of the opposite sign.  Every 8 terms |p| is brought
+// back into [2^-500, 2^500] by an exact power-of-two rescaling (T comes from
+// a bounded operator: its entries are O(1), so 8 terms stay far inside the
+// double range).  Signs and zero tests read the bit pattern (integer pipe):
+// on this part every FP64 instruction takes a long issue slot of the narrow
+// FP64 pipe, and only the three of the recurrence remain on the path.
+__device__ __forceinline__ bool neg_nonzero(long long b) { return b < 0 && (b << 1) != 0; }
 __device__ __forceinline__ int sturm_count(int m, const double *a, const double *b2, double x) {
+  constexpr long long kBig = 0x5F30000000000000LL;     // bits of 2^500
+  constexpr long long kSmall = 0x20B0000000000000LL;   // bits of 2^-500
   double pm = 1.0, p = a[0] - x;
-  int cnt = 0;
   if (p == 0.0) p = -1e-300;
-  if (p < 0.0) cnt++;
+  long long pb = __double_as_longlong(p);
+  int cnt = neg_nonzero(pb) ? 1 : 0;
   for (int i = 1; i < m; i++) {
     double q = fma(a[i] - x, p, -b2[i - 1] * pm);
-    if (q == 0.0) q = (p > 0.0) ? -1e-300 * fabs(p) : 1e-300 * fabs(p);
-    if ((q < 0.0) != (p < 0.0)) cnt++;
+    long long qb = __double_as_longlong(q);
+    if ((qb << 1) == 0) {
+      q = neg_nonzero(pb) ? 1e-300 * fabs(p) : -1e-300 * fabs(p);
+      qb = __double_as_longlong(q);
+    }
+    cnt += neg_nonzero(qb) != neg_nonzero(pb) ? 1 : 0;
     pm = p;
     p = q;
-    const double ap = fabs(p);
-    if (ap > 0x1.0p+500) { p *= 0x1.0p-500; pm *= 0x1.0p-500; }
-    else if (ap < 0x1.0p-500) { p *= 0x1.0p+500; pm *= 0x1.0p+500; }
+    pb = qb;
+    if ((i & 7) == 0) {
+      const long long ab = qb & 0x7FFFFFFFFFFFFFFFLL;
+      if (ab > kBig) { p *= 0x1.0p-500; pm *= 0x1.0p-500; pb = __double_as_longlong(p); }
+      else if (ab < kSmall) { p *= 0x1.0p+500; pm *= 0x1.0p+500; pb = __double_as_longlong(p); }
+    }
   }
   return cnt;
 }
 
-// Eigenvalue gi (0 = largest) of T_m by Sturm-sequence multisection, computed
-// by the 32 lanes of the calling warp (all get the value): each round the
-// lanes evaluate 32 interior points of the current bracket (5 bits per round),
-// starting from the Gershgorin interval.  a, b2: diagonal and squared
-// off-diagonal (b2[i] = be[i]^2, i + 1 < m); be: off-diagonal.
-__device__ __forceinline__ double tridiag_eig_warp(int m, const double *a, const double *b2,
-                                                   const double *be, int gi) {
-  const int lane = threadIdx.x & 31;
-  double lo = 1e300, hi = -1e300;
-  for (int i = lane; i < m; i += 32) {
-    const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
+// Eigenvalue gi (0 = largest) of T_m by Sturm-sequence multisection.  Every
+// thread of the CTA calls it; the first P threads (P a multiple of 32, one
+// warp per SM sub-partition for P = 128) evaluate P interior points of the
+// current bracket per round (log2(P + 1) bits per round), starting from the
+// Gershgorin interval widened by 1e-9 of its span.  a, b2: diagonal and
+// squared off-diagonal (b2[i] = be[i]^2, i + 1 < m) in shared memory; be:
+// off-diagonal; bc: 2 doubles of shared memory.  All threads get the value.
+template <int P, int ROUNDS>
+__device__ __forceinline__ double tridiag_eig_cta(int m, const double *a, const double *b2,
+                                                  const double *be, int gi, double *bc) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = tid; i < m; i += 32) {
+      const double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < m ? fabs(be[i]) : 0.0);
+      lo = fmin(lo, a[i] - r);
+      hi = fmax(hi, a[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (tid == 0) { bc[0] = lo; bc[1] = hi; }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
+  __syncthreads();
+  const double lo = bc[0], hi = bc[1];
+  __syncthreads();
   const double span = fmax(hi - lo, 1e-300);
   double blo = lo - 1e-9 * span, bhi = hi + 1e-9 * span;
   const int target = m - 1 - gi;
-  for (int round = 0; round < 12; round++) {
-    const double x = blo + (bhi - blo) * double(lane + 1) * (1.0 / 33.0);
-    const int c = sturm_count(m, a, b2, x);
-    // lanes whose point has count <= target lie below the eigenvalue
-    const unsigned below = __ballot_sync(0xffffffffu, c <= target);
-    const int nb = __popc(below);            // counts are monotone in x
-    const double nlo = nb > 0 ? blo + (bhi - blo) * double(nb) * (1.0 / 33.0) : blo;
-    const double nhi = nb < 32 ? blo + (bhi - blo) * double(nb + 1) * (1.0 / 33.0) : bhi;
+  constexpr double kStep = 1.0 / double(P + 1);
+  for (int round = 0; round < ROUNDS; round++) {
+    int below = 0;
+    if (tid < P) {
+      const double x = blo + (bhi - blo) * double(tid + 1) * kStep;
+      below = sturm_count(m, a, b2, x) <= target;   // points below the eigenvalue
+    }
+    const int nb = __syncthreads_count(below);        // counts are monotone in x
+    const double nlo = nb > 0 ? blo + (bhi - blo) * double(nb) * kStep : blo;
+    const double nhi = nb < P ? blo + (bhi - blo) * double(nb + 1) * kStep : bhi;
     blo = nlo;
     bhi = nhi;
   }
   return 0.5 * (blo + bhi);
 }
+constexpr int kEigPoints = 128;   // points per round (4 warps)
+constexpr int kEigRounds = 9;     // 9 x log2(129) = 63 bits
 
-// The nv largest eigenvalues of T_m, descending, into vals.  One warp per
-// eigenvalue (CTA = 4 warps, grid covers nv).  Spreading the eigenvalues over
-// many SMs matters because the FP64 pipe of one SM is narrow.  Dynamic shared
-// memory: 2m doubles.
-__global__ void k_tridiag_values(int m, const double *al, const double *be,
-                                 int nv, double *vals) {
+// The nv largest eigenvalues of T_m, descending, into vals: CTA gi computes
+// eigenvalue gi with kEigPoints threads.  Spreading the eigenvalues over
+// many SMs matters because the FP64 pipe of one SM is narrow.  Dynamic
+// shared memory: 2m + 2 doubles.
+__global__ void __launch_bounds__(kEigPoints) k_tridiag_values(int m, const double *al, const double *be,
+                                                                int nv, double *vals) {
   extern __shared__ double shm[];
-  double *a = shm, *b2 = shm + m;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < m; i += blockDim.x) {
+  double *a = shm, *b2 = shm + m, *bc = shm + 2 * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
     a[i] = al[i];
     b2[i] = (i + 1 < m) ? be[i] * be[i] : 0.0;
   }
   __syncthreads();
-  const int gi = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);   // eigenvalue index
+  const int gi = blockIdx.x;
   if (gi >= nv) return;
-  const double v = tridiag_eig_warp(m, a, b2, be, gi);
-  if ((tid & 31) == 0) vals[gi] = v;
+  const double v = tridiag_eig_cta<kEigPoints, kEigRounds>(m, a, b2, be, gi, bc);
+  if (threadIdx.x == 0) vals[gi] = v;
 }
 
 // *out = sum of the first k entries of v (fixed order)

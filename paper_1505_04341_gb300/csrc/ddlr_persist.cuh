@@ -21,6 +21,11 @@ constexpr int kPzThreads = 512;          // threads per CTA of the persistent ke
 constexpr int kPzMaxLevels = 8;          // deepest factor served (levels per block)
 constexpr unsigned long long kPzWaitNs = 2000000000ull;   // barrier wait limit (2 s)
 
+// loads of operator data, which no kernel writes while a persistent kernel
+// runs: through the read-only path, so they can stay in L1 across barriers
+template <typename T>
+__device__ __forceinline__ T ro(const T *p) { return __ldg(p); }
+
 // arrival counter of the grid barrier (zeroed before each launch) and the
 // shared timeout flag
 struct GridSync {
@@ -40,7 +45,8 @@ __device__ __forceinline__ unsigned long long pz_clock_ns() {
 }
 
 // Grid barrier of a cooperative launch (every CTA resident).  The counter only
-// grows: barrier number e is passed once e * gridDim.x arrivals are visible.
+// grows: barrier number e is passed once e * gridDim.x arrivals are visible
+// (release add on arrival, acquire loads while waiting).
 // Thread 0 waits at most kPzWaitNs, or until another CTA has reported a
 // timeout; then the flag is set and every thread gets false (the kernel
 // returns).  Writes before the barrier are visible to every CTA after it.
@@ -50,8 +56,9 @@ __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
   ++epoch;
   if (threadIdx.x == 0) {
     const unsigned target = epoch * gridDim.x;
-    __threadfence();
-    atomicAdd(g.count, 1u);
+    // release: the CTA's writes (ordered before by the CTA barrier) become
+    // visible to every CTA whose acquire load sees this arrival
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(g.count) : "memory");
     int ok = 1;
     unsigned long long t0 = 0;
     unsigned it = 0;
@@ -68,7 +75,6 @@ __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -91,9 +97,20 @@ struct PzOp {
   const int *a_soff, *a_sw, *a_col;
   const double *a_val;
   const double *dsc;                   // D^-1/2 (scaled systems) or null
+  const unsigned char *lvl0;           // 1 for rows on the first level of their block
+  int fuse0;                           // >= 2 levels: the producer of a solve's input
+                                       // also does its first forward level
   double *part;                        // 3 x gridDim.x x pstride partial sums
   GridSync gs;
 };
+
+// The first forward level of z = A0^-1 x for row r, done by the phase that
+// produces x_r (xv = x_r, already scaled): rows on the first level of their
+// block have no lower neighbours, so z_r = x_r / L_rr, exactly what the level
+// solve computes for them.
+__device__ __forceinline__ void pz_l0(const PzOp &O, int r, double xv, double *z) {
+  if (O.fuse0 && ro(O.lvl0 + r)) z[r] = xv * ro(O.dinv + r);
+}
 
 // this CTA's rows [r0, r1) of a vector of N rows
 __device__ __forceinline__ void pz_range(int N, int &r0, int &r1) {
@@ -139,13 +156,13 @@ __device__ __forceinline__ void pz_get_cols(const double *pt, int pstride, int n
     double s = 0;
     for (int g = l; g < (int)gridDim.x; g += 32) s += pt[(size_t)g * pstride + c];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (l == 0) dst[c] = coef ? coef[c] * s : s;
+    if (l == 0) dst[c] = coef ? ro(coef + c) * s : s;
   }
   __syncthreads();
   if (H) {
     for (int c = threadIdx.x; c < ncol; c += NT) {
       double s = 0;
-      for (int b = 0; b < ncol; b++) s += H[c * ncol + b] * tmp[b];
+      for (int b = 0; b < ncol; b++) s += ro(H + c * ncol + b) * tmp[b];
       out[c] = s;
     }
     __syncthreads();
@@ -161,7 +178,7 @@ __device__ __forceinline__ void pz_utx(int k, const double *U, const double *x, 
   const int c = threadIdx.x % k, g = threadIdx.x / k;
   double acc = 0;
   if (g < G)
-    for (int r = r0 + g; r < r1; r += G) acc += U[(size_t)r * k + c] * (xsc ? x[r] * xsc[r] : x[r]);
+    for (int r = r0 + g; r < r1; r += G) acc += ro(U + (size_t)r * k + c) * (xsc ? x[r] * ro(xsc + r) : x[r]);
   red[threadIdx.x] = (g < G) ? acc : 0.0;
   __syncthreads();
   if (threadIdx.x < k) {
@@ -175,50 +192,57 @@ __device__ __forceinline__ void pz_utx(int k, const double *U, const double *x, 
 // One level L of every block: mode 0 forward, 1 backward, 2 forward then
 // backward (the top level).  x is read as xsc .* x when xsc is given.  Rows
 // finalised here (modes 1, 2) add racc_r * (zsc_r) z_r to acc when racc is
-// given.
+// given; z2 (level 0, backward) receives the first forward level of a solve
+// whose input is z.
 template <int NT>
 __device__ __forceinline__ void pz_level(const PzOp &O, int L, int mode, const double *x, const double *xsc,
-                                         double *z, const double *racc, const double *zsc, double &acc) {
+                                         double *z, const double *racc, const double *zsc, double &acc,
+                                         double *z2) {
   const int c0 = O.lvl_ptr[L];
   const unsigned nv = (unsigned)(O.lvl_ptr[L + 1] - c0) * (unsigned)kChunk;
   for (unsigned v = blockIdx.x * NT + threadIdx.x; v < nv; v += gridDim.x * NT) {
-    const int4 ch = O.chunks[c0 + (int)(v / kChunk)];
+    const int4 ch = ro(O.chunks + c0 + (int)(v / kChunk));
     const int i = (int)(v % kChunk);
     if (i >= ch.z) continue;
     const int ii = ch.y + i;
-    const int r = O.S.lvl_row0[ch.x] + ii, sl = O.S.lvl_slice0[ch.x] + (ii >> 5), ln = ii & 31;
+    const int r = ro(O.S.lvl_row0 + ch.x) + ii, sl = ro(O.S.lvl_slice0 + ch.x) + (ii >> 5), ln = ii & 31;
     double zr;
+    const double dr = ro(O.dinv + r);
     if (mode == 1) {
-      const int off = O.S.u_soff[sl] + ln, w = O.S.u_sw[sl];
+      const int off = ro(O.S.u_soff + sl) + ln, w = ro(O.S.u_sw + sl);
       double t = z[r];
-      for (int kk = 0; kk < w; kk++) t -= O.uval[off + kk * 32] * z[O.S.u_col[off + kk * 32]];
-      zr = t * O.dinv[r];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.S.u_col + off + kk * 32)];
+      zr = t * dr;
     } else {
-      const int off = O.S.l_soff[sl] + ln, w = O.S.l_sw[sl];
-      double t = xsc ? x[r] * xsc[r] : x[r];
-      for (int kk = 0; kk < w; kk++) t -= O.lval[off + kk * 32] * z[O.S.l_col[off + kk * 32]];
-      zr = t * O.dinv[r];
-      if (mode == 2) zr = zr * O.dinv[r];
+      const int off = ro(O.S.l_soff + sl) + ln, w = ro(O.S.l_sw + sl);
+      double t = xsc ? x[r] * ro(xsc + r) : x[r];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.S.l_col + off + kk * 32)];
+      zr = t * dr;
+      if (mode == 2) zr = zr * dr;
     }
     z[r] = zr;
-    if (racc && mode != 0) acc += racc[r] * (zsc ? zsc[r] * zr : zr);
+    if (racc && mode != 0) acc += racc[r] * (zsc ? ro(zsc + r) * zr : zr);
+    if (z2) z2[r] = zr * dr;          // first forward level of a solve with input z
   }
 }
 
 // z = A0^-1 (xsc .* x) (Sec. 4.2), phases separated by grid barriers; the last
-// phase is left open (the caller adds its own work and barrier)
+// phase is left open (the caller adds its own work and barrier).  l0_done:
+// the producer of x has already done the first forward level (pz_l0).  z2:
+// see pz_level (only with fuse0).
 template <int NT>
 __device__ __forceinline__ bool pz_a0(const PzOp &O, const double *x, const double *xsc, double *z,
-                                      const double *racc, const double *zsc, double &acc, unsigned &ep) {
+                                      const double *racc, const double *zsc, double &acc, unsigned &ep,
+                                      bool l0_done, double *z2 = nullptr) {
   const int nL = O.nL;
-  for (int L = 0; L + 1 < nL; L++) {
-    pz_level<NT>(O, L, 0, x, xsc, z, nullptr, nullptr, acc);
+  for (int L = l0_done ? 1 : 0; L + 1 < nL; L++) {
+    pz_level<NT>(O, L, 0, x, xsc, z, nullptr, nullptr, acc, nullptr);
     if (!pz_sync(O.gs, ep)) return false;
   }
-  pz_level<NT>(O, nL - 1, 2, x, xsc, z, racc, zsc, acc);
+  pz_level<NT>(O, nL - 1, 2, x, xsc, z, racc, zsc, acc, nullptr);
   for (int L = nL - 2; L >= 0; L--) {
     if (!pz_sync(O.gs, ep)) return false;
-    pz_level<NT>(O, L, 1, x, xsc, z, racc, zsc, acc);
+    pz_level<NT>(O, L, 1, x, xsc, z, racc, zsc, acc, L == 0 ? z2 : nullptr);
   }
   return true;
 }
@@ -230,7 +254,7 @@ __device__ __forceinline__ bool pz_a0(const PzOp &O, const double *x, const doub
 template <int NT>
 __device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double *u, double *z, double *y,
                                          double *w, double *rhs, const double *racc, double &acc, unsigned &ep,
-                                         int &slot, double *red, double *vec) {
+                                         int &slot, double *red, double *vec, bool l0_done) {
   const double *xsc = O.dsc;
   const int n = O.n, m = O.m, s = O.s, k = O.k;
   if (O.variant == 2) {
@@ -239,27 +263,28 @@ __device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double 
     double *pt = pz_buf(O, slot++);
     pz_utx<NT>(k, O.U, x, xsc, i0, i1, pt, O.pstride, red);     // t = U^T x, this CTA's rows
     double dummy = 0;
-    if (!pz_a0<NT>(O, x, xsc, u, nullptr, nullptr, dummy, ep)) return false;
+    if (!pz_a0<NT>(O, x, xsc, u, nullptr, nullptr, dummy, ep, l0_done)) return false;
     if (!pz_sync(O.gs, ep)) return false;
     pz_get_cols<NT>(pt, O.pstride, k, nullptr, O.Hk, vec, red);   // H_k t
     for (int r = i0 + threadIdx.x; r < i1; r += NT) {
       double t = 0;
       const double *row = O.U + (size_t)r * k;
-      for (int c = 0; c < k; c++) t += row[c] * vec[c];
+      for (int c = 0; c < k; c++) t += ro(row + c) * vec[c];
       const double ur = u[r] + t;
       u[r] = ur;
-      if (racc) acc += racc[r] * (O.dsc ? O.dsc[r] * ur : ur);
+      if (racc) acc += racc[r] * (O.dsc ? ro(O.dsc + r) * ur : ur);
     }
     return true;
   }
   double dummy = 0;
-  if (!pz_a0<NT>(O, x, xsc, z, nullptr, nullptr, dummy, ep)) return false;
+  if (!pz_a0<NT>(O, x, xsc, z, nullptr, nullptr, dummy, ep, l0_done)) return false;
   if (!pz_sync(O.gs, ep)) return false;
   int j0, j1;
   pz_range(s, j0, j1);
   for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // y = E^T z
     double t = 0;
-    for (int q = O.eht_rp[j]; q < O.eht_rp[j + 1]; q++) t += O.eht[q] * z[O.eht_ci[q]];
+    const int q1 = ro(O.eht_rp + j + 1);
+    for (int q = ro(O.eht_rp + j); q < q1; q++) t += ro(O.eht + q) * z[ro(O.eht_ci + q)];
     y[j] = O.ia * t - O.a * z[m + j];
   }
   __syncthreads();
@@ -267,25 +292,30 @@ __device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double 
   pz_utx<NT>(k, O.U, y, nullptr, j0, j1, pt, O.pstride, red);     // D U^T y, this CTA's rows
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT>(pt, O.pstride, k, O.coef, nullptr, vec, red);
-  const double i1mt = *O.inv1mt;
+  const double i1mt = ro(O.inv1mt);
   for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // w = G^-1 y; x_C - a w
     double t = 0;
     const double *row = O.U + (size_t)j * k;
-    for (int c = 0; c < k; c++) t += row[c] * vec[c];
+    for (int c = 0; c < k; c++) t += ro(row + c) * vec[c];
     const double wj = i1mt * y[j] + t;
     w[j] = wj;
-    rhs[m + j] = (xsc ? x[m + j] * xsc[m + j] : x[m + j]) - O.a * wj;
+    const double rv = (xsc ? x[m + j] * ro(xsc + m + j) : x[m + j]) - O.a * wj;
+    rhs[m + j] = rv;
+    pz_l0(O, m + j, rv, u);
   }
   if (!pz_sync(O.gs, ep)) return false;
   int i0, i1;
   pz_range(m, i0, i1);
   for (int i = i0 + threadIdx.x; i < i1; i += NT) {                // x_B + a^-1 Ehat w
     double t = 0;
-    for (int q = O.eh_rp[i]; q < O.eh_rp[i + 1]; q++) t += O.eh[q] * w[O.eh_ci[q]];
-    rhs[i] = (xsc ? x[i] * xsc[i] : x[i]) + O.ia * t;
+    const int q1 = ro(O.eh_rp + i + 1);
+    for (int q = ro(O.eh_rp + i); q < q1; q++) t += ro(O.eh + q) * w[ro(O.eh_ci + q)];
+    const double rv = (xsc ? x[i] * ro(xsc + i) : x[i]) + O.ia * t;
+    rhs[i] = rv;
+    pz_l0(O, i, rv, u);
   }
   if (!pz_sync(O.gs, ep)) return false;
-  return pz_a0<NT>(O, rhs, nullptr, u, racc, O.dsc, acc, ep);
+  return pz_a0<NT>(O, rhs, nullptr, u, racc, O.dsc, acc, ep, O.fuse0 != 0);
 }
 
 // ------------------------------------------------------------------- PCG
@@ -300,7 +330,7 @@ struct PzPcg {
 
 // z_i of the preconditioned residual (u scaled back on scaled systems)
 __device__ __forceinline__ double pz_zval(const PzOp &O, const double *u, int i) {
-  return O.dsc ? O.dsc[i] * u[i] : u[i];
+  return O.dsc ? ro(O.dsc + i) * u[i] : u[i];
 }
 
 // PCG from x0 = 0 (Sec. 5) with the stopping rule, true-residual confirmation
@@ -314,6 +344,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
   const int n = O.n;
   int i0, i1;
   pz_range(n, i0, i1);
+  // the first A0 solve of the preconditioner writes here (its first level
+  // is done by whoever produces r)
+  double *a0out = O.variant == 2 ? P.u : P.z;
   double acc = 0;
   for (int i = i0 + threadIdx.x; i < i1; i += NT) {
     const double bi = P.b[i];
@@ -321,6 +354,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     P.r[i] = bi;
     P.p0[i] = 0.0;
     acc += bi * bi;
+    pz_l0(O, i, O.dsc ? bi * ro(O.dsc + i) : bi, a0out);
   }
   double *pt = pz_buf(O, slot++);
   pz_put<NT>(acc, pt, O.pstride, red);
@@ -332,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
   double rz = 0, beta = 0, rr = bb, rt2 = 0, pq = 0, alpha = 0;
   if (!done) {
     acc = 0;
-    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec)) return;
+    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec, O.fuse0 != 0)) return;
     pt = pz_buf(O, slot++);
     pz_put<NT>(acc, pt, O.pstride, red);
     if (!pz_sync(O.gs, ep)) return;
@@ -348,11 +382,11 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
       const double pi = fma(beta, pold[i], pz_zval(O, P.u, i));
       pnew[i] = pi;
       const int g = i >> 5, l = i & 31;
-      const int off = O.a_soff[g] + l, wd = O.a_sw[g];
+      const int off = ro(O.a_soff + g) + l, wd = ro(O.a_sw + g);
       double qi = 0;
       for (int kk = 0; kk < wd; kk++) {
-        const int cc = O.a_col[off + kk * 32];
-        qi += O.a_val[off + kk * 32] * fma(beta, pold[cc], pz_zval(O, P.u, cc));
+        const int cc = ro(O.a_col + off + kk * 32);
+        qi += ro(O.a_val + off + kk * 32) * fma(beta, pold[cc], pz_zval(O, P.u, cc));
       }
       P.q[i] = qi;
       acc += pi * qi;
@@ -370,6 +404,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
       const double ri = P.r[i] - alpha * P.q[i];
       P.r[i] = ri;
       acc += ri * ri;
+      pz_l0(O, i, O.dsc ? ri * ro(O.dsc + i) : ri, a0out);
     }
     pt = pz_buf(O, slot++);
     pz_put<NT>(acc, pt, O.pstride, red);
@@ -382,9 +417,9 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
       acc = 0;
       for (int i = i0 + threadIdx.x; i < i1; i += NT) {
         const int g = i >> 5, l = i & 31;
-        const int off = O.a_soff[g] + l, wd = O.a_sw[g];
+        const int off = ro(O.a_soff + g) + l, wd = ro(O.a_sw + g);
         double ax = 0;
-        for (int kk = 0; kk < wd; kk++) ax += O.a_val[off + kk * 32] * P.x[O.a_col[off + kk * 32]];
+        for (int kk = 0; kk < wd; kk++) ax += ro(O.a_val + off + kk * 32) * P.x[ro(O.a_col + off + kk * 32)];
         const double tr = P.b[i] - ax;
         P.t[i] = tr;
         acc += tr * tr;
@@ -396,14 +431,18 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
       if (rt2 <= tol2) { status = 0; done = true; break; }
       restart = true;                       // continue from the true residual
       if (its >= P.maxit) { status = 5; break; }
-      for (int i = i0 + threadIdx.x; i < i1; i += NT) P.r[i] = P.t[i];
+      for (int i = i0 + threadIdx.x; i < i1; i += NT) {
+        const double ti = P.t[i];
+        P.r[i] = ti;
+        pz_l0(O, i, O.dsc ? ti * ro(O.dsc + i) : ti, a0out);
+      }
       if (!pz_sync(O.gs, ep)) return;
     } else if (its >= P.maxit) {
       status = 5;
       break;
     }
     acc = 0;
-    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec)) return;
+    if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec, O.fuse0 != 0)) return;
     pt = pz_buf(O, slot++);
     pz_put<NT>(acc, pt, O.pstride, red);
     if (!pz_sync(O.gs, ep)) return;
@@ -517,20 +556,24 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
       double t;
       if (i < m) {
         t = 0;
-        for (int q = O.eh_rp[i]; q < O.eh_rp[i + 1]; q++) t += O.eh[q] * L.qcur[O.eh_ci[q]];
+        const int q1 = ro(O.eh_rp + i + 1);
+        for (int q = ro(O.eh_rp + i); q < q1; q++) t += ro(O.eh + q) * L.qcur[ro(O.eh_ci + q)];
         t *= O.ia;
       } else {
         t = -O.a * L.qcur[i - m];
       }
       v[i] = t;
+      pz_l0(O, i, t, z);
     }
     if (!pz_sync(O.gs, ep)) return;
     double dummy = 0;
-    if (!pz_a0<NT>(O, v, nullptr, z, nullptr, nullptr, dummy, ep)) return;
+    const bool f0 = O.fuse0 != 0;
+    // DDLR-2: the first solve's last level also does the second's first
+    if (!pz_a0<NT>(O, v, nullptr, z, nullptr, nullptr, dummy, ep, f0, O.variant == 2 && f0 ? v : nullptr)) return;
     if (!pz_sync(O.gs, ep)) return;
     double *res = z;
     if (O.variant == 2) {
-      if (!pz_a0<NT>(O, z, nullptr, v, nullptr, nullptr, dummy, ep)) return;
+      if (!pz_a0<NT>(O, z, nullptr, v, nullptr, nullptr, dummy, ep, f0)) return;
       if (!pz_sync(O.gs, ep)) return;
       res = v;
     }
@@ -538,7 +581,8 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
     double acc = 0;
     for (int r = j0 + threadIdx.x; r < j1; r += NT) {
       double t = 0;
-      for (int q = O.eht_rp[r]; q < O.eht_rp[r + 1]; q++) t += O.eht[q] * res[O.eht_ci[q]];
+      const int q1 = ro(O.eht_rp + r + 1);
+      for (int q = ro(O.eht_rp + r); q < q1; q++) t += ro(O.eht + q) * res[ro(O.eht_ci + q)];
       const double wr = O.ia * t - O.a * res[m + r];
       L.w[r] = wr;
       acc += L.qcur[r] * wr;
@@ -580,7 +624,7 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
       // ascending original index), orthogonalised against Q_{j+1}
       restarts += 1;
       for (int r = j0 + threadIdx.x; r < j1; r += NT)
-        L.w[r] = d_sm64_pm1(S0.seed + (unsigned long long)restarts, (unsigned long long)L.rank[r]);
+        L.w[r] = d_sm64_pm1(S0.seed + (unsigned long long)restarts, (unsigned long long)ro(L.rank + r));
       __syncthreads();
       double nn = 0;
       if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, nn)) return;
@@ -598,20 +642,18 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
     if (j >= mmax) stop = true;
     if (!pz_sync(O.gs, ep)) return;
     if (!stop && L.check > 0 && j % L.check == 0 && j >= k + 1 && j < mmax) {
-      // eq. converge: k largest eigenvalues of T_j and T_{j-1}, warp 0 of
-      // CTA e computes eigenvalue e % k of T_{j - e / k}
+      // eq. converge: k largest eigenvalues of T_j and T_{j-1}; CTA e
+      // computes eigenvalue e % k of T_{j - e / k}
       for (int e = blockIdx.x; e < 2 * k; e += gridDim.x) {
-        if (threadIdx.x < 32) {
-          const int mm = j - e / k;
-          for (int i = threadIdx.x; i < mm; i += 32) {
-            ea[i] = L.al[i];
-            eb2[i] = (i + 1 < mm) ? L.be[i] * L.be[i] : 0.0;
-          }
-          __syncwarp();
-          const double ev = tridiag_eig_warp(mm, ea, eb2, L.be, e % k);
-          if (threadIdx.x == 0) L.etop[e] = ev;
-          __syncwarp();
+        const int mm = j - e / k;
+        for (int i = threadIdx.x; i < mm; i += NT) {
+          ea[i] = L.al[i];
+          eb2[i] = (i + 1 < mm) ? L.be[i] * L.be[i] : 0.0;
         }
+        __syncthreads();
+        const double ev = tridiag_eig_cta<kEigPoints, kEigRounds>(mm, ea, eb2, L.be, e % k, bc);
+        if (threadIdx.x == 0) L.etop[e] = ev;
+        __syncthreads();
       }
       if (!pz_sync(O.gs, ep)) return;
       double s0 = 0, s1 = 0;
