@@ -91,6 +91,8 @@ typedef struct {
   int batch_block_chunks;  /* rows per pass picked by the autotuner for the batched
                               level solve (0 before the first batched call)       */
   int batch_block_elem;    /* block size picked for the batched row kernels      */
+  double plan_ms;          /* host analysis (orderings, levels, layouts) of setup */
+  int persistent;          /* bit 0: PCG, bit 1: Lanczos run as one cooperative launch */
 } ddlr_info;
 
 typedef struct {

@@ -156,6 +156,9 @@ struct ddlr_ctx {
   unsigned char *pz_lvl0 = nullptr;  // rows on the first level of their block
   int pz_grid = 0, pz_pstride = 0, pz_mmax = 0;
   bool pz_pcg = false, pz_lz = false;
+  // algorithmic bytes moved by the persistent launches since the last reset
+  double pz_pcg_bytes = 0, pz_lz_bytes = 0;
+  long long pz_pcg_runs = 0, pz_lz_runs = 0;
   // workspaces
   double *w64[8] = {nullptr};
   float *w32[8] = {nullptr};
@@ -176,6 +179,7 @@ struct ddlr_ctx {
   std::vector<double> fam_ms;
   std::vector<long long> fam_cnt;
   double setup_ms = 0;
+  double plan_ms = 0;
 
   template <typename T>
   T *alloc(size_t n) {
@@ -432,7 +436,8 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
 }
 
 // persistent-kernel helpers (defined with the allocation code)
-PzOp make_pzop(ddlr_ctx *c);
+template <typename T, typename TU>
+PzOp<T, TU> make_pzop(ddlr_ctx *c);
 void pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
 size_t pz_lz_smem(int mmax);
 
@@ -593,7 +598,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
                          (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
     const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
     if (persist) {
-      PzOp O = make_pzop(c);
+      PzOp<double, double> O = make_pzop<double, double>(c);
       PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps};
       void *args[] = {&O, &Lz};
       pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax), args);
@@ -659,6 +664,18 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     LzState hs;
     ck(cudaMemcpy(&hs, L.st, sizeof(hs), cudaMemcpyDeviceToHost), "D2H");
+    if (persist) {
+      // per step: E q, one (DDLR-2: two) A0 solves, E^T, the three-term update
+      // and normalisation, and two CGS passes reading Q_{j+1} twice each
+      double a0 = 0;
+      ddlr_get_traffic(c, nullptr, &a0, nullptr, 0);
+      const double ne = double(P.nnz_ehat), sd = double(s) * 8.0, nd = double(n) * 8.0;
+      const double step = ne * 12.0 + sd + nd + (c->opt.variant == 2 ? 2.0 : 1.0) * a0 + ne * 12.0 + nd + sd +
+                          8.0 * sd;
+      const double steps = double(hs.j);
+      c->pz_lz_bytes += steps * step + 4.0 * sd * steps * (steps + 1.0) / 2.0;
+      c->pz_lz_runs += 1;
+    }
     const int mm = hs.conv_m > 0 ? hs.conv_m : std::min(hs.j, mmax);
     if (hs.nan_step >= 0 && hs.nan_step < mm) st = DDLR_ERR_NAN;
     if (st == DDLR_OK) {
@@ -803,11 +820,18 @@ size_t pz_lz_smem(int mmax) { return size_t(kPzThreads + 32 + 3 * mmax + 2) * si
 
 // Whole-solve persistent kernels serve shallow factors (every block at most
 // kPzMaxLevels levels deep) on devices with cooperative launch; one CTA per
-// SM.  DDLR_PERSIST=0 keeps the kernel-per-phase path.
+// SM.  The Lanczos process then always runs persistent.  PCG runs persistent
+// up to kPzPcgRowsPerSm rows per SM: beyond that the per-phase kernels, with
+// four times the resident threads, hide the gather latency better (measured
+// on GB300, 7-point Laplacian: 64^3 73 vs 91 us per iteration, 128^3 633 vs
+// 489).  DDLR_PERSIST=0 keeps the kernel-per-phase path everywhere, =1 uses
+// the persistent PCG at every size.
+constexpr int kPzPcgRowsPerSm = 3000;
 void pz_setup(ddlr_ctx *c, int mmax) {
   const Plan &P = c->P;
   const char *env = getenv("DDLR_PERSIST");
   if (env && env[0] == '0') return;
+  const bool force = env && env[0] == '1';
   const int nL = int(P.ch_all_ptr.size()) - 1;
   if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
   const int k = c->opt.rank_k;
@@ -819,7 +843,10 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   if (!coop || sms <= 0 || k > kPzThreads) return;
   const size_t sp = pz_pcg_smem(k), sl = pz_lz_smem(mmax);
   int occ_p = 0, occ_l = 0;
-  ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_pcg_persist<kPzThreads>, kPzThreads, sp), "occupancy");
+  const void *pcg_fn = c->opt.precision == 0 ? (const void *)k_pcg_persist<kPzThreads, double, double>
+                       : c->opt.uk_bf16    ? (const void *)k_pcg_persist<kPzThreads, float, __nv_bfloat16>
+                                           : (const void *)k_pcg_persist<kPzThreads, float, float>;
+  ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pcg_fn, kPzThreads, sp), "occupancy");
   if (sl <= size_t(optin)) {
     ck(cudaFuncSetAttribute(k_lz_persist<kPzThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sl)), "attr");
     ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, k_lz_persist<kPzThreads>, kPzThreads, sl), "occupancy");
@@ -827,7 +854,7 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   c->pz_grid = sms;
   c->pz_pstride = std::max(k, mmax + 2);
   c->pz_mmax = mmax;
-  c->pz_pcg = c->opt.precision == 0 && occ_p >= 1;
+  c->pz_pcg = occ_p >= 1 && (force || P.n <= (long long)kPzPcgRowsPerSm * sms);
   c->pz_lz = occ_l >= 1;
   if (!c->pz_pcg && !c->pz_lz) return;
   c->pz_part = c->alloc<double>(size_t(3) * c->pz_grid * c->pz_pstride);
@@ -841,9 +868,15 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   c->pz_lvl0 = c->upload(f0);
 }
 
-PzOp make_pzop(ddlr_ctx *c) {
+template <typename T> const T *pz_u(ddlr_ctx *c);
+template <> const double *pz_u<double>(ddlr_ctx *c) { return c->U64; }
+template <> const float *pz_u<float>(ddlr_ctx *c) { return c->U32; }
+template <> const __nv_bfloat16 *pz_u<__nv_bfloat16>(ddlr_ctx *c) { return c->Ub16; }
+
+template <typename T, typename TU>
+PzOp<T, TU> make_pzop(ddlr_ctx *c) {
   const Plan &P = c->P;
-  PzOp O{};
+  PzOp<T, TU> O{};
   O.n = P.n; O.m = P.m; O.s = P.s; O.k = c->opt.rank_k; O.variant = c->opt.variant;
   O.nL = int(P.ch_all_ptr.size()) - 1;
   O.pstride = c->pz_pstride;
@@ -851,10 +884,10 @@ PzOp make_pzop(ddlr_ctx *c) {
   for (int i = 0; i <= O.nL; i++) O.lvl_ptr[i] = P.ch_all_ptr[i];
   O.S = c->S;
   O.chunks = reinterpret_cast<const int4 *>(c->chunks);
-  O.lval = c->l64; O.uval = c->u64; O.dinv = c->dinv64;
-  O.eh_rp = c->eh_rp; O.eh_ci = c->eh_ci; O.eh = c->eh64;
-  O.eht_rp = c->eht_rp; O.eht_ci = c->eht_ci; O.eht = c->eht64;
-  O.U = c->U64; O.coef = c->coef64; O.inv1mt = c->inv1mt64; O.Hk = c->Hk64;
+  O.lval = Prec<T>::l(c); O.uval = Prec<T>::u(c); O.dinv = Prec<T>::dinv(c);
+  O.eh_rp = c->eh_rp; O.eh_ci = c->eh_ci; O.eh = Prec<T>::eh(c);
+  O.eht_rp = c->eht_rp; O.eht_ci = c->eht_ci; O.eht = Prec<T>::eht(c);
+  O.U = pz_u<TU>(c); O.coef = Prec<T>::coef(c); O.inv1mt = Prec<T>::inv1mt(c); O.Hk = Prec<T>::Hk(c);
   O.a_soff = c->a_soff; O.a_sw = c->a_sw; O.a_col = c->a_col; O.a_val = c->a_val;
   O.dsc = c->dsc_dev;
   O.lvl0 = c->pz_lvl0;
@@ -863,6 +896,20 @@ PzOp make_pzop(ddlr_ctx *c) {
   O.gs.count = c->pz_bar;
   O.gs.err = c->dflag + 3;
   return O;
+}
+
+// the whole PCG solve in one persistent launch, preconditioner in T (U_k in TU)
+template <typename T, typename TU>
+void pcg_persist(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, T *u, T *z, T *y, T *w,
+                 T *rhs) {
+  PzOp<T, TU> O = make_pzop<T, TU>(c);
+  PzPcg<T> Pp{};
+  Pp.b = b; Pp.x = x; Pp.r = c->pv[1]; Pp.p0 = c->pv[3]; Pp.p1 = c->pv[2]; Pp.q = c->pv[4]; Pp.t = c->pv[5];
+  Pp.zo = c->pv[6];
+  Pp.u = u; Pp.z = z; Pp.y = y; Pp.w = w; Pp.rhs = rhs;
+  Pp.st = c->pcg; Pp.tol = tol; Pp.maxit = maxit;
+  void *args[] = {&O, &Pp};
+  pz_launch(c, "pcg_persist", (const void *)k_pcg_persist<kPzThreads, T, TU>, pz_pcg_smem(c->opt.rank_k), args);
 }
 
 // one cooperative launch of a persistent kernel on the handle's stream
@@ -1022,7 +1069,7 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   const int *gate = pcg_gate(c);
   const char *ng = getenv("DDLR_NO_GRAPH");
   // the whole solve in one persistent kernel when the factors are shallow
-  const bool persist = c->pz_pcg && !flexible &&
+  const bool persist = c->pz_pcg &&
                        (long long)(maxit + 2) * pz_barriers_per_iteration(c) * c->pz_grid < (1LL << 31);
   const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
   cudaStream_t user = c->stream;
@@ -1031,10 +1078,13 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
     ~Restore() { c->stream = s; }
   } restore{c, user};
   if (persist) {
-    PzOp O = make_pzop(c);
-    PzPcg Pp{b, x, r, z, p, zo, q, c->pv[5], c->w64[0], c->w64[1], c->w64[2], c->w64[3], c->pcg, tol, maxit};
-    void *args[] = {&O, &Pp};
-    pz_launch(c, "pcg_persist", (const void *)k_pcg_persist<kPzThreads>, pz_pcg_smem(c->opt.rank_k), args);
+    if (c->opt.precision == 0)
+      pcg_persist<double, double>(c, b, x, tol, maxit, c->pv[7], c->w64[0], c->w64[1], c->w64[2], c->w64[3]);
+    else if (c->opt.uk_bf16)
+      pcg_persist<float, __nv_bfloat16>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1], c->w32[2],
+                                        c->w32[3]);
+    else
+      pcg_persist<float, float>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1], c->w32[2], c->w32[3]);
   } else {
     if (use_graph) {
       ck(cudaEventRecord(c->ev_fork, user), "event");
@@ -1103,6 +1153,17 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
     ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
   }
   if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  if (persist) {
+    // x, r, p, b set up and one apply; per iteration one apply, A p with the
+    // p update (A once, p_old, z, p, q), the x and r updates, and z_old for
+    // flexible CG
+    double apply = 0;
+    ddlr_get_traffic(c, &apply, nullptr, nullptr, 0);
+    const double nd = double(n) * 8.0, nnz = double(P.nnz);
+    const double it = apply + nnz * 12.0 + 4.0 * nd + 6.0 * nd + (flexible ? 2.0 * nd : 0.0);
+    c->pz_pcg_bytes += 4.0 * nd + apply + double(hs.its) * it;
+    c->pz_pcg_runs += 1;
+  }
   if (info) {
     info->its = hs.its;
     info->relres = hs.bb > 0 ? std::sqrt(c->h_pin[0] / hs.bb) : 0.0;
@@ -1544,6 +1605,7 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
     std::string err;
     ddlr_status s1 = build_plan(n, rowptr, colind, val, part, p, c->opt, c->P, err);
     if (s1 != DDLR_OK) { c->err = err; return s1; }
+    c->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     ck(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
@@ -1767,6 +1829,8 @@ ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
   info->batch_block_chunks = c->bt.chunk_per;
   info->batch_block_elem = c->bt.bd_elem;
   info->setup_ms = c->setup_ms;
+  info->plan_ms = c->plan_ms;
+  info->persistent = (c->pz_pcg ? 1 : 0) | (c->pz_lz ? 2 : 0);
   return DDLR_OK;
 }
 
@@ -1892,6 +1956,8 @@ ddlr_status ddlr_reset_counters(ddlr_handle c) {
   c->launches = 0;
   for (auto &v : c->fam_ms) v = 0;
   for (auto &v : c->fam_cnt) v = 0;
+  c->pz_pcg_bytes = c->pz_lz_bytes = 0;
+  c->pz_pcg_runs = c->pz_lz_runs = 0;
   return DDLR_OK;
 }
 
@@ -1940,6 +2006,8 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "pcg_axpy") b = 6.0 * n * 8.0;
       else if (f == "pcg_dot2") b = 3.0 * n * 8.0;
       else if (f == "pcg_p") b = (c->opt.precision == 1 ? 4.0 : 3.0) * n * 8.0;
+      else if (f == "pcg_persist") b = c->pz_pcg_runs ? c->pz_pcg_bytes / double(c->pz_pcg_runs) : 0.0;
+      else if (f == "lanczos_persist") b = c->pz_lz_runs ? c->pz_lz_bytes / double(c->pz_lz_runs) : 0.0;
       family_bytes[i] = b;
     }
   }

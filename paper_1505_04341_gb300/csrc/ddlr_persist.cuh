@@ -81,19 +81,22 @@ __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
   return s_ok != 0;
 }
 
-// Operator data of the preconditioner in device order (FP64).
+// Operator data of the preconditioner in device order: local factors, E and
+// the low-rank data in precision T (U_k in TU), A and the scaling in FP64.
+template <typename T, typename TU>
 struct PzOp {
   int n, m, s, k, variant, nL, pstride;
   double a, ia;
   int lvl_ptr[kPzMaxLevels + 1];       // level-chunk list offsets, levels of all blocks
   SolveLayout S;
   const int4 *chunks;
-  const double *lval, *uval, *dinv;
+  const T *lval, *uval, *dinv;
   const int *eh_rp, *eh_ci;
-  const double *eh;
+  const T *eh;
   const int *eht_rp, *eht_ci;
-  const double *eht;
-  const double *U, *coef, *inv1mt, *Hk;
+  const T *eht;
+  const TU *U;
+  const T *coef, *inv1mt, *Hk;
   const int *a_soff, *a_sw, *a_col;
   const double *a_val;
   const double *dsc;                   // D^-1/2 (scaled systems) or null
@@ -104,11 +107,18 @@ struct PzOp {
   GridSync gs;
 };
 
+// x_r as the preconditioner reads it: (xsc_r x_r) rounded to T
+template <typename T, typename TX>
+__device__ __forceinline__ T pz_in(const TX *x, const double *xsc, int r) {
+  return xsc ? T(double(x[r]) * ro(xsc + r)) : T(x[r]);
+}
+
 // The first forward level of z = A0^-1 x for row r, done by the phase that
-// produces x_r (xv = x_r, already scaled): rows on the first level of their
-// block have no lower neighbours, so z_r = x_r / L_rr, exactly what the level
-// solve computes for them.
-__device__ __forceinline__ void pz_l0(const PzOp &O, int r, double xv, double *z) {
+// produces x_r (xv = x_r as read): rows on the first level of their block
+// have no lower neighbours, so z_r = x_r / L_rr, exactly what the level solve
+// computes for them.
+template <typename T, typename TU>
+__device__ __forceinline__ void pz_l0(const PzOp<T, TU> &O, int r, T xv, T *z) {
   if (O.fuse0 && ro(O.lvl0 + r)) z[r] = xv * ro(O.dinv + r);
 }
 
@@ -119,7 +129,8 @@ __device__ __forceinline__ void pz_range(int N, int &r0, int &r1) {
   r1 = min(N, r0 + per);
 }
 
-__device__ __forceinline__ double *pz_buf(const PzOp &O, int slot) {
+template <typename T, typename TU>
+__device__ __forceinline__ double *pz_buf(const PzOp<T, TU> &O, int slot) {
   return O.part + (size_t)(slot % 3) * gridDim.x * O.pstride;
 }
 
@@ -145,23 +156,24 @@ __device__ __forceinline__ double pz_get(const double *pt, int pstride, double *
   return r;
 }
 
-// out[c] = (coef ? coef[c] : 1) * sum_g pt[g * pstride + c], c < ncol, in shared
-// memory; with H (ncol x ncol row-major): out = H * (those sums)
-template <int NT>
-__device__ __forceinline__ void pz_get_cols(const double *pt, int pstride, int ncol, const double *coef,
-                                            const double *H, double *out, double *tmp) {
+// out[c] = (coef ? coef[c] : 1) * sum_g pt[g * pstride + c], c < ncol, in
+// precision T in shared memory; with H (ncol x ncol row-major): out = H *
+// (those sums)
+template <int NT, typename T>
+__device__ __forceinline__ void pz_get_cols(const double *pt, int pstride, int ncol, const T *coef, const T *H,
+                                            T *out, T *tmp) {
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  double *dst = H ? tmp : out;
+  T *dst = H ? tmp : out;
   for (int c = wi; c < ncol; c += NT / 32) {
-    double s = 0;
-    for (int g = l; g < (int)gridDim.x; g += 32) s += pt[(size_t)g * pstride + c];
+    T s = 0;
+    for (int g = l; g < (int)gridDim.x; g += 32) s += T(pt[(size_t)g * pstride + c]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (l == 0) dst[c] = coef ? ro(coef + c) * s : s;
   }
   __syncthreads();
   if (H) {
     for (int c = threadIdx.x; c < ncol; c += NT) {
-      double s = 0;
+      T s = 0;
       for (int b = 0; b < ncol; b++) s += ro(H + c * ncol + b) * tmp[b];
       out[c] = s;
     }
@@ -170,34 +182,33 @@ __device__ __forceinline__ void pz_get_cols(const double *pt, int pstride, int n
 }
 
 // this CTA's partials pt[blockIdx.x * pstride + c] = sum_{r in [r0,r1)} U[r][c] x_r
-// (U row-major, k columns, x optionally scaled by xsc); red: NT doubles
-template <int NT>
-__device__ __forceinline__ void pz_utx(int k, const double *U, const double *x, const double *xsc, int r0,
-                                       int r1, double *pt, int pstride, double *red) {
+// in precision T (U row-major, k columns, x read as pz_in); red: NT doubles
+template <int NT, typename T, typename TU, typename TX>
+__device__ __forceinline__ void pz_utx(int k, const TU *U, const TX *x, const double *xsc, int r0, int r1,
+                                       double *pt, int pstride, double *red) {
   const int G = NT / k;
   const int c = threadIdx.x % k, g = threadIdx.x / k;
-  double acc = 0;
+  T acc = 0;
   if (g < G)
-    for (int r = r0 + g; r < r1; r += G) acc += ro(U + (size_t)r * k + c) * (xsc ? x[r] * ro(xsc + r) : x[r]);
-  red[threadIdx.x] = (g < G) ? acc : 0.0;
+    for (int r = r0 + g; r < r1; r += G) acc += T(to_acc(ro(U + (size_t)r * k + c))) * pz_in<T>(x, xsc, r);
+  T *rt = reinterpret_cast<T *>(red);
+  rt[threadIdx.x] = (g < G) ? acc : T(0);
   __syncthreads();
   if (threadIdx.x < k) {
-    double s = 0;
-    for (int gg = 0; gg < G; gg++) s += red[gg * k + threadIdx.x];
-    pt[(size_t)blockIdx.x * pstride + threadIdx.x] = s;
+    T s = 0;
+    for (int gg = 0; gg < G; gg++) s += rt[gg * k + threadIdx.x];
+    pt[(size_t)blockIdx.x * pstride + threadIdx.x] = double(s);
   }
   __syncthreads();
 }
 
 // One level L of every block: mode 0 forward, 1 backward, 2 forward then
-// backward (the top level).  x is read as xsc .* x when xsc is given.  Rows
-// finalised here (modes 1, 2) add racc_r * (zsc_r) z_r to acc when racc is
-// given; z2 (level 0, backward) receives the first forward level of a solve
-// whose input is z.
-template <int NT>
-__device__ __forceinline__ void pz_level(const PzOp &O, int L, int mode, const double *x, const double *xsc,
-                                         double *z, const double *racc, const double *zsc, double &acc,
-                                         double *z2) {
+// backward (the top level).  x is read as pz_in.  Rows finalised here (modes
+// 1, 2) add racc_r (zsc_r z_r) to acc when racc is given; z2 (level 0,
+// backward) receives the first forward level of a solve whose input is z.
+template <int NT, typename T, typename TU, typename TX>
+__device__ __forceinline__ void pz_level(const PzOp<T, TU> &O, int L, int mode, const TX *x, const double *xsc,
+                                         T *z, const double *racc, const double *zsc, double &acc, T *z2) {
   const int c0 = O.lvl_ptr[L];
   const unsigned nv = (unsigned)(O.lvl_ptr[L + 1] - c0) * (unsigned)kChunk;
   for (unsigned v = blockIdx.x * NT + threadIdx.x; v < nv; v += gridDim.x * NT) {
@@ -206,100 +217,102 @@ __device__ __forceinline__ void pz_level(const PzOp &O, int L, int mode, const d
     if (i >= ch.z) continue;
     const int ii = ch.y + i;
     const int r = ro(O.S.lvl_row0 + ch.x) + ii, sl = ro(O.S.lvl_slice0 + ch.x) + (ii >> 5), ln = ii & 31;
-    double zr;
-    const double dr = ro(O.dinv + r);
+    T zr;
+    const T dr = ro(O.dinv + r);
     if (mode == 1) {
       const int off = ro(O.S.u_soff + sl) + ln, w = ro(O.S.u_sw + sl);
-      double t = z[r];
+      T t = z[r];
       for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.S.u_col + off + kk * 32)];
       zr = t * dr;
     } else {
       const int off = ro(O.S.l_soff + sl) + ln, w = ro(O.S.l_sw + sl);
-      double t = xsc ? x[r] * ro(xsc + r) : x[r];
+      T t = pz_in<T>(x, xsc, r);
       for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.S.l_col + off + kk * 32)];
       zr = t * dr;
       if (mode == 2) zr = zr * dr;
     }
     z[r] = zr;
-    if (racc && mode != 0) acc += racc[r] * (zsc ? ro(zsc + r) * zr : zr);
+    if (racc && mode != 0) acc += racc[r] * (zsc ? ro(zsc + r) * double(zr) : double(zr));
     if (z2) z2[r] = zr * dr;          // first forward level of a solve with input z
   }
 }
 
-// z = A0^-1 (xsc .* x) (Sec. 4.2), phases separated by grid barriers; the last
-// phase is left open (the caller adds its own work and barrier).  l0_done:
-// the producer of x has already done the first forward level (pz_l0).  z2:
-// see pz_level (only with fuse0).
-template <int NT>
-__device__ __forceinline__ bool pz_a0(const PzOp &O, const double *x, const double *xsc, double *z,
+// z = A0^-1 x (Sec. 4.2), x read as pz_in, phases separated by grid barriers;
+// the last phase is left open (the caller adds its own work and barrier).
+// l0_done: the producer of x has already done the first forward level
+// (pz_l0).  z2: see pz_level (only with fuse0).
+template <int NT, typename T, typename TU, typename TX>
+__device__ __forceinline__ bool pz_a0(const PzOp<T, TU> &O, const TX *x, const double *xsc, T *z,
                                       const double *racc, const double *zsc, double &acc, unsigned &ep,
-                                      bool l0_done, double *z2 = nullptr) {
+                                      bool l0_done, T *z2 = nullptr) {
   const int nL = O.nL;
   for (int L = l0_done ? 1 : 0; L + 1 < nL; L++) {
-    pz_level<NT>(O, L, 0, x, xsc, z, nullptr, nullptr, acc, nullptr);
+    pz_level<NT>(O, L, 0, x, xsc, z, nullptr, nullptr, acc, (T *)nullptr);
     if (!pz_sync(O.gs, ep)) return false;
   }
-  pz_level<NT>(O, nL - 1, 2, x, xsc, z, racc, zsc, acc, nullptr);
+  pz_level<NT>(O, nL - 1, 2, x, xsc, z, racc, zsc, acc, (T *)nullptr);
   for (int L = nL - 2; L >= 0; L--) {
     if (!pz_sync(O.gs, ep)) return false;
-    pz_level<NT>(O, L, 1, x, xsc, z, racc, zsc, acc, L == 0 ? z2 : nullptr);
+    pz_level<NT>(O, L, 1, x, xsc, z, racc, zsc, acc, L == 0 ? z2 : (T *)nullptr);
   }
   return true;
 }
 
-// u = M^-1 (dsc .* x) without the final dsc scaling, DDLR-1 (Algorithm 1,
-// prop. gkt) or DDLR-2 (eq. Form2a).  acc collects sum_r racc_r (dsc_r u_r)
-// over the rows this CTA finalises.  Scratch: z (n), y, w (s), rhs (n).  The
-// last phase is left open.  `slot` is the next partial-sum buffer.
-template <int NT>
-__device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double *u, double *z, double *y,
-                                         double *w, double *rhs, const double *racc, double &acc, unsigned &ep,
-                                         int &slot, double *red, double *vec, bool l0_done) {
+// u = M^-1 (dsc .* x) in precision T without the final dsc scaling, DDLR-1
+// (Algorithm 1, prop. gkt) or DDLR-2 (eq. Form2a); x (FP64) is rounded to T
+// as it is read.  acc collects sum_r racc_r (dsc_r u_r) over the rows this CTA
+// finalises.  Scratch: z (n), y, w (s), rhs (n).  The last phase is left
+// open.  `slot` is the next partial-sum buffer.
+template <int NT, typename T, typename TU>
+__device__ __forceinline__ bool pz_apply(const PzOp<T, TU> &O, const double *x, T *u, T *z, T *y, T *w, T *rhs,
+                                         const double *racc, double &acc, unsigned &ep, int &slot, double *red,
+                                         T *vec, bool l0_done) {
   const double *xsc = O.dsc;
   const int n = O.n, m = O.m, s = O.s, k = O.k;
   if (O.variant == 2) {
     int i0, i1;
     pz_range(n, i0, i1);
     double *pt = pz_buf(O, slot++);
-    pz_utx<NT>(k, O.U, x, xsc, i0, i1, pt, O.pstride, red);     // t = U^T x, this CTA's rows
+    pz_utx<NT, T>(k, O.U, x, xsc, i0, i1, pt, O.pstride, red);     // t = U^T x, this CTA's rows
     double dummy = 0;
     if (!pz_a0<NT>(O, x, xsc, u, nullptr, nullptr, dummy, ep, l0_done)) return false;
     if (!pz_sync(O.gs, ep)) return false;
-    pz_get_cols<NT>(pt, O.pstride, k, nullptr, O.Hk, vec, red);   // H_k t
+    pz_get_cols<NT, T>(pt, O.pstride, k, nullptr, O.Hk, vec, reinterpret_cast<T *>(red));   // H_k t
     for (int r = i0 + threadIdx.x; r < i1; r += NT) {
-      double t = 0;
-      const double *row = O.U + (size_t)r * k;
-      for (int c = 0; c < k; c++) t += ro(row + c) * vec[c];
-      const double ur = u[r] + t;
+      T t = 0;
+      const TU *row = O.U + (size_t)r * k;
+      for (int c = 0; c < k; c++) t += T(to_acc(ro(row + c))) * vec[c];
+      const T ur = u[r] + t;
       u[r] = ur;
-      if (racc) acc += racc[r] * (O.dsc ? ro(O.dsc + r) * ur : ur);
+      if (racc) acc += racc[r] * (O.dsc ? ro(O.dsc + r) * double(ur) : double(ur));
     }
     return true;
   }
   double dummy = 0;
   if (!pz_a0<NT>(O, x, xsc, z, nullptr, nullptr, dummy, ep, l0_done)) return false;
   if (!pz_sync(O.gs, ep)) return false;
+  const T a = T(O.a), ia = T(O.ia);
   int j0, j1;
   pz_range(s, j0, j1);
   for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // y = E^T z
-    double t = 0;
+    T t = 0;
     const int q1 = ro(O.eht_rp + j + 1);
     for (int q = ro(O.eht_rp + j); q < q1; q++) t += ro(O.eht + q) * z[ro(O.eht_ci + q)];
-    y[j] = O.ia * t - O.a * z[m + j];
+    y[j] = ia * t - a * z[m + j];
   }
   __syncthreads();
   double *pt = pz_buf(O, slot++);
-  pz_utx<NT>(k, O.U, y, nullptr, j0, j1, pt, O.pstride, red);     // D U^T y, this CTA's rows
+  pz_utx<NT, T>(k, O.U, y, (const double *)nullptr, j0, j1, pt, O.pstride, red);   // D U^T y, this CTA's rows
   if (!pz_sync(O.gs, ep)) return false;
-  pz_get_cols<NT>(pt, O.pstride, k, O.coef, nullptr, vec, red);
-  const double i1mt = ro(O.inv1mt);
+  pz_get_cols<NT, T>(pt, O.pstride, k, O.coef, (const T *)nullptr, vec, reinterpret_cast<T *>(red));
+  const T i1mt = ro(O.inv1mt);
   for (int j = j0 + threadIdx.x; j < j1; j += NT) {                // w = G^-1 y; x_C - a w
-    double t = 0;
-    const double *row = O.U + (size_t)j * k;
-    for (int c = 0; c < k; c++) t += ro(row + c) * vec[c];
-    const double wj = i1mt * y[j] + t;
+    T t = 0;
+    const TU *row = O.U + (size_t)j * k;
+    for (int c = 0; c < k; c++) t += T(to_acc(ro(row + c))) * vec[c];
+    const T wj = i1mt * y[j] + t;
     w[j] = wj;
-    const double rv = (xsc ? x[m + j] * ro(xsc + m + j) : x[m + j]) - O.a * wj;
+    const T rv = pz_in<T>(x, xsc, m + j) - a * wj;
     rhs[m + j] = rv;
     pz_l0(O, m + j, rv, u);
   }
@@ -307,38 +320,45 @@ __device__ __forceinline__ bool pz_apply(const PzOp &O, const double *x, double 
   int i0, i1;
   pz_range(m, i0, i1);
   for (int i = i0 + threadIdx.x; i < i1; i += NT) {                // x_B + a^-1 Ehat w
-    double t = 0;
+    T t = 0;
     const int q1 = ro(O.eh_rp + i + 1);
     for (int q = ro(O.eh_rp + i); q < q1; q++) t += ro(O.eh + q) * w[ro(O.eh_ci + q)];
-    const double rv = (xsc ? x[i] * ro(xsc + i) : x[i]) + O.ia * t;
+    const T rv = pz_in<T>(x, xsc, i) + ia * t;
     rhs[i] = rv;
     pz_l0(O, i, rv, u);
   }
   if (!pz_sync(O.gs, ep)) return false;
-  return pz_a0<NT>(O, rhs, nullptr, u, racc, O.dsc, acc, ep, O.fuse0 != 0);
+  return pz_a0<NT>(O, rhs, (const double *)nullptr, u, racc, O.dsc, acc, ep, O.fuse0 != 0);
 }
 
 // ------------------------------------------------------------------- PCG
+template <typename T>
 struct PzPcg {
   const double *b;
-  double *x, *r, *u, *p0, *p1, *q, *t;
-  double *z, *y, *w, *rhs;
+  double *x, *r, *p0, *p1, *q, *t, *zo;
+  T *u, *z, *y, *w, *rhs;
   PcgState *st;
   double tol;
   int maxit;
 };
 
-// z_i of the preconditioned residual (u scaled back on scaled systems)
-__device__ __forceinline__ double pz_zval(const PzOp &O, const double *u, int i) {
-  return O.dsc ? ro(O.dsc + i) * u[i] : u[i];
+// z_i of the preconditioned residual: u_i in FP64, scaled back on scaled
+// systems
+template <typename T, typename TU>
+__device__ __forceinline__ double pz_zval(const PzOp<T, TU> &O, const T *u, int i) {
+  return O.dsc ? ro(O.dsc + i) * double(u[i]) : double(u[i]);
 }
 
 // PCG from x0 = 0 (Sec. 5) with the stopping rule, true-residual confirmation
-// and restart of the level-by-level path; the final state goes to P.st.
-template <int NT>
-__global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
+// and restart of the level-by-level path; the final state goes to P.st.  With
+// an FP32 preconditioner (T = float) the outer loop is flexible CG in FP64:
+// beta = (r_new.z_new - r_new.z_old) / r.z.
+template <int NT, typename T, typename TU>
+__global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp<T, TU> O, PzPcg<T> P) {
+  constexpr bool kFlex = sizeof(T) < sizeof(double);
   extern __shared__ double pz_sm[];
-  double *red = pz_sm, *bc = pz_sm + NT, *vec = pz_sm + NT + 32;
+  double *red = pz_sm, *bc = pz_sm + NT;
+  T *vec = reinterpret_cast<T *>(pz_sm + NT + 32);
   unsigned ep = 0;
   int slot = 0;
   const int n = O.n;
@@ -346,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
   pz_range(n, i0, i1);
   // the first A0 solve of the preconditioner writes here (its first level
   // is done by whoever produces r)
-  double *a0out = O.variant == 2 ? P.u : P.z;
+  T *a0out = O.variant == 2 ? P.u : P.z;
   double acc = 0;
   for (int i = i0 + threadIdx.x; i < i1; i += NT) {
     const double bi = P.b[i];
@@ -354,7 +374,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     P.r[i] = bi;
     P.p0[i] = 0.0;
     acc += bi * bi;
-    pz_l0(O, i, O.dsc ? bi * ro(O.dsc + i) : bi, a0out);
+    pz_l0(O, i, pz_in<T>(P.b, O.dsc, i), a0out);
   }
   double *pt = pz_buf(O, slot++);
   pz_put<NT>(acc, pt, O.pstride, red);
@@ -363,7 +383,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
   const double tol2 = P.tol * P.tol * bb;
   int its = 0, status = 0;
   bool done = (bb == 0.0);
-  double rz = 0, beta = 0, rr = bb, rt2 = 0, pq = 0, alpha = 0;
+  double rz = 0, beta = 0, rr = bb, rt2 = 0, pq = 0, alpha = 0, rzo = 0;
   if (!done) {
     acc = 0;
     if (!pz_apply<NT>(O, P.r, P.u, P.z, P.y, P.w, P.rhs, P.r, acc, ep, slot, red, vec, O.fuse0 != 0)) return;
@@ -379,8 +399,10 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     // p = z + beta p_old (into the other buffer), q = A p, p.q
     acc = 0;
     for (int i = i0 + threadIdx.x; i < i1; i += NT) {
-      const double pi = fma(beta, pold[i], pz_zval(O, P.u, i));
+      const double zi = pz_zval(O, P.u, i);
+      const double pi = fma(beta, pold[i], zi);
       pnew[i] = pi;
+      if (kFlex) P.zo[i] = zi;
       const int g = i >> 5, l = i & 31;
       const int off = ro(O.a_soff + g) + l, wd = ro(O.a_sw + g);
       double qi = 0;
@@ -397,19 +419,23 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     pq = pz_get(pt, O.pstride, bc);
     alpha = rz / pq;
     if (!(alpha == alpha) || isinf(alpha)) { status = 7; break; }
-    // x += alpha p; r -= alpha q; r.r
+    // x += alpha p; r -= alpha q; r.r (and r.z_old for flexible CG)
     acc = 0;
+    double acc2 = 0;
     for (int i = i0 + threadIdx.x; i < i1; i += NT) {
       P.x[i] += alpha * pnew[i];
       const double ri = P.r[i] - alpha * P.q[i];
       P.r[i] = ri;
       acc += ri * ri;
-      pz_l0(O, i, O.dsc ? ri * ro(O.dsc + i) : ri, a0out);
+      if (kFlex) acc2 += ri * P.zo[i];
+      pz_l0(O, i, pz_in<T>(P.r, O.dsc, i), a0out);
     }
     pt = pz_buf(O, slot++);
     pz_put<NT>(acc, pt, O.pstride, red);
+    if (kFlex) pz_put<NT>(acc2, pt + 1, O.pstride, red);
     if (!pz_sync(O.gs, ep)) return;
     rr = pz_get(pt, O.pstride, bc);
+    if (kFlex) rzo = pz_get(pt + 1, O.pstride, bc);
     its += 1;
     if (!(rr == rr) || isinf(rr)) { status = 7; break; }
     if (rr <= tol2) {
@@ -432,9 +458,8 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
       restart = true;                       // continue from the true residual
       if (its >= P.maxit) { status = 5; break; }
       for (int i = i0 + threadIdx.x; i < i1; i += NT) {
-        const double ti = P.t[i];
-        P.r[i] = ti;
-        pz_l0(O, i, O.dsc ? ti * ro(O.dsc + i) : ti, a0out);
+        P.r[i] = P.t[i];
+        pz_l0(O, i, pz_in<T>(P.t, O.dsc, i), a0out);
       }
       if (!pz_sync(O.gs, ep)) return;
     } else if (its >= P.maxit) {
@@ -447,7 +472,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     pz_put<NT>(acc, pt, O.pstride, red);
     if (!pz_sync(O.gs, ep)) return;
     const double rzn = pz_get(pt, O.pstride, bc);
-    beta = restart ? 0.0 : rzn / rz;
+    beta = restart ? 0.0 : (kFlex ? (rzn - rzo) / rz : rzn / rz);
     rz = rzn;
     restart = false;
     if (!(rzn == rzn) || isinf(rzn)) { status = 7; break; }
@@ -459,7 +484,7 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp O, PzPcg P) {
     PcgState *st = P.st;
     st->rz = rz; st->pq = pq; st->alpha = alpha; st->beta = beta; st->rr = rr; st->bb = bb;
     st->tol2 = tol2; st->rt2 = rt2; st->its = its; st->maxit = P.maxit; st->done = 1; st->status = status;
-    st->check_true = 0; st->restart = 0; st->flexible = 0;
+    st->check_true = 0; st->restart = 0; st->flexible = kFlex ? 1 : 0;
   }
 }
 
@@ -506,18 +531,18 @@ __device__ __forceinline__ double pz_gemvN(const double *Q, long long ld, int nc
 // Two classical Gram-Schmidt passes of w against Q_{ncol} (rows [j0, j1) of
 // this CTA), then ||w||^2 over all rows, returned to every thread.
 template <int NT>
-__device__ __forceinline__ bool pz_cgs2(const PzOp &O, const PzLz &L, int ncol, int j0, int j1, unsigned &ep,
+__device__ __forceinline__ bool pz_cgs2(const PzOp<double, double> &O, const PzLz &L, int ncol, int j0, int j1, unsigned &ep,
                                         int &slot, double *red, double *bc, double *cs, double &ww_out) {
   double *pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
   if (!pz_sync(O.gs, ep)) return false;
-  pz_get_cols<NT>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
+  pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
   pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
   __syncthreads();
   pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
   if (!pz_sync(O.gs, ep)) return false;
-  pz_get_cols<NT>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
+  pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
   const double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
   pt = pz_buf(O, slot++);
   pz_put<NT>(ww, pt, O.pstride, red);
@@ -533,7 +558,7 @@ __device__ __forceinline__ bool pz_cgs2(const PzOp &O, const PzLz &L, int ncol, 
 // and T_{m-1}); breakdown restarts as the level-by-level path does them.
 // Shared memory: NT + 32 + (m_max + 2) + 2 m_max doubles.
 template <int NT>
-__global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp O, PzLz L) {
+__global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, PzLz L) {
   extern __shared__ double pz_sm[];
   double *red = pz_sm, *bc = pz_sm + NT;
   LzState S0 = *L.st;

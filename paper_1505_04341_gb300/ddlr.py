@@ -47,7 +47,8 @@ class ddlr_info(ctypes.Structure):
                 ("nnz_factor", ctypes.c_longlong), ("nnz_ehat", ctypes.c_longlong),
                 ("fill_ratio", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("setup_ms", ctypes.c_double), ("batch_block_chunks", ctypes.c_int),
-                ("batch_block_elem", ctypes.c_int)]
+                ("batch_block_elem", ctypes.c_int), ("plan_ms", ctypes.c_double),
+                ("persistent", ctypes.c_int)]
 
 
 class ddlr_solve_info(ctypes.Structure):

@@ -145,3 +145,28 @@ def test_pcg_maxit_and_zero_rhs(monkeypatch):
     x0, info0 = h.pcg(torch.zeros_like(b), tol=1e-8)
     assert info0[0]["its"] == 0 and float(x0.abs().max()) == 0.0
     h.close()
+
+
+@pytest.mark.parametrize("persist", ["1", "0"])
+@pytest.mark.parametrize("bf16", [0, 1])
+@pytest.mark.parametrize("case", ["lap3d_32_v1", "lap3d_32_v2", "jump_32_scaled_v1"])
+def test_mixed_precision_pcg(case, bf16, persist, monkeypatch):
+    """FP32 factors and solves, U_k in FP32 or BF16, flexible CG in FP64: the
+    true relative residual reaches tol and the iteration count stays within
+    max(3, 10%) of the FP64 oracle's."""
+    build, variant, k, sd = CASES[case]
+    A, part, p = build()
+    h = _handle(monkeypatch, persist, A, part, p, variant=variant, rank_k=k, factor=0, scale_diag=sd,
+                precision=1, uk_bf16=bf16, **MC)
+    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=0, scale_diag=sd, **MC)
+    b = W.rhs(A[0], 0)
+    h.reset_counters()
+    x, info = h.pcg(torch.tensor(b, device="cuda"), tol=1e-8)
+    xo, its_o, _, st = orc.pcg(b, 1e-8)
+    assert st == "OK"
+    assert info[0]["status"] == "OK" and info[0]["relres"] <= 1e-8
+    assert abs(info[0]["its"] - its_o) <= max(3, its_o // 10), (info, its_o)
+    assert _rel(x.cpu().numpy(), xo) < 1e-6
+    assert ("pcg_persist" in _families(h)) == (persist == "1")
+    assert (h.info()["persistent"] & 1) == (persist == "1")
+    h.close()
