@@ -14,11 +14,20 @@
 //    level, elimination position).  This is a topological order of the
 //    factor's dependency graph, so it leaves the factor unchanged and lets
 //    every level be solved in parallel.
+//
+// The analysis runs on all host cores: rows, slices and blocks are
+// independent, and every flat CSR output is built in two passes (count per
+// row, prefix sum, fill), so the plan does not depend on the thread count.
 #include "ddlr_plan.h"
 
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <numeric>
+#include <thread>
 
 namespace ddlr {
 
@@ -31,6 +40,93 @@ inline int find_pos(const int *rp, const int *ci, int r, int c) {
   return (it != e && *it == c) ? int(it - ci) : -1;
 }
 
+// A fixed set of worker threads for the lifetime of one analysis.  run(n, f)
+// calls f(lo, hi) on disjoint ranges covering [0, n) (static split, one per
+// worker) and returns when all are done; run_dynamic(n, f) hands out single
+// indices in order to whichever worker is free.
+class Pool {
+ public:
+  explicit Pool(int nt) : nt_(std::max(1, nt)) {
+    for (int t = 1; t < nt_; t++) th_.emplace_back([this, t] { loop(t); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+      gen_++;
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+  int size() const { return nt_; }
+  void run(long long n, const std::function<void(long long, long long)> &f, long long min_chunk = 2048) {
+    if (n <= 0) return;
+    const int parts = int(std::min<long long>(nt_, std::max<long long>(1, n / min_chunk)));
+    if (parts <= 1) { f(0, n); return; }
+    job_ = [&f, n, parts](int t) {
+      if (t >= parts) return;
+      f(n * t / parts, n * (t + 1) / parts);
+    };
+    dispatch();
+  }
+  void run_dynamic(int n, const std::function<void(int)> &f) {
+    if (n <= 0) return;
+    std::atomic<int> next(0);
+    job_ = [&f, &next, n](int) {
+      for (int i = next++; i < n; i = next++) f(i);
+    };
+    dispatch();
+  }
+
+ private:
+  void dispatch() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      pending_ = nt_ - 1;
+      gen_++;
+    }
+    cv_.notify_all();
+    job_(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [this] { return pending_ == 0; });
+  }
+  void loop(int t) {
+    unsigned long long seen = 0;
+    while (true) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      job_(t);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--pending_ == 0) done_cv_.notify_one();
+    }
+  }
+  int nt_;
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  std::function<void(int)> job_;
+  unsigned long long gen_ = 0;
+  int pending_ = 0;
+  bool stop_ = false;
+};
+
+int plan_threads(long long work) {
+  const int hw = int(std::thread::hardware_concurrency());
+  const int by_size = int(std::min<long long>(64, std::max<long long>(1, work / 20000)));
+  return std::max(1, std::min({hw > 0 ? hw : 1, 32, by_size}));
+}
+
+// exclusive prefix sum of counts[0..n) into offsets[0..n]
+template <typename T>
+void prefix(const std::vector<T> &counts, std::vector<T> &offsets) {
+  offsets.assign(counts.size() + 1, 0);
+  for (size_t i = 0; i < counts.size(); i++) offsets[i + 1] = offsets[i] + counts[i];
+}
+
 }  // namespace
 
 ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
@@ -41,37 +137,64 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     return DDLR_ERR_INVALID;
   }
   if (rp[0] != 0) { err = "rowptr[0] != 0"; return DDLR_ERR_INVALID; }
-  for (int i = 0; i < n; i++) {
-    if (rp[i + 1] < rp[i]) { err = "rowptr not monotone"; return DDLR_ERR_INVALID; }
-    if (part[i] < 0 || part[i] >= p) { err = "part out of range"; return DDLR_ERR_INVALID; }
-    bool diag = false;
-    for (int q = rp[i]; q < rp[i + 1]; q++) {
-      if (ci[q] < 0 || ci[q] >= n) { err = "column index out of range"; return DDLR_ERR_INVALID; }
-      if (q > rp[i] && ci[q] <= ci[q - 1]) { err = "columns not strictly ascending"; return DDLR_ERR_INVALID; }
-      if (ci[q] == i) diag = true;
-    }
-    if (!diag) { err = "missing diagonal entry"; return DDLR_ERR_INVALID; }
-  }
-  const long long nnz = rp[n];
   for (int i = 0; i < n; i++)
-    for (int q = rp[i]; q < rp[i + 1]; q++) {
-      int t = find_pos(rp, ci, ci[q], i);
-      if (t < 0 || val[t] != val[q]) { err = "matrix is not symmetric"; return DDLR_ERR_INVALID; }
-    }
+    if (rp[i + 1] < rp[i]) { err = "rowptr not monotone"; return DDLR_ERR_INVALID; }
+  const long long nnz = rp[n];
+  Pool pool(plan_threads(nnz));
+
+  // ---- input checks: the first offending row (in row order) names the error
+  {
+    std::vector<int> bad_row(pool.size(), n);
+    std::vector<const char *> bad_msg(pool.size(), nullptr);
+    std::atomic<int> slot(0);
+    pool.run(n, [&](long long lo, long long hi) {
+      const int me = slot++;
+      for (int i = int(lo); i < int(hi); i++) {
+        const char *msg = nullptr;
+        if (part[i] < 0 || part[i] >= p) msg = "part out of range";
+        bool diag = false;
+        for (int q = rp[i]; q < rp[i + 1] && !msg; q++) {
+          if (ci[q] < 0 || ci[q] >= n) { msg = "column index out of range"; break; }
+          if (q > rp[i] && ci[q] <= ci[q - 1]) { msg = "columns not strictly ascending"; break; }
+          if (ci[q] == i) diag = true;
+        }
+        if (!msg && !diag) msg = "missing diagonal entry";
+        if (msg) { bad_row[me] = i; bad_msg[me] = msg; return; }
+      }
+    });
+    int first = n;
+    const char *msg = nullptr;
+    for (int t = 0; t < pool.size(); t++)
+      if (bad_msg[t] && bad_row[t] < first) { first = bad_row[t]; msg = bad_msg[t]; }
+    if (msg) { err = msg; return DDLR_ERR_INVALID; }
+    std::atomic<int> asym(0);
+    pool.run(n, [&](long long lo, long long hi) {
+      for (int i = int(lo); i < int(hi) && !asym.load(std::memory_order_relaxed); i++)
+        for (int q = rp[i]; q < rp[i + 1]; q++) {
+          const int t = find_pos(rp, ci, ci[q], i);
+          if (t < 0 || val[t] != val[q]) { asym = 1; return; }
+        }
+    });
+    if (asym) { err = "matrix is not symmetric"; return DDLR_ERR_INVALID; }
+  }
   P = Plan();
   P.n = n; P.p = p; P.nnz = nnz;
   P.orig_row.resize(nnz); P.orig_col.resize(nnz); P.diag_pos.resize(n);
-  for (int i = 0; i < n; i++)
-    for (int q = rp[i]; q < rp[i + 1]; q++) {
-      P.orig_row[q] = i; P.orig_col[q] = ci[q];
-      if (ci[q] == i) P.diag_pos[i] = q;
-    }
+  pool.run(n, [&](long long lo, long long hi) {
+    for (int i = int(lo); i < int(hi); i++)
+      for (int q = rp[i]; q < rp[i + 1]; q++) {
+        P.orig_row[q] = i; P.orig_col[q] = ci[q];
+        if (ci[q] == i) P.diag_pos[i] = q;
+      }
+  });
 
   // ---- Sec. 2.1 classification and eq. (Bmat) order
   std::vector<char> iface(n, 0);
-  for (int i = 0; i < n; i++)
-    for (int q = rp[i]; q < rp[i + 1]; q++)
-      if (part[ci[q]] != part[i]) { iface[i] = 1; break; }
+  pool.run(n, [&](long long lo, long long hi) {
+    for (int i = int(lo); i < int(hi); i++)
+      for (int q = rp[i]; q < rp[i + 1]; q++)
+        if (part[ci[q]] != part[i]) { iface[i] = 1; break; }
+  });
   std::vector<std::vector<int>> members(p + 1);
   for (int i = 0; i < n; i++) members[iface[i] ? p : part[i]].push_back(i);
   int s = int(members[p].size());
@@ -79,29 +202,34 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   if (opt.rank_k < 1 || opt.rank_k > s) { err = "rank_k must be in [1, s]"; return DDLR_ERR_INVALID; }
   P.s = s; P.m = n - s;
   std::vector<int> blk_of(n);
-  for (int b = 0; b <= p; b++) for (int i : members[b]) blk_of[i] = b;
+  std::vector<int> loc(n, -1);   // index of a node inside its own block
+  for (int b = 0; b <= p; b++)
+    for (int t = 0; t < int(members[b].size()); t++) { blk_of[members[b][t]] = b; loc[members[b][t]] = t; }
 
   const bool exact = opt.factor == 1;
   P.perm.resize(n); P.iperm.resize(n);
   P.blk_row0.assign(p + 2, 0);
+  for (int b = 0; b <= p; b++) P.blk_row0[b + 1] = P.blk_row0[b] + int(members[b].size());
   // per node: level in its block's factor; lower factor pattern per device
-  // row as device-order columns (flat CSR, filled block by block)
+  // row as device-order columns (per block, joined afterwards)
   std::vector<int> level_of(n, 0);
-  std::vector<int> low_rp(n + 1, 0), low_ci;
-  low_ci.reserve(size_t(nnz));
-  int row_w = 0;
-  std::vector<int> loc(n, -1);   // index of a node inside its own block
-  for (int b = 0; b <= p; b++)
-    for (int t = 0; t < int(members[b].size()); t++) loc[members[b][t]] = t;
-  std::vector<int> arp, aci, ord, epos, lrp, lci, lev, dev, col, used, cnt;
-  for (int b = 0; b <= p; b++) {
+  std::vector<int> low_cnt(n, 0);
+  std::vector<std::vector<int>> low_blk(p + 1);
+  std::vector<int> blk_levels(p + 1, 0), blk_colors(p + 1, 0);
+  std::vector<const char *> blk_err(p + 1, nullptr);
+  // blocks in decreasing size, so the largest (usually C_a) starts first
+  std::vector<int> border(p + 1);
+  std::iota(border.begin(), border.end(), 0);
+  std::stable_sort(border.begin(), border.end(),
+                   [&](int a, int b) { return members[a].size() > members[b].size(); });
+  pool.run_dynamic(p + 1, [&](int bi) {
+    const int b = border[bi];
     const std::vector<int> &mem = members[b];
     const int nb = int(mem.size());
-    P.blk_row0[b] = row_w;
+    const int row_w = P.blk_row0[b];
+    std::vector<int> arp(nb + 1, 0), aci, ord(nb), epos(nb), lrp, lci, lev, dev, col, used, cnt;
     // block graph (local indices, flat CSR): A restricted to the block, plus,
     // for interior blocks, the pattern of Ehat Ehat^T
-    arp.assign(nb + 1, 0);
-    aci.clear();
     for (int t = 0; t < nb; t++) {
       const int i = mem[t];
       const size_t a0 = aci.size();
@@ -112,7 +240,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
           for (int q2 = rp[j]; q2 < rp[j + 1]; q2++) {
             const int r = ci[q2];
             if (r != i && !iface[r]) {
-              if (blk_of[r] != b) { err = "Ehat Ehat^T couples two subdomains"; return DDLR_ERR_INVALID; }
+              if (blk_of[r] != b) { blk_err[b] = "Ehat Ehat^T couples two subdomains"; return; }
               aci.push_back(loc[r]);
             }
           }
@@ -123,8 +251,6 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       arp[t + 1] = int(aci.size());
     }
     // elimination order
-    ord.resize(nb);
-    epos.resize(nb);
     std::iota(ord.begin(), ord.end(), 0);
     if ((b == p && opt.c_order == 1) || (b < p && opt.b_order == 1)) {
       col.assign(nb, -1);
@@ -137,7 +263,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         col[t] = c;
         nc = std::max(nc, c + 1);
       }
-      if (b == p) P.ncolors = nc;
+      blk_colors[b] = nc;
       // stable counting sort by colour
       cnt.assign(nc + 1, 0);
       for (int t = 0; t < nb; t++) cnt[col[t] + 1]++;
@@ -147,7 +273,6 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     for (int e = 0; e < nb; e++) epos[ord[e]] = e;
     // lower pattern in elimination positions (flat CSR lrp/lci)
     lrp.assign(nb + 1, 0);
-    lci.clear();
     for (int e = 0; e < nb; e++) {
       const int t = ord[e];
       const size_t l0 = lci.size();
@@ -166,7 +291,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         std::sort(c.begin(), c.end());
         c.erase(std::unique(c.begin(), c.end()), c.end());
         total += (long long)c.size();
-        if (total > 60000000LL) { err = "exact factor too large"; return DDLR_ERR_INVALID; }
+        if (total > 60000000LL) { blk_err[b] = "exact factor too large"; return; }
         if (!c.empty()) {
           int par = c[0];
           for (size_t t = 1; t < c.size(); t++) cols[par].push_back(c[t]);
@@ -188,8 +313,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       lev[e] = l;
       maxlev = std::max(maxlev, l);
     }
-    if (b < p) P.levels_interior = std::max(P.levels_interior, nb ? maxlev + 1 : 0);
-    else P.levels_c = maxlev + 1;
+    blk_levels[b] = nb ? maxlev + 1 : 0;
     // device order: (level, elimination position), stable counting sort
     cnt.assign(maxlev + 2, 0);
     for (int e = 0; e < nb; e++) cnt[lev[e] + 1]++;
@@ -198,98 +322,122 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     for (int e = 0; e < nb; e++) dev[cnt[lev[e]]++] = e;
     std::vector<int> drow(nb);   // elimination position -> device row
     for (int d = 0; d < nb; d++) drow[dev[d]] = row_w + d;
+    std::vector<int> &lowb = low_blk[b];
+    lowb.reserve(lci.size());
     for (int d = 0; d < nb; d++) {
       const int e = dev[d];
       const int i = mem[ord[e]];
       P.perm[row_w + d] = i;
       level_of[i] = lev[e];
-      for (int q = lrp[e]; q < lrp[e + 1]; q++) low_ci.push_back(drow[lci[q]]);
-      low_rp[row_w + d + 1] = int(low_ci.size());
+      for (int q = lrp[e]; q < lrp[e + 1]; q++) lowb.push_back(drow[lci[q]]);
+      low_cnt[row_w + d] = lrp[e + 1] - lrp[e];
     }
-    row_w += nb;
-  }
-  P.blk_row0[p + 1] = row_w;
-  for (int g = 0; g < n; g++) P.iperm[P.perm[g]] = g;
+  });
+  for (int b = 0; b <= p; b++)
+    if (blk_err[b]) { err = blk_err[b]; return DDLR_ERR_INVALID; }
+  for (int b = 0; b < p; b++) P.levels_interior = std::max(P.levels_interior, blk_levels[b]);
+  P.levels_c = std::max(1, blk_levels[p]);
+  if (opt.c_order == 1) P.ncolors = blk_colors[p];
+  std::vector<int> low_rp, low_ci;
+  prefix(low_cnt, low_rp);
+  low_ci.resize(low_rp[n]);
+  pool.run_dynamic(p + 1, [&](int b) {
+    std::copy(low_blk[b].begin(), low_blk[b].end(), low_ci.begin() + low_rp[P.blk_row0[b]]);
+  });
+  std::vector<std::vector<int>>().swap(low_blk);
+  pool.run(n, [&](long long lo, long long hi) {
+    for (int g = int(lo); g < int(hi); g++) P.iperm[P.perm[g]] = g;
+  });
   const int m = P.m;
 
   // ---- A in device order, sliced ELL for the SpMV
   {
-    int ns = (n + kSlice - 1) / kSlice;
+    const int ns = (n + kSlice - 1) / kSlice;
     P.a_nslice = ns;
-    P.a_soff.assign(ns + 1, 0);
     P.a_sw.assign(ns, 0);
-    for (int g = 0; g < ns; g++) {
-      int w = 0;
-      for (int l = 0; l < kSlice; l++) {
-        int r = g * kSlice + l;
-        if (r < n) { int i = P.perm[r]; w = std::max(w, rp[i + 1] - rp[i]); }
+    pool.run(ns, [&](long long lo, long long hi) {
+      for (int g = int(lo); g < int(hi); g++) {
+        int w = 0;
+        for (int l = 0; l < kSlice; l++) {
+          const int r = g * kSlice + l;
+          if (r < n) { const int i = P.perm[r]; w = std::max(w, rp[i + 1] - rp[i]); }
+        }
+        P.a_sw[g] = w;
       }
-      P.a_sw[g] = w;
-      P.a_soff[g + 1] = P.a_soff[g] + w * kSlice;
-    }
+    }, 256);
+    P.a_soff.assign(ns + 1, 0);
+    for (int g = 0; g < ns; g++) P.a_soff[g + 1] = P.a_soff[g] + P.a_sw[g] * kSlice;
     P.a_col.assign(P.a_soff[ns], 0);
     P.a_src.assign(P.a_soff[ns], -1);
-    std::vector<std::pair<int, int>> ent;
-    for (int g = 0; g < ns; g++)
-      for (int l = 0; l < kSlice; l++) {
-        int r = g * kSlice + l;
-        int rr = r < n ? r : n - 1;
-        ent.clear();
-        if (r < n) {
-          int i = P.perm[r];
-          for (int q = rp[i]; q < rp[i + 1]; q++) ent.push_back({P.iperm[ci[q]], q});
-          std::sort(ent.begin(), ent.end());
+    pool.run(ns, [&](long long lo, long long hi) {
+      std::vector<std::pair<int, int>> ent;
+      for (int g = int(lo); g < int(hi); g++)
+        for (int l = 0; l < kSlice; l++) {
+          const int r = g * kSlice + l;
+          const int rr = r < n ? r : n - 1;
+          ent.clear();
+          if (r < n) {
+            const int i = P.perm[r];
+            for (int q = rp[i]; q < rp[i + 1]; q++) ent.push_back({P.iperm[ci[q]], q});
+            std::sort(ent.begin(), ent.end());
+          }
+          for (int kk = 0; kk < P.a_sw[g]; kk++) {
+            const int slot = P.a_soff[g] + kk * kSlice + l;
+            if (kk < int(ent.size())) { P.a_col[slot] = ent[kk].first; P.a_src[slot] = ent[kk].second; }
+            else { P.a_col[slot] = rr; P.a_src[slot] = -1; }
+          }
         }
-        for (int kk = 0; kk < P.a_sw[g]; kk++) {
-          int slot = P.a_soff[g] + kk * kSlice + l;
-          if (kk < int(ent.size())) { P.a_col[slot] = ent[kk].first; P.a_src[slot] = ent[kk].second; }
-          else { P.a_col[slot] = rr; P.a_src[slot] = -1; }
-        }
-      }
+    }, 256);
   }
 
-  // ---- Ehat (interior rows) and Ehat^T (interface rows)
-  P.eh_rp.assign(m + 1, 0);
-  for (int g = 0; g < m; g++) {
-    int i = P.perm[g];
-    std::vector<std::pair<int, int>> ent;
-    for (int q = rp[i]; q < rp[i + 1]; q++)
-      if (iface[ci[q]]) ent.push_back({P.iperm[ci[q]] - m, q});
-    std::sort(ent.begin(), ent.end());
-    for (auto &e : ent) { P.eh_ci.push_back(e.first); P.eh_src.push_back(e.second); }
-    P.eh_rp[g + 1] = int(P.eh_ci.size());
+  // ---- Ehat (interior rows) and Ehat^T (interface rows): count, prefix, fill
+  {
+    auto build = [&](int rows, int row0, bool want_iface, int shift, std::vector<int> &rpo,
+                     std::vector<int> &cio, std::vector<int> &srco) {
+      std::vector<int> cntr(rows, 0);
+      pool.run(rows, [&](long long lo, long long hi) {
+        for (int g = int(lo); g < int(hi); g++) {
+          const int i = P.perm[row0 + g];
+          int c = 0;
+          for (int q = rp[i]; q < rp[i + 1]; q++) c += (iface[ci[q]] != 0) == want_iface;
+          cntr[g] = c;
+        }
+      });
+      prefix(cntr, rpo);
+      cio.resize(rpo[rows]);
+      srco.resize(rpo[rows]);
+      pool.run(rows, [&](long long lo, long long hi) {
+        std::vector<std::pair<int, int>> ent;
+        for (int g = int(lo); g < int(hi); g++) {
+          const int i = P.perm[row0 + g];
+          ent.clear();
+          for (int q = rp[i]; q < rp[i + 1]; q++)
+            if ((iface[ci[q]] != 0) == want_iface) ent.push_back({P.iperm[ci[q]] - shift, q});
+          std::sort(ent.begin(), ent.end());
+          for (size_t t = 0; t < ent.size(); t++) {
+            cio[rpo[g] + t] = ent[t].first;
+            srco[rpo[g] + t] = ent[t].second;
+          }
+        }
+      });
+    };
+    build(m, 0, true, m, P.eh_rp, P.eh_ci, P.eh_src);
+    build(s, m, false, 0, P.eht_rp, P.eht_ci, P.eht_src);
   }
   P.nnz_ehat = (long long)P.eh_ci.size();
-  P.eht_rp.assign(s + 1, 0);
-  for (int j = 0; j < s; j++) {
-    int i = P.perm[m + j];
-    std::vector<std::pair<int, int>> ent;
-    for (int q = rp[i]; q < rp[i + 1]; q++)
-      if (!iface[ci[q]]) ent.push_back({P.iperm[ci[q]], q});
-    std::sort(ent.begin(), ent.end());
-    for (auto &e : ent) { P.eht_ci.push_back(e.first); P.eht_src.push_back(e.second); }
-    P.eht_rp[j + 1] = int(P.eht_ci.size());
-  }
 
-  // ---- factor pattern in device order with value sources
-  P.f_rp.assign(n + 1, 0);
+  // ---- factor pattern in device order with value sources: row g holds its
+  // lower columns (ascending) and the diagonal last; the Ehat Ehat^T terms of
+  // each entry are counted in a first pass and written in a second
   {
-    const size_t nf_est = low_ci.size() + size_t(n);
-    P.f_ci.reserve(nf_est); P.f_row.reserve(nf_est); P.f_src.reserve(nf_est);
-    P.f_prp.reserve(nf_est + 1); P.f_cdiag.reserve(nf_est);
-  }
-  P.f_prp.push_back(0);
-  std::vector<std::array<int, 3>> pairs;
-  std::vector<int> cols;
-  for (int g = 0; g < n; g++) {
-    const int i = P.perm[g];
-    const int b = blk_of[i];
-    cols.assign(low_ci.begin() + low_rp[g], low_ci.begin() + low_rp[g + 1]);
-    cols.push_back(g);
-    std::sort(cols.begin(), cols.end());
-    // Ehat Ehat^T contributions of row i: (original column, pa, pb)
-    pairs.clear();
-    if (b < p) {
+    P.f_rp.assign(n + 1, 0);
+    for (int g = 0; g < n; g++) P.f_rp[g + 1] = P.f_rp[g] + low_cnt[g] + 1;
+    const long long nf = P.f_rp[n];
+    P.f_ci.resize(nf); P.f_row.resize(nf); P.f_src.resize(nf); P.f_cdiag.resize(nf);
+    std::vector<int> ecnt(nf, 0);   // Ehat Ehat^T terms per factor entry
+    // (original column, pa, pb) for row i of an interior block
+    auto row_pairs = [&](int i, std::vector<std::array<int, 3>> &pairs) {
+      pairs.clear();
       for (int q = rp[i]; q < rp[i + 1]; q++) {
         const int j = ci[q];
         if (!iface[j]) continue;
@@ -299,20 +447,52 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
           pairs.push_back({r, q, find_pos(rp, ci, r, j)});
         }
       }
-    }
-    for (int c : cols) {
-      const int j = P.perm[c];
-      P.f_ci.push_back(c);
-      P.f_row.push_back(g);
-      P.f_src.push_back(find_pos(rp, ci, i, j));
-      for (const auto &pr : pairs)
-        if (pr[0] == j) { P.f_pa.push_back(pr[1]); P.f_pb.push_back(pr[2]); }
-      P.f_prp.push_back(int(P.f_pa.size()));
-      P.f_cdiag.push_back((b == p && c == g) ? 1 : 0);
-    }
-    P.f_rp[g + 1] = int(P.f_ci.size());
+    };
+    pool.run(n, [&](long long lo, long long hi) {
+      std::vector<std::array<int, 3>> pairs;
+      std::vector<int> cols;
+      for (int g = int(lo); g < int(hi); g++) {
+        const int i = P.perm[g];
+        const int b = blk_of[i];
+        cols.assign(low_ci.begin() + low_rp[g], low_ci.begin() + low_rp[g + 1]);
+        cols.push_back(g);
+        std::sort(cols.begin(), cols.end());
+        if (b < p) row_pairs(i, pairs); else pairs.clear();
+        long long e = P.f_rp[g];
+        for (int c : cols) {
+          const int j = P.perm[c];
+          P.f_ci[e] = c;
+          P.f_row[e] = g;
+          P.f_src[e] = find_pos(rp, ci, i, j);
+          P.f_cdiag[e] = (b == p && c == g) ? 1 : 0;
+          int k = 0;
+          for (const auto &pr : pairs) k += pr[0] == j;
+          ecnt[e] = k;
+          e++;
+        }
+      }
+    });
+    prefix(ecnt, P.f_prp);
+    P.f_pa.resize(P.f_prp[nf]);
+    P.f_pb.resize(P.f_prp[nf]);
+    pool.run(n, [&](long long lo, long long hi) {
+      std::vector<std::array<int, 3>> pairs;
+      for (int g = int(lo); g < int(hi); g++) {
+        const int i = P.perm[g];
+        if (blk_of[i] >= p) continue;
+        row_pairs(i, pairs);
+        if (pairs.empty()) continue;
+        for (long long e = P.f_rp[g]; e < P.f_rp[g + 1]; e++) {
+          const int j = P.perm[P.f_ci[e]];
+          int w = P.f_prp[e];
+          for (const auto &pr : pairs)
+            if (pr[0] == j) { P.f_pa[w] = pr[1]; P.f_pb[w] = pr[2]; w++; }
+        }
+      }
+    });
   }
   P.nnz_factor = (long long)P.f_ci.size();
+  std::vector<int>().swap(low_ci);
 
   // ---- level records, slices and the triangular-solve layouts
   P.blk_lvl0.assign(p + 2, 0);
@@ -337,15 +517,14 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   for (int l = 0; l < nlev; l++)
     P.lvl_slice0[l + 1] = P.lvl_slice0[l] + (P.lvl_nrows[l] + kSlice - 1) / kSlice;
   P.nslice = P.lvl_slice0[nlev];
-  // factorisation schedule by local level number
+  // factorisation schedule by local level number (stable counting sort)
   {
-    std::vector<std::vector<int>> byL(maxL);
-    for (int g = 0; g < n; g++) byL[level_of[P.perm[g]]].push_back(g);
-    P.fl_ptr.assign(maxL + 1, 0);
-    for (int L = 0; L < maxL; L++) {
-      for (int g : byL[L]) P.fl_rows.push_back(g);
-      P.fl_ptr[L + 1] = int(P.fl_rows.size());
-    }
+    std::vector<int> lc(maxL, 0);
+    for (int g = 0; g < n; g++) lc[level_of[P.perm[g]]]++;
+    prefix(lc, P.fl_ptr);
+    P.fl_rows.resize(n);
+    std::vector<int> fill(P.fl_ptr.begin(), P.fl_ptr.end() - 1);
+    for (int g = 0; g < n; g++) P.fl_rows[fill[level_of[P.perm[g]]]++] = g;
   }
   // upper (L^T) rows: for device row c, the factor entries (g, c), g != c,
   // in ascending g (flat CSR up_rp / up_q)
@@ -361,8 +540,8 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   }
   auto upper_size = [&](int r) { return up_rp[r + 1] - up_rp[r]; };
   auto upper_at = [&](int r, int kk) { return up_q[up_rp[r] + kk]; };
-  P.l_soff.assign(P.nslice + 1, 0); P.l_sw.assign(P.nslice, 0);
-  P.u_soff.assign(P.nslice + 1, 0); P.u_sw.assign(P.nslice, 0);
+  P.l_sw.assign(P.nslice, 0);
+  P.u_sw.assign(P.nslice, 0);
   std::vector<int> slice_row0(P.nslice), slice_rows(P.nslice), slice_blk(P.nslice);
   for (int b = 0; b <= p; b++)
     for (int l = P.blk_lvl0[b]; l < P.blk_lvl0[b + 1]; l++)
@@ -372,44 +551,52 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         slice_rows[g] = std::min(kSlice, P.lvl_nrows[l] - off);
         slice_blk[g] = b;
       }
-  for (int g = 0; g < P.nslice; g++) {
-    int wl = 0, wu = 0;
-    for (int t = 0; t < slice_rows[g]; t++) {
-      int r = slice_row0[g] + t;
-      wl = std::max(wl, P.f_rp[r + 1] - P.f_rp[r] - 1);
-      wu = std::max(wu, upper_size(r));
+  pool.run(P.nslice, [&](long long lo, long long hi) {
+    for (int g = int(lo); g < int(hi); g++) {
+      int wl = 0, wu = 0;
+      for (int t = 0; t < slice_rows[g]; t++) {
+        int r = slice_row0[g] + t;
+        wl = std::max(wl, P.f_rp[r + 1] - P.f_rp[r] - 1);
+        wu = std::max(wu, upper_size(r));
+      }
+      P.l_sw[g] = wl; P.u_sw[g] = wu;
     }
-    P.l_sw[g] = wl; P.u_sw[g] = wu;
-    P.l_soff[g + 1] = P.l_soff[g] + wl * kSlice;
-    P.u_soff[g + 1] = P.u_soff[g] + wu * kSlice;
+  }, 256);
+  P.l_soff.assign(P.nslice + 1, 0);
+  P.u_soff.assign(P.nslice + 1, 0);
+  for (int g = 0; g < P.nslice; g++) {
+    P.l_soff[g + 1] = P.l_soff[g] + P.l_sw[g] * kSlice;
+    P.u_soff[g + 1] = P.u_soff[g] + P.u_sw[g] * kSlice;
   }
   P.l_col.assign(P.l_soff[P.nslice], 0);
   P.u_col.assign(P.u_soff[P.nslice], 0);
   P.map_l.assign(P.nnz_factor, -1);
   P.map_u.assign(P.nnz_factor, -1);
-  for (int g = 0; g < P.nslice; g++) {
-    int b = slice_blk[g];
-    int first = P.blk_row0[b], last = P.blk_row0[b + 1] - 1;
-    for (int t = 0; t < kSlice; t++) {
-      int r = slice_row0[g] + t;
-      bool live = t < slice_rows[g];
-      int nl = live ? P.f_rp[r + 1] - P.f_rp[r] - 1 : 0;
-      for (int kk = 0; kk < P.l_sw[g]; kk++) {
-        int slot = P.l_soff[g] + kk * kSlice + t;
-        if (kk < nl) { int q = P.f_rp[r] + kk; P.l_col[slot] = P.f_ci[q]; P.map_l[q] = slot; }
-        else P.l_col[slot] = first;   // level-0 row: final before any use
-      }
-      int nu = live ? upper_size(r) : 0;
-      for (int kk = 0; kk < P.u_sw[g]; kk++) {
-        int slot = P.u_soff[g] + kk * kSlice + t;
-        if (kk < nu) { int q = upper_at(r, kk); P.u_col[slot] = P.f_row[q]; P.map_u[q] = slot; }
-        else P.u_col[slot] = last;    // top-level row: final before any use
+  pool.run(P.nslice, [&](long long lo, long long hi) {
+    for (int g = int(lo); g < int(hi); g++) {
+      int b = slice_blk[g];
+      int first = P.blk_row0[b], last = P.blk_row0[b + 1] - 1;
+      for (int t = 0; t < kSlice; t++) {
+        int r = slice_row0[g] + t;
+        bool live = t < slice_rows[g];
+        int nl = live ? P.f_rp[r + 1] - P.f_rp[r] - 1 : 0;
+        for (int kk = 0; kk < P.l_sw[g]; kk++) {
+          int slot = P.l_soff[g] + kk * kSlice + t;
+          if (kk < nl) { int q = P.f_rp[r] + kk; P.l_col[slot] = P.f_ci[q]; P.map_l[q] = slot; }
+          else P.l_col[slot] = first;   // level-0 row: final before any use
+        }
+        int nu = live ? upper_size(r) : 0;
+        for (int kk = 0; kk < P.u_sw[g]; kk++) {
+          int slot = P.u_soff[g] + kk * kSlice + t;
+          if (kk < nu) { int q = upper_at(r, kk); P.u_col[slot] = P.f_row[q]; P.map_u[q] = slot; }
+          else P.u_col[slot] = last;    // top-level row: final before any use
+        }
       }
     }
-  }
+  }, 256);
   // level chunks: all blocks by level number, and C_a alone
   {
-    const int maxL = int(P.fl_ptr.size()) - 1;
+    const int maxL2 = int(P.fl_ptr.size()) - 1;
     auto add = [&](int rec) {
       for (int i0 = 0; i0 < P.lvl_nrows[rec]; i0 += kChunk) {
         P.chunks.push_back(rec);
@@ -418,14 +605,14 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         P.chunks.push_back(0);
       }
     };
-    P.ch_all_ptr.assign(maxL + 1, 0);
-    for (int L = 0; L < maxL; L++) {
+    P.ch_all_ptr.assign(maxL2 + 1, 0);
+    for (int L = 0; L < maxL2; L++) {
       for (int b = 0; b <= p; b++)
         if (P.blk_lvl0[b] + L < P.blk_lvl0[b + 1]) add(P.blk_lvl0[b] + L);
       P.ch_all_ptr[L + 1] = int(P.chunks.size() / 4);
     }
     const int Lc = P.blk_lvl0[p + 1] - P.blk_lvl0[p];
-    P.ch_c_ptr.assign(Lc + 1, P.ch_all_ptr[maxL]);
+    P.ch_c_ptr.assign(Lc + 1, P.ch_all_ptr[maxL2]);
     for (int L = 0; L < Lc; L++) {
       add(P.blk_lvl0[p] + L);
       P.ch_c_ptr[L + 1] = int(P.chunks.size() / 4);
@@ -438,13 +625,15 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       P.row_slot[P.lvl_row0[l] + i] = (P.lvl_slice0[l] + i / kSlice) * kSlice + i % kSlice;
   P.l_span.assign(2 * size_t(n), 0);
   P.u_span.assign(2 * size_t(n), 0);
-  for (int g = 0; g < n; g++) {
-    const int sl = P.row_slot[g] / kSlice, ln = P.row_slot[g] % kSlice;
-    P.l_span[2 * g] = P.l_soff[sl] + ln;
-    P.l_span[2 * g + 1] = P.f_rp[g + 1] - P.f_rp[g] - 1;
-    P.u_span[2 * g] = P.u_soff[sl] + ln;
-    P.u_span[2 * g + 1] = upper_size(g);
-  }
+  pool.run(n, [&](long long lo, long long hi) {
+    for (int g = int(lo); g < int(hi); g++) {
+      const int sl = P.row_slot[g] / kSlice, ln = P.row_slot[g] % kSlice;
+      P.l_span[2 * g] = P.l_soff[sl] + ln;
+      P.l_span[2 * g + 1] = P.f_rp[g + 1] - P.f_rp[g] - 1;
+      P.u_span[2 * g] = P.u_soff[sl] + ln;
+      P.u_span[2 * g + 1] = upper_size(g);
+    }
+  });
   for (int b = 0; b < p; b++) {
     const int l0 = P.blk_lvl0[b], l1 = P.blk_lvl0[b + 1];
     if (l1 == l0) continue;
