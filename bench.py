@@ -109,13 +109,15 @@ class Clocks:
 
 def _traffic_from_profile():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, valid only while the kernel sources are unchanged."""
+    summary, valid only while the kernel sources (both headers) are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = os.path.join(ROOT, "paper_1505_04341_gb300", "csrc", "ddlr_kernels.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("ddlr_kernels.cuh", "ddlr_persist.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1505_04341_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:16]
     if d.get("kernels_sha") != sha:
         return None
     return d
