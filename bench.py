@@ -360,6 +360,25 @@ def run_ours(args):
                  "single_rhs_iterations": inf1[0]["its"], "maxit": MAXIT4,
                  "autotuned_block": [info4["batch_block_chunks"], info4["batch_block_elem"]]}
         h4.close()
+        # the plain FP64 form on the same problem, one right-hand side
+        h5 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
+                      scale_diag=1, precision=0)
+        x5 = torch.zeros_like(b1)
+        h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
+        flush.fill_(1.0)
+        f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        f0.record(stream)
+        h5.refactor()
+        f1.record(stream)
+        _, inf5 = h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
+        f2.record(stream)
+        f2.synchronize()
+        batch["fp64_single_rhs"] = {"setup_ms": round(f0.elapsed_time(f1), 3),
+                                    "solve_ms": round(f1.elapsed_time(f2), 3),
+                                    "iterations": inf5[0]["its"], "true_relres": inf5[0]["relres"]}
+        batch["mixed_batched_per_rhs_speedup_vs_fp64_single"] = round(
+            f1.elapsed_time(f2) / (e1.elapsed_time(e2) / 32), 2)
+        h5.close()
         del B4, X4
 
     # serving line: 512 requests over grid edges {32, 48, 64, 96, 128}

@@ -95,7 +95,10 @@ struct ddlr_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Plan P;
   std::string err;
-  std::vector<void *> allocs;
+  std::vector<void *> allocs;   // device chunks of the handle's arena
+  char *arena_cur = nullptr;
+  size_t arena_left = 0;
+  static constexpr size_t kArenaChunk = size_t(32) << 20;
   long long dev_bytes = 0;
 
   // plan arrays on the device
@@ -183,12 +186,23 @@ struct ddlr_ctx {
 
   template <typename T>
   T *alloc(size_t n) {
+    // bump allocation (256-byte aligned) from chunks of at least kArenaChunk
+    // bytes: one cudaMalloc per chunk instead of one per array
     if (n == 0) n = 1;
-    void *p = nullptr;
-    ck(cudaMalloc(&p, n * sizeof(T)), "cudaMalloc");
-    allocs.push_back(p);
-    dev_bytes += (long long)(n * sizeof(T));
-    return (T *)p;
+    const size_t bytes = (n * sizeof(T) + 255) & ~size_t(255);
+    if (bytes > arena_left) {
+      const size_t chunk = std::max(bytes, kArenaChunk);
+      void *p = nullptr;
+      ck(cudaMalloc(&p, chunk), "cudaMalloc");
+      allocs.push_back(p);
+      arena_cur = static_cast<char *>(p);
+      arena_left = chunk;
+    }
+    T *r = reinterpret_cast<T *>(arena_cur);
+    arena_cur += bytes;
+    arena_left -= bytes;
+    dev_bytes += (long long)bytes;
+    return r;
   }
   template <typename T>
   T *upload(const std::vector<T> &v) {
@@ -199,6 +213,8 @@ struct ddlr_ctx {
   void release() {
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
+    arena_cur = nullptr;
+    arena_left = 0;
     dev_bytes = 0;
   }
 
@@ -557,13 +573,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
       ck(cudaMallocHost(&W.h_st, sizeof(LzState)), "cudaMallocHost");
       ck(cudaEventCreateWithFlags(&W.ev_chk, cudaEventDisableTiming), "event");
       ck(cudaEventCreateWithFlags(&W.ev_done, cudaEventDisableTiming), "event");
-      std::vector<int> rank(s);
-      {
-        std::vector<std::pair<int, int>> o(s);
-        for (int j = 0; j < s; j++) o[j] = {P.perm[m0 + j], j};
-        std::sort(o.begin(), o.end());
-        for (int r = 0; r < s; r++) rank[o[r].second] = r;
-      }
+      const std::vector<int> &rank = P.iface_rank;
       std::vector<double> byrank(s), hv(s);
       double nn = 0;
       for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }

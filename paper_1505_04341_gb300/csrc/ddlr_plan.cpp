@@ -349,6 +349,10 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     for (int g = int(lo); g < int(hi); g++) P.iperm[P.perm[g]] = g;
   });
   const int m = P.m;
+  // the interface list is in ascending original index, so a node's place in
+  // it is its rank in that order
+  P.iface_rank.resize(s);
+  for (int j = 0; j < s; j++) P.iface_rank[j] = loc[P.perm[m + j]];
 
   // ---- A in device order, sliced ELL for the SpMV
   {

@@ -24,6 +24,7 @@ struct Plan {
   // ordering: device order ("new") -> original index, and inverse
   std::vector<int> perm, iperm;
   std::vector<int> blk_row0;   // p+2: block b = rows [blk_row0[b], blk_row0[b+1]); block p = C_a
+  std::vector<int> iface_rank; // s: rank of interface row m+j in ascending original index
   // original CSR helpers (for scaling on the device)
   std::vector<int> orig_row;   // nnz: row of each original entry
   std::vector<int> orig_col;   // nnz: column of each original entry
