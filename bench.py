@@ -399,15 +399,19 @@ def run_ours(args):
         srv.close()
 
     # end to end through the C ABI from host buffers
-    e2e_ms = []
+    e2e_ms, e2e_parts = [], []
     for i in range(args.steps + 1):
         t0 = time.perf_counter()
         he = pkg.DDLR(A, part, p, **OPTS)
+        t1 = time.perf_counter()
         xh, _ = he.pcg(b_host, tol=TOL)
         dt = (time.perf_counter() - t0) * 1e3
+        pinfo = he.info()
         he.close()
         if i > 0:
             e2e_ms.append(dt)
+            e2e_parts.append({"setup_ms": round((t1 - t0) * 1e3, 2), "plan_ms": round(pinfo["plan_ms"], 2),
+                              "pcg_ms": round(dt - (t1 - t0) * 1e3, 2)})
     e2e = statistics.mean(e2e_ms)
     if ws > 1:
         t = torch.tensor([e2e], device="cuda", dtype=torch.float64)
@@ -445,6 +449,7 @@ def run_ours(args):
                                 "apply_algorithmic_GBps": round(mixed_apply_gbs, 1)},
             "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
                                             "iterations": [i["its"] for i in inf_nat]},
+            "e2e_parts": e2e_parts,
             "precision_lap3d_128_b8_k32": prec,
             "batching_jump3d_96_cut5_32rhs": batch,
             "serving_lap3d_32_to_128_512req": serving,
