@@ -128,6 +128,8 @@ struct ddlr_ctx {
   TmaCfg tma64{}, tma32{};
   bool use_tma64 = false, use_tma32 = false;
   bool use_sf64 = false, use_sf32 = false;   // synchronisation-free interior solve
+  int chunk_rows = 0;         // rows per thread of the level-chunk solve: 0 = 2 (FP64) / 4 (FP32);
+                              // DDLR_CHUNK_ROWS=1|2|4 fixes it
   int2 *l_span = nullptr, *u_span = nullptr;
   int *blk_row0 = nullptr;
   int *chunks = nullptr;
@@ -341,6 +343,7 @@ template <> struct Prec<float> {
 // ----------------------------------------------------------- A0 solve
 // z = A0^-1 x in device order: all interior blocks in one launch (CTA per
 // block) on the main stream, the C_a levels on the second stream.
+static_assert(kChunk == kThreads, "a level chunk is one CTA's rows");
 constexpr int kShallowLevels = 8;   // at most this deep: solve level by level over all blocks
 
 // levels [L0, L1) of the chunk lists ptr: forward up to the top, the top
@@ -351,9 +354,16 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
   const int nL = int(ptr.size()) - 1;
   auto launch = [&](int L, int mode) {
     const int nch = ptr[L + 1] - ptr[L];
-    if (nch > 0)
-      KL(c, fam, st, k_sptrsv_chunks<T>, nch, kThreads, 0, c->S,
-         reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, x, z, gate);
+    if (nch <= 0) return;
+    const int4 *chk = reinterpret_cast<const int4 *>(c->chunks) + ptr[L];
+    // measured at 128^3 (A0 solve): FP64 best with 2 rows per thread, FP32 with 4
+    const int rows = c->chunk_rows ? c->chunk_rows : (sizeof(T) == 8 ? 2 : 4);
+    if (rows == 4)
+      KL(c, fam, st, (k_sptrsv_chunks<T, 4>), nch, kThreads / 4, 0, c->S, chk, mode, lv, uv, di, x, z, gate);
+    else if (rows == 2)
+      KL(c, fam, st, (k_sptrsv_chunks<T, 2>), nch, kThreads / 2, 0, c->S, chk, mode, lv, uv, di, x, z, gate);
+    else
+      KL(c, fam, st, (k_sptrsv_chunks<T, 1>), nch, kThreads, 0, c->S, chk, mode, lv, uv, di, x, z, gate);
   };
   for (int L = 0; L + 1 < nL; L++) launch(L, 0);
   if (nL > 0) launch(nL - 1, 2);
@@ -982,6 +992,8 @@ void allocate(ddlr_ctx *c) {
     // (DDLR_SOLVE=tma|sf|plain)
     const char *env = getenv("DDLR_SOLVE");
     const std::string kind = env ? env : "tma";
+    const char *cr = getenv("DDLR_CHUNK_ROWS");
+    if (cr && (cr[0] == '1' || cr[0] == '2' || cr[0] == '4')) c->chunk_rows = cr[0] - '0';
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

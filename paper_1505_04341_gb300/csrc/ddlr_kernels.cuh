@@ -436,25 +436,55 @@ k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l
   for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
 }
 
+// solve_row without the store: the value z_r takes (forward or backward)
+template <typename T, bool FWD>
+__device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val, const T *dinv, const T *x,
+                                             const T *z, int slice, int lane, int r) {
+  const int *soff = FWD ? S.l_soff : S.u_soff;
+  const int *sw = FWD ? S.l_sw : S.u_sw;
+  const int *col = FWD ? S.l_col : S.u_col;
+  const int off = soff[slice] + lane, w = sw[slice];
+  T acc = FWD ? x[r] : z[r];
+  for (int kk = 0; kk < w; kk++) {
+    const int c = col[off + kk * 32];
+    acc -= val[off + kk * 32] * z[c];
+  }
+  return acc * dinv[r];
+}
+
 // One dependency level of many blocks in one launch: CTA q solves chunk q
-// = (level record, first row, rows) of that level; mode 0 forward, 1
-// backward, 2 forward then backward (a level that is the top level of every
-// block it contains).
-template <typename T>
-__global__ void k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode,
-                                const T *lval, const T *uval, const T *dinv,
-                                const T *x, T *z, const int *gate) {
+// = (level record, first row, rows <= kThreads) of that level; mode 0
+// forward, 1 backward, 2 forward then backward (a level that is the top
+// level of every block it contains).  Each of the kThreads / R threads
+// solves R rows: it computes all R values (loads only: rows of one level do
+// not depend on each other) before storing any, so R dependent load chains
+// are in flight per thread.  The value of each row does not depend on R.
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads / R)
+k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, const T *uval, const T *dinv,
+                const T *x, T *z, const int *gate) {
   if (gate && *gate) return;
+  constexpr int NT = kThreads / R;
   const int4 ch = chunks[blockIdx.x];
   const int lvl = ch.x, r0 = S.lvl_row0[lvl], s0 = S.lvl_slice0[lvl];
-  for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += blockDim.x) {
+  T v[R];
+#pragma unroll
+  for (int u = 0; u < R; u++) {
+    const int t = threadIdx.x + u * NT;
+    if (t >= ch.z) continue;
+    const int i = ch.y + t;
     const int r = r0 + i, sl = s0 + (i >> 5), ln = i & 31;
     if (mode == 1) {
-      solve_row<T, false>(S, uval, dinv, x, z, sl, ln, r);
+      v[u] = solve_row_value<T, false>(S, uval, dinv, x, z, sl, ln, r);
     } else {
-      solve_row<T, true>(S, lval, dinv, x, z, sl, ln, r);
-      if (mode == 2) z[r] = z[r] * dinv[r];
+      v[u] = solve_row_value<T, true>(S, lval, dinv, x, z, sl, ln, r);
+      if (mode == 2) v[u] = v[u] * dinv[r];
     }
+  }
+#pragma unroll
+  for (int u = 0; u < R; u++) {
+    const int t = threadIdx.x + u * NT;
+    if (t < ch.z) z[r0 + ch.y + t] = v[u];
   }
 }
 

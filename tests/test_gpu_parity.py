@@ -76,6 +76,31 @@ def test_a0_solve_and_factor_parity(name, kind, monkeypatch):
     h.close()
 
 
+@pytest.mark.parametrize("rows", ["1", "2", "4"])
+@pytest.mark.parametrize("name", ["3d_20_ic0_multicolour", "3d_24_ic0_multicolour_all", "jump_32_multicolour_all"])
+def test_level_chunk_solve_rows_per_thread(name, rows, monkeypatch):
+    """The level-chunk solve with 1, 2 or 4 rows per thread (all blocks of a
+    level per launch) against the oracle, FP64 and FP32; the FP64 result
+    does not depend on the rows per thread."""
+    A, part, p, factor, c_order = PROBLEMS[name]()
+    monkeypatch.setenv("DDLR_CHUNK_ROWS", rows)
+    monkeypatch.setenv("DDLR_PERSIST", "0")
+    orc = O.Oracle(A, part, p, k=4, factor=factor, **_orders(c_order))
+    x = W.rhs(A[0], 5)
+    ref = orc.a0_solve(x)
+    for precision, tol in ((0, 1e-12), (1, 1e-4)):
+        h = pkg.DDLR(A, part, p, rank_k=4, factor=factor, precision=precision, **_orders(c_order))
+        y = h.a0_solve(torch.tensor(x, device="cuda")).cpu().numpy()
+        assert _rel(y, ref) < tol, (precision, _rel(y, ref))
+        if precision == 0:
+            monkeypatch.setenv("DDLR_CHUNK_ROWS", "1")
+            h1 = pkg.DDLR(A, part, p, rank_k=4, factor=factor, **_orders(c_order))
+            assert np.array_equal(h1.a0_solve(torch.tensor(x, device="cuda")).cpu().numpy(), y)
+            h1.close()
+            monkeypatch.setenv("DDLR_CHUNK_ROWS", rows)
+        h.close()
+
+
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("name", ["2d_64x64_C1_exact", "3d_24_ic0_natural", "3d_20_ic0_multicolour",
                                   "jump_32_cuts", "3d_24_ic0_multicolour_all"])
