@@ -365,6 +365,11 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
     else
       KL(c, fam, st, (k_sptrsv_chunks<T, 1>), nch, kThreads, 0, c->S, chk, mode, lv, uv, di, x, z, gate);
   };
+  if (nL == 2) {            // multicolour factors: two launches, see modes 3 and 4
+    launch(1, 3);
+    launch(0, 4);
+    return;
+  }
   for (int L = 0; L + 1 < nL; L++) launch(L, 0);
   if (nL > 0) launch(nL - 1, 2);
   for (int L = nL - 2; L >= 0; L--) launch(L, 1);
@@ -1281,6 +1286,11 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
       KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,
          reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, X, Z, R, gate);
   };
+  if (nL == 2) {            // multicolour factors: two launches, see modes 3 and 4
+    launch(1, 3);
+    launch(0, 4);
+    return;
+  }
   for (int L = 0; L + 1 < nL; L++) launch(L, 0);
   if (nL > 0) launch(nL - 1, 2);
   for (int L = nL - 2; L >= 0; L--) launch(L, 1);

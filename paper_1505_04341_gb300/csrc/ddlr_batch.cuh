@@ -25,7 +25,7 @@ __device__ __forceinline__ void red_range(long long nrows, int g, int G, long lo
 }
 
 // one dependency level of many blocks, R right-hand sides: CTA q solves chunk q;
-// thread -> (row sub-index, column); mode as k_sptrsv_chunks
+// thread -> (row sub-index, column); mode as k_sptrsv_chunks (0-4)
 template <typename T>
 __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
                                    const T *lval, const T *uval, const T *dinv,
@@ -36,7 +36,8 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
   const int per = blockDim.x / R;
   const int q = threadIdx.x % R, sub = threadIdx.x / R;
   if (sub >= per) return;
-  const bool bwd = mode == 1;
+  const bool bwd = mode == 1 || mode == 4;
+  const bool from_x = mode == 3 || mode == 4;   // first forward level formed where read
   const int *soff = bwd ? S.u_soff : S.l_soff;
   const int *sw = bwd ? S.u_sw : S.l_sw;
   const int *col = bwd ? S.u_col : S.l_col;
@@ -44,12 +45,15 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
   for (int i = ch.y + sub; i < ch.y + ch.z; i += per) {
     const int r = r0 + i, sl = s0 + (i >> 5), ln = i & 31;
     const int off = soff[sl] + ln, w = sw[sl];
-    T acc = (bwd ? Z : X)[(long long)r * R + q];
-    for (int kk = 0; kk < w; kk++)
-      acc -= val[off + kk * 32] * Z[(long long)col[off + kk * 32] * R + q];
     const T d = dinv[r];
+    T acc = mode == 4 ? X[(long long)r * R + q] * d : (bwd ? Z : X)[(long long)r * R + q];
+    for (int kk = 0; kk < w; kk++) {
+      const int c = col[off + kk * 32];
+      const T zc = (from_x && !bwd) ? X[(long long)c * R + q] * dinv[c] : Z[(long long)c * R + q];
+      acc -= val[off + kk * 32] * zc;
+    }
     acc *= d;
-    if (mode == 2) acc *= d;
+    if (mode == 2 || mode == 3) acc *= d;
     Z[(long long)r * R + q] = acc;
   }
 }

@@ -436,18 +436,21 @@ k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l
   for (int i = tid; i < nb; i += NT) z[rb0 + i] = zs[i];
 }
 
-// solve_row without the store: the value z_r takes (forward or backward)
-template <typename T, bool FWD>
+// solve_row without the store: the value z_r takes (forward or backward).
+// FROM_X: the first forward level was not stored; its value x_c / L_cc is
+// formed where it is read (forward: the dependencies of a second-level row,
+// all on the first level; backward on the first level: the row's own value).
+template <typename T, bool FWD, bool FROM_X>
 __device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val, const T *dinv, const T *x,
                                              const T *z, int slice, int lane, int r) {
   const int *soff = FWD ? S.l_soff : S.u_soff;
   const int *sw = FWD ? S.l_sw : S.u_sw;
   const int *col = FWD ? S.l_col : S.u_col;
   const int off = soff[slice] + lane, w = sw[slice];
-  T acc = FWD ? x[r] : z[r];
+  T acc = FWD ? x[r] : (FROM_X ? x[r] * dinv[r] : z[r]);
   for (int kk = 0; kk < w; kk++) {
     const int c = col[off + kk * 32];
-    acc -= val[off + kk * 32] * z[c];
+    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? x[c] * dinv[c] : z[c]);
   }
   return acc * dinv[r];
 }
@@ -455,7 +458,10 @@ __device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val,
 // One dependency level of many blocks in one launch: CTA q solves chunk q
 // = (level record, first row, rows <= kThreads) of that level; mode 0
 // forward, 1 backward, 2 forward then backward (a level that is the top
-// level of every block it contains).  Each of the kThreads / R threads
+// level of every block it contains).  Two-level factors skip the first
+// forward level: mode 3 = mode 2 on the second level reading its
+// dependencies as x_c / L_cc, mode 4 = mode 1 on the first level starting
+// from x_r / L_rr (the values that level would have stored).  Each of the kThreads / R threads
 // solves R rows: it computes all R values (loads only: rows of one level do
 // not depend on each other) before storing any, so R dependent load chains
 // are in flight per thread.  The value of each row does not depend on R.
@@ -475,9 +481,13 @@ k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, cons
     const int i = ch.y + t;
     const int r = r0 + i, sl = s0 + (i >> 5), ln = i & 31;
     if (mode == 1) {
-      v[u] = solve_row_value<T, false>(S, uval, dinv, x, z, sl, ln, r);
+      v[u] = solve_row_value<T, false, false>(S, uval, dinv, x, z, sl, ln, r);
+    } else if (mode == 4) {
+      v[u] = solve_row_value<T, false, true>(S, uval, dinv, x, z, sl, ln, r);
+    } else if (mode == 3) {
+      v[u] = solve_row_value<T, true, true>(S, lval, dinv, x, z, sl, ln, r) * dinv[r];
     } else {
-      v[u] = solve_row_value<T, true>(S, lval, dinv, x, z, sl, ln, r);
+      v[u] = solve_row_value<T, true, false>(S, lval, dinv, x, z, sl, ln, r);
       if (mode == 2) v[u] = v[u] * dinv[r];
     }
   }
