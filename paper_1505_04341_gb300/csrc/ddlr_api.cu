@@ -133,6 +133,7 @@ struct ddlr_ctx {
   int2 *l_span = nullptr, *u_span = nullptr;
   int *blk_row0 = nullptr;
   int *chunks = nullptr;
+  int4 *lv_desc = nullptr;    // level-order row descriptors (shallow factors)
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -375,6 +376,36 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
   for (int L = nL - 2; L >= 0; L--) launch(L, 1);
 }
 
+// the same sweeps over the level-order descriptor list (all blocks)
+template <typename T>
+void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv, const T *uv, const T *di,
+                 const T *x, T *z, const int *gate) {
+  const std::vector<int> &ptr = c->P.lv_ptr;
+  const int nL = int(ptr.size()) - 1;
+  const int rows = c->chunk_rows ? c->chunk_rows : (sizeof(T) == 8 ? 2 : 4);
+  auto launch = [&](int L, int mode) {
+    const int cnt = ptr[L + 1] - ptr[L];
+    if (cnt <= 0) return;
+    const int4 *d = c->lv_desc + ptr[L];
+    const int grid = (cnt + kThreads - 1) / kThreads;
+    const int *lc = c->S.l_col, *uc = c->S.u_col;
+    if (rows == 4)
+      KL(c, fam, st, (k_sptrsv_desc<T, 4>), grid, kThreads / 4, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+    else if (rows == 2)
+      KL(c, fam, st, (k_sptrsv_desc<T, 2>), grid, kThreads / 2, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+    else
+      KL(c, fam, st, (k_sptrsv_desc<T, 1>), grid, kThreads, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+  };
+  if (nL == 2) {
+    launch(1, 3);
+    launch(0, 4);
+    return;
+  }
+  for (int L = 0; L + 1 < nL; L++) launch(L, 0);
+  if (nL > 0) launch(nL - 1, 2);
+  for (int L = nL - 2; L >= 0; L--) launch(L, 1);
+}
+
 // z = A0^-1 x in device order (Sec. 4.2: the p local solves with B_{i,a} and
 // the solve with C_a).  Shallow factors (multicolour orders): every level of
 // all blocks in one launch.  Deep factors: all interior blocks in one launch
@@ -384,7 +415,8 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   const Plan &P = c->P;
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
   if (std::max(P.levels_interior, P.levels_c) <= kShallowLevels) {
-    chunk_sweeps<T>(c, c->stream, P.ch_all_ptr, "sptrsv_levels", lv, uv, di, x, z, gate);
+    if (c->lv_desc) desc_sweeps<T>(c, c->stream, "sptrsv_levels", lv, uv, di, x, z, gate);
+    else chunk_sweeps<T>(c, c->stream, P.ch_all_ptr, "sptrsv_levels", lv, uv, di, x, z, gate);
     return;
   }
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
@@ -859,6 +891,7 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   const bool force = env && env[0] == '1';
   const int nL = int(P.ch_all_ptr.size()) - 1;
   if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
+  if (P.lv_desc.empty() || int(P.lv_ptr.size()) != nL + 1) return;
   const int k = c->opt.rank_k;
   int dev = 0, sms = 0, coop = 0, optin = 0;
   ck(cudaGetDevice(&dev), "cudaGetDevice");
@@ -906,9 +939,10 @@ PzOp<T, TU> make_pzop(ddlr_ctx *c) {
   O.nL = int(P.ch_all_ptr.size()) - 1;
   O.pstride = c->pz_pstride;
   O.a = c->opt.alpha; O.ia = 1.0 / c->opt.alpha;
-  for (int i = 0; i <= O.nL; i++) O.lvl_ptr[i] = P.ch_all_ptr[i];
-  O.S = c->S;
-  O.chunks = reinterpret_cast<const int4 *>(c->chunks);
+  for (int i = 0; i <= O.nL; i++) O.lvl_ptr[i] = P.lv_ptr[i];
+  O.desc = c->lv_desc;
+  O.l_col = c->S.l_col;
+  O.u_col = c->S.u_col;
   O.lval = Prec<T>::l(c); O.uval = Prec<T>::u(c); O.dinv = Prec<T>::dinv(c);
   O.eh_rp = c->eh_rp; O.eh_ci = c->eh_ci; O.eh = Prec<T>::eh(c);
   O.eht_rp = c->eht_rp; O.eht_ci = c->eht_ci; O.eht = Prec<T>::eht(c);
@@ -991,6 +1025,7 @@ void allocate(ddlr_ctx *c) {
   c->u_span = reinterpret_cast<int2 *>(c->upload(P.u_span));
   c->blk_row0 = c->upload(P.blk_row0);
   c->chunks = c->upload(P.chunks);
+  if (!P.lv_desc.empty()) c->lv_desc = reinterpret_cast<int4 *>(c->upload(P.lv_desc));
   {
     // interior-solve kernel for deep factors: TMA-pipelined level schedule
     // (default), synchronisation-free, or plain level schedule
@@ -1280,7 +1315,16 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
   const std::vector<int> &ptr = P.ch_all_ptr;
   const int nL = int(ptr.size()) - 1;
+  const std::vector<int> &dptr = P.lv_ptr;
   auto launch = [&](int L, int mode) {
+    if (c->lv_desc) {
+      const int cnt = dptr[L + 1] - dptr[L];
+      if (cnt > 0)
+        KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr<T>, (cnt + kThreads - 1) / kThreads,
+           chunk_block(c, R), 0, c->lv_desc + dptr[L], cnt, mode, c->S.l_col, c->S.u_col, lv, uv, di, X, Z, R,
+           gate);
+      return;
+    }
     const int nch = ptr[L + 1] - ptr[L];
     if (nch > 0)
       KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,

@@ -58,6 +58,38 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
   }
 }
 
+// k_sptrsv_chunks_mr from the level-order descriptor list: CTA q solves rows
+// [q kThreads, (q+1) kThreads) of the level's list (count rows)
+template <typename T>
+__global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
+                                 const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
+                                 const int *gate) {
+  if (gate && *gate) return;
+  const int per = blockDim.x / R;
+  const int q = threadIdx.x % R, sub = threadIdx.x / R;
+  if (sub >= per) return;
+  const bool bwd = mode == 1 || mode == 4;
+  const bool from_x = mode == 3 || mode == 4;
+  const int *col = bwd ? u_col : l_col;
+  const T *val = bwd ? uval : lval;
+  const int i0 = blockIdx.x * kThreads, i1 = min(count, i0 + kThreads);
+  for (int i = i0 + sub; i < i1; i += per) {
+    const int4 dsc = desc[i];
+    const int r = dsc.x, off = bwd ? dsc.z : dsc.y;
+    const int w = bwd ? int(unsigned(dsc.w) >> 16) : int(unsigned(dsc.w) & 0xffffu);
+    const T d = dinv[r];
+    T acc = mode == 4 ? X[(long long)r * R + q] * d : (bwd ? Z : X)[(long long)r * R + q];
+    for (int kk = 0; kk < w; kk++) {
+      const int c = col[off + kk * 32];
+      const T zc = (from_x && !bwd) ? X[(long long)c * R + q] * dinv[c] : Z[(long long)c * R + q];
+      acc -= val[off + kk * 32] * zc;
+    }
+    acc *= d;
+    if (mode == 2 || mode == 3) acc *= d;
+    Z[(long long)r * R + q] = acc;
+  }
+}
+
 // Y = E^T Z = a^-1 Ehat^T Z_B - a Z_C   (interface rows j, columns q)
 template <typename T>
 __global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,

@@ -498,6 +498,62 @@ k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, cons
   }
 }
 
+// Row value from a level-order descriptor d = {row, first L slot, first L^T
+// slot, L entries | L^T entries << 16} (the row's own entries only, no slice
+// padding); FROM_X as in solve_row_value, dr = 1 / L_rr.
+template <typename T, bool FWD, bool FROM_X>
+__device__ __forceinline__ T desc_row_value(const int4 d, const int *col, const T *val, const T *dinv,
+                                            const T *x, const T *z, T dr) {
+  const int off = FWD ? d.y : d.z;
+  const int w = FWD ? int(unsigned(d.w) & 0xffffu) : int(unsigned(d.w) >> 16);
+  const int r = d.x;
+  T acc = FWD ? x[r] : (FROM_X ? x[r] * dr : z[r]);
+  for (int kk = 0; kk < w; kk++) {
+    const int c = col[off + kk * 32];
+    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? x[c] * dinv[c] : z[c]);
+  }
+  return acc * dr;
+}
+
+// mode 0-4 as k_sptrsv_chunks for one row given by its descriptor
+template <typename T>
+__device__ __forceinline__ T desc_row_mode(int mode, const int4 d, const int *l_col, const int *u_col,
+                                           const T *lval, const T *uval, const T *dinv, const T *x,
+                                           const T *z, T dr) {
+  if (mode == 1) return desc_row_value<T, false, false>(d, u_col, uval, dinv, x, z, dr);
+  if (mode == 4) return desc_row_value<T, false, true>(d, u_col, uval, dinv, x, z, dr);
+  if (mode == 3) return desc_row_value<T, true, true>(d, l_col, lval, dinv, x, z, dr) * dr;
+  const T v = desc_row_value<T, true, false>(d, l_col, lval, dinv, x, z, dr);
+  return mode == 2 ? v * dr : v;
+}
+
+// One dependency level of every block, rows from the level-order descriptor
+// list (count rows): three dependent loads per row (descriptor, entries,
+// gathered values) instead of five through the chunk tables.  R rows per
+// thread as k_sptrsv_chunks; the value of each row does not depend on R.
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads / R)
+k_sptrsv_desc(const int4 *desc, int count, int mode, const int *l_col, const int *u_col, const T *lval,
+              const T *uval, const T *dinv, const T *x, T *z, const int *gate) {
+  if (gate && *gate) return;
+  constexpr int NT = kThreads / R;
+  const int base = blockIdx.x * kThreads + threadIdx.x;
+  T v[R];
+  int rr[R];
+#pragma unroll
+  for (int u = 0; u < R; u++) {
+    const int idx = base + u * NT;
+    rr[u] = -1;
+    if (idx >= count) continue;
+    const int4 d = desc[idx];
+    v[u] = desc_row_mode<T>(mode, d, l_col, u_col, lval, uval, dinv, x, z, dinv[d.x]);
+    rr[u] = d.x;
+  }
+#pragma unroll
+  for (int u = 0; u < R; u++)
+    if (rr[u] >= 0) z[rr[u]] = v[u];
+}
+
 // One level of one block (used for C_a, whose levels span the whole GPU):
 // mode 0 forward, 1 backward, 2 forward then backward on the same (top) level.
 template <typename T>

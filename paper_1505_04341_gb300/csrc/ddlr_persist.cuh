@@ -10,7 +10,7 @@
 // partials in the same fixed order, so all CTAs take the same branch without
 // a broadcast.  Elementwise work runs on a contiguous row range per CTA
 // (a multiple of 32 rows, one SELL slice per warp); the level solves walk the
-// level-chunk lists of all blocks exactly as the level-by-level kernels do.
+// level-order row descriptors of all blocks as the level-by-level kernels do.
 #pragma once
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -87,9 +87,9 @@ template <typename T, typename TU>
 struct PzOp {
   int n, m, s, k, variant, nL, pstride;
   double a, ia;
-  int lvl_ptr[kPzMaxLevels + 1];       // level-chunk list offsets, levels of all blocks
-  SolveLayout S;
-  const int4 *chunks;
+  int lvl_ptr[kPzMaxLevels + 1];       // level-order descriptor offsets, levels of all blocks
+  const int4 *desc;                    // {row, first L slot, first L^T slot, counts} per row
+  const int *l_col, *u_col;            // sliced-ELL columns of L and L^T
   const T *lval, *uval, *dinv;
   const int *eh_rp, *eh_ci;
   const T *eh;
@@ -209,25 +209,21 @@ __device__ __forceinline__ void pz_utx(int k, const TU *U, const TX *x, const do
 template <int NT, typename T, typename TU, typename TX>
 __device__ __forceinline__ void pz_level(const PzOp<T, TU> &O, int L, int mode, const TX *x, const double *xsc,
                                          T *z, const double *racc, const double *zsc, double &acc, T *z2) {
-  const int c0 = O.lvl_ptr[L];
-  const unsigned nv = (unsigned)(O.lvl_ptr[L + 1] - c0) * (unsigned)kChunk;
-  for (unsigned v = blockIdx.x * NT + threadIdx.x; v < nv; v += gridDim.x * NT) {
-    const int4 ch = ro(O.chunks + c0 + (int)(v / kChunk));
-    const int i = (int)(v % kChunk);
-    if (i >= ch.z) continue;
-    const int ii = ch.y + i;
-    const int r = ro(O.S.lvl_row0 + ch.x) + ii, sl = ro(O.S.lvl_slice0 + ch.x) + (ii >> 5), ln = ii & 31;
+  const int c0 = O.lvl_ptr[L], cnt = O.lvl_ptr[L + 1] - c0;
+  for (int v = blockIdx.x * NT + threadIdx.x; v < cnt; v += gridDim.x * NT) {
+    const int4 d = ro(O.desc + c0 + v);
+    const int r = d.x;
     T zr;
     const T dr = ro(O.dinv + r);
     if (mode == 1) {
-      const int off = ro(O.S.u_soff + sl) + ln, w = ro(O.S.u_sw + sl);
+      const int off = d.z, w = int(unsigned(d.w) >> 16);
       T t = z[r];
-      for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.S.u_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.u_col + off + kk * 32)];
       zr = t * dr;
     } else {
-      const int off = ro(O.S.l_soff + sl) + ln, w = ro(O.S.l_sw + sl);
+      const int off = d.y, w = int(unsigned(d.w) & 0xffffu);
       T t = pz_in<T>(x, xsc, r);
-      for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.S.l_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.l_col + off + kk * 32)];
       zr = t * dr;
       if (mode == 2) zr = zr * dr;
     }

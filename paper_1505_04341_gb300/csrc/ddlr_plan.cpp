@@ -638,6 +638,28 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       P.u_span[2 * g + 1] = upper_size(g);
     }
   });
+  {
+    const int maxL2 = int(P.fl_ptr.size()) - 1;
+    bool fits = true;
+    for (int g = 0; g < n && fits; g++) fits = P.l_span[2 * g + 1] < 65536 && P.u_span[2 * g + 1] < 65536;
+    if (fits) {
+      P.lv_ptr.assign(maxL2 + 1, 0);
+      P.lv_desc.reserve(4 * size_t(n));
+      for (int L = 0; L < maxL2; L++) {
+        for (int b = 0; b <= p; b++) {
+          const int rec = P.blk_lvl0[b] + L;
+          if (rec >= P.blk_lvl0[b + 1]) continue;
+          for (int r = P.lvl_row0[rec]; r < P.lvl_row0[rec] + P.lvl_nrows[rec]; r++) {
+            P.lv_desc.push_back(r);
+            P.lv_desc.push_back(P.l_span[2 * r]);
+            P.lv_desc.push_back(P.u_span[2 * r]);
+            P.lv_desc.push_back(P.l_span[2 * r + 1] | (P.u_span[2 * r + 1] << 16));
+          }
+        }
+        P.lv_ptr[L + 1] = int(P.lv_desc.size() / 4);
+      }
+    }
+  }
   for (int b = 0; b < p; b++) {
     const int l0 = P.blk_lvl0[b], l1 = P.blk_lvl0[b + 1];
     if (l1 == l0) continue;

@@ -62,6 +62,11 @@ struct Plan {
   // = [ch_c_ptr[L], ch_c_ptr[L+1])
   std::vector<int> chunks;                // 4 ints per chunk
   std::vector<int> ch_all_ptr, ch_c_ptr;
+  // level-order row descriptors: level L of every block (blocks in order) =
+  // entries [lv_ptr[L], lv_ptr[L+1]), each {row, first slot of its L row,
+  // first slot of its L^T row, L entries | L^T entries << 16}; empty when a
+  // row has 65,536 entries or more (the chunk tables then serve alone)
+  std::vector<int> lv_ptr, lv_desc;
   // statistics
   int levels_interior = 0, levels_c = 0, ncolors = 0;
   long long nnz_ehat = 0, nnz_factor = 0;
