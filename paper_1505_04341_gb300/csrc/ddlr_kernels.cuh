@@ -1361,6 +1361,9 @@ __global__ void k_tridiag_vectors(int m, const double *al, const double *be,
       }
     }
     if (d[m - 1] == 0.0) d[m - 1] = 1e-15 * tnorm;
+    // reciprocal pivots, once: the three solves below multiply (an FP64
+    // division costs about ten times a multiply on this part)
+    for (int i = 0; i < m; i++) d[i] = 1.0 / d[i];
     double *b = Y + size_t(v) * m;
     for (int r = 0; r < m; r++) {
       // start vector: 1 + small deterministic perturbation per (v, r)
@@ -1374,10 +1377,10 @@ __global__ void k_tridiag_vectors(int m, const double *al, const double *be,
         if (flags[i] != 0.0) { const double t = b[i]; b[i] = b[i + 1]; b[i + 1] = t; }
         b[i + 1] -= dl[i] * b[i];
       }
-      // back substitution with U (diag d, super du, second super du2)
-      b[m - 1] = b[m - 1] / d[m - 1];
-      if (m > 1) b[m - 2] = (b[m - 2] - du[m - 2] * b[m - 1]) / d[m - 2];
-      for (int i = m - 3; i >= 0; i--) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / d[i];
+      // back substitution with U (reciprocal diagonal d, super du, second super du2)
+      b[m - 1] = b[m - 1] * d[m - 1];
+      if (m > 1) b[m - 2] = (b[m - 2] - du[m - 2] * b[m - 1]) * d[m - 2];
+      for (int i = m - 3; i >= 0; i--) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) * d[i];
       double nn = 0;
       for (int r = 0; r < m; r++) nn = fma(b[r], b[r], nn);
       const double inv = 1.0 / sqrt(nn);

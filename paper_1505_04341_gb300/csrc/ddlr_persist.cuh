@@ -571,22 +571,33 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
   pz_range(s, j0, j1);
   double bprev = j > 0 ? L.be[j - 1] : 0.0;
   double *v = L.v, *z = L.z;
-  while (!stop) {
-    // v = E q_j (eq. EF)
+  // v = E q (eq. EF) on this CTA's rows, q = src, or src * rdiv when rdiv != 0
+  // (the product that forms the stored q, so E acts on exactly that vector)
+  auto evec = [&](const double *src, double rdiv) {
     for (int i = i0 + threadIdx.x; i < i1; i += NT) {
       double t;
       if (i < m) {
         t = 0;
         const int q1 = ro(O.eh_rp + i + 1);
-        for (int q = ro(O.eh_rp + i); q < q1; q++) t += ro(O.eh + q) * L.qcur[ro(O.eh_ci + q)];
+        for (int q = ro(O.eh_rp + i); q < q1; q++) {
+          const int c = ro(O.eh_ci + q);
+          t += ro(O.eh + q) * (rdiv != 0.0 ? src[c] * rdiv : src[c]);
+        }
         t *= O.ia;
       } else {
-        t = -O.a * L.qcur[i - m];
+        t = -O.a * (rdiv != 0.0 ? src[i - m] * rdiv : src[i - m]);
       }
       v[i] = t;
       pz_l0(O, i, t, z);
     }
-    if (!pz_sync(O.gs, ep)) return;
+  };
+  bool have_v = false;   // E q_j already formed in the previous step's last phase
+  while (!stop) {
+    if (!have_v) {
+      evec(L.qcur, 0.0);
+      if (!pz_sync(O.gs, ep)) return;
+    }
+    have_v = false;
     double dummy = 0;
     const bool f0 = O.fuse0 != 0;
     // DDLR-2: the first solve's last level also does the second's first
@@ -631,10 +642,13 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
     }
     scale = fmax(scale, fabs(alpha));
     const bool brk = beta <= 1e-12 * (scale > 0 ? scale : 1.0);
+    // q_{j+1} = w * (1 / beta): one division, then products (an FP64
+    // division is about ten FP64 issue slots on this part)
+    double rdiv = 1.0 / beta;
     if (!brk) {
       scale = fmax(scale, beta);
       for (int r = j0 + threadIdx.x; r < j1; r += NT) {
-        const double q1 = L.w[r] / beta;
+        const double q1 = L.w[r] * rdiv;
         L.Q[(long long)(j + 1) * L.ld + r] = q1;
         L.qprev[r] = L.qcur[r];
         L.qcur[r] = q1;
@@ -650,8 +664,9 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
       double nn = 0;
       if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, nn)) return;
       const double nrm = sqrt(nn);
+      rdiv = 1.0 / nrm;
       for (int r = j0 + threadIdx.x; r < j1; r += NT) {
-        const double q1 = L.w[r] / nrm;
+        const double q1 = L.w[r] * rdiv;
         L.Q[(long long)(j + 1) * L.ld + r] = q1;
         L.qprev[r] = L.qcur[r];
         L.qcur[r] = q1;
@@ -661,6 +676,10 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
     }
     j += 1;
     if (j >= mmax) stop = true;
+    if (!stop) {        // the next step's E q_{j+1}, in the same phase
+      evec(L.w, rdiv);
+      have_v = true;
+    }
     if (!pz_sync(O.gs, ep)) return;
     if (!stop && L.check > 0 && j % L.check == 0 && j >= k + 1 && j < mmax) {
       // eq. converge: k largest eigenvalues of T_j and T_{j-1}; CTA e
