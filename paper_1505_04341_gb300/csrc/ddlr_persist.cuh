@@ -392,22 +392,23 @@ __global__ void __launch_bounds__(NT, 1) k_pcg_persist(PzOp<T, TU> O, PzPcg<T> P
   double *pold = P.p0, *pnew = P.p1;
   bool restart = false;
   while (!done) {
-    // p = z + beta p_old (into the other buffer), q = A p, p.q
-    acc = 0;
+    // p = z + beta p_old (into the other buffer), then q = A p, p.q: two
+    // phases, since forming p inside the product would double its FP64
+    // instructions, the scarce resource of this part
     for (int i = i0 + threadIdx.x; i < i1; i += NT) {
       const double zi = pz_zval(O, P.u, i);
-      const double pi = fma(beta, pold[i], zi);
-      pnew[i] = pi;
+      pnew[i] = fma(beta, pold[i], zi);
       if (kFlex) P.zo[i] = zi;
+    }
+    if (!pz_sync(O.gs, ep)) return;
+    acc = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += NT) {
       const int g = i >> 5, l = i & 31;
       const int off = ro(O.a_soff + g) + l, wd = ro(O.a_sw + g);
       double qi = 0;
-      for (int kk = 0; kk < wd; kk++) {
-        const int cc = ro(O.a_col + off + kk * 32);
-        qi += ro(O.a_val + off + kk * 32) * fma(beta, pold[cc], pz_zval(O, P.u, cc));
-      }
+      for (int kk = 0; kk < wd; kk++) qi += ro(O.a_val + off + kk * 32) * pnew[ro(O.a_col + off + kk * 32)];
       P.q[i] = qi;
-      acc += pi * qi;
+      acc += pnew[i] * qi;
     }
     pt = pz_buf(O, slot++);
     pz_put<NT>(acc, pt, O.pstride, red);
@@ -496,17 +497,41 @@ struct PzLz {
 };
 
 // partials of Q_{ncol}^T w over this CTA's rows [r0, r1), warp per column
+// (red: NT/32 doubles of shared memory).  With fewer columns than warps the
+// rows are split into nseg segments per column so every warp works; the
+// segment sums are added in a fixed order.
 template <int NT>
 __device__ __forceinline__ void pz_gemvT(const double *Q, long long ld, int ncol, const double *w, int r0,
-                                         int r1, double *pt, int pstride) {
+                                         int r1, double *pt, int pstride, double *red) {
+  constexpr int NW = NT / 32;
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int j = wi; j < ncol; j += NT / 32) {
+  if (ncol >= NW) {
+    for (int j = wi; j < ncol; j += NW) {
+      const double *q = Q + (long long)j * ld;
+      double acc = 0;
+      for (int r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (l == 0) pt[(size_t)blockIdx.x * pstride + j] = acc;
+    }
+    return;
+  }
+  const int nseg = NW / ncol, len = (r1 - r0 + nseg - 1) / nseg;
+  if (wi < ncol * nseg) {
+    const int j = wi / nseg, sg = wi % nseg;
+    const int a = r0 + sg * len, b = min(r1, a + len);
     const double *q = Q + (long long)j * ld;
     double acc = 0;
-    for (int r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+    for (int r = a + l; r < b; r += 32) acc += q[r] * w[r];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (l == 0) pt[(size_t)blockIdx.x * pstride + j] = acc;
+    if (l == 0) red[wi] = acc;
   }
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double sum = 0;
+    for (int sg = 0; sg < nseg; sg++) sum += red[threadIdx.x * nseg + sg];
+    pt[(size_t)blockIdx.x * pstride + threadIdx.x] = sum;
+  }
+  __syncthreads();
 }
 
 // w_r -= sum_j Q[j][r] c_j on this CTA's rows; returns this thread's sum of w_r^2
@@ -530,13 +555,13 @@ template <int NT>
 __device__ __forceinline__ bool pz_cgs2(const PzOp<double, double> &O, const PzLz &L, int ncol, int j0, int j1, unsigned &ep,
                                         int &slot, double *red, double *bc, double *cs, double &ww_out) {
   double *pt = pz_buf(O, slot++);
-  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
+  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
   pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
   __syncthreads();
   pt = pz_buf(O, slot++);
-  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride);
+  pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
   const double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
