@@ -28,13 +28,18 @@ template <> struct AccOf<__nv_bfloat16> { using type = float; };
 // deterministic block sum of one value per thread (result valid in thread 0)
 template <typename T, int NT>
 __device__ __forceinline__ T block_sum(T v, T *sm) {
+  static_assert((NT / 32 & (NT / 32 - 1)) == 0 && NT / 32 <= 32, "power-of-two warps, at most 32");
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) sm[w] = v;
   __syncthreads();
   T r = 0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < NT / 32; i++) r += sm[i];
+  if (w == 0) {
+    // the warp sums as a tree (log2 of the warp count dependent adds, not
+    // one per warp: FP64 add latency is long on this part)
+    r = l < NT / 32 ? sm[l] : T(0);
+    for (int o = NT / 64; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
   __syncthreads();
   return r;
 }
