@@ -501,7 +501,7 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
 // persistent-kernel helpers (defined with the allocation code)
 template <typename T, typename TU>
 PzOp<T, TU> make_pzop(ddlr_ctx *c);
-void pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
+bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
 size_t pz_lz_smem(int mmax);
 
 // ------------------------------------------------------------- Lanczos
@@ -651,15 +651,16 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     const char *ng = getenv("DDLR_NO_GRAPH");
     // every step and test in one persistent kernel when the factors are shallow
     const int nLz = int(P.ch_all_ptr.size()) - 1;
-    const bool persist = c->pz_lz && mmax <= c->pz_mmax &&
-                         (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
-    const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
+    bool persist = c->pz_lz && mmax <= c->pz_mmax &&
+                   (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
     if (persist) {
       PzOp<double, double> O = make_pzop<double, double>(c);
       PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps};
       void *args[] = {&O, &Lz};
-      pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax), args);
+      persist = pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax),
+                          args);
     }
+    const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
     if (use_graph) {
       ck(cudaEventRecord(c->ev_fork, user), "event");
       ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
@@ -959,7 +960,7 @@ PzOp<T, TU> make_pzop(ddlr_ctx *c) {
 
 // the whole PCG solve in one persistent launch, preconditioner in T (U_k in TU)
 template <typename T, typename TU>
-void pcg_persist(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, T *u, T *z, T *y, T *w,
+bool pcg_persist(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, T *u, T *z, T *y, T *w,
                  T *rhs) {
   PzOp<T, TU> O = make_pzop<T, TU>(c);
   PzPcg<T> Pp{};
@@ -968,15 +969,30 @@ void pcg_persist(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   Pp.u = u; Pp.z = z; Pp.y = y; Pp.w = w; Pp.rhs = rhs;
   Pp.st = c->pcg; Pp.tol = tol; Pp.maxit = maxit;
   void *args[] = {&O, &Pp};
-  pz_launch(c, "pcg_persist", (const void *)k_pcg_persist<kPzThreads, T, TU>, pz_pcg_smem(c->opt.rank_k), args);
+  return pz_launch(c, "pcg_persist", (const void *)k_pcg_persist<kPzThreads, T, TU>, pz_pcg_smem(c->opt.rank_k),
+                   args);
 }
 
-// one cooperative launch of a persistent kernel on the handle's stream
-void pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args) {
+// one cooperative launch of a persistent kernel on the handle's stream;
+// false (and the handle keeps to the per-phase kernels from then on) when the
+// launch is refused, e.g. because every CTA cannot be resident at once
+bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args) {
   ck(cudaMemsetAsync(c->pz_bar, 0, sizeof(unsigned), c->stream), "memset");
   ddlr_ctx::Scope sc(c, fam, c->stream);
-  ck(cudaLaunchCooperativeKernel(fn, dim3(c->pz_grid), dim3(kPzThreads), args, smem, c->stream),
-     "cudaLaunchCooperativeKernel");
+  // DDLR_FAKE_COOP_REFUSAL=1 stands in for a refused launch (tests of the
+  // fallback; no kernel is launched then)
+  const char *fake = getenv("DDLR_FAKE_COOP_REFUSAL");
+  const cudaError_t e = (fake && fake[0] == '1')
+                            ? cudaErrorCooperativeLaunchTooLarge
+                            : cudaLaunchCooperativeKernel(fn, dim3(c->pz_grid), dim3(kPzThreads), args, smem,
+                                                          c->stream);
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+    cudaGetLastError();   // not sticky: clear it
+    c->pz_pcg = c->pz_lz = false;
+    return false;
+  }
+  ck(e, "cudaLaunchCooperativeKernel");
+  return true;
 }
 
 // grid barriers of one PCG iteration and of one Lanczos step, upper bounds
@@ -1131,9 +1147,8 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   const int *gate = pcg_gate(c);
   const char *ng = getenv("DDLR_NO_GRAPH");
   // the whole solve in one persistent kernel when the factors are shallow
-  const bool persist = c->pz_pcg &&
-                       (long long)(maxit + 2) * pz_barriers_per_iteration(c) * c->pz_grid < (1LL << 31);
-  const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
+  bool persist = c->pz_pcg &&
+                 (long long)(maxit + 2) * pz_barriers_per_iteration(c) * c->pz_grid < (1LL << 31);
   cudaStream_t user = c->stream;
   struct Restore {
     ddlr_ctx *c; cudaStream_t s;
@@ -1141,13 +1156,17 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
   } restore{c, user};
   if (persist) {
     if (c->opt.precision == 0)
-      pcg_persist<double, double>(c, b, x, tol, maxit, c->pv[7], c->w64[0], c->w64[1], c->w64[2], c->w64[3]);
+      persist = pcg_persist<double, double>(c, b, x, tol, maxit, c->pv[7], c->w64[0], c->w64[1], c->w64[2],
+                                            c->w64[3]);
     else if (c->opt.uk_bf16)
-      pcg_persist<float, __nv_bfloat16>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1], c->w32[2],
-                                        c->w32[3]);
+      persist = pcg_persist<float, __nv_bfloat16>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1],
+                                                  c->w32[2], c->w32[3]);
     else
-      pcg_persist<float, float>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1], c->w32[2], c->w32[3]);
-  } else {
+      persist = pcg_persist<float, float>(c, b, x, tol, maxit, c->w32[4], c->w32[0], c->w32[1], c->w32[2],
+                                          c->w32[3]);
+  }
+  const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
+  if (!persist) {
     if (use_graph) {
       ck(cudaEventRecord(c->ev_fork, user), "event");
       ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");

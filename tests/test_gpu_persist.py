@@ -170,3 +170,21 @@ def test_mixed_precision_pcg(case, bf16, persist, monkeypatch):
     assert ("pcg_persist" in _families(h)) == (persist == "1")
     assert (h.info()["persistent"] & 1) == (persist == "1")
     h.close()
+
+
+def test_refused_cooperative_launch_falls_back(monkeypatch):
+    """A refused cooperative launch (faked on the host) leaves the handle on
+    the per-phase kernels: setup and PCG still meet the oracle bars."""
+    build, variant, k, sd = CASES["lap3d_32_v1"]
+    A, part, p = build()
+    monkeypatch.setenv("DDLR_FAKE_COOP_REFUSAL", "1")
+    h = _handle(monkeypatch, "1", A, part, p, variant=variant, rank_k=k, factor=0, **MC)
+    assert h.info()["persistent"] == 0
+    orc = O.Oracle(A, part, p, variant=variant, k=k, factor=0, **MC)
+    assert h.info()["lanczos_steps"] == orc.msteps
+    b = W.rhs(A[0], 0)
+    x, info = h.pcg(torch.tensor(b, device="cuda"), tol=1e-8)
+    _, its_o, _, _ = orc.pcg(b, 1e-8)
+    assert info[0]["status"] == "OK" and info[0]["relres"] <= 1e-8
+    assert abs(info[0]["its"] - its_o) <= 1
+    h.close()
