@@ -128,6 +128,17 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind,
  * forming, factorisation, Lanczos, low-rank data).  Synchronous. */
 ddlr_status ddlr_refactor(ddlr_handle h, const double *val);
 
+/* Improve the preconditioner by raising the rank k without discarding the
+ * Lanczos vectors already computed (Sec. 3.4, "Improving a given
+ * preconditioner"): the Lanczos process continues from its last step, with
+ * the step limit (lanczos_max, else 5 k_new) and the convergence test of
+ * eq. converge taken for k_new, then U_k and Lambda_k / H_k are rebuilt for
+ * k_new.  When neither run is stopped by the convergence test, the result is
+ * the one ddlr_setup with rank k_new would give.  The arrays of the old rank
+ * stay allocated until ddlr_destroy.  Synchronous.  Errors: INVALID (k_new <=
+ * rank_k, k_new > s or > 256), NAN, NOT_SPD, CUDA. */
+ddlr_status ddlr_increase_rank(ddlr_handle h, int k_new);
+
 /* y = M^-1 x (Algorithm 1 for DDLR-1, eq. Form2a for DDLR-2) for nrhs vectors.
  * With nrhs > 1 the vectors are processed in batches of up to 64 in one set of
  * launches (row-major blocks, one lane per vector); a column's result does not

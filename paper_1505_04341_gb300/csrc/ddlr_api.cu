@@ -576,7 +576,9 @@ void lanczos_step(ddlr_ctx *c, const LzBufs &L) {
 // steps (one CUDA graph each) without waiting; each test runs on the second
 // stream while later steps proceed, and sets the device stop flag when met;
 // the host reads that flag once per test, one test later.
-ddlr_status run_lanczos(ddlr_ctx *c) {
+// resume: continue the process from the device state (more steps for a
+// larger k, Sec. 3.4) instead of starting from q_1
+ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
   const Plan &P = c->P;
   const int s = P.s, n = P.n, m0 = P.m, k = c->opt.rank_k;
   int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
@@ -638,14 +640,28 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     L.nrm = W.nrm; L.rank = W.rank; L.st = W.st;
     double *ework = W.ework, *etop = W.etop, *evals = W.evals, *esum = W.esum, *eY = W.eY;
     cudaEvent_t ev_chk = W.ev_chk, ev_done = W.ev_done;
-    ck(cudaMemsetAsync(L.be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
-    ck(cudaMemsetAsync(L.qprev, 0, sizeof(double) * s, c->stream), "memset");
-    ck(cudaMemcpyAsync(L.Q, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
-    ck(cudaMemcpyAsync(L.qcur, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
     LzState &h0 = *W.h_st;
-    h0 = LzState{};
-    h0.j = 0; h0.stop = 0; h0.no_break = 1; h0.restarts = 0; h0.conv_m = 0; h0.nan_step = -1;
-    h0.mmax = mmax; h0.scale = 0.0; h0.seed = c->opt.seed;
+    int j_start = 0;
+    if (resume) {
+      // the state after the last step (j, scale, restarts, q_j, q_{j-1}, T_j)
+      // with the new step limit; a convergence met before is tested again
+      ck(cudaMemcpyAsync(&h0, L.st, sizeof(h0), cudaMemcpyDeviceToHost, c->stream), "D2H");
+      ck(cudaStreamSynchronize(c->stream), "sync");
+      if (h0.nan_step >= 0) throw Fail{DDLR_ERR_NAN, "the Lanczos process met a NaN; set up again"};
+      h0.mmax = mmax;
+      h0.stop = h0.j >= mmax ? 1 : 0;
+      h0.no_break = 1;
+      h0.conv_m = 0;
+      j_start = h0.j;
+    } else {
+      ck(cudaMemsetAsync(L.be, 0, sizeof(double) * (mmax + 1), c->stream), "memset");
+      ck(cudaMemsetAsync(L.qprev, 0, sizeof(double) * s, c->stream), "memset");
+      ck(cudaMemcpyAsync(L.Q, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
+      ck(cudaMemcpyAsync(L.qcur, W.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "copy");
+      h0 = LzState{};
+      h0.j = 0; h0.stop = 0; h0.no_break = 1; h0.restarts = 0; h0.conv_m = 0; h0.nan_step = -1;
+      h0.mmax = mmax; h0.scale = 0.0; h0.seed = c->opt.seed;
+    }
     ck(cudaMemcpyAsync(L.st, &h0, sizeof(h0), cudaMemcpyHostToDevice, c->stream), "H2D");
 
     const char *ng = getenv("DDLR_NO_GRAPH");
@@ -685,7 +701,7 @@ ddlr_status run_lanczos(ddlr_ctx *c) {
     }
     int *hstop = reinterpret_cast<int *>(c->h_pin + 8);
     bool pending = false;
-    for (int j = 0; j < (persist ? 0 : mmax); j++) {
+    for (int j = j_start; j < (persist ? 0 : mmax); j++) {
       if (use_graph) {
         ck(cudaGraphLaunch(W.exec, c->stream), "cudaGraphLaunch");
         c->launches += c->lz_nodes;
@@ -1725,6 +1741,80 @@ ddlr_status ddlr_refactor(ddlr_handle c, const double *val) {
     if (val)
       ck(cudaMemcpyAsync(c->val, val, sizeof(double) * c->P.nnz, cudaMemcpyDefault, c->stream), "copy values");
     return numeric_setup(c);
+  });
+}
+
+ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
+  if (!c) return DDLR_ERR_INVALID;
+  const Plan &P = c->P;
+  const int k_old = c->opt.rank_k;
+  if (k_new <= k_old || k_new > P.s || k_new > 256) {
+    c->err = "ddlr_increase_rank: need rank_k < k_new <= min(s, 256)";
+    return DDLR_ERR_INVALID;
+  }
+  if (!c->lw.ready) { c->err = "ddlr_increase_rank: no Lanczos state"; return DDLR_ERR_INVALID; }
+  return run_guarded(c, [&]() -> ddlr_status {
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    ck(cudaStreamSynchronize(c->stream2), "sync");
+    auto mmax_of = [&](int k) {
+      int mm = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
+      return std::max(std::min(mm, P.s), k);
+    };
+    const int m_old = mmax_of(k_old), m_new = mmax_of(k_new);
+    const int s = P.s, n = P.n, k = k_new;
+    auto &W = c->lw;
+    // graphs hold the old arrays' addresses
+    if (W.exec) { cudaGraphExecDestroy(W.exec); W.exec = nullptr; }
+    if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+    batch_free(c);
+    // Lanczos workspace for m_new steps: the basis and T_j carried over (the
+    // old arrays stay in the handle's arena until it is destroyed)
+    if (m_new > m_old) {
+      double *Q = c->alloc<double>(size_t(s) * size_t(m_new + 1));
+      double *al = c->alloc<double>(m_new + 1), *be = c->alloc<double>(m_new + 1);
+      ck(cudaMemsetAsync(be, 0, sizeof(double) * (m_new + 1), c->stream), "memset");
+      ck(cudaMemcpyAsync(Q, W.Q, sizeof(double) * size_t(s) * size_t(m_old + 1), cudaMemcpyDeviceToDevice,
+                         c->stream), "copy");
+      ck(cudaMemcpyAsync(al, W.al, sizeof(double) * (m_old + 1), cudaMemcpyDeviceToDevice, c->stream), "copy");
+      ck(cudaMemcpyAsync(be, W.be, sizeof(double) * (m_old + 1), cudaMemcpyDeviceToDevice, c->stream), "copy");
+      W.Q = Q; W.al = al; W.be = be;
+      W.cvec = c->alloc<double>(m_new + 2);
+      W.evals = c->alloc<double>(m_new);
+    }
+    W.ework = c->alloc<double>(5 * size_t(m_new) * k);
+    W.etop = c->alloc<double>(2 * k + 1);
+    W.eY = c->alloc<double>(size_t(m_new) * k);
+    if (c->opt.variant == 2) {
+      W.V = c->alloc<double>(size_t(s) * k);
+      W.EV = c->alloc<double>(size_t(n) * k);
+      W.kp = c->alloc<double>(size_t(kRedGrid) * k * k);
+      W.hw = c->alloc<double>(size_t(k) * k + k);
+    }
+    // low-rank data and reduction buffers for k_new
+    c->opt.rank_k = k;
+    c->U64 = c->alloc<double>(size_t(c->urows) * k);
+    c->coef64 = c->alloc<double>(k);
+    c->Hk64 = c->alloc<double>(size_t(k) * k);
+    ck(cudaMemsetAsync(c->coef64, 0, sizeof(double) * k, c->stream), "memset");
+    ck(cudaMemsetAsync(c->Hk64, 0, sizeof(double) * k * k, c->stream), "memset");
+    c->part64 = c->alloc<double>(size_t(kRedGrid) * std::max(k + 2, m_new + 2) + 2 * kRedGrid);
+    if (c->opt.precision == 1) {
+      if (c->opt.uk_bf16) c->Ub16 = c->alloc<__nv_bfloat16>(size_t(c->urows) * k);
+      else c->U32 = c->alloc<float>(size_t(c->urows) * k);
+      c->coef32 = c->alloc<float>(k);
+      c->Hk32 = c->alloc<float>(size_t(k) * k);
+      c->part32 = c->alloc<float>(size_t(kRedGrid) * (k + 2));
+    }
+    if (c->pz_pcg || c->pz_lz) pz_setup(c, m_new);
+    const ddlr_status st = run_lanczos(c, true);
+    if (st != DDLR_OK) {
+      c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
+                                      : "NaN/Inf in the Lanczos process";
+      return st;
+    }
+    make_low_precision(c);
+    sync(c);
+    return DDLR_OK;
   });
 }
 

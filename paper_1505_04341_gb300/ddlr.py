@@ -64,7 +64,7 @@ class ddlr_server_options(ctypes.Structure):
 
 # every entry point declared in include/ddlr.h
 EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
-           "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_get_info", "ddlr_get_ritz",
+           "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
            "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "ddlr_setup": ([I, P, P, P, P, I, ctypes.POINTER(ddlr_options), P,
                         ctypes.POINTER(P)], I),
         "ddlr_refactor": ([P, P], I),
+        "ddlr_increase_rank": ([P, I], I),
         "ddlr_apply": ([P, P, P, I, I], I),
         "ddlr_a0_solve": ([P, P, P, I, I], I),
         "ddlr_a0_solve_noalloc": ([P, P, P], I),
@@ -216,6 +217,10 @@ class DDLR:
 
     def set_stream(self, stream):
         _check(_lib, self._h, _lib.ddlr_set_stream(self._h, self._stream_ptr(stream)))
+
+    def increase_rank(self, k_new: int):
+        """Raise the rank to k_new, continuing the Lanczos process (Sec. 3.4)."""
+        _check(_lib, self._h, _lib.ddlr_increase_rank(self._h, int(k_new)))
 
     def refactor(self, val=None):
         ptr = None
