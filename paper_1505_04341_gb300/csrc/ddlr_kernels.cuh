@@ -559,25 +559,6 @@ k_sptrsv_desc(const int4 *desc, int count, int mode, const int *l_col, const int
     if (rr[u] >= 0) z[rr[u]] = v[u];
 }
 
-// One level of one block (used for C_a, whose levels span the whole GPU):
-// mode 0 forward, 1 backward, 2 forward then backward on the same (top) level.
-template <typename T>
-__global__ void k_sptrsv_level(SolveLayout S, int lvl, int mode, const T *lval,
-                               const T *uval, const T *dinv, const T *x, T *z,
-                               const int *gate) {
-  if (gate && *gate) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nr = S.lvl_nrows[lvl];
-  if (i >= nr) return;
-  const int r = S.lvl_row0[lvl] + i, sl = S.lvl_slice0[lvl] + (i >> 5), ln = i & 31;
-  if (mode == 1) {
-    solve_row<T, false>(S, uval, dinv, x, z, sl, ln, r);
-  } else {
-    solve_row<T, true>(S, lval, dinv, x, z, sl, ln, r);
-    if (mode == 2) z[r] = z[r] * dinv[r];
-  }
-}
-
 // ======================================================= E, E^T products
 // v = E w + xadd = [a^-1 Ehat w ; -a w] + xadd   (eq. EF), rows [0, n)
 template <typename T>
@@ -817,12 +798,6 @@ __global__ void k_permute_out(int n, const int *perm, const T *in, T *out) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[perm[g]] = in[g];
 }
-// with diagonal scaling: out = dsc .* (permuted in)
-__global__ void k_permute_in_scaled(int n, const int *perm, const double *dsc,
-                                    const double *in, double *out) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < n) { int i = perm[g]; out[g] = in[i] * (dsc ? dsc[i] : 1.0); }
-}
 
 // partial sums of ||b - q||^2
 template <int NT>
@@ -980,55 +955,6 @@ __global__ void k_pcg_p(long long n, const PcgState *st, const double *z,
 }
 
 // ================================================================ Lanczos
-// c[j] partials of Q^T w over a CTA's row range, warp per column
-// (Q column-major, ld rows).  partials[blk * ncol + j].
-template <int NT>
-__global__ void __launch_bounds__(NT)
-k_gemvT_partial(int s, int ncol, const double *Q, long long ld, const double *w,
-                double *partials) {
-  const int nw = NT / 32, wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const long long chunk = ((long long)s + gridDim.x - 1) / gridDim.x;
-  const long long r0 = (long long)blockIdx.x * chunk;
-  const long long r1 = min((long long)s, r0 + chunk);
-  for (int j = wi; j < ncol; j += nw) {
-    const double *q = Q + (long long)j * ld;
-    double acc = 0;
-    for (long long r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (l == 0) partials[(long long)blockIdx.x * ncol + j] = acc;
-  }
-}
-
-// w -= Q c (c of length ncol)
-__global__ void k_gemvN_sub(int s, int ncol, const double *Q, long long ld,
-                            const double *c, double *w) {
-  extern __shared__ unsigned char smraw[];
-  double *cs = reinterpret_cast<double *>(smraw);
-  for (int j = threadIdx.x; j < ncol; j += blockDim.x) cs[j] = c[j];
-  __syncthreads();
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= s) return;
-  double acc = 0;
-  for (int j = 0; j < ncol; j++) acc += Q[(long long)j * ld + r] * cs[j];
-  w[r] -= acc;
-}
-
-// w -= alpha_j q_j + beta_{j-1} q_{j-1}
-__global__ void k_lz_three_term(int s, const double *al, const double *be, int j,
-                                const double *qj, const double *qjm1, double *w) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= s) return;
-  double v = w[r] - al[j] * qj[r];
-  if (qjm1) v -= be[j - 1] * qjm1[r];
-  w[r] = v;
-}
-
-__global__ void k_scale_into(int s, const double *num, const double *den,
-                             double *out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < s) out[r] = num[r] / (*den);
-}
-
 // ------------------------------------------------ device-driven Lanczos step
 // Control state of the Lanczos recurrence kept on the device, so a step needs
 // no host round trip and can be replayed as one CUDA graph: the step index,
