@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -72,6 +72,8 @@ def _load():
         lib.or_factor_nnz.argtypes = [P]
         lib.or_factor_nnz.restype = ctypes.c_long
         lib.or_factor_coo.argtypes = [P, P, P, P]
+        lib.or_cheb_bounds.argtypes = [P, P]
+        lib.or_set_cheb_bounds.argtypes = [P, D, D]
         lib.or_sm64_pm1.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
         lib.or_sm64_pm1.restype = D
         _lib = lib
@@ -94,12 +96,15 @@ class Oracle:
     (1: theta = Ritz_{k+1}, 0: theta = 0), factor (0: IC(0), 1: exact),
     c_order (0: ascending index, 1: greedy multicolour) of C_a, b_order (the
     same choice for the interior blocks), scale_diag,
-    lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed.
+    lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed,
+    c_solver (0: C_a factored; 1: Chebyshev with block Jacobi, Sec. 4.3),
+    cheb_steps (5) and cheb_lanczos (20, steps of the spectrum estimate).
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
-                 lanczos_check=10, lanczos_eps=1e-4, seed=0):
+                 lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
+                 cheb_steps=5, cheb_lanczos=20):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -111,7 +116,8 @@ class Oracle:
                           int(variant), int(k), float(alpha), int(theta_mode),
                           int(factor), int(c_order), int(b_order), int(scale_diag),
                           int(lanczos_max), int(lanczos_check),
-                          float(lanczos_eps), int(seed), ctypes.byref(h))
+                          float(lanczos_eps), int(seed), int(c_solver),
+                          int(cheb_steps), int(cheb_lanczos), ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h
@@ -127,6 +133,17 @@ class Oracle:
         if h is not None and _lib is not None:
             _lib.or_destroy(h)
             self._h = None
+
+    @property
+    def cheb_bounds(self):
+        """(lo, hi): the spectrum interval of the Chebyshev C_a solve"""
+        b = np.empty(2)
+        _load().or_cheb_bounds(self._h, _ptr(b))
+        return float(b[0]), float(b[1])
+
+    def set_cheb_bounds(self, lo, hi):
+        """Replace the Chebyshev interval (the setup's low-rank data stay)."""
+        _load().or_set_cheb_bounds(self._h, float(lo), float(hi))
 
     def apply(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)

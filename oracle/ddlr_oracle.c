@@ -24,6 +24,11 @@
  *     G_{k,theta}^-1 = (1-theta)^-1 I + U_k [(I-L_k)^-1 - (1-theta)^-1 I] U_k^T;
  *   - Sec. 3.3 (eq. Form2a, lemma 1): DDLR-2 apply A0^-1 + U_k H_k U_k^T with
  *     U_k = A0^-1 E V_k and H_k = (I - U_k^T E V_k)^-1;
+ *   - Sec. 4.3: the solve with C_a by a factorisation (c_solver 0) or by
+ *     preconditioned Chebyshev iterations (c_solver 1) with the block Jacobi
+ *     preconditioner D_a (the diagonal blocks of C_a that couple interface
+ *     nodes of one subdomain), the spectrum of the pair (C_a, D_a) estimated
+ *     by a few Lanczos steps with residual-norm safeguards;
  *   - Sec. 5: preconditioned CG from x0 = 0.
  *
  * Readings where the paper is silent are the same as the CUDA library's and are
@@ -243,20 +248,63 @@ typedef struct {
   int ncolors;     /* colours of C_a (c_order 1) */
   double *work;    /* n scratch */
   double *work2;   /* n scratch */
+  /* Sec. 4.3, c_solver 1: bf[p] factors D_a; Ca is the whole C_a */
+  int c_solver, cheb_t, cheb_m;
+  sp Ca;           /* s x s, interface indices (new index - m) */
+  double cheb_lo, cheb_hi;
 } oracle;
 
 void or_free(oracle *o);
 
+/* z = F^-1 x for block b's factor F (x, z in the block's eq. Bmat order) */
+static void block_solve(oracle *o, int b, const double *x, double *z) {
+  blockfac *f = &o->bf[b];
+  double *t = o->work2;
+  for (int e = 0; e < f->nb; e++) t[e] = x[f->ord[e]];
+  fac_solve(f, t);
+  for (int e = 0; e < f->nb; e++) z[f->ord[e]] = t[e];
+}
+
+/* Chebyshev iteration for C_a x = y from x_0 = 0 with the preconditioner D_a
+ * (factored as block p), for the eigenvalues of D_a^-1 C_a taken in
+ * [lo, hi]: centre c = (hi+lo)/2, half-width d = (hi-lo)/2.  The error after
+ * t steps is T_t((c - L)/d) / T_t(c/d) applied to the initial error, L the
+ * operator D_a^-1 C_a.  The recurrence follows from the three-term recurrence
+ * of the Chebyshev polynomials T_j, with r_j = T_j(c/d) / T_{j+1}(c/d):
+ *   r_0 = d/c,   r_{j+1} = d / (2c - d r_j),
+ *   x_1 = x_0 + s_0,  s_0 = (1/c) D^-1 y,
+ *   s_j = r_j r_{j-1} s_{j-1} + 2/(2c - d r_{j-1}) D^-1 (y - C_a x_j),
+ *   x_{j+1} = x_j + s_j,
+ * written with d only in numerators, so d = 0 (a one-point spectrum) gives
+ * plain Richardson steps with step 1/c. */
+static void cheb_solve(oracle *o, const double *y, double *x) {
+  int s = o->s, t = o->cheb_t;
+  double c = 0.5 * (o->cheb_hi + o->cheb_lo), d = 0.5 * (o->cheb_hi - o->cheb_lo);
+  double *r = (double *)malloc(sizeof(double) * (size_t)s);
+  double *z = (double *)malloc(sizeof(double) * (size_t)s);
+  double *sd = (double *)malloc(sizeof(double) * (size_t)s);
+  double *cs = (double *)malloc(sizeof(double) * (size_t)s);
+  block_solve(o, o->p, y, z);
+  for (int i = 0; i < s; i++) { sd[i] = z[i] / c; x[i] = sd[i]; r[i] = y[i]; }
+  double rho = d / c;
+  for (int j = 1; j < t; j++) {
+    sp_mv(&o->Ca, sd, cs);                       /* r_j = r_{j-1} - C_a s_{j-1} */
+    for (int i = 0; i < s; i++) r[i] -= cs[i];
+    block_solve(o, o->p, r, z);
+    double den = 2.0 * c - d * rho;
+    double rho_n = d / den;
+    for (int i = 0; i < s; i++) sd[i] = rho_n * rho * sd[i] + (2.0 / den) * z[i];
+    for (int i = 0; i < s; i++) x[i] += sd[i];
+    rho = rho_n;
+  }
+  free(r); free(z); free(sd); free(cs);
+}
+
 /* A0 solve in new order: p local solves with B_{i,a} and one with C_a */
 static void a0_solve(oracle *o, const double *x, double *z) {
-  for (int b = 0; b <= o->p; b++) {
-    blockfac *f = &o->bf[b];
-    int off = o->boff[b];
-    double *t = o->work2;
-    for (int e = 0; e < f->nb; e++) t[e] = x[off + f->ord[e]];
-    fac_solve(f, t);
-    for (int e = 0; e < f->nb; e++) z[off + f->ord[e]] = t[e];
-  }
+  for (int b = 0; b < o->p; b++) block_solve(o, b, x + o->boff[b], z + o->boff[b]);
+  if (o->c_solver == 1) cheb_solve(o, x + o->m, z + o->m);
+  else block_solve(o, o->p, x + o->m, z + o->m);
 }
 
 /* v = E w = [a^-1 Ehat w ; -a w]  (eq. EF), w of length s, v of length n */
@@ -424,14 +472,72 @@ static int lanczos(oracle *o, int k, int mmax, int check, double eps, uint64_t s
   return m;
 }
 
+/* Spectrum estimate of D_a^-1 C_a (Sec. 4.3): Lanczos on the pair (C_a, D_a),
+ * i.e. symmetric Lanczos in the D_a inner product, for cheb_m steps (fewer at
+ * an invariant subspace), from the SplitMix64 stream seed + 2^32 taken in
+ * ascending original index of the interface nodes.  With p_j = D_a q_j:
+ *   w = C_a q_j - beta_{j-1} p_{j-1},  alpha_j = q_j^T w,  w -= alpha_j p_j,
+ *   z = D_a^-1 w,  beta_j = sqrt(w^T z),  q_{j+1} = z / beta_j,
+ *   p_{j+1} = w / beta_j.
+ * Ritz values of T_m are estimates, not bounds; each Ritz value lies within
+ * beta_m |e_m^T y| of an eigenvalue (y its unit eigenvector of T_m), so the
+ * interval is widened by that residual norm at both ends.  A lower end that
+ * the widening takes to zero or below falls back to the smallest Ritz value. */
+static int cheb_estimate(oracle *o, uint64_t seed) {
+  int s = o->s, mmax = o->cheb_m;
+  double *r = (double *)malloc(sizeof(double) * (size_t)s);
+  double *z = (double *)malloc(sizeof(double) * (size_t)s);
+  double *q = (double *)malloc(sizeof(double) * (size_t)s);
+  double *pv = (double *)malloc(sizeof(double) * (size_t)s);
+  double *pp = (double *)calloc((size_t)s, sizeof(double));
+  double *w = (double *)malloc(sizeof(double) * (size_t)s);
+  double *al = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  double *be = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  if (!r || !z || !q || !pv || !pp || !w || !al || !be) return OR_NOMEM;
+  /* start vector in ascending original index: the interface part of the new
+   * order is already ascending */
+  for (int j = 0; j < s; j++) r[j] = sm64_pm1(seed + 0x100000000ULL, (uint64_t)j);
+  block_solve(o, o->p, r, z);
+  double beta = sqrt(dot(s, r, z)), scale = 0.0;
+  int m = 0;
+  for (int j = 0; j < mmax; j++) {
+    for (int i = 0; i < s; i++) { q[i] = z[i] / beta; pv[i] = r[i] / beta; }
+    sp_mv(&o->Ca, q, w);
+    if (j > 0) for (int i = 0; i < s; i++) w[i] -= be[j - 1] * pp[i];
+    al[j] = dot(s, q, w);
+    for (int i = 0; i < s; i++) w[i] -= al[j] * pv[i];
+    block_solve(o, o->p, w, z);
+    double ww = dot(s, w, z);
+    be[j] = ww > 0.0 ? sqrt(ww) : 0.0;
+    m = j + 1;
+    if (fabs(al[j]) > scale) scale = fabs(al[j]);
+    if (be[j] <= 1e-14 * scale) break;      /* invariant subspace: T_m is exact */
+    memcpy(pp, pv, sizeof(double) * (size_t)s);
+    memcpy(r, w, sizeof(double) * (size_t)s);
+    beta = be[j];
+  }
+  double *vals = (double *)malloc(sizeof(double) * (size_t)m);
+  double *vecs = (double *)malloc(sizeof(double) * (size_t)m * m);
+  tri_eig(m, al, be, vals, vecs);
+  double bm = be[m - 1];
+  o->cheb_hi = vals[0] + bm * fabs(vecs[(size_t)(m - 1) * m + 0]);
+  o->cheb_lo = vals[m - 1] - bm * fabs(vecs[(size_t)(m - 1) * m + (m - 1)]);
+  if (!(o->cheb_lo > 0.0)) o->cheb_lo = vals[m - 1];
+  free(r); free(z); free(q); free(pv); free(pp); free(w); free(al); free(be); free(vals); free(vecs);
+  return (o->cheb_lo > 0.0 && o->cheb_hi >= o->cheb_lo) ? OR_OK : OR_NOT_SPD;
+}
+
 /* ------------------------------------------------------------ public API */
 int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              const int *part, int p, int variant, int k, double alpha,
              int theta_mode, int factor, int c_order, int b_order, int scale_diag,
              int lanczos_max, int lanczos_check, double lanczos_eps,
-             unsigned long long seed, void **out) {
+             unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
+             void **out) {
   *out = NULL;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
+    return OR_INVALID;
+  if (c_solver < 0 || c_solver > 1 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)))
     return OR_INVALID;
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
@@ -454,6 +560,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   o->n = n; o->p = p; o->variant = variant; o->k = k; o->alpha = alpha;
   o->theta_mode = theta_mode; o->factor = factor; o->c_order = c_order;
   o->scale_diag = scale_diag;
+  o->c_solver = c_solver; o->cheb_t = cheb_steps; o->cheb_m = cheb_lanczos;
   int st = OR_OK;
   long nnz = rowptr[n];
 
@@ -569,7 +676,11 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     for (int g = off; g < off + nb; g++)
       for (int q = o->Ap.rp[g]; q < o->Ap.rp[g + 1]; q++) {
         int c = o->Ap.ci[q];
-        if (c >= off && c < off + nb) { t[nt].r = g - off; t[nt].c = c - off; t[nt].v = o->Ap.va[q]; nt++; }
+        if (c < off || c >= off + nb) continue;
+        /* Chebyshev mode: block p is D_a, which keeps only the couplings
+         * between interface nodes of the same subdomain */
+        if (b == p && c_solver == 1 && part[o->perm[g]] != part[o->perm[c]]) continue;
+        t[nt].r = g - off; t[nt].c = c - off; t[nt].v = o->Ap.va[q]; nt++;
       }
     if (b < p) {
       double ia2 = 1.0 / (alpha * alpha);
@@ -640,6 +751,24 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   free(blk);
   free(iface);
   if (st != OR_OK) { or_free(o); return st; }
+
+  /* Sec. 4.3, c_solver 1: the whole C_a = C + a^2 I for the Chebyshev
+   * iteration, and the spectrum estimate of (C_a, D_a) */
+  if (c_solver == 1) {
+    long cap = s;
+    for (int g = m; g < n; g++) cap += o->Ap.rp[g + 1] - o->Ap.rp[g];
+    trip *t = (trip *)malloc(sizeof(trip) * (size_t)cap);
+    long nt = 0;
+    for (int g = m; g < n; g++) {
+      for (int q = o->Ap.rp[g]; q < o->Ap.rp[g + 1]; q++)
+        if (o->Ap.ci[q] >= m) { t[nt].r = g - m; t[nt].c = o->Ap.ci[q] - m; t[nt].v = o->Ap.va[q]; nt++; }
+      t[nt].r = g - m; t[nt].c = g - m; t[nt].v = alpha * alpha; nt++;
+    }
+    st = sp_from_trips(&o->Ca, s, t, nt);
+    free(t);
+    if (st == OR_OK) st = cheb_estimate(o, (uint64_t)seed);
+    if (st != OR_OK) { or_free(o); return st; }
+  }
 
   /* low-rank part (Sec. 4.4) */
   int mmax = lanczos_max > 0 ? lanczos_max : 5 * k;
@@ -728,7 +857,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
 void or_free(oracle *o) {
   if (!o) return;
   free(o->perm); free(o->iperm); free(o->boff); free(o->dsc);
-  sp_free(&o->A); sp_free(&o->Ap); sp_free(&o->Eh); sp_free(&o->EhT);
+  sp_free(&o->A); sp_free(&o->Ap); sp_free(&o->Eh); sp_free(&o->EhT); sp_free(&o->Ca);
   if (o->bf) {
     for (int b = 0; b <= o->p; b++) {
       free(o->bf[b].ord); free(o->bf[b].D); sp_free(&o->bf[b].L);
@@ -956,4 +1085,17 @@ void or_factor_coo(void *h, int *ri, int *cj, double *v) {
 /* SplitMix64 value in [-1, 1): exposed so the tests can pin the generator */
 double or_sm64_pm1(unsigned long long seed, unsigned long long i) {
   return sm64_pm1((uint64_t)seed, (uint64_t)i);
+}
+
+/* Chebyshev data (c_solver 1): out = {lo, hi} of the spectrum interval used */
+void or_cheb_bounds(void *h, double *out) {
+  oracle *o = (oracle *)h;
+  out[0] = o->cheb_lo; out[1] = o->cheb_hi;
+}
+
+/* replace the interval (tests: closed-form Chebyshev polynomials); the low-
+ * rank data of the setup are kept */
+void or_set_cheb_bounds(void *h, double lo, double hi) {
+  oracle *o = (oracle *)h;
+  o->cheb_lo = lo; o->cheb_hi = hi;
 }
