@@ -72,6 +72,16 @@ typedef struct {
   double lanczos_eps;      /* tolerance of eq. converge; default 1e-4 (Sec. 5)    */
   unsigned long long seed; /* SplitMix64 stream of the Lanczos start vector       */
   int max_nrhs;            /* largest nrhs used with this handle (workspace)      */
+  int c_solver;            /* solve with C_a (Sec. 4.3): 0 = factored like a local
+                              block (c_order, factor); 1 = preconditioned Chebyshev
+                              iterations with the block Jacobi preconditioner D_a
+                              (the couplings of C_a inside one subdomain, factored
+                              like a local block) on a spectrum interval estimated
+                              by Lanczos on (C_a, D_a)                             */
+  int cheb_steps;          /* c_solver 1: Chebyshev steps per solve (default 5,
+                              Sec. 5)                                               */
+  int cheb_lanczos;        /* c_solver 1: Lanczos steps of the spectrum estimate
+                              (default 20)                                          */
 } ddlr_options;
 
 typedef struct {
@@ -93,6 +103,8 @@ typedef struct {
   int batch_block_elem;    /* block size picked for the batched row kernels      */
   double plan_ms;          /* host analysis (orderings, levels, layouts) of setup */
   int persistent;          /* bit 0: PCG, bit 1: Lanczos run as one cooperative launch */
+  double cheb_lo, cheb_hi; /* c_solver 1: spectrum interval of D_a^-1 C_a in use  */
+  int cheb_lanczos_steps;  /* c_solver 1: Lanczos steps the estimate took         */
 } ddlr_info;
 
 typedef struct {
@@ -103,7 +115,7 @@ typedef struct {
 
 /* Fills *opt with the defaults named above (variant 1, k 16, alpha 1,
  * theta_mode 1, IC(0), c_order 0, b_order 0, FP64, lanczos 5k/10/1e-4, seed 0,
- * max_nrhs 1).
+ * max_nrhs 1, c_solver 0, cheb_steps 5, cheb_lanczos 20).
  * Returns DDLR_ERR_INVALID for a NULL pointer. */
 ddlr_status ddlr_options_default(ddlr_options *opt);
 
@@ -212,6 +224,14 @@ ddlr_status ddlr_get_lowrank(ddlr_handle h, double *U, double *lam,
  * lam/theta are used by DDLR-1, Hk by DDLR-2.  Synchronous. */
 ddlr_status ddlr_set_lowrank(ddlr_handle h, const double *U, const double *lam,
                              double theta, const double *Hk);
+
+/* Replace the spectrum interval [lo, hi] of D_a^-1 C_a on which the Chebyshev
+ * solve with C_a runs (c_solver 1, Sec. 4.3): a caller that knows bounds of
+ * the spectrum, or injection of reference data for parity checks.  The
+ * iteration's coefficients are recomputed on the device; the low-rank data
+ * are kept (they were built with the previous interval).  Synchronous.
+ * Errors: INVALID (c_solver 0, or not 0 < lo <= hi). */
+ddlr_status ddlr_set_cheb_bounds(ddlr_handle h, double lo, double hi);
 
 /* Kernel accounting: number of library kernel launches since the last reset,
  * and per-family device time accumulated with CUDA events recorded on the

@@ -18,6 +18,7 @@
 
 #include "ddlr.h"
 #include "ddlr_batch.cuh"
+#include "ddlr_cheb.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -79,6 +80,8 @@ struct ddlr_ctx {
            *T = nullptr, *Zo = nullptr, *S = nullptr;
     double *w64[5] = {nullptr};
     float *w32[7] = {nullptr};
+    double *cb64[5] = {nullptr};   // Chebyshev C_a solve: x, s (two), r, D^-1 r
+    float *cb32[5] = {nullptr};
     double *part64 = nullptr;
     float *part32 = nullptr;
     PcgStateMR *st = nullptr;
@@ -134,6 +137,16 @@ struct ddlr_ctx {
   int *blk_row0 = nullptr;
   int *chunks = nullptr;
   int4 *lv_desc = nullptr;    // level-order row descriptors (shallow factors)
+  // Chebyshev solve with C_a (c_solver 1): C_a as CSR over the interface
+  // rows, the coefficient table (see ddlr_cheb.cuh), single-RHS workspaces
+  int *cc_rp = nullptr, *cc_ci = nullptr, *cc_src = nullptr, *cc_diag = nullptr, *cz_rank = nullptr;
+  double *cc64 = nullptr, *ctab64 = nullptr;
+  float *cc32 = nullptr, *ctab32 = nullptr;
+  double *cb64[5] = {nullptr};
+  float *cb32[5] = {nullptr};
+  double *cz_al = nullptr, *cz_be = nullptr, *cz_vals = nullptr, *cz_Y = nullptr, *cz_work = nullptr,
+         *cz_b0 = nullptr;
+  int cheb_msteps = 0;
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -406,6 +419,44 @@ void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv, con
   for (int L = nL - 2; L >= 0; L--) launch(L, 1);
 }
 
+// ------------------------------------------- Chebyshev solve with C_a
+template <typename T> struct ChebP;
+template <> struct ChebP<double> {
+  static const double *cv(ddlr_ctx *c) { return c->cc64; }
+  static const double *tab(ddlr_ctx *c) { return c->ctab64; }
+  static double *buf(ddlr_ctx *c, int R, int i) { return R == 1 ? c->cb64[i] : c->bt.cb64[i]; }
+};
+template <> struct ChebP<float> {
+  static const float *cv(ddlr_ctx *c) { return c->cc32; }
+  static const float *tab(ddlr_ctx *c) { return c->ctab32; }
+  static float *buf(ddlr_ctx *c, int R, int i) { return R == 1 ? c->cb32[i] : c->bt.cb32[i]; }
+};
+
+// z = D_a^-1 x on the interface rows (the C_a block's levels alone; R
+// right-hand sides row-major)
+template <typename T>
+void cheb_dsolve(ddlr_ctx *c, cudaStream_t st, const T *x, T *z, int R, const int *gate);
+
+// x_C -> C_a^-1 x_C by cheb_steps Chebyshev steps (ddlr_cheb.cuh).  On entry
+// the interface rows of z hold D_a^-1 x_C (the A0 sweeps formed it, since
+// block p is D_a); on return they hold the Chebyshev iterate x_t.
+template <typename T>
+void cheb_tail(ddlr_ctx *c, cudaStream_t st, const T *x, T *z, int R, const int *gate) {
+  const Plan &P = c->P;
+  const int s = P.s, m = P.m, t = c->opt.cheb_steps;
+  const unsigned grid = unsigned(((long long)s * R + kThreads - 1) / kThreads);
+  T *xacc = ChebP<T>::buf(c, R, 0), *sd[2] = {ChebP<T>::buf(c, R, 1), ChebP<T>::buf(c, R, 2)};
+  T *r = ChebP<T>::buf(c, R, 3), *zt = ChebP<T>::buf(c, R, 4);
+  const T *cv = ChebP<T>::cv(c), *tab = ChebP<T>::tab(c);
+  KL(c, "cheb", st, k_cheb_first<T>, grid, kThreads, 0, s, m, R, c->cc_rp, c->cc_ci, cv, tab, t, x, z, sd[0],
+     xacc, r, gate);
+  for (int j = 1; j < t; j++) {
+    cheb_dsolve<T>(c, st, r, zt, R, gate);
+    KL(c, "cheb", st, k_cheb_step<T>, grid, kThreads, 0, s, m, R, c->cc_rp, c->cc_ci, cv, tab, t, j, zt,
+       sd[(j - 1) & 1], sd[j & 1], xacc, r, z, gate);
+  }
+}
+
 // z = A0^-1 x in device order (Sec. 4.2: the p local solves with B_{i,a} and
 // the solve with C_a).  Shallow factors (multicolour orders): every level of
 // all blocks in one launch.  Deep factors: all interior blocks in one launch
@@ -414,9 +465,11 @@ template <typename T>
 void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   const Plan &P = c->P;
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  const bool cheb = c->opt.c_solver == 1;
   if (std::max(P.levels_interior, P.levels_c) <= kShallowLevels) {
     if (c->lv_desc) desc_sweeps<T>(c, c->stream, "sptrsv_levels", lv, uv, di, x, z, gate);
     else chunk_sweeps<T>(c, c->stream, P.ch_all_ptr, "sptrsv_levels", lv, uv, di, x, z, gate);
+    if (cheb) cheb_tail<T>(c, c->stream, x, z, 1, gate);
     return;
   }
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
@@ -437,6 +490,7 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
     }
   }
   chunk_sweeps<T>(c, c->stream2, P.ch_c_ptr, "sptrsv_c", lv, uv, di, x, z, gate);
+  if (cheb) cheb_tail<T>(c, c->stream2, x, z, 1, gate);
   ck(cudaEventRecord(c->ev_join, c->stream2), "event");
   ck(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "wait");
 }
@@ -838,6 +892,76 @@ const int *pcg_gate(ddlr_ctx *c) {
                                        offsetof(PcgState, done));
 }
 
+// Chebyshev C_a solve (Sec. 4.3): C_a's values, then the spectrum estimate of
+// D_a^-1 C_a by Lanczos on the pair (C_a, D_a) in the D_a inner product (with
+// p_j = D_a q_j: w = C_a q_j - beta_{j-1} p_{j-1}, alpha_j = q_j^T w,
+// w -= alpha_j p_j, z = D_a^-1 w, beta_j = sqrt(w^T z), q_{j+1} = z/beta_j,
+// p_{j+1} = w/beta_j), stopped early at an invariant subspace (beta_j <=
+// 1e-14 max |alpha|); then the Ritz values and vectors of T_m and the
+// widened interval with its coefficient table (ddlr_cheb.cuh).  Every step
+// runs on the device; the host reads beta_j only to decide the early stop.
+ddlr_status cheb_setup(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int s = P.s, m = P.m, t = c->opt.cheb_steps, me = c->opt.cheb_lanczos;
+  const long long ncc = (long long)P.cc_ci.size();
+  const double a = c->opt.alpha;
+  KL(c, "setup", c->stream, k_gather<double>, nblk(ncc), kThreads, 0, ncc, c->cc_src, c->vals, c->cc64);
+  KL(c, "setup", c->stream, k_cc_add_diag, nblk(s), kThreads, 0, s, c->cc_diag, a * a, c->cc64);
+  if (c->opt.precision == 1)
+    KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ncc), kThreads, 0, ncc, c->cc64, c->cc32,
+       (const int *)nullptr);
+  double *r = c->w64[0], *z = c->w64[1], *q = c->w64[2], *pv = c->w64[3], *pp = c->w64[4], *w = c->w64[5];
+  const double *lv = c->l64, *uv = c->u64, *di = c->dinv64;
+  KL(c, "setup", c->stream, k_cheb_start, nblk(s), kThreads, 0, s, m, c->cz_rank, c->opt.seed, r);
+  chunk_sweeps<double>(c, c->stream, P.ch_c_ptr, "cheb_dsolve", lv, uv, di, r, z, nullptr);
+  KL(c, "setup", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, r + m, z + m, c->part64,
+     (const int *)nullptr);
+  KL(c, "setup", c->stream, k_cheb_reduce_norm, 1, 32, 0, kRedGrid, c->part64, c->cz_b0);
+  int msteps = 0;
+  double scale = 0.0;
+  for (int j = 0; j < me; j++) {
+    const double *beta = j == 0 ? c->cz_b0 : c->cz_be + (j - 1);
+    KL(c, "setup", c->stream, k_cheb_lz_qp, nblk(s), kThreads, 0, s, m, beta, z, r, q, pv);
+    KL(c, "setup", c->stream, k_cheb_lz_w, nblk(s), kThreads, 0, s, m, c->cc_rp, c->cc_ci, c->cc64, q, pp,
+       j > 0 ? c->cz_be + (j - 1) : (const double *)nullptr, w);
+    KL(c, "setup", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, q + m, w + m,
+       c->part64, (const int *)nullptr);
+    KL(c, "setup", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, c->cz_al + j, 0,
+       (const int *)nullptr);
+    KL(c, "setup", c->stream, k_cheb_lz_sub, nblk(s), kThreads, 0, s, m, c->cz_al + j, pv, w);
+    chunk_sweeps<double>(c, c->stream, P.ch_c_ptr, "cheb_dsolve", lv, uv, di, w, z, nullptr);
+    KL(c, "setup", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, w + m, z + m,
+       c->part64, (const int *)nullptr);
+    KL(c, "setup", c->stream, k_cheb_reduce_norm, 1, 32, 0, kRedGrid, c->part64, c->cz_be + j);
+    double ab[2];
+    read_dev(c, &ab[0], c->cz_al + j, sizeof(double));
+    read_dev(c, &ab[1], c->cz_be + j, sizeof(double));
+    if (!std::isfinite(ab[0]) || !std::isfinite(ab[1])) {
+      c->err = "NaN/Inf in the spectrum estimate of the Chebyshev C_a solve";
+      return DDLR_ERR_NAN;
+    }
+    msteps = j + 1;
+    scale = std::max(scale, std::fabs(ab[0]));
+    if (ab[1] <= 1e-14 * scale) break;
+    std::swap(pp, pv);   // p_j becomes p_{j-1}
+    std::swap(r, w);     // w becomes the next r
+  }
+  c->cheb_msteps = msteps;
+  KL(c, "setup", c->stream, k_tridiag_values, msteps, kEigPoints, (2 * msteps + 2) * sizeof(double), msteps,
+     c->cz_al, c->cz_be, msteps, c->cz_vals);
+  KL(c, "setup", c->stream, k_tridiag_vectors, 1, 256, 0, msteps, c->cz_al, c->cz_be, msteps, c->cz_vals, c->cz_Y,
+     c->cz_work);
+  KL(c, "setup", c->stream, k_cheb_bounds, 1, 32, 0, msteps, c->cz_vals, c->cz_Y, c->cz_be, t, c->ctab64,
+     c->ctab32);
+  double lohi[2];
+  read_dev(c, lohi, c->ctab64, sizeof(lohi));
+  if (!(lohi[0] > 0.0) || !(lohi[1] >= lohi[0])) {
+    c->err = "the spectrum estimate of D_a^-1 C_a is not positive";
+    return DDLR_ERR_NOT_SPD;
+  }
+  return DDLR_OK;
+}
+
 // device-side numeric setup from the resident values (Sec. 4.1: local factors, low-rank data)
 ddlr_status numeric_setup(ddlr_ctx *c) {
   auto t0 = std::chrono::steady_clock::now();
@@ -875,6 +999,10 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
     c->err = "non-positive pivot in a local factorisation";
     return DDLR_ERR_BREAKDOWN;
   }
+  if (c->opt.c_solver == 1) {
+    ddlr_status cs = cheb_setup(c);
+    if (cs != DDLR_OK) return cs;
+  }
   ddlr_status st = run_lanczos(c);
   if (st != DDLR_OK) {
     c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
@@ -905,6 +1033,9 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   const Plan &P = c->P;
   const char *env = getenv("DDLR_PERSIST");
   if (env && env[0] == '0') return;
+  // the persistent kernels solve with the factored C_a only; the Chebyshev
+  // C_a solve runs in the kernel-per-phase path
+  if (c->opt.c_solver == 1) return;
   const bool force = env && env[0] == '1';
   const int nL = int(P.ch_all_ptr.size()) - 1;
   if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
@@ -1121,6 +1252,26 @@ void allocate(ddlr_ctx *c) {
     for (int i = 0; i < 8; i++) c->w32[i] = c->alloc<float>(n);
     c->part32 = c->alloc<float>(size_t(kRedGrid) * (k + 2));
   }
+  if (c->opt.c_solver == 1) {
+    const int t = c->opt.cheb_steps, me = c->opt.cheb_lanczos;
+    c->cc_rp = c->upload(P.cc_rp); c->cc_ci = c->upload(P.cc_ci);
+    c->cc_src = c->upload(P.cc_src); c->cc_diag = c->upload(P.cc_diag);
+    c->cz_rank = c->upload(P.iface_rank);
+    c->cc64 = c->alloc<double>(P.cc_ci.size());
+    c->ctab64 = c->alloc<double>(2 * t + 1);
+    c->ctab32 = c->alloc<float>(2 * t + 1);
+    for (int i = 0; i < 5; i++) c->cb64[i] = c->alloc<double>(n);
+    if (c->opt.precision == 1) {
+      c->cc32 = c->alloc<float>(P.cc_ci.size());
+      for (int i = 0; i < 5; i++) c->cb32[i] = c->alloc<float>(n);
+    }
+    c->cz_al = c->alloc<double>(me + 1);
+    c->cz_be = c->alloc<double>(me + 1);
+    c->cz_vals = c->alloc<double>(me + 1);
+    c->cz_Y = c->alloc<double>(size_t(me) * me);
+    c->cz_work = c->alloc<double>(size_t(5) * me * me);
+    c->cz_b0 = c->alloc<double>(1);
+  }
   c->pcg = c->alloc<PcgState>(1);
   for (int i = 0; i < 8; i++) c->pv[i] = c->alloc<double>(n);
   c->stg_in = c->alloc<double>(n);
@@ -1312,6 +1463,11 @@ void batch_alloc(ddlr_ctx *c, int R) {
     B.part32 = (float *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 4);
   }
   B.part64 = (double *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 8);
+  if (c->opt.c_solver == 1)
+    for (int i = 0; i < 5; i++) {
+      B.cb64[i] = (double *)al(nR * 8);
+      if (c->opt.precision == 1) B.cb32[i] = (float *)al(nR * 4);
+    }
   B.st = (PcgStateMR *)al(sizeof(PcgStateMR));
   B.R = R;
   B.chunk_per = tuned ? per_c : std::max(1, 256 / R);
@@ -1366,6 +1522,32 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
          reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, X, Z, R, gate);
   };
   if (nL == 2) {            // multicolour factors: two launches, see modes 3 and 4
+    launch(1, 3);
+    launch(0, 4);
+  } else {
+    for (int L = 0; L + 1 < nL; L++) launch(L, 0);
+    if (nL > 0) launch(nL - 1, 2);
+    for (int L = nL - 2; L >= 0; L--) launch(L, 1);
+  }
+  if (c->opt.c_solver == 1) cheb_tail<T>(c, c->stream, X, Z, R, gate);
+}
+
+template <typename T>
+void cheb_dsolve(ddlr_ctx *c, cudaStream_t st, const T *x, T *z, int R, const int *gate) {
+  const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  const std::vector<int> &ptr = c->P.ch_c_ptr;
+  if (R == 1) {
+    chunk_sweeps<T>(c, st, ptr, "cheb_dsolve", lv, uv, di, x, z, gate);
+    return;
+  }
+  const int nL = int(ptr.size()) - 1;
+  auto launch = [&](int L, int mode) {
+    const int nch = ptr[L + 1] - ptr[L];
+    if (nch > 0)
+      KL(c, "cheb_dsolve", st, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,
+         reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, x, z, R, gate);
+  };
+  if (nL == 2) {
     launch(1, 3);
     launch(0, 4);
     return;
@@ -1689,6 +1871,9 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->lanczos_eps = 1e-4;
   o->seed = 0;
   o->max_nrhs = 1;
+  o->c_solver = 0;
+  o->cheb_steps = 5;
+  o->cheb_lanczos = 20;
   return DDLR_OK;
 }
 
@@ -1703,7 +1888,9 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
   if ((o.variant != 1 && o.variant != 2) || !(o.alpha > 0) || (o.precision != 0 && o.precision != 1) ||
       (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) ||
       (o.b_order != 0 && o.b_order != 1) || o.rank_k < 1 ||
-      o.rank_k > 256) {
+      o.rank_k > 256 || (o.c_solver != 0 && o.c_solver != 1) ||
+      (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
+                           o.cheb_lanczos > 1000))) {
     g_setup_error = "invalid options";
     return DDLR_ERR_INVALID;
   }
@@ -2016,6 +2203,13 @@ ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
   info->setup_ms = c->setup_ms;
   info->plan_ms = c->plan_ms;
   info->persistent = (c->pz_pcg ? 1 : 0) | (c->pz_lz ? 2 : 0);
+  if (c->opt.c_solver == 1) {
+    double lohi[2] = {0, 0};
+    if (cudaMemcpy(lohi, c->ctab64, sizeof(lohi), cudaMemcpyDeviceToHost) != cudaSuccess) return DDLR_ERR_CUDA;
+    info->cheb_lo = lohi[0];
+    info->cheb_hi = lohi[1];
+    info->cheb_lanczos_steps = c->cheb_msteps;
+  }
   return DDLR_OK;
 }
 
@@ -2069,6 +2263,19 @@ ddlr_status ddlr_get_lowrank(ddlr_handle c, double *U, double *lam, double *thet
     if (lam) for (int i = 0; i < k; i++) lam[i] = i < int(c->ritz.size()) ? c->ritz[i] : 0.0;
     if (theta) *theta = c->theta;
     if (Hk) read_dev(c, Hk, c->Hk64, sizeof(double) * k * k);
+    return DDLR_OK;
+  });
+}
+
+ddlr_status ddlr_set_cheb_bounds(ddlr_handle c, double lo, double hi) {
+  if (!c) return DDLR_ERR_INVALID;
+  if (c->opt.c_solver != 1 || !(lo > 0.0) || !(hi >= lo) || !std::isfinite(hi)) {
+    c->err = "ddlr_set_cheb_bounds: needs c_solver 1 and 0 < lo <= hi";
+    return DDLR_ERR_INVALID;
+  }
+  return run_guarded(c, [&]() -> ddlr_status {
+    KL(c, "setup", c->stream, k_cheb_coef, 1, 32, 0, lo, hi, c->opt.cheb_steps, c->ctab64, c->ctab32);
+    sync(c);
     return DDLR_OK;
   });
 }
@@ -2162,7 +2369,16 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
   // sweep, the inverse diagonal, the right-hand side read and the result written
   const double blocks = 2.0 * (off_int * (v + 4.0) + 3.0 * m * v);
   const double cblk = 2.0 * (off_c * (v + 4.0) + 3.0 * s * v);
-  const double a0 = blocks + cblk;
+  // Chebyshev C_a solve (block p factors D_a): t - 1 more D_a solves, and the
+  // step kernels stream C_a (values, indices, row pointers) and the x, s, r
+  // vectors (ddlr_cheb.cuh)
+  double cheb_k = 0.0;
+  const int t = c->opt.cheb_steps;
+  if (c->opt.c_solver == 1) {
+    const double ccb = double(P.cc_ci.size()) * (v + 4.0) + 4.0 * s;
+    cheb_k = t == 1 ? 2.0 * s * v : (ccb + 5.0 * s * v) + (t - 2) * (ccb + 7.0 * s * v) + 4.0 * s * v;
+  }
+  const double a0 = blocks + cblk + (c->opt.c_solver == 1 ? (t - 1) * cblk + cheb_k : 0.0);
   const double et = ne * (v + 4.0) + 4.0 * s + 2.0 * s * v;
   const double urows = c->urows;
   const double utx = urows * k * ub + urows * v;
@@ -2173,14 +2389,18 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
   if (apply_bytes) *apply_bytes = apply;
   if (a0_bytes) *a0_bytes = a0;
   if (family_bytes) {
-    const double clev = std::max(1, 2 * P.levels_c - 1);
+    // launches per A0 sweep pair: two for two-level factors (modes 3 and 4),
+    // else forward, top and backward levels
+    auto sweeps = [](int L) { return L == 2 ? 2 : std::max(1, 2 * L - 1); };
+    const double clev = sweeps(P.levels_c);
     const double nnz_a = double(P.nnz);
     for (int i = 0; i < cap_f && i < int(c->fam_names.size()); i++) {
       const std::string &f = c->fam_names[i];
       double b = 0.0;
       if (f == "sptrsv_blocks") b = blocks;
-      else if (f == "sptrsv_levels") b = a0 / std::max(1, 2 * std::max(P.levels_interior, P.levels_c) - 1);
-      else if (f == "sptrsv_c") b = cblk / clev;
+      else if (f == "sptrsv_levels") b = (blocks + cblk) / sweeps(std::max(P.levels_interior, P.levels_c));
+      else if (f == "sptrsv_c" || f == "cheb_dsolve") b = cblk / clev;
+      else if (f == "cheb") b = cheb_k / t;
       else if (f == "et") b = et;
       else if (f == "utx") b = utx;
       else if (f == "w_rhs") b = wr;

@@ -235,7 +235,10 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       const size_t a0 = aci.size();
       for (int q = rp[i]; q < rp[i + 1]; q++) {
         const int j = ci[q];
-        if (j != i && blk_of[j] == b) aci.push_back(loc[j]);
+        // Chebyshev mode (Sec. 4.3): block p is the block Jacobi matrix D_a,
+        // the couplings of C_a between interface nodes of one subdomain
+        if (j != i && blk_of[j] == b && (b < p || opt.c_solver != 1 || part[j] == part[i]))
+          aci.push_back(loc[j]);
         if (b < p && iface[j]) {
           for (int q2 = rp[j]; q2 < rp[j + 1]; q2++) {
             const int r = ci[q2];
@@ -429,6 +432,38 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     build(s, m, false, 0, P.eht_rp, P.eht_ci, P.eht_src);
   }
   P.nnz_ehat = (long long)P.eh_ci.size();
+
+  // ---- C_a = C + a^2 I as CSR over the interface rows (Chebyshev mode)
+  if (opt.c_solver == 1) {
+    std::vector<int> cntr(s, 0);
+    pool.run(s, [&](long long lo, long long hi) {
+      for (int g = int(lo); g < int(hi); g++) {
+        const int i = P.perm[m + g];
+        int c = 0;
+        for (int q = rp[i]; q < rp[i + 1]; q++) c += iface[ci[q]] != 0;
+        cntr[g] = c;
+      }
+    });
+    prefix(cntr, P.cc_rp);
+    P.cc_ci.resize(P.cc_rp[s]);
+    P.cc_src.resize(P.cc_rp[s]);
+    P.cc_diag.resize(s);
+    pool.run(s, [&](long long lo, long long hi) {
+      std::vector<std::pair<int, int>> ent;
+      for (int g = int(lo); g < int(hi); g++) {
+        const int i = P.perm[m + g];
+        ent.clear();
+        for (int q = rp[i]; q < rp[i + 1]; q++)
+          if (iface[ci[q]]) ent.push_back({P.iperm[ci[q]] - m, q});
+        std::sort(ent.begin(), ent.end());
+        for (size_t t = 0; t < ent.size(); t++) {
+          P.cc_ci[P.cc_rp[g] + t] = ent[t].first;
+          P.cc_src[P.cc_rp[g] + t] = ent[t].second;
+          if (ent[t].first == g) P.cc_diag[g] = P.cc_rp[g] + int(t);
+        }
+      }
+    });
+  }
 
   // ---- factor pattern in device order with value sources: row g holds its
   // lower columns (ascending) and the diagonal last; the Ehat Ehat^T terms of

@@ -37,6 +37,10 @@ struct Plan {
   std::vector<int> eh_rp, eh_ci, eh_src;
   // Ehat^T rows (interface rows, s) -> interior row (device index < m)
   std::vector<int> eht_rp, eht_ci, eht_src;
+  // C_a over the interface rows (Chebyshev mode only): columns = device
+  // index - m, ascending; value source in the original arrays; the position
+  // of each row's diagonal (a^2 is added there)
+  std::vector<int> cc_rp, cc_ci, cc_src, cc_diag;
   // factor pattern: CSR in device order, columns ascending, diagonal last
   std::vector<int> f_rp, f_ci, f_row;
   std::vector<int> f_src;               // value source in the original arrays, -1 = fill

@@ -34,7 +34,9 @@ class ddlr_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("uk_bf16", ctypes.c_int),
                 ("scale_diag", ctypes.c_int), ("lanczos_max", ctypes.c_int),
                 ("lanczos_check", ctypes.c_int), ("lanczos_eps", ctypes.c_double),
-                ("seed", ctypes.c_ulonglong), ("max_nrhs", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("max_nrhs", ctypes.c_int),
+                ("c_solver", ctypes.c_int), ("cheb_steps", ctypes.c_int),
+                ("cheb_lanczos", ctypes.c_int)]
 
 
 class ddlr_info(ctypes.Structure):
@@ -48,7 +50,8 @@ class ddlr_info(ctypes.Structure):
                 ("fill_ratio", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("setup_ms", ctypes.c_double), ("batch_block_chunks", ctypes.c_int),
                 ("batch_block_elem", ctypes.c_int), ("plan_ms", ctypes.c_double),
-                ("persistent", ctypes.c_int)]
+                ("persistent", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("cheb_lanczos_steps", ctypes.c_int)]
 
 
 class ddlr_solve_info(ctypes.Structure):
@@ -65,7 +68,7 @@ class ddlr_server_options(ctypes.Structure):
 # every entry point declared in include/ddlr.h
 EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
            "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
-           "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank",
+           "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank", "ddlr_set_cheb_bounds",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
            "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
            "ddlr_destroy", "ddlr_server_options_default", "ddlr_server_create",
@@ -102,6 +105,7 @@ def load(path: str | None = None):
         "ddlr_get_factor_coo": ([P, ctypes.POINTER(LL), P, P, P], I),
         "ddlr_get_lowrank": ([P, P, P, P, P], I),
         "ddlr_set_lowrank": ([P, P, P, D, P], I),
+        "ddlr_set_cheb_bounds": ([P, D, D], I),
         "ddlr_set_timing": ([P, I], I),
         "ddlr_get_counters": ([P, ctypes.POINTER(LL), ctypes.c_char_p, I, P, P,
                                I, ctypes.POINTER(I)], I),
@@ -312,6 +316,11 @@ class DDLR:
         _check(_lib, self._h, _lib.ddlr_set_lowrank(
             self._h, _np_ptr(U), None if lam is None else _np_ptr(lam), float(theta),
             None if Hk is None else _np_ptr(Hk)))
+
+    def set_cheb_bounds(self, lo, hi):
+        """Spectrum interval of D_a^-1 C_a for the Chebyshev C_a solve
+        (c_solver=1, Sec. 4.3)."""
+        _check(_lib, self._h, _lib.ddlr_set_cheb_bounds(self._h, float(lo), float(hi)))
 
     def set_timing(self, on=True):
         _check(_lib, self._h, _lib.ddlr_set_timing(self._h, int(bool(on))))
