@@ -285,6 +285,43 @@ def run_ours(args):
     v2_apply_ms, v2_apply_gbs = apply_rate(h2)
     h2.close()
 
+    # the solve with C_a (Sec. 4.3): factored against 5 preconditioned
+    # Chebyshev steps with the block Jacobi D_a, on the same problem
+    def a0_rate(hh, reps=20):
+        y = torch.empty_like(b)
+        for _ in range(3):
+            hh.a0_solve(b, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hh.a0_solve(b, y)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        return t, hh.traffic()["a0_bytes"] / (t * 1e-3) / 1e9
+
+    c_solve = {}
+    for name, extra in (("factored_natural", dict(b_order=0, c_order=0)),
+                        ("chebyshev_natural", dict(b_order=0, c_order=0, c_solver=1)),
+                        ("factored_multicolour", dict()),
+                        ("chebyshev_multicolour", dict(c_solver=1))):
+        hc = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
+        step(hc, x)
+        ms_c, inf_c = timed_steps(hc, 2)
+        a_ms, a_gbs = apply_rate(hc)
+        z_ms, z_gbs = a0_rate(hc)
+        ic = hc.info()
+        c_solve[name] = {"ms_per_solve": round(statistics.mean(ms_c), 3),
+                         "iterations": [i["its"] for i in inf_c],
+                         "true_relres_max": max(i["relres"] for i in inf_c),
+                         "apply_ms": round(a_ms, 4), "a0_solve_ms": round(z_ms, 4),
+                         "a0_algorithmic_GBps": round(z_gbs, 1), "levels_c": ic["levels_c"],
+                         "persistent": ic["persistent"]}
+        if extra.get("c_solver"):
+            c_solve[name]["interval"] = [ic["cheb_lo"], ic["cheb_hi"]]
+            c_solve[name]["steps"] = OPTS.get("cheb_steps", 5)
+        hc.close()
+
     # precision line: 128^3 Laplacian, 512 boxes, k = 32 -- FP64 against mixed
     # (FP32 factors and solves, BF16 or FP32 U_k, FP64 flexible CG)
     prec = {}
@@ -462,6 +499,7 @@ def run_ours(args):
             "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
                                             "iterations": [i["its"] for i in inf_nat]},
             "e2e_parts": e2e_parts,
+            "c_alpha_solve_factored_vs_chebyshev": c_solve,
             "precision_lap3d_128_b8_k32": prec,
             "batching_jump3d_96_cut5_32rhs": batch,
             "serving_lap3d_32_to_128_512req": serving,

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -125,12 +126,18 @@ struct ddlr_ctx {
   double *fval = nullptr;     // factor values (CSR)
   double *l64 = nullptr, *u64 = nullptr, *dinv64 = nullptr, *eh64 = nullptr, *eht64 = nullptr;
   float *l32 = nullptr, *u32 = nullptr, *dinv32 = nullptr, *eh32 = nullptr, *eht32 = nullptr;
+  // two-level factors: L values pre-scaled by 1 / L_cc of their column (the
+  // second level's forward sweep reads x_c directly); DDLR_PRESCALE=0 keeps
+  // the unscaled form
+  double *lx64 = nullptr;
+  float *lx32 = nullptr;
   double *dinvs64 = nullptr;  // inverse diagonal in slice layout (TMA solve)
   float *dinvs32 = nullptr;
   int *row_slot = nullptr;
   TmaCfg tma64{}, tma32{};
   bool use_tma64 = false, use_tma32 = false;
   bool use_sf64 = false, use_sf32 = false;   // synchronisation-free interior solve
+  bool uvec = true;           // vector-load U_k products (DDLR_UVEC=0: scalar kernels)
   int chunk_rows = 0;         // rows per thread of the level-chunk solve: 0 = 2 (FP64) / 4 (FP32);
                               // DDLR_CHUNK_ROWS=1|2|4 fixes it
   int2 *l_span = nullptr, *u_span = nullptr;
@@ -329,6 +336,7 @@ bool tma_config(const Plan &P, TmaCfg &cfg) {
 template <typename T> struct Prec;
 template <> struct Prec<double> {
   static const double *l(ddlr_ctx *c) { return c->l64; }
+  static const double *lx(ddlr_ctx *c) { return c->lx64; }
   static const double *u(ddlr_ctx *c) { return c->u64; }
   static const double *dinv(ddlr_ctx *c) { return c->dinv64; }
   static const double *dinvs(ddlr_ctx *c) { return c->dinvs64; }
@@ -342,6 +350,7 @@ template <> struct Prec<double> {
 };
 template <> struct Prec<float> {
   static const float *l(ddlr_ctx *c) { return c->l32; }
+  static const float *lx(ddlr_ctx *c) { return c->lx32; }
   static const float *u(ddlr_ctx *c) { return c->u32; }
   static const float *dinv(ddlr_ctx *c) { return c->dinv32; }
   static const float *dinvs(ddlr_ctx *c) { return c->dinvs32; }
@@ -364,12 +373,14 @@ constexpr int kShallowLevels = 8;   // at most this deep: solve level by level o
 // level forward and backward in one pass, then backward down
 template <typename T>
 void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, const char *fam,
-                  const T *lv, const T *uv, const T *di, const T *x, T *z, const int *gate) {
+                  const T *lv0, const T *uv, const T *di, const T *x, T *z, const int *gate) {
   const int nL = int(ptr.size()) - 1;
+  const T *lx = Prec<T>::lx(c);
   auto launch = [&](int L, int mode) {
     const int nch = ptr[L + 1] - ptr[L];
     if (nch <= 0) return;
     const int4 *chk = reinterpret_cast<const int4 *>(c->chunks) + ptr[L];
+    const T *lv = mode == 5 ? lx : lv0;
     // measured at 128^3 (A0 solve): FP64 best with 2 rows per thread, FP32 with 4
     const int rows = c->chunk_rows ? c->chunk_rows : (sizeof(T) == 8 ? 2 : 4);
     if (rows == 4)
@@ -379,8 +390,8 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
     else
       KL(c, fam, st, (k_sptrsv_chunks<T, 1>), nch, kThreads, 0, c->S, chk, mode, lv, uv, di, x, z, gate);
   };
-  if (nL == 2) {            // multicolour factors: two launches, see modes 3 and 4
-    launch(1, 3);
+  if (nL == 2) {            // multicolour factors: two launches, see modes 3 (5) and 4
+    launch(1, lx ? 5 : 3);
     launch(0, 4);
     return;
   }
@@ -391,14 +402,16 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
 
 // the same sweeps over the level-order descriptor list (all blocks)
 template <typename T>
-void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv, const T *uv, const T *di,
+void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv0, const T *uv, const T *di,
                  const T *x, T *z, const int *gate) {
   const std::vector<int> &ptr = c->P.lv_ptr;
   const int nL = int(ptr.size()) - 1;
   const int rows = c->chunk_rows ? c->chunk_rows : (sizeof(T) == 8 ? 2 : 4);
+  const T *lx = Prec<T>::lx(c);
   auto launch = [&](int L, int mode) {
     const int cnt = ptr[L + 1] - ptr[L];
     if (cnt <= 0) return;
+    const T *lv = mode == 5 ? lx : lv0;
     const int4 *d = c->lv_desc + ptr[L];
     const int grid = (cnt + kThreads - 1) / kThreads;
     const int *lc = c->S.l_col, *uc = c->S.u_col;
@@ -410,7 +423,7 @@ void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv, con
       KL(c, fam, st, (k_sptrsv_desc<T, 1>), grid, kThreads, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
   };
   if (nL == 2) {
-    launch(1, 3);
+    launch(1, lx ? 5 : 3);
     launch(0, 4);
     return;
   }
@@ -495,6 +508,124 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   ck(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "wait");
 }
 
+// ------------------------------------------------ U_k products
+// Vector-load kernels (16-byte loads, several rows in flight per thread) when
+// a row of U_k is 1..32 loads of 16 bytes; DDLR_UVEC=0 keeps the scalar ones.
+constexpr int kUvecNT = 512, kUvecUnr = 4, kUrowsUnr = 4;
+
+template <typename TU>
+int uvec_lanes(ddlr_ctx *c, int k) {
+  constexpr int E = Unpack16<TU>::E;
+  if (!c->uvec || k % E) return 0;
+  const int L = k / E;
+  return (L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) ? L : 0;
+}
+
+// partials of t = U^T x over kRedGrid CTAs (rows of U = nrows)
+template <typename T, typename TU>
+void launch_utx(ddlr_ctx *c, long long nrows, int k, const TU *U, const T *x, T *part, const int *gate) {
+#define DDLR_UTX(Lc)                                                                                   \
+  KL(c, "utx", c->stream, (k_utx_vec<T, TU, Lc, kUvecNT, kUvecUnr>), kRedGrid, kUvecNT, 0, nrows, U, x, part, \
+     gate)
+  switch (uvec_lanes<TU>(c, k)) {
+    case 1: DDLR_UTX(1); break;
+    case 2: DDLR_UTX(2); break;
+    case 4: DDLR_UTX(4); break;
+    case 8: DDLR_UTX(8); break;
+    case 16: DDLR_UTX(16); break;
+    case 32: DDLR_UTX(32); break;
+    default:
+      KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0, int(nrows), k, U, x, part, gate);
+  }
+#undef DDLR_UTX
+}
+
+// blocks of 256 threads for the row-dot kernels: enough warps for the rows,
+// at most 16 CTAs per SM-equivalent of a 152-SM part
+inline unsigned urows_grid(long long nrows, int L) {
+  const long long rows_per_cta = (long long)(32 / L) * (kThreads / 32) * kUrowsUnr;
+  return (unsigned)std::max<long long>(1, std::min<long long>((nrows + rows_per_cta - 1) / rows_per_cta, 152 * 16));
+}
+
+// FP64 row products: shared-memory tiles, thread per row (k even, k <= 64)
+inline bool urows_smem(ddlr_ctx *c, int k) { return c->uvec && k % 2 == 0 && k <= 64; }
+inline size_t urows_smem_bytes(int k) { return size_t(64 + kRowTile * (k + 1)) * sizeof(double); }
+// thread-per-row direct kernels (k = 4, 8, 16, 32): one row per thread, at
+// most 8 CTAs of 256 per SM-equivalent of a 152-SM part, grid-stride beyond
+inline unsigned urows_direct_grid(long long nrows) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((nrows + kThreads - 1) / kThreads, 152 * 8));
+}
+inline unsigned urows_smem_grid(long long nrows) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((nrows + kRowTile - 1) / kRowTile, 152 * 8));
+}
+
+template <typename T, typename TU>
+void launch_w_rhs(ddlr_ctx *c, int s, int m, int k, const TU *U, const T *t, const T *y, const T *inv1mt, T a,
+                  const T *x, T *w, T *rhs, const int *gate) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<TU, double>::value) {
+    const unsigned gd = urows_direct_grid(s);
+    switch (c->uvec ? k : 0) {
+      case 4: KL(c, "w_rhs", c->stream, k_w_rhs_direct<2>, gd, kThreads, 0, s, m, U, t, y, inv1mt, a, x, w, rhs, gate); return;
+      case 8: KL(c, "w_rhs", c->stream, k_w_rhs_direct<4>, gd, kThreads, 0, s, m, U, t, y, inv1mt, a, x, w, rhs, gate); return;
+      case 16: KL(c, "w_rhs", c->stream, k_w_rhs_direct<8>, gd, kThreads, 0, s, m, U, t, y, inv1mt, a, x, w, rhs, gate); return;
+      case 32: KL(c, "w_rhs", c->stream, k_w_rhs_direct<16>, gd, kThreads, 0, s, m, U, t, y, inv1mt, a, x, w, rhs, gate); return;
+      default: break;
+    }
+    if (urows_smem(c, k)) {
+      KL(c, "w_rhs", c->stream, k_w_rhs_smem, urows_smem_grid(s), kRowTile, urows_smem_bytes(k), s, m, k, U, t,
+         y, inv1mt, a, x, w, rhs, gate);
+      return;
+    }
+  }
+#define DDLR_WR(Lc)                                                                                    \
+  KL(c, "w_rhs", c->stream, (k_w_rhs_vec<T, TU, Lc, kUrowsUnr>), urows_grid(s, Lc), kThreads, 0, s, m, U, t, y, \
+     inv1mt, a, x, w, rhs, gate)
+  switch (uvec_lanes<TU>(c, k)) {
+    case 1: DDLR_WR(1); break;
+    case 2: DDLR_WR(2); break;
+    case 4: DDLR_WR(4); break;
+    case 8: DDLR_WR(8); break;
+    case 16: DDLR_WR(16); break;
+    case 32: DDLR_WR(32); break;
+    default:
+      KL(c, "w_rhs", c->stream, (k_w_rhs<T, TU>), nblk(s), kThreads, k * sizeof(T), s, m, k, U, t, y, inv1mt, a,
+         x, w, rhs, gate);
+  }
+#undef DDLR_WR
+}
+
+template <typename T, typename TU>
+void launch_u_add(ddlr_ctx *c, long long n, int k, const TU *U, const T *h, T *u, const int *gate) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<TU, double>::value) {
+    const unsigned gd = urows_direct_grid(n);
+    switch (c->uvec ? k : 0) {
+      case 4: KL(c, "u_add", c->stream, k_u_add_direct<2>, gd, kThreads, 0, n, U, h, u, gate); return;
+      case 8: KL(c, "u_add", c->stream, k_u_add_direct<4>, gd, kThreads, 0, n, U, h, u, gate); return;
+      case 16: KL(c, "u_add", c->stream, k_u_add_direct<8>, gd, kThreads, 0, n, U, h, u, gate); return;
+      case 32: KL(c, "u_add", c->stream, k_u_add_direct<16>, gd, kThreads, 0, n, U, h, u, gate); return;
+      default: break;
+    }
+    if (urows_smem(c, k)) {
+      KL(c, "u_add", c->stream, k_u_add_smem, urows_smem_grid(n), kRowTile, urows_smem_bytes(k), n, k, U, h, u,
+         gate);
+      return;
+    }
+  }
+#define DDLR_UA(Lc)                                                                                    \
+  KL(c, "u_add", c->stream, (k_u_add_vec<T, TU, Lc, kUrowsUnr>), urows_grid(n, Lc), kThreads, 0, n, U, h, u, gate)
+  switch (uvec_lanes<TU>(c, k)) {
+    case 1: DDLR_UA(1); break;
+    case 2: DDLR_UA(2); break;
+    case 4: DDLR_UA(4); break;
+    case 8: DDLR_UA(8); break;
+    case 16: DDLR_UA(16); break;
+    case 32: DDLR_UA(32); break;
+    default:
+      KL(c, "u_add", c->stream, (k_u_add<T, TU>), nblk(n), kThreads, k * sizeof(T), int(n), k, U, h, u, gate);
+  }
+#undef DDLR_UA
+}
+
 // ----------------------------------------------------------- M^-1 apply
 // u = M^-1 x in device order.  DDLR-1: Algorithm 1 with prop. gkt;
 // DDLR-2: eq. Form2a.  Uses workspaces 0..3 of precision T.
@@ -510,24 +641,20 @@ void apply_dev(ddlr_ctx *c, const TU *U, const T *x, T *u, const int *gate) {
     a0_solve<T>(c, x, z, gate);                                      // A0 z = x
     KL(c, "et", c->stream, k_et<T>, nblk(s), kThreads, 0,            // y = E^T z
        s, m, c->eht_rp, c->eht_ci, Prec<T>::eht(c), ia, a, z, y, gate);
-    KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0,
-       s, k, U, y, part, gate);                                      // t = D U^T y
+    launch_utx<T, TU>(c, s, k, U, y, part, gate);                     // t = D U^T y
     KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
        kRedGrid, k, part, Prec<T>::coef(c), (const T *)nullptr, t, gate);
-    KL(c, "w_rhs", c->stream, (k_w_rhs<T, TU>), nblk(s), kThreads, k * sizeof(T),
-       s, m, k, U, t, y, Prec<T>::inv1mt(c), a, x, w, rhs, gate);    // w, x_C - a w
+    launch_w_rhs<T, TU>(c, s, m, k, U, t, y, Prec<T>::inv1mt(c), a, x, w, rhs, gate);   // w, x_C - a w
     KL(c, "e_int", c->stream, k_e_interior<T>, nblk(m), kThreads, 0,
        m, c->eh_rp, c->eh_ci, Prec<T>::eh(c), ia, w, x, rhs, gate);   // x_B + a^-1 Ehat w
     a0_solve<T>(c, rhs, u, gate);                                    // A0 u = x + v
   } else {
     T *t = Prec<T>::w(c, 4);
     a0_solve<T>(c, x, u, gate);
-    KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0,
-       n, k, U, x, part, gate);
+    launch_utx<T, TU>(c, n, k, U, x, part, gate);
     KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
        kRedGrid, k, part, (const T *)nullptr, Prec<T>::Hk(c), t, gate);
-    KL(c, "u_add", c->stream, (k_u_add<T, TU>), nblk(n), kThreads, k * sizeof(T),
-       n, k, U, t, u, gate);
+    launch_u_add<T, TU>(c, n, k, U, t, u, gate);
   }
 }
 
@@ -873,6 +1000,9 @@ void make_low_precision(ddlr_ctx *c) {
   if (c->opt.precision == 0) return;
   const long long ll = (long long)P.l_col.size(), lu = (long long)P.u_col.size();
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ll), kThreads, 0, ll, c->l64, c->l32, (const int *)nullptr);
+  if (c->lx32)
+    KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ll), kThreads, 0, ll, c->lx64, c->lx32,
+       (const int *)nullptr);
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(lu), kThreads, 0, lu, c->u64, c->u32, (const int *)nullptr);
   KL(c, "setup", c->stream, (k_cast<float, double>), nblk(P.n), kThreads, 0, (long long)P.n, c->dinv64, c->dinv32, (const int *)nullptr);
   const long long nds = (long long)P.nslice * kSlice;
@@ -992,6 +1122,11 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   ck(cudaMemsetAsync(c->u64, 0, sizeof(double) * P.u_col.size(), c->stream), "memset");
   KL(c, "setup", c->stream, k_solve_layout<double>, nblk(nf), kThreads, 0, (int)nf, c->f_row, c->f_rp,
      c->map_l, c->map_u, c->row_slot, c->fval, c->l64, c->u64, c->dinv64, c->dinvs64);
+  if (c->lx64) {
+    const long long nsl = (long long)P.l_col.size();
+    KL(c, "setup", c->stream, k_prescale_cols<double>, nblk(nsl), kThreads, 0, nsl, c->S.l_col, c->l64,
+       c->dinv64, c->lx64);
+  }
   int fl[4];
   read_dev(c, fl, c->dflag, sizeof(fl));
   if (fl[3]) { c->err = "a bounded device wait timed out"; return DDLR_ERR_TIMEOUT; }
@@ -1180,6 +1315,14 @@ void allocate(ddlr_ctx *c) {
   c->fval = c->alloc<double>(P.nnz_factor);
   c->l64 = c->alloc<double>(P.l_col.size());
   c->u64 = c->alloc<double>(P.u_col.size());
+  {
+    const char *pe = getenv("DDLR_PRESCALE");
+    const int nL = int(P.ch_all_ptr.size()) - 1, nLc = int(P.ch_c_ptr.size()) - 1;
+    if (!(pe && pe[0] == '0') && (nL == 2 || nLc == 2)) {
+      c->lx64 = c->alloc<double>(P.l_col.size());
+      if (c->opt.precision == 1) c->lx32 = c->alloc<float>(P.l_col.size());
+    }
+  }
   c->dinv64 = c->alloc<double>(n);
   c->dinvs64 = c->alloc<double>(size_t(P.nslice) * kSlice);
   ck(cudaMemsetAsync(c->dinvs64, 0, sizeof(double) * size_t(P.nslice) * kSlice, c->stream), "memset");
@@ -1195,6 +1338,8 @@ void allocate(ddlr_ctx *c) {
     // (DDLR_SOLVE=tma|sf|plain)
     const char *env = getenv("DDLR_SOLVE");
     const std::string kind = env ? env : "tma";
+    const char *uv = getenv("DDLR_UVEC");
+    c->uvec = !(uv && uv[0] == '0');
     const char *cr = getenv("DDLR_CHUNK_ROWS");
     if (cr && (cr[0] == '1' || cr[0] == '2' || cr[0] == '4')) c->chunk_rows = cr[0] - '0';
     int dev = 0, optin = 0;
@@ -1213,6 +1358,12 @@ void allocate(ddlr_ctx *c) {
       ck(cudaFuncSetAttribute(k_sptrsv_blocks_sf<float, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(sf_smem_bytes<float>(P))), "attr");
     ck(cudaFuncSetAttribute(k_tridiag_values, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10), "attr");
+    ck(cudaFuncSetAttribute(k_w_rhs_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(urows_smem_bytes(64))),
+       "attr");
+    ck(cudaFuncSetAttribute(k_w_rhs_smem, cudaFuncAttributePreferredSharedMemoryCarveout, 100), "attr");
+    ck(cudaFuncSetAttribute(k_u_add_smem, cudaFuncAttributePreferredSharedMemoryCarveout, 100), "attr");
+    ck(cudaFuncSetAttribute(k_u_add_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(urows_smem_bytes(64))),
+       "attr");
     if (c->use_tma64)
       ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(tma_smem_bytes<double>(c->tma64))), "attr");
@@ -1503,11 +1654,12 @@ inline int batch_width(const ddlr_ctx *c) {
 template <typename T>
 void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
   const Plan &P = c->P;
-  const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  const T *lv0 = Prec<T>::l(c), *lx = Prec<T>::lx(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
   const std::vector<int> &ptr = P.ch_all_ptr;
   const int nL = int(ptr.size()) - 1;
   const std::vector<int> &dptr = P.lv_ptr;
   auto launch = [&](int L, int mode) {
+    const T *lv = mode == 5 ? lx : lv0;
     if (c->lv_desc) {
       const int cnt = dptr[L + 1] - dptr[L];
       if (cnt > 0)
@@ -1521,8 +1673,8 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
       KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,
          reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, X, Z, R, gate);
   };
-  if (nL == 2) {            // multicolour factors: two launches, see modes 3 and 4
-    launch(1, 3);
+  if (nL == 2) {            // multicolour factors: two launches, see modes 3 (5) and 4
+    launch(1, lx ? 5 : 3);
     launch(0, 4);
   } else {
     for (int L = 0; L + 1 < nL; L++) launch(L, 0);
@@ -1534,21 +1686,22 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
 
 template <typename T>
 void cheb_dsolve(ddlr_ctx *c, cudaStream_t st, const T *x, T *z, int R, const int *gate) {
-  const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  const T *lv0 = Prec<T>::l(c), *lx = Prec<T>::lx(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
   const std::vector<int> &ptr = c->P.ch_c_ptr;
   if (R == 1) {
-    chunk_sweeps<T>(c, st, ptr, "cheb_dsolve", lv, uv, di, x, z, gate);
+    chunk_sweeps<T>(c, st, ptr, "cheb_dsolve", lv0, uv, di, x, z, gate);
     return;
   }
   const int nL = int(ptr.size()) - 1;
   auto launch = [&](int L, int mode) {
+    const T *lv = mode == 5 ? lx : lv0;
     const int nch = ptr[L + 1] - ptr[L];
     if (nch > 0)
       KL(c, "cheb_dsolve", st, k_sptrsv_chunks_mr<T>, nch, chunk_block(c, R), 0, c->S,
          reinterpret_cast<const int4 *>(c->chunks) + ptr[L], mode, lv, uv, di, x, z, R, gate);
   };
   if (nL == 2) {
-    launch(1, 3);
+    launch(1, lx ? 5 : 3);
     launch(0, 4);
     return;
   }

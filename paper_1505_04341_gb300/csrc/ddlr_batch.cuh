@@ -37,7 +37,8 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
   const int q = threadIdx.x % R, sub = threadIdx.x / R;
   if (sub >= per) return;
   const bool bwd = mode == 1 || mode == 4;
-  const bool from_x = mode == 3 || mode == 4;   // first forward level formed where read
+  const bool from_x = mode == 3 || mode == 4 || mode == 5;   // first forward level formed where read
+  const bool pre = mode == 5;                                 // values pre-scaled by 1 / L_cc
   const int *soff = bwd ? S.u_soff : S.l_soff;
   const int *sw = bwd ? S.u_sw : S.l_sw;
   const int *col = bwd ? S.u_col : S.l_col;
@@ -49,11 +50,12 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
     T acc = mode == 4 ? X[(long long)r * R + q] * d : (bwd ? Z : X)[(long long)r * R + q];
     for (int kk = 0; kk < w; kk++) {
       const int c = col[off + kk * 32];
-      const T zc = (from_x && !bwd) ? X[(long long)c * R + q] * dinv[c] : Z[(long long)c * R + q];
+      const T zc = (from_x && !bwd) ? (pre ? X[(long long)c * R + q] : X[(long long)c * R + q] * dinv[c])
+                                    : Z[(long long)c * R + q];
       acc -= val[off + kk * 32] * zc;
     }
     acc *= d;
-    if (mode == 2 || mode == 3) acc *= d;
+    if (mode == 2 || mode == 3 || mode == 5) acc *= d;
     Z[(long long)r * R + q] = acc;
   }
 }
@@ -69,7 +71,8 @@ __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const in
   const int q = threadIdx.x % R, sub = threadIdx.x / R;
   if (sub >= per) return;
   const bool bwd = mode == 1 || mode == 4;
-  const bool from_x = mode == 3 || mode == 4;
+  const bool from_x = mode == 3 || mode == 4 || mode == 5;
+  const bool pre = mode == 5;
   const int *col = bwd ? u_col : l_col;
   const T *val = bwd ? uval : lval;
   const int i0 = blockIdx.x * kThreads, i1 = min(count, i0 + kThreads);
@@ -81,11 +84,12 @@ __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const in
     T acc = mode == 4 ? X[(long long)r * R + q] * d : (bwd ? Z : X)[(long long)r * R + q];
     for (int kk = 0; kk < w; kk++) {
       const int c = col[off + kk * 32];
-      const T zc = (from_x && !bwd) ? X[(long long)c * R + q] * dinv[c] : Z[(long long)c * R + q];
+      const T zc = (from_x && !bwd) ? (pre ? X[(long long)c * R + q] : X[(long long)c * R + q] * dinv[c])
+                                    : Z[(long long)c * R + q];
       acc -= val[off + kk * 32] * zc;
     }
     acc *= d;
-    if (mode == 2 || mode == 3) acc *= d;
+    if (mode == 2 || mode == 3 || mode == 5) acc *= d;
     Z[(long long)r * R + q] = acc;
   }
 }

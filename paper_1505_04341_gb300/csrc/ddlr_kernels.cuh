@@ -65,6 +65,14 @@ __global__ void k_gather(long long cnt, const int *src, const double *in, T *out
 
 // initial values of the factor pattern: entries of B_{i,a} = B_i + a^-2 E_i E_i^T
 // and C_a = C + a^2 I (eq. split)
+// L values of a two-level factor scaled by the inverse diagonal of their
+// column: lx[slot] = l[slot] / L_cc (padding slots hold 0 and stay 0)
+template <typename T>
+__global__ void k_prescale_cols(long long nslot, const int *col, const T *l, const T *dinv, T *lx) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nslot) lx[i] = l[i] * dinv[col[i]];
+}
+
 __global__ void k_factor_init(int nf, const int *f_src, const int *f_prp,
                               const int *pa, const int *pb,
                               const unsigned char *cdiag, const double *as,
@@ -445,7 +453,9 @@ k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l
 // FROM_X: the first forward level was not stored; its value x_c / L_cc is
 // formed where it is read (forward: the dependencies of a second-level row,
 // all on the first level; backward on the first level: the row's own value).
-template <typename T, bool FWD, bool FROM_X>
+// PRE (forward FROM_X only): the values are L_rc / L_cc, scaled once at setup,
+// so an entry costs one FMA on x_c and no gather of 1 / L_cc.
+template <typename T, bool FWD, bool FROM_X, bool PRE = false>
 __device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val, const T *dinv, const T *x,
                                              const T *z, int slice, int lane, int r) {
   const int *soff = FWD ? S.l_soff : S.u_soff;
@@ -455,7 +465,7 @@ __device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val,
   T acc = FWD ? x[r] : (FROM_X ? x[r] * dinv[r] : z[r]);
   for (int kk = 0; kk < w; kk++) {
     const int c = col[off + kk * 32];
-    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? x[c] * dinv[c] : z[c]);
+    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? (PRE ? x[c] : x[c] * dinv[c]) : z[c]);
   }
   return acc * dinv[r];
 }
@@ -466,7 +476,8 @@ __device__ __forceinline__ T solve_row_value(const SolveLayout &S, const T *val,
 // level of every block it contains).  Two-level factors skip the first
 // forward level: mode 3 = mode 2 on the second level reading its
 // dependencies as x_c / L_cc, mode 4 = mode 1 on the first level starting
-// from x_r / L_rr (the values that level would have stored).  Each of the kThreads / R threads
+// from x_r / L_rr (the values that level would have stored); mode 5 = mode 3
+// with the second level's L values pre-scaled by 1 / L_cc of their columns.  Each of the kThreads / R threads
 // solves R rows: it computes all R values (loads only: rows of one level do
 // not depend on each other) before storing any, so R dependent load chains
 // are in flight per thread.  The value of each row does not depend on R.
@@ -491,6 +502,8 @@ k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, cons
       v[u] = solve_row_value<T, false, true>(S, uval, dinv, x, z, sl, ln, r);
     } else if (mode == 3) {
       v[u] = solve_row_value<T, true, true>(S, lval, dinv, x, z, sl, ln, r) * dinv[r];
+    } else if (mode == 5) {
+      v[u] = solve_row_value<T, true, true, true>(S, lval, dinv, x, z, sl, ln, r) * dinv[r];
     } else {
       v[u] = solve_row_value<T, true, false>(S, lval, dinv, x, z, sl, ln, r);
       if (mode == 2) v[u] = v[u] * dinv[r];
@@ -505,8 +518,8 @@ k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, cons
 
 // Row value from a level-order descriptor d = {row, first L slot, first L^T
 // slot, L entries | L^T entries << 16} (the row's own entries only, no slice
-// padding); FROM_X as in solve_row_value, dr = 1 / L_rr.
-template <typename T, bool FWD, bool FROM_X>
+// padding); FROM_X and PRE as in solve_row_value, dr = 1 / L_rr.
+template <typename T, bool FWD, bool FROM_X, bool PRE = false>
 __device__ __forceinline__ T desc_row_value(const int4 d, const int *col, const T *val, const T *dinv,
                                             const T *x, const T *z, T dr) {
   const int off = FWD ? d.y : d.z;
@@ -515,7 +528,7 @@ __device__ __forceinline__ T desc_row_value(const int4 d, const int *col, const 
   T acc = FWD ? x[r] : (FROM_X ? x[r] * dr : z[r]);
   for (int kk = 0; kk < w; kk++) {
     const int c = col[off + kk * 32];
-    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? x[c] * dinv[c] : z[c]);
+    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? (PRE ? x[c] : x[c] * dinv[c]) : z[c]);
   }
   return acc * dr;
 }
@@ -528,6 +541,7 @@ __device__ __forceinline__ T desc_row_mode(int mode, const int4 d, const int *l_
   if (mode == 1) return desc_row_value<T, false, false>(d, u_col, uval, dinv, x, z, dr);
   if (mode == 4) return desc_row_value<T, false, true>(d, u_col, uval, dinv, x, z, dr);
   if (mode == 3) return desc_row_value<T, true, true>(d, l_col, lval, dinv, x, z, dr) * dr;
+  if (mode == 5) return desc_row_value<T, true, true, true>(d, l_col, lval, dinv, x, z, dr) * dr;
   const T v = desc_row_value<T, true, false>(d, l_col, lval, dinv, x, z, dr);
   return mode == 2 ? v * dr : v;
 }
@@ -703,6 +717,249 @@ __global__ void k_u_add(int nrows, int k, const TU *U, const T *h, T *u,
   const TU *row = U + r * k;
   for (int c = 0; c < k; c++) acc += T(to_acc(row[c])) * hs[c];
   u[r] += acc;
+}
+
+// --------------------------------------------- vector-load U products
+// U row-major (rows x k) read as 16-byte vectors: E = 16 / sizeof(TU) values
+// per load, L = k / E lanes per row, so one warp load covers 32 / L whole rows
+// (512 contiguous bytes) and every thread keeps UNR loads in flight before
+// its FMAs.  Used when k * sizeof(TU) is a multiple of 16 and L divides 32
+// (k = 16 or 32 with FP64, FP32 or BF16 U_k); else the kernels above.
+template <typename TU> struct Unpack16;
+template <> struct Unpack16<double> {
+  static constexpr int E = 2;
+  template <typename T> __device__ __forceinline__ static void run(const uint4 &v, T *o) {
+    o[0] = T(__hiloint2double(int(v.y), int(v.x)));
+    o[1] = T(__hiloint2double(int(v.w), int(v.z)));
+  }
+};
+template <> struct Unpack16<float> {
+  static constexpr int E = 4;
+  template <typename T> __device__ __forceinline__ static void run(const uint4 &v, T *o) {
+    o[0] = T(__uint_as_float(v.x));
+    o[1] = T(__uint_as_float(v.y));
+    o[2] = T(__uint_as_float(v.z));
+    o[3] = T(__uint_as_float(v.w));
+  }
+};
+template <> struct Unpack16<__nv_bfloat16> {
+  static constexpr int E = 8;
+  template <typename T> __device__ __forceinline__ static void run(const uint4 &v, T *o) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      __nv_bfloat162 b;
+      memcpy(&b, &w[i], sizeof(b));
+      const float2 f = __bfloat1622float2(b);
+      o[2 * i] = T(f.x);
+      o[2 * i + 1] = T(f.y);
+    }
+  }
+};
+
+// stage 1 of t = U^T x: partials[blk][c] over this CTA's rows (fixed grid,
+// fixed order)
+template <typename T, typename TU, int L, int NT, int UNR>
+__global__ void __launch_bounds__(NT, 2)   // two CTAs per SM: the fixed grid of 2 x 152 in one wave
+k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate) {
+  if (gate && *gate) return;
+  constexpr int E = Unpack16<TU>::E, K = L * E, RW = 32 / L, NW = NT / 32;
+  __shared__ T red[NW][K];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int cg = lane % L, ro = lane / L;
+  const long long gw = (long long)blockIdx.x * NW + wi, W = (long long)gridDim.x * NW;
+  const uint4 *U4 = reinterpret_cast<const uint4 *>(U);
+  T acc[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) acc[i] = T(0);
+  for (long long r0 = gw * RW; r0 < nrows; r0 += W * RW * UNR) {
+    uint4 v[UNR];
+    T xv[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      const long long r = r0 + (long long)u * W * RW + ro;
+      v[u] = r < nrows ? U4[r * L + cg] : make_uint4(0u, 0u, 0u, 0u);
+      xv[u] = r < nrows ? x[r] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      T e[E];
+      Unpack16<TU>::run(v[u], e);
+#pragma unroll
+      for (int i = 0; i < E; i++) acc[i] += e[i] * xv[u];
+    }
+  }
+  // lanes cg, cg + L, ... hold the same columns
+#pragma unroll
+  for (int o = L; o < 32; o <<= 1)
+#pragma unroll
+    for (int i = 0; i < E; i++) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+  if (ro == 0)
+#pragma unroll
+    for (int i = 0; i < E; i++) red[wi][cg * E + i] = acc[i];
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += NT) {
+    T sum = 0;
+    for (int w = 0; w < NW; w++) sum += red[w][c];
+    partials[(long long)blockIdx.x * K + c] = sum;
+  }
+}
+
+// row dot products d_r = U[r][:] . t, L lanes per row, UNR rows in flight per
+// thread; the epilogue gets (row, d_r) in lane cg == 0 of each row group:
+// DDLR-1 (rows = s): w_j = t_0 y_j + d_j, rhs_{m+j} = x_{m+j} - a w_j;
+// DDLR-2 (rows = n): u_r += d_r.
+template <typename T, typename TU, int L, int UNR, typename Epi>
+__device__ __forceinline__ void u_rows_dot(long long nrows, const TU *U, const T *t, Epi epi) {
+  constexpr int E = Unpack16<TU>::E, RW = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int cg = lane % L, ro = lane / L;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
+  T tv[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) tv[i] = t[cg * E + i];
+  const uint4 *U4 = reinterpret_cast<const uint4 *>(U);
+  for (long long r0 = gw * RW; r0 < nrows; r0 += W * RW * UNR) {
+    uint4 v[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      const long long r = r0 + (long long)u * W * RW + ro;
+      v[u] = r < nrows ? U4[r * L + cg] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      T e[E];
+      Unpack16<TU>::run(v[u], e);
+      T d = 0;
+#pragma unroll
+      for (int i = 0; i < E; i++) d += e[i] * tv[i];
+#pragma unroll
+      for (int o = 1; o < L; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      const long long r = r0 + (long long)u * W * RW + ro;
+      if (cg == 0 && r < nrows) epi(r, d);
+    }
+  }
+}
+
+// FP64 row dot products d_r = U[r][:] . t, one thread per row: on this part an
+// FP64 warp instruction costs the same whatever the active lanes, so a
+// cross-lane reduction would multiply the FP64 instructions; instead a tile of
+// kRowTile rows is loaded with coalesced 16-byte loads into shared memory
+// (row stride k + 1) and each thread sums its row there.  k even, k <= 64.
+constexpr int kRowTile = 128;
+template <typename Epi>
+__device__ __forceinline__ void u_rows_dot_smem(long long nrows, int k, const double *U, const double *t,
+                                                double *tile, double *ts, Epi epi) {
+  for (int c = threadIdx.x; c < k; c += blockDim.x) ts[c] = t[c];
+  const int ld = k + 1;
+  const long long ntiles = (nrows + kRowTile - 1) / kRowTile;
+  for (long long tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+    const long long r0 = tl * kRowTile;
+    const int rows = (int)min((long long)kRowTile, nrows - r0);
+    const int half = rows * k / 2;   // 16-byte chunks of the tile (k even)
+    const double2 *src = reinterpret_cast<const double2 *>(U + r0 * k);
+    __syncthreads();                 // previous tile consumed (and ts written)
+    for (int q = threadIdx.x; q < half; q += blockDim.x) {
+      const double2 v = src[q];
+      const int e = 2 * q, rr = e / k, cc = e - rr * k;   // cc even, cc + 1 < k
+      tile[rr * ld + cc] = v.x;
+      tile[rr * ld + cc + 1] = v.y;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const double *row = tile + i * ld;
+      double d = 0;
+      for (int c = 0; c < k; c++) d += row[c] * ts[c];
+      epi(r0 + i, d);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRowTile)
+k_w_rhs_smem(int s, int m, int k, const double *U, const double *t, const double *y, const double *inv1mt,
+             double a, const double *x, double *w, double *rhs, const int *gate) {
+  if (gate && *gate) return;
+  extern __shared__ double dsm[];
+  const double it = *inv1mt;
+  u_rows_dot_smem(s, k, U, t, dsm + 64, dsm, [&](long long j, double d) {
+    const double wj = it * y[j] + d;
+    w[j] = wj;
+    rhs[m + j] = x[m + j] - a * wj;
+  });
+}
+
+__global__ void __launch_bounds__(kRowTile)
+k_u_add_smem(long long nrows, int k, const double *U, const double *h, double *u, const int *gate) {
+  if (gate && *gate) return;
+  extern __shared__ double dsm[];
+  u_rows_dot_smem(nrows, k, U, h, dsm + 64, dsm, [&](long long r, double d) { u[r] += d; });
+}
+
+// The same FP64 row dot products without the tile: thread per row, its row
+// read as KV = k/2 16-byte loads issued back to back, at most 8 at a time (the
+// warp's loads cover 32 whole rows, so every sector fetched is used), then k
+// FMAs in two chains; t is read from shared memory (broadcast).
+template <int KV, typename Epi>
+__device__ __forceinline__ void u_rows_dot_direct(long long nrows, const double *U, const double *t, Epi epi) {
+  constexpr int CH = KV < 8 ? KV : 8;
+  __shared__ double ts[2 * KV];
+  for (int c = threadIdx.x; c < 2 * KV; c += blockDim.x) ts[c] = t[c];
+  __syncthreads();
+  const double2 *U2 = reinterpret_cast<const double2 *>(U);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double d0 = 0, d1 = 0;
+#pragma unroll 1
+    for (int q0 = 0; q0 < KV; q0 += CH) {
+      double2 v[CH];
+#pragma unroll
+      for (int q = 0; q < CH; q++) v[q] = U2[r * KV + q0 + q];
+#pragma unroll
+      for (int q = 0; q < CH; q++) {
+        d0 += v[q].x * ts[2 * (q0 + q)];
+        d1 += v[q].y * ts[2 * (q0 + q) + 1];
+      }
+    }
+    epi(r, d0 + d1);
+  }
+}
+
+template <int KV>
+__global__ void __launch_bounds__(kThreads, 3) k_w_rhs_direct(int s, int m, const double *U, const double *t, const double *y,
+                               const double *inv1mt, double a, const double *x, double *w, double *rhs,
+                               const int *gate) {
+  if (gate && *gate) return;
+  const double it = *inv1mt;
+  u_rows_dot_direct<KV>(s, U, t, [&](long long j, double d) {
+    const double wj = it * y[j] + d;
+    w[j] = wj;
+    rhs[m + j] = x[m + j] - a * wj;
+  });
+}
+
+template <int KV>
+__global__ void __launch_bounds__(kThreads, 3) k_u_add_direct(long long nrows, const double *U, const double *h, double *u, const int *gate) {
+  if (gate && *gate) return;
+  u_rows_dot_direct<KV>(nrows, U, h, [&](long long r, double d) { u[r] += d; });
+}
+
+template <typename T, typename TU, int L, int UNR>
+__global__ void k_w_rhs_vec(int s, int m, const TU *U, const T *t, const T *y, const T *inv1mt, T a,
+                            const T *x, T *w, T *rhs, const int *gate) {
+  if (gate && *gate) return;
+  const T it = *inv1mt;
+  u_rows_dot<T, TU, L, UNR>(s, U, t, [&](long long j, T d) {
+    const T wj = it * y[j] + d;
+    w[j] = wj;
+    rhs[m + j] = x[m + j] - a * wj;
+  });
+}
+
+template <typename T, typename TU, int L, int UNR>
+__global__ void k_u_add_vec(long long nrows, const TU *U, const T *h, T *u, const int *gate) {
+  if (gate && *gate) return;
+  u_rows_dot<T, TU, L, UNR>(nrows, U, h, [&](long long r, T d) { u[r] += d; });
 }
 
 // ===================================================== vectors and PCG

@@ -6,7 +6,12 @@ printing the CUDA-event time per repetition and the algorithmic bytes.  Used
 as the command under ncu for the kernel summaries in profiles/:
 
     python -m paper_1505_04341_gb300.profile_kernels --workload lap3d_128_b8 \
-        --op a0 --reps 5 [--variant 1] [--k 16] [--precision 0]
+        --op a0 --reps 5 [--variant 1] [--k 16] [--precision 0] [--c-solver 0]
+        [--families]
+
+--families adds a second pass with per-launch CUDA events (ddlr_set_timing)
+and prints the device time, launches and algorithmic GB/s of every kernel
+family.
 """
 from __future__ import annotations
 
@@ -32,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--c-order", type=int, default=1)
     ap.add_argument("--b-order", type=int, default=1)
     ap.add_argument("--lanczos-max", type=int, default=0)
+    ap.add_argument("--c-solver", type=int, default=0)
+    ap.add_argument("--families", action="store_true")
     args = ap.parse_args(argv)
 
     import torch
@@ -45,7 +52,7 @@ def main(argv=None):
     n = A[0]
     h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=0,
              c_order=args.c_order, b_order=args.b_order, precision=args.precision,
-             uk_bf16=args.bf16,
+             uk_bf16=args.bf16, c_solver=args.c_solver,
              lanczos_max=args.lanczos_max)
     b = torch.tensor(W.rhs(n, 0), device="cuda")
     y = torch.empty_like(b)
@@ -73,7 +80,22 @@ def main(argv=None):
     tr = h.traffic()
     byts = tr["a0_bytes"] if args.op == "a0" else tr["apply_bytes"]
     best = min(times)
-    print(json.dumps({"workload": args.workload, "op": args.op, "ms": times,
+    fam = None
+    if args.families:
+        h.reset_counters()
+        h.set_timing(True)
+        for _ in range(args.reps):
+            once()
+        torch.cuda.synchronize()
+        h.set_timing(False)
+        cnt = h.counters()["families"]
+        fb = h.traffic()["family_bytes"]
+        fam = {f: {"us_per_launch": round(v["ms"] * 1e3 / v["launches"], 2),
+                   "launches_per_rep": v["launches"] / args.reps,
+                   "GBps": (round(fb.get(f, 0) / (v["ms"] * 1e-3 / v["launches"]) / 1e9, 1)
+                            if fb.get(f, 0) > 0 and v["ms"] > 0 else None)}
+               for f, v in cnt.items() if v["launches"] > 0}
+    print(json.dumps({"workload": args.workload, "op": args.op, "ms": times, "families": fam,
                       "best_ms": best, "algorithmic_bytes": byts,
                       "GBps_best": byts / (best * 1e-3) / 1e9 if args.op != "pcg" else None,
                       "info": {k: v for k, v in h.info().items()
