@@ -138,6 +138,7 @@ struct ddlr_ctx {
   bool use_tma64 = false, use_tma32 = false;
   bool use_sf64 = false, use_sf32 = false;   // synchronisation-free interior solve
   bool uvec = true;           // vector-load U_k products (DDLR_UVEC=0: scalar kernels)
+  unsigned *udone = nullptr;  // arrival counter of the fused U^T x reduction (0 between launches)
   int chunk_rows = 0;         // rows per thread of the level-chunk solve: 0 = 2 (FP64) / 4 (FP32);
                               // DDLR_CHUNK_ROWS=1|2|4 fixes it
   int2 *l_span = nullptr, *u_span = nullptr;
@@ -521,21 +522,25 @@ int uvec_lanes(ddlr_ctx *c, int k) {
   return (L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) ? L : 0;
 }
 
-// partials of t = U^T x over kRedGrid CTAs (rows of U = nrows)
+// out = coef .* (U^T x) or H (U^T x) (rows of U = nrows): the vector kernel
+// with the final reduction in its last CTA, else partials over kRedGrid CTAs
+// and k_reduce_cols
 template <typename T, typename TU>
-void launch_utx(ddlr_ctx *c, long long nrows, int k, const TU *U, const T *x, T *part, const int *gate) {
+void launch_utx(ddlr_ctx *c, long long nrows, int k, const TU *U, const T *x, T *part, const T *coef,
+                const T *H, T *out, const int *gate) {
 #define DDLR_UTX(Lc)                                                                                   \
   KL(c, "utx", c->stream, (k_utx_vec<T, TU, Lc, kUvecNT, kUvecUnr>), kRedGrid, kUvecNT, 0, nrows, U, x, part, \
-     gate)
+     gate, c->udone, coef, H, out)
   switch (uvec_lanes<TU>(c, k)) {
-    case 1: DDLR_UTX(1); break;
-    case 2: DDLR_UTX(2); break;
-    case 4: DDLR_UTX(4); break;
-    case 8: DDLR_UTX(8); break;
-    case 16: DDLR_UTX(16); break;
-    case 32: DDLR_UTX(32); break;
+    case 1: DDLR_UTX(1); return;
+    case 2: DDLR_UTX(2); return;
+    case 4: DDLR_UTX(4); return;
+    case 8: DDLR_UTX(8); return;
+    case 16: DDLR_UTX(16); return;
+    case 32: DDLR_UTX(32); return;
     default:
       KL(c, "utx", c->stream, (k_utx_partial<T, TU, 256>), kRedGrid, 256, 0, int(nrows), k, U, x, part, gate);
+      KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T), kRedGrid, k, part, coef, H, out, gate);
   }
 #undef DDLR_UTX
 }
@@ -641,9 +646,7 @@ void apply_dev(ddlr_ctx *c, const TU *U, const T *x, T *u, const int *gate) {
     a0_solve<T>(c, x, z, gate);                                      // A0 z = x
     KL(c, "et", c->stream, k_et<T>, nblk(s), kThreads, 0,            // y = E^T z
        s, m, c->eht_rp, c->eht_ci, Prec<T>::eht(c), ia, a, z, y, gate);
-    launch_utx<T, TU>(c, s, k, U, y, part, gate);                     // t = D U^T y
-    KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
-       kRedGrid, k, part, Prec<T>::coef(c), (const T *)nullptr, t, gate);
+    launch_utx<T, TU>(c, s, k, U, y, part, Prec<T>::coef(c), (const T *)nullptr, t, gate);   // t = D U^T y
     launch_w_rhs<T, TU>(c, s, m, k, U, t, y, Prec<T>::inv1mt(c), a, x, w, rhs, gate);   // w, x_C - a w
     KL(c, "e_int", c->stream, k_e_interior<T>, nblk(m), kThreads, 0,
        m, c->eh_rp, c->eh_ci, Prec<T>::eh(c), ia, w, x, rhs, gate);   // x_B + a^-1 Ehat w
@@ -651,9 +654,7 @@ void apply_dev(ddlr_ctx *c, const TU *U, const T *x, T *u, const int *gate) {
   } else {
     T *t = Prec<T>::w(c, 4);
     a0_solve<T>(c, x, u, gate);
-    launch_utx<T, TU>(c, n, k, U, x, part, gate);
-    KL(c, "reduce", c->stream, k_reduce_cols<T>, 1, 256, k * sizeof(T),
-       kRedGrid, k, part, (const T *)nullptr, Prec<T>::Hk(c), t, gate);
+    launch_utx<T, TU>(c, n, k, U, x, part, (const T *)nullptr, Prec<T>::Hk(c), t, gate);
     launch_u_add<T, TU>(c, n, k, U, t, u, gate);
   }
 }
@@ -1383,6 +1384,8 @@ void allocate(ddlr_ctx *c) {
   ck(cudaMemsetAsync(c->Hk64, 0, sizeof(double) * k * k, c->stream), "memset");
   ck(cudaMemsetAsync(c->inv1mt64, 0, sizeof(double), c->stream), "memset");
   c->dflag = c->alloc<int>(4);
+  c->udone = c->alloc<unsigned>(1);
+  ck(cudaMemsetAsync(c->udone, 0, sizeof(unsigned), c->stream), "memset");
   for (int i = 0; i < 8; i++) c->w64[i] = c->alloc<double>(n);
   int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
   mmax = std::max(std::min(mmax, P.s), k);

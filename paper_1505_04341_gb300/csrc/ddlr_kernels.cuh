@@ -759,9 +759,14 @@ template <> struct Unpack16<__nv_bfloat16> {
 
 // stage 1 of t = U^T x: partials[blk][c] over this CTA's rows (fixed grid,
 // fixed order)
+// With done != nullptr the CTA that finishes last (arrival counter, no
+// waiting) also does stage 2 in the order of k_reduce_cols: out = coef .* sum
+// (coef != nullptr), then out = H out (H != nullptr, k x k), and re-arms the
+// counter.
 template <typename T, typename TU, int L, int NT, int UNR>
 __global__ void __launch_bounds__(NT, 2)   // two CTAs per SM: the fixed grid of 2 x 152 in one wave
-k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate) {
+k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate, unsigned *done = nullptr,
+          const T *coef = nullptr, const T *H = nullptr, T *out = nullptr) {
   if (gate && *gate) return;
   constexpr int E = Unpack16<TU>::E, K = L * E, RW = 32 / L, NW = NT / 32;
   __shared__ T red[NW][K];
@@ -803,6 +808,33 @@ k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate
     for (int w = 0; w < NW; w++) sum += red[w][c];
     partials[(long long)blockIdx.x * K + c] = sum;
   }
+  if (!done) return;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int G = gridDim.x;
+  T *tmp = &red[0][0];   // K values
+  for (int c = wi; c < K; c += NW) {
+    T sum = 0;
+    for (int g = lane; g < G; g += 32) sum += __ldcg(partials + (long long)g * K + c);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) tmp[c] = coef ? coef[c] * sum : sum;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += NT) {
+    if (H) {
+      T sum = 0;
+      for (int b = 0; b < K; b++) sum += H[c * K + b] * tmp[b];
+      out[c] = sum;
+    } else {
+      out[c] = tmp[c];
+    }
+  }
+  if (threadIdx.x == 0) *done = 0u;
 }
 
 // row dot products d_r = U[r][:] . t, L lanes per row, UNR rows in flight per

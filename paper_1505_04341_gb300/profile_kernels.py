@@ -39,6 +39,9 @@ def main(argv=None):
     ap.add_argument("--lanczos-max", type=int, default=0)
     ap.add_argument("--c-solver", type=int, default=0)
     ap.add_argument("--families", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--scale-diag", type=int, default=0)
+    ap.add_argument("--maxit", type=int, default=500)
     args = ap.parse_args(argv)
 
     import torch
@@ -52,9 +55,13 @@ def main(argv=None):
     n = A[0]
     h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=0,
              c_order=args.c_order, b_order=args.b_order, precision=args.precision,
-             uk_bf16=args.bf16, c_solver=args.c_solver,
-             lanczos_max=args.lanczos_max)
-    b = torch.tensor(W.rhs(n, 0), device="cuda")
+             uk_bf16=args.bf16, c_solver=args.c_solver, scale_diag=args.scale_diag,
+             max_nrhs=args.nrhs, lanczos_max=args.lanczos_max)
+    if args.nrhs == 1:
+        b = torch.tensor(W.rhs(n, 0), device="cuda")
+    else:   # n x nrhs column-major block
+        import numpy as np
+        b = torch.tensor(np.stack([W.rhs(n, s) for s in range(args.nrhs)], axis=1), device="cuda").T.contiguous().T
     y = torch.empty_like(b)
     stream = torch.cuda.current_stream()
 
@@ -64,7 +71,7 @@ def main(argv=None):
         elif args.op == "apply":
             h.apply(b, y)
         else:
-            h.pcg(b, y, tol=1e-8)
+            h.pcg(b, y, tol=1e-8, maxit=args.maxit)
 
     once()
     torch.cuda.synchronize()
