@@ -59,9 +59,11 @@ typedef struct {
   int factor;              /* local solver: 0 = IC(0) on the block pattern,
                               1 = exact Cholesky (IC on the symbolic fill pattern) */
   int c_order;             /* elimination order of C_a: 0 = ascending original
-                              index, 1 = greedy multicolour (2 colours on grids)   */
+                              index, 1 = multicolour (the two colour classes of a
+                              bipartite graph, else greedy colouring)              */
   int b_order;             /* elimination order inside the interior blocks B_{i,a}:
-                              0 = ascending original index, 1 = greedy multicolour */
+                              0 = ascending original index, 1 = multicolour as for
+                              c_order                                              */
   int precision;           /* 0 = FP64 throughout; 1 = mixed: FP32 factors and
                               triangular solves, FP32/BF16 U_k, inside an FP64
                               flexible CG                                          */

@@ -16,7 +16,7 @@
  *     A0 = blkdiag(B + a^-2 Ehat Ehat^T, C + a^2 I), A = A0 - E E^T;
  *   - Sec. 4.1, 5: local solvers = incomplete Cholesky IC(0) on the pattern
  *     (or exact Cholesky, dense), one factor per B_{i,a} and one for C_a, each
- *     in its elimination order (ascending index, or greedy multicolour);
+ *     in its elimination order (ascending index, or multicolour);
  *   - Sec. 4.4 (eq. converge): Lanczos on H = E^T A0^-1 E (DDLR-1) or on
  *     E^T A0^-2 E (DDLR-2), with full reorthogonalisation (two classical
  *     Gram-Schmidt passes), convergence checked every `check` steps;
@@ -33,9 +33,10 @@
  *
  * Readings where the paper is silent are the same as the CUDA library's and are
  * listed with the design notes: natural (ascending original index) elimination
- * order inside interior blocks (b_order 0) or greedy multicolour (b_order 1);
+ * order inside interior blocks (b_order 0) or multicolour (b_order 1: the two
+ * colour classes of a bipartite block graph, else a greedy colouring);
  * C_a factored like a local block, in ascending original index (c_order 0) or
- * greedy multicolour order (c_order 1); Lanczos
+ * multicolour order (c_order 1); Lanczos
  * start vector from SplitMix64; breakdown restarts; theta = Ritz_{k+1}.
  */
 #include <math.h>
@@ -702,20 +703,52 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     free(t);
     if (st != OR_OK) { sp_free(&B); break; }
 
-    /* elimination order: ascending index, or greedy multicolour for C_a */
+    /* elimination order: ascending index, or multicolour.  Multicolour: a
+     * bipartite block graph is split into its two colour classes (each
+     * connected component's lowest-index node in class 0); any other graph
+     * is coloured greedily (ascending index, smallest colour no lower-indexed
+     * neighbour has).  Nodes are then eliminated by colour, then index. */
     for (int e = 0; e < nb; e++) f->ord[e] = e;
     if ((b == p && c_order == 1) || (b < p && b_order == 1)) {
-      int *col = (int *)malloc(sizeof(int) * (size_t)nb);
+      int *col = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
       int *used = (int *)calloc((size_t)nb + 2, sizeof(int));
       int nc = 0;
-      for (int r = 0; r < nb; r++) {
-        for (int q = B.rp[r]; q < B.rp[r + 1]; q++)
-          if (B.ci[q] < r) used[col[B.ci[q]]] = r + 1;
-        int c = 0;
-        while (used[c] == r + 1) c++;
-        col[r] = c;
-        if (c + 1 > nc) nc = c + 1;
+      /* two-colouring: give every node the class its component's lowest node
+       * forces, following edges from lower to higher visited nodes (a plain
+       * depth-first walk with an explicit stack), and verify every edge */
+      int *stack = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
+      for (int r = 0; r < nb; r++) col[r] = -1;
+      for (int r0 = 0; r0 < nb; r0++) {
+        if (col[r0] >= 0) continue;
+        int top = 0;
+        col[r0] = 0;
+        stack[top++] = r0;
+        while (top > 0) {
+          int u = stack[--top];
+          for (int q = B.rp[u]; q < B.rp[u + 1]; q++) {
+            int v = B.ci[q];
+            if (v != u && col[v] < 0) { col[v] = 1 - col[u]; stack[top++] = v; }
+          }
+        }
       }
+      int bip = 1;
+      for (int r = 0; r < nb && bip; r++)
+        for (int q = B.rp[r]; q < B.rp[r + 1]; q++)
+          if (B.ci[q] != r && col[B.ci[q]] == col[r]) { bip = 0; break; }
+      if (bip) {
+        for (int r = 0; r < nb; r++) if (col[r] + 1 > nc) nc = col[r] + 1;
+      } else {
+        nc = 0;
+        for (int r = 0; r < nb; r++) {
+          for (int q = B.rp[r]; q < B.rp[r + 1]; q++)
+            if (B.ci[q] < r) used[col[B.ci[q]]] = r + 1;
+          int c = 0;
+          while (used[c] == r + 1) c++;
+          col[r] = c;
+          if (c + 1 > nc) nc = c + 1;
+        }
+      }
+      free(stack);
       if (b == p) o->ncolors = nc;
       int e = 0;
       for (int c = 0; c < nc; c++)

@@ -1749,22 +1749,26 @@ void precond_mr(ddlr_ctx *c, const double *Rr, double *Z, int R, const int *gate
   const int n = c->P.n;
   const long long nR = (long long)n * R;
   const int bd = c->bt.bd_elem;
-  const double *in = Rr;
-  if (c->dsc_dev) {
-    KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Rr, c->bt.S, gate);
-    in = c->bt.S;
-  }
   if (c->opt.precision == 0) {
+    const double *in = Rr;
+    if (c->dsc_dev) {
+      KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Rr, c->bt.S,
+         gate);
+      in = c->bt.S;
+    }
     apply_mr<double, double>(c, c->U64, in, Z, R, gate);
+    if (c->dsc_dev)
+      KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Z, Z, gate);
   } else {
+    // scaling and change of precision in one pass each way
     float *i32 = c->bt.w32[5], *o32 = c->bt.w32[6];
-    KL(c, "vec_mr", c->stream, (k_cast<float, double>), eblk(nR, bd), bd, 0, nR, in, i32, gate);
+    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<float, double>), eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev,
+       Rr, i32, gate);
     if (c->opt.uk_bf16) apply_mr<float, __nv_bfloat16>(c, c->Ub16, i32, o32, R, gate);
     else apply_mr<float, float>(c, c->U32, i32, o32, R, gate);
-    KL(c, "vec_mr", c->stream, (k_cast<double, float>), eblk(nR, bd), bd, 0, nR, o32, Z, gate);
+    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<double, float>), eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev,
+       o32, Z, gate);
   }
-  if (c->dsc_dev)
-    KL(c, "vec_mr", c->stream, k_scale_rows_mr, eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev, Z, Z, gate);
 }
 
 // Autotuner: block shapes of the batched solve kernels, picked by timing the
@@ -1835,7 +1839,11 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   KL(c, "pcg_mr", c->stream, k_pcgmr_rr, 1, 64, 0, B.st, part, kRedGrid);
   KL(c, "pcg_mr", c->stream, k_pcgmr_true_res, eblk(nR, bd), bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
      B.B, B.X, B.T);
-  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part, gate);
+  // T.T only when a column's true residual is checked this iteration
+  const int *gate_chk = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
+                                                      offsetof(PcgStateMR, no_check));
+  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part,
+     gate_chk);
   KL(c, "pcg_mr", c->stream, k_pcgmr_true_dec, 1, 64, 0, B.st, part, kRedGrid);
   KL(c, "pcg_mr", c->stream, k_pcgmr_copy_r, eblk(nR, bd), bd, 0, (long long)n, B.st, B.T, B.Rr);
   precond_mr(c, B.Rr, B.Z, R, gate);

@@ -14,6 +14,14 @@
 
 namespace ddlr {
 
+// (row, column) of element idx of a row-major n x R block.  32-bit unsigned
+// division when idx fits (a 64-bit division is a long instruction sequence,
+// a large share of these streaming kernels' work)
+__device__ __forceinline__ long long row_of(long long idx, int R) {
+  return idx < 0xffffffffLL ? (long long)(unsigned(idx) / unsigned(R)) : idx / R;
+}
+__device__ __forceinline__ int col_of(long long idx, long long row, int R) { return int(idx - row * R); }
+
 constexpr int kMaxR = 64;   // right-hand sides per batched launch
 
 // rows [r0, r1) of reduction range g out of G over nrows rows
@@ -101,8 +109,8 @@ __global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,
                         const int *gate) {
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long j = idx / R;
-  const int q = int(idx % R);
+  const long long j = row_of(idx, R);
+  const int q = col_of(idx, j, R);
   if (j >= s) return;
   T acc = 0;
   for (int p = eht_rp[j]; p < eht_rp[j + 1]; p++) acc += eht_val[p] * Z[(long long)eht_ci[p] * R + q];
@@ -116,8 +124,8 @@ __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
                                 int R, const int *gate) {
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long r = idx / R;
-  const int q = int(idx % R);
+  const long long r = row_of(idx, R);
+  const int q = col_of(idx, r, R);
   if (r >= m) return;
   T acc = 0;
   for (int p = eh_rp[r]; p < eh_rp[r + 1]; p++) acc += eh_val[p] * W[(long long)eh_ci[p] * R + q];
@@ -198,8 +206,8 @@ __global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const 
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = Tm[o];
   __syncthreads();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long j = idx / R;
-  const int q = int(idx % R);
+  const long long j = row_of(idx, R);
+  const int q = col_of(idx, j, R);
   if (j >= s) return;
   const TU *u = U + j * k;
   T acc = 0;
@@ -218,8 +226,8 @@ __global__ void k_u_add_mr(long long nrows, int k, const TU *U, const T *HT, T *
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = HT[o];
   __syncthreads();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long r = idx / R;
-  const int q = int(idx % R);
+  const long long r = row_of(idx, R);
+  const int q = col_of(idx, r, R);
   if (r >= nrows) return;
   const TU *u = U + r * k;
   T acc = 0;
@@ -233,8 +241,8 @@ __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
                           const T *val, const T *P, T *Q, int R, const int *gate) {
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long r = idx / R;
-  const int q = int(idx % R);
+  const long long r = row_of(idx, R);
+  const int q = col_of(idx, r, R);
   if (r >= n) return;
   const int g = int(r >> 5), l = int(r & 31);
   const int off = soff[g] + l, w = sw[g];
@@ -292,7 +300,9 @@ struct PcgStateMR {
   double rz[kMaxR], pq[kMaxR], alpha[kMaxR], beta[kMaxR], rr[kMaxR], bb[kMaxR];
   double tol2[kMaxR], rt2[kMaxR];
   int its[kMaxR], done[kMaxR], status[kMaxR], check[kMaxR], restart[kMaxR];
-  int R, maxit, flexible, all_done, any_check, pad[3];
+  int R, maxit, flexible, all_done, any_check;
+  int no_check;   // 1 unless some column's true residual is to be checked this iteration
+  int pad[2];
 };
 
 __device__ __forceinline__ double col_sum(const double *partials, int G, int R, int off) {
@@ -305,7 +315,7 @@ __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int 
                              double tol, int maxit, int flexible) {
   const int q = threadIdx.x;
   if (q == 0) {
-    st->R = R; st->maxit = maxit; st->flexible = flexible; st->any_check = 0;
+    st->R = R; st->maxit = maxit; st->flexible = flexible; st->any_check = 0; st->no_check = 1;
   }
   if (q < R) {
     const double bb = col_sum(partials, G, R, q);
@@ -355,7 +365,7 @@ __global__ void k_pcgmr_update(long long n, const PcgStateMR *st, const double *
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
-  const int q = int(idx % R);
+  const int q = col_of(idx, row_of(idx, R), R);
   if (st->done[q]) return;
   const double a = st->alpha[q];
   X[idx] += a * P[idx];
@@ -380,7 +390,7 @@ __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
     }
   }
   __syncthreads();
-  if (q == 0) st->any_check = anyc;
+  if (q == 0) { st->any_check = anyc; st->no_check = anyc ? 0 : 1; }
 }
 
 // T = B - A X for the columns whose true residual is to be checked
@@ -390,8 +400,8 @@ __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, c
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long r = idx / R;
-  const int q = int(idx % R);
+  const long long r = row_of(idx, R);
+  const int q = col_of(idx, r, R);
   if (r >= n || !st->check[q]) return;
   const int g = int(r >> 5), l = int(r & 31);
   const int off = soff[g] + l, w = sw[g];
@@ -401,8 +411,9 @@ __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, c
 }
 
 __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) {
-  if (st->all_done || !st->any_check) return;
   const int q = threadIdx.x, R = st->R;
+  if (q == 0) st->no_check = 1;   // the check of this iteration is consumed here
+  if (st->all_done || !st->any_check) return;
   if (q < R && st->check[q] && !st->done[q]) {
     const double rt2 = col_sum(partials, G, R, q);
     st->rt2[q] = rt2;
@@ -420,7 +431,7 @@ __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
-  const int q = int(idx % R);
+  const int q = col_of(idx, row_of(idx, R), R);
   if (st->restart[q] && !st->done[q]) Rr[idx] = Tt[idx];
 }
 
@@ -451,7 +462,7 @@ __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, do
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
-  const int q = int(idx % R);
+  const int q = col_of(idx, row_of(idx, R), R);
   if (st->done[q]) return;
   const double z = Z[idx];
   P[idx] = z + st->beta[q] * P[idx];
@@ -470,23 +481,35 @@ __global__ void k_batch_in(int n, int R, const int *perm, const double *in, long
                            double *out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
-  const long long g = idx / R;
-  const int q = int(idx % R);
+  const long long g = row_of(idx, R);
+  const int q = col_of(idx, g, R);
   out[idx] = in[q * ld + perm[g]];
 }
 __global__ void k_batch_out(int n, int R, const int *perm, const double *in, double *out,
                             long long ld) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
-  const long long g = idx / R;
-  const int q = int(idx % R);
+  const long long g = row_of(idx, R);
+  const int q = col_of(idx, g, R);
   out[q * ld + perm[g]] = in[idx];
 }
+// out = TO(in * d_row) (d == nullptr: no scaling): the diagonal scaling of the
+// scaled system and the change of precision of the preconditioner in one pass
+template <typename TO, typename TI>
+__global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *in, TO *out, const int *gate) {
+  if (gate && *gate) return;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * R) {
+    const double v = double(in[idx]);
+    out[idx] = TO(d ? v * d[row_of(idx, R)] : v);
+  }
+}
+
 __global__ void k_scale_rows_mr(long long n, int R, const double *d, const double *in,
                                 double *out, const int *gate) {
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < n * R) out[idx] = in[idx] * d[idx / R];
+  if (idx < n * R) out[idx] = in[idx] * d[row_of(idx, R)];
 }
 
 }  // namespace ddlr

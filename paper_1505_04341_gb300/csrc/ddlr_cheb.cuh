@@ -123,7 +123,7 @@ __global__ void k_cheb_first(int s, int m, int R, const int *rp, const int *ci, 
   if (gate && *gate) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * R) return;
-  const int i = int(e / R), col = int(e - (long long)i * R);
+  const int i = R == 1 ? int(e) : int(unsigned(e) / unsigned(R)), col = int(e - (long long)i * R);
   const long long g = (long long)(m + i) * R + col;
   const T c0 = tab[2];
   const T di = c0 * z[g];
@@ -144,7 +144,7 @@ __global__ void k_cheb_step(int s, int m, int R, const int *rp, const int *ci, c
   if (gate && *gate) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * R) return;
-  const int i = int(e / R), col = int(e - (long long)i * R);
+  const int i = R == 1 ? int(e) : int(unsigned(e) / unsigned(R)), col = int(e - (long long)i * R);
   const long long g = (long long)(m + i) * R + col;
   const T c1 = tab[2 + j], c2 = tab[1 + t + j];
   const T dn = c1 * dold[g] + c2 * zt[g];

@@ -8,8 +8,9 @@
 //    B_{b,a} = B_b + a^-2 E_b E_b^T, block p is C_a = C + a^2 I.
 //  * Local solvers (Sec. 5): incomplete Cholesky with zero fill on the block
 //    pattern, or exact Cholesky on the symbolic fill pattern.  The elimination
-//    order is ascending original index (b_order 0) or greedy multicolour
-//    (b_order 1) for interior blocks, and likewise (c_order) for C_a.
+//    order is ascending original index (b_order 0) or multicolour (b_order
+//    1: the two colour classes of a bipartite block graph, else greedy
+//    colouring) for interior blocks, and likewise (c_order) for C_a.
 //  * Device order: inside every block the rows are sorted by (dependency
 //    level, elimination position).  This is a topological order of the
 //    factor's dependency graph, so it leaves the factor unchanged and lets
@@ -256,15 +257,43 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     // elimination order
     std::iota(ord.begin(), ord.end(), 0);
     if ((b == p && opt.c_order == 1) || (b < p && opt.b_order == 1)) {
+      // a bipartite block graph takes its two-colouring: breadth-first from
+      // the lowest unvisited node of each component, which gets colour 0
+      // (unique, and the same colouring the greedy rule finds whenever that
+      // one needs only two colours); otherwise greedy: ascending index, the
+      // smallest colour no lower-indexed neighbour has
       col.assign(nb, -1);
-      used.assign(nb + 2, -1);
       int nc = 0;
-      for (int t = 0; t < nb; t++) {
-        for (int q = arp[t]; q < arp[t + 1]; q++) if (aci[q] < t) used[col[aci[q]]] = t;
-        int c = 0;
-        while (used[c] == t) c++;
-        col[t] = c;
-        nc = std::max(nc, c + 1);
+      bool bip = true;
+      {
+        std::vector<int> queue(nb);
+        for (int t0 = 0; t0 < nb && bip; t0++) {
+          if (col[t0] >= 0) continue;
+          col[t0] = 0;
+          int head = 0, tail = 0;
+          queue[tail++] = t0;
+          while (head < tail && bip) {
+            const int u = queue[head++];
+            for (int q = arp[u]; q < arp[u + 1]; q++) {
+              const int v = aci[q];
+              if (col[v] < 0) { col[v] = 1 - col[u]; queue[tail++] = v; }
+              else if (col[v] == col[u]) { bip = false; break; }
+            }
+          }
+        }
+        if (bip) for (int t = 0; t < nb; t++) nc = std::max(nc, col[t] + 1);
+      }
+      if (!bip) {
+        col.assign(nb, -1);
+        used.assign(nb + 2, -1);
+        nc = 0;
+        for (int t = 0; t < nb; t++) {
+          for (int q = arp[t]; q < arp[t + 1]; q++) if (aci[q] < t) used[col[aci[q]]] = t;
+          int c = 0;
+          while (used[c] == t) c++;
+          col[t] = c;
+          nc = std::max(nc, c + 1);
+        }
       }
       blk_colors[b] = nc;
       // stable counting sort by colour
