@@ -1832,24 +1832,24 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   double *part = B.part64;
   KL(c, "spmv_mr", c->stream, k_spmv_mr<double>, eblk(nR, bd), bd, 0, n, c->a_soff, c->a_sw, c->a_col,
      c->a_val, B.P, B.Q, R, gate);
-  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.P, B.Q, (const double *)nullptr, part, gate);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_alpha, 1, 64, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_update, eblk(nR, bd), bd, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr);
-  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Rr, (const double *)nullptr, part, gate);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_rr, 1, 64, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_true_res, eblk(nR, bd), bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
+  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.P, B.Q, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_alpha, 1, kScalarThreads, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr_axpy", c->stream, k_pcgmr_update, eblk(nR, bd), bd, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr);
+  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Rr, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_rr, 1, kScalarThreads, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr_check", c->stream, k_pcgmr_true_res, eblk(nR, bd), bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
      B.B, B.X, B.T);
   // T.T only when a column's true residual is checked this iteration
   const int *gate_chk = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
                                                       offsetof(PcgStateMR, no_check));
-  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part,
+  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part,
      gate_chk);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_true_dec, 1, 64, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_copy_r, eblk(nR, bd), bd, 0, (long long)n, B.st, B.T, B.Rr);
+  KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_true_dec, 1, kScalarThreads, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr_check", c->stream, k_pcgmr_copy_r, eblk(nR, bd), bd, 0, (long long)n, B.st, B.T, B.Rr);
   precond_mr(c, B.Rr, B.Z, R, gate);
-  KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, flexible ? B.Zo : B.Z, part, gate);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_beta, 1, 64, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_p, eblk(nR, bd), bd, 0, (long long)n, B.st, B.Z, B.P, flexible ? B.Zo : (double *)nullptr);
+  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, flexible ? B.Zo : B.Z, part, gate);
+  KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_beta, 1, kScalarThreads, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr_p", c->stream, k_pcgmr_p, eblk(nR, bd), bd, 0, (long long)n, B.st, B.Z, B.P, flexible ? B.Zo : (double *)nullptr);
 }
 
 // block PCG on B.B (device order, row-major, R columns) -> B.X
@@ -1878,10 +1878,10 @@ void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info
   ck(cudaMemsetAsync(B.X, 0, sizeof(double) * nR, c->stream), "memset");
   ck(cudaMemcpyAsync(B.Rr, B.B, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
   KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.B, B.B, (const double *)nullptr, part, (const int *)nullptr);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_init, 1, 64, 0, B.st, part, kRedGrid, R, tol, maxit, flexible);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_init, 1, kScalarThreads, 0, B.st, part, kRedGrid, R, tol, maxit, flexible);
   precond_mr(c, B.Rr, B.Z, R, gate);
   KL(c, "pcg_mr", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, (const double *)nullptr, part, gate);
-  KL(c, "pcg_mr", c->stream, k_pcgmr_rz0, 1, 64, 0, B.st, part, kRedGrid);
+  KL(c, "pcg_mr", c->stream, k_pcgmr_rz0, 1, kScalarThreads, 0, B.st, part, kRedGrid);
   ck(cudaMemcpyAsync(B.P, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
   ck(cudaMemcpyAsync(B.Zo, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
   auto &GR = B.graphs[R];

@@ -305,20 +305,32 @@ struct PcgStateMR {
   int pad[2];
 };
 
-__device__ __forceinline__ double col_sum(const double *partials, int G, int R, int off) {
-  double s = 0;
-  for (int g = 0; g < G; g++) s += partials[(long long)g * 2 * R + off];
-  return s;
+// sums[o] = sum over the G partial rows of column o (o < no), a warp per
+// column: lanes take every 32nd partial in order, then a shuffle tree (a
+// serial sum of G = 304 FP64 values is ~20k cycles of add latency here).
+// Every thread of the block must call it (it ends in a barrier).
+constexpr int kScalarThreads = 1024;
+__device__ __forceinline__ void col_sums(const double *partials, int G, int R, int no, double *sums) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int o = w; o < no; o += nw) {
+    double v = 0;
+    for (int g = l; g < G; g += 32) v += partials[(long long)g * 2 * R + o];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (l == 0) sums[o] = v;
+  }
+  __syncthreads();
 }
 
 __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int R,
                              double tol, int maxit, int flexible) {
   const int q = threadIdx.x;
+  __shared__ double sm[kMaxR];
+  col_sums(partials, G, R, R, sm);
   if (q == 0) {
     st->R = R; st->maxit = maxit; st->flexible = flexible; st->any_check = 0; st->no_check = 1;
   }
   if (q < R) {
-    const double bb = col_sum(partials, G, R, q);
+    const double bb = sm[q];
     st->bb[q] = bb;
     st->tol2[q] = tol * tol * bb;
     st->its[q] = 0; st->status[q] = 0; st->check[q] = 0; st->restart[q] = 0;
@@ -336,8 +348,10 @@ __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int 
 __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
+  __shared__ double sm[kMaxR];
+  col_sums(partials, G, R, R, sm);
   if (q < R && !st->done[q]) {
-    const double s = col_sum(partials, G, R, q);
+    const double s = sm[q];
     st->rz[q] = s;
     if (!(s == s) || isinf(s)) { st->status[q] = 7; st->done[q] = 1; }
   }
@@ -346,10 +360,12 @@ __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
 __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
+  __shared__ double sm[kMaxR];
+  col_sums(partials, G, R, R, sm);
   if (q < R) {
     double a = 0.0;
     if (!st->done[q]) {
-      const double pq = col_sum(partials, G, R, q);
+      const double pq = sm[q];
       st->pq[q] = pq;
       a = st->rz[q] / pq;
       if (!(a == a) || isinf(a)) { st->status[q] = 7; st->done[q] = 1; a = 0.0; }
@@ -376,10 +392,11 @@ __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ int anyc;
+  __shared__ double sm[kMaxR];
   if (q == 0) anyc = 0;
-  __syncthreads();
+  col_sums(partials, G, R, R, sm);
   if (q < R && !st->done[q]) {
-    const double rr = col_sum(partials, G, R, q);
+    const double rr = sm[q];
     st->rr[q] = rr;
     st->its[q] += 1;
     if (!(rr == rr) || isinf(rr)) { st->status[q] = 7; st->done[q] = 1; }
@@ -414,8 +431,10 @@ __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) 
   const int q = threadIdx.x, R = st->R;
   if (q == 0) st->no_check = 1;   // the check of this iteration is consumed here
   if (st->all_done || !st->any_check) return;
+  __shared__ double sm[kMaxR];
+  col_sums(partials, G, R, R, sm);
   if (q < R && st->check[q] && !st->done[q]) {
-    const double rt2 = col_sum(partials, G, R, q);
+    const double rt2 = sm[q];
     st->rt2[q] = rt2;
     if (rt2 <= st->tol2[q]) { st->status[q] = 0; st->done[q] = 1; }
     else {
@@ -438,9 +457,11 @@ __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *
 __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
+  __shared__ double sm[2 * kMaxR];
+  col_sums(partials, G, R, 2 * R, sm);
   if (q < R && !st->done[q]) {
-    const double rzn = col_sum(partials, G, R, q);
-    const double rzo = col_sum(partials, G, R, R + q);
+    const double rzn = sm[q];
+    const double rzo = sm[R + q];
     double beta = st->flexible ? (rzn - rzo) / st->rz[q] : rzn / st->rz[q];
     if (st->restart[q]) beta = 0.0;
     st->beta[q] = beta;
