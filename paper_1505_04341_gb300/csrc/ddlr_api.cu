@@ -139,6 +139,7 @@ struct ddlr_ctx {
   bool use_sf64 = false, use_sf32 = false;   // synchronisation-free interior solve
   bool uvec = true;           // vector-load U_k products (DDLR_UVEC=0: scalar kernels)
   unsigned *udone = nullptr;  // arrival counter of the fused U^T x reduction (0 between launches)
+  unsigned *pdone = nullptr;  // arrival counter of the fused per-phase PCG reductions
   int chunk_rows = 0;         // rows per thread of the level-chunk solve: 0 = 2 (FP64) / 4 (FP32);
                               // DDLR_CHUNK_ROWS=1|2|4 fixes it
   int2 *l_span = nullptr, *u_span = nullptr;
@@ -513,6 +514,7 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
 // Vector-load kernels (16-byte loads, several rows in flight per thread) when
 // a row of U_k is 1..32 loads of 16 bytes; DDLR_UVEC=0 keeps the scalar ones.
 constexpr int kUvecNT = 512, kUvecUnr = 4, kUrowsUnr = 4;
+
 
 template <typename TU>
 int uvec_lanes(ddlr_ctx *c, int k) {
@@ -1386,6 +1388,8 @@ void allocate(ddlr_ctx *c) {
   c->dflag = c->alloc<int>(4);
   c->udone = c->alloc<unsigned>(1);
   ck(cudaMemsetAsync(c->udone, 0, sizeof(unsigned), c->stream), "memset");
+  c->pdone = c->alloc<unsigned>(1);
+  ck(cudaMemsetAsync(c->pdone, 0, sizeof(unsigned), c->stream), "memset");
   for (int i = 0; i < 8; i++) c->w64[i] = c->alloc<double>(n);
   int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
   mmax = std::max(std::min(mmax, P.s), k);
@@ -1435,22 +1439,26 @@ void allocate(ddlr_ctx *c) {
 
 // one PCG iteration (Sec. 5) on device-order vectors; every kernel reads its
 // scalars from the device state and returns at once after convergence
+
 void pcg_iteration(ddlr_ctx *c, const double *b, double *x, int flexible) {
   const int n = c->P.n;
   double *r = c->pv[1], *z = c->pv[2], *p = c->pv[3], *q = c->pv[4], *t = c->pv[5], *zo = c->pv[6];
   double *part = c->part64;
   const int *gate = pcg_gate(c);
+  // x, r update with r.r and the residual test in one launch, and r.z with
+  // beta in one launch (last-CTA reductions); q = A p keeps a row per thread
+  // (fusing p.q into it needs a capped grid, which measured slower)
   KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, p, q, gate);
   KL(c, "pcg_dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, p, q, part, gate);
   KL(c, "pcg_scalar", c->stream, k_pcg_alpha, 1, 32, 0, c->pcg, part, kRedGrid);
-  KL(c, "pcg_axpy", c->stream, k_pcg_update<256>, kRedGrid, 256, 0, (long long)n, c->pcg, p, q, x, r, part);
-  KL(c, "pcg_scalar", c->stream, k_pcg_rr, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_axpy", c->stream, k_pcg_update_rr<256>, kRedGrid, 256, 0, (long long)n, c->pcg, p, q, x, r, part,
+     c->pdone);
   KL(c, "pcg_check", c->stream, k_pcg_true_res<256>, kRedGrid, 256, 0, n, c->pcg, c->a_soff, c->a_sw, c->a_col, c->a_val, b, x, t, part);
   KL(c, "pcg_scalar", c->stream, k_pcg_true_dec, 1, 32, 0, c->pcg, part, kRedGrid);
   KL(c, "pcg_check", c->stream, k_pcg_copy_r, nblk(n), kThreads, 0, (long long)n, c->pcg, t, r);
   precond(c, r, z, gate);
-  KL(c, "pcg_dot2", c->stream, (k_dot2_partial<double, 256>), kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part, gate);
-  KL(c, "pcg_scalar", c->stream, k_pcg_beta, 1, 32, 0, c->pcg, part, kRedGrid);
+  KL(c, "pcg_dot2", c->stream, k_dot2_beta<256>, kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part,
+     c->pcg, c->pdone);
   KL(c, "pcg_p", c->stream, k_pcg_p, nblk(n), kThreads, 0, (long long)n, c->pcg, z, p, flexible ? zo : (double *)nullptr);
 }
 

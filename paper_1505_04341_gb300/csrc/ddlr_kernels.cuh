@@ -1232,6 +1232,86 @@ __global__ void k_pcg_beta(PcgState *st, const double *partials, int G) {
   }
 }
 
+// ---- fused forms of the per-phase PCG (one launch instead of a reduction
+// kernel plus a one-CTA scalar kernel): every CTA writes its partial sum; the
+// CTA that arrives last (arrival counter, no waiting) sums all partials in a
+// fixed order, updates the PCG state and re-arms the counter.
+__device__ __forceinline__ bool pcg_last_cta(unsigned *done) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// fixed-order sum of G partials by one CTA (valid in thread 0)
+template <int NT>
+__device__ __forceinline__ double pcg_sum_partials(const double *partials, int G, double *sm) {
+  double v = 0;
+  for (int g = threadIdx.x; g < G; g += NT) v += __ldcg(partials + g);
+  return block_sum<double, NT>(v, sm);
+}
+
+// x += alpha p; r -= alpha q; then the recursive-residual test of k_pcg_rr
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_pcg_update_rr(long long n, PcgState *st, const double *p, const double *q, double *x, double *r,
+                double *partials, unsigned *done) {
+  if (st->done) return;
+  __shared__ double sm[NT / 32];
+  const double a = st->alpha;
+  double acc = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+    x[i] += a * p[i];
+    const double ri = r[i] - a * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  acc = block_sum<double, NT>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (!pcg_last_cta(done)) return;
+  const double rr = pcg_sum_partials<NT>(partials, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    *done = 0u;
+    st->rr = rr;
+    st->its += 1;
+    if (!(rr == rr) || isinf(rr)) { st->status = 7; st->done = 1; return; }
+    st->check_true = (rr <= st->tol2) ? 1 : 0;
+    if (!st->check_true && st->its >= st->maxit) { st->status = 5; st->done = 1; }
+  }
+}
+
+// r.z and r.zold, then the beta update of k_pcg_beta
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_dot2_beta(long long n, const double *r, const double *z, const double *zo, double *partials, PcgState *st,
+            unsigned *done) {
+  if (st->done) return;
+  __shared__ double sm[NT / 32];
+  double a1 = 0, a2 = 0;
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+    a1 += r[i] * z[i];
+    a2 += r[i] * zo[i];
+  }
+  a1 = block_sum<double, NT>(a1, sm);
+  a2 = block_sum<double, NT>(a2, sm);
+  if (threadIdx.x == 0) { partials[blockIdx.x] = a1; partials[gridDim.x + blockIdx.x] = a2; }
+  if (!pcg_last_cta(done)) return;
+  const double rzn = pcg_sum_partials<NT>(partials, gridDim.x, sm);
+  const double rzo = pcg_sum_partials<NT>(partials + gridDim.x, gridDim.x, sm);
+  if (threadIdx.x == 0) {
+    *done = 0u;
+    double beta = st->flexible ? (rzn - rzo) / st->rz : rzn / st->rz;
+    if (st->restart) beta = 0.0;
+    st->beta = beta;
+    st->rz = rzn;
+    st->restart = 0;
+    if (!(rzn == rzn) || isinf(rzn)) { st->status = 7; st->done = 1; }
+  }
+}
+
 // p = z + beta p (and z_old = z for flexible CG)
 __global__ void k_pcg_p(long long n, const PcgState *st, const double *z,
                         double *p, double *zold) {
