@@ -1455,7 +1455,9 @@ void pcg_iteration(ddlr_ctx *c, const double *b, double *x, int flexible) {
      c->pdone);
   KL(c, "pcg_check", c->stream, k_pcg_true_res<256>, kRedGrid, 256, 0, n, c->pcg, c->a_soff, c->a_sw, c->a_col, c->a_val, b, x, t, part);
   KL(c, "pcg_scalar", c->stream, k_pcg_true_dec, 1, 32, 0, c->pcg, part, kRedGrid);
-  KL(c, "pcg_check", c->stream, k_pcg_copy_r, nblk(n), kThreads, 0, (long long)n, c->pcg, t, r);
+  // bounded grid: it returns at once in all but restart iterations
+  KL(c, "pcg_check", c->stream, k_pcg_copy_r, std::min<unsigned>(nblk(n), 152 * 8), kThreads, 0, (long long)n, c->pcg,
+     t, r);
   precond(c, r, z, gate);
   KL(c, "pcg_dot2", c->stream, k_dot2_beta<256>, kRedGrid, 256, 0, (long long)n, r, z, flexible ? zo : z, part,
      c->pcg, c->pdone);
@@ -1845,7 +1847,9 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   KL(c, "pcg_mr_axpy", c->stream, k_pcgmr_update, eblk(nR, bd), bd, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr);
   KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Rr, (const double *)nullptr, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_rr, 1, kScalarThreads, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr_check", c->stream, k_pcgmr_true_res, eblk(nR, bd), bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
+  // the check kernels run on a bounded grid: most iterations they return at once
+  const unsigned gchk = (unsigned)std::min<long long>(eblk(nR, bd), 152LL * 8);
+  KL(c, "pcg_mr_check", c->stream, k_pcgmr_true_res, gchk, bd, 0, n, B.st, c->a_soff, c->a_sw, c->a_col, c->a_val,
      B.B, B.X, B.T);
   // T.T only when a column's true residual is checked this iteration
   const int *gate_chk = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
@@ -1853,7 +1857,7 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.T, B.T, (const double *)nullptr, part,
      gate_chk);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_true_dec, 1, kScalarThreads, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr_check", c->stream, k_pcgmr_copy_r, eblk(nR, bd), bd, 0, (long long)n, B.st, B.T, B.Rr);
+  KL(c, "pcg_mr_check", c->stream, k_pcgmr_copy_r, gchk, bd, 0, (long long)n, B.st, B.T, B.Rr);
   precond_mr(c, B.Rr, B.Z, R, gate);
   KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Z, flexible ? B.Zo : B.Z, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_beta, 1, kScalarThreads, 0, B.st, part, kRedGrid);

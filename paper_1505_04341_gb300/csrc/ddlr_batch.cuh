@@ -416,15 +416,17 @@ __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, c
                                  const double *X, double *Tt) {
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long r = row_of(idx, R);
-  const int q = col_of(idx, r, R);
-  if (r >= n || !st->check[q]) return;
-  const int g = int(r >> 5), l = int(r & 31);
-  const int off = soff[g] + l, w = sw[g];
-  double ax = 0;
-  for (int kk = 0; kk < w; kk++) ax += val[off + kk * 32] * X[(long long)col[off + kk * 32] * R + q];
-  Tt[idx] = B[idx] - ax;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * R;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long r = row_of(idx, R);
+    const int q = col_of(idx, r, R);
+    if (!st->check[q]) continue;
+    const int g = int(r >> 5), l = int(r & 31);
+    const int off = soff[g] + l, w = sw[g];
+    double ax = 0;
+    for (int kk = 0; kk < w; kk++) ax += val[off + kk * 32] * X[(long long)col[off + kk * 32] * R + q];
+    Tt[idx] = B[idx] - ax;
+  }
 }
 
 __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) {
@@ -445,13 +447,15 @@ __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) 
   if (q < R) st->check[q] = 0;
 }
 
+// (a restart is only ever set by a true-residual check of this iteration)
 __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *Tt, double *Rr) {
-  if (st->all_done) return;
+  if (st->all_done || !st->any_check) return;
   const int R = st->R;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * R) return;
-  const int q = col_of(idx, row_of(idx, R), R);
-  if (st->restart[q] && !st->done[q]) Rr[idx] = Tt[idx];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n * R;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = col_of(idx, row_of(idx, R), R);
+    if (st->restart[q] && !st->done[q]) Rr[idx] = Tt[idx];
+  }
 }
 
 __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {

@@ -1213,8 +1213,8 @@ __global__ void k_pcg_true_dec(PcgState *st, const double *partials, int G) {
 __global__ void k_pcg_copy_r(long long n, const PcgState *st, const double *t,
                              double *r) {
   if (st->done || !st->restart) return;
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) r[i] = t[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    r[i] = t[i];
 }
 
 // beta = rz_new / rz (Hestenes-Stiefel) or (rz_new - r.z_old) / rz (flexible)
