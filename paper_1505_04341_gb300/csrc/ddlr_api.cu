@@ -229,8 +229,9 @@ struct ddlr_ctx {
     dev_bytes += (long long)bytes;
     return r;
   }
-  template <typename T>
-  T *upload(const std::vector<T> &v) {
+  template <typename V>
+  auto upload(const V &v) -> typename V::value_type * {
+    using T = typename V::value_type;
     T *d = alloc<T>(v.size());
     if (!v.empty()) ck(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream), "upload");
     return d;
@@ -806,7 +807,7 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
       ck(cudaMallocHost(&W.h_st, sizeof(LzState)), "cudaMallocHost");
       ck(cudaEventCreateWithFlags(&W.ev_chk, cudaEventDisableTiming), "event");
       ck(cudaEventCreateWithFlags(&W.ev_done, cudaEventDisableTiming), "event");
-      const std::vector<int> &rank = P.iface_rank;
+      const auto &rank = P.iface_rank;
       std::vector<double> byrank(s), hv(s);
       double nn = 0;
       for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }

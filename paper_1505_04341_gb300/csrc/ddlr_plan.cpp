@@ -122,8 +122,8 @@ int plan_threads(long long work) {
 }
 
 // exclusive prefix sum of counts[0..n) into offsets[0..n]
-template <typename T>
-void prefix(const std::vector<T> &counts, std::vector<T> &offsets) {
+template <typename C, typename D>
+void prefix(const C &counts, D &offsets) {
   offsets.assign(counts.size() + 1, 0);
   for (size_t i = 0; i < counts.size(); i++) offsets[i + 1] = offsets[i] + counts[i];
 }
@@ -197,6 +197,11 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
         if (part[ci[q]] != part[i]) { iface[i] = 1; break; }
   });
   std::vector<std::vector<int>> members(p + 1);
+  {
+    std::vector<int> msize(p + 1, 0);
+    for (int i = 0; i < n; i++) msize[iface[i] ? p : part[i]]++;
+    for (int b = 0; b <= p; b++) members[b].reserve(msize[b]);
+  }
   for (int i = 0; i < n; i++) members[iface[i] ? p : part[i]].push_back(i);
   int s = int(members[p].size());
   if (s == 0) { err = "no interface nodes (p = 1?)"; return DDLR_ERR_INVALID; }
@@ -370,7 +375,8 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   for (int b = 0; b < p; b++) P.levels_interior = std::max(P.levels_interior, blk_levels[b]);
   P.levels_c = std::max(1, blk_levels[p]);
   if (opt.c_order == 1) P.ncolors = blk_colors[p];
-  std::vector<int> low_rp, low_ci;
+  std::vector<int> low_rp;
+  pvec<int> low_ci;
   prefix(low_cnt, low_rp);
   low_ci.resize(low_rp[n]);
   pool.run_dynamic(p + 1, [&](int b) {
@@ -403,8 +409,8 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     }, 256);
     P.a_soff.assign(ns + 1, 0);
     for (int g = 0; g < ns; g++) P.a_soff[g + 1] = P.a_soff[g] + P.a_sw[g] * kSlice;
-    P.a_col.assign(P.a_soff[ns], 0);
-    P.a_src.assign(P.a_soff[ns], -1);
+    P.a_col.resize(P.a_soff[ns]);   // every slot is written below
+    P.a_src.resize(P.a_soff[ns]);
     pool.run(ns, [&](long long lo, long long hi) {
       std::vector<std::pair<int, int>> ent;
       for (int g = int(lo); g < int(hi); g++)
@@ -429,7 +435,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   // ---- Ehat (interior rows) and Ehat^T (interface rows): count, prefix, fill
   {
     auto build = [&](int rows, int row0, bool want_iface, int shift, std::vector<int> &rpo,
-                     std::vector<int> &cio, std::vector<int> &srco) {
+                     pvec<int> &cio, pvec<int> &srco) {
       std::vector<int> cntr(rows, 0);
       pool.run(rows, [&](long long lo, long long hi) {
         for (int g = int(lo); g < int(hi); g++) {
@@ -502,7 +508,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     for (int g = 0; g < n; g++) P.f_rp[g + 1] = P.f_rp[g] + low_cnt[g] + 1;
     const long long nf = P.f_rp[n];
     P.f_ci.resize(nf); P.f_row.resize(nf); P.f_src.resize(nf); P.f_cdiag.resize(nf);
-    std::vector<int> ecnt(nf, 0);   // Ehat Ehat^T terms per factor entry
+    pvec<int> ecnt(nf);             // Ehat Ehat^T terms per factor entry (all written below)
     // (original column, pa, pb) for row i of an interior block
     auto row_pairs = [&](int i, std::vector<std::array<int, 3>> &pairs) {
       pairs.clear();
@@ -560,7 +566,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     });
   }
   P.nnz_factor = (long long)P.f_ci.size();
-  std::vector<int>().swap(low_ci);
+  pvec<int>().swap(low_ci);
 
   // ---- level records, slices and the triangular-solve layouts
   P.blk_lvl0.assign(p + 2, 0);
@@ -596,11 +602,12 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   }
   // upper (L^T) rows: for device row c, the factor entries (g, c), g != c,
   // in ascending g (flat CSR up_rp / up_q)
-  std::vector<int> up_rp(n + 1, 0), up_q;
+  std::vector<int> up_rp(n + 1, 0);
+  pvec<int> up_q;
   for (int g = 0; g < n; g++)
     for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_rp[P.f_ci[q] + 1]++;
   for (int c = 0; c < n; c++) up_rp[c + 1] += up_rp[c];
-  up_q.assign(up_rp[n], 0);
+  up_q.resize(up_rp[n]);
   {
     std::vector<int> fill(up_rp.begin(), up_rp.end() - 1);
     for (int g = 0; g < n; g++)
@@ -636,10 +643,13 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     P.l_soff[g + 1] = P.l_soff[g] + P.l_sw[g] * kSlice;
     P.u_soff[g + 1] = P.u_soff[g] + P.u_sw[g] * kSlice;
   }
-  P.l_col.assign(P.l_soff[P.nslice], 0);
-  P.u_col.assign(P.u_soff[P.nslice], 0);
-  P.map_l.assign(P.nnz_factor, -1);
-  P.map_u.assign(P.nnz_factor, -1);
+  P.l_col.resize(P.l_soff[P.nslice]);   // every slot is written below
+  P.u_col.resize(P.u_soff[P.nslice]);
+  P.map_l.resize(P.nnz_factor);
+  P.map_u.resize(P.nnz_factor);
+  pool.run(P.nnz_factor, [&](long long lo, long long hi) {   // -1: diagonal entries
+    for (long long e = lo; e < hi; e++) { P.map_l[e] = -1; P.map_u[e] = -1; }
+  });
   pool.run(P.nslice, [&](long long lo, long long hi) {
     for (int g = int(lo); g < int(hi); g++) {
       int b = slice_blk[g];
@@ -687,12 +697,12 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     }
   }
   // inverse diagonal in slice layout, and the capacities of the TMA solve
-  P.row_slot.assign(n, 0);
+  P.row_slot.resize(n);   // the levels cover every row
   for (int l = 0; l < nlev; l++)
     for (int i = 0; i < P.lvl_nrows[l]; i++)
       P.row_slot[P.lvl_row0[l] + i] = (P.lvl_slice0[l] + i / kSlice) * kSlice + i % kSlice;
-  P.l_span.assign(2 * size_t(n), 0);
-  P.u_span.assign(2 * size_t(n), 0);
+  P.l_span.resize(2 * size_t(n));   // written for every row below
+  P.u_span.resize(2 * size_t(n));
   pool.run(n, [&](long long lo, long long hi) {
     for (int g = int(lo); g < int(hi); g++) {
       const int sl = P.row_slot[g] / kSlice, ln = P.row_slot[g] % kSlice;
