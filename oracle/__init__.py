@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, I, I, I, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, I, I, I, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -98,13 +98,16 @@ class Oracle:
     same choice for the interior blocks), scale_diag,
     lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed,
     c_solver (0: C_a factored; 1: Chebyshev with block Jacobi, Sec. 4.3),
-    cheb_steps (5) and cheb_lanczos (20, steps of the spectrum estimate).
+    cheb_steps (5) and cheb_lanczos (20, steps of the spectrum estimate),
+    lowrank_method (0: Lanczos; 1: randomized subspace iteration with
+    ell = k + rand_oversample columns and rand_power power steps).
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
-                 cheb_steps=5, cheb_lanczos=20):
+                 cheb_steps=5, cheb_lanczos=20, lowrank_method=0, rand_oversample=10,
+                 rand_power=2):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -117,7 +120,8 @@ class Oracle:
                           int(factor), int(c_order), int(b_order), int(scale_diag),
                           int(lanczos_max), int(lanczos_check),
                           float(lanczos_eps), int(seed), int(c_solver),
-                          int(cheb_steps), int(cheb_lanczos), ctypes.byref(h))
+                          int(cheb_steps), int(cheb_lanczos), int(lowrank_method),
+                          int(rand_oversample), int(rand_power), ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h

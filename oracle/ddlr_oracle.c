@@ -528,18 +528,79 @@ static int cheb_estimate(oracle *o, uint64_t seed) {
   return (o->cheb_lo > 0.0 && o->cheb_hi >= o->cheb_lo) ? OR_OK : OR_NOT_SPD;
 }
 
+/* Randomized subspace iteration for the low-rank part (the randomized
+ * techniques the conclusion names as a faster alternative to Lanczos; the
+ * method of Halko, Martinsson and Tropp): with the operator Op of the
+ * Lanczos process (H = E^T A0^-1 E, or E^T A0^-2 E for DDLR-2),
+ *   Omega = s x ell test matrix, column c = SplitMix64 stream seed + 2^33 + c
+ *           over the interface nodes in ascending original index;
+ *   Q = orth(Op Omega); q times: Q = orth(Op Q);
+ *   B = Q^T (Op Q), symmetrised; B = Y diag(theta) Y^T, theta descending.
+ * orth = the QR factor with positive diagonal R (classical Gram-Schmidt,
+ * two passes, column by column).  Q is s x ell column-major, Y ell x ell
+ * row-major (Y[j * ell + c] = component j of vector c), as tri_eig gives. */
+static void orth_cols(int s, int ell, double *Q) {
+  double *c = (double *)malloc(sizeof(double) * (size_t)(ell + 1));
+  for (int j = 0; j < ell; j++) {
+    double *w = Q + (size_t)j * s;
+    cgs2(s, j, Q, w, c);
+    double nw = sqrt(dot(s, w, w));
+    for (int r = 0; r < s; r++) w[r] /= nw;
+  }
+  free(c);
+}
+
+static void rand_subspace(oracle *o, int ell, int power, uint64_t seed, double *Q, double *vals, double *Y) {
+  int s = o->s;
+  double *W = (double *)malloc(sizeof(double) * (size_t)s * ell);
+  for (int c = 0; c < ell; c++)
+    for (int r = 0; r < s; r++) Q[(size_t)c * s + r] = sm64_pm1(seed + 0x200000000ULL + (uint64_t)c, (uint64_t)r);
+  for (int c = 0; c < ell; c++) lanczos_op(o, Q + (size_t)c * s, W + (size_t)c * s);
+  memcpy(Q, W, sizeof(double) * (size_t)s * ell);
+  orth_cols(s, ell, Q);
+  for (int it = 0; it < power; it++) {
+    for (int c = 0; c < ell; c++) lanczos_op(o, Q + (size_t)c * s, W + (size_t)c * s);
+    memcpy(Q, W, sizeof(double) * (size_t)s * ell);
+    orth_cols(s, ell, Q);
+  }
+  for (int c = 0; c < ell; c++) lanczos_op(o, Q + (size_t)c * s, W + (size_t)c * s);
+  double *B = (double *)malloc(sizeof(double) * (size_t)ell * ell);
+  double *V = (double *)malloc(sizeof(double) * (size_t)ell * ell);
+  for (int a = 0; a < ell; a++)
+    for (int b = 0; b < ell; b++) B[a * ell + b] = dot(s, Q + (size_t)a * s, W + (size_t)b * s);
+  for (int a = 0; a < ell; a++)
+    for (int b = a + 1; b < ell; b++) {
+      double v = 0.5 * (B[a * ell + b] + B[b * ell + a]);
+      B[a * ell + b] = v; B[b * ell + a] = v;
+    }
+  jacobi_eig(ell, B, V);
+  int *idx = (int *)malloc(sizeof(int) * (size_t)ell);
+  for (int i = 0; i < ell; i++) idx[i] = i;
+  for (int i = 1; i < ell; i++) {          /* stable insertion sort, descending */
+    int v = idx[i], j = i - 1;
+    while (j >= 0 && B[idx[j] * ell + idx[j]] < B[v * ell + v]) { idx[j + 1] = idx[j]; j--; }
+    idx[j + 1] = v;
+  }
+  for (int c = 0; c < ell; c++) {
+    vals[c] = B[idx[c] * ell + idx[c]];
+    for (int r = 0; r < ell; r++) Y[r * ell + c] = V[r * ell + idx[c]];
+  }
+  free(W); free(B); free(V); free(idx);
+}
+
 /* ------------------------------------------------------------ public API */
 int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              const int *part, int p, int variant, int k, double alpha,
              int theta_mode, int factor, int c_order, int b_order, int scale_diag,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
-             void **out) {
+             int lowrank_method, int rand_oversample, int rand_power, void **out) {
   *out = NULL;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
     return OR_INVALID;
   if (c_solver < 0 || c_solver > 1 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)))
     return OR_INVALID;
+  if (lowrank_method < 0 || lowrank_method > 1 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
     if (part[i] < 0 || part[i] >= p) return OR_INVALID;
@@ -803,19 +864,31 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     if (st != OR_OK) { or_free(o); return st; }
   }
 
-  /* low-rank part (Sec. 4.4) */
+  /* low-rank part (Sec. 4.4): Lanczos, or the randomized subspace iteration */
   int mmax = lanczos_max > 0 ? lanczos_max : 5 * k;
   if (mmax > s) mmax = s;
   if (mmax < k) mmax = k;
+  int ell = k + rand_oversample;
+  if (ell > s) ell = s;
+  if (lowrank_method == 1) mmax = ell;
   double *Q = (double *)malloc(sizeof(double) * (size_t)s * (size_t)(mmax + 1));
   double *al = (double *)calloc((size_t)mmax + 1, sizeof(double));
   double *be = (double *)calloc((size_t)mmax + 1, sizeof(double));
   if (!Q || !al || !be) { free(Q); free(al); free(be); or_free(o); return OR_NOMEM; }
-  int mm = lanczos(o, k, mmax, lanczos_check, lanczos_eps, (uint64_t)seed, Q, al, be);
+  int mm;
+  double *Y;
+  if (lowrank_method == 1) {
+    mm = ell;
+    o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
+    Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+    rand_subspace(o, ell, rand_power, (uint64_t)seed, Q, o->ritz, Y);
+  } else {
+    mm = lanczos(o, k, mmax, lanczos_check, lanczos_eps, (uint64_t)seed, Q, al, be);
+    o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
+    Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+    tri_eig(mm, al, be, o->ritz, Y);
+  }
   o->msteps = mm;
-  o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
-  double *Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
-  tri_eig(mm, al, be, o->ritz, Y);
   /* Ritz vectors: (Q_m Y)_k, s x k row-major */
   double *V = (double *)calloc((size_t)s * k, sizeof(double));
   for (int r = 0; r < s; r++)
