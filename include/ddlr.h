@@ -84,11 +84,19 @@ typedef struct {
                               Sec. 5)                                               */
   int cheb_lanczos;        /* c_solver 1: Lanczos steps of the spectrum estimate
                               (default 20)                                          */
+  int lowrank_method;      /* 0 = Lanczos (Sec. 4.4, default); 1 = randomized
+                              subspace iteration (the faster technique the
+                              conclusion names): ell = rank_k + rand_oversample
+                              columns (at most 64, at most s), rand_power power
+                              steps, Rayleigh-Ritz on the ell-dimensional basis   */
+  int rand_oversample;     /* lowrank_method 1: oversampling p (default 10)      */
+  int rand_power;          /* lowrank_method 1: power steps q (default 2)         */
 } ddlr_options;
 
 typedef struct {
   int n, p, s, m, k, variant, precision;
-  int lanczos_steps;       /* m of Sec. 4.4 (steps actually taken)                */
+  int lanczos_steps;       /* m of Sec. 4.4 (steps actually taken); with
+                              lowrank_method 1 the basis size ell                  */
   int ncolors;             /* colours of C_a (c_order 1), else 0                  */
   int levels_interior;     /* max dependency levels of an interior block factor   */
   int levels_c;            /* dependency levels of the C_a factor                 */
@@ -117,7 +125,8 @@ typedef struct {
 
 /* Fills *opt with the defaults named above (variant 1, k 16, alpha 1,
  * theta_mode 1, IC(0), c_order 0, b_order 0, FP64, lanczos 5k/10/1e-4, seed 0,
- * max_nrhs 1, c_solver 0, cheb_steps 5, cheb_lanczos 20).
+ * max_nrhs 1, c_solver 0, cheb_steps 5, cheb_lanczos 20, lowrank_method 0,
+ * rand_oversample 10, rand_power 2).
  * Returns DDLR_ERR_INVALID for a NULL pointer. */
 ddlr_status ddlr_options_default(ddlr_options *opt);
 
@@ -150,7 +159,7 @@ ddlr_status ddlr_refactor(ddlr_handle h, const double *val);
  * k_new.  When neither run is stopped by the convergence test, the result is
  * the one ddlr_setup with rank k_new would give.  The arrays of the old rank
  * stay allocated until ddlr_destroy.  Synchronous.  Errors: INVALID (k_new <=
- * rank_k, k_new > s or > 256), NAN, NOT_SPD, CUDA. */
+ * rank_k, k_new > s or > 256, lowrank_method 1), NAN, NOT_SPD, CUDA. */
 ddlr_status ddlr_increase_rank(ddlr_handle h, int k_new);
 
 /* y = M^-1 x (Algorithm 1 for DDLR-1, eq. Form2a for DDLR-2) for nrhs vectors.

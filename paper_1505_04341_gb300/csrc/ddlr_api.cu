@@ -20,6 +20,7 @@
 #include "ddlr.h"
 #include "ddlr_batch.cuh"
 #include "ddlr_cheb.cuh"
+#include "ddlr_rand.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -155,6 +156,15 @@ struct ddlr_ctx {
   float *cb32[5] = {nullptr};
   double *cz_al = nullptr, *cz_be = nullptr, *cz_vals = nullptr, *cz_Y = nullptr, *cz_work = nullptr,
          *cz_b0 = nullptr;
+  // randomized low-rank build (lowrank_method 1), allocated at first use
+  struct RandWork {
+    bool ready = false;
+    int L = 0;
+    double *Yb = nullptr, *Qb = nullptr, *V = nullptr, *Z = nullptr, *Z2 = nullptr, *part = nullptr, *G = nullptr,
+           *Linv = nullptr, *d = nullptr, *e = nullptr, *Hv = nullptr, *vals = nullptr, *eY = nullptr, *work = nullptr;
+    double *Vk = nullptr, *EV = nullptr, *vc = nullptr, *ev = nullptr, *uc = nullptr, *kp = nullptr, *hw = nullptr;
+    int *rank = nullptr;
+  } rw;
   int cheb_msteps = 0;
   // low-rank data (device order)
   int urows = 0;
@@ -1026,6 +1036,129 @@ const int *pcg_gate(ddlr_ctx *c) {
                                        offsetof(PcgState, done));
 }
 
+void batch_alloc(ddlr_ctx *c, int R);
+template <typename T>
+void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate);
+
+// Randomized subspace iteration for the low-rank part (ddlr_rand.cuh):
+// Omega -> Q = orth(Op Omega), q power steps, B = Q^T Op Q, eigenpairs of B,
+// then U_k / Lambda_k / theta (DDLR-1) or V_k -> U_k = A0^-1 E V_k, H_k
+// (DDLR-2) as after Lanczos.  Op on a block = batched E, A0 solve(s), E^T.
+ddlr_status run_randomized(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int n = P.n, m = P.m, s = P.s, k = c->opt.rank_k;
+  const int L = std::min(k + c->opt.rand_oversample, s);
+  auto &R = c->rw;
+  if (!R.ready) {
+    R.L = L;
+    R.Yb = c->alloc<double>(size_t(s) * L);
+    R.Qb = c->alloc<double>(size_t(s) * L);
+    R.V = c->alloc<double>(size_t(n) * L);
+    R.Z = c->alloc<double>(size_t(n) * L);
+    if (c->opt.variant == 2) R.Z2 = c->alloc<double>(size_t(n) * L);
+    R.part = c->alloc<double>(size_t(kRedGrid) * L * L);
+    R.G = c->alloc<double>(size_t(L) * L);
+    R.Linv = c->alloc<double>(size_t(L) * L);
+    R.d = c->alloc<double>(L);
+    R.e = c->alloc<double>(L);
+    R.Hv = c->alloc<double>(size_t(L) * L);
+    R.vals = c->alloc<double>(L);
+    R.eY = c->alloc<double>(size_t(L) * k);
+    R.work = c->alloc<double>(size_t(5) * L * k);
+    R.rank = c->upload(P.iface_rank);
+    if (c->opt.variant == 2) {
+      R.Vk = c->alloc<double>(size_t(s) * k);
+      R.EV = c->alloc<double>(size_t(n) * k);
+      R.vc = c->alloc<double>(s);
+      R.ev = c->alloc<double>(n);
+      R.uc = c->alloc<double>(n);
+      R.kp = c->alloc<double>(size_t(kRedGrid) * k * k);
+      R.hw = c->alloc<double>(size_t(k) * k + k);
+    }
+    if (c->opt.c_solver == 1) batch_alloc(c, L);   // Chebyshev work blocks of the batched A0 solve
+    R.ready = true;
+  }
+  if (c->bt.chunk_per == 0) c->bt.chunk_per = std::max(1, 256 / L);
+  const double a = c->opt.alpha;
+  const int np = L * L;
+  // Y (s x L) -> W (s x L) = Op Y
+  auto op = [&](const double *Y, double *Wout) {
+    KL(c, "rand_op", c->stream, k_e_block, nblk((long long)n * L), kThreads, 0, m, s, L, c->eh_rp, c->eh_ci,
+       c->eh64, 1.0 / a, a, Y, R.V);
+    a0_solve_mr<double>(c, R.V, R.Z, L, nullptr);
+    const double *Zf = R.Z;
+    if (c->opt.variant == 2) {
+      a0_solve_mr<double>(c, R.Z, R.Z2, L, nullptr);
+      Zf = R.Z2;
+    }
+    KL(c, "rand_op", c->stream, k_et_mr<double>, nblk((long long)s * L), kThreads, 0, s, m, c->eht_rp,
+       c->eht_ci, c->eht64, 1.0 / a, a, Zf, Wout, L, (const int *)nullptr);
+  };
+  auto gram = [&](const double *X, const double *Y) {
+    KL(c, "rand_orth", c->stream, k_gram_partial, kRedGrid, kGramNT, 0, (long long)s, L, X, Y, R.part);
+    KL(c, "rand_orth", c->stream, k_gram_reduce, (np + 255) / 256, 256, 0, kRedGrid, np, R.part, R.G);
+  };
+  // Cholesky QR twice; the orthonormal factor ends in Y's buffer (Q is scratch)
+  auto orth = [&](double *Y, double *Q) {
+    gram(Y, Y);
+    KL(c, "rand_orth", c->stream, k_chol_inv, 1, kRandMaxL, 0, L, R.G, R.Linv, c->dflag + 0);
+    KL(c, "rand_orth", c->stream, k_apply_rinv, nblk(s), kThreads, 0, (long long)s, L, Y, R.Linv, Q);
+    gram(Q, Q);
+    KL(c, "rand_orth", c->stream, k_chol_inv, 1, kRandMaxL, 0, L, R.G, R.Linv, c->dflag + 0);
+    KL(c, "rand_orth", c->stream, k_apply_rinv, nblk(s), kThreads, 0, (long long)s, L, Q, R.Linv, Y);
+  };
+  ck(cudaMemsetAsync(c->dflag, 0, 4 * sizeof(int), c->stream), "memset");
+  KL(c, "rand_op", c->stream, k_rand_omega, nblk((long long)s * L), kThreads, 0, s, L, R.rank, c->opt.seed, R.Qb);
+  op(R.Qb, R.Yb);
+  orth(R.Yb, R.Qb);                       // Q in Yb
+  for (int it = 0; it < c->opt.rand_power; it++) {
+    op(R.Yb, R.Qb);
+    orth(R.Qb, R.Yb);                     // Q in Qb
+    std::swap(R.Yb, R.Qb);                // keep Q in Yb
+  }
+  op(R.Yb, R.Qb);                         // W = Op Q in Qb
+  gram(R.Yb, R.Qb);                       // B = Q^T W in G
+  KL(c, "rand_eig", c->stream, k_sym_tridiag, 1, kRandMaxL, 0, L, R.G, R.d, R.e, R.Hv);
+  KL(c, "rand_eig", c->stream, k_tridiag_values, L, kEigPoints, (2 * L + 2) * sizeof(double), L, R.d, R.e, L,
+     R.vals);
+  KL(c, "rand_eig", c->stream, k_tridiag_vectors, 1, 256, 0, L, R.d, R.e, k, R.vals, R.eY, R.work);
+  KL(c, "rand_eig", c->stream, k_back_transform, 1, 64, 0, L, k, R.Hv, R.eY);
+  int fl[4];
+  read_dev(c, fl, c->dflag, sizeof(fl));
+  if (fl[0]) { c->err = "randomized range basis is rank-deficient (Cholesky QR failed)"; return DDLR_ERR_BREAKDOWN; }
+  c->msteps = L;
+  c->ritz.assign(L, 0.0);
+  read_dev(c, c->ritz.data(), R.vals, sizeof(double) * L);
+  for (double v : c->ritz)
+    if (!std::isfinite(v)) { c->err = "NaN/Inf in the randomized low-rank build"; return DDLR_ERR_NAN; }
+  if (c->opt.variant == 1) {
+    KL(c, "ritz", c->stream, k_rm_gemm, nblk(s), kThreads, 0, (long long)s, L, k, R.Yb, R.eY, c->U64);
+    KL(c, "ritz", c->stream, k_ddlr1_coef, 1, 32, 0, L, k, c->opt.theta_mode, R.vals, c->theta_d, c->inv1mt64,
+       c->coef64, c->dflag + 1);
+    read_dev(c, &c->theta, c->theta_d, sizeof(double));
+  } else {
+    // V_k = Q Y_k; U_k = A0^-1 E V_k; H_k = (I - U_k^T E V_k)^-1
+    KL(c, "ritz", c->stream, k_rm_gemm, nblk(s), kThreads, 0, (long long)s, L, k, R.Yb, R.eY, R.Vk);
+    for (int cc = 0; cc < k; cc++) {
+      KL(c, "ritz", c->stream, k_get_col, nblk(s), kThreads, 0, (long long)s, k, cc, R.Vk, R.vc);
+      KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0, m, s, c->eh_rp, c->eh_ci, c->eh64, 1.0 / a,
+         a, R.vc, (const double *)nullptr, R.ev, (const int *)nullptr);
+      KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, R.ev, R.EV);
+      a0_solve<double>(c, R.ev, R.uc, nullptr);
+      KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, R.uc, c->U64);
+    }
+    KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, R.EV, R.kp);
+    KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, R.kp, R.hw, c->Hk64, c->dflag + 1);
+    c->theta = 0.0;
+  }
+  read_dev(c, fl, c->dflag, sizeof(fl));
+  if (fl[3]) return DDLR_ERR_TIMEOUT;
+  if (fl[2]) return DDLR_ERR_NAN;
+  if (fl[1]) return DDLR_ERR_NOT_SPD;
+  sync(c);
+  return DDLR_OK;
+}
+
 // Chebyshev C_a solve (Sec. 4.3): C_a's values, then the spectrum estimate of
 // D_a^-1 C_a by Lanczos on the pair (C_a, D_a) in the D_a inner product (with
 // p_j = D_a q_j: w = C_a q_j - beta_{j-1} p_{j-1}, alpha_j = q_j^T w,
@@ -1142,7 +1275,7 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
     ddlr_status cs = cheb_setup(c);
     if (cs != DDLR_OK) return cs;
   }
-  ddlr_status st = run_lanczos(c);
+  ddlr_status st = c->opt.lowrank_method == 1 ? run_randomized(c) : run_lanczos(c);
   if (st != DDLR_OK) {
     c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
                                     : "NaN/Inf in the Lanczos process";
@@ -2051,6 +2184,9 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->c_solver = 0;
   o->cheb_steps = 5;
   o->cheb_lanczos = 20;
+  o->lowrank_method = 0;
+  o->rand_oversample = 10;
+  o->rand_power = 2;
   return DDLR_OK;
 }
 
@@ -2067,7 +2203,10 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
       (o.b_order != 0 && o.b_order != 1) || o.rank_k < 1 ||
       o.rank_k > 256 || (o.c_solver != 0 && o.c_solver != 1) ||
       (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
-                           o.cheb_lanczos > 1000))) {
+                           o.cheb_lanczos > 1000)) ||
+      (o.lowrank_method != 0 && o.lowrank_method != 1) ||
+      (o.lowrank_method == 1 && (o.rand_oversample < 0 || o.rand_power < 0 || o.rand_power > 100 ||
+                                 o.rank_k + o.rand_oversample > kRandMaxL))) {
     g_setup_error = "invalid options";
     return DDLR_ERR_INVALID;
   }
@@ -2114,6 +2253,10 @@ ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
   const int k_old = c->opt.rank_k;
   if (k_new <= k_old || k_new > P.s || k_new > 256) {
     c->err = "ddlr_increase_rank: need rank_k < k_new <= min(s, 256)";
+    return DDLR_ERR_INVALID;
+  }
+  if (c->opt.lowrank_method != 0) {
+    c->err = "ddlr_increase_rank continues the Lanczos process: lowrank_method 0 only";
     return DDLR_ERR_INVALID;
   }
   if (!c->lw.ready) { c->err = "ddlr_increase_rank: no Lanczos state"; return DDLR_ERR_INVALID; }

@@ -36,7 +36,8 @@ class ddlr_options(ctypes.Structure):
                 ("lanczos_check", ctypes.c_int), ("lanczos_eps", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("max_nrhs", ctypes.c_int),
                 ("c_solver", ctypes.c_int), ("cheb_steps", ctypes.c_int),
-                ("cheb_lanczos", ctypes.c_int)]
+                ("cheb_lanczos", ctypes.c_int), ("lowrank_method", ctypes.c_int),
+                ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int)]
 
 
 class ddlr_info(ctypes.Structure):
