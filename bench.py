@@ -322,6 +322,18 @@ def run_ours(args):
             c_solve[name]["steps"] = OPTS.get("cheb_steps", 5)
         hc.close()
 
+    # the low-rank build: Lanczos (Sec. 4.4) against the randomized subspace
+    # iteration (ell = k + 10, 2 power steps), setup and solve split
+    lowrank = {}
+    for name, extra in (("lanczos", dict()), ("randomized", dict(lowrank_method=1))):
+        hr = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
+        step(hr, x)
+        su, so = split_once(hr)
+        _, inf_r = hr.pcg(b, x, tol=TOL)
+        lowrank[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3), "total_ms": round(su + so, 3),
+                         "iterations": inf_r[0]["its"], "basis": hr.info()["lanczos_steps"]}
+        hr.close()
+
     # precision line: 128^3 Laplacian, 512 boxes, k = 32 -- FP64 against mixed
     # (FP32 factors and solves, BF16 or FP32 U_k, FP64 flexible CG)
     prec = {}
@@ -332,7 +344,8 @@ def run_ours(args):
         x3 = torch.zeros_like(b3)
         sol = {}
         for name, extra in (("fp64", dict(precision=0)), ("mixed_bf16", dict(precision=1, uk_bf16=1)),
-                            ("mixed_fp32", dict(precision=1, uk_bf16=0))):
+                            ("mixed_fp32", dict(precision=1, uk_bf16=0)),
+                            ("fp64_randomized_lowrank", dict(precision=0, lowrank_method=1))):
             h3 = pkg.DDLR(A3, part3, p3, **dict(OPTS, rank_k=32, **extra))
             h3.refactor()
             h3.pcg(b3, x3, tol=TOL)
@@ -500,6 +513,7 @@ def run_ours(args):
                                             "iterations": [i["its"] for i in inf_nat]},
             "e2e_parts": e2e_parts,
             "c_alpha_solve_factored_vs_chebyshev": c_solve,
+            "lowrank_lanczos_vs_randomized": lowrank,
             "precision_lap3d_128_b8_k32": prec,
             "batching_jump3d_96_cut5_32rhs": batch,
             "serving_lap3d_32_to_128_512req": serving,
