@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, I, I, I, I, I, I, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -100,14 +100,17 @@ class Oracle:
     c_solver (0: C_a factored; 1: Chebyshev with block Jacobi, Sec. 4.3),
     cheb_steps (5) and cheb_lanczos (20, steps of the spectrum estimate),
     lowrank_method (0: Lanczos; 1: randomized subspace iteration with
-    ell = k + rand_oversample columns and rand_power power steps).
+    ell = k + rand_oversample columns and rand_power power steps),
+    c_solver 2 = MR approximate inverse of C_a (Algorithm 2) with mr_iters
+    iterations, at most mr_lfil entries per column of Z and drop tolerance
+    mr_droptol relative to the column norm.
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
                  cheb_steps=5, cheb_lanczos=20, lowrank_method=0, rand_oversample=10,
-                 rand_power=2):
+                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -121,7 +124,8 @@ class Oracle:
                           int(lanczos_max), int(lanczos_check),
                           float(lanczos_eps), int(seed), int(c_solver),
                           int(cheb_steps), int(cheb_lanczos), int(lowrank_method),
-                          int(rand_oversample), int(rand_power), ctypes.byref(h))
+                          int(rand_oversample), int(rand_power), int(mr_iters), int(mr_lfil),
+                          float(mr_droptol), ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h

@@ -28,7 +28,9 @@
  *     preconditioned Chebyshev iterations (c_solver 1) with the block Jacobi
  *     preconditioner D_a (the diagonal blocks of C_a that couple interface
  *     nodes of one subdomain), the spectrum of the pair (C_a, D_a) estimated
- *     by a few Lanczos steps with residual-norm safeguards;
+ *     by a few Lanczos steps with residual-norm safeguards, or by the
+ *     approximate inverse of self-preconditioned MR iterations with
+ *     dual-threshold dropping (c_solver 2, Algorithm 2);
  *   - Sec. 5: preconditioned CG from x0 = 0.
  *
  * Readings where the paper is silent are the same as the CUDA library's and are
@@ -251,6 +253,10 @@ typedef struct {
   double *work2;   /* n scratch */
   /* Sec. 4.3, c_solver 1: bf[p] factors D_a; Ca is the whole C_a */
   int c_solver, cheb_t, cheb_m;
+  int mr_iters, mr_lfil;        /* c_solver 2 */
+  double mr_droptol;
+  int *xcnt, **xrow;            /* X ~ C_a^-1 by columns: rows ascending */
+  double **xval;
   sp Ca;           /* s x s, interface indices (new index - m) */
   double cheb_lo, cheb_hi;
 } oracle;
@@ -301,11 +307,148 @@ static void cheb_solve(oracle *o, const double *y, double *x) {
   free(r); free(z); free(sd); free(cs);
 }
 
+/* solve with C_a by the approximate inverse: z = X y, X by columns */
+static void mr_apply(oracle *o, const double *y, double *z) {
+  for (int i = 0; i < o->s; i++) z[i] = 0.0;
+  for (int j = 0; j < o->s; j++)
+    for (int t = 0; t < o->xcnt[j]; t++) z[o->xrow[j][t]] += o->xval[j][t] * y[j];
+}
+
 /* A0 solve in new order: p local solves with B_{i,a} and one with C_a */
 static void a0_solve(oracle *o, const double *x, double *z) {
   for (int b = 0; b < o->p; b++) block_solve(o, b, x + o->boff[b], z + o->boff[b]);
   if (o->c_solver == 1) cheb_solve(o, x + o->m, z + o->m);
+  else if (o->c_solver == 2) mr_apply(o, x + o->m, z + o->m);
   else block_solve(o, o->p, x + o->m, z + o->m);
+}
+
+/* Self-preconditioned global MR iterations with dual-threshold dropping
+ * (Sec. 4.3, Algorithm 2) for X ~ C_a^-1, column by column:
+ *   X_0 = diag(C_a)^-1;  for each of mr_iters iterations:
+ *   R = I - C_a X,  Z = X R,  drop in Z,  beta = tr(R^T C_a Z) / ||C_a Z||_F^2,
+ *   X = X + beta Z.
+ * Dropping in column z_j: entries with |z_ij| <= mr_droptol ||z_j||_2 go,
+ * then only the mr_lfil largest in magnitude stay (ties: lower row first).
+ * tr(R^T C_a Z) = sum_j r_j . (C_a z_j) and ||C_a Z||_F^2 = sum_j ||C_a z_j||^2.
+ * A zero ||C_a Z|| (R = 0 after dropping) ends the iterations. */
+typedef struct { int i; double v; } ent;
+static int ent_mag_cmp(const void *a, const void *b) {
+  const ent *x = (const ent *)a, *y = (const ent *)b;
+  double ax = fabs(x->v), ay = fabs(y->v);
+  if (ax > ay) return -1;
+  if (ax < ay) return 1;
+  return (x->i > y->i) - (x->i < y->i);
+}
+static int ent_row_cmp(const void *a, const void *b) {
+  const ent *x = (const ent *)a, *y = (const ent *)b;
+  return (x->i > y->i) - (x->i < y->i);
+}
+
+static int mr_build(oracle *o) {
+  int s = o->s;
+  const sp *C = &o->Ca;
+  o->xcnt = (int *)calloc((size_t)s, sizeof(int));
+  o->xrow = (int **)calloc((size_t)s, sizeof(int *));
+  o->xval = (double **)calloc((size_t)s, sizeof(double *));
+  int *zcnt = (int *)calloc((size_t)s, sizeof(int));
+  ent **zc = (ent **)calloc((size_t)s, sizeof(ent *));
+  double *r = (double *)calloc((size_t)s, sizeof(double));
+  double *z = (double *)calloc((size_t)s, sizeof(double));
+  double *w = (double *)calloc((size_t)s, sizeof(double));
+  ent *cand = (ent *)malloc(sizeof(ent) * (size_t)s);
+  if (!o->xcnt || !o->xrow || !o->xval || !zcnt || !zc || !r || !z || !w || !cand) return OR_NOMEM;
+  for (int j = 0; j < s; j++) {
+    double cjj = 0.0;
+    for (int q = C->rp[j]; q < C->rp[j + 1]; q++) if (C->ci[q] == j) cjj = C->va[q];
+    o->xcnt[j] = 1;
+    o->xrow[j] = (int *)malloc(sizeof(int));
+    o->xval[j] = (double *)malloc(sizeof(double));
+    o->xrow[j][0] = j;
+    o->xval[j][0] = 1.0 / cjj;
+  }
+  for (int it = 0; it < o->mr_iters; it++) {
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < s; j++) {
+      /* r_j = e_j - C_a x_j */
+      for (int i = 0; i < s; i++) { r[i] = 0.0; z[i] = 0.0; w[i] = 0.0; }
+      r[j] = 1.0;
+      for (int t = 0; t < o->xcnt[j]; t++) {
+        int i = o->xrow[j][t];
+        for (int q = C->rp[i]; q < C->rp[i + 1]; q++) r[C->ci[q]] -= C->va[q] * o->xval[j][t];
+      }
+      /* z_j = X r_j (self-preconditioned residual) */
+      for (int l = 0; l < s; l++)
+        if (r[l] != 0.0)
+          for (int t = 0; t < o->xcnt[l]; t++) z[o->xrow[l][t]] += o->xval[l][t] * r[l];
+      /* dual-threshold dropping */
+      double nz2 = 0.0;
+      for (int i = 0; i < s; i++) nz2 += z[i] * z[i];
+      double thr = o->mr_droptol * sqrt(nz2);
+      int nc = 0;
+      for (int i = 0; i < s; i++)
+        if (z[i] != 0.0 && fabs(z[i]) > thr) { cand[nc].i = i; cand[nc].v = z[i]; nc++; }
+      qsort(cand, (size_t)nc, sizeof(ent), ent_mag_cmp);
+      if (nc > o->mr_lfil) nc = o->mr_lfil;
+      qsort(cand, (size_t)nc, sizeof(ent), ent_row_cmp);
+      zcnt[j] = nc;
+      zc[j] = (ent *)malloc(sizeof(ent) * (size_t)(nc > 0 ? nc : 1));
+      memcpy(zc[j], cand, sizeof(ent) * (size_t)nc);
+      /* w_j = C_a z_j; the trace and norm terms */
+      for (int t = 0; t < nc; t++) {
+        int i = cand[t].i;
+        for (int q = C->rp[i]; q < C->rp[i + 1]; q++) w[C->ci[q]] += C->va[q] * cand[t].v;
+      }
+      for (int i = 0; i < s; i++) { num += r[i] * w[i]; den += w[i] * w[i]; }
+    }
+    if (!(den > 0.0)) {
+      for (int j = 0; j < s; j++) free(zc[j]);
+      break;
+    }
+    double beta = num / den;
+    /* X = X + beta Z, column by column (rows stay ascending) */
+    for (int j = 0; j < s; j++) {
+      int na = o->xcnt[j], nb = zcnt[j], a = 0, b = 0, t = 0;
+      int *ri = (int *)malloc(sizeof(int) * (size_t)(na + nb));
+      double *rv = (double *)malloc(sizeof(double) * (size_t)(na + nb));
+      while (a < na || b < nb) {
+        if (b >= nb || (a < na && o->xrow[j][a] < zc[j][b].i)) { ri[t] = o->xrow[j][a]; rv[t] = o->xval[j][a]; a++; }
+        else if (a >= na || zc[j][b].i < o->xrow[j][a]) { ri[t] = zc[j][b].i; rv[t] = beta * zc[j][b].v; b++; }
+        else { ri[t] = o->xrow[j][a]; rv[t] = o->xval[j][a] + beta * zc[j][b].v; a++; b++; }
+        t++;
+      }
+      free(o->xrow[j]); free(o->xval[j]); free(zc[j]);
+      o->xrow[j] = ri; o->xval[j] = rv; o->xcnt[j] = t;
+    }
+  }
+  free(zcnt); free(zc); free(r); free(z); free(w); free(cand);
+  /* CG needs a symmetric preconditioner: the solve applies the symmetric
+   * part (X + X^T) / 2 (dropping makes X itself unsymmetric) */
+  long nt = 0;
+  for (int j = 0; j < s; j++) nt += 2 * o->xcnt[j];
+  trip *t = (trip *)malloc(sizeof(trip) * (size_t)(nt > 0 ? nt : 1));
+  long w2 = 0;
+  for (int j = 0; j < s; j++)
+    for (int q = 0; q < o->xcnt[j]; q++) {
+      int i = o->xrow[j][q];
+      double v = 0.5 * o->xval[j][q];
+      t[w2].r = j; t[w2].c = i; t[w2].v = v; w2++;   /* column j, row i */
+      t[w2].r = i; t[w2].c = j; t[w2].v = v; w2++;   /* column i, row j */
+    }
+  sp S;
+  memset(&S, 0, sizeof S);
+  int st = sp_from_trips(&S, s, t, w2);
+  free(t);
+  if (st != OR_OK) return st;
+  for (int j = 0; j < s; j++) {
+    int cnt = S.rp[j + 1] - S.rp[j];
+    free(o->xrow[j]); free(o->xval[j]);
+    o->xrow[j] = (int *)malloc(sizeof(int) * (size_t)(cnt > 0 ? cnt : 1));
+    o->xval[j] = (double *)malloc(sizeof(double) * (size_t)(cnt > 0 ? cnt : 1));
+    o->xcnt[j] = cnt;
+    for (int q = 0; q < cnt; q++) { o->xrow[j][q] = S.ci[S.rp[j] + q]; o->xval[j][q] = S.va[S.rp[j] + q]; }
+  }
+  sp_free(&S);
+  return OR_OK;
 }
 
 /* v = E w = [a^-1 Ehat w ; -a w]  (eq. EF), w of length s, v of length n */
@@ -594,11 +737,13 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              int theta_mode, int factor, int c_order, int b_order, int scale_diag,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
-             int lowrank_method, int rand_oversample, int rand_power, void **out) {
+             int lowrank_method, int rand_oversample, int rand_power, int mr_iters, int mr_lfil,
+             double mr_droptol, void **out) {
   *out = NULL;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
     return OR_INVALID;
-  if (c_solver < 0 || c_solver > 1 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)))
+  if (c_solver < 0 || c_solver > 2 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)) ||
+      (c_solver == 2 && (mr_iters < 0 || mr_lfil < 1 || !(mr_droptol >= 0.0))))
     return OR_INVALID;
   if (lowrank_method < 0 || lowrank_method > 1 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
   for (int i = 0; i < n; i++) {
@@ -623,6 +768,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   o->theta_mode = theta_mode; o->factor = factor; o->c_order = c_order;
   o->scale_diag = scale_diag;
   o->c_solver = c_solver; o->cheb_t = cheb_steps; o->cheb_m = cheb_lanczos;
+  o->mr_iters = mr_iters; o->mr_lfil = mr_lfil; o->mr_droptol = mr_droptol;
   int st = OR_OK;
   long nnz = rowptr[n];
 
@@ -848,7 +994,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
 
   /* Sec. 4.3, c_solver 1: the whole C_a = C + a^2 I for the Chebyshev
    * iteration, and the spectrum estimate of (C_a, D_a) */
-  if (c_solver == 1) {
+  if (c_solver >= 1) {
     long cap = s;
     for (int g = m; g < n; g++) cap += o->Ap.rp[g + 1] - o->Ap.rp[g];
     trip *t = (trip *)malloc(sizeof(trip) * (size_t)cap);
@@ -860,7 +1006,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     }
     st = sp_from_trips(&o->Ca, s, t, nt);
     free(t);
-    if (st == OR_OK) st = cheb_estimate(o, (uint64_t)seed);
+    if (st == OR_OK) st = c_solver == 1 ? cheb_estimate(o, (uint64_t)seed) : mr_build(o);
     if (st != OR_OK) { or_free(o); return st; }
   }
 
@@ -964,6 +1110,8 @@ void or_free(oracle *o) {
   if (!o) return;
   free(o->perm); free(o->iperm); free(o->boff); free(o->dsc);
   sp_free(&o->A); sp_free(&o->Ap); sp_free(&o->Eh); sp_free(&o->EhT); sp_free(&o->Ca);
+  if (o->xrow) for (int j = 0; j < o->s; j++) { free(o->xrow[j]); free(o->xval[j]); }
+  free(o->xrow); free(o->xval); free(o->xcnt);
   if (o->bf) {
     for (int b = 0; b <= o->p; b++) {
       free(o->bf[b].ord); free(o->bf[b].D); sp_free(&o->bf[b].L);
