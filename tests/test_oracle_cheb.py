@@ -151,6 +151,6 @@ def test_default_chebyshev_preconditions_pcg():
 def test_chebyshev_rejects_bad_options():
     A = W.laplacian((8, 8))
     part, p = W.box_partition((8, 8), (2, 2))
-    for kw in (dict(c_solver=2), dict(c_solver=1, cheb_steps=0), dict(c_solver=1, cheb_lanczos=0)):
+    for kw in (dict(c_solver=3), dict(c_solver=1, cheb_steps=0), dict(c_solver=1, cheb_lanczos=0)):
         with pytest.raises(O.OracleError, match="INVALID"):
             O.Oracle(A, part, p, k=2, **kw)
