@@ -79,7 +79,10 @@ typedef struct {
                               iterations with the block Jacobi preconditioner D_a
                               (the couplings of C_a inside one subdomain, factored
                               like a local block) on a spectrum interval estimated
-                              by Lanczos on (C_a, D_a)                             */
+                              by Lanczos on (C_a, D_a); 2 = product with the
+                              symmetric part of an approximate inverse X of C_a
+                              from self-preconditioned MR iterations with
+                              dual-threshold dropping (Algorithm 2)               */
   int cheb_steps;          /* c_solver 1: Chebyshev steps per solve (default 5,
                               Sec. 5)                                               */
   int cheb_lanczos;        /* c_solver 1: Lanczos steps of the spectrum estimate
@@ -91,6 +94,11 @@ typedef struct {
                               steps, Rayleigh-Ritz on the ell-dimensional basis   */
   int rand_oversample;     /* lowrank_method 1: oversampling p (default 10)      */
   int rand_power;          /* lowrank_method 1: power steps q (default 2)         */
+  int mr_iters;            /* c_solver 2: MR iterations (default 3)              */
+  int mr_lfil;             /* c_solver 2: entries kept per column of Z (default 8;
+                              1 + mr_iters * mr_lfil <= 32)                        */
+  double mr_droptol;       /* c_solver 2: drop tolerance relative to the column
+                              norm of Z (default 1e-3)                             */
 } ddlr_options;
 
 typedef struct {
@@ -126,7 +134,7 @@ typedef struct {
 /* Fills *opt with the defaults named above (variant 1, k 16, alpha 1,
  * theta_mode 1, IC(0), c_order 0, b_order 0, FP64, lanczos 5k/10/1e-4, seed 0,
  * max_nrhs 1, c_solver 0, cheb_steps 5, cheb_lanczos 20, lowrank_method 0,
- * rand_oversample 10, rand_power 2).
+ * rand_oversample 10, rand_power 2, mr_iters 3, mr_lfil 8, mr_droptol 1e-3).
  * Returns DDLR_ERR_INVALID for a NULL pointer. */
 ddlr_status ddlr_options_default(ddlr_options *opt);
 

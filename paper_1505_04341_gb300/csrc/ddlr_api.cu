@@ -21,6 +21,7 @@
 #include "ddlr_batch.cuh"
 #include "ddlr_cheb.cuh"
 #include "ddlr_rand.cuh"
+#include "ddlr_mr.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -166,6 +167,16 @@ struct ddlr_ctx {
     int *rank = nullptr;
   } rw;
   int cheb_msteps = 0;
+  // approximate inverse of C_a (c_solver 2): columns of X during the MR
+  // iterations, then the symmetric part as row CSR (ptr, distinct counts)
+  struct MrWork {
+    int *xcnt = nullptr, *xrow = nullptr, *zcnt = nullptr, *zrow = nullptr;
+    double *xval = nullptr, *zval = nullptr, *num = nullptr, *den = nullptr, *beta = nullptr;
+    int *rcnt = nullptr, *ptr = nullptr, *cursor = nullptr, *col = nullptr, *ucnt = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;
+    long long nnz = 0;       // distinct entries of the symmetric part
+  } mr;
   // low-rank data (device order)
   int urows = 0;
   double *U64 = nullptr, *coef64 = nullptr, *Hk64 = nullptr, *theta_d = nullptr, *inv1mt64 = nullptr;
@@ -458,6 +469,17 @@ template <> struct ChebP<float> {
   static float *buf(ddlr_ctx *c, int R, int i) { return R == 1 ? c->cb32[i] : c->bt.cb32[i]; }
 };
 
+// z_C = Xs x_C by the approximate inverse (c_solver 2)
+template <typename T> const T *mr_vals(ddlr_ctx *c);
+template <> const double *mr_vals<double>(ddlr_ctx *c) { return c->mr.val; }
+template <> const float *mr_vals<float>(ddlr_ctx *c) { return c->mr.val32; }
+template <typename T>
+void mr_apply_c(ddlr_ctx *c, cudaStream_t st, const T *x, T *z, int R, const int *gate) {
+  const int s = c->P.s, m = c->P.m;
+  KL(c, "mr_apply", st, k_mr_apply<T>, nblk((long long)s * R), kThreads, 0, s, m, R, c->mr.ptr, c->mr.ucnt,
+     c->mr.col, mr_vals<T>(c), x, z, gate);
+}
+
 // z = D_a^-1 x on the interface rows (the C_a block's levels alone; R
 // right-hand sides row-major)
 template <typename T>
@@ -496,6 +518,7 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
     if (c->lv_desc) desc_sweeps<T>(c, c->stream, "sptrsv_levels", lv, uv, di, x, z, gate);
     else chunk_sweeps<T>(c, c->stream, P.ch_all_ptr, "sptrsv_levels", lv, uv, di, x, z, gate);
     if (cheb) cheb_tail<T>(c, c->stream, x, z, 1, gate);
+    else if (c->opt.c_solver == 2) mr_apply_c<T>(c, c->stream, x, z, 1, gate);
     return;
   }
   ck(cudaEventRecord(c->ev_fork, c->stream), "event");
@@ -517,6 +540,7 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   }
   chunk_sweeps<T>(c, c->stream2, P.ch_c_ptr, "sptrsv_c", lv, uv, di, x, z, gate);
   if (cheb) cheb_tail<T>(c, c->stream2, x, z, 1, gate);
+  else if (c->opt.c_solver == 2) mr_apply_c<T>(c, c->stream2, x, z, 1, gate);
   ck(cudaEventRecord(c->ev_join, c->stream2), "event");
   ck(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "wait");
 }
@@ -1167,16 +1191,60 @@ ddlr_status run_randomized(ddlr_ctx *c) {
 // 1e-14 max |alpha|); then the Ritz values and vectors of T_m and the
 // widened interval with its coefficient table (ddlr_cheb.cuh).  Every step
 // runs on the device; the host reads beta_j only to decide the early stop.
-ddlr_status cheb_setup(ddlr_ctx *c) {
+// C_a = C + a^2 I values over the interface rows (from the resident, possibly
+// scaled, values)
+void cc_values(ddlr_ctx *c) {
   const Plan &P = c->P;
-  const int s = P.s, m = P.m, t = c->opt.cheb_steps, me = c->opt.cheb_lanczos;
   const long long ncc = (long long)P.cc_ci.size();
   const double a = c->opt.alpha;
   KL(c, "setup", c->stream, k_gather<double>, nblk(ncc), kThreads, 0, ncc, c->cc_src, c->vals, c->cc64);
-  KL(c, "setup", c->stream, k_cc_add_diag, nblk(s), kThreads, 0, s, c->cc_diag, a * a, c->cc64);
-  if (c->opt.precision == 1)
+  KL(c, "setup", c->stream, k_cc_add_diag, nblk(P.s), kThreads, 0, P.s, c->cc_diag, a * a, c->cc64);
+  if (c->opt.precision == 1 && c->cc32)
     KL(c, "setup", c->stream, (k_cast<float, double>), nblk(ncc), kThreads, 0, ncc, c->cc64, c->cc32,
        (const int *)nullptr);
+}
+
+// approximate inverse of C_a by MR iterations (ddlr_mr.cuh), then its
+// symmetric part as row CSR for the solve
+ddlr_status mr_setup(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int s = P.s;
+  auto &M = c->mr;
+  cc_values(c);
+  const MrX X{M.xcnt, M.xrow, M.xval};
+  KL(c, "setup", c->stream, k_mr_init, nblk(s), kThreads, 0, s, c->cc_diag, c->cc64, X);
+  for (int it = 0; it < c->opt.mr_iters; it++) {
+    KL(c, "mr", c->stream, k_mr_column, nblk(s, 128), 128, 0, s, c->cc_rp, c->cc_ci, c->cc64, X, c->opt.mr_lfil,
+       c->opt.mr_droptol, M.zcnt, M.zrow, M.zval, M.num, M.den);
+    KL(c, "mr", c->stream, k_mr_beta, 1, 256, 0, s, M.num, M.den, M.beta);
+    KL(c, "mr", c->stream, k_mr_update, nblk(s), kThreads, 0, s, X, M.zcnt, M.zrow, M.zval, M.beta);
+  }
+  ck(cudaMemsetAsync(M.rcnt, 0, sizeof(int) * s, c->stream), "memset");
+  ck(cudaMemsetAsync(M.cursor, 0, sizeof(int) * s, c->stream), "memset");
+  KL(c, "mr", c->stream, k_mr_sym_count, nblk(s), kThreads, 0, s, X, M.rcnt);
+  KL(c, "mr", c->stream, k_mr_scan, 1, 1024, 0, s, M.rcnt, M.ptr);
+  KL(c, "mr", c->stream, k_mr_sym_fill, nblk(s), kThreads, 0, s, X, M.ptr, M.cursor, M.col, M.val);
+  KL(c, "mr", c->stream, k_mr_sym_sort, nblk(s), kThreads, 0, s, M.ptr, M.col, M.val, M.ucnt);
+  if (M.val32) {
+    int tot = 0;
+    read_dev(c, &tot, M.ptr + s, sizeof(int));
+    KL(c, "mr", c->stream, (k_cast<float, double>), nblk(tot), kThreads, 0, (long long)tot, M.val, M.val32,
+       (const int *)nullptr);
+  }
+  std::vector<int> u(s);
+  read_dev(c, u.data(), M.ucnt, sizeof(int) * s);
+  M.nnz = 0;
+  for (int v : u) M.nnz += v;
+  double b = 0;
+  read_dev(c, &b, M.beta, sizeof(double));
+  if (!std::isfinite(b)) { c->err = "NaN/Inf in the MR approximate inverse"; return DDLR_ERR_NAN; }
+  return DDLR_OK;
+}
+
+ddlr_status cheb_setup(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int s = P.s, m = P.m, t = c->opt.cheb_steps, me = c->opt.cheb_lanczos;
+  cc_values(c);
   double *r = c->w64[0], *z = c->w64[1], *q = c->w64[2], *pv = c->w64[3], *pp = c->w64[4], *w = c->w64[5];
   const double *lv = c->l64, *uv = c->u64, *di = c->dinv64;
   KL(c, "setup", c->stream, k_cheb_start, nblk(s), kThreads, 0, s, m, c->cz_rank, c->opt.seed, r);
@@ -1274,6 +1342,9 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   if (c->opt.c_solver == 1) {
     ddlr_status cs = cheb_setup(c);
     if (cs != DDLR_OK) return cs;
+  } else if (c->opt.c_solver == 2) {
+    ddlr_status cs = mr_setup(c);
+    if (cs != DDLR_OK) return cs;
   }
   ddlr_status st = c->opt.lowrank_method == 1 ? run_randomized(c) : run_lanczos(c);
   if (st != DDLR_OK) {
@@ -1307,7 +1378,7 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   if (env && env[0] == '0') return;
   // the persistent kernels solve with the factored C_a only; the Chebyshev
   // C_a solve runs in the kernel-per-phase path
-  if (c->opt.c_solver == 1) return;
+  if (c->opt.c_solver != 0) return;
   const bool force = env && env[0] == '1';
   const int nL = int(P.ch_all_ptr.size()) - 1;
   if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
@@ -1543,6 +1614,21 @@ void allocate(ddlr_ctx *c) {
     c->inv1mt32 = c->alloc<float>(1);
     for (int i = 0; i < 8; i++) c->w32[i] = c->alloc<float>(n);
     c->part32 = c->alloc<float>(size_t(kRedGrid) * (k + 2));
+  }
+  if (c->opt.c_solver == 2) {
+    const int s = P.s;
+    c->cc_rp = c->upload(P.cc_rp); c->cc_ci = c->upload(P.cc_ci);
+    c->cc_src = c->upload(P.cc_src); c->cc_diag = c->upload(P.cc_diag);
+    c->cc64 = c->alloc<double>(P.cc_ci.size());
+    auto &M = c->mr;
+    const size_t cap = size_t(s) * kMrCap;
+    M.xcnt = c->alloc<int>(s); M.xrow = c->alloc<int>(cap); M.xval = c->alloc<double>(cap);
+    M.zcnt = c->alloc<int>(s); M.zrow = c->alloc<int>(cap); M.zval = c->alloc<double>(cap);
+    M.num = c->alloc<double>(s); M.den = c->alloc<double>(s); M.beta = c->alloc<double>(1);
+    M.rcnt = c->alloc<int>(s); M.ptr = c->alloc<int>(size_t(s) + 1); M.cursor = c->alloc<int>(s);
+    M.ucnt = c->alloc<int>(s);
+    M.col = c->alloc<int>(2 * cap); M.val = c->alloc<double>(2 * cap);
+    if (c->opt.precision == 1) M.val32 = c->alloc<float>(2 * cap);
   }
   if (c->opt.c_solver == 1) {
     const int t = c->opt.cheb_steps, me = c->opt.cheb_lanczos;
@@ -1829,6 +1915,7 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
     for (int L = nL - 2; L >= 0; L--) launch(L, 1);
   }
   if (c->opt.c_solver == 1) cheb_tail<T>(c, c->stream, X, Z, R, gate);
+  else if (c->opt.c_solver == 2) mr_apply_c<T>(c, c->stream, X, Z, R, gate);
 }
 
 template <typename T>
@@ -2187,6 +2274,9 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->lowrank_method = 0;
   o->rand_oversample = 10;
   o->rand_power = 2;
+  o->mr_iters = 3;
+  o->mr_lfil = 8;
+  o->mr_droptol = 1e-3;
   return DDLR_OK;
 }
 
@@ -2201,7 +2291,9 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
   if ((o.variant != 1 && o.variant != 2) || !(o.alpha > 0) || (o.precision != 0 && o.precision != 1) ||
       (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) ||
       (o.b_order != 0 && o.b_order != 1) || o.rank_k < 1 ||
-      o.rank_k > 256 || (o.c_solver != 0 && o.c_solver != 1) ||
+      o.rank_k > 256 || o.c_solver < 0 || o.c_solver > 2 ||
+      (o.c_solver == 2 && (o.mr_iters < 0 || o.mr_lfil < 1 || o.mr_lfil >= kMrCap ||
+                           1 + (long long)o.mr_iters * o.mr_lfil > kMrCap || !(o.mr_droptol >= 0.0))) ||
       (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
                            o.cheb_lanczos > 1000)) ||
       (o.lowrank_method != 0 && o.lowrank_method != 1) ||
@@ -2219,6 +2311,17 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
     std::string err;
     ddlr_status s1 = build_plan(n, rowptr, colind, val, part, p, c->opt, c->P, err);
     if (s1 != DDLR_OK) { c->err = err; return s1; }
+    if (c->opt.c_solver == 2) {
+      // the per-column work of the MR iterations holds r_j and C_a z_j in
+      // fixed local arrays: rows of C_a times the column capacity must fit
+      int maxc = 0;
+      for (int i = 0; i < c->P.s; i++) maxc = std::max(maxc, c->P.cc_rp[i + 1] - c->P.cc_rp[i]);
+      const long long cap = 1 + (long long)c->opt.mr_iters * c->opt.mr_lfil;
+      if (cap * maxc + 1 > kMrCand || (long long)c->opt.mr_lfil * maxc > kMrCand) {
+        c->err = "c_solver 2: (1 + mr_iters * mr_lfil) x the longest row of C_a exceeds 256";
+        return DDLR_ERR_INVALID;
+      }
+    }
     c->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     ck(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking), "cudaStreamCreate");
     ck(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "cudaStreamCreate");

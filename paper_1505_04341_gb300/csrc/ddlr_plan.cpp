@@ -242,8 +242,11 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       for (int q = rp[i]; q < rp[i + 1]; q++) {
         const int j = ci[q];
         // Chebyshev mode (Sec. 4.3): block p is the block Jacobi matrix D_a,
-        // the couplings of C_a between interface nodes of one subdomain
-        if (j != i && blk_of[j] == b && (b < p || opt.c_solver != 1 || part[j] == part[i]))
+        // the couplings of C_a between interface nodes of one subdomain; with
+        // the approximate inverse (c_solver 2) block p is left diagonal (the
+        // A0 sweeps' C_a rows are then replaced by the product with X)
+        if (j != i && blk_of[j] == b &&
+            (b < p || opt.c_solver == 0 || (opt.c_solver == 1 && part[j] == part[i])))
           aci.push_back(loc[j]);
         if (b < p && iface[j]) {
           for (int q2 = rp[j]; q2 < rp[j + 1]; q2++) {
@@ -468,8 +471,9 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   }
   P.nnz_ehat = (long long)P.eh_ci.size();
 
-  // ---- C_a = C + a^2 I as CSR over the interface rows (Chebyshev mode)
-  if (opt.c_solver == 1) {
+  // ---- C_a = C + a^2 I as CSR over the interface rows (Chebyshev and
+  // approximate-inverse modes)
+  if (opt.c_solver >= 1) {
     std::vector<int> cntr(s, 0);
     pool.run(s, [&](long long lo, long long hi) {
       for (int g = int(lo); g < int(hi); g++) {

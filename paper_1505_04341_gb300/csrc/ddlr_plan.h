@@ -57,7 +57,7 @@ struct Plan {
   // Ehat^T rows (interface rows, s) -> interior row (device index < m)
   std::vector<int> eht_rp;
   pvec<int> eht_ci, eht_src;
-  // C_a over the interface rows (Chebyshev mode only): columns = device
+  // C_a over the interface rows (c_solver 1 and 2 only): columns = device
   // index - m, ascending; value source in the original arrays; the position
   // of each row's diagonal (a^2 is added there)
   std::vector<int> cc_rp;

@@ -37,7 +37,8 @@ class ddlr_options(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("max_nrhs", ctypes.c_int),
                 ("c_solver", ctypes.c_int), ("cheb_steps", ctypes.c_int),
                 ("cheb_lanczos", ctypes.c_int), ("lowrank_method", ctypes.c_int),
-                ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int)]
+                ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int),
+                ("mr_iters", ctypes.c_int), ("mr_lfil", ctypes.c_int), ("mr_droptol", ctypes.c_double)]
 
 
 class ddlr_info(ctypes.Structure):

@@ -176,7 +176,7 @@ def test_mixed_precision_and_batched_solve():
 def test_bad_chebyshev_options_and_bounds():
     A = W.laplacian((16, 16))
     part, p = W.box_partition((16, 16), (2, 2))
-    for kw in (dict(c_solver=2), dict(c_solver=1, cheb_steps=0), dict(c_solver=1, cheb_steps=65),
+    for kw in (dict(c_solver=3), dict(c_solver=1, cheb_steps=0), dict(c_solver=1, cheb_steps=65),
                dict(c_solver=1, cheb_lanczos=0)):
         with pytest.raises(pkg.DdlrError, match="INVALID"):
             pkg.DDLR(A, part, p, rank_k=4, **kw)
