@@ -303,8 +303,10 @@ def run_ours(args):
     c_solve = {}
     for name, extra in (("factored_natural", dict(b_order=0, c_order=0)),
                         ("chebyshev_natural", dict(b_order=0, c_order=0, c_solver=1)),
+                        ("mr_inverse_natural", dict(b_order=0, c_order=0, c_solver=2)),
                         ("factored_multicolour", dict()),
-                        ("chebyshev_multicolour", dict(c_solver=1))):
+                        ("chebyshev_multicolour", dict(c_solver=1)),
+                        ("mr_inverse_multicolour", dict(c_solver=2))):
         hc = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
         step(hc, x)
         ms_c, inf_c = timed_steps(hc, 2)
@@ -317,7 +319,7 @@ def run_ours(args):
                          "apply_ms": round(a_ms, 4), "a0_solve_ms": round(z_ms, 4),
                          "a0_algorithmic_GBps": round(z_gbs, 1), "levels_c": ic["levels_c"],
                          "persistent": ic["persistent"]}
-        if extra.get("c_solver"):
+        if extra.get("c_solver") == 1:
             c_solve[name]["interval"] = [ic["cheb_lo"], ic["cheb_hi"]]
             c_solve[name]["steps"] = OPTS.get("cheb_steps", 5)
         hc.close()
@@ -512,7 +514,7 @@ def run_ours(args):
             "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
                                             "iterations": [i["its"] for i in inf_nat]},
             "e2e_parts": e2e_parts,
-            "c_alpha_solve_factored_vs_chebyshev": c_solve,
+            "c_alpha_solve_factored_chebyshev_mr": c_solve,
             "lowrank_lanczos_vs_randomized": lowrank,
             "precision_lap3d_128_b8_k32": prec,
             "batching_jump3d_96_cut5_32rhs": batch,

@@ -2801,7 +2801,10 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
     const double ccb = double(P.cc_ci.size()) * (v + 4.0) + 4.0 * s;
     cheb_k = t == 1 ? 2.0 * s * v : (ccb + 5.0 * s * v) + (t - 2) * (ccb + 7.0 * s * v) + 4.0 * s * v;
   }
-  const double a0 = blocks + cblk + (c->opt.c_solver == 1 ? (t - 1) * cblk + cheb_k : 0.0);
+  // approximate inverse (c_solver 2): the C_a block's rows are diagonal in
+  // the sweeps, then one row-wise product with the symmetric part of X
+  const double mr_k = c->opt.c_solver == 2 ? double(c->mr.nnz) * (v + 4.0) + 8.0 * s + 2.0 * s * v : 0.0;
+  const double a0 = blocks + cblk + (c->opt.c_solver == 1 ? (t - 1) * cblk + cheb_k : 0.0) + mr_k;
   const double et = ne * (v + 4.0) + 4.0 * s + 2.0 * s * v;
   const double urows = c->urows;
   const double utx = urows * k * ub + urows * v;
@@ -2824,6 +2827,7 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "sptrsv_levels") b = (blocks + cblk) / sweeps(std::max(P.levels_interior, P.levels_c));
       else if (f == "sptrsv_c" || f == "cheb_dsolve") b = cblk / clev;
       else if (f == "cheb") b = cheb_k / t;
+      else if (f == "mr_apply") b = mr_k;
       else if (f == "et") b = et;
       else if (f == "utx") b = utx;
       else if (f == "w_rhs") b = wr;
