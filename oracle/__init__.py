@@ -100,7 +100,8 @@ class Oracle:
     c_solver (0: C_a factored; 1: Chebyshev with block Jacobi, Sec. 4.3),
     cheb_steps (5) and cheb_lanczos (20, steps of the spectrum estimate),
     lowrank_method (0: Lanczos; 1: randomized subspace iteration with
-    ell = k + rand_oversample columns and rand_power power steps),
+    ell = k + rand_oversample columns and rand_power power steps; 2: Lanczos
+    bidiagonalisation of A0^-1 E, DDLR-2 only),
     c_solver 2 = MR approximate inverse of C_a (Algorithm 2) with mr_iters
     iterations, at most mr_lfil entries per column of Z and drop tolerance
     mr_droptol relative to the column norm.

@@ -693,6 +693,72 @@ static void orth_cols(int s, int ell, double *Q) {
   free(c);
 }
 
+/* Lanczos (Golub-Kahan) bidiagonalisation of K = A0^-1 E (n x s) for DDLR-2
+ * (Sec. 4.4, the alternative that yields U_k and V_k together):
+ *   v_1 = the Lanczos start vector;  for j = 1, 2, ...:
+ *   u = K v_j - beta_{j-1} u_{j-1},  alpha_j = ||u||,  u_j = u / alpha_j;
+ *   v = K^T u_j - alpha_j v_j,       beta_j = ||v||,   v_{j+1} = v / beta_j;
+ * with both sequences fully reorthogonalised (two classical Gram-Schmidt
+ * passes).  K V_m = U_m B_m with B_m upper bidiagonal (alpha on the diagonal,
+ * beta above it), so B_m^T B_m (diagonal alpha_j^2 + beta_{j-1}^2, off-
+ * diagonal alpha_j beta_j) is the tridiagonal matrix Lanczos on
+ * K^T K = E^T A0^-2 E would give from the same start.  The convergence test
+ * of eq. converge runs on its eigenvalues; a beta_j or alpha_j at or below
+ * 1e-12 of the largest seen ends the process (invariant subspace).  V is
+ * s x (mmax+1) and U n x mmax, column-major; td / te receive B_m^T B_m. */
+static int lbd(oracle *o, int k, int mmax, int check, double eps, uint64_t seed, double *V, double *U,
+               double *td, double *te) {
+  int s = o->s, n = o->n;
+  double *al = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  double *be = (double *)calloc((size_t)mmax + 1, sizeof(double));
+  double *u = (double *)malloc(sizeof(double) * (size_t)n);
+  double *t = (double *)malloc(sizeof(double) * (size_t)n);
+  double *v = (double *)malloc(sizeof(double) * (size_t)s);
+  double *c = (double *)malloc(sizeof(double) * (size_t)(mmax + 2));
+  for (int r = 0; r < s; r++) V[r] = sm64_pm1(seed, (uint64_t)r);
+  double nv = sqrt(dot(s, V, V));
+  for (int r = 0; r < s; r++) V[r] /= nv;
+  double scale = 0.0;
+  int m = 0;
+  for (int j = 0; j < mmax; j++) {
+    double *vj = V + (size_t)j * s;
+    e_mult(o, vj, t);                         /* u = K v_j - beta_{j-1} u_{j-1} */
+    a0_solve(o, t, u);
+    if (j > 0) for (int r = 0; r < n; r++) u[r] -= be[j - 1] * U[(size_t)(j - 1) * n + r];
+    cgs2(n, j, U, u, c);
+    al[j] = sqrt(dot(n, u, u));
+    if (al[j] > scale) scale = al[j];
+    m = j + 1;
+    if (!(al[j] > 1e-12 * scale)) { m = j; break; }
+    for (int r = 0; r < n; r++) U[(size_t)j * n + r] = u[r] / al[j];
+    a0_solve(o, U + (size_t)j * n, t);        /* v = K^T u_j - alpha_j v_j */
+    et_mult(o, t, v);
+    for (int r = 0; r < s; r++) v[r] -= al[j] * vj[r];
+    cgs2(s, j + 1, V, v, c);
+    be[j] = sqrt(dot(s, v, v));
+    if (be[j] > scale) scale = be[j];
+    for (int i = 0; i < m; i++) {
+      td[i] = al[i] * al[i] + (i > 0 ? be[i - 1] * be[i - 1] : 0.0);
+      te[i] = al[i] * be[i];
+    }
+    if (check > 0 && m % check == 0 && m >= k + 1) {
+      double sig = topk_sum(m, td, te, k);
+      double spv = topk_sum(m - 1, td, te, k);
+      if (fabs(sig - spv) < eps * fabs(spv)) break;
+    }
+    if (m == mmax || !(be[j] > 1e-12 * scale)) break;
+    for (int r = 0; r < s; r++) V[(size_t)(j + 1) * s + r] = v[r] / be[j];
+  }
+  for (int i = 0; i < m; i++) {
+    td[i] = al[i] * al[i] + (i > 0 ? be[i - 1] * be[i - 1] : 0.0);
+    te[i] = al[i] * be[i];
+  }
+  /* B_m itself, for U_k = U_m (B_m Y_k): al and be kept behind td / te */
+  for (int i = 0; i < m; i++) { td[mmax + 1 + i] = al[i]; te[mmax + 1 + i] = be[i]; }
+  free(al); free(be); free(u); free(t); free(v); free(c);
+  return m;
+}
+
 static void rand_subspace(oracle *o, int ell, int power, uint64_t seed, double *Q, double *vals, double *Y) {
   int s = o->s;
   double *W = (double *)malloc(sizeof(double) * (size_t)s * ell);
@@ -745,7 +811,8 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   if (c_solver < 0 || c_solver > 2 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)) ||
       (c_solver == 2 && (mr_iters < 0 || mr_lfil < 1 || !(mr_droptol >= 0.0))))
     return OR_INVALID;
-  if (lowrank_method < 0 || lowrank_method > 1 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
+  if (lowrank_method < 0 || lowrank_method > 2 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
+  if (lowrank_method == 2 && variant != 2) return OR_INVALID;   /* bidiagonalisation: DDLR-2 */
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
     if (part[i] < 0 || part[i] >= p) return OR_INVALID;
@@ -1023,7 +1090,16 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   if (!Q || !al || !be) { free(Q); free(al); free(be); or_free(o); return OR_NOMEM; }
   int mm;
   double *Y;
-  if (lowrank_method == 1) {
+  double *Ub = NULL, *tdb = NULL, *teb = NULL;   /* bidiagonalisation: U_m and B_m */
+  if (lowrank_method == 2) {
+    Ub = (double *)malloc(sizeof(double) * (size_t)n * (size_t)mmax);
+    tdb = (double *)calloc(2 * (size_t)mmax + 2, sizeof(double));
+    teb = (double *)calloc(2 * (size_t)mmax + 2, sizeof(double));
+    mm = lbd(o, k, mmax, lanczos_check, lanczos_eps, (uint64_t)seed, Q, Ub, tdb, teb);
+    o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
+    Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
+    tri_eig(mm, tdb, teb, o->ritz, Y);
+  } else if (lowrank_method == 1) {
     mm = ell;
     o->ritz = (double *)malloc(sizeof(double) * (size_t)mm);
     Y = (double *)malloc(sizeof(double) * (size_t)mm * mm);
@@ -1043,7 +1119,8 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
       for (int j = 0; j < mm; j++) acc += Q[(size_t)j * s + r] * Y[j * mm + c];
       V[(size_t)r * k + c] = acc;
     }
-  free(Q); free(al); free(be); free(Y);
+  free(Q); free(al); free(be);
+  if (lowrank_method != 2) { free(Y); Y = NULL; }   /* the bidiagonal tail needs Y */
 
   if (variant == 1) {
     o->urows = s;
@@ -1064,7 +1141,17 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     for (int c = 0; c < k; c++) {
       for (int r = 0; r < s; r++) vc[r] = V[(size_t)r * k + c];
       e_mult(o, vc, ev);
-      a0_solve(o, ev, uc);
+      if (lowrank_method == 2) {
+        /* U_k = K V_k = U_m (B_m Y_k): no further solves with A0 */
+        for (int r = 0; r < n; r++) uc[r] = 0.0;
+        for (int i = 0; i < mm; i++) {
+          double g = tdb[mmax + 1 + i] * Y[(size_t)i * mm + c];
+          if (i + 1 < mm) g += teb[mmax + 1 + i] * Y[(size_t)(i + 1) * mm + c];
+          for (int r = 0; r < n; r++) uc[r] += Ub[(size_t)i * n + r] * g;
+        }
+      } else {
+        a0_solve(o, ev, uc);
+      }
       for (int r = 0; r < n; r++) { EV[(size_t)r * k + c] = ev[r]; o->U[(size_t)r * k + c] = uc[r]; }
     }
     double *K = (double *)calloc((size_t)k * k, sizeof(double));
@@ -1100,6 +1187,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
       free(e);
     }
     free(EV); free(vc); free(ev); free(uc); free(K); free(IK); free(V);
+    free(Y); free(Ub); free(tdb); free(teb);
     if (cst != OR_OK) { or_free(o); return OR_NOT_SPD; }
   }
   *out = o;
