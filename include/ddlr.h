@@ -91,7 +91,10 @@ typedef struct {
                               subspace iteration (the faster technique the
                               conclusion names): ell = rank_k + rand_oversample
                               columns (at most 64, at most s), rand_power power
-                              steps, Rayleigh-Ritz on the ell-dimensional basis   */
+                              steps, Rayleigh-Ritz on the ell-dimensional basis;
+                              2 = Lanczos bidiagonalisation of A0^-1 E (DDLR-2
+                              only, Sec. 4.4): U_k and V_k together, the same
+                              step limit and eq. converge test as Lanczos        */
   int rand_oversample;     /* lowrank_method 1: oversampling p (default 10)      */
   int rand_power;          /* lowrank_method 1: power steps q (default 2)         */
   int mr_iters;            /* c_solver 2: MR iterations (default 3)              */

@@ -22,6 +22,7 @@
 #include "ddlr_cheb.cuh"
 #include "ddlr_rand.cuh"
 #include "ddlr_mr.cuh"
+#include "ddlr_lbd.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -166,6 +167,15 @@ struct ddlr_ctx {
     double *Vk = nullptr, *EV = nullptr, *vc = nullptr, *ev = nullptr, *uc = nullptr, *kp = nullptr, *hw = nullptr;
     int *rank = nullptr;
   } rw;
+  // Lanczos bidiagonalisation (lowrank_method 2), allocated at first use
+  struct LbdWork {
+    bool ready = false;
+    int mmax = 0;
+    double *Vq = nullptr, *Uq = nullptr, *al = nullptr, *be = nullptr, *td = nullptr, *te = nullptr, *t = nullptr,
+           *u = nullptr, *v = nullptr, *cpart = nullptr, *cvec = nullptr, *evals = nullptr, *eY = nullptr,
+           *work = nullptr, *esum = nullptr, *etop = nullptr, *G = nullptr, *Vk = nullptr, *EV = nullptr,
+           *vc = nullptr, *ev = nullptr, *kp = nullptr, *hw = nullptr, *q0 = nullptr;
+  } lb;
   int cheb_msteps = 0;
   // approximate inverse of C_a (c_solver 2): columns of X during the MR
   // iterations, then the symmetric part as row CSR (ptr, distinct counts)
@@ -1064,6 +1074,144 @@ void batch_alloc(ddlr_ctx *c, int R);
 template <typename T>
 void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate);
 
+// Lanczos bidiagonalisation of K = A0^-1 E for DDLR-2 (ddlr_lbd.cuh): the
+// steps run kernel by kernel with the scalars on the device; the host reads
+// alpha_j and beta_j only for the stop decisions (breakdown, step limit, the
+// eq. converge test on B_m^T B_m every lanczos_check steps, as for Lanczos)
+ddlr_status run_lbd(ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int n = P.n, m0 = P.m, s = P.s, k = c->opt.rank_k;
+  int mmax = c->opt.lanczos_max > 0 ? c->opt.lanczos_max : 5 * k;
+  mmax = std::max(std::min(mmax, s), k);
+  const int check = c->opt.lanczos_check;
+  const double eps = c->opt.lanczos_eps, a = c->opt.alpha;
+  auto &B = c->lb;
+  if (!B.ready) {
+    B.mmax = mmax;
+    B.Vq = c->alloc<double>(size_t(s) * (mmax + 1));
+    B.Uq = c->alloc<double>(size_t(n) * mmax);
+    B.al = c->alloc<double>(mmax + 1); B.be = c->alloc<double>(mmax + 1);
+    B.td = c->alloc<double>(mmax + 1); B.te = c->alloc<double>(mmax + 1);
+    B.t = c->alloc<double>(n); B.u = c->alloc<double>(n); B.v = c->alloc<double>(s);
+    B.cpart = c->alloc<double>(size_t(kRedGrid) * (mmax + 2));
+    B.cvec = c->alloc<double>(mmax + 2);
+    B.evals = c->alloc<double>(mmax);
+    B.eY = c->alloc<double>(size_t(mmax) * k);
+    B.work = c->alloc<double>(size_t(5) * mmax * k);
+    B.esum = c->alloc<double>(2);
+    B.etop = c->alloc<double>(2 * size_t(k));
+    B.G = c->alloc<double>(size_t(mmax) * k);
+    B.Vk = c->alloc<double>(size_t(s) * k);
+    B.EV = c->alloc<double>(size_t(n) * k);
+    B.vc = c->alloc<double>(s); B.ev = c->alloc<double>(n);
+    B.kp = c->alloc<double>(size_t(kRedGrid) * k * k);
+    B.hw = c->alloc<double>(size_t(k) * k + k);
+    // start vector: the Lanczos one (SplitMix64 stream seed over the
+    // interface nodes in ascending original index, normalised)
+    const auto &rank = P.iface_rank;
+    std::vector<double> byrank(s), hv(s);
+    double nn = 0;
+    for (int r = 0; r < s; r++) { byrank[r] = sm64_pm1(c->opt.seed, (uint64_t)r); nn += byrank[r] * byrank[r]; }
+    nn = std::sqrt(nn);
+    for (int j = 0; j < s; j++) hv[j] = byrank[rank[j]] / nn;
+    B.q0 = c->upload(hv);
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    B.ready = true;
+  }
+  auto cgs2 = [&](long long rows, int ncol, const double *Q, double *w) {
+    if (ncol <= 0) return;
+    for (int pass = 0; pass < 2; pass++) {
+      KL(c, "lbd_cgs", c->stream, k_cgs_partial<256>, kRedGrid, 256, 0, rows, ncol, Q, rows, w, B.cpart);
+      KL(c, "lbd_cgs", c->stream, k_cgs_reduce, (ncol * 32 + 255) / 256, 256, 0, kRedGrid, ncol, B.cpart, B.cvec);
+      KL(c, "lbd_cgs", c->stream, k_cgs_sub, nblk(rows), kThreads, ncol * sizeof(double), rows, ncol, Q, rows,
+         B.cvec, w);
+    }
+  };
+  auto norm = [&](long long rows, const double *x, double *out) {
+    KL(c, "lbd", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, rows, x, x, c->part64,
+       (const int *)nullptr);
+    KL(c, "lbd", c->stream, k_cheb_reduce_norm, 1, 32, 0, kRedGrid, c->part64, out);
+  };
+  ck(cudaMemcpyAsync(B.Vq, B.q0, sizeof(double) * s, cudaMemcpyDeviceToDevice, c->stream), "D2D");
+  double scale = 0.0;
+  int mm = 0;
+  for (int j = 0; j < mmax; j++) {
+    const double *vj = B.Vq + (size_t)j * s;
+    double *uj = B.Uq + (size_t)j * n;
+    // u = K v_j - beta_{j-1} u_{j-1}, reorthogonalised; alpha_j = ||u||
+    KL(c, "lbd", c->stream, k_e_vec<double>, nblk(n), kThreads, 0, m0, s, c->eh_rp, c->eh_ci, c->eh64, 1.0 / a, a,
+       vj, (const double *)nullptr, B.t, (const int *)nullptr);
+    a0_solve<double>(c, B.t, B.u, nullptr);
+    if (j > 0) KL(c, "lbd", c->stream, k_lbd_axpy, nblk(n), kThreads, 0, (long long)n, B.be + j - 1, uj - n, B.u);
+    cgs2(n, j, B.Uq, B.u);
+    norm(n, B.u, B.al + j);
+    double aj = 0;
+    read_dev(c, &aj, B.al + j, sizeof(double));
+    if (!std::isfinite(aj)) { c->err = "NaN/Inf in the bidiagonalisation"; return DDLR_ERR_NAN; }
+    scale = std::max(scale, aj);
+    if (!(aj > 1e-12 * scale)) break;          // K v_j in the span of U_{j-1}
+    mm = j + 1;
+    KL(c, "lbd", c->stream, k_lbd_scale, nblk(n), kThreads, 0, (long long)n, B.u, B.al + j, uj);
+    // v = K^T u_j - alpha_j v_j, reorthogonalised; beta_j = ||v||
+    a0_solve<double>(c, uj, B.t, nullptr);
+    KL(c, "lbd", c->stream, k_et<double>, nblk(s), kThreads, 0, s, m0, c->eht_rp, c->eht_ci, c->eht64, 1.0 / a, a,
+       B.t, B.v, (const int *)nullptr);
+    KL(c, "lbd", c->stream, k_lbd_axpy, nblk(s), kThreads, 0, (long long)s, B.al + j, vj, B.v);
+    cgs2(s, j + 1, B.Vq, B.v);
+    norm(s, B.v, B.be + j);
+    double bj = 0;
+    read_dev(c, &bj, B.be + j, sizeof(double));
+    if (!std::isfinite(bj)) { c->err = "NaN/Inf in the bidiagonalisation"; return DDLR_ERR_NAN; }
+    scale = std::max(scale, bj);
+    if (check > 0 && mm % check == 0 && mm >= k + 1) {
+      // eq. converge on the k largest eigenvalues of B^T B for m and m - 1
+      const size_t sm1 = (2 * size_t(mm) + 2) * sizeof(double);
+      KL(c, "lbd", c->stream, k_lbd_tri, nblk(mm), kThreads, 0, mm, B.al, B.be, B.td, B.te);
+      KL(c, "lbd", c->stream, k_tridiag_values, k, kEigPoints, sm1, mm, B.td, B.te, k, B.etop);
+      KL(c, "lbd", c->stream, k_sum_first, 1, 32, 0, k, B.etop, B.esum);
+      KL(c, "lbd", c->stream, k_tridiag_values, k, kEigPoints, sm1, mm - 1, B.td, B.te, k, B.etop + k);
+      KL(c, "lbd", c->stream, k_sum_first, 1, 32, 0, k, B.etop + k, B.esum + 1);
+      double sg[2];
+      read_dev(c, sg, B.esum, sizeof(sg));
+      if (std::fabs(sg[0] - sg[1]) < eps * std::fabs(sg[1])) break;
+    }
+    if (mm == mmax || !(bj > 1e-12 * scale)) break;
+    KL(c, "lbd", c->stream, k_lbd_scale, nblk(s), kThreads, 0, (long long)s, B.v, B.be + j, B.Vq + (size_t)(j + 1) * s);
+  }
+  if (mm < k) {
+    c->err = "the bidiagonalisation ended before k steps (rank of A0^-1 E below k)";
+    return DDLR_ERR_BREAKDOWN;
+  }
+  // eigenpairs of B_m^T B_m; V_k = V_m Y_k; U_k = U_m (B_m Y_k)
+  KL(c, "lbd", c->stream, k_lbd_tri, nblk(mm), kThreads, 0, mm, B.al, B.be, B.td, B.te);
+  KL(c, "eig", c->stream, k_tridiag_values, mm, kEigPoints, (2 * mm + 2) * sizeof(double), mm, B.td, B.te, mm,
+     B.evals);
+  KL(c, "eig", c->stream, k_tridiag_vectors, 1, 256, 0, mm, B.td, B.te, k, B.evals, B.eY, B.work);
+  c->msteps = mm;
+  c->ritz.assign(mm, 0.0);
+  read_dev(c, c->ritz.data(), B.evals, sizeof(double) * mm);
+  KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(s), kThreads, 0, s, mm, k, B.Vq, (long long)s, B.eY, B.Vk);
+  KL(c, "ritz", c->stream, k_lbd_bmy, nblk((long long)mm * k), kThreads, 0, mm, k, B.al, B.be, B.eY, B.G);
+  KL(c, "ritz", c->stream, k_ritz_gemm<16>, nblk(n), kThreads, 0, n, mm, k, B.Uq, (long long)n, B.G, c->U64);
+  // H_k = (I - U_k^T E V_k)^-1
+  ck(cudaMemsetAsync(c->dflag, 0, 4 * sizeof(int), c->stream), "memset");
+  for (int cc = 0; cc < k; cc++) {
+    KL(c, "ritz", c->stream, k_get_col, nblk(s), kThreads, 0, (long long)s, k, cc, B.Vk, B.vc);
+    KL(c, "e_vec", c->stream, k_e_vec<double>, nblk(n), kThreads, 0, m0, s, c->eh_rp, c->eh_ci, c->eh64, 1.0 / a, a,
+       B.vc, (const double *)nullptr, B.ev, (const int *)nullptr);
+    KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, B.ev, B.EV);
+  }
+  KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, B.EV, B.kp);
+  KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, B.kp, B.hw, c->Hk64, c->dflag + 1);
+  c->theta = 0.0;
+  int fl[4];
+  read_dev(c, fl, c->dflag, sizeof(fl));
+  if (fl[2]) return DDLR_ERR_NAN;
+  if (fl[1]) return DDLR_ERR_NOT_SPD;
+  sync(c);
+  return DDLR_OK;
+}
+
 // Randomized subspace iteration for the low-rank part (ddlr_rand.cuh):
 // Omega -> Q = orth(Op Omega), q power steps, B = Q^T Op Q, eigenpairs of B,
 // then U_k / Lambda_k / theta (DDLR-1) or V_k -> U_k = A0^-1 E V_k, H_k
@@ -1346,7 +1494,9 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
     ddlr_status cs = mr_setup(c);
     if (cs != DDLR_OK) return cs;
   }
-  ddlr_status st = c->opt.lowrank_method == 1 ? run_randomized(c) : run_lanczos(c);
+  ddlr_status st = c->opt.lowrank_method == 1   ? run_randomized(c)
+                   : c->opt.lowrank_method == 2 ? run_lbd(c)
+                                                : run_lanczos(c);
   if (st != DDLR_OK) {
     c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
                                     : "NaN/Inf in the Lanczos process";
@@ -2296,7 +2446,7 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
                            1 + (long long)o.mr_iters * o.mr_lfil > kMrCap || !(o.mr_droptol >= 0.0))) ||
       (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
                            o.cheb_lanczos > 1000)) ||
-      (o.lowrank_method != 0 && o.lowrank_method != 1) ||
+      o.lowrank_method < 0 || o.lowrank_method > 2 || (o.lowrank_method == 2 && o.variant != 2) ||
       (o.lowrank_method == 1 && (o.rand_oversample < 0 || o.rand_power < 0 || o.rand_power > 100 ||
                                  o.rank_k + o.rand_oversample > kRandMaxL))) {
     g_setup_error = "invalid options";
