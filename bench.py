@@ -325,9 +325,12 @@ def run_ours(args):
         hc.close()
 
     # the low-rank build: Lanczos (Sec. 4.4) against the randomized subspace
-    # iteration (ell = k + 10, 2 power steps), setup and solve split
+    # iteration (ell = k + 10, 2 power steps), for DDLR-1 and DDLR-2, and for
+    # DDLR-2 the Lanczos bidiagonalisation of A0^-1 E; setup and solve split
     lowrank = {}
-    for name, extra in (("lanczos", dict()), ("randomized", dict(lowrank_method=1))):
+    for name, extra in (("lanczos", dict()), ("randomized", dict(lowrank_method=1)),
+                        ("ddlr2_lanczos", dict(variant=2)), ("ddlr2_randomized", dict(variant=2, lowrank_method=1)),
+                        ("ddlr2_bidiagonalisation", dict(variant=2, lowrank_method=2))):
         hr = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
         step(hr, x)
         su, so = split_once(hr)
