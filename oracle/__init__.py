@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, I, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -65,6 +65,8 @@ def _load():
         lib.or_pcg.argtypes = [P, P, P, D, I, I, ctypes.POINTER(I),
                                ctypes.POINTER(D)]
         lib.or_pcg.restype = I
+        lib.or_gmres.argtypes = [P, P, P, D, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+        lib.or_gmres.restype = I
         lib.or_info.argtypes = [P, P, ctypes.POINTER(D)]
         lib.or_ritz.argtypes = [P, P]
         lib.or_perm.argtypes = [P, P]
@@ -104,14 +106,16 @@ class Oracle:
     bidiagonalisation of A0^-1 E, DDLR-2 only),
     c_solver 2 = MR approximate inverse of C_a (Algorithm 2) with mr_iters
     iterations, at most mr_lfil entries per column of Z and drop tolerance
-    mr_droptol relative to the column norm.
+    mr_droptol relative to the column norm.  indefinite=1 accepts a
+    preconditioner that is not SPD (Ritz values >= 1 for DDLR-1, an
+    indefinite I - K for DDLR-2) for use with GMRES.
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
                  cheb_steps=5, cheb_lanczos=20, lowrank_method=0, rand_oversample=10,
-                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3):
+                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3, indefinite=0):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -126,7 +130,7 @@ class Oracle:
                           float(lanczos_eps), int(seed), int(c_solver),
                           int(cheb_steps), int(cheb_lanczos), int(lowrank_method),
                           int(rand_oversample), int(rand_power), int(mr_iters), int(mr_lfil),
-                          float(mr_droptol), ctypes.byref(h))
+                          float(mr_droptol), int(indefinite), ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h
@@ -175,6 +179,17 @@ class Oracle:
         st = _load().or_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit),
                             int(bool(flexible)), ctypes.byref(its),
                             ctypes.byref(rel))
+        return x, its.value, rel.value, STATUS.get(st, st)
+
+    def gmres(self, b, tol=1e-8, maxit=500, restart=40):
+        """Right-preconditioned GMRES(restart) from x0 = 0.
+        Returns (x, its, true_relres, status)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        its = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = _load().or_gmres(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), int(restart),
+                              ctypes.byref(its), ctypes.byref(rel))
         return x, its.value, rel.value, STATUS.get(st, st)
 
     @property

@@ -31,7 +31,11 @@
  *     by a few Lanczos steps with residual-norm safeguards, or by the
  *     approximate inverse of self-preconditioned MR iterations with
  *     dual-threshold dropping (c_solver 2, Algorithm 2);
- *   - Sec. 5: preconditioned CG from x0 = 0.
+ *   - Sec. 5: preconditioned CG from x0 = 0; for indefinite problems (or a
+ *     preconditioner that is not SPD) restarted GMRES(m), right-preconditioned,
+ *     from x0 = 0, with the setup accepting Ritz values >= 1 (DDLR-1) and an
+ *     indefinite I - K (DDLR-2, inverted by Gaussian elimination with partial
+ *     pivoting).
  *
  * Readings where the paper is silent are the same as the CUDA library's and are
  * listed with the design notes: natural (ascending original index) elimination
@@ -193,6 +197,36 @@ static int chol_dense(int n, double *a) {
   }
   for (int i = 0; i < n; i++)
     for (int j = i + 1; j < n; j++) a[(size_t)i * n + j] = 0.0;
+  return OR_OK;
+}
+
+/* inverse of a dense n x n matrix (row-major, destroyed) by Gauss-Jordan
+ * elimination with partial pivoting; a pivot of magnitude <= 1e-14 times the
+ * largest entry of the matrix means singular (BREAKDOWN) */
+static int gauss_jordan_inverse(int n, double *a, double *inv) {
+  double amax = 0.0;
+  for (int i = 0; i < n * n; i++) amax = fmax(amax, fabs(a[i]));
+  for (int r = 0; r < n; r++)
+    for (int c = 0; c < n; c++) inv[r * n + c] = (r == c) ? 1.0 : 0.0;
+  for (int j = 0; j < n; j++) {
+    int piv = j;
+    for (int r = j + 1; r < n; r++)
+      if (fabs(a[r * n + j]) > fabs(a[piv * n + j])) piv = r;
+    if (!(fabs(a[piv * n + j]) > 1e-14 * amax)) return OR_BREAKDOWN;
+    if (piv != j)
+      for (int c = 0; c < n; c++) {
+        double t = a[j * n + c]; a[j * n + c] = a[piv * n + c]; a[piv * n + c] = t;
+        t = inv[j * n + c]; inv[j * n + c] = inv[piv * n + c]; inv[piv * n + c] = t;
+      }
+    double d = a[j * n + j];
+    for (int c = 0; c < n; c++) { a[j * n + c] /= d; inv[j * n + c] /= d; }
+    for (int r = 0; r < n; r++) {
+      if (r == j) continue;
+      double f = a[r * n + j];
+      if (f == 0.0) continue;
+      for (int c = 0; c < n; c++) { a[r * n + c] -= f * a[j * n + c]; inv[r * n + c] -= f * inv[j * n + c]; }
+    }
+  }
   return OR_OK;
 }
 
@@ -804,7 +838,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
              int lowrank_method, int rand_oversample, int rand_power, int mr_iters, int mr_lfil,
-             double mr_droptol, void **out) {
+             double mr_droptol, int indefinite, void **out) {
   *out = NULL;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
     return OR_INVALID;
@@ -1128,8 +1162,16 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     o->lam = (double *)malloc(sizeof(double) * (size_t)k);
     for (int c = 0; c < k; c++) o->lam[c] = o->ritz[c];
     o->theta = (theta_mode == 1 && k < mm) ? o->ritz[k] : 0.0;
-    /* prop. spd-1: M is SPD when theta < 1 and every lambda_i < 1 */
-    if (!(o->lam[0] < 1.0) || !(o->theta < 1.0)) { or_free(o); return OR_NOT_SPD; }
+    if (!indefinite) {
+      /* prop. spd-1: M is SPD when theta < 1 and every lambda_i < 1 */
+      if (!(o->lam[0] < 1.0) || !(o->theta < 1.0)) { or_free(o); return OR_NOT_SPD; }
+    } else {
+      /* Ritz values above 1 are kept (A indefinite); G_{k,theta} must only be
+       * invertible: 1 - lambda_i and 1 - theta away from zero */
+      int sing = !(fabs(1.0 - o->theta) > 1e-12);
+      for (int c = 0; c < k; c++) sing |= !(fabs(1.0 - o->lam[c]) > 1e-12);
+      if (sing) { or_free(o); return OR_BREAKDOWN; }
+    }
   } else {
     /* U_k = A0^-1 E V_k (n x k); K = U_k^T (E V_k); H_k = (I - K)^-1 */
     o->urows = n;
@@ -1161,13 +1203,17 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
         for (int r = 0; r < n; r++) acc += o->U[(size_t)r * k + a] * EV[(size_t)r * k + b];
         K[a * k + b] = acc;
       }
-    /* I - K, symmetrised, Cholesky (failure: not SPD, prop. spd-2), inverse */
+    /* I - K, symmetrised, Cholesky (failure: not SPD, prop. spd-2), inverse;
+     * indefinite: Gauss-Jordan elimination with partial pivoting */
     double *IK = (double *)calloc((size_t)k * k, sizeof(double));
     for (int a = 0; a < k; a++)
       for (int b = 0; b < k; b++)
         IK[a * k + b] = (a == b ? 1.0 : 0.0) - 0.5 * (K[a * k + b] + K[b * k + a]);
-    int cst = chol_dense(k, IK);
-    if (cst == OR_OK) {
+    int cst = indefinite ? OR_BREAKDOWN : chol_dense(k, IK);
+    if (indefinite) {
+      o->Hk = (double *)calloc((size_t)k * k, sizeof(double));
+      if (gauss_jordan_inverse(k, IK, o->Hk) == OR_OK) cst = OR_OK;
+    } else if (cst == OR_OK) {
       o->Hk = (double *)calloc((size_t)k * k, sizeof(double));
       double *e = (double *)malloc(sizeof(double) * (size_t)k);
       for (int c = 0; c < k; c++) {
@@ -1188,7 +1234,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     }
     free(EV); free(vc); free(ev); free(uc); free(K); free(IK); free(V);
     free(Y); free(Ub); free(tdb); free(teb);
-    if (cst != OR_OK) { or_free(o); return OR_NOT_SPD; }
+    if (cst != OR_OK) { or_free(o); return indefinite ? OR_BREAKDOWN : OR_NOT_SPD; }
   }
   *out = o;
   return OR_OK;
@@ -1353,6 +1399,96 @@ done:
   *its_out = its;
   *relres_out = rel;
   free(r); free(z); free(zo); free(p); free(q);
+  return st;
+}
+
+/* Restarted GMRES(m) (Saad and Schultz), right-preconditioned: the Krylov
+ * space is that of A M^-1 from r0, and x = x0 + M^-1 V_j y.  Used in Sec. 5
+ * for the indefinite problems with m = 40.  From x0 = 0; each cycle runs
+ * Arnoldi with two classical Gram-Schmidt passes (the Hessenberg entry is
+ * the sum of both passes' coefficients), keeps the least-squares problem
+ * triangular with Givens rotations, so |g_{j+1}| is the residual norm of the
+ * current iterate, and ends when that norm is <= tol ||b||, after m steps,
+ * at maxit steps in total, or when the new Arnoldi vector is zero.  Then
+ * y = R^-1 g, x += M^-1 (V y), and the true residual b - A x both decides
+ * convergence and starts the next cycle.  its = Arnoldi steps. */
+int or_gmres(void *h, const double *b, double *x, double tol, int maxit, int restart,
+             int *its_out, double *relres_out) {
+  oracle *o = (oracle *)h;
+  int n = o->n, m = restart;
+  if (m < 1 || maxit < 0) return OR_INVALID;
+  double *V = (double *)malloc(sizeof(double) * (size_t)n * (m + 1));
+  double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double));   /* H[i + j (m+1)] */
+  double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+  double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+  double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  double *y = (double *)malloc(sizeof(double) * (size_t)m);
+  double *c = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  double *r = (double *)malloc(sizeof(double) * (size_t)n);
+  double *z = (double *)malloc(sizeof(double) * (size_t)n);
+  double *w = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+  double bn = sqrt(dot(n, b, b)), beta = bn;
+  int its = 0, st = OR_NOCONV;
+  while (1) {
+    if (beta <= tol * bn) { st = OR_OK; break; }
+    if (!(beta == beta)) { st = OR_BREAKDOWN; break; }
+    if (its >= maxit) break;
+    for (int i = 0; i < n; i++) V[i] = r[i] / beta;
+    for (int i = 0; i <= m; i++) g[i] = 0.0;
+    g[0] = beta;
+    int j = 0;
+    while (j < m && its < maxit) {
+      double *hj = H + (size_t)j * (m + 1);
+      or_apply(o, V + (size_t)j * n, z);          /* w = A M^-1 v_j */
+      sp_mv(&o->A, z, w);
+      for (int i = 0; i <= j; i++) hj[i] = 0.0;
+      for (int pass = 0; pass < 2; pass++) {
+        for (int i = 0; i <= j; i++) c[i] = dot(n, V + (size_t)i * n, w);
+        for (int i = 0; i <= j; i++) {
+          for (int q = 0; q < n; q++) w[q] -= c[i] * V[(size_t)i * n + q];
+          hj[i] += c[i];
+        }
+      }
+      double hn = sqrt(dot(n, w, w));
+      hj[j + 1] = hn;
+      if (hn > 0.0)
+        for (int q = 0; q < n; q++) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+      for (int i = 0; i < j; i++) {              /* earlier rotations */
+        double t = cs[i] * hj[i] + sn[i] * hj[i + 1];
+        hj[i + 1] = -sn[i] * hj[i] + cs[i] * hj[i + 1];
+        hj[i] = t;
+      }
+      double d = hypot(hj[j], hj[j + 1]);        /* the rotation that zeroes h_{j+1,j} */
+      cs[j] = d > 0.0 ? hj[j] / d : 1.0;
+      sn[j] = d > 0.0 ? hj[j + 1] / d : 0.0;
+      hj[j] = d;
+      hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      its++;
+      j++;
+      if (fabs(g[j]) <= tol * bn || !(hn > 0.0)) break;
+    }
+    for (int i = j - 1; i >= 0; i--) {           /* R y = g */
+      double t = g[i];
+      for (int l = i + 1; l < j; l++) t -= H[i + (size_t)l * (m + 1)] * y[l];
+      y[i] = t / H[i + (size_t)i * (m + 1)];
+    }
+    for (int q = 0; q < n; q++) {
+      double t = 0.0;
+      for (int l = 0; l < j; l++) t += V[(size_t)l * n + q] * y[l];
+      w[q] = t;
+    }
+    or_apply(o, w, z);
+    for (int q = 0; q < n; q++) x[q] += z[q];
+    sp_mv(&o->A, x, w);
+    for (int q = 0; q < n; q++) r[q] = b[q] - w[q];
+    beta = sqrt(dot(n, r, r));
+  }
+  *its_out = its;
+  *relres_out = bn > 0 ? beta / bn : 0.0;
+  free(V); free(H); free(cs); free(sn); free(g); free(y); free(c); free(r); free(z); free(w);
   return st;
 }
 

@@ -96,6 +96,17 @@ def laplacian(shape) -> tuple:
                        np.concatenate(vals))
 
 
+def shifted_laplacian(shape, sigma: float) -> tuple:
+    """The Laplacian of ``laplacian(shape)`` minus sigma I: the symmetric
+    indefinite model problem -Lap u - c u of Sec. 5.1 (c > 0) with h^2 scaled
+    out, indefinite once sigma exceeds the smallest eigenvalue."""
+    n, rp, ci, va = laplacian(shape)
+    va = va.copy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    va[rows == ci] -= float(sigma)
+    return n, rp, ci, va
+
+
 def box_partition(shape, parts) -> tuple[np.ndarray, int]:
     """Split each grid axis into ``parts[a]`` equal ranges (cut at floor(i*N/P)).
 
@@ -211,6 +222,8 @@ def workload(name: str):
     lap3d_128_b8   : 3-D 128^3 7-point Laplacian, 8^3 boxes (n=2,097,152)
     jump3d_96_cut5 : 3-D 96^3 jump-coefficient FV, 5x5x5 random cuts
     lap3d_E        : 3-D E^3 Laplacian with (E/16)^3 boxes, E in {32,48,64,96,128}
+    indef3d_64_s3e-2 : 3-D 64^3 Laplacian minus 3e-2 I, 4x4x2 boxes (32)
+    indef2d_128_s1e-1: 2-D 128^2 Laplacian minus 1e-1 I, 2x1 boxes (2)
     """
     if name == "lap2d_64_b2x2":
         shape = (64, 64)
@@ -228,6 +241,14 @@ def workload(name: str):
         shape = (96, 96, 96)
         A = jump_coefficient_fv(96, 8, 0)
         part, p = random_cut_partition(96, 5, 0)
+    elif name == "indef3d_64_s3e-2":
+        shape = (64, 64, 64)
+        A = shifted_laplacian(shape, 3e-2)
+        part, p = box_partition(shape, (4, 4, 2))
+    elif name == "indef2d_128_s1e-1":
+        shape = (128, 128)
+        A = shifted_laplacian(shape, 1e-1)
+        part, p = box_partition(shape, (2, 1))
     elif name.startswith("lap3d_") and name[6:].isdigit():
         e = int(name[6:])
         shape = (e, e, e)
