@@ -339,6 +339,36 @@ def run_ours(args):
                          "iterations": inf_r[0]["its"], "basis": hr.info()["lanczos_steps"]}
         hr.close()
 
+    # indefinite line (Sec. 5, the 64^3 row of the indefinite table: the
+    # Laplacian minus 3e-2 I, 32 subdomains, rank 64): DDLR with GMRES(40) to a
+    # 1e-6 relative residual (at most 4000 steps), setup and solve split
+    indef = {}
+    if not args.skip_large:
+        wi = W.workload("indef3d_64_s3e-2")
+        Ai, parti, pi = wi["A"], wi["part"], wi["p"]
+        bi = torch.tensor(W.rhs(Ai[0], 0), device="cuda")
+        xi = torch.zeros_like(bi)
+        for name, extra in (("ddlr1", dict(variant=1)), ("ddlr2", dict(variant=2))):
+            try:
+                hi = pkg.DDLR(Ai, parti, pi, **dict(OPTS, rank_k=64, indefinite=1, **extra))
+            except pkg.DdlrError as e:
+                indef[name] = {"status": e.status}
+                continue
+            hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
+            flush.fill_(1.0)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            hi.refactor()
+            e1.record(stream)
+            _, ii = hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
+            e2.record(stream)
+            e2.synchronize()
+            inf_i = hi.info()
+            indef[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
+                           "iterations": ii["its"], "status": ii["status"], "true_relres": ii["relres"],
+                           "lanczos_steps": inf_i["lanczos_steps"], "lambda_max": inf_i["lambda_max"]}
+            hi.close()
+
     # precision line: 128^3 Laplacian, 512 boxes, k = 32 -- FP64 against mixed
     # (FP32 factors and solves, BF16 or FP32 U_k, FP64 flexible CG)
     prec = {}
@@ -519,6 +549,7 @@ def run_ours(args):
             "e2e_parts": e2e_parts,
             "c_alpha_solve_factored_chebyshev_mr": c_solve,
             "lowrank_lanczos_vs_randomized": lowrank,
+            "indefinite_lap3d_64_s3e-2_gmres40_k64": indef,
             "precision_lap3d_128_b8_k32": prec,
             "batching_jump3d_96_cut5_32rhs": batch,
             "serving_lap3d_32_to_128_512req": serving,

@@ -102,6 +102,15 @@ typedef struct {
                               1 + mr_iters * mr_lfil <= 32)                        */
   double mr_droptol;       /* c_solver 2: drop tolerance relative to the column
                               norm of Z (default 1e-3)                             */
+  int indefinite;          /* 1 = accept a preconditioner that is not SPD, for
+                              ddlr_gmres (Sec. 5: indefinite problems and
+                              preconditioners found not SPD).  DDLR-1 keeps Ritz
+                              values >= 1 and needs only 1 - lambda_i and
+                              1 - theta away from zero; DDLR-2 inverts I - K by
+                              Gauss-Jordan elimination with partial pivoting.  A
+                              singular G_{k,theta} or I - K gives BREAKDOWN.  The
+                              local factors stay IC(0) / Cholesky, so A0 must be
+                              positive definite (else BREAKDOWN).  Default 0.   */
 } ddlr_options;
 
 typedef struct {
@@ -220,6 +229,23 @@ ddlr_status ddlr_a0_solve_noalloc(ddlr_handle h, const double *x, double *y);
  * else DDLR_ERR_NOCONV or DDLR_ERR_NAN. */
 ddlr_status ddlr_pcg(ddlr_handle h, const double *b, double *x, int nrhs,
                      int ld, double tol, int maxit, ddlr_solve_info *info);
+
+/* Restarted GMRES(restart) from x0 = 0 (Sec. 5: GMRES(40) for the indefinite
+ * problems and for preconditioners found not SPD), right-preconditioned by
+ * M^-1: Arnoldi on A M^-1 with two classical Gram-Schmidt passes and Givens
+ * rotations.  The preconditioned vectors Z = M^-1 V are kept (n x restart
+ * doubles of workspace, allocated on first use), so the update x += Z y needs
+ * no further apply, and an FP32 M^-1 (precision 1) is used as in flexible
+ * GMRES.  A cycle ends when the rotated residual norm is <= tol ||b||, after
+ * restart steps, at maxit steps in total, or when the new Arnoldi vector is
+ * zero; the true residual b - A x then decides convergence and starts the
+ * next cycle.  b, x: n doubles, host or device memory, original order, one
+ * right-hand side.  maxit <= 0: 500; restart <= 0: 40; restart <= 512.  info
+ * (host memory, may be NULL): its = Arnoldi steps (products with A), relres =
+ * true relative residual.  Synchronous.  Returns DDLR_OK, DDLR_ERR_NOCONV or
+ * DDLR_ERR_NAN; INVALID for NULL vectors, tol <= 0 or restart > 512. */
+ddlr_status ddlr_gmres(ddlr_handle h, const double *b, double *x, double tol,
+                       int maxit, int restart, ddlr_solve_info *info);
 
 /* Sizes, counts and scalars of the handle (host struct). */
 ddlr_status ddlr_get_info(ddlr_handle h, ddlr_info *info);

@@ -23,6 +23,7 @@
 #include "ddlr_rand.cuh"
 #include "ddlr_mr.cuh"
 #include "ddlr_lbd.cuh"
+#include "ddlr_gmres.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -176,6 +177,13 @@ struct ddlr_ctx {
            *work = nullptr, *esum = nullptr, *etop = nullptr, *G = nullptr, *Vk = nullptr, *EV = nullptr,
            *vc = nullptr, *ev = nullptr, *kp = nullptr, *hw = nullptr, *q0 = nullptr;
   } lb;
+  // restarted GMRES: Arnoldi basis V (n x (m+1)), Z = M^-1 V (n x m), H
+  // ((m+1) x m), rotations, g, y, CGS partials, device scalars
+  struct GmresWork {
+    int m = 0;
+    double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr,
+           *cpart = nullptr, *cvec = nullptr, *st = nullptr;
+  } gm;
   int cheb_msteps = 0;
   // approximate inverse of C_a (c_solver 2): columns of X during the MR
   // iterations, then the symmetric part as row CSR (ptr, distinct counts)
@@ -800,6 +808,9 @@ void lanczos_step(ddlr_ctx *c, const LzBufs &L) {
   KL(c, "lanczos", c->stream, k_lz_advance, 1, 32, 0, L.st);
 }
 
+void hk_finalize(ddlr_ctx *c, int k, const double *kp, double *hw);
+ddlr_status lowrank_status(ddlr_ctx *c, const int *fl);
+
 // Lanczos with full reorthogonalisation and the convergence test of
 // eq. converge every `check` steps (Sec. 4.4, Sec. 5).  The host enqueues the
 // steps (one CUDA graph each) without waiting; each test runs on the second
@@ -1009,14 +1020,12 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
           KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, uc, c->U64);
         }
         KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, EV, kp);
-        KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, kp, hw, c->Hk64, c->dflag + 1);
+        hk_finalize(c, k, kp, hw);
         c->theta = 0.0;
       }
       int fl[4];
       read_dev(c, fl, c->dflag, sizeof(fl));
-      if (fl[3]) st = DDLR_ERR_TIMEOUT;
-      else if (fl[2]) st = DDLR_ERR_NAN;
-      else if (fl[1]) st = DDLR_ERR_NOT_SPD;
+      st = lowrank_status(c, fl);
     }
     sync(c);
   } catch (...) {
@@ -1073,6 +1082,46 @@ const int *pcg_gate(ddlr_ctx *c) {
 void batch_alloc(ddlr_ctx *c, int R);
 template <typename T>
 void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate);
+
+// H_k = (I - U_k^T E V_k)^-1 for DDLR-2 from the k_utv_partial partials:
+// Cholesky (an I - K that is not positive definite sets the NOT_SPD flag,
+// prop. spd-2) or, in the indefinite mode, Gauss-Jordan with partial pivoting
+// (a singular I - K sets the same flag, read as BREAKDOWN)
+void hk_finalize(ddlr_ctx *c, int k, const double *kp, double *hw) {
+  if (c->opt.indefinite)
+    KL(c, "ritz", c->stream, k_hk_finalize_gj, 1, 32, 0, kRedGrid, k, kp, hw, c->Hk64, c->dflag + 1);
+  else
+    KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, kp, hw, c->Hk64, c->dflag + 1);
+}
+
+// status of a finished low-rank build from the device flags (timeout, NaN,
+// not SPD).  In the indefinite mode DDLR-1 keeps Ritz values >= 1 (the flag
+// of k_ddlr1_coef is ignored) and only needs G_{k,theta} invertible:
+// 1 - lambda_i and 1 - theta away from zero; DDLR-2's flag then means a
+// singular I - K.  Both are BREAKDOWN.
+ddlr_status lowrank_status(ddlr_ctx *c, const int *fl) {
+  if (fl[3]) return DDLR_ERR_TIMEOUT;
+  if (fl[2]) return DDLR_ERR_NAN;
+  if (!c->opt.indefinite) return fl[1] ? DDLR_ERR_NOT_SPD : DDLR_OK;
+  if (c->opt.variant == 2) return fl[1] ? DDLR_ERR_BREAKDOWN : DDLR_OK;
+  const int k = c->opt.rank_k;
+  bool sing = !(std::fabs(1.0 - c->theta) > 1e-12);
+  for (int i = 0; i < k && i < int(c->ritz.size()); i++) sing |= !(std::fabs(1.0 - c->ritz[i]) > 1e-12);
+  for (double v : c->ritz)
+    if (!std::isfinite(v)) return DDLR_ERR_NAN;
+  return sing ? DDLR_ERR_BREAKDOWN : DDLR_OK;
+}
+
+const char *lowrank_error(ddlr_ctx *c, ddlr_status st) {
+  switch (st) {
+    case DDLR_ERR_NOT_SPD: return "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)";
+    case DDLR_ERR_BREAKDOWN:
+      return c->opt.indefinite ? "G_{k,theta} or I - K is singular, or the low-rank process stopped early"
+                               : "the low-rank process stopped before k steps";
+    case DDLR_ERR_TIMEOUT: return "a bounded device wait timed out";
+    default: return "NaN/Inf in the low-rank build";
+  }
+}
 
 // Lanczos bidiagonalisation of K = A0^-1 E for DDLR-2 (ddlr_lbd.cuh): the
 // steps run kernel by kernel with the scalars on the device; the host reads
@@ -1202,12 +1251,12 @@ ddlr_status run_lbd(ddlr_ctx *c) {
     KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, B.ev, B.EV);
   }
   KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, B.EV, B.kp);
-  KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, B.kp, B.hw, c->Hk64, c->dflag + 1);
+  hk_finalize(c, k, B.kp, B.hw);
   c->theta = 0.0;
   int fl[4];
   read_dev(c, fl, c->dflag, sizeof(fl));
-  if (fl[2]) return DDLR_ERR_NAN;
-  if (fl[1]) return DDLR_ERR_NOT_SPD;
+  const ddlr_status fst = lowrank_status(c, fl);
+  if (fst != DDLR_OK) return fst;
   sync(c);
   return DDLR_OK;
 }
@@ -1320,13 +1369,12 @@ ddlr_status run_randomized(ddlr_ctx *c) {
       KL(c, "ritz", c->stream, k_set_col, nblk(n), kThreads, 0, (long long)n, k, cc, R.uc, c->U64);
     }
     KL(c, "ritz", c->stream, k_utv_partial, kRedGrid, 256, 0, (long long)n, k, c->U64, R.EV, R.kp);
-    KL(c, "ritz", c->stream, k_hk_finalize, 1, 32, 0, kRedGrid, k, R.kp, R.hw, c->Hk64, c->dflag + 1);
+    hk_finalize(c, k, R.kp, R.hw);
     c->theta = 0.0;
   }
   read_dev(c, fl, c->dflag, sizeof(fl));
-  if (fl[3]) return DDLR_ERR_TIMEOUT;
-  if (fl[2]) return DDLR_ERR_NAN;
-  if (fl[1]) return DDLR_ERR_NOT_SPD;
+  const ddlr_status fst = lowrank_status(c, fl);
+  if (fst != DDLR_OK) return fst;
   sync(c);
   return DDLR_OK;
 }
@@ -1498,8 +1546,7 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
                    : c->opt.lowrank_method == 2 ? run_lbd(c)
                                                 : run_lanczos(c);
   if (st != DDLR_OK) {
-    c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
-                                    : "NaN/Inf in the Lanczos process";
+    c->err = lowrank_error(c, st);
     return st;
   }
   make_low_precision(c);
@@ -1951,6 +1998,100 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
     info->relres = hs.bb > 0 ? std::sqrt(c->h_pin[0] / hs.bb) : 0.0;
     info->status = hs.status == 0 ? DDLR_OK : (hs.status == 5 ? DDLR_ERR_NOCONV : DDLR_ERR_NAN);
     if (hs.done == 0) info->status = DDLR_ERR_NOCONV;
+  }
+}
+
+constexpr int kGmresMaxRestart = 512;
+
+// Restarted GMRES(m) on device-order vectors b -> x (Sec. 5: GMRES(40) for
+// the indefinite problems), right-preconditioned, kernels in ddlr_gmres.cuh.
+// The host reads the rotated residual norm and h_{j+1,j} after every Arnoldi
+// step to end the cycle; the true residual b - A x ends each cycle.
+void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, int m, ddlr_solve_info *info) {
+  const int n = c->P.n;
+  auto &G = c->gm;
+  if (G.m < m) {
+    // grown arrays replace the old ones; the arena keeps the old until destroy
+    G.V = c->alloc<double>(size_t(n) * (m + 1));
+    G.Z = c->alloc<double>(size_t(n) * m);
+    G.H = c->alloc<double>(size_t(m + 1) * m);
+    G.cs = c->alloc<double>(m); G.sn = c->alloc<double>(m);
+    G.g = c->alloc<double>(m + 1); G.y = c->alloc<double>(m);
+    G.cpart = c->alloc<double>(size_t(kRedGrid) * (m + 1));
+    G.cvec = c->alloc<double>(m + 1);
+    G.st = c->alloc<double>(4);
+    G.m = m;
+  }
+  const int ld = m + 1;
+  double *r = c->pv[1], *w = c->pv[3], *q = c->pv[4];
+  auto norm_to = [&](const double *v, double *o1, double *o2) {
+    KL(c, "gmres", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, v, v, c->part64,
+       (const int *)nullptr);
+    KL(c, "gmres", c->stream, k_gm_norm, 1, 32, 0, kRedGrid, c->part64, o1, o2);
+  };
+  auto read2 = [&](const double *src, double *dst) {
+    ck(cudaMemcpyAsync(c->h_pin, src, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    dst[0] = c->h_pin[0];
+    dst[1] = c->h_pin[1];
+  };
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream), "memset");
+  ck(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  norm_to(b, G.st + 2, G.st + 3);
+  double sc[2];
+  read2(G.st + 2, sc);
+  const double bn = sc[0];
+  double beta = bn;
+  int its = 0, status = DDLR_ERR_NOCONV;
+  while (true) {
+    if (!std::isfinite(beta)) { status = DDLR_ERR_NAN; break; }
+    if (beta <= tol * bn) { status = DDLR_OK; break; }
+    if (its >= maxit) break;
+    KL(c, "gmres", c->stream, k_lbd_scale, nblk(n), kThreads, 0, (long long)n, r, G.st + 2, G.V);   // v_0 = r / beta
+    KL(c, "gmres", c->stream, k_gm_ginit, 1, std::max(32, ((m + 1 + 31) / 32) * 32), 0, m, G.st + 2, G.g);
+    int j = 0;
+    bool nan = false;
+    while (j < m && its < maxit) {
+      const double *vj = G.V + size_t(j) * n;
+      double *zj = G.Z + size_t(j) * n, *hcol = G.H + size_t(j) * ld;
+      precond(c, vj, zj, nullptr);                                                        // z_j = M^-1 v_j
+      KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, zj, w,
+         (const int *)nullptr);                                                           // w = A z_j
+      for (int pass = 0; pass < 2; pass++) {
+        KL(c, "gmres_cgs", c->stream, k_cgs_partial<256>, kRedGrid, 256, 0, (long long)n, j + 1, G.V, (long long)n, w,
+           G.cpart);
+        KL(c, "gmres_cgs", c->stream, k_gm_reduce_acc, ((j + 1) * 32 + 255) / 256, 256, 0, kRedGrid, j + 1, G.cpart,
+           G.cvec, hcol, pass == 0 ? 1 : 0);
+        KL(c, "gmres_cgs", c->stream, k_cgs_sub, nblk(n), kThreads, (j + 1) * sizeof(double), (long long)n, j + 1, G.V,
+           (long long)n, G.cvec, w);
+      }
+      norm_to(w, hcol + j + 1, G.st + 1);                                                 // h_{j+1,j}
+      KL(c, "gmres", c->stream, k_lbd_scale, nblk(n), kThreads, 0, (long long)n, w, G.st + 1,
+         G.V + size_t(j + 1) * n);
+      KL(c, "gmres", c->stream, k_gm_givens, 1, 32, 0, j, hcol, G.cs, G.sn, G.g, G.st);
+      read2(G.st, sc);
+      its++;
+      j++;
+      if (!std::isfinite(sc[0]) || !std::isfinite(sc[1])) { nan = true; break; }
+      if (sc[0] <= tol * bn || !(sc[1] > 0.0)) break;
+    }
+    if (nan) { status = DDLR_ERR_NAN; break; }
+    KL(c, "gmres", c->stream, k_gm_backsolve, 1, 32, 0, j, G.H, ld, G.g, G.y);
+    KL(c, "gmres", c->stream, k_gm_update, nblk(n), kThreads, j * sizeof(double), (long long)n, j, G.Z, G.y, x);
+    KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, x, q,
+       (const int *)nullptr);
+    KL(c, "gmres", c->stream, k_gm_resid, nblk(n), kThreads, 0, (long long)n, b, q, r);
+    norm_to(r, G.st + 2, G.st + 3);
+    read2(G.st + 2, sc);
+    beta = sc[0];
+  }
+  int dfl[4];
+  read_dev(c, dfl, c->dflag, sizeof(dfl));
+  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  if (info) {
+    info->its = its;
+    info->relres = bn > 0 ? beta / bn : 0.0;
+    info->status = status;
   }
 }
 
@@ -2427,6 +2568,7 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->mr_iters = 3;
   o->mr_lfil = 8;
   o->mr_droptol = 1e-3;
+  o->indefinite = 0;
   return DDLR_OK;
 }
 
@@ -2447,6 +2589,7 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
       (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
                            o.cheb_lanczos > 1000)) ||
       o.lowrank_method < 0 || o.lowrank_method > 2 || (o.lowrank_method == 2 && o.variant != 2) ||
+      (o.indefinite != 0 && o.indefinite != 1) ||
       (o.lowrank_method == 1 && (o.rand_oversample < 0 || o.rand_power < 0 || o.rand_power > 100 ||
                                  o.rank_k + o.rand_oversample > kRandMaxL))) {
     g_setup_error = "invalid options";
@@ -2568,8 +2711,7 @@ ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
     if (c->pz_pcg || c->pz_lz) pz_setup(c, m_new);
     const ddlr_status st = run_lanczos(c, true);
     if (st != DDLR_OK) {
-      c->err = st == DDLR_ERR_NOT_SPD ? "preconditioner is not SPD (lambda_max >= 1 or I - K not PD)"
-                                      : "NaN/Inf in the Lanczos process";
+      c->err = lowrank_error(c, st);
       return st;
     }
     make_low_precision(c);
@@ -2754,6 +2896,25 @@ ddlr_status ddlr_pcg(ddlr_handle c, const double *b, double *x, int nrhs, int ld
   }
   if (agg != DDLR_OK) c->err = agg == DDLR_ERR_NOCONV ? "PCG did not converge" : "NaN/Inf in PCG";
   return agg;
+}
+
+ddlr_status ddlr_gmres(ddlr_handle c, const double *b, double *x, double tol, int maxit, int restart,
+                       ddlr_solve_info *info) {
+  if (!c) return DDLR_ERR_INVALID;
+  if (maxit <= 0) maxit = 500;
+  if (restart <= 0) restart = 40;
+  if (!(tol > 0) || restart > kGmresMaxRestart) { c->err = "tol must be positive, restart <= 512"; return DDLR_ERR_INVALID; }
+  ddlr_solve_info inf{};
+  ddlr_status st = vec_call(c, b, x, 1, c->P.n, [&](const double *bd, double *xd) {
+    const int n = c->P.n;
+    KL(c, "perm", c->stream, k_permute_in<double>, nblk(n), kThreads, 0, n, c->perm, bd, c->pv[0]);
+    gmres_dev(c, c->pv[0], c->pv[2], tol, maxit, restart, &inf);
+    KL(c, "perm", c->stream, k_permute_out<double>, nblk(n), kThreads, 0, n, c->perm, c->pv[2], xd);
+  });
+  if (st != DDLR_OK) return st;
+  if (info) *info = inf;
+  if (inf.status != DDLR_OK) c->err = inf.status == DDLR_ERR_NOCONV ? "GMRES did not converge" : "NaN/Inf in GMRES";
+  return (ddlr_status)inf.status;
 }
 
 ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {

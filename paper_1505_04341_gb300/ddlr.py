@@ -38,7 +38,8 @@ class ddlr_options(ctypes.Structure):
                 ("c_solver", ctypes.c_int), ("cheb_steps", ctypes.c_int),
                 ("cheb_lanczos", ctypes.c_int), ("lowrank_method", ctypes.c_int),
                 ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int),
-                ("mr_iters", ctypes.c_int), ("mr_lfil", ctypes.c_int), ("mr_droptol", ctypes.c_double)]
+                ("mr_iters", ctypes.c_int), ("mr_lfil", ctypes.c_int), ("mr_droptol", ctypes.c_double),
+                ("indefinite", ctypes.c_int)]
 
 
 class ddlr_info(ctypes.Structure):
@@ -69,7 +70,7 @@ class ddlr_server_options(ctypes.Structure):
 
 # every entry point declared in include/ddlr.h
 EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
-           "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
+           "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_gmres", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank", "ddlr_set_cheb_bounds",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
            "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
@@ -102,6 +103,7 @@ def load(path: str | None = None):
         "ddlr_a0_solve": ([P, P, P, I, I], I),
         "ddlr_a0_solve_noalloc": ([P, P, P], I),
         "ddlr_pcg": ([P, P, P, I, I, D, I, ctypes.POINTER(ddlr_solve_info)], I),
+        "ddlr_gmres": ([P, P, P, D, I, I, ctypes.POINTER(ddlr_solve_info)], I),
         "ddlr_get_info": ([P, ctypes.POINTER(ddlr_info)], I),
         "ddlr_get_ritz": ([P, P, I, ctypes.POINTER(I)], I),
         "ddlr_get_factor_coo": ([P, ctypes.POINTER(LL), P, P, P], I),
@@ -278,6 +280,21 @@ class DDLR:
         if st not in (0, 5, 7) or (check and st != 0):
             _check(_lib, self._h, st)
         return x, [dict(its=i.its, relres=i.relres, status=STATUS[i.status]) for i in infos]
+
+    def gmres(self, b, x=None, tol=1e-8, maxit=500, restart=40, check=True):
+        """Right-preconditioned GMRES(restart) from x0 = 0 (one RHS).  Returns
+        (x, ddlr_solve_info as a dict); raises on NOCONV/NAN when check is
+        true."""
+        x = self._like(b) if x is None else x
+        pb, n, nr = _vec_ptr(b)
+        px, n2, nr2 = _vec_ptr(x)
+        if n != self.n or n2 != self.n or nr != 1 or nr2 != 1:
+            raise ValueError("shape mismatch: one vector of length n expected")
+        inf = ddlr_solve_info()
+        st = _lib.ddlr_gmres(self._h, pb, px, float(tol), int(maxit), int(restart), ctypes.byref(inf))
+        if st not in (0, 5, 7) or (check and st != 0):
+            _check(_lib, self._h, st)
+        return x, dict(its=inf.its, relres=inf.relres, status=STATUS[inf.status])
 
     def info(self) -> dict:
         inf = ddlr_info()
