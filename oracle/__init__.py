@@ -95,7 +95,8 @@ class Oracle:
 
     ``A = (n, rowptr, colind, val)`` full symmetric CSR, ``part[i]`` in [0, p).
     Options follow the library's: variant 1/2, rank k, alpha, theta_mode
-    (1: theta = Ritz_{k+1}, 0: theta = 0), factor (0: IC(0), 1: exact),
+    (1: theta = Ritz_{k+1}, 0: theta = 0), factor (0: IC(0), 1: exact
+    Cholesky, 2: incomplete LDL^T on the pattern, 3: exact LDL^T),
     c_order (0: ascending index, 1: greedy multicolour) of C_a, b_order (the
     same choice for the interior blocks), scale_diag,
     lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed,

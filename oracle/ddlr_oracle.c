@@ -15,8 +15,10 @@
  *   - Sec. 3.1 (eq. EF, split): E = [a^-1 Ehat ; -a I],
  *     A0 = blkdiag(B + a^-2 Ehat Ehat^T, C + a^2 I), A = A0 - E E^T;
  *   - Sec. 4.1, 5: local solvers = incomplete Cholesky IC(0) on the pattern
- *     (or exact Cholesky, dense), one factor per B_{i,a} and one for C_a, each
- *     in its elimination order (ascending index, or multicolour);
+ *     (or exact Cholesky, dense), or for indefinite blocks incomplete LDL^T on
+ *     the pattern (or exact LDL^T, dense, no pivoting), one factor per
+ *     B_{i,a} and one for C_a, each in its elimination order (ascending
+ *     index, or multicolour);
  *   - Sec. 4.4 (eq. converge): Lanczos on H = E^T A0^-1 E (DDLR-1) or on
  *     E^T A0^-2 E (DDLR-2), with full reorthogonalisation (two classical
  *     Gram-Schmidt passes), convergence checked every `check` steps;
@@ -128,8 +130,9 @@ static double sm64_pm1(uint64_t seed, uint64_t i) {
 typedef struct {
   int nb;        /* block size */
   int *ord;      /* ord[e] = block-local row (eq. Bmat order) eliminated e-th */
-  int exact;     /* 1: dense Cholesky, 0: IC(0) */
-  sp L;          /* IC(0): rows in elimination order, lower part incl. diagonal */
+  int exact;     /* 1: dense factor, 0: incomplete on the pattern */
+  int ldl;       /* 1: L D L^T with unit L, d_i stored in the diagonal slot */
+  sp L;          /* incomplete: rows in elimination order, lower part incl. diagonal */
   double *D;     /* exact: dense nb x nb lower factor, row-major */
 } blockfac;
 
@@ -137,28 +140,12 @@ typedef struct {
  *   l_ij = (s_ij - sum_{t<j, t in P_i and P_j} l_it l_jt) / l_jj   (j < i)
  *   l_ii = sqrt(s_ii - sum_{t<i} l_it^2)
  * over the lower pattern P_i of S; a pivot <= 0 is a breakdown. */
+static int ic0_pattern(const sp *S, sp *L);
+
 static int ic0(const sp *S, sp *L) {
+  int st = ic0_pattern(S, L);
+  if (st != OR_OK) return st;
   int n = S->nr;
-  long nnz = 0;
-  for (int i = 0; i < n; i++)
-    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
-      if (S->ci[q] <= i) nnz++;
-  L->nr = n;
-  L->rp = (int *)calloc((size_t)n + 1, sizeof(int));
-  L->ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
-  L->va = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
-  if (!L->rp || !L->ci || !L->va) return OR_NOMEM;
-  long w = 0;
-  for (int i = 0; i < n; i++) {
-    int has_diag = 0;
-    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
-      if (S->ci[q] <= i) {
-        L->ci[w] = S->ci[q]; L->va[w] = S->va[q]; w++;
-        if (S->ci[q] == i) has_diag = 1;
-      }
-    if (!has_diag) return OR_BREAKDOWN;
-    L->rp[i + 1] = (int)w;
-  }
   for (int i = 0; i < n; i++) {
     int b = L->rp[i], e = L->rp[i + 1];   /* diagonal is the last entry */
     for (int q = b; q < e - 1; q++) {
@@ -181,6 +168,32 @@ static int ic0(const sp *S, sp *L) {
   return OR_OK;
 }
 
+/* the lower part of S (incl. diagonal) copied into L, rows in order */
+static int ic0_pattern(const sp *S, sp *L) {
+  int n = S->nr;
+  long nnz = 0;
+  for (int i = 0; i < n; i++)
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
+      if (S->ci[q] <= i) nnz++;
+  L->nr = n;
+  L->rp = (int *)calloc((size_t)n + 1, sizeof(int));
+  L->ci = (int *)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+  L->va = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  if (!L->rp || !L->ci || !L->va) return OR_NOMEM;
+  long w = 0;
+  for (int i = 0; i < n; i++) {
+    int has_diag = 0;
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
+      if (S->ci[q] <= i) {
+        L->ci[w] = S->ci[q]; L->va[w] = S->va[q]; w++;
+        if (S->ci[q] == i) has_diag = 1;
+      }
+    if (!has_diag) return OR_BREAKDOWN;
+    L->rp[i + 1] = (int)w;
+  }
+  return OR_OK;
+}
+
 /* dense Cholesky S = L L^T (row-major lower); pivot <= 0 is a breakdown */
 static int chol_dense(int n, double *a) {
   for (int j = 0; j < n; j++) {
@@ -192,6 +205,58 @@ static int chol_dense(int n, double *a) {
     for (int i = j + 1; i < n; i++) {
       double s = a[(size_t)i * n + j];
       for (int t = 0; t < j; t++) s -= a[(size_t)i * n + t] * a[(size_t)j * n + t];
+      a[(size_t)i * n + j] = s / d;
+    }
+  }
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) a[(size_t)i * n + j] = 0.0;
+  return OR_OK;
+}
+
+/* incomplete LDL^T of S on its lower pattern P (same storage as ic0, d_i in
+ * the diagonal slot, L unit lower):
+ *   l_ij = (s_ij - sum_{t<j, t in P_i and P_j} l_it d_t l_jt) / d_j   (j < i)
+ *   d_i  = s_ii - sum_{t<i} l_it^2 d_t
+ * for symmetric indefinite blocks (Sec. 5: "incomplete Cholesky or LDL");
+ * no pivoting, a zero (or non-finite) pivot is a breakdown. */
+static int ildl0(const sp *S, sp *L) {
+  int st = ic0_pattern(S, L);
+  if (st != OR_OK) return st;
+  int n = S->nr;
+  for (int i = 0; i < n; i++) {
+    int b = L->rp[i], e = L->rp[i + 1];
+    for (int q = b; q < e - 1; q++) {
+      int j = L->ci[q];
+      double s = L->va[q];
+      int qa = b, qb = L->rp[j], eb = L->rp[j + 1] - 1;
+      while (qa < q && qb < eb) {
+        if (L->ci[qa] == L->ci[qb]) {
+          s -= L->va[qa] * L->va[L->rp[L->ci[qa] + 1] - 1] * L->va[qb];
+          qa++; qb++;
+        } else if (L->ci[qa] < L->ci[qb]) qa++;
+        else qb++;
+      }
+      L->va[q] = s / L->va[eb];
+    }
+    double d = L->va[e - 1];
+    for (int q = b; q < e - 1; q++) d -= L->va[q] * L->va[q] * L->va[L->rp[L->ci[q] + 1] - 1];
+    if (!(d != 0.0) || !isfinite(d)) return OR_BREAKDOWN;
+    L->va[e - 1] = d;
+  }
+  return OR_OK;
+}
+
+/* dense S = L D L^T without pivoting (row-major; unit L below the diagonal,
+ * d_j on it); a zero or non-finite pivot is a breakdown */
+static int ldl_dense(int n, double *a) {
+  for (int j = 0; j < n; j++) {
+    double d = a[(size_t)j * n + j];
+    for (int t = 0; t < j; t++) d -= a[(size_t)j * n + t] * a[(size_t)j * n + t] * a[(size_t)t * n + t];
+    if (!(d != 0.0) || !isfinite(d)) return OR_BREAKDOWN;
+    a[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; i++) {
+      double s = a[(size_t)i * n + j];
+      for (int t = 0; t < j; t++) s -= a[(size_t)i * n + t] * a[(size_t)t * n + t] * a[(size_t)j * n + t];
       a[(size_t)i * n + j] = s / d;
     }
   }
@@ -230,10 +295,36 @@ static int gauss_jordan_inverse(int n, double *a, double *inv) {
   return OR_OK;
 }
 
-/* solve (L L^T) x = b in place, b in elimination order */
+/* solve (L L^T) x = b, or (L D L^T) x = b, in place, b in elimination order */
 static void fac_solve(const blockfac *f, double *b) {
   int n = f->nb;
-  if (f->exact) {
+  if (f->ldl && f->exact) {
+    const double *D = f->D;
+    for (int i = 0; i < n; i++) {
+      double s = b[i];
+      for (int t = 0; t < i; t++) s -= D[(size_t)i * n + t] * b[t];
+      b[i] = s;
+    }
+    for (int i = 0; i < n; i++) b[i] /= D[(size_t)i * n + i];
+    for (int i = n - 1; i >= 0; i--) {
+      double s = b[i];
+      for (int t = i + 1; t < n; t++) s -= D[(size_t)t * n + i] * b[t];
+      b[i] = s;
+    }
+  } else if (f->ldl) {
+    const sp *L = &f->L;
+    for (int i = 0; i < n; i++) {          /* L y = b, unit diagonal */
+      double s = b[i];
+      int e = L->rp[i + 1] - 1;
+      for (int q = L->rp[i]; q < e; q++) s -= L->va[q] * b[L->ci[q]];
+      b[i] = s;
+    }
+    for (int i = 0; i < n; i++) b[i] /= L->va[L->rp[i + 1] - 1];
+    for (int i = n - 1; i >= 0; i--) {     /* L^T x = D^-1 y (column form) */
+      int e = L->rp[i + 1] - 1;
+      for (int q = L->rp[i]; q < e; q++) b[L->ci[q]] -= L->va[q] * b[i];
+    }
+  } else if (f->exact) {
     const double *D = f->D;
     for (int i = 0; i < n; i++) {
       double s = b[i];
@@ -847,6 +938,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     return OR_INVALID;
   if (lowrank_method < 0 || lowrank_method > 2 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
   if (lowrank_method == 2 && variant != 2) return OR_INVALID;   /* bidiagonalisation: DDLR-2 */
+  if (factor < 0 || factor > 3) return OR_INVALID;
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
     if (part[i] < 0 || part[i] >= p) return OR_INVALID;
@@ -1077,15 +1169,16 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     memset(&S, 0, sizeof S);
     sp_from_trips(&S, nb, t3, n3);
     free(t3); free(pos); sp_free(&B);
-    if (factor == 1) {
+    f->ldl = factor >= 2;
+    if (factor == 1 || factor == 3) {
       f->exact = 1;
       f->D = (double *)calloc((size_t)nb * nb + 1, sizeof(double));
       if (!f->D) { st = OR_NOMEM; sp_free(&S); break; }
       for (int r = 0; r < nb; r++)
         for (int q = S.rp[r]; q < S.rp[r + 1]; q++) f->D[(size_t)r * nb + S.ci[q]] = S.va[q];
-      st = chol_dense(nb, f->D);
+      st = factor == 3 ? ldl_dense(nb, f->D) : chol_dense(nb, f->D);
     } else {
-      st = ic0(&S, &f->L);
+      st = factor == 2 ? ildl0(&S, &f->L) : ic0(&S, &f->L);
     }
     sp_free(&S);
   }
