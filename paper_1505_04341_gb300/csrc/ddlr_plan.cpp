@@ -196,13 +196,29 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       for (int q = rp[i]; q < rp[i + 1]; q++)
         if (part[ci[q]] != part[i]) { iface[i] = 1; break; }
   });
+  // members of every block in ascending index: a counting sort over fixed
+  // row ranges (per-range counts, offsets, parallel fill)
   std::vector<std::vector<int>> members(p + 1);
   {
-    std::vector<int> msize(p + 1, 0);
-    for (int i = 0; i < n; i++) msize[iface[i] ? p : part[i]]++;
-    for (int b = 0; b <= p; b++) members[b].reserve(msize[b]);
+    const int nr = pool.size();
+    std::vector<int> rcnt(size_t(nr) * (p + 1), 0);
+    pool.run_dynamic(nr, [&](int t) {
+      int *c = rcnt.data() + size_t(t) * (p + 1);
+      for (long long i = n * (long long)t / nr; i < n * (long long)(t + 1) / nr; i++) c[iface[i] ? p : part[i]]++;
+    });
+    for (int b = 0; b <= p; b++) {
+      int tot = 0;
+      for (int t = 0; t < nr; t++) { const int c = rcnt[size_t(t) * (p + 1) + b]; rcnt[size_t(t) * (p + 1) + b] = tot; tot += c; }
+      members[b].resize(tot);
+    }
+    pool.run_dynamic(nr, [&](int t) {
+      int *c = rcnt.data() + size_t(t) * (p + 1);
+      for (long long i = n * (long long)t / nr; i < n * (long long)(t + 1) / nr; i++) {
+        const int b = iface[i] ? p : part[i];
+        members[b][c[b]++] = int(i);
+      }
+    });
   }
-  for (int i = 0; i < n; i++) members[iface[i] ? p : part[i]].push_back(i);
   int s = int(members[p].size());
   if (s == 0) { err = "no interface nodes (p = 1?)"; return DDLR_ERR_INVALID; }
   if (opt.rank_k < 1 || opt.rank_k > s) { err = "rank_k must be in [1, s]"; return DDLR_ERR_INVALID; }
@@ -595,27 +611,57 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   for (int l = 0; l < nlev; l++)
     P.lvl_slice0[l + 1] = P.lvl_slice0[l] + (P.lvl_nrows[l] + kSlice - 1) / kSlice;
   P.nslice = P.lvl_slice0[nlev];
-  // factorisation schedule by local level number (stable counting sort)
-  {
-    std::vector<int> lc(maxL, 0);
-    for (int g = 0; g < n; g++) lc[level_of[P.perm[g]]]++;
-    prefix(lc, P.fl_ptr);
-    P.fl_rows.resize(n);
-    std::vector<int> fill(P.fl_ptr.begin(), P.fl_ptr.end() - 1);
-    for (int g = 0; g < n; g++) P.fl_rows[fill[level_of[P.perm[g]]]++] = g;
+  // level records in (local level, block) order: level L of every block,
+  // blocks ascending.  A block's level-L rows are one contiguous record
+  // (record blk_lvl0[b] + L, since every level up to a block's last is
+  // non-empty), so this is the stable sort of the rows by local level: the
+  // factorisation schedule, and the order of the level-order descriptors
+  std::vector<int> lrec, lrec_out(1, 0);
+  lrec.reserve(nlev);
+  lrec_out.reserve(size_t(nlev) + 1);
+  P.fl_ptr.assign(maxL + 1, 0);
+  for (int L = 0; L < maxL; L++) {
+    for (int b = 0; b <= p; b++) {
+      const int rec = P.blk_lvl0[b] + L;
+      if (rec >= P.blk_lvl0[b + 1]) continue;
+      lrec.push_back(rec);
+      lrec_out.push_back(lrec_out.back() + P.lvl_nrows[rec]);
+    }
+    P.fl_ptr[L + 1] = lrec_out.back();
   }
+  P.fl_rows.resize(n);
+  pool.run(int(lrec.size()), [&](long long lo, long long hi) {
+    for (long long t = lo; t < hi; t++)
+      for (int i = 0; i < P.lvl_nrows[lrec[t]]; i++) P.fl_rows[lrec_out[t] + i] = P.lvl_row0[lrec[t]] + i;
+  }, 16);
   // upper (L^T) rows: for device row c, the factor entries (g, c), g != c,
   // in ascending g (flat CSR up_rp / up_q)
+  // The factor is block diagonal, so each block is transposed on its own
+  // (rows ascending inside a block give ascending g per column).
   std::vector<int> up_rp(n + 1, 0);
   pvec<int> up_q;
-  for (int g = 0; g < n; g++)
-    for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_rp[P.f_ci[q] + 1]++;
-  for (int c = 0; c < n; c++) up_rp[c + 1] += up_rp[c];
-  up_q.resize(up_rp[n]);
   {
-    std::vector<int> fill(up_rp.begin(), up_rp.end() - 1);
-    for (int g = 0; g < n; g++)
-      for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_q[fill[P.f_ci[q]]++] = q;
+    std::vector<int> boff(p + 2, 0);   // strictly lower entries of the blocks before b
+    for (int b = 0; b <= p; b++) {
+      const int r0 = P.blk_row0[b], r1 = P.blk_row0[b + 1];
+      boff[b + 1] = boff[b] + (P.f_rp[r1] - P.f_rp[r0]) - (r1 - r0);
+    }
+    up_q.resize(boff[p + 1]);
+    pool.run_dynamic(p + 1, [&](int bi) {
+      const int b = border[bi];
+      const int r0 = P.blk_row0[b], r1 = P.blk_row0[b + 1];
+      for (int g = r0; g < r1; g++)   // counts into up_rp[c + 1], c in this block
+        for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_rp[P.f_ci[q] + 1]++;
+      std::vector<int> fill(r1 - r0);
+      int run = boff[b];
+      for (int c = r0; c < r1; c++) {
+        fill[c - r0] = run;
+        run += up_rp[c + 1];
+        up_rp[c + 1] = run;
+      }
+      for (int g = r0; g < r1; g++)
+        for (int q = P.f_rp[g]; q < P.f_rp[g + 1] - 1; q++) up_q[fill[P.f_ci[q] - r0]++] = q;
+    });
   }
   auto upper_size = [&](int r) { return up_rp[r + 1] - up_rp[r]; };
   auto upper_at = [&](int r, int kk) { return up_q[up_rp[r] + kk]; };
@@ -717,25 +763,25 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
     }
   });
   {
-    const int maxL2 = int(P.fl_ptr.size()) - 1;
-    bool fits = true;
-    for (int g = 0; g < n && fits; g++) fits = P.l_span[2 * g + 1] < 65536 && P.u_span[2 * g + 1] < 65536;
+    std::atomic<bool> fits(true);
+    pool.run(n, [&](long long lo, long long hi) {
+      for (long long g = lo; g < hi; g++)
+        if (!(P.l_span[2 * g + 1] < 65536 && P.u_span[2 * g + 1] < 65536)) { fits = false; return; }
+    });
     if (fits) {
-      P.lv_ptr.assign(maxL2 + 1, 0);
-      P.lv_desc.reserve(4 * size_t(n));
-      for (int L = 0; L < maxL2; L++) {
-        for (int b = 0; b <= p; b++) {
-          const int rec = P.blk_lvl0[b] + L;
-          if (rec >= P.blk_lvl0[b + 1]) continue;
-          for (int r = P.lvl_row0[rec]; r < P.lvl_row0[rec] + P.lvl_nrows[rec]; r++) {
-            P.lv_desc.push_back(r);
-            P.lv_desc.push_back(P.l_span[2 * r]);
-            P.lv_desc.push_back(P.u_span[2 * r]);
-            P.lv_desc.push_back(P.l_span[2 * r + 1] | (P.u_span[2 * r + 1] << 16));
-          }
+      // the rows in (local level, block) order, as in the schedule
+      P.lv_ptr = P.fl_ptr;
+      P.lv_desc.resize(4 * size_t(n));
+      pool.run(n, [&](long long lo, long long hi) {
+        for (long long t = lo; t < hi; t++) {
+          const int r = P.fl_rows[t];
+          int *d = P.lv_desc.data() + 4 * t;
+          d[0] = r;
+          d[1] = P.l_span[2 * r];
+          d[2] = P.u_span[2 * r];
+          d[3] = P.l_span[2 * r + 1] | (P.u_span[2 * r + 1] << 16);
         }
-        P.lv_ptr[L + 1] = int(P.lv_desc.size() / 4);
-      }
+      });
     }
   }
   for (int b = 0; b < p; b++) {

@@ -94,7 +94,8 @@ struct Plan {
   // entries [lv_ptr[L], lv_ptr[L+1]), each {row, first slot of its L row,
   // first slot of its L^T row, L entries | L^T entries << 16}; empty when a
   // row has 65,536 entries or more (the chunk tables then serve alone)
-  std::vector<int> lv_ptr, lv_desc;
+  std::vector<int> lv_ptr;
+  pvec<int> lv_desc;
   // statistics
   int levels_interior = 0, levels_c = 0, ncolors = 0;
   long long nnz_ehat = 0, nnz_factor = 0;
