@@ -57,7 +57,13 @@ typedef struct {
   int theta_mode;          /* DDLR-1: 1 = theta = lambda_{k+1} (default, Sec. 5),
                               0 = theta = 0 (eq. Lambda-1)                         */
   int factor;              /* local solver: 0 = IC(0) on the block pattern,
-                              1 = exact Cholesky (IC on the symbolic fill pattern) */
+                              1 = exact Cholesky (IC on the symbolic fill pattern),
+                              2 = incomplete L D L^T on the block pattern, 3 =
+                              exact L D L^T (symbolic fill pattern); 2 and 3 do
+                              not pivot (a zero pivot is BREAKDOWN), serve
+                              indefinite blocks (Sec. 5), and need precision 0,
+                              c_solver 0 and lowrank_method 0 or 2; their
+                              right-hand sides are solved one at a time        */
   int c_order;             /* elimination order of C_a: 0 = ascending original
                               index, 1 = multicolour (the two colour classes of a
                               bipartite graph, else greedy colouring)              */

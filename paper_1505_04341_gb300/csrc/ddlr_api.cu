@@ -24,6 +24,7 @@
 #include "ddlr_mr.cuh"
 #include "ddlr_lbd.cuh"
 #include "ddlr_gmres.cuh"
+#include "ddlr_ldl.cuh"
 #include "ddlr_internal.h"
 #include "ddlr_kernels.cuh"
 #include "ddlr_plan.h"
@@ -531,6 +532,22 @@ template <typename T>
 void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
   const Plan &P = c->P;
   const T *lv = Prec<T>::l(c), *uv = Prec<T>::u(c), *di = Prec<T>::dinv(c);
+  if (c->opt.factor >= 2) {
+    // L D L^T factors: forward over the levels of all blocks, then backward
+    // with D^-1 (ddlr_ldl.cuh)
+    static_assert(kChunk == kChunkThreads, "level chunks are one row per thread");
+    const std::vector<int> &ptr = P.ch_all_ptr;
+    const int nL = int(ptr.size()) - 1;
+    const int4 *chk = reinterpret_cast<const int4 *>(c->chunks);
+    for (int s = 0; s < 2 * nL; s++) {
+      const int fwd = s < nL, L = fwd ? s : 2 * nL - 1 - s;
+      const int nch = ptr[L + 1] - ptr[L];
+      if (nch > 0)
+        KL(c, "sptrsv_levels", c->stream, k_ldl_sweep<T>, nch, kChunkThreads, 0, c->S, chk + ptr[L], fwd, lv, uv,
+           di, x, z, gate);
+    }
+    return;
+  }
   const bool cheb = c->opt.c_solver == 1;
   if (std::max(P.levels_interior, P.levels_c) <= kShallowLevels) {
     if (c->lv_desc) desc_sweeps<T>(c, c->stream, "sptrsv_levels", lv, uv, di, x, z, gate);
@@ -1516,8 +1533,12 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   for (int L = 0; L < nL; L++) {
     const int cnt = P.fl_ptr[L + 1] - P.fl_ptr[L];
     if (cnt == 0) continue;
-    KL(c, "factor", c->stream, k_ic_level, nblk(cnt), kThreads, 0, cnt, c->fl_rows + P.fl_ptr[L],
-       c->f_rp, c->f_ci, c->fval, c->dflag);
+    if (c->opt.factor >= 2)
+      KL(c, "factor", c->stream, k_ildl_level, nblk(cnt), kThreads, 0, cnt, c->fl_rows + P.fl_ptr[L],
+         c->f_rp, c->f_ci, c->fval, c->dflag);
+    else
+      KL(c, "factor", c->stream, k_ic_level, nblk(cnt), kThreads, 0, cnt, c->fl_rows + P.fl_ptr[L],
+         c->f_rp, c->f_ci, c->fval, c->dflag);
   }
   ck(cudaMemsetAsync(c->l64, 0, sizeof(double) * P.l_col.size(), c->stream), "memset");
   ck(cudaMemsetAsync(c->u64, 0, sizeof(double) * P.u_col.size(), c->stream), "memset");
@@ -1573,9 +1594,10 @@ void pz_setup(ddlr_ctx *c, int mmax) {
   const Plan &P = c->P;
   const char *env = getenv("DDLR_PERSIST");
   if (env && env[0] == '0') return;
-  // the persistent kernels solve with the factored C_a only; the Chebyshev
-  // C_a solve runs in the kernel-per-phase path
-  if (c->opt.c_solver != 0) return;
+  // the persistent kernels solve with Cholesky-factored C_a only; the
+  // Chebyshev and MR C_a solves and L D L^T factors run in the
+  // kernel-per-phase path
+  if (c->opt.c_solver != 0 || c->opt.factor >= 2) return;
   const bool force = env && env[0] == '1';
   const int nL = int(P.ch_all_ptr.size()) - 1;
   if (nL < 1 || nL > kPzMaxLevels || std::max(P.levels_interior, P.levels_c) > kShallowLevels) return;
@@ -2171,6 +2193,7 @@ inline unsigned eblk(long long cnt, int bd) { return (unsigned)((cnt + bd - 1) /
 // "solve column by column"
 inline int batch_width(const ddlr_ctx *c) {
   const int k = c->opt.rank_k;
+  if (c->opt.factor >= 2) return 0;   // L D L^T factors: one right-hand side at a time
   return k <= 64 ? std::min(kMaxR, 1024 / k) : 0;
 }
 
@@ -2581,7 +2604,9 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
   ddlr_options o;
   if (opt) o = *opt; else ddlr_options_default(&o);
   if ((o.variant != 1 && o.variant != 2) || !(o.alpha > 0) || (o.precision != 0 && o.precision != 1) ||
-      (o.factor != 0 && o.factor != 1) || (o.c_order != 0 && o.c_order != 1) ||
+      o.factor < 0 || o.factor > 3 ||
+      (o.factor >= 2 && (o.precision != 0 || o.c_solver != 0 || o.lowrank_method == 1)) ||
+      (o.c_order != 0 && o.c_order != 1) ||
       (o.b_order != 0 && o.b_order != 1) || o.rank_k < 1 ||
       o.rank_k > 256 || o.c_solver < 0 || o.c_solver > 2 ||
       (o.c_solver == 2 && (o.mr_iters < 0 || o.mr_lfil < 1 || o.mr_lfil >= kMrCap ||

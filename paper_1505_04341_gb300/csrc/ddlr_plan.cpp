@@ -228,7 +228,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
   for (int b = 0; b <= p; b++)
     for (int t = 0; t < int(members[b].size()); t++) { blk_of[members[b][t]] = b; loc[members[b][t]] = t; }
 
-  const bool exact = opt.factor == 1;
+  const bool exact = opt.factor == 1 || opt.factor == 3;   // symbolic fill pattern
   P.perm.resize(n); P.iperm.resize(n);
   P.blk_row0.assign(p + 2, 0);
   for (int b = 0; b <= p; b++) P.blk_row0[b + 1] = P.blk_row0[b] + int(members[b].size());

@@ -44,28 +44,9 @@ def indef_a0():
     return A, part, p, D, A0
 
 
-def _nine_point(N, sigma):
-    """9-point stencil (diagonal 8 - sigma, -1 to the 8 neighbours): its
-    graph has triangles, so ILDL(0) has update terms inside the pattern,
-    which the 5-point stencil never has."""
-    rows, cols, vals = [], [], []
-    for y in range(N):
-        for x in range(N):
-            i = y * N + x
-            rows.append(i); cols.append(i); vals.append(8.0 - sigma)
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    if (dx or dy) and 0 <= x + dx < N and 0 <= y + dy < N:
-                        rows.append(i); cols.append((y + dy) * N + x + dx); vals.append(-1.0)
-    import scipy.sparse as sps
-    S = sps.csr_matrix((vals, (rows, cols)), shape=(N * N, N * N))
-    S.sort_indices()
-    return N * N, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64)
-
-
 @pytest.fixture(scope="module")
 def nine_point():
-    A = _nine_point(12, 2.0)
+    A = W.nine_point(12, 2.0)
     part, p = W.box_partition((12, 12), (2, 2))
     D = DenseDDLR(A, part, p)
     A0 = D.to_original(D.A0)

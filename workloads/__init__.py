@@ -107,6 +107,23 @@ def shifted_laplacian(shape, sigma: float) -> tuple:
     return n, rp, ci, va
 
 
+def nine_point(N: int, sigma: float = 0.0) -> tuple:
+    """2-D N x N 9-point stencil: diagonal 8 - sigma, -1 to the 8 neighbours
+    (Dirichlet).  Its graph has triangles, unlike the 5/7-point Laplacians,
+    so incomplete factorisations on its pattern have update terms inside the
+    pattern."""
+    rows, cols, vals = [], [], []
+    for y in range(N):
+        for x in range(N):
+            i = y * N + x
+            rows.append(i); cols.append(i); vals.append(8.0 - sigma)
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if (dx or dy) and 0 <= x + dx < N and 0 <= y + dy < N:
+                        rows.append(i); cols.append((y + dy) * N + x + dx); vals.append(-1.0)
+    return _coo_to_csr(N * N, np.array(rows), np.array(cols), np.array(vals))
+
+
 def box_partition(shape, parts) -> tuple[np.ndarray, int]:
     """Split each grid axis into ``parts[a]`` equal ranges (cut at floor(i*N/P)).
 
