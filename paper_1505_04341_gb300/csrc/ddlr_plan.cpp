@@ -573,7 +573,7 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       std::vector<std::array<int, 3>> pairs;
       for (int g = int(lo); g < int(hi); g++) {
         const int i = P.perm[g];
-        if (blk_of[i] >= p) continue;
+        if (blk_of[i] >= p || P.f_prp[P.f_rp[g + 1]] == P.f_prp[P.f_rp[g]]) continue;   // no terms in this row
         row_pairs(i, pairs);
         if (pairs.empty()) continue;
         for (long long e = P.f_rp[g]; e < P.f_rp[g + 1]; e++) {
