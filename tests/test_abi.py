@@ -78,3 +78,21 @@ def test_null_handle_calls(lib):
     assert lib.ddlr_destroy(None) == 0
     assert lib.ddlr_apply(None, None, None, 1, 1) == 1
     assert lib.ddlr_get_info(None, None) == 1
+
+
+def test_setup_rejects_bad_option_combinations_on_host(lib):
+    """Option validation runs before any device work: the values and the
+    combinations the library does not serve are INVALID (status 1)."""
+    A = W.laplacian((8, 8))
+    part, p = W.box_partition((8, 8), (2, 2))
+    for kw in (dict(factor=4), dict(factor=-1), dict(factor=2, precision=1), dict(factor=3, c_solver=1),
+               dict(factor=2, c_solver=2), dict(factor=3, lowrank_method=1), dict(indefinite=2),
+               dict(lowrank_method=2, variant=1), dict(lowrank_method=3), dict(c_solver=3),
+               dict(c_solver=2, mr_iters=4, mr_lfil=8), dict(c_solver=1, cheb_steps=0),
+               dict(lowrank_method=1, rand_oversample=-1), dict(precision=2), dict(alpha=0.0)):
+        st, msg = _setup_status(lib, A, part, p, rank_k=2, **kw)
+        assert st == 1, kw
+
+
+def test_gmres_entry_point_rejects_null_handle(lib):
+    assert lib.ddlr_gmres(None, None, None, 1e-8, 10, 40, None) == 1
