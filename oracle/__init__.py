@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, I, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, I, I, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -97,6 +97,8 @@ class Oracle:
     Options follow the library's: variant 1/2, rank k, alpha, theta_mode
     (1: theta = Ritz_{k+1}, 0: theta = 0), factor (0: IC(0), 1: exact
     Cholesky, 2: incomplete LDL^T on the pattern, 3: exact LDL^T),
+    fill_level (incomplete factors: the level of fill of their pattern, 0 =
+    the pattern of A0),
     c_order (0: ascending index, 1: greedy multicolour) of C_a, b_order (the
     same choice for the interior blocks), scale_diag,
     lanczos_max (0: 5k), lanczos_check (10), lanczos_eps (1e-4), seed,
@@ -116,7 +118,7 @@ class Oracle:
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
                  cheb_steps=5, cheb_lanczos=20, lowrank_method=0, rand_oversample=10,
-                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3, indefinite=0):
+                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3, indefinite=0, fill_level=0):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -131,7 +133,7 @@ class Oracle:
                           float(lanczos_eps), int(seed), int(c_solver),
                           int(cheb_steps), int(cheb_lanczos), int(lowrank_method),
                           int(rand_oversample), int(rand_power), int(mr_iters), int(mr_lfil),
-                          float(mr_droptol), int(indefinite), ctypes.byref(h))
+                          float(mr_droptol), int(indefinite), int(fill_level), ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h

@@ -15,8 +15,9 @@
  *   - Sec. 3.1 (eq. EF, split): E = [a^-1 Ehat ; -a I],
  *     A0 = blkdiag(B + a^-2 Ehat Ehat^T, C + a^2 I), A = A0 - E E^T;
  *   - Sec. 4.1, 5: local solvers = incomplete Cholesky IC(0) on the pattern
- *     (or exact Cholesky, dense), or for indefinite blocks incomplete LDL^T on
- *     the pattern (or exact LDL^T, dense, no pivoting), one factor per
+ *     (or on the level-of-fill pattern of a given level, or exact Cholesky,
+ *     dense), or for indefinite blocks incomplete LDL^T on the same patterns
+ *     (or exact LDL^T, dense, no pivoting), one factor per
  *     B_{i,a} and one for C_a, each in its elimination order (ascending
  *     index, or multicolour);
  *   - Sec. 4.4 (eq. converge): Lanczos on H = E^T A0^-1 E (DDLR-1) or on
@@ -211,6 +212,57 @@ static int chol_dense(int n, double *a) {
   for (int i = 0; i < n; i++)
     for (int j = i + 1; j < n; j++) a[(size_t)i * n + j] = 0.0;
   return OR_OK;
+}
+
+/* The pattern of an incomplete factor with level of fill kf (the symmetric
+ * form of the level-of-fill rule): entries of S have level 0; entry (i, j),
+ * j < i, of the up-looking factor receives level lev(i,t) + lev(j,t) + 1 for
+ * every t < j with (i, t) and (j, t) in the pattern, the smallest one
+ * counting, and is kept when that level is <= kf.  Rows are built in order,
+ * columns ascending, every row scanning all earlier columns: slow and plain.
+ * out = S plus an explicit zero at every kept fill position (lower part). */
+static int fill_pattern(const sp *S, int kf, sp *out) {
+  int n = S->nr;
+  const int INF = 1 << 29;
+  int **kc = (int **)calloc((size_t)n + 1, sizeof(int *));   /* kept columns of each row, ascending */
+  int **kl = (int **)calloc((size_t)n + 1, sizeof(int *));   /* and their levels */
+  int *kn = (int *)calloc((size_t)n + 1, sizeof(int));
+  int *lev = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  long nfill = 0;
+  for (int i = 0; i < n; i++) {
+    for (int c = 0; c < i; c++) lev[c] = INF;
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++)
+      if (S->ci[q] < i) lev[S->ci[q]] = 0;
+    int cnt = 0;
+    for (int j = 0; j < i; j++) {
+      /* row j's kept entries (j, t), t < j, against row i's kept (i, t) */
+      for (int a = 0; a < kn[j]; a++) {
+        int t = kc[j][a];
+        if (lev[t] <= kf && lev[t] + kl[j][a] + 1 < lev[j]) lev[j] = lev[t] + kl[j][a] + 1;
+      }
+      if (lev[j] <= kf) cnt++;
+    }
+    kc[i] = (int *)malloc(sizeof(int) * (size_t)(cnt > 0 ? cnt : 1));
+    kl[i] = (int *)malloc(sizeof(int) * (size_t)(cnt > 0 ? cnt : 1));
+    for (int j = 0; j < i; j++)
+      if (lev[j] <= kf) {
+        kc[i][kn[i]] = j; kl[i][kn[i]] = lev[j]; kn[i]++;
+        if (lev[j] > 0) nfill++;
+      }
+  }
+  long nt = S->rp[n] + nfill;
+  trip *t = (trip *)malloc(sizeof(trip) * (size_t)(nt > 0 ? nt : 1));
+  long w = 0;
+  for (int i = 0; i < n; i++) {
+    for (int q = S->rp[i]; q < S->rp[i + 1]; q++) { t[w].r = i; t[w].c = S->ci[q]; t[w].v = S->va[q]; w++; }
+    for (int a = 0; a < kn[i]; a++)
+      if (kl[i][a] > 0) { t[w].r = i; t[w].c = kc[i][a]; t[w].v = 0.0; w++; }
+  }
+  memset(out, 0, sizeof *out);
+  int st = sp_from_trips(out, n, t, w);
+  for (int i = 0; i < n; i++) { free(kc[i]); free(kl[i]); }
+  free(kc); free(kl); free(kn); free(lev); free(t);
+  return st;
 }
 
 /* incomplete LDL^T of S on its lower pattern P (same storage as ic0, d_i in
@@ -929,7 +981,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
              int lowrank_method, int rand_oversample, int rand_power, int mr_iters, int mr_lfil,
-             double mr_droptol, int indefinite, void **out) {
+             double mr_droptol, int indefinite, int fill_level, void **out) {
   *out = NULL;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
     return OR_INVALID;
@@ -938,7 +990,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     return OR_INVALID;
   if (lowrank_method < 0 || lowrank_method > 2 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
   if (lowrank_method == 2 && variant != 2) return OR_INVALID;   /* bidiagonalisation: DDLR-2 */
-  if (factor < 0 || factor > 3) return OR_INVALID;
+  if (factor < 0 || factor > 3 || fill_level < 0) return OR_INVALID;
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
     if (part[i] < 0 || part[i] >= p) return OR_INVALID;
@@ -1177,6 +1229,11 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
       for (int r = 0; r < nb; r++)
         for (int q = S.rp[r]; q < S.rp[r + 1]; q++) f->D[(size_t)r * nb + S.ci[q]] = S.va[q];
       st = factor == 3 ? ldl_dense(nb, f->D) : chol_dense(nb, f->D);
+    } else if (fill_level > 0) {
+      sp F;
+      st = fill_pattern(&S, fill_level, &F);
+      if (st == OR_OK) st = factor == 2 ? ildl0(&F, &f->L) : ic0(&F, &f->L);
+      sp_free(&F);
     } else {
       st = factor == 2 ? ildl0(&S, &f->L) : ic0(&S, &f->L);
     }
