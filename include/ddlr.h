@@ -117,6 +117,13 @@ typedef struct {
                               singular G_{k,theta} or I - K gives BREAKDOWN.  The
                               local factors stay IC(0) / Cholesky, so A0 must be
                               positive definite (else BREAKDOWN).  Default 0.   */
+  int fill_level;          /* incomplete factors (factor 0 and 2): the level of
+                              fill of their pattern -- A0's entries have level
+                              0, eliminating pivot t gives entry (i, j) of two
+                              later neighbours of t the level lev(i,t) +
+                              lev(j,t) + 1, and entries up to this level are
+                              kept.  Default 0 (the pattern of A0); 0..64;
+                              INVALID with factor 1 or 3.                      */
 } ddlr_options;
 
 typedef struct {

@@ -990,7 +990,8 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
     return OR_INVALID;
   if (lowrank_method < 0 || lowrank_method > 2 || rand_oversample < 0 || rand_power < 0) return OR_INVALID;
   if (lowrank_method == 2 && variant != 2) return OR_INVALID;   /* bidiagonalisation: DDLR-2 */
-  if (factor < 0 || factor > 3 || fill_level < 0) return OR_INVALID;
+  if (factor < 0 || factor > 3 || fill_level < 0 || (fill_level > 0 && (factor == 1 || factor == 3)))
+    return OR_INVALID;
   for (int i = 0; i < n; i++) {
     if (rowptr[i + 1] < rowptr[i]) return OR_INVALID;
     if (part[i] < 0 || part[i] >= p) return OR_INVALID;

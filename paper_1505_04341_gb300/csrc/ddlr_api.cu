@@ -2592,6 +2592,7 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->mr_lfil = 8;
   o->mr_droptol = 1e-3;
   o->indefinite = 0;
+  o->fill_level = 0;
   return DDLR_OK;
 }
 
@@ -2614,7 +2615,8 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
       (o.c_solver == 1 && (o.cheb_steps < 1 || o.cheb_steps > kChebMaxSteps || o.cheb_lanczos < 1 ||
                            o.cheb_lanczos > 1000)) ||
       o.lowrank_method < 0 || o.lowrank_method > 2 || (o.lowrank_method == 2 && o.variant != 2) ||
-      (o.indefinite != 0 && o.indefinite != 1) ||
+      (o.indefinite != 0 && o.indefinite != 1) || o.fill_level < 0 || o.fill_level > 64 ||
+      (o.fill_level > 0 && (o.factor == 1 || o.factor == 3)) ||
       (o.lowrank_method == 1 && (o.rand_oversample < 0 || o.rand_power < 0 || o.rand_power > 100 ||
                                  o.rank_k + o.rand_oversample > kRandMaxL))) {
     g_setup_error = "invalid options";

@@ -336,6 +336,41 @@ ddlr_status build_plan(int n, const int *rp, const int *ci, const double *val,
       std::sort(lci.begin() + l0, lci.end());
       lrp[e + 1] = int(lci.size());
     }
+    if (!exact && opt.fill_level > 0) {
+      // level-of-fill pattern: the block's entries have level 0, and
+      // eliminating pivot t gives entry (i, j) of two later neighbours of t
+      // the level lev(i,t) + lev(j,t) + 1; entries of level <= fill_level
+      // are kept (only kept entries produce fill).  Column lists of
+      // (row, level), complete when their pivot is reached.
+      const int kf = opt.fill_level;
+      std::vector<std::vector<std::pair<int, int>>> colv(nb);
+      for (int e = 0; e < nb; e++)
+        for (int q = lrp[e]; q < lrp[e + 1]; q++) colv[lci[q]].push_back({e, 0});
+      long long total = 0;
+      for (int t = 0; t < nb; t++) {
+        std::vector<std::pair<int, int>> &c = colv[t];
+        std::sort(c.begin(), c.end());
+        size_t w = 0;   // one entry per row, its smallest level
+        for (size_t a = 0; a < c.size(); a++) {
+          if (w > 0 && c[w - 1].first == c[a].first) continue;
+          c[w++] = c[a];
+        }
+        c.resize(w);
+        total += (long long)w;
+        if (total > 60000000LL) { blk_err[b] = "fill pattern too large"; return; }
+        for (size_t x = 1; x < c.size(); x++)
+          for (size_t y = 0; y < x; y++) {
+            const int lv = c[x].second + c[y].second + 1;
+            if (lv <= kf) colv[c[y].first].push_back({c[x].first, lv});
+          }
+      }
+      std::vector<int> rc(nb + 1, 0);
+      for (int j = 0; j < nb; j++) for (const auto &pr : colv[j]) rc[pr.first + 1]++;
+      for (int e = 0; e < nb; e++) rc[e + 1] += rc[e];
+      lrp = rc;
+      lci.assign(rc[nb], 0);
+      for (int j = 0; j < nb; j++) for (const auto &pr : colv[j]) lci[rc[pr.first]++] = j;   // ascending j per row
+    }
     if (exact) {
       // symbolic Cholesky: struct(L_{*j}) = struct(A_{*j}) U struct of the
       // children of j in the elimination tree, minus j

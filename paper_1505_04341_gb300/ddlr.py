@@ -39,7 +39,7 @@ class ddlr_options(ctypes.Structure):
                 ("cheb_lanczos", ctypes.c_int), ("lowrank_method", ctypes.c_int),
                 ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int),
                 ("mr_iters", ctypes.c_int), ("mr_lfil", ctypes.c_int), ("mr_droptol", ctypes.c_double),
-                ("indefinite", ctypes.c_int)]
+                ("indefinite", ctypes.c_int), ("fill_level", ctypes.c_int)]
 
 
 class ddlr_info(ctypes.Structure):

@@ -4,7 +4,7 @@
 // them against the definitions on the CPU (no GPU, no CUDA runtime).
 //
 // Input (native-endian int32 unless noted):
-//   n, nnz, p, variant, rank_k, factor, c_order, b_order, c_solver,
+//   n, nnz, p, variant, rank_k, factor, c_order, b_order, c_solver, fill_level,
 //   rowptr[n+1], colind[nnz], val[nnz] (float64), part[n]
 // Output: status, then records {name length, name bytes, count, int32[count]}
 // and a final record of length 0.
@@ -35,7 +35,7 @@ int main(int argc, char **argv) {
   if (argc != 3) return 2;
   FILE *in = std::fopen(argv[1], "rb");
   if (!in) return 2;
-  int hdr[9];
+  int hdr[10];
   if (!rd(in, hdr, sizeof hdr)) return 2;
   const int n = hdr[0], nnz = hdr[1], p = hdr[2];
   std::vector<int> rp(n + 1), ci(nnz), part(n);
@@ -54,6 +54,7 @@ int main(int argc, char **argv) {
   o.c_order = hdr[6];
   o.b_order = hdr[7];
   o.c_solver = hdr[8];
+  o.fill_level = hdr[9];
   o.lanczos_check = 10;
   o.lanczos_eps = 1e-4;
   o.max_nrhs = 1;

@@ -59,12 +59,12 @@ def probe():
     return exe
 
 
-def run_plan(probe, A, part, p, tag, variant=1, k=2, factor=0, c_order=0, b_order=0, c_solver=0):
+def run_plan(probe, A, part, p, tag, variant=1, k=2, factor=0, c_order=0, b_order=0, c_solver=0, fill_level=0):
     n, rp, ci, va = A
     d = os.path.join(HERE, "_build")
     fin, fout = os.path.join(d, f"plan_in_{tag}.bin"), os.path.join(d, f"plan_out_{tag}.bin")
     with open(fin, "wb") as f:
-        np.array([n, len(ci), p, variant, k, factor, c_order, b_order, c_solver], np.int32).tofile(f)
+        np.array([n, len(ci), p, variant, k, factor, c_order, b_order, c_solver, fill_level], np.int32).tofile(f)
         np.asarray(rp, np.int32).tofile(f)
         np.asarray(ci, np.int32).tofile(f)
         np.asarray(va, np.float64).tofile(f)
@@ -152,7 +152,31 @@ def _two_colour(nodes, edges):
     return col
 
 
-def check_plan(P, A, part, p, factor, c_order, b_order, c_solver):
+def _level_pairs(order, edges, k):
+    """Entries (later, earlier) of the level-k incomplete factor for the
+    elimination order `order` (a list of nodes): the graph's edges have level
+    0; pivot t gives each pair of its later neighbours i, j the level
+    lev(i,t) + lev(j,t) + 1, the smallest counting, kept up to k."""
+    pos = {v: e for e, v in enumerate(order)}
+    col = {v: {} for v in order}            # column t -> {later row: level}
+    for a, b in edges:
+        lo, hi = (a, b) if pos[a] < pos[b] else (b, a)
+        col[lo][hi] = 0
+    out = set()
+    for t in order:
+        ent = sorted(col[t].items(), key=lambda kv: pos[kv[0]])
+        for i, lv in ent:
+            out.add((i, t))
+        for x in range(len(ent)):
+            for y in range(x):
+                (i, li), (j, lj) = ent[x], ent[y]
+                cand = li + lj + 1
+                if cand <= k and cand < col[j].get(i, k + 1):
+                    col[j][i] = cand
+    return out
+
+
+def check_plan(P, A, part, p, factor, c_order, b_order, c_solver, fill_level=0):
     n, rp, ci, va = A
     rows = _rows(A)
     part = np.asarray(part)
@@ -182,8 +206,19 @@ def check_plan(P, A, part, p, factor, c_order, b_order, c_solver):
             level[g] = 1 + max((level[c] for c in cols[:-1]), default=-1)
         pairs = {(int(iperm[max(i, j)]), int(iperm[min(i, j)])) for i, j in edges}
         pairs = {(max(a, c), min(a, c)) for a, c in pairs}
-        if factor == 0:
+        if factor == 0 and fill_level == 0:
             assert lower == pairs
+        elif factor == 0:
+            # level-of-fill pattern in the block's elimination order
+            nodes = [int(x) for x in mem]
+            if order == 0:
+                eo = sorted(nodes)
+            else:
+                col = _two_colour(set(nodes), edges)
+                eo = None if col is None else sorted(nodes, key=lambda v: (col[v], v))
+            if eo is not None:
+                want = {(int(iperm[i]), int(iperm[j])) for i, j in _level_pairs(eo, edges, fill_level)}
+                assert pairs <= want and lower == want
         else:
             # exact: the pattern of a dense Cholesky factor of a matrix with
             # the block's graph (random weights, diagonally dominant), in the
@@ -207,7 +242,7 @@ def check_plan(P, A, part, p, factor, c_order, b_order, c_solver):
             col = _two_colour(set(int(x) for x in mem), edges)
             if col is not None:
                 assert all(col[int(perm[c])] == 0 and col[int(perm[g])] == 1 for g, c in pairs)
-                if b == p and edges and factor == 0:
+                if b == p and edges and factor == 0 and fill_level == 0:
                     assert sc[6] == 2 and sc[5] == 2   # two colours, two levels
     f_src = P["f_src"]
     for g in range(n):
@@ -313,6 +348,17 @@ CASES = {
     "2d_20x16_mr": lambda: (W.laplacian((20, 16)),) + W.box_partition((20, 16), (2, 2)) + (0, 1, 1, 2),
 }
 
+FILL_CASES = {
+    "2d_20x16_fill1_natural": lambda: (W.laplacian((20, 16)),) + W.box_partition((20, 16), (2, 2)) + (0, 0, 0, 0, 1),
+    "2d_20x16_fill2_multicolour": lambda: (W.laplacian((20, 16)),) + W.box_partition((20, 16), (2, 2))
+    + (0, 1, 1, 0, 2),
+    "3d_10_fill2_natural": lambda: (W.laplacian((10, 10, 10)),) + W.box_partition((10, 10, 10), (2, 2, 2))
+    + (0, 0, 0, 0, 2),
+    "9pt_14_fill1_natural": lambda: (W.nine_point(14, 0.0),) + W.box_partition((14, 14), (2, 2)) + (0, 0, 0, 0, 1),
+    "2d_20x16_fill3_ldl": lambda: (W.shifted_laplacian((20, 16), 1.0),) + W.box_partition((20, 16), (2, 2))
+    + (2, 0, 1, 0, 3),
+}
+
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_plan_matches_definitions(probe, name):
@@ -320,6 +366,15 @@ def test_plan_matches_definitions(probe, name):
     P = run_plan(probe, A, part, p, name, factor=factor, c_order=c_order, b_order=b_order, c_solver=c_solver)
     assert P["status"] == 0, P.get("error")
     check_plan(P, A, part, p, factor, c_order, b_order, c_solver)
+
+
+@pytest.mark.parametrize("name", list(FILL_CASES))
+def test_fill_plan_matches_definitions(probe, name):
+    A, part, p, factor, c_order, b_order, c_solver, fill = FILL_CASES[name]()
+    P = run_plan(probe, A, part, p, name, factor=factor, c_order=c_order, b_order=b_order, c_solver=c_solver,
+                 fill_level=fill)
+    assert P["status"] == 0, P.get("error")
+    check_plan(P, A, part, p, 0 if factor == 2 else factor, c_order, b_order, c_solver, fill_level=fill)
 
 
 def test_plan_errors(probe):
