@@ -344,6 +344,22 @@ struct ddlr_ctx {
 
 namespace {
 
+// The dynamic shared-memory limit of a kernel (cudaFuncSetAttribute) holds
+// per device for the whole process, for every handle: it is only ever
+// raised, so that a handle created later with a smaller need does not leave
+// an earlier handle's launches above the limit.
+void raise_smem_limit(const void *fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> limit;
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &cur = limit[{fn, dev}];
+  if (bytes <= cur) return;
+  ck(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)), "attr");
+  cur = bytes;
+}
+
 template <typename T>
 size_t sf_smem_bytes(const Plan &P) {
   return ((size_t(P.tma_zs) * sizeof(T) + 15) & ~size_t(15)) + size_t(P.tma_zs) * 4;
@@ -1616,7 +1632,7 @@ void pz_setup(ddlr_ctx *c, int mmax) {
                                            : (const void *)k_pcg_persist<kPzThreads, float, float>;
   ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pcg_fn, kPzThreads, sp), "occupancy");
   if (sl <= size_t(optin)) {
-    ck(cudaFuncSetAttribute(k_lz_persist<kPzThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sl)), "attr");
+    raise_smem_limit((const void *)k_lz_persist<kPzThreads>, sl);
     ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, k_lz_persist<kPzThreads>, kPzThreads, sl), "occupancy");
   }
   c->pz_grid = sms;
@@ -1779,11 +1795,9 @@ void allocate(ddlr_ctx *c) {
     c->use_tma64 = !off && !c->use_sf64 && tma_config<double>(P, c->tma64);
     c->use_tma32 = !off && !c->use_sf32 && tma_config<float>(P, c->tma32);
     if (c->use_sf64)
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_sf<double, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(sf_smem_bytes<double>(P))), "attr");
+      raise_smem_limit((const void *)k_sptrsv_blocks_sf<double, 256, 4>, sf_smem_bytes<double>(P));
     if (c->use_sf32)
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_sf<float, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(sf_smem_bytes<float>(P))), "attr");
+      raise_smem_limit((const void *)k_sptrsv_blocks_sf<float, 256, 4>, sf_smem_bytes<float>(P));
     ck(cudaFuncSetAttribute(k_tridiag_values, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10), "attr");
     ck(cudaFuncSetAttribute(k_w_rhs_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(urows_smem_bytes(64))),
        "attr");
@@ -1792,11 +1806,9 @@ void allocate(ddlr_ctx *c) {
     ck(cudaFuncSetAttribute(k_u_add_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, int(urows_smem_bytes(64))),
        "attr");
     if (c->use_tma64)
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<double, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(tma_smem_bytes<double>(c->tma64))), "attr");
+      raise_smem_limit((const void *)k_sptrsv_blocks_tma<double, 256>, tma_smem_bytes<double>(c->tma64));
     if (c->use_tma32)
-      ck(cudaFuncSetAttribute(k_sptrsv_blocks_tma<float, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(tma_smem_bytes<float>(c->tma32))), "attr");
+      raise_smem_limit((const void *)k_sptrsv_blocks_tma<float, 256>, tma_smem_bytes<float>(c->tma32));
   }
   c->eh64 = c->alloc<double>(P.eh_ci.size());
   c->eht64 = c->alloc<double>(P.eht_ci.size());
