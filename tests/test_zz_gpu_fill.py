@@ -3,7 +3,11 @@ factor 0 or 2) against the oracle, through the C ABI: factor entries and the
 A0 solve within 1e-12, PCG (or GMRES for the indefinite case) within one
 iteration of the oracle's and the true residual; the level patterns
 themselves are checked on the CPU (planner and oracle against the
-definition)."""
+definition).
+
+Collected after the other GPU files: its only GPU run so far came before
+the fix of the process-wide shared-memory limits, so a failure here should
+not stop the files that have run green."""
 import numpy as np
 import pytest
 
