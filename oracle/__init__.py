@@ -55,7 +55,7 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.or_setup.argtypes = [I, P, P, P, P, I, I, I, D, I, I, I, I, I, I, I, D,
-                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, I, I, ctypes.POINTER(P)]
+                                 ctypes.c_ulonglong, I, I, I, I, I, I, I, I, D, I, I, I, ctypes.POINTER(P)]
         lib.or_setup.restype = I
         lib.or_destroy.argtypes = [P]
         lib.or_apply.argtypes = [P, P, P]
@@ -76,6 +76,8 @@ def _load():
         lib.or_factor_coo.argtypes = [P, P, P, P]
         lib.or_cheb_bounds.argtypes = [P, P]
         lib.or_set_cheb_bounds.argtypes = [P, D, D]
+        lib.or_reorth_passes.argtypes = [P]
+        lib.or_reorth_passes.restype = ctypes.c_long
         lib.or_sm64_pm1.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong]
         lib.or_sm64_pm1.restype = D
         _lib = lib
@@ -111,14 +113,17 @@ class Oracle:
     iterations, at most mr_lfil entries per column of Z and drop tolerance
     mr_droptol relative to the column norm.  indefinite=1 accepts a
     preconditioner that is not SPD (Ritz values >= 1 for DDLR-1, an
-    indefinite I - K for DDLR-2) for use with GMRES.
+    indefinite I - K for DDLR-2) for use with GMRES.  lanczos_reorth: 0 = a
+    second Gram-Schmidt pass only when the first shrank the Lanczos vector
+    below 1/sqrt(2) of its norm, 1 = always two passes.
     """
 
     def __init__(self, A, part, p, *, variant=1, k=8, alpha=1.0, theta_mode=1,
                  factor=0, c_order=0, b_order=0, scale_diag=0, lanczos_max=0,
                  lanczos_check=10, lanczos_eps=1e-4, seed=0, c_solver=0,
                  cheb_steps=5, cheb_lanczos=20, lowrank_method=0, rand_oversample=10,
-                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3, indefinite=0, fill_level=0):
+                 rand_power=2, mr_iters=3, mr_lfil=6, mr_droptol=1e-3, indefinite=0, fill_level=0,
+                 lanczos_reorth=0):
         lib = _load()
         n, rp, ci, va = A
         self._keep = [np.ascontiguousarray(rp, dtype=np.int32),
@@ -133,7 +138,8 @@ class Oracle:
                           float(lanczos_eps), int(seed), int(c_solver),
                           int(cheb_steps), int(cheb_lanczos), int(lowrank_method),
                           int(rand_oversample), int(rand_power), int(mr_iters), int(mr_lfil),
-                          float(mr_droptol), int(indefinite), int(fill_level), ctypes.byref(h))
+                          float(mr_droptol), int(indefinite), int(fill_level), int(lanczos_reorth),
+                          ctypes.byref(h))
         if st != 0:
             raise OracleError(st, "setup")
         self._h = h
@@ -194,6 +200,11 @@ class Oracle:
         st = _load().or_gmres(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), int(restart),
                               ctypes.byref(its), ctypes.byref(rel))
         return x, its.value, rel.value, STATUS.get(st, st)
+
+    @property
+    def reorth_passes(self):
+        """Gram-Schmidt passes taken by the Lanczos steps of the setup"""
+        return int(_load().or_reorth_passes(self._h))
 
     @property
     def ritz(self):

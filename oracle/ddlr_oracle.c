@@ -424,6 +424,10 @@ typedef struct {
   double theta;
   double *Hk;      /* k x k (DDLR-2) */
   int msteps;      /* Lanczos steps */
+  int reorth2;     /* 1: two Gram-Schmidt passes every Lanczos step; 0: the
+                      second pass only on cancellation (cgs_reorth) */
+  long reorth_passes;  /* Gram-Schmidt passes of the Lanczos steps (not the
+                          restart vectors, which always take two) */
   double *ritz;    /* all Ritz values of T_m, descending */
   int ncolors;     /* colours of C_a (c_order 1) */
   double *work;    /* n scratch */
@@ -729,19 +733,41 @@ static double topk_sum(int m, const double *al, const double *be, int k) {
   return s;
 }
 
+/* one classical Gram-Schmidt pass: w -= Q_j (Q_j^T w) */
+static void cgs_pass(int s, int j, const double *Q, double *w, double *c) {
+  for (int i = 0; i < j; i++) c[i] = dot(s, Q + (size_t)i * s, w);
+  for (int i = 0; i < j; i++)
+    for (int r = 0; r < s; r++) w[r] -= c[i] * Q[(size_t)i * s + r];
+}
+
 /* w -= Q_j (Q_j^T w), twice (classical Gram-Schmidt, two passes) */
 static void cgs2(int s, int j, const double *Q, double *w, double *c) {
-  for (int pass = 0; pass < 2; pass++) {
-    for (int i = 0; i < j; i++) c[i] = dot(s, Q + (size_t)i * s, w);
-    for (int i = 0; i < j; i++)
-      for (int r = 0; r < s; r++) w[r] -= c[i] * Q[(size_t)i * s + r];
+  cgs_pass(s, j, Q, w, c);
+  cgs_pass(s, j, Q, w, c);
+}
+
+/* Full reorthogonalisation of the Lanczos vector w against Q_j.  always2:
+ * two classical Gram-Schmidt passes.  Otherwise the second pass runs only
+ * when the first one shrank w below 1/sqrt(2) of its norm, i.e.
+ * ||w'||^2 < ||w||^2 / 2 (the criterion of Daniel, Gragg, Kaufman and
+ * Stewart, 1976): without that much cancellation one pass already leaves w
+ * orthogonal to Q_j to working precision.  Returns the number of passes. */
+static int cgs_reorth(int s, int j, const double *Q, double *w, double *c, int always2) {
+  double w0 = dot(s, w, w);
+  cgs_pass(s, j, Q, w, c);
+  if (!always2) {
+    double w1 = dot(s, w, w);
+    if (!(w1 < 0.5 * w0)) return 1;
   }
+  cgs_pass(s, j, Q, w, c);
+  return 2;
 }
 
 /* Lanczos with full reorthogonalisation (Sec. 4.4).  Q is s x mmax, column-
  * major.  Returns the number of steps m and the tridiagonal (al, be). */
 static int lanczos(oracle *o, int k, int mmax, int check, double eps, uint64_t seed,
                    double *Q, double *al, double *be) {
+  const int always2 = o->reorth2;
   int s = o->s;
   double *w = (double *)malloc(sizeof(double) * (size_t)s);
   double *c = (double *)malloc(sizeof(double) * (size_t)(mmax + 1));
@@ -760,7 +786,7 @@ static int lanczos(oracle *o, int k, int mmax, int check, double eps, uint64_t s
     for (int r = 0; r < s; r++) w[r] -= al[j] * q[r];
     if (j > 0)
       for (int r = 0; r < s; r++) w[r] -= be[j - 1] * Q[(size_t)(j - 1) * s + r];
-    cgs2(s, j + 1, Q, w, c);
+    o->reorth_passes += cgs_reorth(s, j + 1, Q, w, c, always2);
     double b = sqrt(dot(s, w, w));
     if (fabs(al[j]) > scale) scale = fabs(al[j]);
     m = j + 1;
@@ -981,8 +1007,9 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
              int lanczos_max, int lanczos_check, double lanczos_eps,
              unsigned long long seed, int c_solver, int cheb_steps, int cheb_lanczos,
              int lowrank_method, int rand_oversample, int rand_power, int mr_iters, int mr_lfil,
-             double mr_droptol, int indefinite, int fill_level, void **out) {
+             double mr_droptol, int indefinite, int fill_level, int lanczos_reorth, void **out) {
   *out = NULL;
+  if (lanczos_reorth < 0 || lanczos_reorth > 1) return OR_INVALID;
   if (n <= 0 || p <= 0 || (variant != 1 && variant != 2) || k < 1 || !(alpha > 0))
     return OR_INVALID;
   if (c_solver < 0 || c_solver > 2 || (c_solver == 1 && (cheb_steps < 1 || cheb_lanczos < 1)) ||
@@ -1015,6 +1042,7 @@ int or_setup(int n, const int *rowptr, const int *colind, const double *val,
   o->scale_diag = scale_diag;
   o->c_solver = c_solver; o->cheb_t = cheb_steps; o->cheb_m = cheb_lanczos;
   o->mr_iters = mr_iters; o->mr_lfil = mr_lfil; o->mr_droptol = mr_droptol;
+  o->reorth2 = lanczos_reorth;
   int st = OR_OK;
   long nnz = rowptr[n];
 
@@ -1650,6 +1678,9 @@ void or_info(void *h, int *out, double *theta) {
   out[5] = o->msteps; out[6] = o->ncolors; out[7] = o->variant; out[8] = o->urows;
   *theta = o->theta;
 }
+
+/* Gram-Schmidt passes taken by the Lanczos steps of the setup */
+long or_reorth_passes(void *h) { return ((oracle *)h)->reorth_passes; }
 
 void or_ritz(void *h, double *out) {
   oracle *o = (oracle *)h;

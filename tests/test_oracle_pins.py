@@ -415,3 +415,62 @@ def test_multicolour_rule_bipartite_and_greedy():
     # the factor is still a correct IC(0) in that order: PCG converges
     _, its9, rel9, st9 = o9.pcg(W.rhs(A9[0], 0), 1e-8)
     assert st9 == "OK" and rel9 <= 1e-8
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_flexible_cg_equals_pcg_for_fixed_preconditioner(variant):
+    """The flexible (Polak-Ribiere) CG of the mixed-precision comparison
+    (Sec. 5 PCG; beta = r_{j+1}^T (z_{j+1} - z_j) / r_j^T z_j).  With a fixed
+    SPD preconditioner r_{j+1}^T z_j = 0 in exact arithmetic, so its beta is
+    the Hestenes-Stiefel one and it produces the iterates of plain PCG up to
+    rounding: the same iteration count within one, the same solution, and the
+    true residual below tol.  (A sign error on z_j is not seen by this pin:
+    that term is zero here.)"""
+    A = W.laplacian((10, 9, 11))
+    part, p = W.box_partition((10, 9, 11), (2, 2, 2))
+    b = W.rhs(A[0], 3)
+    orc = O.Oracle(A, part, p, variant=variant, k=6, factor=0, c_order=1, b_order=1)
+    x0, its0, rel0, st0 = orc.pcg(b, 1e-10)
+    x1, its1, rel1, st1 = orc.pcg(b, 1e-10, flexible=True)
+    assert st0 == "OK" and st1 == "OK"
+    assert abs(its1 - its0) <= 1
+    assert rel1 <= 1e-10
+    assert np.linalg.norm(x1 - x0) <= 1e-10 * np.linalg.norm(x0)
+    # and both solve A x = b (dense solve written from the definition)
+    xs = np.linalg.solve(W.to_dense(A), b)
+    assert np.linalg.norm(x1 - xs) <= 1e-8 * np.linalg.norm(xs)
+    # stopping early: after a fixed number of steps both forms hold the same
+    # iterate (maxit ends both with NOCONV at the same x)
+    xa, ia, _, sa = orc.pcg(b, 1e-14, maxit=7)
+    xb, ib, _, sb = orc.pcg(b, 1e-14, maxit=7, flexible=True)
+    assert ia == ib == 7 and sa == sb == "NOCONV"
+    assert np.linalg.norm(xb - xa) <= 1e-12 * np.linalg.norm(xa)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_lanczos_reorth_criterion(small, variant):
+    """Full reorthogonalisation with the second Gram-Schmidt pass taken only
+    on cancellation (||w'||^2 < ||w||^2 / 2 after the first pass) against two
+    passes every step (Sec. 4.4 Lanczos with reorthogonalisation).  Both give
+    the same Ritz values, an orthonormal U_k, and at full rank M^-1 = A^-1;
+    with room left in the Krylov space one pass per step suffices, and as the
+    space runs out (full rank) the criterion asks for the second pass."""
+    A, part, p, D = small
+    Ainv = np.linalg.inv(W.to_dense(A))
+    one = O.Oracle(A, part, p, variant=variant, k=6, factor=1, lanczos_reorth=0)
+    two = O.Oracle(A, part, p, variant=variant, k=6, factor=1, lanczos_reorth=1)
+    assert one.msteps == two.msteps
+    # the k wanted Ritz values; on the symmetric 6^3 grid H has multiple
+    # eigenvalues whose second copies emerge from rounding, so the unwanted
+    # ones may differ between the two forms
+    np.testing.assert_allclose(one.ritz[:6], two.ritz[:6], rtol=1e-9, atol=0)
+    assert two.reorth_passes == 2 * two.msteps
+    assert one.msteps <= one.reorth_passes < 1.2 * one.msteps
+    if variant == 1:
+        U = one.lowrank()[0]
+        assert np.abs(U.T @ U - np.eye(6)).max() < 1e-12
+    s = D.s
+    full = O.Oracle(A, part, p, variant=variant, k=s, factor=1, lanczos_max=s, lanczos_check=0,
+                    lanczos_reorth=0)
+    assert full.reorth_passes > full.msteps
+    np.testing.assert_allclose(oracle_matrix(full, D.n), Ainv, rtol=0, atol=1e-12)
