@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """DDLR-PCG benchmark on one GB300 (N replicas under torchrun).
 
-A step is one pass of the whole hot path on the 3-D 7-point Laplacian, 64^3
-grid (n = 262,144), 4x4x4 box subdomains, IC(0) local factors, DDLR-1 with
-k = 16, FP64: the device-side preconditioner build (scaling, block forming,
+A step is one pass of the whole hot path on the 3-D 7-point Laplacian, 128^3
+grid (n = 2,097,152), 8x8x8 box subdomains, IC(0) local factors, DDLR-1 with
+k = 32, FP64: the device-side preconditioner build (scaling, block forming,
 batched factorisation, Lanczos with full reorthogonalisation, low-rank data)
 from values resident in HBM, then PCG from x0 = 0 to a 1e-8 true relative
 residual.  `value` is the time to solution per solve (ms, lower is better),
 over all ranks.  `e2e` repeats the step through the C ABI from host buffers
-(host CSR and b in, x out, symbolic setup included).
+(host CSR and b in, x out, host analysis included).  Beside it: the mixed
+precision forms (FP32 factors and sweeps, BF16 or FP32 U_k, FP64 flexible
+CG) of the same step, each solution's error against the FP64 CPU oracle, and
+the other configurations as detail lines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -17,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -27,22 +31,26 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "lap3d_64_b4"
-OPTS = dict(variant=1, rank_k=16, factor=0, c_order=1, b_order=1, precision=0)
+WORKLOAD = "lap3d_128_b8"
+OPTS = dict(variant=1, rank_k=32, factor=0, c_order=1, b_order=1, precision=0)
+SMALL = "lap3d_64_b4"
+SMALL_OPTS = dict(OPTS, rank_k=16)
 TOL = 1e-8
 METRIC = "DDLR-PCG time to 1e-8 rel. residual (setup + solve)"
 UNIT = "ms/solve"
 L2_FLUSH_BYTES = 256 << 20
+REF_SAMPLE_ITS = 3
 
 
 def _config(extra=None):
-    c = {"workload": WORKLOAD, "grid": "64^3 7-point Laplacian, Dirichlet",
-         "n": 262144, "subdomains": "4x4x4 boxes (64)", "variant": "DDLR-1",
+    c = {"workload": WORKLOAD, "grid": "128^3 7-point Laplacian, Dirichlet",
+         "n": 2097152, "subdomains": "8x8x8 boxes (512)", "variant": "DDLR-1",
          "rank_k": OPTS["rank_k"], "local_solver": "IC(0)",
          "interior_order": "greedy multicolour", "c_alpha_order": "greedy multicolour", "alpha": 1.0,
-         "theta": "lambda_{k+1}", "lanczos": "<=5k steps, check every 10, eps 1e-4",
-         "tol": TOL, "rhs": "SplitMix64 seed 0, U[-1,1)",
-         "l2": "flushed (256 MiB write) before every timed step"}
+         "theta": "lambda_{k+1}", "lanczos": "<=5k steps, check every 10, eps 1e-4, full reorthogonalisation "
+                                             "(second Gram-Schmidt pass on cancellation)",
+         "tol": TOL, "rhs": "SplitMix64 seed 0, U[-1,1)", "precision": "FP64",
+         "l2": "working set ~1.6 GB > 129 MB L2; L2 also flushed (256 MiB write) before every timed step"}
     if extra:
         c.update(extra)
     return c
@@ -135,14 +143,58 @@ def _traffic_from_profile():
     return d
 
 
+def _oracle_solve(workload, opts, out_npy, q):
+    """Child process (spawned): the FP64 oracle's full setup + PCG solve of a
+    workload; returns timings and the iteration count, writes x to out_npy."""
+    import numpy as np
+    import oracle
+    import workloads as W
+    w = W.workload(workload)
+    A, part, p = w["A"], w["part"], w["p"]
+    b = W.rhs(A[0], 0)
+    t0 = time.perf_counter()
+    orc = oracle.Oracle(A, part, p, variant=opts["variant"], k=opts["rank_k"], factor=opts["factor"],
+                        c_order=opts["c_order"], b_order=opts["b_order"])
+    t1 = time.perf_counter()
+    x, its, rel, st = orc.pcg(b, TOL)
+    t2 = time.perf_counter()
+    np.save(out_npy, x)
+    q.put({"setup_ms": (t1 - t0) * 1e3, "solve_ms": (t2 - t1) * 1e3, "its": its, "relres": rel,
+           "status": st, "lanczos_steps": orc.msteps})
+
+
+class OracleJob:
+    """The oracle solve of the headline workload in a spawned process, started
+    before the GPU legs so that it runs beside them (one host core)."""
+
+    def __init__(self, workload, opts):
+        self.ctx = mp.get_context("spawn")
+        self.q = self.ctx.Queue()
+        self.npy = tempfile.NamedTemporaryFile(suffix=".npy", delete=False).name
+        self.p = self.ctx.Process(target=_oracle_solve, args=(workload, opts, self.npy, self.q), daemon=True)
+        self.p.start()
+
+    def result(self, timeout=1800):
+        import numpy as np
+        r = self.q.get(timeout=timeout)
+        self.p.join(timeout=60)
+        x = np.load(self.npy)
+        os.unlink(self.npy)
+        return r, x
+
+
 def run_ours(args):
+    ws, rank, local = _dist()
+    orc_job = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        orc_job = OracleJob(WORKLOAD, OPTS)       # spawned before any CUDA call
+
     import numpy as np
     import torch
 
     import paper_1505_04341_gb300 as pkg
     import workloads as W
 
-    ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -162,21 +214,23 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
     h = pkg.DDLR(A, part, p, **OPTS)
 
-    def step(hh, xb):
+    def step(hh, xb, bb=b):
         hh.refactor()
-        _, info = hh.pcg(b, xb, tol=TOL)
+        _, info = hh.pcg(bb, xb, tol=TOL)
         return info[0]
 
-    def timed_steps(hh, K):
+    def timed_steps(hh, K, xb=x, bb=b):
         ms, infos = [], []
         for _ in range(K):
             flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            e0, e1 = ev(), ev()
             e0.record(stream)
-            infos.append(step(hh, x))
+            infos.append(step(hh, xb, bb))
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -209,29 +263,40 @@ def run_ours(args):
                               "note": "timed-only pass (launch-list capture)"}))
         h.close()
         return
+    x_fp64 = x.clone()
 
     # split of one step: setup vs solve (CUDA events on the same stream)
-    def split_once(hh):
+    def split_once(hh, xb=x, bb=b):
         flush.fill_(1.0)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e2 = ev(), ev(), ev()
         e0.record(stream)
         hh.refactor()
         e1.record(stream)
-        hh.pcg(b, x, tol=TOL)
+        _, inf = hh.pcg(bb, xb, tol=TOL)
         e2.record(stream)
         e2.synchronize()
-        return e0.elapsed_time(e1), e1.elapsed_time(e2)
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), inf[0]
 
-    setup_ms, solve_ms = split_once(h)
+    setup_ms, solve_ms, _ = split_once(h)
 
     # roofline: per-kernel-family CUDA-event timing over a second timed pass
-    h.reset_counters()
-    h.set_timing(True)
-    ms_prof, _ = timed_steps(h, max(1, min(args.steps, 3)))
-    h.set_timing(False)
-    cnt = h.counters()
-    tr = h.traffic()
-    fams = cnt["families"]
+    def family_table(hh, K):
+        hh.reset_counters()
+        hh.set_timing(True)
+        timed_steps(hh, K)
+        hh.set_timing(False)
+        cnt = hh.counters()
+        tr = hh.traffic()
+        fams = cnt["families"]
+        tot = max(1e-9, sum(u["ms"] for u in fams.values()))
+        table = {f: dict(ms=round(v["ms"] / K, 4), launches=v["launches"] // K,
+                         share=round(v["ms"] / tot, 4),
+                         algorithmic_GBps=(round(tr["family_bytes"].get(f, 0) * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
+                                           if v["ms"] > 0 and tr["family_bytes"].get(f, 0) > 0 else None))
+                 for f, v in sorted(fams.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"] > 0}
+        return fams, tr, table
+
+    fams, tr, families = family_table(h, max(1, min(args.steps, 3)))
     # dominant kernel: the family with the most device time among the kernels
     # whose algorithmic bytes are accounted (the data-moving hot-path kernels)
     dom = max((f for f in fams if fams[f]["launches"] > 0 and tr["family_bytes"].get(f, 0) > 0),
@@ -246,263 +311,70 @@ def run_ours(args):
             "frac": (achieved / peak) if achieved else None,
             "algorithmic_bytes_per_launch": dom_bytes,
             "avg_launch_us": dom_ms * 1e3,
-            "traffic": (prof.get("dram_bytes_per_launch", {}).get(dom) if prof else None)}
-    families = {f: dict(ms=round(v["ms"], 4), launches=v["launches"],
-                        share=round(v["ms"] / max(1e-9, sum(u["ms"] for u in fams.values())), 4),
-                        gbs=(round(tr["family_bytes"].get(f, 0) * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
-                             if v["ms"] > 0 and tr["family_bytes"].get(f, 0) > 0 else None))
-                for f, v in sorted(fams.items(), key=lambda kv: -kv[1]["ms"])}
+            "traffic": (prof.get("dram_bytes_per_launch", {}).get(dom) if prof else None),
+            "traffic_source": (prof.get("source") if prof else None)}
 
-    # M^-1 apply throughput (device vectors, K back-to-back applies)
-    def apply_rate(hh, reps=20):
-        y = torch.empty_like(b)
+    # M^-1 apply throughput (device vectors, back-to-back applies; the
+    # working set is larger than L2)
+    def apply_rate(hh, bb=b, reps=20):
+        y = torch.empty_like(bb)
         for _ in range(3):
-            hh.apply(b, y)
+            hh.apply(bb, y)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = ev(), ev()
         e0.record(stream)
         for _ in range(reps):
-            hh.apply(b, y)
+            hh.apply(bb, y)
         e1.record(stream)
         e1.synchronize()
         t = e0.elapsed_time(e1) / reps
-        return t, hh.traffic()["apply_bytes"] / (t * 1e-3) / 1e9
+        by = hh.traffic()["apply_bytes"]
+        return {"ms": round(t, 4), "algorithmic_bytes": by, "algorithmic_GBps": round(by / (t * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(by / (t * 1e-3) / 1e9 / peak, 3)}
 
-    apply_ms, apply_gbs = apply_rate(h)
+    apply_fp64 = apply_rate(h)
+    info = h.info()
 
-    # mixed precision form of the same step (FP32 factors/solves, BF16 U_k,
-    # FP64 flexible CG outer loop)
-    hm = pkg.DDLR(A, part, p, **dict(OPTS, precision=1, uk_bf16=1))
-    for _ in range(2):
-        step(hm, x)
-    ms_mixed, inf_mixed = timed_steps(hm, args.steps)
-    x_mixed = x.clone()
-    mixed_apply_ms, mixed_apply_gbs = apply_rate(hm)
-    hm.close()
-    # natural (ascending index) order inside the interior blocks: deeper
-    # factors, fewer iterations
-    hn = pkg.DDLR(A, part, p, **dict(OPTS, b_order=0))
-    step(hn, x)
-    ms_nat, inf_nat = timed_steps(hn, 1)
-    hn.close()
-    # DDLR-2 on the same problem
+    # the mixed precision forms of the same step (FP32 factors and sweeps,
+    # BF16 or FP32 U_k, FP64 flexible CG outer loop, FP64 Lanczos)
+    mixed, sols = {}, {"fp64": x_fp64}
+    for name, extra in (("mixed_bf16", dict(precision=1, uk_bf16=1)), ("mixed_fp32", dict(precision=1, uk_bf16=0))):
+        hm = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
+        for _ in range(2):
+            step(hm, x)
+        ms_m, inf_m = timed_steps(hm, max(3, min(args.steps, 5)))
+        sols[name] = x.clone()
+        su, so, _ = split_once(hm)
+        _, _, fam_m = family_table(hm, 1)
+        mixed[name] = {"ms_per_solve": round(statistics.mean(ms_m), 3), "setup_ms": round(su, 3),
+                       "solve_ms": round(so, 3), "iterations": [i["its"] for i in inf_m],
+                       "true_relres_max": max(i["relres"] for i in inf_m),
+                       "speedup_vs_fp64": round(value / statistics.mean(ms_m), 3),
+                       "apply": apply_rate(hm),
+                       "top_families": dict(list(fam_m.items())[:6])}
+        hm.close()
+
+    # DDLR-2 at the same size (k = 32, FP64)
     h2 = pkg.DDLR(A, part, p, **dict(OPTS, variant=2))
     step(h2, x)
-    ms_v2, inf_v2 = timed_steps(h2, 1)
-    v2_apply_ms, v2_apply_gbs = apply_rate(h2)
+    su2, so2, inf2 = split_once(h2)
+    ddlr2 = {"setup_ms": round(su2, 3), "solve_ms": round(so2, 3), "total_ms": round(su2 + so2, 3),
+             "iterations": inf2["its"], "true_relres": inf2["relres"], "apply": apply_rate(h2)}
     h2.close()
+    # the randomized low-rank build instead of Lanczos (same size, FP64)
+    hr = pkg.DDLR(A, part, p, **dict(OPTS, lowrank_method=1))
+    step(hr, x)
+    sur, sor, infr = split_once(hr)
+    randomized = {"setup_ms": round(sur, 3), "solve_ms": round(sor, 3), "total_ms": round(sur + sor, 3),
+                  "iterations": infr["its"]}
+    hr.close()
 
-    # the solve with C_a (Sec. 4.3): factored against 5 preconditioned
-    # Chebyshev steps with the block Jacobi D_a, on the same problem
-    def a0_rate(hh, reps=20):
-        y = torch.empty_like(b)
-        for _ in range(3):
-            hh.a0_solve(b, y)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            hh.a0_solve(b, y)
-        e1.record(stream)
-        e1.synchronize()
-        t = e0.elapsed_time(e1) / reps
-        return t, hh.traffic()["a0_bytes"] / (t * 1e-3) / 1e9
+    detail_small = _small_legs(args, pkg, W, torch, stream, flush, ev, apply_rate)
+    batch = {} if args.skip_large else _batching_leg(pkg, W, torch, np, stream, flush, ev)
+    serving = {} if args.skip_large else _serving_leg()
 
-    c_solve = {}
-    for name, extra in (("factored_natural", dict(b_order=0, c_order=0)),
-                        ("chebyshev_natural", dict(b_order=0, c_order=0, c_solver=1)),
-                        ("mr_inverse_natural", dict(b_order=0, c_order=0, c_solver=2)),
-                        ("factored_multicolour", dict()),
-                        ("chebyshev_multicolour", dict(c_solver=1)),
-                        ("mr_inverse_multicolour", dict(c_solver=2))):
-        hc = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
-        step(hc, x)
-        ms_c, inf_c = timed_steps(hc, 2)
-        a_ms, a_gbs = apply_rate(hc)
-        z_ms, z_gbs = a0_rate(hc)
-        ic = hc.info()
-        c_solve[name] = {"ms_per_solve": round(statistics.mean(ms_c), 3),
-                         "iterations": [i["its"] for i in inf_c],
-                         "true_relres_max": max(i["relres"] for i in inf_c),
-                         "apply_ms": round(a_ms, 4), "a0_solve_ms": round(z_ms, 4),
-                         "a0_algorithmic_GBps": round(z_gbs, 1), "levels_c": ic["levels_c"],
-                         "persistent": ic["persistent"]}
-        if extra.get("c_solver") == 1:
-            c_solve[name]["interval"] = [ic["cheb_lo"], ic["cheb_hi"]]
-            c_solve[name]["steps"] = OPTS.get("cheb_steps", 5)
-        hc.close()
-
-    # the low-rank build: Lanczos (Sec. 4.4) against the randomized subspace
-    # iteration (ell = k + 10, 2 power steps), for DDLR-1 and DDLR-2, and for
-    # DDLR-2 the Lanczos bidiagonalisation of A0^-1 E; setup and solve split
-    lowrank = {}
-    for name, extra in (("lanczos", dict()), ("randomized", dict(lowrank_method=1)),
-                        ("ddlr2_lanczos", dict(variant=2)), ("ddlr2_randomized", dict(variant=2, lowrank_method=1)),
-                        ("ddlr2_bidiagonalisation", dict(variant=2, lowrank_method=2))):
-        hr = pkg.DDLR(A, part, p, **dict(OPTS, **extra))
-        step(hr, x)
-        su, so = split_once(hr)
-        _, inf_r = hr.pcg(b, x, tol=TOL)
-        lowrank[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3), "total_ms": round(su + so, 3),
-                         "iterations": inf_r[0]["its"], "basis": hr.info()["lanczos_steps"]}
-        hr.close()
-
-    # indefinite line (Sec. 5, the 64^3 row of the indefinite table: the
-    # Laplacian minus 3e-2 I, 32 subdomains, rank 64): DDLR with GMRES(40) to a
-    # 1e-6 relative residual (at most 4000 steps), setup and solve split
-    indef = {}
-    if not args.skip_large:
-        wi = W.workload("indef3d_64_s3e-2")
-        Ai, parti, pi = wi["A"], wi["part"], wi["p"]
-        bi = torch.tensor(W.rhs(Ai[0], 0), device="cuda")
-        xi = torch.zeros_like(bi)
-        for name, extra in (("ddlr1", dict(variant=1)), ("ddlr2", dict(variant=2))):
-            try:
-                hi = pkg.DDLR(Ai, parti, pi, **dict(OPTS, rank_k=64, indefinite=1, **extra))
-            except pkg.DdlrError as e:
-                indef[name] = {"status": e.status}
-                continue
-            hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
-            flush.fill_(1.0)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            hi.refactor()
-            e1.record(stream)
-            _, ii = hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
-            e2.record(stream)
-            e2.synchronize()
-            inf_i = hi.info()
-            indef[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
-                           "iterations": ii["its"], "status": ii["status"], "true_relres": ii["relres"],
-                           "lanczos_steps": inf_i["lanczos_steps"], "lambda_max": inf_i["lambda_max"]}
-            hi.close()
-
-    # precision line: 128^3 Laplacian, 512 boxes, k = 32 -- FP64 against mixed
-    # (FP32 factors and solves, BF16 or FP32 U_k, FP64 flexible CG)
-    prec = {}
-    if not args.skip_large:
-        w3 = W.workload("lap3d_128_b8")
-        A3, part3, p3 = w3["A"], w3["part"], w3["p"]
-        b3 = torch.tensor(W.rhs(A3[0], 0), device="cuda")
-        x3 = torch.zeros_like(b3)
-        sol = {}
-        for name, extra in (("fp64", dict(precision=0)), ("mixed_bf16", dict(precision=1, uk_bf16=1)),
-                            ("mixed_fp32", dict(precision=1, uk_bf16=0)),
-                            ("fp64_randomized_lowrank", dict(precision=0, lowrank_method=1))):
-            h3 = pkg.DDLR(A3, part3, p3, **dict(OPTS, rank_k=32, **extra))
-            h3.refactor()
-            h3.pcg(b3, x3, tol=TOL)
-            flush.fill_(1.0)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            h3.refactor()
-            e1.record(stream)
-            _, inf3 = h3.pcg(b3, x3, tol=TOL)
-            e2.record(stream)
-            e2.synchronize()
-            sol[name] = x3.clone()
-            prec[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
-                          "total_ms": round(e0.elapsed_time(e2), 3), "iterations": inf3[0]["its"],
-                          "true_relres": inf3[0]["relres"]}
-            # M^-1 apply at this size (working set larger than L2)
-            y3 = torch.empty_like(b3)
-            for _ in range(3):
-                h3.apply(b3, y3)
-            e0.record(stream)
-            for _ in range(10):
-                h3.apply(b3, y3)
-            e1.record(stream)
-            e1.synchronize()
-            ta = e0.elapsed_time(e1) / 10
-            prec[name]["apply_ms"] = round(ta, 4)
-            prec[name]["apply_algorithmic_GBps"] = round(h3.traffic()["apply_bytes"] / (ta * 1e-3) / 1e9, 1)
-            h3.close()
-        for name in ("mixed_bf16", "mixed_fp32"):
-            prec[name]["rel_err_vs_fp64_solution"] = float(
-                (sol[name] - sol["fp64"]).norm() / sol["fp64"].norm())
-            prec[name]["speedup_vs_fp64"] = round(prec["fp64"]["total_ms"] / prec[name]["total_ms"], 3)
-        del sol
-    # batching line: 96^3 jump coefficients, 125 uneven boxes, k = 24, 32
-    # right-hand sides in one batched solve (FP32 inner / FP64 outer)
-    batch = {}
-    if not args.skip_large:
-        w4 = W.workload("jump3d_96_cut5")
-        A4, part4, p4 = w4["A"], w4["part"], w4["p"]
-        n4 = A4[0]
-        B4 = torch.tensor(np.stack([W.rhs(n4, s_) for s_ in range(32)], axis=1), device="cuda")
-        B4 = B4.T.contiguous().T
-        X4 = torch.zeros_like(B4)
-        h4 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
-                      scale_diag=1, precision=1, uk_bf16=0, max_nrhs=32)
-        # 10^{+-3} jump coefficients need ~1,000-1,300 iterations at k = 24
-        # (the FP64 oracle: 1,297 with multicolour, 986 with natural orders),
-        # beyond the paper's 500-iteration cap
-        MAXIT4 = 3000
-        h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
-        flush.fill_(1.0)
-        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
-        e0.record(stream)
-        h4.refactor()
-        e1.record(stream)
-        _, inf4 = h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
-        e2.record(stream)
-        b1 = B4[:, 0].contiguous()
-        x1 = torch.zeros_like(b1)
-        _, inf1 = h4.pcg(b1, x1, tol=TOL, maxit=MAXIT4)
-        e3.record(stream)
-        e3.synchronize()
-        its4 = [i["its"] for i in inf4]
-        info4 = h4.info()
-        batch = {"workload": "jump3d_96_cut5", "n": n4, "subdomains": p4, "rank_k": 24, "nrhs": 32,
-                 "setup_ms": round(e0.elapsed_time(e1), 3),
-                 "batched_solve_ms": round(e1.elapsed_time(e2), 3),
-                 "ms_per_rhs": round(e1.elapsed_time(e2) / 32, 3),
-                 "single_rhs_solve_ms": round(e2.elapsed_time(e3), 3),
-                 "throughput_gain_vs_single": round(32 * e2.elapsed_time(e3) / e1.elapsed_time(e2), 2),
-                 "iterations_min_max": [min(its4), max(its4)],
-                 "true_relres_max": max(i["relres"] for i in inf4),
-                 "all_ok": all(i["status"] == "OK" for i in inf4),
-                 "single_rhs_iterations": inf1[0]["its"], "maxit": MAXIT4,
-                 "autotuned_block": [info4["batch_block_chunks"], info4["batch_block_elem"]]}
-        h4.close()
-        # the plain FP64 form on the same problem, one right-hand side
-        h5 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
-                      scale_diag=1, precision=0)
-        x5 = torch.zeros_like(b1)
-        h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
-        flush.fill_(1.0)
-        f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        f0.record(stream)
-        h5.refactor()
-        f1.record(stream)
-        _, inf5 = h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
-        f2.record(stream)
-        f2.synchronize()
-        batch["fp64_single_rhs"] = {"setup_ms": round(f0.elapsed_time(f1), 3),
-                                    "solve_ms": round(f1.elapsed_time(f2), 3),
-                                    "iterations": inf5[0]["its"], "true_relres": inf5[0]["relres"]}
-        batch["mixed_batched_per_rhs_speedup_vs_fp64_single"] = round(
-            f1.elapsed_time(f2) / (e1.elapsed_time(e2) / 32), 2)
-        h5.close()
-        del B4, X4
-
-    # serving line: 512 requests over grid edges {32, 48, 64, 96, 128}
-    # ((edge/16)^3 boxes, k = 16, one RHS each), Poisson arrivals; first
-    # saturated (all submitted at once), then at 50 % and 90 % of that rate
-    serving = {}
-    if not args.skip_large:
-        from paper_1505_04341_gb300 import serve
-        srv, models = serve.setup_server([32, 48, 64, 96, 128], k=16, max_batch=16, max_concurrent=4)
-        recs, mk = serve.run_stream(srv, models, 512, 0.0, seed=0)
-        serving["saturated"] = serve.summarize(recs, mk)
-        sat = serving["saturated"]["solves_per_s"]
-        for frac in (0.5, 0.9):
-            recs, mk = serve.run_stream(srv, models, 512, frac * sat, seed=1)
-            serving[f"load_{frac}"] = serve.summarize(recs, mk)
-        serving["stats"] = srv.stats()
-        serving["setup_s"] = {str(e): round(models[e][2], 3) for e in models}
-        srv.close()
-
-    # end to end through the C ABI from host buffers
+    # end to end through the C ABI from host buffers: host analysis, H2D of
+    # the CSR and b, the device setup, PCG, D2H of x
     e2e_ms, e2e_parts = [], []
     for i in range(args.steps + 1):
         t0 = time.perf_counter()
@@ -516,11 +388,10 @@ def run_ours(args):
             e2e_ms.append(dt)
             e2e_parts.append({"setup_ms": round((t1 - t0) * 1e3, 2), "plan_ms": round(pinfo["plan_ms"], 2),
                               "pcg_ms": round(dt - (t1 - t0) * 1e3, 2)})
-    e2e = statistics.mean(e2e_ms)
-    e2e = _job_ms(e2e, 1, ws)
+    e2e = _job_ms(statistics.mean(e2e_ms), 1, ws)
     h2d = (A[1].nbytes + A[2].nbytes + A[3].nbytes + part.nbytes + b_host.nbytes)
     d2h = b_host.nbytes
-    info = h.info()
+    plan_ms = [pp["plan_ms"] for pp in e2e_parts]
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
@@ -530,91 +401,299 @@ def run_ours(args):
         "config": _config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
+        "host_planner": {"ms": round(statistics.median(plan_ms), 2), "what": "host symbolic analysis "
+                         "(classification, orderings, levels, layouts) inside e2e, not in value",
+                         "threads": os.cpu_count()},
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk,
         "detail": {
             "iterations": its, "true_relres_max": relres,
             "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
-            "lanczos_steps": info["lanczos_steps"], "theta": info["theta"],
-            "fill_ratio": round(info["fill_ratio"], 3), "levels_interior": info["levels_interior"],
-            "levels_c": info["levels_c"], "wall_s": round(wall, 3),
-            "apply_fp64": {"ms": round(apply_ms, 4), "algorithmic_GBps": round(apply_gbs, 1),
-                           "bytes": tr["apply_bytes"]},
+            "lanczos_steps": info["lanczos_steps"], "reorth_passes": info["reorth_passes"],
+            "theta": info["theta"], "fill_ratio": round(info["fill_ratio"], 3),
+            "levels_interior": info["levels_interior"], "levels_c": info["levels_c"],
+            "persistent": info["persistent"], "wall_s": round(wall, 3),
+            "apply_fp64": apply_fp64,
             "kernel_families": families,
-            "mixed_fp32_bf16": {"ms_per_solve": round(statistics.mean(ms_mixed), 3),
-                                "iterations": [i["its"] for i in inf_mixed],
-                                "true_relres_max": max(i["relres"] for i in inf_mixed),
-                                "speedup_vs_fp64": round(value / statistics.mean(ms_mixed), 3),
-                                "apply_ms": round(mixed_apply_ms, 4),
-                                "apply_algorithmic_GBps": round(mixed_apply_gbs, 1)},
-            "natural_interior_order_fp64": {"ms_per_solve": round(statistics.mean(ms_nat), 3),
-                                            "iterations": [i["its"] for i in inf_nat]},
+            "mixed": mixed,
+            "ddlr2_fp64": ddlr2,
+            "randomized_lowrank_fp64": randomized,
             "e2e_parts": e2e_parts,
-            "c_alpha_solve_factored_chebyshev_mr": c_solve,
-            "lowrank_lanczos_vs_randomized": lowrank,
-            "indefinite_lap3d_64_s3e-2_gmres40_k64": indef,
-            "precision_lap3d_128_b8_k32": prec,
+            **detail_small,
             "batching_jump3d_96_cut5_32rhs": batch,
             "serving_lap3d_32_to_128_512req": serving,
-            "ddlr2_fp64": {"ms_per_solve": round(statistics.mean(ms_v2), 3),
-                           "iterations": [i["its"] for i in inf_v2],
-                           "apply_ms": round(v2_apply_ms, 4),
-                           "apply_algorithmic_GBps": round(v2_apply_gbs, 1)},
         },
     }
-    del x_mixed
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
     h.close()
+    if orc_job is not None:
+        r, xo = orc_job.result()
+        xo_t = torch.tensor(xo, device="cuda")
+        vs = {}
+        for name, xs in sols.items():
+            vs[name] = {"rel_err_vs_oracle": float((xs - xo_t).norm() / xo_t.norm()),
+                        "iterations_minus_oracle": ((its[0] if name == "fp64" else mixed[name]["iterations"][0])
+                                                    - r["its"])}
+        out["detail"]["vs_oracle"] = dict(oracle_iterations=r["its"], oracle_relres=r["relres"],
+                                          oracle_lanczos_steps=r["lanczos_steps"], **vs)
+        out["cpu_baseline"] = {"value": round(r["setup_ms"] + r["solve_ms"], 1), "unit": UNIT, "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"one full DDLR-1 setup + PCG solve of {WORKLOAD} (its={r['its']}; setup "
+                                         f"{r['setup_ms']:.0f} ms, solve {r['solve_ms']:.0f} ms), single-threaded C in "
+                                         "a spawned process running beside the GPU legs",
+                               "host_cores_available": os.cpu_count()}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
-def _oracle_step():
+def _small_legs(args, pkg, W, torch, stream, flush, ev, apply_rate):
+    """Detail lines on the 64^3 Laplacian (n = 262,144, 64 boxes, k = 16): the
+    working set (~100 MB) fits in the 129 MB L2, so these are L2-resident
+    timings, not HBM ones."""
+    import numpy as np  # noqa: F401
+    w = W.workload(SMALL)
+    A, part, p = w["A"], w["part"], w["p"]
+    b = torch.tensor(W.rhs(A[0], 0), device="cuda")
+    x = torch.zeros_like(b)
+
+    def split(hh):
+        hh.refactor()
+        hh.pcg(b, x, tol=TOL)
+        flush.fill_(1.0)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        hh.refactor()
+        e1.record(stream)
+        _, inf = hh.pcg(b, x, tol=TOL)
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), inf[0]
+
+    out = {}
+    small = {}
+    for name, extra in (("fp64", dict()), ("mixed_bf16", dict(precision=1, uk_bf16=1)),
+                        ("ddlr2_fp64", dict(variant=2)), ("natural_interior_order_fp64", dict(b_order=0))):
+        hh = pkg.DDLR(A, part, p, **dict(SMALL_OPTS, **extra))
+        su, so, inf = split(hh)
+        small[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3), "total_ms": round(su + so, 3),
+                       "iterations": inf["its"], "true_relres": inf["relres"],
+                       "persistent": hh.info()["persistent"]}
+        hh.close()
+    out["l2_resident_lap3d_64_b4_k16"] = small
+
+    def a0_rate(hh, reps=20):
+        y = torch.empty_like(b)
+        for _ in range(3):
+            hh.a0_solve(b, y)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            hh.a0_solve(b, y)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # the solve with C_a (Sec. 4.3): factored against 5 preconditioned
+    # Chebyshev steps with the block Jacobi D_a and the MR approximate inverse
+    c_solve = {}
+    for name, extra in (("factored_natural", dict(b_order=0, c_order=0)),
+                        ("chebyshev_natural", dict(b_order=0, c_order=0, c_solver=1)),
+                        ("mr_inverse_natural", dict(b_order=0, c_order=0, c_solver=2)),
+                        ("factored_multicolour", dict()),
+                        ("chebyshev_multicolour", dict(c_solver=1)),
+                        ("mr_inverse_multicolour", dict(c_solver=2))):
+        hc = pkg.DDLR(A, part, p, **dict(SMALL_OPTS, **extra))
+        su, so, inf = split(hc)
+        c_solve[name] = {"ms_per_solve": round(su + so, 3), "iterations": inf["its"],
+                         "a0_solve_ms": round(a0_rate(hc), 4), "levels_c": hc.info()["levels_c"]}
+        hc.close()
+    out["c_alpha_solve_lap3d_64_b4"] = c_solve
+
+    # the low-rank builds: Lanczos, randomized, bidiagonalisation (DDLR-2)
+    lowrank = {}
+    for name, extra in (("lanczos", dict()), ("randomized", dict(lowrank_method=1)),
+                        ("lanczos_two_passes", dict(lanczos_reorth=1)),
+                        ("ddlr2_lanczos", dict(variant=2)), ("ddlr2_randomized", dict(variant=2, lowrank_method=1)),
+                        ("ddlr2_bidiagonalisation", dict(variant=2, lowrank_method=2))):
+        hr = pkg.DDLR(A, part, p, **dict(SMALL_OPTS, **extra))
+        su, so, inf = split(hr)
+        lowrank[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3), "total_ms": round(su + so, 3),
+                         "iterations": inf["its"], "basis": hr.info()["lanczos_steps"]}
+        hr.close()
+    out["lowrank_build_lap3d_64_b4"] = lowrank
+
+    # indefinite line (Sec. 5, the 64^3 row of the indefinite table: the
+    # Laplacian minus 3e-2 I, 32 subdomains, rank 64): GMRES(40) to a 1e-6
+    # relative residual (at most 4000 steps), setup and solve split
+    indef = {}
+    if not args.skip_large:
+        wi = W.workload("indef3d_64_s3e-2")
+        Ai, parti, pi = wi["A"], wi["part"], wi["p"]
+        bi = torch.tensor(W.rhs(Ai[0], 0), device="cuda")
+        xi = torch.zeros_like(bi)
+        for name, extra in (("ddlr1", dict(variant=1)), ("ddlr2", dict(variant=2))):
+            try:
+                hi = pkg.DDLR(Ai, parti, pi, **dict(SMALL_OPTS, rank_k=64, indefinite=1, **extra))
+            except pkg.DdlrError as e:
+                indef[name] = {"status": e.status}
+                continue
+            hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
+            flush.fill_(1.0)
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record(stream)
+            hi.refactor()
+            e1.record(stream)
+            _, ii = hi.gmres(bi, xi, tol=1e-6, maxit=4000, check=False)
+            e2.record(stream)
+            e2.synchronize()
+            inf_i = hi.info()
+            indef[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
+                           "iterations": ii["its"], "status": ii["status"], "true_relres": ii["relres"],
+                           "lanczos_steps": inf_i["lanczos_steps"], "lambda_max": inf_i["lambda_max"]}
+            hi.close()
+    out["indefinite_lap3d_64_s3e-2_gmres40_k64"] = indef
+    return out
+
+
+def _batching_leg(pkg, W, torch, np, stream, flush, ev):
+    """96^3 jump coefficients, 125 uneven boxes, k = 24, 32 right-hand sides in
+    one batched solve (FP32 inner / FP64 outer) against single FP64 solves."""
+    w4 = W.workload("jump3d_96_cut5")
+    A4, part4, p4 = w4["A"], w4["part"], w4["p"]
+    n4 = A4[0]
+    B4 = torch.tensor(np.stack([W.rhs(n4, s_) for s_ in range(32)], axis=1), device="cuda")
+    B4 = B4.T.contiguous().T
+    X4 = torch.zeros_like(B4)
+    h4 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
+                  scale_diag=1, precision=1, uk_bf16=0, max_nrhs=32)
+    # 10^{+-3} jump coefficients need ~1,000-1,300 iterations at k = 24
+    # (the FP64 oracle: 1,297 with multicolour, 986 with natural orders),
+    # beyond the paper's 500-iteration cap
+    MAXIT4 = 3000
+    h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
+    flush.fill_(1.0)
+    e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+    e0.record(stream)
+    h4.refactor()
+    e1.record(stream)
+    _, inf4 = h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
+    e2.record(stream)
+    b1 = B4[:, 0].contiguous()
+    x1 = torch.zeros_like(b1)
+    _, inf1 = h4.pcg(b1, x1, tol=TOL, maxit=MAXIT4)
+    e3.record(stream)
+    e3.synchronize()
+    its4 = [i["its"] for i in inf4]
+    info4 = h4.info()
+    # per-family device time and algorithmic bytes of one batched solve
+    h4.reset_counters()
+    h4.set_timing(True)
+    h4.pcg(B4, X4, tol=TOL, maxit=MAXIT4)
+    h4.set_timing(False)
+    cnt = h4.counters()
+    tr = h4.traffic()
+    fams = {f: dict(ms=round(v["ms"], 3), launches=v["launches"],
+                    algorithmic_GBps=(round(tr["family_bytes"].get(f, 0) * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
+                                      if v["ms"] > 0 and tr["family_bytes"].get(f, 0) > 0 else None))
+            for f, v in sorted(cnt["families"].items(), key=lambda kv: -kv[1]["ms"]) if v["launches"] > 0}
+    batch = {"workload": "jump3d_96_cut5", "n": n4, "subdomains": p4, "rank_k": 24, "nrhs": 32,
+             "setup_ms": round(e0.elapsed_time(e1), 3),
+             "batched_solve_ms": round(e1.elapsed_time(e2), 3),
+             "ms_per_rhs": round(e1.elapsed_time(e2) / 32, 3),
+             "single_rhs_solve_ms": round(e2.elapsed_time(e3), 3),
+             "throughput_gain_vs_single": round(32 * e2.elapsed_time(e3) / e1.elapsed_time(e2), 2),
+             "iterations_min_max": [min(its4), max(its4)],
+             "true_relres_max": max(i["relres"] for i in inf4),
+             "all_ok": all(i["status"] == "OK" for i in inf4),
+             "single_rhs_iterations": inf1[0]["its"], "maxit": MAXIT4,
+             "autotuned_block": [info4["batch_block_chunks"], info4["batch_block_elem"]],
+             "batched_apply_bytes_32rhs": tr.get("batch_apply_bytes"),
+             "kernel_families": fams}
+    h4.close()
+    # the plain FP64 form on the same problem, one right-hand side
+    h5 = pkg.DDLR(A4, part4, p4, variant=1, rank_k=24, factor=0, c_order=1, b_order=1,
+                  scale_diag=1, precision=0)
+    x5 = torch.zeros_like(b1)
+    h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
+    flush.fill_(1.0)
+    f0, f1, f2 = ev(), ev(), ev()
+    f0.record(stream)
+    h5.refactor()
+    f1.record(stream)
+    _, inf5 = h5.pcg(b1, x5, tol=TOL, maxit=MAXIT4)
+    f2.record(stream)
+    f2.synchronize()
+    batch["fp64_single_rhs"] = {"setup_ms": round(f0.elapsed_time(f1), 3),
+                                "solve_ms": round(f1.elapsed_time(f2), 3),
+                                "iterations": inf5[0]["its"], "true_relres": inf5[0]["relres"]}
+    batch["mixed_batched_per_rhs_speedup_vs_fp64_single"] = round(
+        f1.elapsed_time(f2) / (e1.elapsed_time(e2) / 32), 2)
+    h5.close()
+    return batch
+
+
+def _serving_leg():
+    """512 requests over grid edges {32, 48, 64, 96, 128} ((edge/16)^3 boxes,
+    k = 16, one RHS each), Poisson arrivals; first saturated (all submitted at
+    once), then at 50 % and 90 % of that rate."""
+    from paper_1505_04341_gb300 import serve
+    serving = {}
+    srv, models = serve.setup_server([32, 48, 64, 96, 128], k=16, max_batch=16, max_concurrent=4)
+    recs, mk = serve.run_stream(srv, models, 512, 0.0, seed=0)
+    serving["saturated"] = serve.summarize(recs, mk)
+    sat = serving["saturated"]["solves_per_s"]
+    for frac in (0.5, 0.9):
+        recs, mk = serve.run_stream(srv, models, 512, frac * sat, seed=1)
+        serving[f"load_{frac}"] = serve.summarize(recs, mk)
+    serving["stats"] = srv.stats()
+    serving["setup_s"] = {str(e): round(models[e][2], 3) for e in models}
+    srv.close()
+    return serving
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload.  A full solve takes minutes
+    on one core, so a step is a bounded sample: REF_SAMPLE_ITS PCG iterations
+    with the oracle's preconditioner.  The oracle's setup (timed once) and one
+    full PCG solve (its iteration count) run before the warm-up steps; value =
+    setup + iterations x (mean step time / REF_SAMPLE_ITS)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
     import oracle
     import workloads as W
     w = W.workload(WORKLOAD)
     A, part, p = w["A"], w["part"], w["p"]
     b = W.rhs(A[0], 0)
     t0 = time.perf_counter()
-    orc = oracle.Oracle(A, part, p, variant=1, k=OPTS["rank_k"], factor=0,
+    orc = oracle.Oracle(A, part, p, variant=OPTS["variant"], k=OPTS["rank_k"], factor=OPTS["factor"],
                         c_order=OPTS["c_order"], b_order=OPTS["b_order"])
-    x, its, rel, st = orc.pcg(b, TOL)
-    dt = (time.perf_counter() - t0) * 1e3
+    setup = (time.perf_counter() - t0) * 1e3
+    _, its_full, rel, st = orc.pcg(b, TOL)
     assert st == "OK"
-    return dt, its, rel
 
+    def sample():
+        t = time.perf_counter()
+        _, k, _, _ = orc.pcg(b, TOL, maxit=REF_SAMPLE_ITS)
+        assert k == REF_SAMPLE_ITS
+        return (time.perf_counter() - t) * 1e3
 
-def cpu_baseline():
-    """The FP64 oracle as it stands (single-threaded C) on the host cores: one
-    full setup + PCG solve of the same workload (about 5-15 s)."""
-    dt, its, rel = _oracle_step()
-    return {"value": round(dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 full DDLR-1 setup + PCG solve of {WORKLOAD} (its={its})",
-            "host_cores_available": os.cpu_count()}
-
-
-def run_reference(args):
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return
     for _ in range(args.warmup):
-        _oracle_step()
-    ms = []
-    for _ in range(args.steps):
-        dt, its, rel = _oracle_step()
-        ms.append(dt)
-    v = statistics.mean(ms)
+        sample()
+    ms = [sample() for _ in range(args.steps)]
+    per_it = statistics.mean(ms) / REF_SAMPLE_ITS
+    v = setup + its_full * per_it
+    smp = (f"oracle setup of {WORKLOAD} timed once ({setup:.0f} ms) + its x per-iteration time, the latter "
+           f"from {REF_SAMPLE_ITS}-iteration PCG samples (one per step); its = {its_full} from one full oracle "
+           f"solve run before the warm-up")
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT,
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators, no dataset)",
-           "config": _config({"impl": "FP64 CPU oracle (plain C, single thread)"}),
-           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": f"full DDLR-1 setup + PCG solve of {WORKLOAD} per step"},
+           "config": _config({"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp},
            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -628,7 +707,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-large", action="store_true",
-                    help="skip the 128^3 precision and 96^3 batching legs")
+                    help="skip the indefinite, batching and serving detail legs")
     ap.add_argument("--timed-only", action="store_true",
                     help="run only the warm-up and timed steps (for an ncu launch list)")
     args = ap.parse_args()

@@ -124,6 +124,19 @@ typedef struct {
                               lev(j,t) + 1, and entries up to this level are
                               kept.  Default 0 (the pattern of A0); 0..64;
                               INVALID with factor 1 or 3.                      */
+  int lanczos_reorth;      /* full reorthogonalisation of each Lanczos vector
+                              against all earlier ones (Sec. 4.4 Lanczos with
+                              reorthogonalisation): 0 (default) = one classical
+                              Gram-Schmidt pass, and a second one when the
+                              first left less than half of ||w||^2 (the DGKS
+                              criterion); 1 = two passes every step.  A restart
+                              vector always takes two.                        */
+  double wait_limit_s;     /* limit of every bounded device wait, seconds (grid
+                              barriers of the persistent kernels, ready flags of
+                              the synchronisation-free solve; the TMA solve waits
+                              at least 1 s for its copies): when it runs out the
+                              kernel records it and returns, and the call gives
+                              DDLR_ERR_TIMEOUT.  Default 2; (0, 3600].          */
 } ddlr_options;
 
 typedef struct {
@@ -148,6 +161,8 @@ typedef struct {
   int persistent;          /* bit 0: PCG, bit 1: Lanczos run as one cooperative launch */
   double cheb_lo, cheb_hi; /* c_solver 1: spectrum interval of D_a^-1 C_a in use  */
   int cheb_lanczos_steps;  /* c_solver 1: Lanczos steps the estimate took         */
+  int reorth_passes;       /* Gram-Schmidt passes of the Lanczos steps of the last
+                              build (lowrank_method 0; restart vectors excluded) */
 } ddlr_info;
 
 typedef struct {
@@ -226,8 +241,9 @@ ddlr_status ddlr_a0_solve(ddlr_handle h, const double *x, double *y, int nrhs,
  * entry of the array is written before it is read.  All calls in the process
  * share the array, so calls whose work overlaps on the GPU (other streams,
  * other handles, other threads) race: order them (one stream, or events).
+ * The device current at the call must be the one the handle was set up on.
  * Errors: INVALID for n > 1,048,576, a precision-1 handle, NULL or host
- * pointers; CUDA if the set-up fails. */
+ * pointers, another current device; CUDA if the set-up fails. */
 ddlr_status ddlr_a0_solve_noalloc(ddlr_handle h, const double *x, double *y);
 
 /* Preconditioned CG from x0 = 0 (Sec. 5) for each of nrhs right-hand sides,
@@ -316,6 +332,14 @@ ddlr_status ddlr_get_traffic(ddlr_handle h, double *apply_bytes,
 
 /* Use another stream (cudaStream_t) for later calls. */
 ddlr_status ddlr_set_stream(ddlr_handle h, void *cuda_stream);
+
+/* Change the limit of the handle's bounded device waits (ddlr_options
+ * wait_limit_s) to `seconds` in (0, 3600].  Synchronises the handle's stream;
+ * captured CUDA graphs are rebuilt at their next use.  A wait that runs out
+ * sets a device flag, every CTA of the kernel returns, and the call that
+ * launched it returns DDLR_ERR_TIMEOUT (its results are invalid); the flag is
+ * cleared then, so the handle stays usable.  Errors: INVALID. */
+ddlr_status ddlr_set_wait_limit(ddlr_handle h, double seconds);
 
 /* Text of the last error on this handle; with h == NULL, of the last failed
  * ddlr_setup on this thread.  Never NULL. */

@@ -69,6 +69,8 @@ thread_local std::string g_setup_error;
 
 struct ddlr_ctx {
   ddlr_options opt{};
+  int device = 0;                  // the device current at setup; all its memory is there
+  unsigned long long wait_ns = 2000000000ull;   // limit of every bounded device wait
   cudaStream_t stream = nullptr;   // caller's stream
   cudaStream_t stream2 = nullptr;  // C_a solve branch (forked with events)
   cudaStream_t gstream = nullptr;  // internal stream of the PCG graph
@@ -100,6 +102,8 @@ struct ddlr_ctx {
     std::map<int, G> graphs;            // one captured PCG iteration per width R
     int chunk_per = 0, bd_elem = 256;   // autotuned: rows per pass of the level solve, row-kernel block
     bool tuned = false;
+    int last_R = 0;                     // width of the last batched solve (byte accounting)
+    bool tc = true;                     // U_k products on the tensor cores (FP32 vectors; DDLR_BATCH_TC=0: scalar)
   } bt;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Plan P;
@@ -203,6 +207,7 @@ struct ddlr_ctx {
   __nv_bfloat16 *Ub16 = nullptr;
   std::vector<double> ritz;
   int msteps = 0;
+  int lz_passes = 0;          // Gram-Schmidt passes of the last Lanczos build
   double theta = 0.0;
   int *dflag = nullptr;       // device error flags [0]=breakdown [1]=notspd [2]=eig fail
   // Lanczos workspace, start vector and step graph, kept for refactors
@@ -378,7 +383,10 @@ bool tma_config(const Plan &P, TmaCfg &cfg) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (P.tma_zs <= 0 || sms <= 0) return false;
   const int cps = std::max(1, std::min(4, (P.p + sms - 1) / sms));
-  const long long budget = std::min<long long>(optin, per_sm / cps - 1024);
+  // the kernel's static shared memory (its abort word) comes out of the same
+  // per-block limit as the dynamic part
+  constexpr long long kStatic = 128;
+  const long long budget = std::min<long long>(optin, per_sm / cps - 1024) - kStatic;
   cfg = TmaCfg{P.tma_zs, P.tma_nl, P.tma_ns, 0};
   const long long fixed = (long long)tma_smem_bytes<T>(cfg);
   const long long stage_max = (long long)P.tma_e * (long long)(sizeof(T) + 4) +
@@ -580,10 +588,10 @@ void a0_solve(ddlr_ctx *c, const T *x, T *z, const int *gate) {
     if (sizeof(T) == 8 ? c->use_sf64 : c->use_sf32) {
       KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_sf<T, 256, 4>), P.p, 256, sf_smem_bytes<T>(P),
          c->blk_row0, RowSpan{c->l_span, c->u_span}, c->S.l_col, lv, c->S.u_col, uv, di, x, z, gate,
-         c->dflag + 3);
+         c->dflag + 3, c->wait_ns);
     } else if (use) {
       KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks_tma<T, 256>), P.p, 256, tma_smem_bytes<T>(cfg),
-         c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, cfg, c->dflag + 3);
+         c->S, lv, uv, Prec<T>::dinvs(c), x, z, gate, cfg, c->dflag + 3, std::max(c->wait_ns, kTmaMinWaitNs));
     } else {
       KL(c, "sptrsv_blocks", c->stream, (k_sptrsv_blocks<T, 256>), P.p, 256, 0,
          c->S, lv, uv, di, x, z, gate);
@@ -773,6 +781,8 @@ template <typename T, typename TU>
 PzOp<T, TU> make_pzop(ddlr_ctx *c);
 bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
 size_t pz_lz_smem(int mmax);
+[[noreturn]] void timeout_fail(ddlr_ctx *c);
+void clear_timeout(ddlr_ctx *c);
 
 // ------------------------------------------------------------- Lanczos
 void sync(ddlr_ctx *c) { ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"); }
@@ -783,8 +793,9 @@ void read_dev(ddlr_ctx *c, void *h, const void *d, size_t bytes) {
 }
 
 // one Lanczos step j (Sec. 4.4) with every scalar and index on the device:
-// w = Op q_j; alpha_j; three-term update; two classical Gram-Schmidt passes
-// against Q_{j+1}; beta_j; breakdown decision; q_{j+1} (or a restart vector
+// w = Op q_j; alpha_j; three-term update; full reorthogonalisation against
+// Q_{j+1} (one classical Gram-Schmidt pass, a second one on cancellation);
+// beta_j; breakdown decision; q_{j+1} (or a restart vector
 // orthogonalised against Q_{j+1}); j += 1.  Kernels return at once once the
 // stop flag is set.
 struct LzBufs {
@@ -816,24 +827,36 @@ void lanczos_step(ddlr_ctx *c, const LzBufs &L) {
      c->part64, stop);
   KL(c, "dot", c->stream, k_lz_reduce_at, 1, 32, 0, kRedGrid, c->part64, L.al, L.st, 0, stop);
   KL(c, "lanczos", c->stream, k_lz_three_term_d, nblk(s), kThreads, 0, s, L.al, L.be, L.st, L.qcur, L.qprev, L.w);
-  auto cgs2 = [&](const int *gate) {
-    for (int pass = 0; pass < 2; pass++) {
-      KL(c, "cgs2", c->stream, k_gemvT_partial_d<256>, kRedGrid, 256, 0, s, L.Q, L.ld, L.w, c->part64, L.st,
-         gate, (const int *)nullptr);
-      KL(c, "cgs2", c->stream, k_reduce_cols_d, (L.mmax + 8) / 8, 256, 0, kRedGrid, c->part64, L.cvec, L.st, gate,
-         (const int *)nullptr);
-      KL(c, "cgs2", c->stream, k_gemvN_sub_d, nblk(s), kThreads, csm, s, L.Q, L.ld, L.cvec, L.w, L.st, gate,
-         (const int *)nullptr);
-    }
+  // one classical Gram-Schmidt pass against Q_{j+1}; skipped when *gate != 0
+  // or *gate_inv == 0
+  auto cgs_pass = [&](const int *gate, const int *gate_inv) {
+    KL(c, "cgs2", c->stream, k_gemvT_partial_d<256>, kRedGrid, 256, 0, s, L.Q, L.ld, L.w, c->part64, L.st,
+       gate, gate_inv);
+    KL(c, "cgs2", c->stream, k_reduce_cols_d, (L.mmax + 8) / 8, 256, 0, kRedGrid, c->part64, L.cvec, L.st, gate,
+       gate_inv);
+    KL(c, "cgs2", c->stream, k_gemvN_sub_d, nblk(s), kThreads, csm, s, L.Q, L.ld, L.cvec, L.w, L.st, gate,
+       gate_inv);
   };
-  cgs2(stop);
+  auto wnorm2 = [&](double *out, const int *gate) {
+    KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.w, L.w, c->part64, gate);
+    KL(c, "dot", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, out, 0, gate);
+  };
+  // full reorthogonalisation: the second pass when the first left less than
+  // half of ||w||^2 (or always, lanczos_reorth 1)
+  const int *pass2 = reinterpret_cast<const int *>(reinterpret_cast<const char *>(L.st) + offsetof(LzState, pass2));
+  wnorm2(L.nrm + 2, stop);
+  cgs_pass(stop, nullptr);
+  wnorm2(L.nrm + 3, stop);
+  KL(c, "lanczos", c->stream, k_lz_dgks, 1, 32, 0, L.st, L.nrm + 2, c->opt.lanczos_reorth);
+  cgs_pass(stop, pass2);
   KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.w, L.w, c->part64, stop);
   KL(c, "dot", c->stream, k_lz_reduce_at, 1, 32, 0, kRedGrid, c->part64, L.be, L.st, 1, stop);
   KL(c, "lanczos", c->stream, k_lz_decide, 1, 32, 0, L.st, L.al, L.be);
   KL(c, "lanczos", c->stream, k_lz_normalize, nblk(s), kThreads, 0, s, L.w, L.be, L.Q, L.ld, L.qcur, L.qprev, L.st);
   // breakdown: restart from a fresh vector orthogonalised against Q_{j+1}
   KL(c, "lanczos", c->stream, k_lz_randvec, nblk(s), kThreads, 0, s, L.rank, L.st, L.w);
-  cgs2(nobrk);
+  cgs_pass(nobrk, nullptr);
+  cgs_pass(nobrk, nullptr);
   KL(c, "dot", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)s, L.w, L.w, c->part64, nobrk);
   KL(c, "dot", c->stream, k_reduce_scalar, 1, 32, 0, kRedGrid, c->part64, L.nrm, 1, nobrk);
   KL(c, "lanczos", c->stream, k_lz_restart_norm, nblk(s), kThreads, 0, s, L.w, L.nrm, L.Q, L.ld, L.qcur, L.qprev,
@@ -944,7 +967,8 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
                    (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
     if (persist) {
       PzOp<double, double> O = make_pzop<double, double>(c);
-      PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps};
+      PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps,
+              c->opt.lanczos_reorth};
       void *args[] = {&O, &Lz};
       persist = pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax),
                           args);
@@ -1013,18 +1037,33 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
     ck(cudaMemcpy(&hs, L.st, sizeof(hs), cudaMemcpyDeviceToHost), "D2H");
     if (persist) {
       // per step: E q, one (DDLR-2: two) A0 solves, E^T, the three-term update
-      // and normalisation, and two CGS passes reading Q_{j+1} twice each
+      // and normalisation, and one or two CGS passes reading Q_{j+1} twice
+      // each (the second pass on npass2 of the steps)
       double a0 = 0;
       ddlr_get_traffic(c, nullptr, &a0, nullptr, 0);
       const double ne = double(P.nnz_ehat), sd = double(s) * 8.0, nd = double(n) * 8.0;
       const double step = ne * 12.0 + sd + nd + (c->opt.variant == 2 ? 2.0 : 1.0) * a0 + ne * 12.0 + nd + sd +
                           8.0 * sd;
       const double steps = double(hs.j);
-      c->pz_lz_bytes += steps * step + 4.0 * sd * steps * (steps + 1.0) / 2.0;
+      const double passes = steps > 0 ? 1.0 + double(hs.npass2) / steps : 1.0;
+      c->pz_lz_bytes += steps * step + passes * 2.0 * sd * steps * (steps + 1.0) / 2.0;
       c->pz_lz_runs += 1;
+    }
+    c->lz_passes = hs.j + hs.npass2;
+    {
+      // a bounded wait of the persistent kernel ran out: the state is not
+      // that of a finished process
+      int fl[4];
+      read_dev(c, fl, c->dflag, sizeof(fl));
+      if (fl[3]) {
+        clear_timeout(c);
+        c->err = "a bounded device wait timed out";
+        return DDLR_ERR_TIMEOUT;
+      }
     }
     const int mm = hs.conv_m > 0 ? hs.conv_m : std::min(hs.j, mmax);
     if (hs.nan_step >= 0 && hs.nan_step < mm) st = DDLR_ERR_NAN;
+    if (st == DDLR_OK && mm < 1) throw Fail{DDLR_ERR_BREAKDOWN, "the Lanczos process took no step"};
     if (st == DDLR_OK) {
       c->msteps = mm;
       const int nvals = mm;
@@ -1133,7 +1172,7 @@ void hk_finalize(ddlr_ctx *c, int k, const double *kp, double *hw) {
 // 1 - lambda_i and 1 - theta away from zero; DDLR-2's flag then means a
 // singular I - K.  Both are BREAKDOWN.
 ddlr_status lowrank_status(ddlr_ctx *c, const int *fl) {
-  if (fl[3]) return DDLR_ERR_TIMEOUT;
+  if (fl[3]) { clear_timeout(c); return DDLR_ERR_TIMEOUT; }
   if (fl[2]) return DDLR_ERR_NAN;
   if (!c->opt.indefinite) return fl[1] ? DDLR_ERR_NOT_SPD : DDLR_OK;
   if (c->opt.variant == 2) return fl[1] ? DDLR_ERR_BREAKDOWN : DDLR_OK;
@@ -1567,7 +1606,7 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
   }
   int fl[4];
   read_dev(c, fl, c->dflag, sizeof(fl));
-  if (fl[3]) { c->err = "a bounded device wait timed out"; return DDLR_ERR_TIMEOUT; }
+  if (fl[3]) { clear_timeout(c); c->err = "a bounded device wait timed out"; return DDLR_ERR_TIMEOUT; }
   if (fl[0]) {
     c->err = "non-positive pivot in a local factorisation";
     return DDLR_ERR_BREAKDOWN;
@@ -1680,6 +1719,11 @@ PzOp<T, TU> make_pzop(ddlr_ctx *c) {
   O.part = c->pz_part;
   O.gs.count = c->pz_bar;
   O.gs.err = c->dflag + 3;
+  O.gs.wait_ns = c->wait_ns;
+  // tests of the timeout path: DDLR_TEST_UNMET_BARRIER=1 makes the first grid
+  // barrier of this launch wait for an arrival that never comes
+  const char *um = getenv("DDLR_TEST_UNMET_BARRIER");
+  O.gs.unmet = (um && um[0] == '1') ? 1 : 0;
   return O;
 }
 
@@ -2015,7 +2059,7 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
     ck(cudaEventRecord(c->ev_join, c->stream), "event");
     ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
   }
-  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  if (dfl[3]) timeout_fail(c);
   if (persist) {
     // x, r, p, b set up and one apply; per iteration one apply, A p with the
     // p update (A once, p_old, z, p, q), the x and r updates, and z_old for
@@ -2121,7 +2165,7 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
   }
   int dfl[4];
   read_dev(c, dfl, c->dflag, sizeof(dfl));
-  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  if (dfl[3]) timeout_fail(c);
   if (info) {
     info->its = its;
     info->relres = bn > 0 ? beta / bn : 0.0;
@@ -2179,6 +2223,8 @@ void batch_alloc(ddlr_ctx *c, int R) {
     }
   B.st = (PcgStateMR *)al(sizeof(PcgStateMR));
   B.R = R;
+  const char *tce = getenv("DDLR_BATCH_TC");
+  B.tc = !(tce && tce[0] == '0') && k <= 64;
   B.chunk_per = tuned ? per_c : std::max(1, 256 / R);
   B.bd_elem = tuned ? bd_e : 256;
   B.tuned = tuned;
@@ -2283,21 +2329,52 @@ void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *ga
     a0_solve_mr<T>(c, X, Z, R, gate);
     KL(c, "et_mr", c->stream, k_et_mr<T>, eblk((long long)s * R, bd), bd, 0, s, m, c->eht_rp, c->eht_ci,
        Prec<T>::eht(c), ia, a, Z, Y, R, gate);
-    KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->bt.tc) {
+        KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+      } else {
+        KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part,
+           gate);
+      }
+    } else {
+      KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+    }
     KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, Prec<T>::coef(c),
        (const T *)nullptr, Tm, gate);
-    KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr<T, TU>), eblk((long long)s * R, bd), bd, 0, s, m, k, U, Tm, Y,
-       Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->bt.tc) {
+        KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr_tc<TU>), (unsigned)((s + 127) / 128), 256, 0, s, m, k, U, Tm, Y,
+           Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
+      } else {
+        KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr<T, TU>), eblk((long long)s * R, bd), bd, 0, s, m, k, U, Tm, Y,
+           Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
+      }
+    } else {
+      KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr<T, TU>), eblk((long long)s * R, bd), bd, 0, s, m, k, U, Tm, Y,
+         Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
+    }
     KL(c, "e_int_mr", c->stream, k_e_interior_mr<T>, eblk((long long)m * R, bd), bd, 0, m, c->eh_rp, c->eh_ci,
        Prec<T>::eh(c), ia, W, X, RHS, R, gate);
     a0_solve_mr<T>(c, RHS, Out, R, gate);
   } else {
     a0_solve_mr<T>(c, X, Out, R, gate);
-    KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
+    bool tc = false;
+    if constexpr (std::is_same<T, float>::value) tc = c->bt.tc;
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
+    }
+    if (!tc)
+      KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
     KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, (const T *)nullptr,
        Prec<T>::Hk(c), Tm, gate);
-    KL(c, "u_add_mr", c->stream, (k_u_add_mr<T, TU>), eblk((long long)n * R, bd), bd, 0, (long long)n, k, U, Tm,
-       Out, R, gate);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc)
+        KL(c, "u_add_mr", c->stream, (k_u_add_mr_tc<TU>), (unsigned)((n + 127) / 128), 256, 0, (long long)n, k, U,
+           Tm, Out, R, gate);
+    }
+    if (!tc)
+      KL(c, "u_add_mr", c->stream, (k_u_add_mr<T, TU>), eblk((long long)n * R, bd), bd, 0, (long long)n, k, U, Tm,
+         Out, R, gate);
   }
 }
 
@@ -2432,6 +2509,7 @@ void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info
     c->stream = c->gstream;
   }
   batch_autotune(c, R);
+  B.last_R = R;
   double *part = B.part64;
   const int bd = B.bd_elem;
   ck(cudaMemsetAsync(B.X, 0, sizeof(double) * nR, c->stream), "memset");
@@ -2497,7 +2575,7 @@ void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info
     ck(cudaEventRecord(c->ev_join, c->stream), "event");
     ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
   }
-  if (dfl[3]) throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+  if (dfl[3]) timeout_fail(c);
   for (int q = 0; q < R; q++) {
     double rt2 = 0;
     for (int g = 0; g < kRedGrid; g++) rt2 += hp[size_t(g) * 2 * R + q];   // fixed order
@@ -2538,7 +2616,21 @@ void batch_store(ddlr_ctx *c, const double *srcb, double *y, int ld, int R, bool
 // ====================================================================== ABI
 
 namespace {
+// A bounded device wait ran out: clear the flag (the next call starts clean)
+// and report DDLR_ERR_TIMEOUT
+void clear_timeout(ddlr_ctx *c) {
+  cudaMemsetAsync(c->dflag + 3, 0, sizeof(int), c->stream);
+  cudaStreamSynchronize(c->stream);
+}
+[[noreturn]] void timeout_fail(ddlr_ctx *c) {
+  clear_timeout(c);
+  throw Fail{DDLR_ERR_TIMEOUT, "a bounded device wait timed out"};
+}
+
 ddlr_status run_guarded(ddlr_ctx *c, const std::function<ddlr_status()> &f) {
+  // a launch error left by an earlier call that already returned its own
+  // status is not this call's error
+  cudaGetLastError();
   try {
     ddlr_status st = f();
     if (st == DDLR_OK) {
@@ -2605,6 +2697,8 @@ ddlr_status ddlr_options_default(ddlr_options *o) {
   o->mr_droptol = 1e-3;
   o->indefinite = 0;
   o->fill_level = 0;
+  o->lanczos_reorth = 0;
+  o->wait_limit_s = 2.0;
   return DDLR_OK;
 }
 
@@ -2629,6 +2723,7 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
       o.lowrank_method < 0 || o.lowrank_method > 2 || (o.lowrank_method == 2 && o.variant != 2) ||
       (o.indefinite != 0 && o.indefinite != 1) || o.fill_level < 0 || o.fill_level > 64 ||
       (o.fill_level > 0 && (o.factor == 1 || o.factor == 3)) ||
+      (o.lanczos_reorth != 0 && o.lanczos_reorth != 1) || !(o.wait_limit_s > 0) || o.wait_limit_s > 3600 ||
       (o.lowrank_method == 1 && (o.rand_oversample < 0 || o.rand_power < 0 || o.rand_power > 100 ||
                                  o.rank_k + o.rand_oversample > kRandMaxL))) {
     g_setup_error = "invalid options";
@@ -2639,10 +2734,12 @@ ddlr_status ddlr_setup(int n, const int *rowptr, const int *colind, const double
   if (!c) { g_setup_error = "host allocation failed"; return DDLR_ERR_OOM; }
   c->opt = o;
   c->stream = (cudaStream_t)cuda_stream;
+  c->wait_ns = (unsigned long long)(o.wait_limit_s * 1e9);
   ddlr_status st = run_guarded(c, [&]() -> ddlr_status {
     std::string err;
     ddlr_status s1 = build_plan(n, rowptr, colind, val, part, p, c->opt, c->P, err);
     if (s1 != DDLR_OK) { c->err = err; return s1; }
+    ck(cudaGetDevice(&c->device), "cudaGetDevice");
     if (c->opt.c_solver == 2) {
       // the per-column work of the MR iterations holds r_j and C_a z_j in
       // fixed local arrays: rows of C_a times the column capacity must fit
@@ -2797,6 +2894,7 @@ ddlr_status ddlr_apply(ddlr_handle c, const double *x, double *y, int nrhs, int 
         const int R = std::min(W, nrhs - j0);
         batch_alloc(c, R);
         batch_autotune(c, R);
+        c->bt.last_R = R;
         batch_load(c, x + size_t(j0) * ld, ld, R, hx, c->bt.Rr);
         precond_mr(c, c->bt.Rr, c->bt.Z, R, nullptr);
         batch_store(c, c->bt.Z, y + size_t(j0) * ld, ld, R, hy);
@@ -2838,7 +2936,9 @@ ddlr_status ddlr_a0_solve(ddlr_handle c, const double *x, double *y, int nrhs, i
 namespace {
 constexpr int kNoAllocMaxN = 1 << 20;
 }
-static __device__ __align__(256) double g_noalloc_scratch[2 * (1 << 20)];
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
+static_assert(sizeof(g_noalloc_scratch) == 2 * size_t(kNoAllocMaxN) * sizeof(double),
+              "the two vectors of the no-allocation solve must fit the array");
 
 namespace {
 std::mutex g_noalloc_mu;
@@ -2864,8 +2964,14 @@ ddlr_status ddlr_a0_solve_noalloc(ddlr_handle c, const double *x, double *y) {
   const bool timing = c->timing;
   c->timing = false;   // per-kernel timing would create events
   ddlr_status st = run_guarded(c, [&]() -> ddlr_status {
+    // the array's address is per device: look it up on the handle's device,
+    // which must be the current one (a kernel given another device's address
+    // would read that device's memory)
     int dev = 0;
     ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != c->device)
+      throw Fail{DDLR_ERR_INVALID, "ddlr_a0_solve_noalloc: the current device (" + std::to_string(dev) +
+                                       ") is not the handle's device (" + std::to_string(c->device) + ")"};
     if (dev < 0 || dev >= 128) throw Fail{DDLR_ERR_INVALID, "device index out of range"};
     double *scratch = nullptr;
     {
@@ -2976,6 +3082,7 @@ ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
   info->setup_ms = c->setup_ms;
   info->plan_ms = c->plan_ms;
   info->persistent = (c->pz_pcg ? 1 : 0) | (c->pz_lz ? 2 : 0);
+  info->reorth_passes = c->lz_passes;
   if (c->opt.c_solver == 1) {
     double lohi[2] = {0, 0};
     if (cudaMemcpy(lohi, c->ctab64, sizeof(lohi), cudaMemcpyDeviceToHost) != cudaSuccess) return DDLR_ERR_CUDA;
@@ -3126,6 +3233,21 @@ ddlr_status ddlr_reset_counters(ddlr_handle c) {
   return DDLR_OK;
 }
 
+// algorithmic bytes of one batched A0 solve of R columns (level launches of
+// k_sptrsv_*_mr): the off-diagonal factor entries and the inverse diagonal once
+// per sweep, every column read and written once per sweep (gathered reads of
+// other rows as cache hits)
+static double batch_a0_bytes(const ddlr_ctx *c, double R) {
+  const Plan &P = c->P;
+  const double v = c->opt.precision == 1 ? 4.0 : 8.0;
+  const double off = double(P.nnz_factor) - double(P.n);
+  return 2.0 * (off * (v + 4.0) + double(P.n) * v + 2.0 * double(P.n) * R * v);
+}
+static double batch_a0_launches(const ddlr_ctx *c) {
+  const int nL = int(c->P.ch_all_ptr.size()) - 1;
+  return nL == 2 ? 2.0 : double(std::max(1, 2 * nL - 1));
+}
+
 ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_bytes,
                              double *family_bytes, int cap_f) {
   if (!c) return DDLR_ERR_INVALID;
@@ -3170,6 +3292,7 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
     auto sweeps = [](int L) { return L == 2 ? 2 : std::max(1, 2 * L - 1); };
     const double clev = sweeps(P.levels_c);
     const double nnz_a = double(P.nnz);
+    const double R = std::max(1, c->bt.last_R);
     for (int i = 0; i < cap_f && i < int(c->fam_names.size()); i++) {
       const std::string &f = c->fam_names[i];
       double b = 0.0;
@@ -3189,6 +3312,20 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "pcg_dot2") b = 3.0 * n * 8.0;
       else if (f == "pcg_p") b = (c->opt.precision == 1 ? 4.0 : 3.0) * n * 8.0;
       else if (f == "pcg_persist") b = c->pz_pcg_runs ? c->pz_pcg_bytes / double(c->pz_pcg_runs) : 0.0;
+      // batched (R right-hand sides, R = the width of the last batched call):
+      // operator data once per launch, R columns of every vector
+      else if (f == "sptrsv_levels_mr") b = batch_a0_bytes(c, R) / batch_a0_launches(c);
+      else if (f == "et_mr") b = ne * (v + 4.0) + 4.0 * s + 2.0 * s * R * v;
+      else if (f == "utx_mr") b = urows * k * ub + urows * R * v;
+      else if (f == "reduce_mr") b = double(kRedGrid) * k * R * v + k * R * v;
+      else if (f == "w_rhs_mr") b = s * k * ub + 4.0 * s * R * v;
+      else if (f == "e_int_mr") b = ne * (v + 4.0) + 4.0 * m + 2.0 * m * R * v;
+      else if (f == "u_add_mr") b = n * k * ub + 2.0 * n * R * v;
+      else if (f == "spmv_mr") b = nnz_a * 12.0 + 2.0 * n * R * 8.0;
+      else if (f == "pcg_mr_dot") b = 2.0 * n * R * 8.0;
+      else if (f == "pcg_mr_axpy") b = 6.0 * n * R * 8.0;
+      else if (f == "pcg_mr_p") b = (c->opt.precision == 1 ? 4.0 : 3.0) * n * R * 8.0;
+      else if (f == "vec_mr") b = n * R * (8.0 + v) + (c->dsc_dev ? 8.0 * n : 0.0);
       else if (f == "lanczos_persist") b = c->pz_lz_runs ? c->pz_lz_bytes / double(c->pz_lz_runs) : 0.0;
       family_bytes[i] = b;
     }
@@ -3200,6 +3337,23 @@ ddlr_status ddlr_set_stream(ddlr_handle c, void *s) {
   if (!c) return DDLR_ERR_INVALID;
   c->stream = (cudaStream_t)s;
   return DDLR_OK;
+}
+
+ddlr_status ddlr_set_wait_limit(ddlr_handle c, double seconds) {
+  if (!c) return DDLR_ERR_INVALID;
+  if (!(seconds > 0) || seconds > 3600) { c->err = "wait limit must be in (0, 3600] seconds"; return DDLR_ERR_INVALID; }
+  return run_guarded(c, [&]() -> ddlr_status {
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    c->wait_ns = (unsigned long long)(seconds * 1e9);
+    c->opt.wait_limit_s = seconds;
+    // captured graphs hold the old limit in their kernel arguments
+    if (c->lw.exec) { cudaGraphExecDestroy(c->lw.exec); c->lw.exec = nullptr; }
+    if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+    for (auto &kv : c->bt.graphs)
+      if (kv.second.exec) { cudaGraphExecDestroy(kv.second.exec); kv.second.exec = nullptr; }
+    c->bt.graphs.clear();
+    return DDLR_OK;
+  });
 }
 
 const char *ddlr_last_error(ddlr_handle c) {

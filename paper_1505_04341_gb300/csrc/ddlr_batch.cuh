@@ -235,6 +235,221 @@ __global__ void k_u_add_mr(long long nrows, int k, const TU *U, const T *HT, T *
   Uo[r * R + q] += acc;
 }
 
+// --------------------------------------------- tensor-core U_k products
+// The multi-RHS U_k products are dense GEMMs (s x k by k x R, reduced over the
+// s rows for U_k^T Y), so with FP32 preconditioner vectors they run on the
+// tensor cores: mma.sync m16n8k8 with TF32 operands and FP32 accumulation.
+// An FP32 operand x is split into its TF32 rounding hi and the TF32 rounding
+// of x - hi; the three products hi*hi + hi*lo + lo*hi keep about the accuracy
+// of FP32 products (the dropped lo*lo term is 2^-22 relative).  A BF16 U_k is
+// exact in TF32 (lo = 0): two products.  An output element depends only on
+// its own row of one operand and column of the other, and the row ranges and
+// their order are those of the scalar kernels, so a column's result does not
+// depend on the other columns of its batch.
+__device__ __forceinline__ unsigned tf32_of(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// d += a * b with both split: three products (two when a is exact in TF32)
+template <bool kAExact>
+__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                           const unsigned (&bh)[2], const unsigned (&bl)[2]) {
+  if (!kAExact) mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+template <typename TU> struct TcExact { static constexpr bool v = false; };
+template <> struct TcExact<__nv_bfloat16> { static constexpr bool v = true; };
+
+// partials[g][c*R + q] = sum over the rows of range g of U[row][c] Y[row][q]
+// (stage 1 of U_k^T Y, as k_utx_mr_partial), on the tensor cores.  256
+// threads; k <= 64, R <= 64.  The CTA streams its rows in stages of 32 rows
+// (the U and Y tiles of a stage are contiguous in memory), zero-padded to
+// 16-column (c) and 8-column (q) tiles; warp w owns output tiles w and w + 8.
+constexpr int kTcRows = 32, kTcUS = 68, kTcYS = 72;   // smem strides: conflict-free fragment reads
+template <typename TU>
+__global__ void __launch_bounds__(256)
+k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *partials, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ float us[kTcRows * kTcUS];
+  __shared__ float ys[kTcRows * kTcYS];
+  constexpr bool kEx = TcExact<TU>::v;
+  long long r0, r1;
+  red_range(nrows, blockIdx.x, gridDim.x, r0, r1);
+  const int MT = (k + 15) >> 4, NQ = (R + 7) >> 3, ntile = MT * NQ;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int i = threadIdx.x; i < kTcRows * kTcUS; i += blockDim.x) us[i] = 0.f;
+  for (int i = threadIdx.x; i < kTcRows * kTcYS; i += blockDim.x) ys[i] = 0.f;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  __syncthreads();
+  for (long long base = r0; base < r1; base += kTcRows) {
+    const int nt = int(min((long long)kTcRows, r1 - base));
+    const TU *ub = U + base * k;
+    const float *yb = Y + base * R;
+    for (int i = threadIdx.x; i < nt * k; i += blockDim.x) {
+      const int rr = int(unsigned(i) / unsigned(k));
+      us[rr * kTcUS + (i - rr * k)] = to_acc(ub[i]);
+    }
+    for (int i = threadIdx.x; i < nt * R; i += blockDim.x) {
+      const int rr = int(unsigned(i) / unsigned(R));
+      ys[rr * kTcYS + (i - rr * R)] = yb[i];
+    }
+    if (nt < kTcRows) {          // last stage of the range: zero the rows past its end
+      for (int i = threadIdx.x; i < (kTcRows - nt) * 64; i += blockDim.x) {
+        const int rr = nt + (i >> 6), c = i & 63;
+        us[rr * kTcUS + c] = 0.f;
+        ys[rr * kTcYS + c] = 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int sl = 0; sl < 2; sl++) {
+      const int tt = w + 8 * sl;
+      if (tt < ntile) {
+        const int c0 = (tt / NQ) << 4, q0 = (tt % NQ) << 3;
+#pragma unroll
+        for (int kk = 0; kk < kTcRows; kk += 8) {
+          unsigned ah[4], al[4], bh[2], bl[2];
+          tf32_split(us[(kk + t) * kTcUS + c0 + g], ah[0], al[0]);
+          tf32_split(us[(kk + t) * kTcUS + c0 + g + 8], ah[1], al[1]);
+          tf32_split(us[(kk + t + 4) * kTcUS + c0 + g], ah[2], al[2]);
+          tf32_split(us[(kk + t + 4) * kTcUS + c0 + g + 8], ah[3], al[3]);
+          tf32_split(ys[(kk + t) * kTcYS + q0 + g], bh[0], bl[0]);
+          tf32_split(ys[(kk + t + 4) * kTcYS + q0 + g], bh[1], bl[1]);
+          mma_tf32x3<kEx>(acc[sl], ah, al, bh, bl);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int no = k * R;
+#pragma unroll
+  for (int sl = 0; sl < 2; sl++) {
+    const int tt = w + 8 * sl;
+    if (tt >= ntile) continue;
+    const int c0 = (tt / NQ) << 4, q0 = (tt % NQ) << 3;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int c = c0 + g + ((e & 2) ? 8 : 0), q = q0 + 2 * t + (e & 1);
+      if (c < k && q < R) partials[(long long)blockIdx.x * no + c * R + q] = acc[sl][e];
+    }
+  }
+}
+
+// Rows [j0, j0 + 16) of D = U_k Tm (U row-major nrows x k, Tm k x R) on the
+// tensor cores for one warp: acc[nq] holds the 16 x 8 tile of columns
+// [8 nq, 8 nq + 8).  ts: Tm in shared memory with row stride TS (floats).
+template <typename TU>
+__device__ __forceinline__ void tc_rows_times_small(long long nrows, int k, const TU *U, const float *ts, int TS,
+                                                    int NQ, long long j0, float (&acc)[8][4]) {
+  constexpr bool kEx = TcExact<TU>::v;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long ja = j0 + g, jb = j0 + g + 8;
+  for (int c0 = 0; c0 < k; c0 += 8) {
+    const int ca = c0 + t, cb = c0 + t + 4;
+    auto uat = [&](long long j, int c) { return (j < nrows && c < k) ? to_acc(U[j * k + c]) : 0.f; };
+    unsigned ah[4], al[4];
+    tf32_split(uat(ja, ca), ah[0], al[0]);
+    tf32_split(uat(jb, ca), ah[1], al[1]);
+    tf32_split(uat(ja, cb), ah[2], al[2]);
+    tf32_split(uat(jb, cb), ah[3], al[3]);
+#pragma unroll
+    for (int nq = 0; nq < 8; nq++) {
+      if (nq < NQ) {
+        unsigned bh[2], bl[2];
+        tf32_split(ca < k ? ts[ca * TS + nq * 8 + g] : 0.f, bh[0], bl[0]);
+        tf32_split(cb < k ? ts[cb * TS + nq * 8 + g] : 0.f, bh[1], bl[1]);
+        mma_tf32x3<kEx>(acc[nq], ah, al, bh, bl);
+      }
+    }
+  }
+}
+
+// shared-memory copy of the k x R block Tm with row stride TS (zero-padded to
+// a multiple of 8 columns); returns TS.  ts holds k * TS floats.
+__device__ __forceinline__ int tc_stage_small(const float *Tm, int k, int R, float *ts) {
+  const int TS = ((R + 31) & ~31) + 8;      // = 8 (mod 32): conflict-free B fragment reads
+  for (int o = threadIdx.x; o < k * TS; o += blockDim.x) {
+    const int c = o / TS, q = o - c * TS;
+    ts[o] = q < R ? Tm[c * R + q] : 0.f;
+  }
+  __syncthreads();
+  return TS;
+}
+
+// k_w_rhs_mr on the tensor cores: W = Y/(1-theta) + U_k Tm ; RHS_C = X_C - a W.
+// A warp computes 16 interface rows x all R columns.  256 threads.
+template <typename TU>
+__global__ void __launch_bounds__(256)
+k_w_rhs_mr_tc(int s, int m, int k, const TU *U, const float *Tm, const float *Y, const float *inv1mt, float a,
+              const float *X, float *W, float *RHS, int R, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ float ts[64 * 72];
+  const int TS = tc_stage_small(Tm, k, R, ts);
+  const int NQ = (R + 7) >> 3;
+  const long long j0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16;
+  if (j0 >= s) return;
+  float acc[8][4];
+#pragma unroll
+  for (int nq = 0; nq < 8; nq++) acc[nq][0] = acc[nq][1] = acc[nq][2] = acc[nq][3] = 0.f;
+  tc_rows_times_small<TU>(s, k, U, ts, TS, NQ, j0, acc);
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const float i1 = *inv1mt;
+#pragma unroll
+  for (int nq = 0; nq < 8; nq++) {
+    if (nq >= NQ) continue;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const long long j = j0 + g + ((e & 2) ? 8 : 0);
+      const int q = nq * 8 + 2 * t + (e & 1);
+      if (j < s && q < R) {
+        const float wj = i1 * Y[j * R + q] + acc[nq][e];
+        W[j * R + q] = wj;
+        RHS[(m + j) * R + q] = X[(m + j) * R + q] - a * wj;
+      }
+    }
+  }
+}
+
+// k_u_add_mr on the tensor cores: Uo += U_k HT (DDLR-2, all rows)
+template <typename TU>
+__global__ void __launch_bounds__(256)
+k_u_add_mr_tc(long long nrows, int k, const TU *U, const float *HT, float *Uo, int R, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ float ts[64 * 72];
+  const int TS = tc_stage_small(HT, k, R, ts);
+  const int NQ = (R + 7) >> 3;
+  const long long j0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16;
+  if (j0 >= nrows) return;
+  float acc[8][4];
+#pragma unroll
+  for (int nq = 0; nq < 8; nq++) acc[nq][0] = acc[nq][1] = acc[nq][2] = acc[nq][3] = 0.f;
+  tc_rows_times_small<TU>(nrows, k, U, ts, TS, NQ, j0, acc);
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nq = 0; nq < 8; nq++) {
+    if (nq >= NQ) continue;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const long long j = j0 + g + ((e & 2) ? 8 : 0);
+      const int q = nq * 8 + 2 * t + (e & 1);
+      if (j < nrows && q < R) Uo[j * R + q] += acc[nq][e];
+    }
+  }
+}
+
 // Q = A P (sliced ELL, device order), R columns
 template <typename T>
 __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,

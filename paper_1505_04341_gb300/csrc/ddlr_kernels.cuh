@@ -194,7 +194,17 @@ struct TmaCfg {
   int ns_cap;      // slices of the largest block + 1
   int ring_bytes;  // staging ring (multiple of 128, >= the largest stage)
 };
+// nanoseconds of the global timer (bounded waits)
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 constexpr int kNBar = 64;       // mbarriers = stages in flight at most
+// the TMA solve waits at least this long for its copies (a CTA must not exit
+// with copies still in flight into its shared memory)
+constexpr unsigned long long kTmaMinWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -250,8 +260,9 @@ __host__ __device__ inline size_t tma_smem_bytes(const TmaCfg &c) {
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s,
-                    const T *x, T *z, const int *gate, TmaCfg cfg, int *err) {
+                    const T *x, T *z, const int *gate, TmaCfg cfg, int *err, unsigned long long limit_ns) {
   if (gate && *gate) return;
+  __shared__ int s_abort;
   extern __shared__ __align__(128) unsigned char smraw[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);
   unsigned char *ring = smraw + 8 * kNBar;
@@ -303,6 +314,7 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
     for (int q = 0; q < kNBar; q++) mbar_init(bar + q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_abort = 0;
   }
   int jn = 0;   // producer: next stage to issue
   auto produce = [&](int jc) {
@@ -328,10 +340,29 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
   for (int j = 0; j < nstage; j++) {
     const unsigned par = unsigned(j / kNBar) & 1u;
     if (!mbar_try_wait(bar + (j % kNBar), par)) {
-      const long long t0 = clock64();
+      // bounded wait; a thread that gives up tells the others (the decision
+      // to stop is the CTA's, taken at the barrier below)
+      const unsigned long long t0 = gtimer_ns();
       while (!mbar_try_wait(bar + (j % kNBar), par)) {
-        if (clock64() - t0 > (1LL << 32)) { *err = 1; return; }
+        if (*(volatile int *)&s_abort) break;
+        if (gtimer_ns() - t0 > limit_ns) { atomicExch(&s_abort, 1); break; }
       }
+    }
+    __syncthreads();
+    if (s_abort) {
+      // the copies issued for stages j .. jn-1 may still be in flight into
+      // this CTA's shared memory: the producer waits for them (bounded)
+      // before the CTA exits
+      if (tid == PROD) {
+        *err = 1;
+        for (int q = j; q < jn; q++) {
+          const unsigned pq = unsigned(q / kNBar) & 1u;
+          const unsigned long long t0 = gtimer_ns();
+          while (!mbar_try_wait(bar + (q % kNBar), pq) && gtimer_ns() - t0 < limit_ns) {
+          }
+        }
+      }
+      return;
     }
     const int4 g0 = sg0[j], g1 = sg1[j];
     const bool fwd = j < NL;
@@ -364,13 +395,14 @@ k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s
 struct RowSpan { const int2 *l, *u; };
 
 template <typename T>
-__device__ __forceinline__ void sf_wait(int *flag, int target, int *err, bool &late) {
+__device__ __forceinline__ void sf_wait(int *flag, int target, int *err, bool &late,
+                                        unsigned long long limit_ns) {
   cuda::atomic_ref<int, cuda::thread_scope_block> f(*flag);
   if (f.load(cuda::memory_order_acquire) >= target) return;
-  const long long t0 = clock64();
+  const unsigned long long t0 = gtimer_ns();
   while (f.load(cuda::memory_order_acquire) < target) {
     __nanosleep(32);
-    if (!late && clock64() - t0 > (1LL << 31)) { late = true; *err = 1; }
+    if (!late && gtimer_ns() - t0 > limit_ns) { late = true; *err = 1; }
     if (late) return;                 // give up waiting; the result is flagged invalid
   }
 }
@@ -388,7 +420,7 @@ template <typename T, int NT, int WR>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l_val,
                    const int *u_col, const T *u_val, const T *dinv, const T *x, T *z,
-                   const int *gate, int *err) {
+                   const int *gate, int *err, unsigned long long limit_ns) {
   if (gate && *gate) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -431,13 +463,13 @@ k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l
 #pragma unroll
       for (int kk = 0; kk < WR; kk++) {
         if (kk < sp.y) {
-          sf_wait<T>(flag + cc[kk], target, err, late);
+          sf_wait<T>(flag + cc[kk], target, err, late, limit_ns);
           acc -= cv[kk] * zs[cc[kk]];
         }
       }
       for (int kk = WR; kk < sp.y; kk++) {          // rows wider than WR
         const int c = col[sp.x + 32 * kk] - rb0;
-        sf_wait<T>(flag + c, target, err, late);
+        sf_wait<T>(flag + c, target, err, late, limit_ns);
         acc -= val[sp.x + 32 * kk] * zs[c];
       }
       zs[i] = acc * dd;
@@ -1336,7 +1368,10 @@ struct LzState {
   int restarts;     // restarts so far (SplitMix64 stream seed + restarts)
   int conv_m;       // m at which eq. converge was met (0: not met)
   int nan_step;     // first step with a non-finite alpha or beta (-1: none)
-  int mmax, pad;
+  int mmax;
+  int pass2;        // 1: this step's reorthogonalisation takes a second pass
+  int npass2;       // steps that took the second pass (restart vectors excluded)
+  int pad;
   double scale;     // max |alpha_i|, beta_i seen (breakdown threshold)
   unsigned long long seed;
 };
@@ -1423,6 +1458,14 @@ __global__ void k_gemvN_sub_d(int s, const double *Q, long long ld, const double
 }
 
 // breakdown decision of step j (beta_j <= 1e-12 max(|alpha_i|, beta_i))
+// Second Gram-Schmidt pass of a Lanczos step: always when always2, else when
+// the first pass left less than half of ||w||^2 (nrm[0] before, nrm[1] after)
+__global__ void k_lz_dgks(LzState *st, const double *nrm, int always2) {
+  if (st->stop || threadIdx.x != 0) return;
+  st->pass2 = (always2 || nrm[1] < 0.5 * nrm[0]) ? 1 : 0;
+  st->npass2 += st->pass2;
+}
+
 __global__ void k_lz_decide(LzState *st, const double *al, const double *be) {
   if (st->stop || threadIdx.x != 0) return;
   const int j = st->j;

@@ -19,7 +19,7 @@ namespace ddlr {
 
 constexpr int kPzThreads = 512;          // threads per CTA of the persistent kernels
 constexpr int kPzMaxLevels = 8;          // deepest factor served (levels per block)
-constexpr unsigned long long kPzWaitNs = 2000000000ull;   // barrier wait limit (2 s)
+
 
 // loads of operator data, which no kernel writes while a persistent kernel
 // runs: through the read-only path, so they can stay in L1 across barriers
@@ -31,6 +31,9 @@ __device__ __forceinline__ T ro(const T *p) { return __ldg(p); }
 struct GridSync {
   unsigned *count;
   int *err;
+  unsigned long long wait_ns;   // wait limit of one barrier (the handle's wait_limit_s)
+  int unmet;                    // tests: the first barrier waits for one arrival that
+                                // never comes, so it runs out after wait_ns
 };
 
 __device__ __forceinline__ unsigned pz_ld_acquire(const unsigned *p) {
@@ -47,7 +50,7 @@ __device__ __forceinline__ unsigned long long pz_clock_ns() {
 // Grid barrier of a cooperative launch (every CTA resident).  The counter only
 // grows: barrier number e is passed once e * gridDim.x arrivals are visible
 // (release add on arrival, acquire loads while waiting).
-// Thread 0 waits at most kPzWaitNs, or until another CTA has reported a
+// Thread 0 waits at most g.wait_ns, or until another CTA has reported a
 // timeout; then the flag is set and every thread gets false (the kernel
 // returns).  Writes before the barrier are visible to every CTA after it.
 __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
@@ -55,7 +58,7 @@ __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
   __syncthreads();
   ++epoch;
   if (threadIdx.x == 0) {
-    const unsigned target = epoch * gridDim.x;
+    const unsigned target = epoch * gridDim.x + ((g.unmet && epoch == 1) ? 1u : 0u);
     // release: the CTA's writes (ordered before by the CTA barrier) become
     // visible to every CTA whose acquire load sees this arrival
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(g.count) : "memory");
@@ -68,7 +71,7 @@ __device__ __forceinline__ bool pz_sync(const GridSync &g, unsigned &epoch) {
         const unsigned long long t = pz_clock_ns();
         if (t0 == 0) {
           t0 = t;
-        } else if (t - t0 > kPzWaitNs) {
+        } else if (t - t0 > g.wait_ns) {
           atomicExch(g.err, 1);
           ok = 0;
           break;
@@ -494,6 +497,7 @@ struct PzLz {
   LzState *st;
   int check, k;
   double eps;
+  int reorth2;      // 1: two Gram-Schmidt passes every step
 };
 
 // partials of Q_{ncol}^T w over this CTA's rows [r0, r1), warp per column
@@ -549,22 +553,38 @@ __device__ __forceinline__ double pz_gemvN(const double *Q, long long ld, int nc
   return ww;
 }
 
-// Two classical Gram-Schmidt passes of w against Q_{ncol} (rows [j0, j1) of
-// this CTA), then ||w||^2 over all rows, returned to every thread.
+// Full reorthogonalisation of w against Q_{ncol} (rows [j0, j1) of this CTA):
+// one classical Gram-Schmidt pass, and a second one when always2 or when the
+// first left less than half of ||w||^2 (the DGKS criterion; every CTA reads
+// the same partials in the same order, so all take the same branch).  ww0 is
+// this thread's share of ||w||^2 before the first pass.  Returns ||w||^2
+// after the last pass to every thread.
 template <int NT>
-__device__ __forceinline__ bool pz_cgs2(const PzOp<double, double> &O, const PzLz &L, int ncol, int j0, int j1, unsigned &ep,
-                                        int &slot, double *red, double *bc, double *cs, double &ww_out) {
+__device__ __forceinline__ bool pz_cgs(const PzOp<double, double> &O, const PzLz &L, int ncol, int j0, int j1,
+                                       unsigned &ep, int &slot, double *red, double *bc, double *cs, bool always2,
+                                       double ww0, double &ww_out, int &npass2) {
   double *pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
-  if (!pz_sync(O.gs, ep)) return false;
-  pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
-  pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
   __syncthreads();
+  pz_put<NT>(ww0, pt + ncol, O.pstride, red);       // column ncol: ||w||^2 before
+  if (!pz_sync(O.gs, ep)) return false;
+  pz_get_cols<NT, double>(pt, O.pstride, ncol + 1, nullptr, nullptr, cs, red);
+  const double w0 = cs[ncol];
+  double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  pt = pz_buf(O, slot++);
+  pz_put<NT>(ww, pt, O.pstride, red);
+  if (!pz_sync(O.gs, ep)) return false;
+  ww = pz_get(pt, O.pstride, bc);
+  if (!always2 && !(ww < 0.5 * w0)) {
+    ww_out = ww;
+    return true;
+  }
+  npass2 += 1;
   pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
-  const double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
   pt = pz_buf(O, slot++);
   pz_put<NT>(ww, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
@@ -587,7 +607,7 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
   unsigned ep = 0;
   int slot = 0;
   const int n = O.n, m = O.m, s = O.s, k = L.k;
-  int j = S0.j, restarts = S0.restarts, conv_m = S0.conv_m, nan_step = S0.nan_step;
+  int j = S0.j, restarts = S0.restarts, conv_m = S0.conv_m, nan_step = S0.nan_step, npass2 = S0.npass2;
   bool stop = S0.stop != 0;
   double scale = S0.scale;
   const int mmax = S0.mmax;
@@ -649,15 +669,17 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
     if (!pz_sync(O.gs, ep)) return;
     const double alpha = pz_get(pt, O.pstride, bc);
     if (blockIdx.x == 0 && threadIdx.x == 0) L.al[j] = alpha;
-    // three-term recurrence, then two CGS passes against Q_{j+1}
+    // three-term recurrence, then full reorthogonalisation against Q_{j+1}
+    double ww0 = 0;
     for (int r = j0 + threadIdx.x; r < j1; r += NT) {
       double t = L.w[r] - alpha * L.qcur[r];
       if (j > 0) t -= bprev * L.qprev[r];
       L.w[r] = t;
+      ww0 += t * t;
     }
     __syncthreads();
     double ww = 0;
-    if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, ww)) return;
+    if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, L.reorth2 != 0, ww0, ww, npass2)) return;
     const double beta = sqrt(ww);
     if (blockIdx.x == 0 && threadIdx.x == 0) L.be[j] = beta;
     if (!(alpha == alpha) || isinf(alpha) || !(beta == beta) || isinf(beta)) {
@@ -687,7 +709,8 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
         L.w[r] = d_sm64_pm1(S0.seed + (unsigned long long)restarts, (unsigned long long)ro(L.rank + r));
       __syncthreads();
       double nn = 0;
-      if (!pz_cgs2<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, nn)) return;
+      int unused = 0;
+      if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, true, 0.0, nn, unused)) return;
       const double nrm = sqrt(nn);
       rdiv = 1.0 / nrm;
       for (int r = j0 + threadIdx.x; r < j1; r += NT) {
@@ -735,7 +758,7 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     LzState *st = L.st;
     st->j = j; st->stop = 1; st->no_break = 1; st->restarts = restarts; st->conv_m = conv_m;
-    st->nan_step = nan_step; st->scale = scale;
+    st->nan_step = nan_step; st->scale = scale; st->npass2 = npass2;
   }
 }
 

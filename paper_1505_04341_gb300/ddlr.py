@@ -39,7 +39,8 @@ class ddlr_options(ctypes.Structure):
                 ("cheb_lanczos", ctypes.c_int), ("lowrank_method", ctypes.c_int),
                 ("rand_oversample", ctypes.c_int), ("rand_power", ctypes.c_int),
                 ("mr_iters", ctypes.c_int), ("mr_lfil", ctypes.c_int), ("mr_droptol", ctypes.c_double),
-                ("indefinite", ctypes.c_int), ("fill_level", ctypes.c_int)]
+                ("indefinite", ctypes.c_int), ("fill_level", ctypes.c_int),
+                ("lanczos_reorth", ctypes.c_int), ("wait_limit_s", ctypes.c_double)]
 
 
 class ddlr_info(ctypes.Structure):
@@ -54,7 +55,8 @@ class ddlr_info(ctypes.Structure):
                 ("setup_ms", ctypes.c_double), ("batch_block_chunks", ctypes.c_int),
                 ("batch_block_elem", ctypes.c_int), ("plan_ms", ctypes.c_double),
                 ("persistent", ctypes.c_int), ("cheb_lo", ctypes.c_double),
-                ("cheb_hi", ctypes.c_double), ("cheb_lanczos_steps", ctypes.c_int)]
+                ("cheb_hi", ctypes.c_double), ("cheb_lanczos_steps", ctypes.c_int),
+                ("reorth_passes", ctypes.c_int)]
 
 
 class ddlr_solve_info(ctypes.Structure):
@@ -73,7 +75,7 @@ EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
            "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_gmres", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank", "ddlr_set_cheb_bounds",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
-           "ddlr_get_traffic", "ddlr_set_stream", "ddlr_last_error",
+           "ddlr_get_traffic", "ddlr_set_stream", "ddlr_set_wait_limit", "ddlr_last_error",
            "ddlr_destroy", "ddlr_server_options_default", "ddlr_server_create",
            "ddlr_server_add_model", "ddlr_server_submit", "ddlr_server_wait",
            "ddlr_server_stats", "ddlr_server_last_error", "ddlr_server_destroy"]
@@ -116,6 +118,7 @@ def load(path: str | None = None):
         "ddlr_reset_counters": ([P], I),
         "ddlr_get_traffic": ([P, P, P, P, I], I),
         "ddlr_set_stream": ([P, P], I),
+        "ddlr_set_wait_limit": ([P, D], I),
         "ddlr_last_error": ([P], ctypes.c_char_p),
         "ddlr_destroy": ([P], I),
         "ddlr_server_options_default": ([ctypes.POINTER(ddlr_server_options)], I),
@@ -222,6 +225,10 @@ class DDLR:
             self._h = None
 
     __del__ = close
+
+    def set_wait_limit(self, seconds):
+        """Limit of the handle's bounded device waits (seconds)."""
+        _check(_lib, self._h, _lib.ddlr_set_wait_limit(self._h, float(seconds)))
 
     def set_stream(self, stream):
         _check(_lib, self._h, _lib.ddlr_set_stream(self._h, self._stream_ptr(stream)))

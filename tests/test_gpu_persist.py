@@ -188,3 +188,38 @@ def test_refused_cooperative_launch_falls_back(monkeypatch):
     assert info[0]["status"] == "OK" and info[0]["relres"] <= 1e-8
     assert abs(info[0]["its"] - its_o) <= 1
     h.close()
+
+
+@pytest.mark.parametrize("persist", ["1", "0"])
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_reorthogonalisation_passes(reorth, variant, persist, monkeypatch):
+    """Full reorthogonalisation with the second Gram-Schmidt pass on
+    cancellation (lanczos_reorth 0) or every step (1): the GPU takes the same
+    passes as the oracle, the same steps, Ritz values within 1e-8, an
+    orthonormal U_k; near full rank the second pass is taken."""
+    A = W.laplacian((32, 32, 32))
+    part, p = W.box_partition((32, 32, 32), (2, 2, 2))
+    kw = dict(variant=variant, factor=0, lanczos_reorth=reorth, **MC)
+    h = _handle(monkeypatch, persist, A, part, p, rank_k=8, **kw)
+    orc = O.Oracle(A, part, p, k=8, **kw)
+    inf = h.info()
+    assert inf["lanczos_steps"] == orc.msteps
+    np.testing.assert_allclose(h.ritz()[:9], orc.ritz[:9], rtol=1e-8)
+    assert inf["reorth_passes"] == orc.reorth_passes
+    assert inf["reorth_passes"] == (2 if reorth else 1) * orc.msteps
+    if variant == 1:
+        U = h.lowrank()[0]
+        np.testing.assert_allclose(U.T @ U, np.eye(8), atol=1e-10)
+    h.close()
+    # exhausting the Krylov space: cancellation, so the criterion takes the
+    # second pass too (exact 2-D factors, k = s)
+    A2 = W.laplacian((16, 16))
+    part2, p2 = W.box_partition((16, 16), (2, 2))
+    s = O.Oracle(A2, part2, p2, variant=variant, k=2, factor=1, **MC).s
+    kw2 = dict(variant=variant, factor=1, lanczos_reorth=reorth, **MC)
+    h2 = _handle(monkeypatch, persist, A2, part2, p2, rank_k=s, **kw2)
+    orc2 = O.Oracle(A2, part2, p2, k=s, **kw2)
+    assert h2.info()["lanczos_steps"] == orc2.msteps
+    assert h2.info()["reorth_passes"] == orc2.reorth_passes > orc2.msteps
+    h2.close()

@@ -21,6 +21,10 @@ def _handle(name, **kw):
 @pytest.mark.parametrize("name,kw", [
     ("lap2d_64_b2x2", dict(variant=1, rank_k=8, factor=0)),
     ("lap3d_32", dict(variant=2, rank_k=8, factor=0, c_order=1, b_order=1)),
+    # the other A0 branches: Chebyshev and MR solves with C_a, L D L^T factors
+    ("lap3d_32", dict(variant=1, rank_k=8, factor=0, c_order=1, b_order=1, c_solver=1)),
+    ("lap2d_64_b2x2", dict(variant=1, rank_k=8, factor=0, c_solver=2)),
+    ("lap3d_32", dict(variant=1, rank_k=8, factor=2, c_order=1, b_order=1)),
 ])
 def test_noalloc_matches_a0_solve_twice(name, kw):
     import torch
@@ -57,3 +61,27 @@ def test_noalloc_rejects_bad_arguments():
             h32.a0_solve_noalloc(x, torch.zeros_like(x))
     finally:
         h32.close()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged():
+    """The call allocates nothing: after one call has loaded the kernels, the
+    free device memory (cudaMemGetInfo) is the same before and after repeated
+    calls, the first call on a freshly set-up handle included."""
+    import torch
+    h0, n = _handle("lap3d_32", variant=1, rank_k=8, factor=0, c_order=1, b_order=1)
+    x = torch.tensor(W.rhs(n, 0), device="cuda")
+    y = torch.empty_like(x)
+    h0.a0_solve_noalloc(x, y)
+    torch.cuda.synchronize()
+    h1, _ = _handle("lap3d_32", variant=1, rank_k=8, factor=0, c_order=1, b_order=1)
+    try:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(4):
+            h1.a0_solve_noalloc(x, y)
+            h0.a0_solve_noalloc(x, y)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        h0.close()
+        h1.close()
