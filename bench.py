@@ -637,10 +637,11 @@ def _batching_leg(pkg, W, torch, np, stream, flush, ev):
 def _serving_leg():
     """512 requests over grid edges {32, 48, 64, 96, 128} ((edge/16)^3 boxes,
     k = 16, one RHS each), Poisson arrivals; first saturated (all submitted at
-    once), then at 50 % and 90 % of that rate."""
+    once), then at 50 % and 90 % of that rate.  Continuous batching: up to 16
+    slots per model, every model with its own block on the GPU."""
     from paper_1505_04341_gb300 import serve
     serving = {}
-    srv, models = serve.setup_server([32, 48, 64, 96, 128], k=16, max_batch=16, max_concurrent=4)
+    srv, models = serve.setup_server([32, 48, 64, 96, 128], k=16, max_batch=16, max_concurrent=8)
     recs, mk = serve.run_stream(srv, models, 512, 0.0, seed=0)
     serving["saturated"] = serve.summarize(recs, mk)
     sat = serving["saturated"]["solves_per_s"]

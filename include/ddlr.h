@@ -352,19 +352,24 @@ ddlr_status ddlr_destroy(ddlr_handle h);
  * A solve service on one GPU (no counterpart in the paper; it serves many
  * solves with resident preconditioners, the amortisation the paper's
  * conclusion points to).  Every model (a matrix with its DDLR setup) stays
- * resident and has a worker thread with its own CUDA streams.  Requests are
- * queued per model; a free worker takes all waiting requests of its model (up
- * to max_batch) into one batched PCG, so requests arriving while others run
- * join the next batch (continuous batching), and at most max_concurrent
- * batches run on the GPU at once, overlapping across models.  A batch is
- * admitted only if its workspace fits in memory_fraction of the free device
- * memory (narrowed otherwise).  A request's result does not depend on the other
- * requests of its batch. */
+ * resident and has a worker thread with its own CUDA stream.  Requests are
+ * queued per model.  A worker runs a block PCG whose columns are slots
+ * (continuous batching): every few iterations it hands back the columns that
+ * have converged and admits queued requests of its model into the free slots,
+ * so a request waits for a free slot, never for a whole batch; with every slot
+ * busy and requests waiting, the block is widened (up to max_batch columns)
+ * without disturbing the running columns.  At most max_concurrent models hold
+ * a block on the GPU at once, overlapping across models; while another model
+ * waits for a place, a block admits nothing more and gives its place back
+ * once it drains.  A block is opened or
+ * widened only as far as its workspace fits in memory_fraction of the free
+ * device memory.  A request's result does not depend on when it was admitted
+ * or on the other requests of its block. */
 typedef struct ddlr_server_ctx *ddlr_server;
 
 typedef struct {
-  int max_concurrent;      /* batches on the GPU at the same time (default 4)   */
-  int max_batch;           /* right-hand sides per batched solve, 1..64 (16)    */
+  int max_concurrent;      /* models with a block on the GPU at once (default 8) */
+  int max_batch;           /* columns (slots) of a model's block, 1..64 (16)    */
   double tol;              /* relative residual target (1e-8)                   */
   int maxit;               /* iteration cap (500)                               */
   double memory_fraction;  /* share of free device memory usable (0.9)          */
@@ -389,17 +394,21 @@ ddlr_status ddlr_server_submit(ddlr_server s, int model, const double *b,
                                long long *request);
 
 /* Waits for a request (timeout_s <= 0: no limit; TIMEOUT when it expires),
- * copies x (host, n values; may be NULL), its solve info, the latency from
- * submit to completion in seconds and the width of the batch it ran in, then
- * forgets the request.  Returns the request's solve status. */
+ * copies x (host, n values; may be NULL), its solve info (relres: the true
+ * residual of the check that ended the solve; for NOCONV the recursive one),
+ * the latency from submit to completion in seconds and the width of the block
+ * when it finished, then forgets the request.  Returns the request's solve
+ * status. */
 ddlr_status ddlr_server_wait(ddlr_server s, long long request, double timeout_s,
                              double *x, ddlr_solve_info *info,
                              double *latency_s, int *batch);
 
-/* Completed requests, widest batch and most batches in flight seen, models. */
+/* Completed requests, most occupied slots of one block and most blocks on
+ * the GPU seen, models, and the requests admitted into a block in which other
+ * requests were running (continuous batching at work). */
 ddlr_status ddlr_server_stats(ddlr_server s, long long *completed,
                               int *max_batch_seen, int *max_inflight_seen,
-                              int *nmodels);
+                              int *nmodels, long long *admitted_running);
 
 /* Text of the server's last error (never NULL). */
 const char *ddlr_server_last_error(ddlr_server s);

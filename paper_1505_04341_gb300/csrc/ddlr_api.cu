@@ -2488,6 +2488,44 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   KL(c, "pcg_mr_p", c->stream, k_pcgmr_p, eblk(nR, bd), bd, 0, (long long)n, B.st, B.Z, B.P, flexible ? B.Zo : (double *)nullptr);
 }
 
+// the captured graph of one batched iteration of width R on c->stream (a
+// stream in capture mode must not be the caller's legacy stream, so callers
+// capture on the handle's internal stream)
+void mr_graph(ddlr_ctx *c, int R, int flexible) {
+  auto &GR = c->bt.graphs[R];
+  if (GR.exec != nullptr && GR.flex == flexible) return;
+  if (GR.exec) { cudaGraphExecDestroy(GR.exec); GR.exec = nullptr; }
+  const long long l0 = c->launches;
+  const std::vector<long long> f0 = c->fam_cnt;
+  ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+  pcg_mr_iteration(c, R, flexible);
+  cudaGraph_t g = nullptr;
+  ck(cudaStreamEndCapture(c->stream, &g), "capture");
+  cudaError_t e = cudaGraphInstantiate(&GR.exec, g, 0);
+  cudaGraphDestroy(g);
+  ck(e, "cudaGraphInstantiate");
+  GR.flex = flexible;
+  GR.nodes = c->launches - l0;
+  GR.fam_nodes.assign(c->fam_cnt.size(), 0);
+  for (size_t i = 0; i < c->fam_cnt.size(); i++)
+    GR.fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+  c->launches = l0;
+  for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+  for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+}
+
+// one batched iteration of width R on c->stream (the graph when use_graph)
+void mr_iterate(ddlr_ctx *c, int R, int flexible, bool use_graph) {
+  if (use_graph) {
+    auto &GR = c->bt.graphs[R];
+    ck(cudaGraphLaunch(GR.exec, c->stream), "cudaGraphLaunch");
+    c->launches += GR.nodes;
+    for (size_t i = 0; i < GR.fam_nodes.size(); i++) c->fam_cnt[i] += GR.fam_nodes[i];
+  } else {
+    pcg_mr_iteration(c, R, flexible);
+  }
+}
+
 // block PCG on B.B (device order, row-major, R columns) -> B.X
 void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info) {
   auto &B = c->bt;
@@ -2521,38 +2559,10 @@ void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info
   KL(c, "pcg_mr", c->stream, k_pcgmr_rz0, 1, kScalarThreads, 0, B.st, part, kRedGrid);
   ck(cudaMemcpyAsync(B.P, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
   ck(cudaMemcpyAsync(B.Zo, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  auto &GR = B.graphs[R];
-  if (use_graph && (GR.exec == nullptr || GR.flex != flexible)) {
-    if (GR.exec) { cudaGraphExecDestroy(GR.exec); GR.exec = nullptr; }
-    const long long l0 = c->launches;
-    const std::vector<long long> f0 = c->fam_cnt;
-    ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
-    pcg_mr_iteration(c, R, flexible);
-    cudaGraph_t g = nullptr;
-    ck(cudaStreamEndCapture(c->stream, &g), "capture");
-    cudaError_t e = cudaGraphInstantiate(&GR.exec, g, 0);
-    cudaGraphDestroy(g);
-    ck(e, "cudaGraphInstantiate");
-    GR.flex = flexible;
-    GR.nodes = c->launches - l0;
-    GR.fam_nodes.assign(c->fam_cnt.size(), 0);
-    for (size_t i = 0; i < c->fam_cnt.size(); i++)
-      GR.fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
-    c->launches = l0;
-    for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
-    for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
-  }
+  if (use_graph) mr_graph(c, R, flexible);
   const int batch = 4;
   for (int it = 0; it < maxit + batch; it += batch) {
-    for (int bi = 0; bi < batch; bi++) {
-      if (use_graph) {
-        ck(cudaGraphLaunch(GR.exec, c->stream), "cudaGraphLaunch");
-        c->launches += GR.nodes;
-        for (size_t i = 0; i < GR.fam_nodes.size(); i++) c->fam_cnt[i] += GR.fam_nodes[i];
-      } else {
-        pcg_mr_iteration(c, R, flexible);
-      }
-    }
+    for (int bi = 0; bi < batch; bi++) mr_iterate(c, R, flexible, use_graph);
     int done = 0;
     ck(cudaMemcpyAsync(c->h_pin, gate, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
     ck(cudaStreamSynchronize(c->stream), "sync");
@@ -2652,18 +2662,215 @@ ddlr_status run_guarded(ddlr_ctx *c, const std::function<ddlr_status()> &f) {
 
 }  // namespace
 
-// batched PCG of R host right-hand sides (column-major n x R, ld n) into host
-// x through the batched kernels (also for R = 1): the serving runtime's solve
-ddlr_status pcg_batched_host(ddlr_ctx *c, const double *b, double *x, int R, double tol, int maxit,
-                             ddlr_solve_info *info) {
+// ------------------------------------------------ continuous batching (serving)
+// A block PCG of width R whose columns ("slots") are admitted and retired
+// between iterations (ddlr_batch.cuh, continuous batching).  The block's
+// buffers and per-column state stay on the device; idle slots are done
+// columns, which the step kernels skip.
+namespace {
+struct SlotSolver {
+  bool open = false;
+  int R = 0, maxit = 500;
+  double tol = 1e-8;
+  int *mask = nullptr;           // device, kMaxR ints
+  PcgStateMR hs{};               // host copy after the last run
+};
+std::mutex g_slots_mu;
+std::map<ddlr_ctx *, SlotSolver> g_slots;
+SlotSolver &slots_of(ddlr_ctx *c) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  return g_slots[c];
+}
+// capture the iteration graph of width R on the internal stream
+void slots_capture(ddlr_ctx *c, int R, int flexible) {
+  cudaStream_t user = c->stream;
+  ck(cudaEventRecord(c->ev_fork, user), "event");
+  ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+  c->stream = c->gstream;
+  try {
+    mr_graph(c, R, flexible);
+  } catch (...) {
+    c->stream = user;
+    throw;
+  }
+  ck(cudaEventRecord(c->ev_join, c->stream), "event");
+  ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
+  c->stream = user;
+}
+}  // namespace
+
+ddlr_status slots_open(ddlr_ctx *c, int R, double tol, int maxit) {
   return run_guarded(c, [&]() -> ddlr_status {
-    const int n = c->P.n;
+    if (R < 1 || R > std::min(kMaxR, std::max(1, batch_width(c)))) throw Fail{DDLR_ERR_INVALID, "slot width"};
+    SlotSolver &S = slots_of(c);
+    auto &B = c->bt;
     batch_alloc(c, R);
-    batch_load(c, b, n, R, true, c->bt.B);
-    pcg_mr_dev(c, R, tol, maxit, info);
-    batch_store(c, c->bt.X, x, n, R, true);
+    batch_autotune(c, R);
+    B.last_R = R;
+    if (!S.mask) S.mask = c->alloc<int>(kMaxR);
+    const size_t nR = size_t(c->P.n) * R;
+    for (double *v : {B.B, B.X, B.Rr, B.Z, B.P, B.Zo, B.Q, B.T})
+      ck(cudaMemsetAsync(v, 0, sizeof(double) * nR, c->stream), "memset");
+    PcgStateMR h{};
+    h.R = R; h.maxit = maxit; h.flexible = c->opt.precision == 1 ? 1 : 0;
+    h.all_done = 1; h.no_check = 1;
+    for (int q = 0; q < kMaxR; q++) h.done[q] = 1;
+    ck(cudaMemcpyAsync(B.st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream), "H2D");
+    S.hs = h;
+    S.R = R; S.tol = tol; S.maxit = maxit; S.open = true;
+    const char *ng = getenv("DDLR_NO_GRAPH");
+    if (!(c->timing || (ng && ng[0] == '1'))) slots_capture(c, R, h.flexible);
+    sync(c);
     return DDLR_OK;
   });
+}
+
+// lay the open block out again as R1 columns, new column q = old column
+// map[q] (map[q] < 0: a new idle column): every FP64 block that carries state
+// across iterations is moved, and the per-column state with it, so the moved
+// columns continue exactly as before (widening, and narrowing to the busy
+// columns)
+ddlr_status slots_resize(ddlr_ctx *c, int R1, const int *map) {
+  return run_guarded(c, [&]() -> ddlr_status {
+    SlotSolver &S = slots_of(c);
+    if (!S.open) throw Fail{DDLR_ERR_INVALID, "no open slots"};
+    const int R0 = S.R;
+    if (R1 < 1 || R1 > std::min(kMaxR, std::max(1, batch_width(c)))) throw Fail{DDLR_ERR_INVALID, "slot width"};
+    for (int q = 0; q < R1; q++)
+      if (map[q] >= R0) throw Fail{DDLR_ERR_INVALID, "slot map"};
+    const long long n = c->P.n;
+    auto &B = c->bt;
+    std::vector<void *> tmp;
+    double *src[5] = {B.B, B.X, B.Rr, B.P, B.Zo};
+    double *save[5];
+    for (int i = 0; i < 5; i++) {
+      void *p = nullptr;
+      ck(cudaMallocAsync(&p, sizeof(double) * size_t(n) * R0, c->stream), "cudaMallocAsync");
+      tmp.push_back(p);
+      save[i] = static_cast<double *>(p);
+      ck(cudaMemcpyAsync(save[i], src[i], sizeof(double) * size_t(n) * R0, cudaMemcpyDeviceToDevice, c->stream),
+         "copy");
+    }
+    PcgStateMR o{};
+    ck(cudaMemcpyAsync(&o, B.st, sizeof(o), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    sync(c);
+    // the per-column state, permuted on the host
+    PcgStateMR st = o;
+    for (int q = 0; q < kMaxR; q++) {
+      const int f = q < R1 ? map[q] : -1;
+      if (f >= 0) {
+        st.rz[q] = o.rz[f]; st.pq[q] = o.pq[f]; st.alpha[q] = o.alpha[f]; st.beta[q] = o.beta[f];
+        st.rr[q] = o.rr[f]; st.bb[q] = o.bb[f]; st.tol2[q] = o.tol2[f]; st.rt2[q] = o.rt2[f];
+        st.its[q] = o.its[f]; st.done[q] = o.done[f]; st.status[q] = o.status[f]; st.check[q] = o.check[f];
+        st.restart[q] = o.restart[f]; st.fresh[q] = o.fresh[f];
+      } else {
+        st.rz[q] = st.pq[q] = st.alpha[q] = st.beta[q] = st.rr[q] = st.bb[q] = st.tol2[q] = st.rt2[q] = 0.0;
+        st.its[q] = 0; st.done[q] = 1; st.status[q] = 0; st.check[q] = 0; st.restart[q] = 0; st.fresh[q] = 0;
+      }
+    }
+    st.R = R1;
+    int all = 1;
+    for (int q = 0; q < R1; q++) all &= st.done[q];
+    st.all_done = all;
+    batch_alloc(c, R1);                  // reallocates the block buffers when wider than before
+    batch_autotune(c, R1);
+    B.last_R = R1;
+    int hmap[kMaxR];
+    for (int q = 0; q < kMaxR; q++) hmap[q] = q < R1 ? map[q] : -1;
+    ck(cudaMemcpyAsync(S.mask, hmap, sizeof(hmap), cudaMemcpyHostToDevice, c->stream), "H2D");
+    ck(cudaMemcpyAsync(B.st, &st, sizeof(st), cudaMemcpyHostToDevice, c->stream), "H2D");
+    double *dst[5] = {B.B, B.X, B.Rr, B.P, B.Zo};
+    for (int i = 0; i < 5; i++)
+      KL(c, "slots", c->stream, k_relayout, eblk(n * R1, 256), 256, 0, n, R0, R1, S.mask, save[i], dst[i]);
+    for (double *v : {B.Z, B.Q, B.T})
+      ck(cudaMemsetAsync(v, 0, sizeof(double) * size_t(n) * R1, c->stream), "memset");
+    for (void *p : tmp) ck(cudaFreeAsync(p, c->stream), "cudaFreeAsync");
+    S.R = R1;
+    S.hs = st;
+    const char *ng = getenv("DDLR_NO_GRAPH");
+    if (!(c->timing || (ng && ng[0] == '1'))) slots_capture(c, R1, c->opt.precision == 1 ? 1 : 0);
+    sync(c);
+    return DDLR_OK;
+  });
+}
+
+// admit right-hand sides b[i] (host, original order) into free slots slot[i]
+ddlr_status slots_admit(ddlr_ctx *c, int cnt, const int *slot, const double *const *b) {
+  return run_guarded(c, [&]() -> ddlr_status {
+    SlotSolver &S = slots_of(c);
+    if (!S.open) throw Fail{DDLR_ERR_INVALID, "no open slots"};
+    const int n = c->P.n, R = S.R;
+    auto &B = c->bt;
+    int hm[kMaxR] = {0};
+    for (int i = 0; i < cnt; i++) {
+      const int q = slot[i];
+      if (q < 0 || q >= R || hm[q] || !S.hs.done[q]) throw Fail{DDLR_ERR_INVALID, "slot not free"};
+      hm[q] = 1;
+      // staging: the first n doubles of the S block per admitted column
+      ck(cudaMemcpyAsync(B.S, b[i], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "H2D");
+      KL(c, "slots", c->stream, k_col_in, nblk(n), kThreads, 0, n, R, q, c->perm, B.S, B.B);
+    }
+    ck(cudaMemcpyAsync(S.mask, hm, sizeof(hm), cudaMemcpyHostToDevice, c->stream), "H2D");
+    KL(c, "slots", c->stream, k_slot_reset, eblk((long long)n * R, 256), 256, 0, (long long)n, R, S.mask, B.B, B.X,
+       B.Rr, B.P);
+    KL(c, "slots", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.B, B.B, (const double *)nullptr,
+       B.part64, (const int *)nullptr);
+    KL(c, "slots", c->stream, k_slot_init, 1, kScalarThreads, 0, B.st, B.part64, kRedGrid, S.mask, R, S.tol,
+       S.maxit, c->opt.precision == 1 ? 1 : 0);
+    sync(c);       // the host vectors may be released when this returns
+    for (int i = 0; i < cnt; i++) S.hs.done[slot[i]] = 0;
+    return DDLR_OK;
+  });
+}
+
+// run `iters` iterations of the open block; done[q] (host, R ints) then
+// tells which slots have finished (idle slots included)
+ddlr_status slots_run(ddlr_ctx *c, int iters, int *done) {
+  return run_guarded(c, [&]() -> ddlr_status {
+    SlotSolver &S = slots_of(c);
+    if (!S.open) throw Fail{DDLR_ERR_INVALID, "no open slots"};
+    const int flexible = c->opt.precision == 1 ? 1 : 0;
+    const char *ng = getenv("DDLR_NO_GRAPH");
+    const bool use_graph = !(c->timing || (ng && ng[0] == '1'));
+    if (use_graph && !c->bt.graphs[S.R].exec) slots_capture(c, S.R, flexible);
+    for (int i = 0; i < iters; i++) mr_iterate(c, S.R, flexible, use_graph);
+    int dfl[4];
+    ck(cudaMemcpyAsync(&S.hs, c->bt.st, sizeof(S.hs), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    ck(cudaMemcpyAsync(dfl, c->dflag, sizeof(dfl), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    sync(c);
+    if (dfl[3]) timeout_fail(c);
+    for (int q = 0; q < S.R; q++) done[q] = S.hs.done[q];
+    return DDLR_OK;
+  });
+}
+
+// the result of a finished slot (x: host, original order); the slot is free
+// afterwards.  relres: the true residual of the check that ended the solve
+// (status OK), else the recursive residual.
+ddlr_status slots_take(ddlr_ctx *c, int slot, double *x, ddlr_solve_info *info) {
+  return run_guarded(c, [&]() -> ddlr_status {
+    SlotSolver &S = slots_of(c);
+    if (!S.open || slot < 0 || slot >= S.R || !S.hs.done[slot]) throw Fail{DDLR_ERR_INVALID, "slot not finished"};
+    const int n = c->P.n;
+    auto &B = c->bt;
+    KL(c, "slots", c->stream, k_col_out, nblk(n), kThreads, 0, n, S.R, slot, c->perm, B.X, B.S);
+    ck(cudaMemcpyAsync(x, B.S, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    sync(c);
+    const PcgStateMR &h = S.hs;
+    info->its = h.its[slot];
+    const double bb = h.bb[slot];
+    const double r2 = h.status[slot] == 0 ? h.rt2[slot] : h.rr[slot];
+    info->relres = bb > 0 ? std::sqrt(r2 / bb) : 0.0;
+    info->status = h.status[slot] == 0 ? DDLR_OK : (h.status[slot] == 5 ? DDLR_ERR_NOCONV : DDLR_ERR_NAN);
+    return DDLR_OK;
+  });
+}
+
+int slots_width(ddlr_ctx *c) { return slots_of(c).R; }
+
+void slots_forget(ddlr_ctx *c) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  g_slots.erase(c);
 }
 
 extern "C" {
@@ -3363,6 +3570,7 @@ const char *ddlr_last_error(ddlr_handle c) {
 
 ddlr_status ddlr_destroy(ddlr_handle c) {
   if (!c) return DDLR_OK;
+  slots_forget(c);
   if (c->stream2) cudaStreamSynchronize(c->stream2);
   cudaStreamSynchronize(c->stream);
   c->resolve();

@@ -515,6 +515,7 @@ struct PcgStateMR {
   double rz[kMaxR], pq[kMaxR], alpha[kMaxR], beta[kMaxR], rr[kMaxR], bb[kMaxR];
   double tol2[kMaxR], rt2[kMaxR];
   int its[kMaxR], done[kMaxR], status[kMaxR], check[kMaxR], restart[kMaxR];
+  int fresh[kMaxR];   // admitted into a running block: joins at the next preconditioner step
   int R, maxit, flexible, all_done, any_check;
   int no_check;   // 1 unless some column's true residual is to be checked this iteration
   int pad[2];
@@ -548,7 +549,7 @@ __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int 
     const double bb = sm[q];
     st->bb[q] = bb;
     st->tol2[q] = tol * tol * bb;
-    st->its[q] = 0; st->status[q] = 0; st->check[q] = 0; st->restart[q] = 0;
+    st->its[q] = 0; st->status[q] = 0; st->check[q] = 0; st->restart[q] = 0; st->fresh[q] = 0;
     st->done[q] = (bb == 0.0) ? 1 : 0;
     st->rz[q] = 0;
   }
@@ -579,7 +580,7 @@ __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
   col_sums(partials, G, R, R, sm);
   if (q < R) {
     double a = 0.0;
-    if (!st->done[q]) {
+    if (!st->done[q] && !st->fresh[q]) {
       const double pq = sm[q];
       st->pq[q] = pq;
       a = st->rz[q] / pq;
@@ -610,7 +611,7 @@ __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
   __shared__ double sm[kMaxR];
   if (q == 0) anyc = 0;
   col_sums(partials, G, R, R, sm);
-  if (q < R && !st->done[q]) {
+  if (q < R && !st->done[q] && !st->fresh[q]) {
     const double rr = sm[q];
     st->rr[q] = rr;
     st->its[q] += 1;
@@ -682,10 +683,11 @@ __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
     const double rzn = sm[q];
     const double rzo = sm[R + q];
     double beta = st->flexible ? (rzn - rzo) / st->rz[q] : rzn / st->rz[q];
-    if (st->restart[q]) beta = 0.0;
+    if (st->restart[q] || st->fresh[q]) beta = 0.0;
     st->beta[q] = beta;
     st->rz[q] = rzn;
     st->restart[q] = 0;
+    st->fresh[q] = 0;
     if (!(rzn == rzn) || isinf(rzn)) { st->status[q] = 7; st->done[q] = 1; }
   }
   __syncthreads();
@@ -707,6 +709,76 @@ __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, do
   const double z = Z[idx];
   P[idx] = z + st->beta[q] * P[idx];
   if (Zold) Zold[idx] = z;
+}
+
+// ------------------------------------------------ continuous batching (serving)
+// A column admitted into a running block starts as a fresh solve (x0 = 0,
+// r = b, p = 0) marked `fresh`: in the next iteration the step and the
+// residual test skip it (alpha = 0 against p = 0 and A p = 0 leaves x and r
+// unchanged), the preconditioner gives z = M^-1 b, r.z becomes its rz and
+// beta = 0 makes p = z -- the state a solve started alone has after its
+// initial apply.  Every later iteration of the column is the same arithmetic
+// as alone, so its result does not depend on when it was admitted or which
+// other columns share the block.
+
+// column q of a row-major n x R block <- a vector in original order
+__global__ void k_col_in(int n, int R, int q, const int *perm, const double *in, double *out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[(long long)g * R + q] = in[perm[g]];
+}
+// a vector in original order <- column q of a row-major n x R block
+__global__ void k_col_out(int n, int R, int q, const int *perm, const double *in, double *out) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[perm[g]] = in[(long long)g * R + q];
+}
+// admitted columns (mask[q] != 0): X = 0, Rr = B, P = 0
+__global__ void k_slot_reset(long long n, int R, const int *mask, const double *B, double *X, double *Rr,
+                             double *P) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R) return;
+  const int q = col_of(idx, row_of(idx, R), R);
+  if (!mask[q]) return;
+  X[idx] = 0.0;
+  Rr[idx] = B[idx];
+  P[idx] = 0.0;
+}
+// the per-column state of the admitted columns (partials: column sums of B.B)
+__global__ void k_slot_init(PcgStateMR *st, const double *partials, int G, const int *mask, int R, double tol,
+                            int maxit, int flexible) {
+  const int q = threadIdx.x;
+  __shared__ double sm[kMaxR];
+  col_sums(partials, G, R, R, sm);
+  if (q == 0) { st->R = R; st->maxit = maxit; st->flexible = flexible; }
+  if (q < R && mask[q]) {
+    const double bb = sm[q];
+    st->bb[q] = bb;
+    st->tol2[q] = tol * tol * bb;
+    st->rt2[q] = 0.0;
+    st->rr[q] = bb;
+    st->its[q] = 0; st->status[q] = 0; st->check[q] = 0;
+    st->done[q] = (bb == 0.0) ? 1 : 0;
+    st->fresh[q] = 1;       // beta = 0 at its first preconditioner step (and
+    st->restart[q] = 0;     // no copy of a true residual: restart is the
+    st->rz[q] = 0.0;        // mark of a failed check of this iteration)
+  }
+  __syncthreads();
+  if (q == 0) {
+    int all = 1;
+    for (int c = 0; c < R; c++) all &= st->done[c];
+    st->all_done = all;
+    st->any_check = 0;
+    st->no_check = 1;
+  }
+}
+// a block of R0 columns laid out again as R1 columns: column q of the new
+// block is column map[q] of the old one (map[q] < 0: a new, zero column)
+__global__ void k_relayout(long long n, int R0, int R1, const int *map, const double *in, double *out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * R1) return;
+  const long long r = row_of(idx, R1);
+  const int q = col_of(idx, r, R1);
+  const int o = map[q];
+  out[idx] = o >= 0 ? in[r * R0 + o] : 0.0;
 }
 
 // Tt = B - Q (all columns)

@@ -2,15 +2,20 @@
 // continuous batching, memory-based admission.
 //
 // Every registered model (a matrix with its DDLR setup) keeps its factors and
-// low-rank data resident and owns a worker thread with its own CUDA streams.
-// A worker takes every request of its model that is waiting when it becomes
-// free (up to max_batch) and solves them together in one batched PCG; requests
-// that arrive meanwhile wait for the next batch.  At most max_concurrent
-// batches are on the GPU at once across models, so work of different models
-// overlaps on the device.  A batch is admitted only if its workspace fits in
-// the device memory the server may use; otherwise it is narrowed, down to one
-// right-hand side.  The batched solve gives a column the same bits whatever
-// else shares its batch, so a request's result does not depend on the mix.
+// low-rank data resident and owns a worker thread with its own CUDA stream.
+// The worker runs a block PCG whose columns are slots: between chunks of a few
+// iterations it retires the columns that have converged (their results go
+// back to the waiting callers at once) and admits queued requests into the
+// free slots, so a request never waits for a whole batch to finish.  When
+// requests queue up and every slot is busy, the block is widened (up to
+// max_batch columns) without disturbing the running columns.  At most
+// max_concurrent models have a block on the GPU at once, so work of different
+// models overlaps on the device; while another model waits for a place, a
+// block admits nothing more and gives its place back once it drains.  A block is opened or widened only if its
+// workspace fits in the device memory the server may use; otherwise it stays
+// narrower, down to one column.  A column's iterates do not depend on when it
+// was admitted or what shares its block, so a request's result is the same
+// alone and in the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +54,11 @@ struct Model {
   long long nnz = 0;
   std::deque<std::shared_ptr<Request>> queue;
   std::thread worker;
+  // the open block (worker thread; under the server mutex where shared)
+  int width = 0;                                  // columns of the open block (0: none)
+  int active = 0;                                 // occupied slots
+  std::vector<std::shared_ptr<Request>> slot;     // request of each slot (null: free)
+  long long reserved = 0;                         // workspace bytes counted for the block
 };
 
 }  // namespace
@@ -62,63 +72,172 @@ struct ddlr_server_ctx {
   std::map<long long, std::shared_ptr<Request>> reqs;
   long long next_id = 1;
   int inflight = 0;
+  int waiting = 0;          // models waiting for a place on the GPU
   bool stop = false;
   long long completed = 0;
   int max_batch_seen = 0, max_inflight_seen = 0;
+  long long admitted_running = 0;   // admissions into a block with other requests running
   long long reserved = 0;   // workspace bytes admitted and not yet released
   std::string err;
 };
 
 namespace {
 
-// device bytes of a batch of R right-hand sides (FP64 PCG blocks, apply
+// device bytes of a block of R right-hand sides (FP64 PCG blocks, apply
 // workspaces, FP32 copies), a conservative estimate
 long long batch_bytes(int n, int R) { return (long long)n * R * (14 * 8 + 7 * 4) + (1 << 20); }
 
-void worker_loop(ddlr_server_ctx *S, Model *M, int mi) {
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// widest block of at most `want` columns whose workspace fits the memory the
+// server may still use (at least one column); S->mu held
+int fit_width(ddlr_server_ctx *S, Model *M, int want) {
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  const long long budget = (long long)(S->opt.memory_fraction * double(fr)) - S->reserved + M->reserved;
+  int R = std::max(1, std::min(want, S->opt.max_batch));
+  while (R > 1 && batch_bytes(M->n, R) > budget) R /= 2;
+  return R;
+}
+
+void fail_all(ddlr_server_ctx *S, Model *M, ddlr_status st) {
+  const Clock::time_point t = Clock::now();
+  for (auto &rq : M->slot) {
+    if (!rq) continue;
+    rq->info = ddlr_solve_info{0, 0.0, int(st)};
+    rq->x.assign(size_t(M->n), 0.0);
+    rq->t_done = t;
+    rq->batch = M->width;
+    rq->done = true;
+    S->completed++;
+    rq.reset();
+  }
+  M->active = 0;
+}
+
+void worker_loop(ddlr_server_ctx *S, Model *M) {
   cudaSetDevice(S->device);
+  constexpr int kItersPerPoll = 4;
+  std::vector<int> done;
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
-    S->cv_work.wait(lk, [&] { return S->stop || !M->queue.empty(); });
+    S->cv_work.wait(lk, [&] { return S->stop || !M->queue.empty() || M->active > 0; });
     if (S->stop) break;
-    S->cv_slot.wait(lk, [&] { return S->stop || S->inflight < S->opt.max_concurrent; });
-    if (S->stop) break;
-    // admission: widest batch whose workspace fits the memory budget
-    int R = std::min<int>((int)M->queue.size(), S->opt.max_batch);
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    const long long budget = (long long)(S->opt.memory_fraction * double(fr)) - S->reserved;
-    while (R > 1 && batch_bytes(M->n, R) > budget) R /= 2;
-    std::vector<std::shared_ptr<Request>> batch(M->queue.begin(), M->queue.begin() + R);
-    M->queue.erase(M->queue.begin(), M->queue.begin() + R);
-    const long long bytes = batch_bytes(M->n, R);
-    S->reserved += bytes;
-    S->inflight++;
-    S->max_inflight_seen = std::max(S->max_inflight_seen, S->inflight);
-    S->max_batch_seen = std::max(S->max_batch_seen, R);
+    int open_w = 0, resize_w = 0;
+    std::vector<int> map;
+    if (M->width == 0) {
+      // a new block: needs one of the max_concurrent places on the GPU
+      S->waiting++;
+      S->cv_slot.wait(lk, [&] { return S->stop || S->inflight < S->opt.max_concurrent; });
+      S->waiting--;
+      if (S->stop) break;
+      if (M->queue.empty()) continue;
+      open_w = fit_width(S, M, pow2_at_least(int(M->queue.size())));
+      S->inflight++;
+      S->max_inflight_seen = std::max(S->max_inflight_seen, S->inflight);
+      const long long bytes = batch_bytes(M->n, open_w);
+      S->reserved += bytes - M->reserved;
+      M->reserved = bytes;
+      M->width = open_w;
+      M->slot.assign(size_t(open_w), nullptr);
+    } else if (!M->queue.empty() && M->active == M->width && M->width < S->opt.max_batch && S->waiting == 0) {
+      // every slot busy and requests waiting: widen the block (the running
+      // columns keep their slots)
+      const int w = fit_width(S, M, pow2_at_least(M->active + int(M->queue.size())));
+      if (w > M->width) {
+        resize_w = w;
+        map.assign(size_t(w), -1);
+        for (int q = 0; q < M->width; q++) map[q] = q;
+        M->slot.resize(size_t(w));
+      }
+    } else if ((M->queue.empty() || S->waiting > 0) && M->active > 0 && M->active * 4 <= M->width) {
+      // few columns left in a wide block: narrow it to them (an iteration
+      // costs in proportion to the width)
+      const int w = pow2_at_least(M->active);
+      resize_w = w;
+      map.assign(size_t(w), -1);
+      std::vector<std::shared_ptr<Request>> ns(static_cast<size_t>(w), nullptr);
+      int j = 0;
+      for (int q = 0; q < M->width; q++)
+        if (M->slot[q]) { map[j] = q; ns[j] = M->slot[q]; j++; }
+      M->slot.swap(ns);
+    }
+    if (resize_w) {
+      const long long bytes = batch_bytes(M->n, resize_w);
+      S->reserved += bytes - M->reserved;
+      M->reserved = bytes;
+      M->width = resize_w;
+    }
+    // admission into the free slots, first come first served; while other
+    // models wait for a place on the GPU, an open block admits nothing more
+    // and drains, so the places go round
+    const int running = M->active;
+    const bool drain = open_w == 0 && S->waiting > 0 && running > 0;
+    std::vector<int> adm_slot;
+    std::vector<const double *> adm_b;
+    for (int q = 0; q < M->width && !M->queue.empty() && !drain; q++) {
+      if (M->slot[q]) continue;
+      M->slot[q] = M->queue.front();
+      M->queue.pop_front();
+      adm_slot.push_back(q);
+      adm_b.push_back(M->slot[q]->b.data());
+      M->active++;
+    }
+    S->max_batch_seen = std::max(S->max_batch_seen, M->active);
+    if (running > 0) S->admitted_running += (long long)adm_slot.size();
     lk.unlock();
-    const int n = M->n;
-    std::vector<double> B(size_t(n) * R), X(size_t(n) * R);
-    for (int q = 0; q < R; q++) std::memcpy(B.data() + size_t(q) * n, batch[q]->b.data(), sizeof(double) * n);
-    std::vector<ddlr_solve_info> info(R);
-    const ddlr_status st = pcg_batched_host(M->h, B.data(), X.data(), R, S->opt.tol, S->opt.maxit, info.data());
+    ddlr_status st = DDLR_OK;
+    if (open_w) st = slots_open(M->h, open_w, S->opt.tol, S->opt.maxit);
+    if (st == DDLR_OK && resize_w) st = slots_resize(M->h, resize_w, map.data());
+    if (st == DDLR_OK && !adm_slot.empty())
+      st = slots_admit(M->h, int(adm_slot.size()), adm_slot.data(), adm_b.data());
+    done.assign(size_t(M->width), 0);
+    if (st == DDLR_OK) st = slots_run(M->h, kItersPerPoll, done.data());
+    // results of the finished columns, copied out before taking the lock
+    std::vector<std::pair<int, ddlr_solve_info>> fin;
+    std::vector<std::vector<double>> xs;
+    if (st == DDLR_OK) {
+      for (int q = 0; q < M->width; q++) {
+        if (!done[q] || !M->slot[q]) continue;
+        ddlr_solve_info inf{};
+        std::vector<double> x(size_t(M->n));
+        st = slots_take(M->h, q, x.data(), &inf);
+        if (st != DDLR_OK) break;
+        fin.emplace_back(q, inf);
+        xs.push_back(std::move(x));
+      }
+    }
     const Clock::time_point t = Clock::now();
     lk.lock();
-    S->reserved -= bytes;
-    S->inflight--;
-    for (int q = 0; q < R; q++) {
-      Request &rq = *batch[q];
-      rq.x.assign(X.begin() + size_t(q) * n, X.begin() + size_t(q + 1) * n);
-      rq.info = info[q];
-      if (st != DDLR_OK && st != DDLR_ERR_NOCONV && st != DDLR_ERR_NAN) rq.info.status = st;
-      rq.t_done = t;
-      rq.batch = R;
-      rq.done = true;
-      S->completed++;
+    if (st != DDLR_OK) {
+      S->err = ddlr_last_error(M->h);
+      fail_all(S, M, st);
+    } else {
+      for (size_t i = 0; i < fin.size(); i++) {
+        std::shared_ptr<Request> &rq = M->slot[fin[i].first];
+        rq->x = std::move(xs[i]);
+        rq->info = fin[i].second;
+        rq->t_done = t;
+        rq->batch = M->width;
+        rq->done = true;
+        S->completed++;
+        rq.reset();
+        M->active--;
+      }
     }
-    (void)mi;
-    S->cv_slot.notify_all();
-    S->cv_done.notify_all();
+    if (M->active == 0 && (M->queue.empty() || st != DDLR_OK || S->waiting > 0)) {
+      // the block drains (or failed, or others wait): give its place back
+      S->inflight--;
+      S->reserved -= M->reserved;
+      M->reserved = 0;
+      M->width = 0;
+      S->cv_slot.notify_all();
+    }
+    if (!fin.empty() || st != DDLR_OK) S->cv_done.notify_all();
   }
 }
 
@@ -130,7 +249,7 @@ const char *ddlr_server_last_error(ddlr_server S) { return S ? S->err.c_str() : 
 
 ddlr_status ddlr_server_options_default(ddlr_server_options *o) {
   if (!o) return DDLR_ERR_INVALID;
-  o->max_concurrent = 4;
+  o->max_concurrent = 8;
   o->max_batch = 16;
   o->tol = 1e-8;
   o->maxit = 500;
@@ -192,7 +311,7 @@ ddlr_status ddlr_server_add_model(ddlr_server S, int n, const int *rowptr, const
   const int mi = int(S->models.size());
   Model *mp = M.get();
   S->models.push_back(std::move(M));
-  mp->worker = std::thread(worker_loop, S, mp, mi);
+  mp->worker = std::thread(worker_loop, S, mp);
   *model = mi;
   return DDLR_OK;
 }
@@ -236,12 +355,13 @@ ddlr_status ddlr_server_wait(ddlr_server S, long long request, double timeout_s,
 }
 
 ddlr_status ddlr_server_stats(ddlr_server S, long long *completed, int *max_batch_seen,
-                              int *max_inflight_seen, int *nmodels) {
+                              int *max_inflight_seen, int *nmodels, long long *admitted_running) {
   if (!S) return DDLR_ERR_INVALID;
   std::lock_guard<std::mutex> lk(S->mu);
   if (completed) *completed = S->completed;
   if (max_batch_seen) *max_batch_seen = S->max_batch_seen;
   if (max_inflight_seen) *max_inflight_seen = S->max_inflight_seen;
+  if (admitted_running) *admitted_running = S->admitted_running;
   if (nmodels) *nmodels = int(S->models.size());
   return DDLR_OK;
 }

@@ -129,7 +129,7 @@ def load(path: str | None = None):
         "ddlr_server_wait": ([P, LL, D, P, ctypes.POINTER(ddlr_solve_info),
                               ctypes.POINTER(D), ctypes.POINTER(I)], I),
         "ddlr_server_stats": ([P, ctypes.POINTER(LL), ctypes.POINTER(I), ctypes.POINTER(I),
-                               ctypes.POINTER(I)], I),
+                               ctypes.POINTER(I), ctypes.POINTER(LL)], I),
         "ddlr_server_last_error": ([P], ctypes.c_char_p),
         "ddlr_server_destroy": ([P], I),
     }
@@ -378,9 +378,10 @@ class DDLR:
 
 class Server:
     """Solve service (include/ddlr.h, serving section): resident models,
-    continuous batching across requests, admission by device memory."""
+    continuous batching (slots admitted and retired between iterations),
+    admission by device memory."""
 
-    def __init__(self, max_concurrent=4, max_batch=16, tol=1e-8, maxit=500,
+    def __init__(self, max_concurrent=8, max_batch=16, tol=1e-8, maxit=500,
                  memory_fraction=0.9):
         lib = load()
         o = ddlr_server_options()
@@ -428,12 +429,12 @@ class Server:
         return x, dict(its=info.its, relres=info.relres, status=STATUS[info.status]), lat.value, bw.value
 
     def stats(self) -> dict:
-        c = ctypes.c_longlong()
+        c, ar = ctypes.c_longlong(), ctypes.c_longlong()
         mb, mi, nm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._err(_lib.ddlr_server_stats(self._h, ctypes.byref(c), ctypes.byref(mb), ctypes.byref(mi),
-                                         ctypes.byref(nm)))
+                                         ctypes.byref(nm), ctypes.byref(ar)))
         return dict(completed=c.value, max_batch_seen=mb.value, max_inflight_seen=mi.value,
-                    models=nm.value)
+                    models=nm.value, admitted_running=ar.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

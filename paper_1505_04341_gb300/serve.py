@@ -25,7 +25,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def setup_server(edges, k=16, max_batch=16, max_concurrent=4, tol=1e-8):
+def setup_server(edges, k=16, max_batch=16, max_concurrent=8, tol=1e-8):
     import workloads as W
     from paper_1505_04341_gb300 import Server
     srv = Server(max_concurrent=max_concurrent, max_batch=max_batch, tol=tol)
