@@ -2174,6 +2174,9 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
 }
 
 // ============================================================ batched path
+// row ranges (partial sums) of the tensor-core U_k^T Y
+constexpr int kTcRedGrid = 4 * kRedGrid;
+
 void batch_free(ddlr_ctx *c) {
   auto &B = c->bt;
   for (auto &kv : B.graphs)
@@ -2213,7 +2216,8 @@ void batch_alloc(ddlr_ctx *c, int R) {
     B.w32[4] = (float *)al(k * R * 4);
     B.w32[5] = (float *)al(nR * 4);   // cast input
     B.w32[6] = (float *)al(nR * 4);   // cast output
-    B.part32 = (float *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 4);
+    // the tensor-core U_k^T Y writes kTcRedGrid partials plus a k x R sum
+    B.part32 = (float *)al((size_t(kTcRedGrid) + 1) * std::max<size_t>(k * R, 2 * R) * 4);
   }
   B.part64 = (double *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 8);
   if (c->opt.c_solver == 1)
@@ -2267,10 +2271,10 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
     const T *lv = mode == 5 ? lx : lv0;
     if (c->lv_desc) {
       const int cnt = dptr[L + 1] - dptr[L];
+      const int bd = chunk_block(c, R), rows = (bd / R) * kMrRowsPerThread;
       if (cnt > 0)
-        KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr<T>, (cnt + kThreads - 1) / kThreads,
-           chunk_block(c, R), 0, c->lv_desc + dptr[L], cnt, mode, c->S.l_col, c->S.u_col, lv, uv, di, X, Z, R,
-           gate);
+        KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr<T>, (cnt + rows - 1) / rows, bd, 0,
+           c->lv_desc + dptr[L], cnt, mode, c->S.l_col, c->S.u_col, lv, uv, di, X, Z, R, gate);
       return;
     }
     const int nch = ptr[L + 1] - ptr[L];
@@ -2329,20 +2333,24 @@ void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *ga
     a0_solve_mr<T>(c, X, Z, R, gate);
     KL(c, "et_mr", c->stream, k_et_mr<T>, eblk((long long)s * R, bd), bd, 0, s, m, c->eht_rp, c->eht_ci,
        Prec<T>::eht(c), ia, a, Z, Y, R, gate);
+    bool tc = false;
     if constexpr (std::is_same<T, float>::value) {
-      if (c->bt.tc) {
-        KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
-      } else {
-        KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part,
-           gate);
+      tc = c->bt.tc;
+      if (tc) {
+        // more, shorter row ranges than the scalar form: every CTA of the
+        // tensor-core form is resident at once
+        KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kTcRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+        KL(c, "reduce_mr", c->stream, k_reduce_cols_mr<T>, (unsigned)((k * R + 31) / 32), 256, 0, kTcRedGrid,
+           k * R, R, part, Prec<T>::coef(c), Tm, gate);
       }
-    } else {
-      KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
     }
-    KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, Prec<T>::coef(c),
-       (const T *)nullptr, Tm, gate);
+    if (!tc) {
+      KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)s, k, U, Y, R, part, gate);
+      KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, Prec<T>::coef(c),
+         (const T *)nullptr, Tm, gate);
+    }
     if constexpr (std::is_same<T, float>::value) {
-      if (c->bt.tc) {
+      if (tc) {
         KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr_tc<TU>), (unsigned)((s + 127) / 128), 256, 0, s, m, k, U, Tm, Y,
            Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
       } else {
@@ -2361,12 +2369,21 @@ void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *ga
     bool tc = false;
     if constexpr (std::is_same<T, float>::value) tc = c->bt.tc;
     if constexpr (std::is_same<T, float>::value) {
-      if (tc) KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
+      if (tc) {
+        KL(c, "utx_mr", c->stream, (k_utx_mr_tc<TU>), kTcRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
+        // column sums first, then H_k applied to the k x R block
+        T *tmp = part + size_t(kTcRedGrid) * k * R;
+        KL(c, "reduce_mr", c->stream, k_reduce_cols_mr<T>, (unsigned)((k * R + 31) / 32), 256, 0, kTcRedGrid,
+           k * R, R, part, (const T *)nullptr, tmp, gate);
+        KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, 1, k, R, tmp, (const T *)nullptr, Prec<T>::Hk(c),
+           Tm, gate);
+      }
     }
-    if (!tc)
+    if (!tc) {
       KL(c, "utx_mr", c->stream, (k_utx_mr_partial<T, TU>), kRedGrid, 256, 0, (long long)n, k, U, X, R, part, gate);
-    KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, (const T *)nullptr,
-       Prec<T>::Hk(c), Tm, gate);
+      KL(c, "reduce_mr", c->stream, k_reduce_mr<T>, 1, 256, 0, kRedGrid, k, R, part, (const T *)nullptr,
+         Prec<T>::Hk(c), Tm, gate);
+    }
     if constexpr (std::is_same<T, float>::value) {
       if (tc)
         KL(c, "u_add_mr", c->stream, (k_u_add_mr_tc<TU>), (unsigned)((n + 127) / 128), 256, 0, (long long)n, k, U,
@@ -3524,7 +3541,8 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "sptrsv_levels_mr") b = batch_a0_bytes(c, R) / batch_a0_launches(c);
       else if (f == "et_mr") b = ne * (v + 4.0) + 4.0 * s + 2.0 * s * R * v;
       else if (f == "utx_mr") b = urows * k * ub + urows * R * v;
-      else if (f == "reduce_mr") b = double(kRedGrid) * k * R * v + k * R * v;
+      else if (f == "reduce_mr")
+        b = double(c->opt.precision == 1 && c->bt.tc ? kTcRedGrid : kRedGrid) * k * R * v + k * R * v;
       else if (f == "w_rhs_mr") b = s * k * ub + 4.0 * s * R * v;
       else if (f == "e_int_mr") b = ne * (v + 4.0) + 4.0 * m + 2.0 * m * R * v;
       else if (f == "u_add_mr") b = n * k * ub + 2.0 * n * R * v;

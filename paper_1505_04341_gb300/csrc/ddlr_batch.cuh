@@ -69,12 +69,19 @@ __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
 }
 
 // k_sptrsv_chunks_mr from the level-order descriptor list: CTA q solves rows
-// [q kThreads, (q+1) kThreads) of the level's list (count rows)
+// [q P, (q+1) P) of the level's list (count rows), P = kMrRowsPerThread x the
+// rows a pass of the CTA covers (blockDim / R).  A thread takes its
+// kMrRowsPerThread rows together: the rows of a level depend only on rows of
+// other levels, so their descriptor, operand and gathered loads are all in
+// flight at once (a thread walking its rows one by one kept one dependent
+// chain of loads in flight).  Each row's arithmetic is that of one row alone.
+constexpr int kMrRowsPerThread = 4;
 template <typename T>
 __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
                                  const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
                                  const int *gate) {
   if (gate && *gate) return;
+  constexpr int RR = kMrRowsPerThread;
   const int per = blockDim.x / R;
   const int q = threadIdx.x % R, sub = threadIdx.x / R;
   if (sub >= per) return;
@@ -83,22 +90,59 @@ __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const in
   const bool pre = mode == 5;
   const int *col = bwd ? u_col : l_col;
   const T *val = bwd ? uval : lval;
-  const int i0 = blockIdx.x * kThreads, i1 = min(count, i0 + kThreads);
-  for (int i = i0 + sub; i < i1; i += per) {
-    const int4 dsc = desc[i];
-    const int r = dsc.x, off = bwd ? dsc.z : dsc.y;
-    const int w = bwd ? int(unsigned(dsc.w) >> 16) : int(unsigned(dsc.w) & 0xffffu);
-    const T d = dinv[r];
-    T acc = mode == 4 ? X[(long long)r * R + q] * d : (bwd ? Z : X)[(long long)r * R + q];
-    for (int kk = 0; kk < w; kk++) {
-      const int c = col[off + kk * 32];
-      const T zc = (from_x && !bwd) ? (pre ? X[(long long)c * R + q] : X[(long long)c * R + q] * dinv[c])
-                                    : Z[(long long)c * R + q];
-      acc -= val[off + kk * 32] * zc;
+  const int i0 = blockIdx.x * per * RR;
+  int r[RR], off[RR], w[RR];
+  T acc[RR], d[RR];
+  int wmax = 0;
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    const int i = i0 + sub + u * per;
+    r[u] = -1; off[u] = 0; w[u] = 0;
+    if (i < count) {
+      const int4 dsc = desc[i];
+      r[u] = dsc.x;
+      off[u] = bwd ? dsc.z : dsc.y;
+      w[u] = bwd ? int(unsigned(dsc.w) >> 16) : int(unsigned(dsc.w) & 0xffffu);
+      wmax = max(wmax, w[u]);
     }
-    acc *= d;
-    if (mode == 2 || mode == 3 || mode == 5) acc *= d;
-    Z[(long long)r * R + q] = acc;
+  }
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    acc[u] = T(0);
+    d[u] = T(0);
+    if (r[u] >= 0) {
+      d[u] = dinv[r[u]];
+      const long long e = (long long)r[u] * R + q;
+      acc[u] = mode == 4 ? X[e] * d[u] : (bwd ? Z : X)[e];
+    }
+  }
+  for (int kk = 0; kk < wmax; kk++) {
+    int c[RR];
+    T v[RR], zc[RR];
+#pragma unroll
+    for (int u = 0; u < RR; u++) {
+      if (kk < w[u]) {
+        c[u] = col[off[u] + kk * 32];
+        v[u] = val[off[u] + kk * 32];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RR; u++) {
+      if (kk < w[u]) {
+        const long long e = (long long)c[u] * R + q;
+        zc[u] = (from_x && !bwd) ? (pre ? X[e] : X[e] * dinv[c[u]]) : Z[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RR; u++)
+      if (kk < w[u]) acc[u] -= v[u] * zc[u];
+  }
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    if (r[u] < 0) continue;
+    T a = acc[u] * d[u];
+    if (mode == 2 || mode == 3 || mode == 5) a *= d[u];
+    Z[(long long)r[u] * R + q] = a;
   }
 }
 
@@ -345,6 +389,30 @@ k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *p
       const int c = c0 + g + ((e & 2) ? 8 : 0), q = q0 + 2 * t + (e & 1);
       if (c < k && q < R) partials[(long long)blockIdx.x * no + c * R + q] = acc[sl][e];
     }
+  }
+}
+
+// out[o] = (coef ? coef[o / R] : 1) * sum over g < G of partials[g * no + o]
+// (o < no = k R), in a fixed order: warp w of a CTA sums its eighth of the g
+// range for 32 consecutive o (one per lane, coalesced), then the eight warp
+// sums are added in order.  Grid: ceil(no / 32) CTAs of 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_reduce_cols_mr(int G, int no, int R, const T *partials, const T *coef, T *out, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ T sm[8][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int o = blockIdx.x * 32 + l;
+  const int per = (G + 7) / 8, g0 = w * per, g1 = min(G, g0 + per);
+  T v = 0;
+  if (o < no)
+    for (int g = g0; g < g1; g++) v += partials[(long long)g * no + o];
+  sm[w][l] = v;
+  __syncthreads();
+  if (w == 0 && o < no) {
+    T t = 0;
+    for (int ww = 0; ww < 8; ww++) t += sm[ww][l];
+    out[o] = coef ? coef[o / R] * t : t;
   }
 }
 

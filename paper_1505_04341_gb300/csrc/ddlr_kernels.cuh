@@ -1041,18 +1041,34 @@ __global__ void k_spmv(int n, const int *soff, const int *sw, const int *col,
   y[r] = acc;
 }
 
+// Streaming loops over n elements on a fixed grid: thread t of CTA b takes
+// elements i0 + u * G * NT (u = 0..3) per round, i0 = b * NT + t + 4 G NT *
+// round, so a thread has the loads of four elements in flight at once (one at
+// a time kept a few MB in flight, ~2.5 TB/s here) and warps stay coalesced.
+constexpr int kStreamUnr = 4;
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_dot_partial(long long n, const T *a, const T *b, T *partials, const int *gate) {
   if (gate && *gate) return;
   __shared__ T sm[NT / 32];
   T acc = 0;
-  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
-       i += (long long)gridDim.x * NT)
-    acc += a[i] * b[i];
+  const long long st = (long long)gridDim.x * NT;
+  for (long long i0 = (long long)blockIdx.x * NT + threadIdx.x; i0 < n; i0 += kStreamUnr * st) {
+    T av[kStreamUnr], bv[kStreamUnr];
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) {
+      const long long i = i0 + u * st;
+      av[u] = i < n ? a[i] : T(0);
+      bv[u] = i < n ? b[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) acc += av[u] * bv[u];
+  }
   acc = block_sum<T, NT>(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
 }
+
 
 // partial sums of two dot products a.b and a.c
 template <typename T, int NT>
@@ -1295,11 +1311,24 @@ k_pcg_update_rr(long long n, PcgState *st, const double *p, const double *q, dou
   __shared__ double sm[NT / 32];
   const double a = st->alpha;
   double acc = 0;
-  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-    x[i] += a * p[i];
-    const double ri = r[i] - a * q[i];
-    r[i] = ri;
-    acc += ri * ri;
+  const long long stp = (long long)gridDim.x * NT;
+  for (long long i0 = (long long)blockIdx.x * NT + threadIdx.x; i0 < n; i0 += kStreamUnr * stp) {
+    double pv[kStreamUnr], qv[kStreamUnr], xv[kStreamUnr], rv[kStreamUnr];
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) {
+      const long long i = i0 + u * stp;
+      if (i < n) { pv[u] = p[i]; qv[u] = q[i]; xv[u] = x[i]; rv[u] = r[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) {
+      const long long i = i0 + u * stp;
+      if (i < n) {
+        x[i] = xv[u] + a * pv[u];
+        const double ri = rv[u] - a * qv[u];
+        r[i] = ri;
+        acc += ri * ri;
+      }
+    }
   }
   acc = block_sum<double, NT>(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -1323,9 +1352,21 @@ k_dot2_beta(long long n, const double *r, const double *z, const double *zo, dou
   if (st->done) return;
   __shared__ double sm[NT / 32];
   double a1 = 0, a2 = 0;
-  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-    a1 += r[i] * z[i];
-    a2 += r[i] * zo[i];
+  const long long stp = (long long)gridDim.x * NT;
+  for (long long i0 = (long long)blockIdx.x * NT + threadIdx.x; i0 < n; i0 += kStreamUnr * stp) {
+    double rv[kStreamUnr], zv[kStreamUnr], ov[kStreamUnr];
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) {
+      const long long i = i0 + u * stp;
+      rv[u] = i < n ? r[i] : 0.0;
+      zv[u] = i < n ? z[i] : 0.0;
+      ov[u] = i < n ? zo[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnr; u++) {
+      a1 += rv[u] * zv[u];
+      a2 += rv[u] * ov[u];
+    }
   }
   a1 = block_sum<double, NT>(a1, sm);
   a2 = block_sum<double, NT>(a2, sm);

@@ -1,7 +1,8 @@
 """Kernel driver for profiling and timing one operation of the library.
 
 Builds the preconditioner for a named workload and repeats one operation --
-an A0 solve, an M^-1 apply or a PCG solve -- with device-resident vectors,
+an A0 solve, an M^-1 apply, a PCG solve or the device setup from resident
+values (factorisation and Lanczos, `setup`) -- with device-resident vectors,
 printing the CUDA-event time per repetition and the algorithmic bytes.  Used
 as the command under ncu for the kernel summaries in profiles/:
 
@@ -28,7 +29,7 @@ if ROOT not in sys.path:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="lap3d_64_b4")
-    ap.add_argument("--op", default="a0", choices=["a0", "apply", "pcg"])
+    ap.add_argument("--op", default="a0", choices=["a0", "apply", "pcg", "setup"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--variant", type=int, default=1)
     ap.add_argument("--k", type=int, default=16)
@@ -70,6 +71,8 @@ def main(argv=None):
             h.a0_solve(b, y)
         elif args.op == "apply":
             h.apply(b, y)
+        elif args.op == "setup":
+            h.refactor()
         else:
             h.pcg(b, y, tol=1e-8, maxit=args.maxit)
 
@@ -104,7 +107,7 @@ def main(argv=None):
                for f, v in cnt.items() if v["launches"] > 0}
     print(json.dumps({"workload": args.workload, "op": args.op, "ms": times, "families": fam,
                       "best_ms": best, "algorithmic_bytes": byts,
-                      "GBps_best": byts / (best * 1e-3) / 1e9 if args.op != "pcg" else None,
+                      "GBps_best": byts / (best * 1e-3) / 1e9 if args.op in ("a0", "apply") else None,
                       "info": {k: v for k, v in h.info().items()
                                if k in ("n", "s", "p", "k", "levels_interior", "levels_c",
                                         "nnz_factor", "lanczos_steps")}}))
