@@ -533,7 +533,12 @@ def _small_legs(args, pkg, W, torch, stream, flush, ev, apply_rate):
         Ai, parti, pi = wi["A"], wi["part"], wi["p"]
         bi = torch.tensor(W.rhs(Ai[0], 0), device="cuda")
         xi = torch.zeros_like(bi)
-        for name, extra in (("ddlr1", dict(variant=1)), ("ddlr2", dict(variant=2))):
+        # the paper's runs used incomplete factors with fill (fill ratios
+        # 7-9); beside IC(0): level-of-fill IC(1) and incomplete L D L^T with
+        # fill level 2
+        for name, extra in (("ddlr1", dict(variant=1)), ("ddlr2", dict(variant=2)),
+                            ("ddlr1_ic1", dict(variant=1, fill_level=1)),
+                            ("ddlr1_ildl2", dict(variant=1, factor=2, fill_level=2))):
             try:
                 hi = pkg.DDLR(Ai, parti, pi, **dict(SMALL_OPTS, rank_k=64, indefinite=1, **extra))
             except pkg.DdlrError as e:
@@ -551,7 +556,8 @@ def _small_legs(args, pkg, W, torch, stream, flush, ev, apply_rate):
             inf_i = hi.info()
             indef[name] = {"setup_ms": round(e0.elapsed_time(e1), 3), "solve_ms": round(e1.elapsed_time(e2), 3),
                            "iterations": ii["its"], "status": ii["status"], "true_relres": ii["relres"],
-                           "lanczos_steps": inf_i["lanczos_steps"], "lambda_max": inf_i["lambda_max"]}
+                           "lanczos_steps": inf_i["lanczos_steps"], "lambda_max": inf_i["lambda_max"],
+                           "fill_ratio": round(inf_i["fill_ratio"], 2), "levels_interior": inf_i["levels_interior"]}
             hi.close()
     out["indefinite_lap3d_64_s3e-2_gmres40_k64"] = indef
     return out
