@@ -795,7 +795,7 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
 // persistent-kernel helpers (defined with the allocation code)
 template <typename T, typename TU>
 PzOp<T, TU> make_pzop(ddlr_ctx *c);
-bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args);
+bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args, int threads = kPzThreads);
 size_t pz_lz_smem(int mmax);
 [[noreturn]] void timeout_fail(ddlr_ctx *c);
 void clear_timeout(ddlr_ctx *c);
@@ -989,8 +989,8 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
       PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps,
               c->opt.lanczos_reorth};
       void *args[] = {&O, &Lz};
-      persist = pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzThreads>, pz_lz_smem(c->pz_mmax),
-                          args);
+      persist = pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzLzThreads>, pz_lz_smem(c->pz_mmax),
+                          args, kPzLzThreads);
     }
     const bool use_graph = !persist && !c->timing && !(ng && ng[0] == '1');
     if (use_graph) {
@@ -1653,7 +1653,7 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
 
 // ------------------------------------------------ persistent kernels
 size_t pz_pcg_smem(int k) { return size_t(kPzThreads + 32 + k + 2) * sizeof(double); }
-size_t pz_lz_smem(int mmax) { return size_t(kPzThreads + 32 + 3 * mmax + 2) * sizeof(double); }
+size_t pz_lz_smem(int mmax) { return size_t(kPzLzThreads + 32 + 3 * mmax + 2) * sizeof(double); }
 
 // Whole-solve persistent kernels serve shallow factors (every block at most
 // kPzMaxLevels levels deep) on devices with cooperative launch; one CTA per
@@ -1690,8 +1690,9 @@ void pz_setup(ddlr_ctx *c, int mmax) {
                                            : (const void *)k_pcg_persist<kPzThreads, float, float>;
   ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, pcg_fn, kPzThreads, sp), "occupancy");
   if (sl <= size_t(optin)) {
-    raise_smem_limit((const void *)k_lz_persist<kPzThreads>, sl);
-    ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, k_lz_persist<kPzThreads>, kPzThreads, sl), "occupancy");
+    raise_smem_limit((const void *)k_lz_persist<kPzLzThreads>, sl);
+    ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, k_lz_persist<kPzLzThreads>, kPzLzThreads, sl),
+       "occupancy");
   }
   c->pz_grid = sms;
   c->pz_pstride = std::max(k, mmax + 2);
@@ -1764,7 +1765,7 @@ bool pcg_persist(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
 // one cooperative launch of a persistent kernel on the handle's stream;
 // false (and the handle keeps to the per-phase kernels from then on) when the
 // launch is refused, e.g. because every CTA cannot be resident at once
-bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args) {
+bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void **args, int threads) {
   ck(cudaMemsetAsync(c->pz_bar, 0, sizeof(unsigned), c->stream), "memset");
   ddlr_ctx::Scope sc(c, fam, c->stream);
   // DDLR_FAKE_COOP_REFUSAL=1 stands in for a refused launch (tests of the
@@ -1772,7 +1773,7 @@ bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void *
   const char *fake = getenv("DDLR_FAKE_COOP_REFUSAL");
   const cudaError_t e = (fake && fake[0] == '1')
                             ? cudaErrorCooperativeLaunchTooLarge
-                            : cudaLaunchCooperativeKernel(fn, dim3(c->pz_grid), dim3(kPzThreads), args, smem,
+                            : cudaLaunchCooperativeKernel(fn, dim3(c->pz_grid), dim3(threads), args, smem,
                                                           c->stream);
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
     cudaGetLastError();   // not sticky: clear it
@@ -2413,12 +2414,12 @@ void precond_mr(ddlr_ctx *c, const double *Rr, double *Z, int R, const int *gate
   } else {
     // scaling and change of precision in one pass each way
     float *i32 = c->bt.w32[5], *o32 = c->bt.w32[6];
-    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<float, double>), eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev,
-       Rr, i32, gate);
+    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<float, double>), eblk((nR + 3) / 4, 256), 256, 0, (long long)n, R,
+       c->dsc_dev, Rr, i32, gate);
     if (c->opt.uk_bf16) apply_mr<float, __nv_bfloat16>(c, c->Ub16, i32, o32, R, gate);
     else apply_mr<float, float>(c, c->U32, i32, o32, R, gate);
-    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<double, float>), eblk(nR, bd), bd, 0, (long long)n, R, c->dsc_dev,
-       o32, Z, gate);
+    KL(c, "vec_mr", c->stream, (k_scale_cast_mr<double, float>), eblk((nR + 3) / 4, 256), 256, 0, (long long)n, R,
+       c->dsc_dev, o32, Z, gate);
   }
 }
 

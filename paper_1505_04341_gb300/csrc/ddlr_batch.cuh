@@ -874,14 +874,29 @@ __global__ void k_batch_out(int n, int R, const int *perm, const double *in, dou
   out[q * ld + perm[g]] = in[idx];
 }
 // out = TO(in * d_row) (d == nullptr: no scaling): the diagonal scaling of the
-// scaled system and the change of precision of the preconditioner in one pass
+// scaled system and the change of precision of the preconditioner in one pass.
+// A thread takes four consecutive elements (one row index computed for them,
+// the next by increment); launch with ceil(n R / 4) threads.
 template <typename TO, typename TI>
 __global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *in, TO *out, const int *gate) {
   if (gate && *gate) return;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < n * R) {
-    const double v = double(in[idx]);
-    out[idx] = TO(d ? v * d[row_of(idx, R)] : v);
+  const long long nR = n * R;
+  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= nR) return;
+  TI v[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) v[u] = i0 + u < nR ? in[i0 + u] : TI(0);
+  long long r = d ? row_of(i0, R) : 0;
+  int q = d ? col_of(i0, r, R) : 0;
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    if (i0 + u >= nR) break;
+    double x = double(v[u]);
+    if (d) {
+      x *= d[r];
+      if (++q == R) { q = 0; r++; }
+    }
+    out[i0 + u] = TO(x);
   }
 }
 

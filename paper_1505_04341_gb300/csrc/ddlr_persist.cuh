@@ -17,7 +17,11 @@
 
 namespace ddlr {
 
-constexpr int kPzThreads = 512;          // threads per CTA of the persistent kernels
+// threads per CTA of the persistent kernels (one CTA per SM): their phases are
+// gathers and streaming passes bound by load latency, so they run with 32
+// warps per SM (64 registers per thread)
+constexpr int kPzThreads = 1024;
+constexpr int kPzLzThreads = kPzThreads;
 constexpr int kPzMaxLevels = 8;          // deepest factor served (levels per block)
 
 
