@@ -2272,10 +2272,18 @@ void a0_solve_mr(ddlr_ctx *c, const T *X, T *Z, int R, const int *gate) {
     const T *lv = mode == 5 ? lx : lv0;
     if (c->lv_desc) {
       const int cnt = dptr[L + 1] - dptr[L];
-      const int bd = chunk_block(c, R), rows = (bd / R) * kMrRowsPerThread;
-      if (cnt > 0)
-        KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr<T>, (cnt + rows - 1) / rows, bd, 0,
+      if (cnt <= 0) return;
+      constexpr int kV = Vec16<T>::n;
+      if (R % kV == 0) {
+        // 16-byte vectors of kV columns per thread; 256 threads
+        const int per = 256 / (R / kV), rows = per * kMrRowsPerThread;
+        KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr_v<T>, (cnt + rows - 1) / rows, per * (R / kV), 0,
            c->lv_desc + dptr[L], cnt, mode, c->S.l_col, c->S.u_col, lv, uv, di, X, Z, R, gate);
+        return;
+      }
+      const int bd = chunk_block(c, R), rows = (bd / R) * kMrRowsPerThread;
+      KL(c, "sptrsv_levels_mr", c->stream, k_sptrsv_desc_mr<T>, (cnt + rows - 1) / rows, bd, 0,
+         c->lv_desc + dptr[L], cnt, mode, c->S.l_col, c->S.u_col, lv, uv, di, X, Z, R, gate);
       return;
     }
     const int nch = ptr[L + 1] - ptr[L];
@@ -2332,8 +2340,14 @@ void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *ga
   if (c->opt.variant == 1) {
     T *Z = BPrec<T>::w(c, 0), *Y = BPrec<T>::w(c, 1), *W = BPrec<T>::w(c, 2), *RHS = BPrec<T>::w(c, 3);
     a0_solve_mr<T>(c, X, Z, R, gate);
-    KL(c, "et_mr", c->stream, k_et_mr<T>, eblk((long long)s * R, bd), bd, 0, s, m, c->eht_rp, c->eht_ci,
-       Prec<T>::eht(c), ia, a, Z, Y, R, gate);
+    constexpr int kV = Vec16<T>::n;
+    const bool vec = R % kV == 0;
+    if (vec)
+      KL(c, "et_mr", c->stream, k_et_mr_v<T>, eblk((long long)s * (R / kV), 256), 256, 0, s, m, c->eht_rp,
+         c->eht_ci, Prec<T>::eht(c), ia, a, Z, Y, R, gate);
+    else
+      KL(c, "et_mr", c->stream, k_et_mr<T>, eblk((long long)s * R, bd), bd, 0, s, m, c->eht_rp, c->eht_ci,
+         Prec<T>::eht(c), ia, a, Z, Y, R, gate);
     bool tc = false;
     if constexpr (std::is_same<T, float>::value) {
       tc = c->bt.tc;
@@ -2362,8 +2376,12 @@ void apply_mr(ddlr_ctx *c, const TU *U, const T *X, T *Out, int R, const int *ga
       KL(c, "w_rhs_mr", c->stream, (k_w_rhs_mr<T, TU>), eblk((long long)s * R, bd), bd, 0, s, m, k, U, Tm, Y,
          Prec<T>::inv1mt(c), a, X, W, RHS, R, gate);
     }
-    KL(c, "e_int_mr", c->stream, k_e_interior_mr<T>, eblk((long long)m * R, bd), bd, 0, m, c->eh_rp, c->eh_ci,
-       Prec<T>::eh(c), ia, W, X, RHS, R, gate);
+    if (vec)
+      KL(c, "e_int_mr", c->stream, k_e_interior_mr_v<T>, eblk((long long)m * (R / kV), 256), 256, 0, m, c->eh_rp,
+         c->eh_ci, Prec<T>::eh(c), ia, W, X, RHS, R, gate);
+    else
+      KL(c, "e_int_mr", c->stream, k_e_interior_mr<T>, eblk((long long)m * R, bd), bd, 0, m, c->eh_rp, c->eh_ci,
+         Prec<T>::eh(c), ia, W, X, RHS, R, gate);
     a0_solve_mr<T>(c, RHS, Out, R, gate);
   } else {
     a0_solve_mr<T>(c, X, Out, R, gate);

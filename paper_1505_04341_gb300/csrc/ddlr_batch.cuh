@@ -32,6 +32,15 @@ __device__ __forceinline__ void red_range(long long nrows, int g, int G, long lo
   if (r0 > nrows) r0 = nrows;
 }
 
+// Row arithmetic of the batched level solves with explicit rounding (no
+// contraction left to the compiler), so the scalar and the vector kernels --
+// a batch takes one or the other by its width -- give every element the same
+// bits: z = x * d rounded, then acc - v z as one fused multiply-add.
+__device__ __forceinline__ float mr_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mr_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mr_fms(float acc, float v, float z) { return fmaf(-v, z, acc); }
+__device__ __forceinline__ double mr_fms(double acc, double v, double z) { return fma(-v, z, acc); }
+
 // one dependency level of many blocks, R right-hand sides: CTA q solves chunk q;
 // thread -> (row sub-index, column); mode as k_sptrsv_chunks (0-4)
 template <typename T>
@@ -113,7 +122,7 @@ __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const in
     if (r[u] >= 0) {
       d[u] = dinv[r[u]];
       const long long e = (long long)r[u] * R + q;
-      acc[u] = mode == 4 ? X[e] * d[u] : (bwd ? Z : X)[e];
+      acc[u] = mode == 4 ? mr_mul(X[e], d[u]) : (bwd ? Z : X)[e];
     }
   }
   for (int kk = 0; kk < wmax; kk++) {
@@ -130,19 +139,135 @@ __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const in
     for (int u = 0; u < RR; u++) {
       if (kk < w[u]) {
         const long long e = (long long)c[u] * R + q;
-        zc[u] = (from_x && !bwd) ? (pre ? X[e] : X[e] * dinv[c[u]]) : Z[e];
+        zc[u] = (from_x && !bwd) ? (pre ? X[e] : mr_mul(X[e], dinv[c[u]])) : Z[e];
       }
     }
 #pragma unroll
     for (int u = 0; u < RR; u++)
-      if (kk < w[u]) acc[u] -= v[u] * zc[u];
+      if (kk < w[u]) acc[u] = mr_fms(acc[u], v[u], zc[u]);
   }
 #pragma unroll
   for (int u = 0; u < RR; u++) {
     if (r[u] < 0) continue;
-    T a = acc[u] * d[u];
-    if (mode == 2 || mode == 3 || mode == 5) a *= d[u];
+    T a = mr_mul(acc[u], d[u]);
+    if (mode == 2 || mode == 3 || mode == 5) a = mr_mul(a, d[u]);
     Z[(long long)r[u] * R + q] = a;
+  }
+}
+
+// k_sptrsv_desc_mr with 16-byte vectors: a thread takes kV = 16 / sizeof(T)
+// consecutive columns of a row (float4 / double2 loads and stores of X, Z and
+// the gathered rows), so the row's descriptor, column indices, values and
+// index arithmetic are shared by kV columns instead of being redone per
+// column.  Needs R % kV == 0 (the blocks are 16-byte aligned); each element's
+// arithmetic is that of the scalar kernel.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using V = float4;
+  static constexpr int n = 4;
+  __device__ static float get(const V &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+  __device__ static void set(V &v, int i, float x) {
+    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+  }
+};
+template <> struct Vec16<double> {
+  using V = double2;
+  static constexpr int n = 2;
+  __device__ static double get(const V &v, int i) { return i == 0 ? v.x : v.y; }
+  __device__ static void set(V &v, int i, double x) {
+    if (i == 0) v.x = x; else v.y = x;
+  }
+};
+template <typename T>
+__global__ void k_sptrsv_desc_mr_v(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
+                                   const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
+                                   const int *gate) {
+  if (gate && *gate) return;
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int kV = VT::n, RR = kMrRowsPerThread;
+  const int tpr = R / kV;                       // threads per row
+  const int per = blockDim.x / tpr;
+  const int q0 = (threadIdx.x % tpr) * kV, sub = threadIdx.x / tpr;
+  if (sub >= per) return;
+  const bool bwd = mode == 1 || mode == 4;
+  const bool from_x = mode == 3 || mode == 4 || mode == 5;
+  const bool pre = mode == 5;
+  const int *col = bwd ? u_col : l_col;
+  const T *val = bwd ? uval : lval;
+  const int i0 = blockIdx.x * per * RR;
+  int r[RR], off[RR], w[RR];
+  V acc[RR];
+  T d[RR];
+  int wmax = 0;
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    const int i = i0 + sub + u * per;
+    r[u] = -1; off[u] = 0; w[u] = 0;
+    if (i < count) {
+      const int4 dsc = desc[i];
+      r[u] = dsc.x;
+      off[u] = bwd ? dsc.z : dsc.y;
+      w[u] = bwd ? int(unsigned(dsc.w) >> 16) : int(unsigned(dsc.w) & 0xffffu);
+      wmax = max(wmax, w[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    d[u] = T(0);
+    if (r[u] >= 0) {
+      d[u] = dinv[r[u]];
+      const V xv = *reinterpret_cast<const V *>((mode == 4 || !bwd ? X : Z) + (long long)r[u] * R + q0);
+      if (mode == 4) {
+#pragma unroll
+        for (int e = 0; e < kV; e++) VT::set(acc[u], e, mr_mul(VT::get(xv, e), d[u]));
+      } else {
+        acc[u] = xv;
+      }
+    }
+  }
+  for (int kk = 0; kk < wmax; kk++) {
+    int c[RR];
+    T v[RR], dc[RR];
+#pragma unroll
+    for (int u = 0; u < RR; u++) {
+      if (kk < w[u]) {
+        c[u] = col[off[u] + kk * 32];
+        v[u] = val[off[u] + kk * 32];
+      }
+    }
+    V zc[RR];
+#pragma unroll
+    for (int u = 0; u < RR; u++) {
+      if (kk < w[u]) {
+        const bool fx = from_x && !bwd;
+        zc[u] = *reinterpret_cast<const V *>((fx ? X : Z) + (long long)c[u] * R + q0);
+        dc[u] = (fx && !pre) ? dinv[c[u]] : T(1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RR; u++) {
+      if (kk < w[u]) {
+        const bool scale = from_x && !bwd && !pre;
+#pragma unroll
+        for (int e = 0; e < kV; e++) {
+          const T z = scale ? mr_mul(VT::get(zc[u], e), dc[u]) : VT::get(zc[u], e);
+          VT::set(acc[u], e, mr_fms(VT::get(acc[u], e), v[u], z));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < RR; u++) {
+    if (r[u] < 0) continue;
+    V o;
+#pragma unroll
+    for (int e = 0; e < kV; e++) {
+      T a = mr_mul(VT::get(acc[u], e), d[u]);
+      if (mode == 2 || mode == 3 || mode == 5) a = mr_mul(a, d[u]);
+      VT::set(o, e, a);
+    }
+    *reinterpret_cast<V *>(Z + (long long)r[u] * R + q0) = o;
   }
 }
 
@@ -157,8 +282,8 @@ __global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,
   const int q = col_of(idx, j, R);
   if (j >= s) return;
   T acc = 0;
-  for (int p = eht_rp[j]; p < eht_rp[j + 1]; p++) acc += eht_val[p] * Z[(long long)eht_ci[p] * R + q];
-  Y[j * R + q] = ia * acc - a * Z[(m + j) * R + q];
+  for (int p = eht_rp[j]; p < eht_rp[j + 1]; p++) acc = mr_fms(acc, -eht_val[p], Z[(long long)eht_ci[p] * R + q]);
+  Y[j * R + q] = mr_fms(mr_mul(ia, acc), a, Z[(m + j) * R + q]);
 }
 
 // RHS_B = X_B + a^-1 Ehat W   (interior rows)
@@ -172,8 +297,67 @@ __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
   const int q = col_of(idx, r, R);
   if (r >= m) return;
   T acc = 0;
-  for (int p = eh_rp[r]; p < eh_rp[r + 1]; p++) acc += eh_val[p] * W[(long long)eh_ci[p] * R + q];
-  RHS[r * R + q] = X[r * R + q] + ia * acc;
+  for (int p = eh_rp[r]; p < eh_rp[r + 1]; p++) acc = mr_fms(acc, -eh_val[p], W[(long long)eh_ci[p] * R + q]);
+  RHS[r * R + q] = mr_fms(X[r * R + q], -ia, acc);
+}
+
+// k_et_mr and k_e_interior_mr with 16-byte vectors of kV columns per thread
+// (R % kV == 0); per element the arithmetic of the scalar kernels (explicit
+// rounding, so both forms give the same bits)
+template <typename T>
+__global__ void k_et_mr_v(int s, int m, const int *eht_rp, const int *eht_ci, const T *eht_val, T ia, T a,
+                          const T *Z, T *Y, int R, const int *gate) {
+  if (gate && *gate) return;
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int kV = VT::n;
+  const int tpr = R / kV;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long j = t / tpr;
+  if (j >= s) return;
+  const int q0 = int(t - j * tpr) * kV;
+  V acc;
+#pragma unroll
+  for (int e = 0; e < kV; e++) VT::set(acc, e, T(0));
+  for (int p = eht_rp[j]; p < eht_rp[j + 1]; p++) {
+    const T v = eht_val[p];
+    const V z = *reinterpret_cast<const V *>(Z + (long long)eht_ci[p] * R + q0);
+#pragma unroll
+    for (int e = 0; e < kV; e++) VT::set(acc, e, mr_fms(VT::get(acc, e), -v, VT::get(z, e)));
+  }
+  const V zc = *reinterpret_cast<const V *>(Z + (long long)(m + j) * R + q0);
+  V o;
+#pragma unroll
+  for (int e = 0; e < kV; e++) VT::set(o, e, mr_fms(mr_mul(ia, VT::get(acc, e)), a, VT::get(zc, e)));
+  *reinterpret_cast<V *>(Y + j * R + q0) = o;
+}
+
+template <typename T>
+__global__ void k_e_interior_mr_v(int m, const int *eh_rp, const int *eh_ci, const T *eh_val, T ia, const T *W,
+                                  const T *X, T *RHS, int R, const int *gate) {
+  if (gate && *gate) return;
+  using VT = Vec16<T>;
+  using V = typename VT::V;
+  constexpr int kV = VT::n;
+  const int tpr = R / kV;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long r = t / tpr;
+  if (r >= m) return;
+  const int q0 = int(t - r * tpr) * kV;
+  V acc;
+#pragma unroll
+  for (int e = 0; e < kV; e++) VT::set(acc, e, T(0));
+  for (int p = eh_rp[r]; p < eh_rp[r + 1]; p++) {
+    const T v = eh_val[p];
+    const V w = *reinterpret_cast<const V *>(W + (long long)eh_ci[p] * R + q0);
+#pragma unroll
+    for (int e = 0; e < kV; e++) VT::set(acc, e, mr_fms(VT::get(acc, e), -v, VT::get(w, e)));
+  }
+  const V x = *reinterpret_cast<const V *>(X + r * R + q0);
+  V o;
+#pragma unroll
+  for (int e = 0; e < kV; e++) VT::set(o, e, mr_fms(VT::get(x, e), -ia, VT::get(acc, e)));
+  *reinterpret_cast<V *>(RHS + r * R + q0) = o;
 }
 
 // partials[g][c*R + q] = sum over rows of range g (in order) of U[row][c] Y[row][q]

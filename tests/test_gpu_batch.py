@@ -97,3 +97,25 @@ def test_batched_jump_coefficients_mixed_oracle():
         assert abs(infos[j]["its"] - its_o) <= max(3, its_o // 10)
         assert _rel(X[:, j], xo) < 1e-6
     h.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_batch_invariance_across_kernel_forms(precision):
+    """Widths that are a multiple of the 16-byte vector (4 FP32 / 2 FP64
+    columns) take the vector form of the batched level solve, others the
+    scalar form; a column gives the same bits in either."""
+    A = W.jump_coefficient_fv(24, 8, 0)
+    part, p = W.random_cut_partition(24, 3, 0, 6, 12)
+    n = A[0]
+    h = pkg.DDLR(A, part, p, variant=1, rank_k=8, c_order=1, b_order=1, scale_diag=1,
+                 precision=precision, uk_bf16=precision)
+    b0 = W.rhs(n, 100)
+    outs = []
+    for width in (4, 5, 8, 3):
+        B = np.asfortranarray(np.stack([b0] + [W.rhs(n, 10 + j) for j in range(width - 1)], 1))
+        X, inf = h.pcg(B, tol=1e-8)
+        assert inf[0]["status"] == "OK"
+        outs.append((X[:, 0].copy(), inf[0]["its"]))
+    for x, its in outs[1:]:
+        assert its == outs[0][1] and np.array_equal(x, outs[0][0])
+    h.close()
