@@ -107,6 +107,7 @@ struct ddlr_ctx {
     float *cb32[5] = {nullptr};
     double *part64 = nullptr;
     float *part32 = nullptr;
+    double *fpart = nullptr;   // per-64-row-block column partials of the fused step kernels
     PcgStateMR *st = nullptr;
     struct G {
       cudaGraphExec_t exec = nullptr;
@@ -2221,6 +2222,7 @@ void batch_alloc(ddlr_ctx *c, int R) {
     B.part32 = (float *)al((size_t(kTcRedGrid) + 1) * std::max<size_t>(k * R, 2 * R) * 4);
   }
   B.part64 = (double *)al(size_t(kRedGrid) * std::max<size_t>(k * R, 2 * R) * 8);
+  B.fpart = (double *)al(size_t((P.n + kFbRows - 1) / kFbRows) * R * 8);
   if (c->opt.c_solver == 1)
     for (int i = 0; i < 5; i++) {
       B.cb64[i] = (double *)al(nR * 8);
@@ -2500,12 +2502,16 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   const int *gate = reinterpret_cast<const int *>(reinterpret_cast<const char *>(B.st) +
                                                   offsetof(PcgStateMR, all_done));
   double *part = B.part64;
-  KL(c, "spmv_mr", c->stream, k_spmv_mr<double>, eblk(nR, bd), bd, 0, n, c->a_soff, c->a_sw, c->a_col,
-     c->a_val, B.P, B.Q, R, gate);
-  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.P, B.Q, (const double *)nullptr, part, gate);
+  // q = A p with the p.q partials, and the x, r update with the r.r partials,
+  // in one pass each (64-row blocks, then the blocks of each reduction range)
+  const unsigned nb = (unsigned)((n + kFbRows - 1) / kFbRows);
+  KL(c, "spmv_mr", c->stream, k_spmv_pq_mr, nb, kFbLanes * R, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, B.P,
+     B.Q, R, B.fpart, gate);
+  KL(c, "pcg_mr_red", c->stream, k_fused_partials_reduce, kRedGrid, 64, 0, (int)nb, R, B.fpart, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_alpha, 1, kScalarThreads, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr_axpy", c->stream, k_pcgmr_update, eblk(nR, bd), bd, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr);
-  KL(c, "pcg_mr_dot", c->stream, k_dot_mr_partial, kRedGrid, 256, 0, (long long)n, R, B.Rr, B.Rr, (const double *)nullptr, part, gate);
+  KL(c, "pcg_mr_axpy", c->stream, k_update_rr_mr, nb, kFbLanes * R, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr,
+     B.fpart);
+  KL(c, "pcg_mr_red", c->stream, k_fused_partials_reduce, kRedGrid, 64, 0, (int)nb, R, B.fpart, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_rr, 1, kScalarThreads, 0, B.st, part, kRedGrid);
   // the check kernels run on a bounded grid: most iterations they return at once
   const unsigned gchk = (unsigned)std::min<long long>(eblk(nR, bd), 152LL * 8);
@@ -3634,6 +3640,7 @@ ddlr_status ddlr_get_traffic(ddlr_handle c, double *apply_bytes, double *a0_byte
       else if (f == "u_add_mr") b = n * k * ub + 2.0 * n * R * v;
       else if (f == "spmv_mr") b = nnz_a * 12.0 + 2.0 * n * R * 8.0;
       else if (f == "pcg_mr_dot") b = 2.0 * n * R * 8.0;
+      else if (f == "pcg_mr_red") b = (std::ceil(n / kFbRows) + kRedGrid) * R * 8.0;
       else if (f == "pcg_mr_axpy") b = 6.0 * n * R * 8.0;
       else if (f == "pcg_mr_p") b = (c->opt.precision == 1 ? 4.0 : 3.0) * n * R * 8.0;
       else if (f == "vec_mr") b = n * R * (8.0 + v) + (c->dsc_dev ? 8.0 * n : 0.0);

@@ -773,6 +773,93 @@ struct PcgStateMR {
   int pad[2];
 };
 
+// ---- fused step kernels of the block PCG with their column dot products.
+// Rows are taken in blocks of kFbRows = 64; in a block, row lane l (of 8)
+// takes rows l, l + 8, ... of the block in order, a thread owns one (row
+// lane, column) pair, and the 8 lane sums of a column are added in lane order
+// into partials[block][q].  k_fused_partials_reduce then adds the blocks of each
+// of the G = kRedGrid reduction ranges in order into the [g][2R] layout the
+// scalar kernels read.  Nothing in this order depends on R, so a column's dot
+// products are the same in every batch.  Launch: ceil(n / 64) CTAs of 8 R
+// threads.
+constexpr int kFbRows = 64, kFbLanes = 8;
+
+// Q = A P (sliced ELL) and the column partials of P.Q
+__global__ void k_spmv_pq_mr(int n, const int *soff, const int *sw, const int *col, const double *val,
+                             const double *P, double *Q, int R, double *bpart, const int *gate) {
+  if (gate && *gate) return;
+  __shared__ double red[kFbLanes][kMaxR];
+  const int q = threadIdx.x % R, l = threadIdx.x / R;
+  const int r0 = blockIdx.x * kFbRows;
+  double acc = 0.0;
+  for (int i = l; i < kFbRows; i += kFbLanes) {
+    const int r = r0 + i;
+    if (r >= n) break;
+    const int g = r >> 5, ln = r & 31;
+    const int off = soff[g] + ln, w = sw[g];
+    double t = 0;
+    for (int kk = 0; kk < w; kk++) t += val[off + kk * 32] * P[(long long)col[off + kk * 32] * R + q];
+    const long long e = (long long)r * R + q;
+    Q[e] = t;
+    acc = fma(P[e], t, acc);
+  }
+  red[l][q] = acc;
+  __syncthreads();
+  if (l == 0) {
+    double v = 0.0;
+    for (int j = 0; j < kFbLanes; j++) v += red[j][q];
+    bpart[(long long)blockIdx.x * R + q] = v;
+  }
+}
+
+// X += alpha P; Rr -= alpha Q for the running columns, and the column
+// partials of Rr.Rr (all columns)
+__global__ void k_update_rr_mr(long long n, const PcgStateMR *st, const double *P, const double *Q, double *X,
+                               double *Rr, double *bpart) {
+  if (st->all_done) return;
+  __shared__ double red[kFbLanes][kMaxR];
+  const int R = st->R;
+  const int q = threadIdx.x % R, l = threadIdx.x / R;
+  const long long r0 = (long long)blockIdx.x * kFbRows;
+  const bool run = !st->done[q];
+  const double a = st->alpha[q];
+  double acc = 0.0;
+  for (int i = l; i < kFbRows; i += kFbLanes) {
+    const long long r = r0 + i;
+    if (r >= n) break;
+    const long long e = r * R + q;
+    double rv = Rr[e];
+    if (run) {
+      X[e] += a * P[e];
+      rv -= a * Q[e];
+      Rr[e] = rv;
+    }
+    acc = fma(rv, rv, acc);
+  }
+  red[l][q] = acc;
+  __syncthreads();
+  if (l == 0) {
+    double v = 0.0;
+    for (int j = 0; j < kFbLanes; j++) v += red[j][q];
+    bpart[(long long)blockIdx.x * R + q] = v;
+  }
+}
+
+// partials[g][q] (stride 2R) = sum over the blocks of reduction range g, in
+// order, of bpart[block][q]; grid kRedGrid, R threads
+__global__ void k_fused_partials_reduce(int nblocks, int R, const double *bpart, double *partials,
+                                        const int *gate) {
+  if (gate && *gate) return;
+  const int q = threadIdx.x;
+  if (q >= R) return;
+  long long b0, b1;
+  red_range(nblocks, blockIdx.x, gridDim.x, b0, b1);
+  double v = 0.0;
+  for (long long b = b0; b < b1; b++) v += bpart[b * R + q];
+  partials[(long long)blockIdx.x * 2 * R + q] = v;
+}
+
+
 // sums[o] = sum over the G partial rows of column o (o < no), a warp per
 // column: lanes take every 32nd partial in order, then a shuffle tree (a
 // serial sum of G = 304 FP64 values is ~20k cycles of add latency here).
@@ -842,19 +929,6 @@ __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
   }
 }
 
-// X += alpha P; Rr -= alpha Q for the columns still running
-__global__ void k_pcgmr_update(long long n, const PcgStateMR *st, const double *P,
-                               const double *Q, double *X, double *Rr) {
-  if (st->all_done) return;
-  const int R = st->R;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * R) return;
-  const int q = col_of(idx, row_of(idx, R), R);
-  if (st->done[q]) return;
-  const double a = st->alpha[q];
-  X[idx] += a * P[idx];
-  Rr[idx] -= a * Q[idx];
-}
 
 __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
   if (st->all_done) return;
