@@ -484,10 +484,12 @@ void chunk_sweeps(ddlr_ctx *c, cudaStream_t st, const std::vector<int> &ptr, con
   for (int L = nL - 2; L >= 0; L--) launch(L, 1);
 }
 
-// the same sweeps over the level-order descriptor list (all blocks)
-template <typename T>
+// the same sweeps over the level-order descriptor list (all blocks); x may be
+// wider than T (rounded as read), z64 (optional) also receives the result in
+// FP64 (every row's final value is written in FP64 too)
+template <typename T, typename TX = T>
 void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv0, const T *uv, const T *di,
-                 const T *x, T *z, const int *gate) {
+                 const TX *x, T *z, const int *gate, double *z64 = nullptr) {
   const std::vector<int> &ptr = c->P.lv_ptr;
   const int nL = int(ptr.size()) - 1;
   const int rows = c->chunk_rows ? c->chunk_rows : (sizeof(T) == 8 ? 2 : 4);
@@ -499,12 +501,18 @@ void desc_sweeps(ddlr_ctx *c, cudaStream_t st, const char *fam, const T *lv0, co
     const int4 *d = c->lv_desc + ptr[L];
     const int grid = (cnt + kThreads - 1) / kThreads;
     const int *lc = c->S.l_col, *uc = c->S.u_col;
+    // rows are final after the top level (modes 2, 3, 5) and the backward
+    // levels (modes 1, 4)
+    double *o64 = mode == 0 ? nullptr : z64;
     if (rows == 4)
-      KL(c, fam, st, (k_sptrsv_desc<T, 4>), grid, kThreads / 4, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+      KL(c, fam, st, (k_sptrsv_desc<T, 4, TX>), grid, kThreads / 4, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate,
+         o64);
     else if (rows == 2)
-      KL(c, fam, st, (k_sptrsv_desc<T, 2>), grid, kThreads / 2, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+      KL(c, fam, st, (k_sptrsv_desc<T, 2, TX>), grid, kThreads / 2, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate,
+         o64);
     else
-      KL(c, fam, st, (k_sptrsv_desc<T, 1>), grid, kThreads, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate);
+      KL(c, fam, st, (k_sptrsv_desc<T, 1, TX>), grid, kThreads, 0, d, cnt, mode, lc, uc, lv, uv, di, x, z, gate,
+         o64);
   };
   if (nL == 2) {
     launch(1, lx ? 5 : 3);
@@ -772,6 +780,56 @@ void apply_dev(ddlr_ctx *c, const TU *U, const T *x, T *u, const int *gate) {
   }
 }
 
+// the mixed-precision DDLR-1 apply without separate precision casts: for
+// shallow factors solved by the descriptor sweeps, the factored C_a and
+// vector U_k products, with no diagonal scaling (the casts are then plain
+// roundings, done where the values are read and written)
+bool mixed_fused(const ddlr_ctx *c) {
+  const Plan &P = c->P;
+  const int k = c->opt.rank_k;
+  const int E = c->opt.uk_bf16 ? 8 : 4;                  // values per 16-byte load of U_k
+  const int L = k / E;
+  const bool lanes = k % E == 0 && (L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32);
+  const char *off = getenv("DDLR_NO_FUSED_CAST");
+  return c->opt.precision == 1 && c->opt.variant == 1 && !c->dsc_dev && c->opt.c_solver == 0 &&
+         c->opt.factor < 2 && c->lv_desc && std::max(P.levels_interior, P.levels_c) <= kShallowLevels &&
+         c->uvec && lanes && !(off && off[0] == '1');
+}
+
+// DDLR-1 M^-1 x (Algorithm 1) in FP32 on an FP64 x, the result in FP64 u64:
+// apply_dev<float, TU> with x rounded as it is read and the last sweeps
+// writing FP64 (mixed_fused cases only)
+template <typename TU>
+void apply_dev_x64(ddlr_ctx *c, const TU *U, const double *x, double *u64, const int *gate) {
+  const Plan &P = c->P;
+  const int m = P.m, s = P.s, k = c->opt.rank_k;
+  const float a = float(c->opt.alpha), ia = float(1.0 / c->opt.alpha);
+  float *part = c->part32;
+  float *z = c->w32[0], *y = c->w32[1], *w = c->w32[2], *rhs = c->w32[3], *t = c->w32[4], *u = c->w32[7];
+  const float *lv = c->l32, *uv = c->u32, *di = c->dinv32;
+  desc_sweeps<float, double>(c, c->stream, "sptrsv_levels", lv, uv, di, x, z, gate);     // A0 z = x
+  KL(c, "et", c->stream, k_et<float>, nblk(s), kThreads, 0, s, m, c->eht_rp, c->eht_ci, c->eht32, ia, a, z, y,
+     gate);                                                                               // y = E^T z
+  launch_utx<float, TU>(c, s, k, U, y, part, c->coef32, (const float *)nullptr, t, gate);   // t = D U^T y
+  constexpr int E = Unpack16<TU>::E;
+#define DDLR_WRX(Lc)                                                                                          \
+  KL(c, "w_rhs", c->stream, (k_w_rhs_vec<float, TU, Lc, kUrowsUnr, double>), urows_grid(s, Lc), kThreads, 0, s, m, \
+     U, t, y, c->inv1mt32, a, x, w, rhs, gate)
+  switch (k / E) {
+    case 1: DDLR_WRX(1); break;
+    case 2: DDLR_WRX(2); break;
+    case 4: DDLR_WRX(4); break;
+    case 8: DDLR_WRX(8); break;
+    case 16: DDLR_WRX(16); break;
+    case 32: DDLR_WRX(32); break;
+    default: throw Fail{DDLR_ERR_INVALID, "fused mixed apply: unsupported rank"};
+  }
+#undef DDLR_WRX
+  KL(c, "e_int", c->stream, (k_e_interior<float, double>), nblk(m), kThreads, 0, m, c->eh_rp, c->eh_ci, c->eh32, ia,
+     w, x, rhs, gate);                                                                    // x_B + a^-1 Ehat w
+  desc_sweeps<float, float>(c, c->stream, "sptrsv_levels", lv, uv, di, rhs, u, gate, u64);   // A0 u = x + v
+}
+
 // preconditioner on FP64 vectors in device order (scaled system handled here)
 void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
   const int n = c->P.n;
@@ -782,6 +840,11 @@ void precond(ddlr_ctx *c, const double *r, double *z, const int *gate) {
   }
   if (c->opt.precision == 0) {
     apply_dev<double, double>(c, c->U64, rin, z, gate);
+  } else if (mixed_fused(c)) {
+    // the FP32 preconditioner reads the FP64 residual and writes the FP64
+    // result itself (no separate casts)
+    if (c->opt.uk_bf16) apply_dev_x64<__nv_bfloat16>(c, c->Ub16, r, z, gate);
+    else apply_dev_x64<float>(c, c->U32, r, z, gate);
   } else {
     float *r32 = c->w32[6], *z32 = c->w32[7];
     KL(c, "vec", c->stream, (k_cast<float, double>), nblk(n), kThreads, 0, (long long)n, rin, r32, gate);

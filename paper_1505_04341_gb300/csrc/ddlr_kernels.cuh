@@ -551,30 +551,32 @@ k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, cons
 // Row value from a level-order descriptor d = {row, first L slot, first L^T
 // slot, L entries | L^T entries << 16} (the row's own entries only, no slice
 // padding); FROM_X and PRE as in solve_row_value, dr = 1 / L_rr.
-template <typename T, bool FWD, bool FROM_X, bool PRE = false>
+// x may be of a wider type TX (the FP64 residual read by the FP32
+// preconditioner): it is rounded to T as it is read.
+template <typename T, bool FWD, bool FROM_X, bool PRE = false, typename TX = T>
 __device__ __forceinline__ T desc_row_value(const int4 d, const int *col, const T *val, const T *dinv,
-                                            const T *x, const T *z, T dr) {
+                                            const TX *x, const T *z, T dr) {
   const int off = FWD ? d.y : d.z;
   const int w = FWD ? int(unsigned(d.w) & 0xffffu) : int(unsigned(d.w) >> 16);
   const int r = d.x;
-  T acc = FWD ? x[r] : (FROM_X ? x[r] * dr : z[r]);
+  T acc = FWD ? T(x[r]) : (FROM_X ? T(x[r]) * dr : z[r]);
   for (int kk = 0; kk < w; kk++) {
     const int c = col[off + kk * 32];
-    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? (PRE ? x[c] : x[c] * dinv[c]) : z[c]);
+    acc -= val[off + kk * 32] * ((FWD && FROM_X) ? (PRE ? T(x[c]) : T(x[c]) * dinv[c]) : z[c]);
   }
   return acc * dr;
 }
 
 // mode 0-4 as k_sptrsv_chunks for one row given by its descriptor
-template <typename T>
+template <typename T, typename TX = T>
 __device__ __forceinline__ T desc_row_mode(int mode, const int4 d, const int *l_col, const int *u_col,
-                                           const T *lval, const T *uval, const T *dinv, const T *x,
+                                           const T *lval, const T *uval, const T *dinv, const TX *x,
                                            const T *z, T dr) {
-  if (mode == 1) return desc_row_value<T, false, false>(d, u_col, uval, dinv, x, z, dr);
-  if (mode == 4) return desc_row_value<T, false, true>(d, u_col, uval, dinv, x, z, dr);
-  if (mode == 3) return desc_row_value<T, true, true>(d, l_col, lval, dinv, x, z, dr) * dr;
-  if (mode == 5) return desc_row_value<T, true, true, true>(d, l_col, lval, dinv, x, z, dr) * dr;
-  const T v = desc_row_value<T, true, false>(d, l_col, lval, dinv, x, z, dr);
+  if (mode == 1) return desc_row_value<T, false, false, false, TX>(d, u_col, uval, dinv, x, z, dr);
+  if (mode == 4) return desc_row_value<T, false, true, false, TX>(d, u_col, uval, dinv, x, z, dr);
+  if (mode == 3) return desc_row_value<T, true, true, false, TX>(d, l_col, lval, dinv, x, z, dr) * dr;
+  if (mode == 5) return desc_row_value<T, true, true, true, TX>(d, l_col, lval, dinv, x, z, dr) * dr;
+  const T v = desc_row_value<T, true, false, false, TX>(d, l_col, lval, dinv, x, z, dr);
   return mode == 2 ? v * dr : v;
 }
 
@@ -582,10 +584,12 @@ __device__ __forceinline__ T desc_row_mode(int mode, const int4 d, const int *l_
 // list (count rows): three dependent loads per row (descriptor, entries,
 // gathered values) instead of five through the chunk tables.  R rows per
 // thread as k_sptrsv_chunks; the value of each row does not depend on R.
-template <typename T, int R>
+// x of type TX (rounded to T as read); z64 (optional): the rows' final values
+// also written in FP64 (the preconditioner's FP64 output)
+template <typename T, int R, typename TX = T>
 __global__ void __launch_bounds__(kThreads / R)
 k_sptrsv_desc(const int4 *desc, int count, int mode, const int *l_col, const int *u_col, const T *lval,
-              const T *uval, const T *dinv, const T *x, T *z, const int *gate) {
+              const T *uval, const T *dinv, const TX *x, T *z, const int *gate, double *z64 = nullptr) {
   if (gate && *gate) return;
   constexpr int NT = kThreads / R;
   const int base = blockIdx.x * kThreads + threadIdx.x;
@@ -597,12 +601,15 @@ k_sptrsv_desc(const int4 *desc, int count, int mode, const int *l_col, const int
     rr[u] = -1;
     if (idx >= count) continue;
     const int4 d = desc[idx];
-    v[u] = desc_row_mode<T>(mode, d, l_col, u_col, lval, uval, dinv, x, z, dinv[d.x]);
+    v[u] = desc_row_mode<T, TX>(mode, d, l_col, u_col, lval, uval, dinv, x, z, dinv[d.x]);
     rr[u] = d.x;
   }
 #pragma unroll
   for (int u = 0; u < R; u++)
-    if (rr[u] >= 0) z[rr[u]] = v[u];
+    if (rr[u] >= 0) {
+      z[rr[u]] = v[u];
+      if (z64) z64[rr[u]] = double(v[u]);
+    }
 }
 
 // ======================================================= E, E^T products
@@ -626,16 +633,16 @@ __global__ void k_e_vec(int m, int s, const int *eh_rp, const int *eh_ci,
 }
 
 // interior rows only: v_r = xadd_r + a^-1 (Ehat w)_r
-template <typename T>
+template <typename T, typename TX = T>
 __global__ void k_e_interior(int m, const int *eh_rp, const int *eh_ci,
-                             const T *eh_val, T ia, const T *w, const T *xadd,
+                             const T *eh_val, T ia, const T *w, const TX *xadd,
                              T *v, const int *gate) {
   if (gate && *gate) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m) return;
   T acc = 0;
   for (int q = eh_rp[r]; q < eh_rp[r + 1]; q++) acc += eh_val[q] * w[eh_ci[q]];
-  v[r] = xadd[r] + ia * acc;
+  v[r] = T(xadd[r]) + ia * acc;
 }
 
 // y = E^T z = a^-1 Ehat^T z_B - a z_C  (interface rows j in [0, s))
@@ -1008,15 +1015,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_u_add_direct(long long nrows, c
   u_rows_dot_direct<KV>(nrows, U, h, [&](long long r, double d) { u[r] += d; });
 }
 
-template <typename T, typename TU, int L, int UNR>
+template <typename T, typename TU, int L, int UNR, typename TX = T>
 __global__ void k_w_rhs_vec(int s, int m, const TU *U, const T *t, const T *y, const T *inv1mt, T a,
-                            const T *x, T *w, T *rhs, const int *gate) {
+                            const TX *x, T *w, T *rhs, const int *gate) {
   if (gate && *gate) return;
   const T it = *inv1mt;
   u_rows_dot<T, TU, L, UNR>(s, U, t, [&](long long j, T d) {
     const T wj = it * y[j] + d;
     w[j] = wj;
-    rhs[m + j] = x[m + j] - a * wj;
+    rhs[m + j] = T(x[m + j]) - a * wj;
   });
 }
 
