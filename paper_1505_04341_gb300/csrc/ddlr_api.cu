@@ -67,19 +67,6 @@ thread_local std::string g_setup_error;
 
 }  // namespace
 
-// a solve's iteration loop captured as one graph (conditional WHILE node)
-struct LoopGraph {
-  cudaGraphExec_t exec = nullptr;
-  int key = -1;
-  long long nodes = 0;                 // kernel launches of one body iteration
-  std::vector<long long> fam_nodes;
-  void reset() {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    key = -1;
-  }
-};
-
 struct ddlr_ctx {
   ddlr_options opt{};
   int device = 0;                  // the device current at setup; all its memory is there
@@ -89,8 +76,6 @@ struct ddlr_ctx {
   cudaStream_t gstream = nullptr;  // internal stream of the PCG graph
   cudaGraphExec_t pcg_exec = nullptr;
   int pcg_exec_flexible = -1;
-  LoopGraph pcg_loop;              // the per-phase PCG loop as one graph
-  unsigned *loop_ctl = nullptr;    // device {rounds run, round cap} of a loop graph
   long long pcg_nodes = 0;
   std::vector<long long> pcg_fam_nodes;
   long long lz_nodes = 0;
@@ -116,7 +101,6 @@ struct ddlr_ctx {
       std::vector<long long> fam_nodes;
     };
     std::map<int, G> graphs;            // one captured PCG iteration per width R
-    std::map<int, LoopGraph> loops;     // the whole iteration loop per width R
     int chunk_per = 0, bd_elem = 256;   // autotuned: rows per pass of the level solve, row-kernel block
     bool tuned = false;
     int last_R = 0;                     // width of the last batched solve (byte accounting)
@@ -863,9 +847,6 @@ bool pz_launch(ddlr_ctx *c, const char *fam, const void *fn, size_t smem, void *
 size_t pz_lz_smem(int mmax);
 [[noreturn]] void timeout_fail(ddlr_ctx *c);
 void clear_timeout(ddlr_ctx *c);
-void build_loop_graph(ddlr_ctx *c, LoopGraph &LG, int key, int unroll, const int *done,
-                      const std::function<void()> &body);
-void run_loop_graph(ddlr_ctx *c, LoopGraph &LG, int unroll, unsigned max_rounds);
 
 // ------------------------------------------------------------- Lanczos
 void sync(ddlr_ctx *c) { ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"); }
@@ -1950,7 +1931,6 @@ void allocate(ddlr_ctx *c) {
   ck(cudaMemsetAsync(c->Hk64, 0, sizeof(double) * k * k, c->stream), "memset");
   ck(cudaMemsetAsync(c->inv1mt64, 0, sizeof(double), c->stream), "memset");
   c->dflag = c->alloc<int>(4);
-  c->loop_ctl = c->alloc<unsigned>(2);
   c->udone = c->alloc<unsigned>(1);
   ck(cudaMemsetAsync(c->udone, 0, sizeof(unsigned), c->stream), "memset");
   c->pdone = c->alloc<unsigned>(1);
@@ -2092,21 +2072,42 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
     KL(c, "pcg", c->stream, k_pcg_rz0, 1, 32, 0, c->pcg, part, kRedGrid);
     ck(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
     ck(cudaMemcpyAsync(zo, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy");
-    if (use_graph) {
-      // the whole iteration loop in one graph launch, ended on the device
-      constexpr int kUnroll = 2;
-      build_loop_graph(c, c->pcg_loop, flexible, kUnroll, pcg_gate(c), [&] { pcg_iteration(c, b, x, flexible); });
-      run_loop_graph(c, c->pcg_loop, kUnroll, unsigned(maxit / kUnroll + 3));
-    } else {
-      const int batch = 4;
-      for (int it = 0; it < maxit + batch; it += batch) {
-        for (int bi = 0; bi < batch; bi++) pcg_iteration(c, b, x, flexible);
-        int done = 0;
-        ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
-        ck(cudaStreamSynchronize(c->stream), "sync");
-        std::memcpy(&done, c->h_pin, sizeof(int));
-        if (done) break;
+    if (use_graph && (c->pcg_exec == nullptr || c->pcg_exec_flexible != flexible)) {
+      if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+      const long long l0 = c->launches;
+      const std::vector<long long> f0 = c->fam_cnt;
+      ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+      pcg_iteration(c, b, x, flexible);
+      cudaGraph_t g = nullptr;
+      ck(cudaStreamEndCapture(c->stream, &g), "capture");
+      cudaError_t e = cudaGraphInstantiate(&c->pcg_exec, g, 0);
+      cudaGraphDestroy(g);
+      ck(e, "cudaGraphInstantiate");
+      c->pcg_exec_flexible = flexible;
+      c->pcg_nodes = c->launches - l0;
+      c->pcg_fam_nodes.assign(c->fam_cnt.size(), 0);
+      for (size_t i = 0; i < c->fam_cnt.size(); i++)
+        c->pcg_fam_nodes[i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+      c->launches = l0;                    // captured, not yet executed
+      for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+      for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+    }
+    const int batch = 4;
+    for (int it = 0; it < maxit + batch; it += batch) {
+      for (int bi = 0; bi < batch; bi++) {
+        if (use_graph) {
+          ck(cudaGraphLaunch(c->pcg_exec, c->stream), "cudaGraphLaunch");
+          c->launches += c->pcg_nodes;
+          for (size_t i = 0; i < c->pcg_fam_nodes.size(); i++) c->fam_cnt[i] += c->pcg_fam_nodes[i];
+        } else {
+          pcg_iteration(c, b, x, flexible);
+        }
       }
+      int done = 0;
+      ck(cudaMemcpyAsync(c->h_pin, pcg_gate(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+      ck(cudaStreamSynchronize(c->stream), "sync");
+      std::memcpy(&done, c->h_pin, sizeof(int));
+      if (done) break;
     }
   }
   // final true residual
@@ -2245,7 +2246,6 @@ void batch_free(ddlr_ctx *c) {
   auto &B = c->bt;
   for (auto &kv : B.graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-  for (auto &kv : B.loops) kv.second.reset();
   for (void *p : B.mem) cudaFree(p);
   B = ddlr_ctx::Batch();
 }
@@ -2619,65 +2619,6 @@ void mr_graph(ddlr_ctx *c, int R, int flexible) {
   for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
 }
 
-// A solve's whole iteration loop as one graph: a conditional WHILE node
-// whose body is `unroll` iterations (`body`, captured into it) followed by
-// k_loop_cond, so the loop runs on the device with no host round trip until
-// `done` is set.  Launch counts of one body are returned in nodes/fam_nodes.
-void build_loop_graph(ddlr_ctx *c, LoopGraph &LG, int key, int unroll, const int *done,
-                      const std::function<void()> &body) {
-  if (LG.exec && LG.key == key) return;
-  if (LG.exec) { cudaGraphExecDestroy(LG.exec); LG.exec = nullptr; }
-  cudaGraph_t g = nullptr;
-  ck(cudaGraphCreate(&g, 0), "cudaGraphCreate");
-  try {
-    cudaGraphConditionalHandle h;
-    ck(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault), "conditional handle");
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node");
-    cudaGraph_t bg = cp.conditional.phGraph_out[0];
-    const long long l0 = c->launches;
-    const std::vector<long long> f0 = c->fam_cnt;
-    ck(cudaStreamBeginCaptureToGraph(c->stream, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
-       "capture");
-    for (int u = 0; u < unroll; u++) body();
-    k_loop_cond<<<1, 32, 0, c->stream>>>(h, done, c->loop_ctl);
-    cudaGraph_t out = nullptr;
-    ck(cudaStreamEndCapture(c->stream, &out), "capture");
-    LG.nodes = (c->launches - l0) / unroll;
-    LG.fam_nodes.assign(c->fam_cnt.size(), 0);
-    for (size_t i = 0; i < c->fam_cnt.size(); i++)
-      LG.fam_nodes[i] = (c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0)) / unroll;
-    c->launches = l0;
-    for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
-    for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
-    ck(cudaGraphInstantiate(&LG.exec, g, 0), "cudaGraphInstantiate");
-  } catch (...) {
-    cudaGraphDestroy(g);
-    throw;
-  }
-  cudaGraphDestroy(g);
-  LG.key = key;
-}
-// launch the loop graph for at most max_rounds body rounds; returns the
-// number of iterations the body ran (read back; the launch counters are
-// advanced by it)
-void run_loop_graph(ddlr_ctx *c, LoopGraph &LG, int unroll, unsigned max_rounds) {
-  unsigned ctl[2] = {0u, max_rounds};
-  ck(cudaMemcpyAsync(c->loop_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, c->stream), "H2D");
-  ck(cudaGraphLaunch(LG.exec, c->stream), "cudaGraphLaunch");
-  ck(cudaMemcpyAsync(ctl, c->loop_ctl, sizeof(ctl), cudaMemcpyDeviceToHost, c->stream), "D2H");
-  ck(cudaStreamSynchronize(c->stream), "sync");
-  const long long rounds = ctl[0];
-  c->launches += rounds * (LG.nodes * unroll + 1);
-  for (size_t i = 0; i < LG.fam_nodes.size() && i < c->fam_cnt.size(); i++)
-    c->fam_cnt[i] += rounds * unroll * LG.fam_nodes[i];
-}
-
 // one batched iteration of width R on c->stream (the graph when use_graph)
 void mr_iterate(ddlr_ctx *c, int R, int flexible, bool use_graph) {
   if (use_graph) {
@@ -2723,22 +2664,15 @@ void pcg_mr_dev(ddlr_ctx *c, int R, double tol, int maxit, ddlr_solve_info *info
   KL(c, "pcg_mr", c->stream, k_pcgmr_rz0, 1, kScalarThreads, 0, B.st, part, kRedGrid);
   ck(cudaMemcpyAsync(B.P, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
   ck(cudaMemcpyAsync(B.Zo, B.Z, sizeof(double) * nR, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  if (use_graph) {
-    // the whole iteration loop in one graph launch, ended on the device
-    constexpr int kUnroll = 2;
-    auto &LG = B.loops[R];
-    build_loop_graph(c, LG, flexible, kUnroll, gate, [&] { pcg_mr_iteration(c, R, flexible); });
-    run_loop_graph(c, LG, kUnroll, unsigned(maxit / kUnroll + 3));
-  } else {
-    const int batch = 4;
-    for (int it = 0; it < maxit + batch; it += batch) {
-      for (int bi = 0; bi < batch; bi++) mr_iterate(c, R, flexible, false);
-      int done = 0;
-      ck(cudaMemcpyAsync(c->h_pin, gate, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
-      ck(cudaStreamSynchronize(c->stream), "sync");
-      std::memcpy(&done, c->h_pin, sizeof(int));
-      if (done) break;
-    }
+  if (use_graph) mr_graph(c, R, flexible);
+  const int batch = 4;
+  for (int it = 0; it < maxit + batch; it += batch) {
+    for (int bi = 0; bi < batch; bi++) mr_iterate(c, R, flexible, use_graph);
+    int done = 0;
+    ck(cudaMemcpyAsync(c->h_pin, gate, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    std::memcpy(&done, c->h_pin, sizeof(int));
+    if (done) break;
   }
   // true residuals
   KL(c, "spmv_mr", c->stream, k_spmv_mr<double>, eblk(nR, bd), bd, 0, n, c->a_soff, c->a_sw, c->a_col,
@@ -3183,7 +3117,6 @@ ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
     // graphs hold the old arrays' addresses
     if (W.exec) { cudaGraphExecDestroy(W.exec); W.exec = nullptr; }
     if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
-    c->pcg_loop.reset();
     batch_free(c);
     // Lanczos workspace for m_new steps: the basis and T_j carried over (the
     // old arrays stay in the handle's arena until it is destroyed)
@@ -3733,9 +3666,6 @@ ddlr_status ddlr_set_wait_limit(ddlr_handle c, double seconds) {
     for (auto &kv : c->bt.graphs)
       if (kv.second.exec) { cudaGraphExecDestroy(kv.second.exec); kv.second.exec = nullptr; }
     c->bt.graphs.clear();
-    for (auto &kv : c->bt.loops) kv.second.reset();
-    c->bt.loops.clear();
-    c->pcg_loop.reset();
     return DDLR_OK;
   });
 }
@@ -3758,7 +3688,6 @@ ddlr_status ddlr_destroy(ddlr_handle c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
-  c->pcg_loop.reset();
   if (c->lw.exec) cudaGraphExecDestroy(c->lw.exec);
   if (c->lw.ev_chk) cudaEventDestroy(c->lw.ev_chk);
   if (c->lw.ev_done) cudaEventDestroy(c->lw.ev_done);

@@ -1403,19 +1403,6 @@ __global__ void k_pcg_p(long long n, const PcgState *st, const double *z,
   if (zold) zold[i] = zi;
 }
 
-// ------------------------------------------------ device-driven solve loop
-// The body of the WHILE node of a solve graph ends with this kernel: the loop
-// goes on while the solve is not done and fewer than ctl[1] rounds have run
-// (ctl[0] counts them; the cap makes the loop end even if `done` were never
-// set).  The host zeroes ctl[0] and writes ctl[1] before each launch.
-__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int *done, unsigned *ctl) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    const unsigned r = ctl[0] + 1;
-    ctl[0] = r;
-    cudaGraphSetConditional(h, (*done == 0 && r < ctl[1]) ? 1u : 0u);
-  }
-}
-
 // ================================================================ Lanczos
 // ------------------------------------------------ device-driven Lanczos step
 // Control state of the Lanczos recurrence kept on the device, so a step needs
