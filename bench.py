@@ -411,6 +411,7 @@ def run_ours(args):
             "iterations": its, "true_relres_max": relres,
             "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
             "lanczos_steps": info["lanczos_steps"], "reorth_passes": info["reorth_passes"],
+            "reorth_fp32_corrections": info["reorth_fp32"],
             "theta": info["theta"], "fill_ratio": round(info["fill_ratio"], 3),
             "levels_interior": info["levels_interior"], "levels_c": info["levels_c"],
             "persistent": info["persistent"], "wall_s": round(wall, 3),

@@ -163,6 +163,10 @@ typedef struct {
   int cheb_lanczos_steps;  /* c_solver 1: Lanczos steps the estimate took         */
   int reorth_passes;       /* Gram-Schmidt passes of the Lanczos steps of the last
                               build (lowrank_method 0; restart vectors excluded) */
+  int reorth_fp32;         /* of the corrections w -= Q c of those passes (and of
+                              restart vectors), the ones the persistent Lanczos
+                              kernel formed in FP32 from an FP32 copy of Q: only
+                              where their error bound is below FP64 rounding of w */
 } ddlr_info;
 
 typedef struct {
@@ -340,6 +344,18 @@ ddlr_status ddlr_set_stream(ddlr_handle h, void *cuda_stream);
  * launched it returns DDLR_ERR_TIMEOUT (its results are invalid); the flag is
  * cleared then, so the handle stays usable.  Errors: INVALID. */
 ddlr_status ddlr_set_wait_limit(ddlr_handle h, double seconds);
+
+/* Self-test of the library's binary64 <-> binary32 conversions written on the
+ * bit patterns (IEEE 754-2008 Sec. 5.4.2 formatOf conversions: rounding to
+ * nearest, ties to even; widening exact), which the batched mixed-precision
+ * casts use, against the device's own conversion instructions.  in: n
+ * doubles in DEVICE memory (not modified).  dir 0: each value narrowed to
+ * binary32; dir 1: the low 32 bits of each value read as a binary32 and
+ * widened.  *mismatches = the number of results whose bits differ (NaNs of
+ * either kind count as equal when widening).  Synchronous, on the legacy
+ * stream; allocates n doubles of device scratch.  Errors: INVALID (NULL or
+ * host pointer, n < 0, bad dir), CUDA. */
+ddlr_status ddlr_selftest_conversions(const double *in, long long n, int dir, long long *mismatches);
 
 /* Text of the last error on this handle; with h == NULL, of the last failed
  * ddlr_setup on this thread.  Never NULL. */

@@ -209,6 +209,7 @@ struct ddlr_ctx {
   std::vector<double> ritz;
   int msteps = 0;
   int lz_passes = 0;          // Gram-Schmidt passes of the last Lanczos build
+  int lz_fp32 = 0;            // of their corrections, those formed in FP32
   double theta = 0.0;
   int *dflag = nullptr;       // device error flags [0]=breakdown [1]=notspd [2]=eig fail
   // Lanczos workspace, start vector and step graph, kept for refactors
@@ -217,6 +218,7 @@ struct ddlr_ctx {
     double *Q = nullptr, *al = nullptr, *be = nullptr, *cvec = nullptr, *w = nullptr, *qcur = nullptr,
            *qprev = nullptr, *nrm = nullptr, *ework = nullptr, *etop = nullptr, *evals = nullptr,
            *esum = nullptr, *eY = nullptr, *q0 = nullptr;
+    float *Q32 = nullptr;             // FP32 copy of Q (persistent Lanczos)
     double *V = nullptr, *EV = nullptr, *vc = nullptr, *ev = nullptr, *uc = nullptr, *kp = nullptr, *hw = nullptr;
     int *rank = nullptr;
     LzState *st = nullptr;
@@ -245,6 +247,20 @@ struct ddlr_ctx {
   // accounting
   long long launches = 0;
   bool timing = false;
+  // launches carry the dependent-launch attribute (DDLR_NO_PDL=1: plain launches)
+  // (not while a graph is captured: inside the per-iteration graphs the
+  // attribute measured slower, 128^3 PCG 68.3 -> 71.1 ms, while direct
+  // launches gain, 128^3 apply 0.259 -> 0.241 ms)
+  bool pdl = [] {
+    const char *e = getenv("DDLR_NO_PDL");
+    return !(e && e[0] == '1');
+  }();
+  bool capturing = false;
+  struct Capture {   // marks a graph capture on this handle for its scope
+    bool &f;
+    explicit Capture(bool &f_) : f(f_) { f = true; }
+    ~Capture() { f = false; }
+  };
   struct Rec { int fam; cudaEvent_t a, b; };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> evpool;
@@ -342,10 +358,34 @@ struct ddlr_ctx {
   };
 };
 
+// Kernel launch with the handle's family accounting.  With ctx->pdl the
+// launch carries the programmatic-stream-serialisation attribute (see
+// DDLR_PDL_ENTRY): the kernel may be scheduled while its predecessor in the
+// stream finishes, and waits for it on entry.
+template <typename... KArgs, typename... Args>
+void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+              Args &&...args) {
+  if (!pdl) {
+    kern<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 #define KL(ctx, name, strm, kern, grid, block, smem, ...)                      \
   do {                                                                          \
     ddlr_ctx::Scope _sc((ctx), (name), (strm));                                 \
-    kern<<<(grid), (block), (smem), (strm)>>>(__VA_ARGS__);                     \
+    launch_k((ctx)->pdl && !(ctx)->capturing, kern, dim3(grid), dim3(block), size_t(smem), (strm), __VA_ARGS__); \
   } while (0)
 
 namespace {
@@ -1030,9 +1070,11 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
     bool persist = c->pz_lz && mmax <= c->pz_mmax &&
                    (long long)mmax * (4 * (2 * nLz - 1) + 16) * c->pz_grid < (1LL << 31);
     if (persist) {
+      // the kernel fills the FP32 copy of the basis from Q when it starts
+      if (!W.Q32) W.Q32 = c->alloc<float>(size_t(s) * size_t(mmax + 1));
       PzOp<double, double> O = make_pzop<double, double>(c);
       PzLz Lz{L.Q, L.ld, L.al, L.be, L.w, L.qcur, L.qprev, c->w64[0], c->w64[1], etop, L.rank, L.st, check, k, eps,
-              c->opt.lanczos_reorth};
+              c->opt.lanczos_reorth, W.Q32};
       void *args[] = {&O, &Lz};
       persist = pz_launch(c, "lanczos_persist", (const void *)k_lz_persist<kPzLzThreads>, pz_lz_smem(c->pz_mmax),
                           args, kPzLzThreads);
@@ -1045,6 +1087,7 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
       if (!W.exec) {
         const long long l0 = c->launches;
         const std::vector<long long> f0 = c->fam_cnt;
+        ddlr_ctx::Capture cap_(c->capturing);
         ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
         lanczos_step(c, L);
         cudaGraph_t g = nullptr;
@@ -1101,19 +1144,20 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
     ck(cudaMemcpy(&hs, L.st, sizeof(hs), cudaMemcpyDeviceToHost), "D2H");
     if (persist) {
       // per step: E q, one (DDLR-2: two) A0 solves, E^T, the three-term update
-      // and normalisation, and one or two CGS passes reading Q_{j+1} twice
-      // each (the second pass on npass2 of the steps)
+      // and normalisation (with the FP32 copy of q_{j+1}), and the CGS passes:
+      // the basis columns they read in FP64 and in FP32, as counted on the
+      // device
       double a0 = 0;
       ddlr_get_traffic(c, nullptr, &a0, nullptr, 0);
       const double ne = double(P.nnz_ehat), sd = double(s) * 8.0, nd = double(n) * 8.0;
       const double step = ne * 12.0 + sd + nd + (c->opt.variant == 2 ? 2.0 : 1.0) * a0 + ne * 12.0 + nd + sd +
                           8.0 * sd;
       const double steps = double(hs.j);
-      const double passes = steps > 0 ? 1.0 + double(hs.npass2) / steps : 1.0;
-      c->pz_lz_bytes += steps * step + passes * 2.0 * sd * steps * (steps + 1.0) / 2.0;
+      c->pz_lz_bytes += steps * (step + 4.0 * s) + sd * hs.qcols64 + 4.0 * s * hs.qcols32;
       c->pz_lz_runs += 1;
     }
     c->lz_passes = hs.j + hs.npass2;
+    c->lz_fp32 = persist ? hs.nfp32 : 0;
     {
       // a bounded wait of the persistent kernel ran out: the state is not
       // that of a finished process
@@ -1698,7 +1742,9 @@ ddlr_status numeric_setup(ddlr_ctx *c) {
 
 // ------------------------------------------------ persistent kernels
 size_t pz_pcg_smem(int k) { return size_t(kPzThreads + 32 + k + 2) * sizeof(double); }
-size_t pz_lz_smem(int mmax) { return size_t(kPzLzThreads + 32 + 3 * mmax + 2) * sizeof(double); }
+size_t pz_lz_smem(int mmax) {
+  return size_t(kPzLzThreads + 32 + 3 * mmax + 2) * sizeof(double) + size_t(mmax + 2) * sizeof(float);
+}
 
 // Whole-solve persistent kernels serve shallow factors (every block at most
 // kPzMaxLevels levels deep) on devices with cooperative launch; one CTA per
@@ -2076,6 +2122,7 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
       if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
       const long long l0 = c->launches;
       const std::vector<long long> f0 = c->fam_cnt;
+      ddlr_ctx::Capture cap_(c->capturing);
       ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
       pcg_iteration(c, b, x, flexible);
       cudaGraph_t g = nullptr;
@@ -2568,11 +2615,13 @@ void pcg_mr_iteration(ddlr_ctx *c, int R, int flexible) {
   // q = A p with the p.q partials, and the x, r update with the r.r partials,
   // in one pass each (64-row blocks, then the blocks of each reduction range)
   const unsigned nb = (unsigned)((n + kFbRows - 1) / kFbRows);
-  KL(c, "spmv_mr", c->stream, k_spmv_pq_mr, nb, kFbLanes * R, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, B.P,
+  const int fg = fb_groups(R);
+  const unsigned fgrid = (nb + fg - 1) / fg, fthreads = unsigned(fg * kFbLanes * R);
+  KL(c, "spmv_mr", c->stream, k_spmv_pq_mr, fgrid, fthreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, B.P,
      B.Q, R, B.fpart, gate);
   KL(c, "pcg_mr_red", c->stream, k_fused_partials_reduce, kRedGrid, 64, 0, (int)nb, R, B.fpart, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_alpha, 1, kScalarThreads, 0, B.st, part, kRedGrid);
-  KL(c, "pcg_mr_axpy", c->stream, k_update_rr_mr, nb, kFbLanes * R, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr,
+  KL(c, "pcg_mr_axpy", c->stream, k_update_rr_mr, fgrid, fthreads, 0, (long long)n, B.st, B.P, B.Q, B.X, B.Rr,
      B.fpart);
   KL(c, "pcg_mr_red", c->stream, k_fused_partials_reduce, kRedGrid, 64, 0, (int)nb, R, B.fpart, part, gate);
   KL(c, "pcg_mr_scalar", c->stream, k_pcgmr_rr, 1, kScalarThreads, 0, B.st, part, kRedGrid);
@@ -2602,6 +2651,7 @@ void mr_graph(ddlr_ctx *c, int R, int flexible) {
   if (GR.exec) { cudaGraphExecDestroy(GR.exec); GR.exec = nullptr; }
   const long long l0 = c->launches;
   const std::vector<long long> f0 = c->fam_cnt;
+  ddlr_ctx::Capture cap_(c->capturing);
   ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
   pcg_mr_iteration(c, R, flexible);
   cudaGraph_t g = nullptr;
@@ -3129,6 +3179,7 @@ ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
       ck(cudaMemcpyAsync(al, W.al, sizeof(double) * (m_old + 1), cudaMemcpyDeviceToDevice, c->stream), "copy");
       ck(cudaMemcpyAsync(be, W.be, sizeof(double) * (m_old + 1), cudaMemcpyDeviceToDevice, c->stream), "copy");
       W.Q = Q; W.al = al; W.be = be;
+      W.Q32 = nullptr;   // allocated again at the next persistent Lanczos launch
       W.cvec = c->alloc<double>(m_new + 2);
       W.evals = c->alloc<double>(m_new);
     }
@@ -3395,6 +3446,7 @@ ddlr_status ddlr_get_info(ddlr_handle c, ddlr_info *info) {
   info->plan_ms = c->plan_ms;
   info->persistent = (c->pz_pcg ? 1 : 0) | (c->pz_lz ? 2 : 0);
   info->reorth_passes = c->lz_passes;
+  info->reorth_fp32 = c->lz_fp32;
   if (c->opt.c_solver == 1) {
     double lohi[2] = {0, 0};
     if (cudaMemcpy(lohi, c->ctab64, sizeof(lohi), cudaMemcpyDeviceToHost) != cudaSuccess) return DDLR_ERR_CUDA;
@@ -3668,6 +3720,28 @@ ddlr_status ddlr_set_wait_limit(ddlr_handle c, double seconds) {
     c->bt.graphs.clear();
     return DDLR_OK;
   });
+}
+
+ddlr_status ddlr_selftest_conversions(const double *in, long long n, int dir, long long *mismatches) {
+  if (!in || !mismatches || n < 0 || (dir != 0 && dir != 1)) return DDLR_ERR_INVALID;
+  *mismatches = 0;
+  if (n == 0) return DDLR_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, in) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return DDLR_ERR_INVALID;
+  }
+  double *out = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * size_t(n)) != cudaSuccess) return DDLR_ERR_CUDA;
+  k_cvt_check<<<unsigned((n + 255) / 256), 256>>>(n, in, out, dir);
+  std::vector<double> h(static_cast<size_t>(n));
+  cudaError_t e = cudaMemcpy(h.data(), out, sizeof(double) * size_t(n), cudaMemcpyDeviceToHost);
+  cudaFree(out);
+  if (e != cudaSuccess) return DDLR_ERR_CUDA;
+  long long bad = 0;
+  for (double v : h) bad += v != 0.0;
+  *mismatches = bad;
+  return DDLR_OK;
 }
 
 const char *ddlr_last_error(ddlr_handle c) {

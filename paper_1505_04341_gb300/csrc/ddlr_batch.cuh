@@ -47,6 +47,7 @@ template <typename T>
 __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
                                    const T *lval, const T *uval, const T *dinv,
                                    const T *X, T *Z, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int4 ch = chunks[blockIdx.x];
   const int lvl = ch.x, r0 = S.lvl_row0[lvl], s0 = S.lvl_slice0[lvl];
@@ -89,6 +90,7 @@ template <typename T>
 __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
                                  const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
                                  const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   constexpr int RR = kMrRowsPerThread;
   const int per = blockDim.x / R;
@@ -182,6 +184,7 @@ template <typename T>
 __global__ void k_sptrsv_desc_mr_v(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
                                    const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
                                    const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -276,6 +279,7 @@ template <typename T>
 __global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,
                         const T *eht_val, T ia, T a, const T *Z, T *Y, int R,
                         const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long j = row_of(idx, R);
@@ -291,6 +295,7 @@ template <typename T>
 __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
                                 const T *eh_val, T ia, const T *W, const T *X, T *RHS,
                                 int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long r = row_of(idx, R);
@@ -307,6 +312,7 @@ __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
 template <typename T>
 __global__ void k_et_mr_v(int s, int m, const int *eht_rp, const int *eht_ci, const T *eht_val, T ia, T a,
                           const T *Z, T *Y, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -335,6 +341,7 @@ __global__ void k_et_mr_v(int s, int m, const int *eht_rp, const int *eht_ci, co
 template <typename T>
 __global__ void k_e_interior_mr_v(int m, const int *eh_rp, const int *eh_ci, const T *eh_val, T ia, const T *W,
                                   const T *X, T *RHS, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -366,6 +373,7 @@ template <typename T, typename TU>
 __global__ void __launch_bounds__(256)
 k_utx_mr_partial(long long nrows, int k, const TU *U, const T *Y, int R, T *partials,
                  const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T us[32 * 64];
   __shared__ T ys[32 * kMaxR];
@@ -403,6 +411,7 @@ k_utx_mr_partial(long long nrows, int k, const TU *U, const T *Y, int R, T *part
 template <typename T>
 __global__ void k_reduce_mr(int G, int k, int R, const T *partials, const T *coef,
                             const T *H, T *out, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T tmp[1024];
   const int no = k * R;
@@ -429,6 +438,7 @@ template <typename T, typename TU>
 __global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const T *Y,
                            const T *inv1mt, T a, const T *X, T *W, T *RHS, int R,
                            const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T ts[1024];
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = Tm[o];
@@ -449,6 +459,7 @@ __global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const 
 template <typename T, typename TU>
 __global__ void k_u_add_mr(long long nrows, int k, const TU *U, const T *HT, T *Uo, int R,
                            const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T ts[1024];
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = HT[o];
@@ -510,6 +521,7 @@ constexpr int kTcRows = 32, kTcUS = 68, kTcYS = 72;   // smem strides: conflict-
 template <typename TU>
 __global__ void __launch_bounds__(256)
 k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *partials, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float us[kTcRows * kTcUS];
   __shared__ float ys[kTcRows * kTcYS];
@@ -583,6 +595,7 @@ k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *p
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_reduce_cols_mr(int G, int no, int R, const T *partials, const T *coef, T *out, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T sm[8][32];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -647,6 +660,7 @@ template <typename TU>
 __global__ void __launch_bounds__(256)
 k_w_rhs_mr_tc(int s, int m, int k, const TU *U, const float *Tm, const float *Y, const float *inv1mt, float a,
               const float *X, float *W, float *RHS, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float ts[64 * 72];
   const int TS = tc_stage_small(Tm, k, R, ts);
@@ -679,6 +693,7 @@ k_w_rhs_mr_tc(int s, int m, int k, const TU *U, const float *Tm, const float *Y,
 template <typename TU>
 __global__ void __launch_bounds__(256)
 k_u_add_mr_tc(long long nrows, int k, const TU *U, const float *HT, float *Uo, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float ts[64 * 72];
   const int TS = tc_stage_small(HT, k, R, ts);
@@ -706,6 +721,7 @@ k_u_add_mr_tc(long long nrows, int k, const TU *U, const float *HT, float *Uo, i
 template <typename T>
 __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
                           const T *val, const T *P, T *Q, int R, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long r = row_of(idx, R);
@@ -726,6 +742,7 @@ __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
 __global__ void __launch_bounds__(256)
 k_dot_mr_partial(long long n, int R, const double *A, const double *B,
                  const double *C, double *partials, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ double red[8][2 * kMaxR];
   const int w = threadIdx.x >> 5, q = threadIdx.x & 31;
@@ -780,35 +797,49 @@ struct PcgStateMR {
 // into partials[block][q].  k_fused_partials_reduce then adds the blocks of each
 // of the G = kRedGrid reduction ranges in order into the [g][2R] layout the
 // scalar kernels read.  Nothing in this order depends on R, so a column's dot
-// products are the same in every batch.  Launch: ceil(n / 64) CTAs of 8 R
-// threads.
-constexpr int kFbRows = 64, kFbLanes = 8;
+// products are the same in every batch.  Launch: a CTA takes fb_groups(R)
+// row blocks (8 R threads each, at least 256 threads a CTA for small R, so
+// narrow blocks are not held to a few threads per SM by the CTA limit).
+constexpr int kFbRows = 64, kFbLanes = 8, kFbCta = 256, kFbMaxRed = 512;
+__host__ __device__ inline int fb_groups(int R) { return R * kFbLanes >= kFbCta ? 1 : kFbCta / (R * kFbLanes); }
 
-// Q = A P (sliced ELL) and the column partials of P.Q
-__global__ void k_spmv_pq_mr(int n, const int *soff, const int *sw, const int *col, const double *val,
-                             const double *P, double *Q, int R, double *bpart, const int *gate) {
+// Q = A P (sliced ELL) and the column partials of P.Q.  Bound by the FP64
+// pipe (one FMA per stored entry and column, one more for the dot product:
+// 8 per row and column for the 7-point operators), so the products are not
+// batched in wider predicated groups, whose idle lanes still take FP64 issue
+// slots.
+__global__ void k_spmv_pq_mr(int n, const int *__restrict__ soff, const int *__restrict__ sw,
+                             const int *__restrict__ col, const double *__restrict__ val,
+                             const double *__restrict__ P, double *__restrict__ Q, int R, double *bpart,
+                             const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
-  __shared__ double red[kFbLanes][kMaxR];
-  const int q = threadIdx.x % R, l = threadIdx.x / R;
-  const int r0 = blockIdx.x * kFbRows;
+  __shared__ double red[kFbMaxRed];
+  const int gt = kFbLanes * R, gi = threadIdx.x / gt, tt = threadIdx.x % gt;
+  const int q = tt % R, l = tt / R;
+  const int nblk = (n + kFbRows - 1) / kFbRows;
+  const int rb = blockIdx.x * fb_groups(R) + gi;
   double acc = 0.0;
-  for (int i = l; i < kFbRows; i += kFbLanes) {
-    const int r = r0 + i;
-    if (r >= n) break;
-    const int g = r >> 5, ln = r & 31;
-    const int off = soff[g] + ln, w = sw[g];
-    double t = 0;
-    for (int kk = 0; kk < w; kk++) t += val[off + kk * 32] * P[(long long)col[off + kk * 32] * R + q];
-    const long long e = (long long)r * R + q;
-    Q[e] = t;
-    acc = fma(P[e], t, acc);
+  if (rb < nblk) {
+    const int r0 = rb * kFbRows;
+    for (int i = l; i < kFbRows; i += kFbLanes) {
+      const int r = r0 + i;
+      if (r >= n) break;
+      const int g = r >> 5, ln = r & 31;
+      const int off = soff[g] + ln, w = sw[g];
+      double t = 0;
+      for (int kk = 0; kk < w; kk++) t = fma(val[off + kk * 32], P[(long long)col[off + kk * 32] * R + q], t);
+      const long long e = (long long)r * R + q;
+      Q[e] = t;
+      acc = fma(P[e], t, acc);
+    }
   }
-  red[l][q] = acc;
+  red[(gi * kFbLanes + l) * R + q] = acc;
   __syncthreads();
-  if (l == 0) {
+  if (l == 0 && rb < nblk) {
     double v = 0.0;
-    for (int j = 0; j < kFbLanes; j++) v += red[j][q];
-    bpart[(long long)blockIdx.x * R + q] = v;
+    for (int j = 0; j < kFbLanes; j++) v += red[(gi * kFbLanes + j) * R + q];
+    bpart[(long long)rb * R + q] = v;
   }
 }
 
@@ -816,32 +847,38 @@ __global__ void k_spmv_pq_mr(int n, const int *soff, const int *sw, const int *c
 // partials of Rr.Rr (all columns)
 __global__ void k_update_rr_mr(long long n, const PcgStateMR *st, const double *P, const double *Q, double *X,
                                double *Rr, double *bpart) {
+  DDLR_PDL_ENTRY();
   if (st->all_done) return;
-  __shared__ double red[kFbLanes][kMaxR];
+  __shared__ double red[kFbMaxRed];
   const int R = st->R;
-  const int q = threadIdx.x % R, l = threadIdx.x / R;
-  const long long r0 = (long long)blockIdx.x * kFbRows;
+  const int gt = kFbLanes * R, gi = threadIdx.x / gt, tt = threadIdx.x % gt;
+  const int q = tt % R, l = tt / R;
+  const long long nblk = (n + kFbRows - 1) / kFbRows;
+  const long long rb = (long long)blockIdx.x * fb_groups(R) + gi;
   const bool run = !st->done[q];
   const double a = st->alpha[q];
   double acc = 0.0;
-  for (int i = l; i < kFbRows; i += kFbLanes) {
-    const long long r = r0 + i;
-    if (r >= n) break;
-    const long long e = r * R + q;
-    double rv = Rr[e];
-    if (run) {
-      X[e] += a * P[e];
-      rv -= a * Q[e];
-      Rr[e] = rv;
+  if (rb < nblk) {
+    const long long r0 = rb * kFbRows;
+    for (int i = l; i < kFbRows; i += kFbLanes) {
+      const long long r = r0 + i;
+      if (r >= n) break;
+      const long long e = r * R + q;
+      double rv = Rr[e];
+      if (run) {
+        X[e] += a * P[e];
+        rv -= a * Q[e];
+        Rr[e] = rv;
+      }
+      acc = fma(rv, rv, acc);
     }
-    acc = fma(rv, rv, acc);
   }
-  red[l][q] = acc;
+  red[(gi * kFbLanes + l) * R + q] = acc;
   __syncthreads();
-  if (l == 0) {
+  if (l == 0 && rb < nblk) {
     double v = 0.0;
-    for (int j = 0; j < kFbLanes; j++) v += red[j][q];
-    bpart[(long long)blockIdx.x * R + q] = v;
+    for (int j = 0; j < kFbLanes; j++) v += red[(gi * kFbLanes + j) * R + q];
+    bpart[rb * R + q] = v;
   }
 }
 
@@ -849,6 +886,7 @@ __global__ void k_update_rr_mr(long long n, const PcgStateMR *st, const double *
 // order, of bpart[block][q]; grid kRedGrid, R threads
 __global__ void k_fused_partials_reduce(int nblocks, int R, const double *bpart, double *partials,
                                         const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int q = threadIdx.x;
   if (q >= R) return;
@@ -878,6 +916,7 @@ __device__ __forceinline__ void col_sums(const double *partials, int G, int R, i
 
 __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int R,
                              double tol, int maxit, int flexible) {
+  DDLR_PDL_ENTRY();
   const int q = threadIdx.x;
   __shared__ double sm[kMaxR];
   col_sums(partials, G, R, R, sm);
@@ -901,6 +940,7 @@ __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int 
 }
 
 __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
+  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[kMaxR];
@@ -913,6 +953,7 @@ __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
 }
 
 __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
+  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[kMaxR];
@@ -931,6 +972,7 @@ __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
 
 
 __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
+  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ int anyc;
@@ -956,6 +998,7 @@ __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
 __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, const int *sw,
                                  const int *col, const double *val, const double *B,
                                  const double *X, double *Tt) {
+  DDLR_PDL_ENTRY();
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * R;
@@ -972,6 +1015,7 @@ __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, c
 }
 
 __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) {
+  DDLR_PDL_ENTRY();
   const int q = threadIdx.x, R = st->R;
   if (q == 0) st->no_check = 1;   // the check of this iteration is consumed here
   if (st->all_done || !st->any_check) return;
@@ -991,6 +1035,7 @@ __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) 
 
 // (a restart is only ever set by a true-residual check of this iteration)
 __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *Tt, double *Rr) {
+  DDLR_PDL_ENTRY();
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n * R;
@@ -1001,6 +1046,7 @@ __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *
 }
 
 __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
+  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[2 * kMaxR];
@@ -1027,6 +1073,7 @@ __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
 // P = Z + beta P (and Zold = Z) for the columns still running
 __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, double *P,
                           double *Zold) {
+  DDLR_PDL_ENTRY();
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
@@ -1049,17 +1096,20 @@ __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, do
 
 // column q of a row-major n x R block <- a vector in original order
 __global__ void k_col_in(int n, int R, int q, const int *perm, const double *in, double *out) {
+  DDLR_PDL_ENTRY();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[(long long)g * R + q] = in[perm[g]];
 }
 // a vector in original order <- column q of a row-major n x R block
 __global__ void k_col_out(int n, int R, int q, const int *perm, const double *in, double *out) {
+  DDLR_PDL_ENTRY();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[perm[g]] = in[(long long)g * R + q];
 }
 // admitted columns (mask[q] != 0): X = 0, Rr = B, P = 0
 __global__ void k_slot_reset(long long n, int R, const int *mask, const double *B, double *X, double *Rr,
                              double *P) {
+  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
   const int q = col_of(idx, row_of(idx, R), R);
@@ -1071,6 +1121,7 @@ __global__ void k_slot_reset(long long n, int R, const int *mask, const double *
 // the per-column state of the admitted columns (partials: column sums of B.B)
 __global__ void k_slot_init(PcgStateMR *st, const double *partials, int G, const int *mask, int R, double tol,
                             int maxit, int flexible) {
+  DDLR_PDL_ENTRY();
   const int q = threadIdx.x;
   __shared__ double sm[kMaxR];
   col_sums(partials, G, R, R, sm);
@@ -1099,6 +1150,7 @@ __global__ void k_slot_init(PcgStateMR *st, const double *partials, int G, const
 // a block of R0 columns laid out again as R1 columns: column q of the new
 // block is column map[q] of the old one (map[q] < 0: a new, zero column)
 __global__ void k_relayout(long long n, int R0, int R1, const int *map, const double *in, double *out) {
+  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R1) return;
   const long long r = row_of(idx, R1);
@@ -1109,6 +1161,7 @@ __global__ void k_relayout(long long n, int R0, int R1, const int *map, const do
 
 // Tt = B - Q (all columns)
 __global__ void k_sub_mr(long long cnt, const double *B, const double *Q, double *Tt) {
+  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < cnt) Tt[idx] = B[idx] - Q[idx];
 }
@@ -1117,6 +1170,7 @@ __global__ void k_sub_mr(long long cnt, const double *B, const double *Q, double
 // the batch layout (row-major, device order); optional row scaling
 __global__ void k_batch_in(int n, int R, const int *perm, const double *in, long long ld,
                            double *out) {
+  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
   const long long g = row_of(idx, R);
@@ -1125,18 +1179,74 @@ __global__ void k_batch_in(int n, int R, const int *perm, const double *in, long
 }
 __global__ void k_batch_out(int n, int R, const int *perm, const double *in, double *out,
                             long long ld) {
+  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
   const long long g = row_of(idx, R);
   const int q = col_of(idx, g, R);
   out[q * ld + perm[g]] = in[idx];
 }
+// Binary64 <-> binary32 conversions written out on the bit patterns (IEEE 754:
+// rounding to nearest, ties to even, for results in the normal binary32 range;
+// widening is exact), in integer instructions.  On this part the hardware
+// conversions issue to the FP64 pipe, which the scaling multiply already
+// occupies; the streaming cast kernels were bound by that pipe.  Zeros,
+// subnormal results, overflow, infinities and NaNs take the hardware
+// conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned hi = unsigned(b >> 32);
+  const unsigned e = (hi >> 20) & 0x7ffu;            // binary64 biased exponent
+  if (e >= 897u && e <= 1150u) {                      // binary32 biased exponent e - 896 in [1, 254]
+    const unsigned long long m = b & 0x000fffffffffffffull;
+    unsigned f = ((e - 896u) << 23) | unsigned(m >> 29);
+    const unsigned rest = unsigned(m & 0x1fffffffull);   // the 29 bits dropped
+    if (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) f += 1u;   // a carry moves to the exponent
+    return __uint_as_float(f | (hi & 0x80000000u));
+  }
+  return __double2float_rn(x);
+}
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e != 0u && e != 255u) {
+    const unsigned long long b = (static_cast<unsigned long long>(u & 0x80000000u) << 32) |
+                                 (static_cast<unsigned long long>(e + 896u) << 52) |
+                                 (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+    return __longlong_as_double(static_cast<long long>(b));
+  }
+  return double(v);
+}
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ void from_f64(double x, float &o) { o = f64_to_f32_rn(x); }
+__device__ __forceinline__ void from_f64(double x, double &o) { o = x; }
+
+// tests: out[i] = the bit-pattern conversions of in[i] (dir 0: binary64 ->
+// binary32 -> stored widened; dir 1: the binary32 reading of the low word
+// widened), compared with the hardware conversions by the caller
+__global__ void k_cvt_check(long long n, const double *in, double *out, int dir) {
+  DDLR_PDL_ENTRY();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (dir == 0) {
+    const float f = f64_to_f32_rn(in[i]);
+    const float h = __double2float_rn(in[i]);
+    out[i] = __float_as_uint(f) == __float_as_uint(h) ? 0.0 : 1.0;
+  } else {
+    const float v = __uint_as_float(unsigned(__double_as_longlong(in[i])));
+    const double a = f32_to_f64(v), h = double(v);
+    out[i] = (__double_as_longlong(a) == __double_as_longlong(h)) || (v != v && a != a) ? 0.0 : 1.0;
+  }
+}
+
 // out = TO(in * d_row) (d == nullptr: no scaling): the diagonal scaling of the
 // scaled system and the change of precision of the preconditioner in one pass.
 // A thread takes four consecutive elements (one row index computed for them,
 // the next by increment); launch with ceil(n R / 4) threads.
 template <typename TO, typename TI>
 __global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *in, TO *out, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long nR = n * R;
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -1149,17 +1259,18 @@ __global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *i
 #pragma unroll
   for (int u = 0; u < 4; u++) {
     if (i0 + u >= nR) break;
-    double x = double(v[u]);
+    double x = to_f64(v[u]);
     if (d) {
       x *= d[r];
       if (++q == R) { q = 0; r++; }
     }
-    out[i0 + u] = TO(x);
+    from_f64(x, out[i0 + u]);
   }
 }
 
 __global__ void k_scale_rows_mr(long long n, int R, const double *d, const double *in,
                                 double *out, const int *gate) {
+  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < n * R) out[idx] = in[idx] * d[row_of(idx, R)];

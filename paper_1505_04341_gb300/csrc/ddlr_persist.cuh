@@ -502,6 +502,13 @@ struct PzLz {
   int check, k;
   double eps;
   int reorth2;      // 1: two Gram-Schmidt passes every step
+  float *Q32;       // FP32 copy of Q (same layout), for the Gram-Schmidt corrections
+};
+
+// Gram-Schmidt counters of one launch (the same in every CTA)
+struct LzCount {
+  int npass2, nfp32;
+  double q64, q32;
 };
 
 // partials of Q_{ncol}^T w over this CTA's rows [r0, r1), warp per column
@@ -557,16 +564,60 @@ __device__ __forceinline__ double pz_gemvN(const double *Q, long long ld, int nc
   return ww;
 }
 
+// w_r -= sum_j Q32[j][r] c32_j on this CTA's rows, the sum formed in FP32 and
+// subtracted from the FP64 w_r; returns this thread's sum of w_r^2
+template <int NT>
+__device__ __forceinline__ double pz_gemvN32(const float *Q, long long ld, int ncol, const float *cs, double *w,
+                                             int r0, int r1) {
+  double ww = 0;
+  for (int r = r0 + threadIdx.x; r < r1; r += NT) {
+    float acc = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < ncol; j++) acc = fmaf(Q[(long long)j * ld + r], cs[j], acc);
+    const double v = w[r] - double(acc);
+    w[r] = v;
+    ww += v * v;
+  }
+  return ww;
+}
+
+// Whether the correction Q c of a Gram-Schmidt pass may be formed in FP32
+// from the FP32 copy of Q and c rounded to FP32.  With u = 2^-24 its error is
+// at most (ncol + 2) u sum_j |Q_rj| |c_j| per row, so at most
+// (ncol + 2) sqrt(ncol) u ||c|| in norm; FP32 is taken when that bound is
+// below the unit roundoff of FP64 times ||w|| (ww0 = ||w||^2 before the pass),
+// i.e. when the update is as accurate as w's own rounding.  After the
+// three-term recurrence c holds only the rounding-level loss of orthogonality,
+// so the test passes on most steps; restart vectors and second passes after
+// cancellation keep FP64.  Warp 0 sums c.c in a fixed order from the shared c,
+// so every CTA decides alike.  Fills cs32 when it returns true.
+template <int NT>
+__device__ __forceinline__ bool pz_use32(const double *cs, int ncol, double ww0, float *cs32, double *flag) {
+  if (threadIdx.x < 32) {
+    double cc = 0;
+    for (int i = threadIdx.x; i < ncol; i += 32) cc += cs[i] * cs[i];
+    for (int o = 16; o > 0; o >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, o);
+    const double f = double(ncol + 2);
+    if (threadIdx.x == 0) *flag = (f * f * double(ncol) * cc <= 0x1p-58 * ww0) ? 1.0 : 0.0;
+  }
+  for (int i = threadIdx.x; i < ncol; i += NT) cs32[i] = float(cs[i]);
+  __syncthreads();
+  const bool use = *flag != 0.0;
+  __syncthreads();
+  return use;
+}
+
 // Full reorthogonalisation of w against Q_{ncol} (rows [j0, j1) of this CTA):
 // one classical Gram-Schmidt pass, and a second one when always2 or when the
 // first left less than half of ||w||^2 (the DGKS criterion; every CTA reads
 // the same partials in the same order, so all take the same branch).  ww0 is
 // this thread's share of ||w||^2 before the first pass.  Returns ||w||^2
 // after the last pass to every thread.
+// The correction of each pass is formed in FP32 when pz_use32 allows it.
 template <int NT>
 __device__ __forceinline__ bool pz_cgs(const PzOp<double, double> &O, const PzLz &L, int ncol, int j0, int j1,
-                                       unsigned &ep, int &slot, double *red, double *bc, double *cs, bool always2,
-                                       double ww0, double &ww_out, int &npass2) {
+                                       unsigned &ep, int &slot, double *red, double *bc, double *cs, float *cs32,
+                                       bool always2, double ww0, double &ww_out, LzCount &cnt) {
   double *pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
   __syncthreads();
@@ -574,7 +625,17 @@ __device__ __forceinline__ bool pz_cgs(const PzOp<double, double> &O, const PzLz
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT, double>(pt, O.pstride, ncol + 1, nullptr, nullptr, cs, red);
   const double w0 = cs[ncol];
-  double ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  auto update = [&](double wbefore) {
+    cnt.q64 += ncol;
+    if (pz_use32<NT>(cs, ncol, wbefore, cs32, cs + ncol + 1)) {
+      cnt.nfp32 += 1;
+      cnt.q32 += ncol;
+      return pz_gemvN32<NT>(L.Q32, L.ld, ncol, cs32, L.w, j0, j1);
+    }
+    cnt.q64 += ncol;
+    return pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  };
+  double ww = update(w0);
   pt = pz_buf(O, slot++);
   pz_put<NT>(ww, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
@@ -583,12 +644,13 @@ __device__ __forceinline__ bool pz_cgs(const PzOp<double, double> &O, const PzLz
     ww_out = ww;
     return true;
   }
-  npass2 += 1;
+  cnt.npass2 += 1;
+  const double w1 = ww;
   pt = pz_buf(O, slot++);
   pz_gemvT<NT>(L.Q, L.ld, ncol, L.w, j0, j1, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
   pz_get_cols<NT, double>(pt, O.pstride, ncol, nullptr, nullptr, cs, red);
-  ww = pz_gemvN<NT>(L.Q, L.ld, ncol, cs, L.w, j0, j1);
+  ww = update(w1);
   pt = pz_buf(O, slot++);
   pz_put<NT>(ww, pt, O.pstride, red);
   if (!pz_sync(O.gs, ep)) return false;
@@ -601,23 +663,29 @@ __device__ __forceinline__ bool pz_cgs(const PzOp<double, double> &O, const PzLz
 // qcur and Q column j) until m_max steps, a NaN, or the convergence test of
 // eq. converge every `check` steps (sums of the k largest eigenvalues of T_m
 // and T_{m-1}); breakdown restarts as the level-by-level path does them.
-// Shared memory: NT + 32 + (m_max + 2) + 2 m_max doubles.
+// Shared memory: NT + 32 + (m_max + 2) + 2 m_max doubles and m_max + 2 floats.
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, PzLz L) {
   extern __shared__ double pz_sm[];
   double *red = pz_sm, *bc = pz_sm + NT;
   LzState S0 = *L.st;
   double *cs = pz_sm + NT + 32, *ea = cs + S0.mmax + 2, *eb2 = ea + S0.mmax;
+  float *cs32 = reinterpret_cast<float *>(eb2 + S0.mmax);
   unsigned ep = 0;
   int slot = 0;
   const int n = O.n, m = O.m, s = O.s, k = L.k;
-  int j = S0.j, restarts = S0.restarts, conv_m = S0.conv_m, nan_step = S0.nan_step, npass2 = S0.npass2;
+  int j = S0.j, restarts = S0.restarts, conv_m = S0.conv_m, nan_step = S0.nan_step;
+  LzCount cnt{S0.npass2, S0.nfp32, S0.qcols64, S0.qcols32};
   bool stop = S0.stop != 0;
   double scale = S0.scale;
   const int mmax = S0.mmax;
   int i0, i1, j0, j1;
   pz_range(n, i0, i1);
   pz_range(s, j0, j1);
+  // the FP32 copy of the basis so far, this CTA's rows (its only reader)
+  for (int c = 0; c <= j; c++)
+    for (int r = j0 + threadIdx.x; r < j1; r += NT) L.Q32[(long long)c * L.ld + r] = float(L.Q[(long long)c * L.ld + r]);
+  __syncthreads();
   double bprev = j > 0 ? L.be[j - 1] : 0.0;
   double *v = L.v, *z = L.z;
   // v = E q (eq. EF) on this CTA's rows, q = src, or src * rdiv when rdiv != 0
@@ -683,7 +751,7 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
     }
     __syncthreads();
     double ww = 0;
-    if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, L.reorth2 != 0, ww0, ww, npass2)) return;
+    if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, cs32, L.reorth2 != 0, ww0, ww, cnt)) return;
     const double beta = sqrt(ww);
     if (blockIdx.x == 0 && threadIdx.x == 0) L.be[j] = beta;
     if (!(alpha == alpha) || isinf(alpha) || !(beta == beta) || isinf(beta)) {
@@ -701,6 +769,7 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
       for (int r = j0 + threadIdx.x; r < j1; r += NT) {
         const double q1 = L.w[r] * rdiv;
         L.Q[(long long)(j + 1) * L.ld + r] = q1;
+        L.Q32[(long long)(j + 1) * L.ld + r] = float(q1);
         L.qprev[r] = L.qcur[r];
         L.qcur[r] = q1;
       }
@@ -713,13 +782,18 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
         L.w[r] = d_sm64_pm1(S0.seed + (unsigned long long)restarts, (unsigned long long)ro(L.rank + r));
       __syncthreads();
       double nn = 0;
-      int unused = 0;
-      if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, true, 0.0, nn, unused)) return;
+      // a restart vector's passes are counted in bytes, not as second passes
+      LzCount rc{0, 0, 0.0, 0.0};
+      if (!pz_cgs<NT>(O, L, j + 1, j0, j1, ep, slot, red, bc, cs, cs32, true, 0.0, nn, rc)) return;
+      cnt.nfp32 += rc.nfp32;
+      cnt.q64 += rc.q64;
+      cnt.q32 += rc.q32;
       const double nrm = sqrt(nn);
       rdiv = 1.0 / nrm;
       for (int r = j0 + threadIdx.x; r < j1; r += NT) {
         const double q1 = L.w[r] * rdiv;
         L.Q[(long long)(j + 1) * L.ld + r] = q1;
+        L.Q32[(long long)(j + 1) * L.ld + r] = float(q1);
         L.qprev[r] = L.qcur[r];
         L.qcur[r] = q1;
       }
@@ -762,7 +836,8 @@ __global__ void __launch_bounds__(NT, 1) k_lz_persist(PzOp<double, double> O, Pz
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     LzState *st = L.st;
     st->j = j; st->stop = 1; st->no_break = 1; st->restarts = restarts; st->conv_m = conv_m;
-    st->nan_step = nan_step; st->scale = scale; st->npass2 = npass2;
+    st->nan_step = nan_step; st->scale = scale; st->npass2 = cnt.npass2; st->nfp32 = cnt.nfp32;
+    st->qcols64 = cnt.q64; st->qcols32 = cnt.q32;
   }
 }
 

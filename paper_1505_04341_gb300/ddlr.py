@@ -56,7 +56,7 @@ class ddlr_info(ctypes.Structure):
                 ("batch_block_elem", ctypes.c_int), ("plan_ms", ctypes.c_double),
                 ("persistent", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("cheb_lanczos_steps", ctypes.c_int),
-                ("reorth_passes", ctypes.c_int)]
+                ("reorth_passes", ctypes.c_int), ("reorth_fp32", ctypes.c_int)]
 
 
 class ddlr_solve_info(ctypes.Structure):
@@ -75,7 +75,8 @@ EXPORTS = ["ddlr_options_default", "ddlr_setup", "ddlr_refactor", "ddlr_apply",
            "ddlr_a0_solve", "ddlr_a0_solve_noalloc", "ddlr_pcg", "ddlr_gmres", "ddlr_increase_rank", "ddlr_get_info", "ddlr_get_ritz",
            "ddlr_get_factor_coo", "ddlr_get_lowrank", "ddlr_set_lowrank", "ddlr_set_cheb_bounds",
            "ddlr_set_timing", "ddlr_get_counters", "ddlr_reset_counters",
-           "ddlr_get_traffic", "ddlr_set_stream", "ddlr_set_wait_limit", "ddlr_last_error",
+           "ddlr_get_traffic", "ddlr_set_stream", "ddlr_set_wait_limit", "ddlr_selftest_conversions",
+           "ddlr_last_error",
            "ddlr_destroy", "ddlr_server_options_default", "ddlr_server_create",
            "ddlr_server_add_model", "ddlr_server_submit", "ddlr_server_wait",
            "ddlr_server_stats", "ddlr_server_last_error", "ddlr_server_destroy"]
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         "ddlr_get_traffic": ([P, P, P, P, I], I),
         "ddlr_set_stream": ([P, P], I),
         "ddlr_set_wait_limit": ([P, D], I),
+        "ddlr_selftest_conversions": ([P, LL, I, ctypes.POINTER(LL)], I),
         "ddlr_last_error": ([P], ctypes.c_char_p),
         "ddlr_destroy": ([P], I),
         "ddlr_server_options_default": ([ctypes.POINTER(ddlr_server_options)], I),
@@ -166,6 +168,17 @@ def _vec_ptr(v):
     if not v.is_contiguous():
         raise TypeError("contiguous tensor required")
     return ctypes.c_void_p(v.data_ptr()), v.shape[0], 1
+
+
+def selftest_conversions(values, direction: int) -> int:
+    """Mismatches of the library's bit-pattern binary64 <-> binary32
+    conversions against the device's (values: a CUDA float64 tensor; direction
+    0 narrows, 1 widens the low 32 bits read as binary32)."""
+    lib = load()
+    ptr, n, _ = _vec_ptr(values)
+    bad = ctypes.c_longlong(0)
+    _check(lib, None, lib.ddlr_selftest_conversions(ptr, n, int(direction), ctypes.byref(bad)))
+    return bad.value
 
 
 def _check(lib, h, st):

@@ -48,7 +48,7 @@ def main(argv=None):
     import torch
 
     import workloads as W
-    from paper_1505_04341_gb300 import DDLR, build
+    from paper_1505_04341_gb300 import DDLR, DdlrError, build
 
     build()
     w = W.workload(args.workload)
@@ -74,7 +74,11 @@ def main(argv=None):
         elif args.op == "setup":
             h.refactor()
         else:
-            h.pcg(b, y, tol=1e-8, maxit=args.maxit)
+            try:
+                h.pcg(b, y, tol=1e-8, maxit=args.maxit)
+            except DdlrError as e:      # a capped iteration count profiles the same kernels
+                if e.status != "NOCONV":
+                    raise
 
     once()
     torch.cuda.synchronize()

@@ -208,6 +208,12 @@ def test_reorthogonalisation_passes(reorth, variant, persist, monkeypatch):
     np.testing.assert_allclose(h.ritz()[:9], orc.ritz[:9], rtol=1e-8)
     assert inf["reorth_passes"] == orc.reorth_passes
     assert inf["reorth_passes"] == (2 if reorth else 1) * orc.msteps
+    # the persistent kernel forms the corrections in FP32 where their error
+    # bound is below FP64 rounding of w; the per-phase path keeps FP64
+    if persist == "1":
+        assert 0 < inf["reorth_fp32"] <= inf["reorth_passes"]
+    else:
+        assert inf["reorth_fp32"] == 0
     if variant == 1:
         U = h.lowrank()[0]
         np.testing.assert_allclose(U.T @ U, np.eye(8), atol=1e-10)
