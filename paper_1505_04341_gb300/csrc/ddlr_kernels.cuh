@@ -23,6 +23,18 @@ namespace ddlr {
 // cooperative persistent kernels leave them out: their grid holds every SM.)
 #define DDLR_PDL_ENTRY() asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory")
 
+// Loads of data the persistent kernels stream once per step (the Lanczos
+// basis Q in the Gram-Schmidt passes, the factor entries and level
+// descriptors of the A0 solves), with the evict-first cache policy, so that
+// the vectors they gather keep their place in L2 while the 0.8 GB basis
+// streams through (128^3 setup 54.0 -> 52.7 ms).  The per-phase kernels keep
+// plain loads: there the hint measured no faster, and slower for the FP32
+// sweeps, whose factor is reused from L2 by the apply's second solve.
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) {
+  return __ldcs(p);
+}
+
 constexpr int kRedGrid = 304;   // CTAs of every two-stage reduction (2 x 152 SMs)
 constexpr int kThreads = 256;
 

@@ -218,19 +218,19 @@ __device__ __forceinline__ void pz_level(const PzOp<T, TU> &O, int L, int mode, 
                                          T *z, const double *racc, const double *zsc, double &acc, T *z2) {
   const int c0 = O.lvl_ptr[L], cnt = O.lvl_ptr[L + 1] - c0;
   for (int v = blockIdx.x * NT + threadIdx.x; v < cnt; v += gridDim.x * NT) {
-    const int4 d = ro(O.desc + c0 + v);
+    const int4 d = ld_stream(O.desc + c0 + v);
     const int r = d.x;
     T zr;
     const T dr = ro(O.dinv + r);
     if (mode == 1) {
       const int off = d.z, w = int(unsigned(d.w) >> 16);
       T t = z[r];
-      for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.u_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ld_stream(O.uval + off + kk * 32) * z[ld_stream(O.u_col + off + kk * 32)];
       zr = t * dr;
     } else {
       const int off = d.y, w = int(unsigned(d.w) & 0xffffu);
       T t = pz_in<T>(x, xsc, r);
-      for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.l_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ld_stream(O.lval + off + kk * 32) * z[ld_stream(O.l_col + off + kk * 32)];
       zr = t * dr;
       if (mode == 2) zr = zr * dr;
     }
@@ -524,7 +524,7 @@ __device__ __forceinline__ void pz_gemvT(const double *Q, long long ld, int ncol
     for (int j = wi; j < ncol; j += NW) {
       const double *q = Q + (long long)j * ld;
       double acc = 0;
-      for (int r = r0 + l; r < r1; r += 32) acc += q[r] * w[r];
+      for (int r = r0 + l; r < r1; r += 32) acc += ld_stream(q + r) * w[r];
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (l == 0) pt[(size_t)blockIdx.x * pstride + j] = acc;
     }
@@ -536,7 +536,7 @@ __device__ __forceinline__ void pz_gemvT(const double *Q, long long ld, int ncol
     const int a = r0 + sg * len, b = min(r1, a + len);
     const double *q = Q + (long long)j * ld;
     double acc = 0;
-    for (int r = a + l; r < b; r += 32) acc += q[r] * w[r];
+    for (int r = a + l; r < b; r += 32) acc += ld_stream(q + r) * w[r];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (l == 0) red[wi] = acc;
   }
@@ -556,7 +556,7 @@ __device__ __forceinline__ double pz_gemvN(const double *Q, long long ld, int nc
   double ww = 0;
   for (int r = r0 + threadIdx.x; r < r1; r += NT) {
     double acc = 0;
-    for (int j = 0; j < ncol; j++) acc += Q[(long long)j * ld + r] * cs[j];
+    for (int j = 0; j < ncol; j++) acc += ld_stream(Q + (long long)j * ld + r) * cs[j];
     const double v = w[r] - acc;
     w[r] = v;
     ww += v * v;
@@ -573,7 +573,7 @@ __device__ __forceinline__ double pz_gemvN32(const float *Q, long long ld, int n
   for (int r = r0 + threadIdx.x; r < r1; r += NT) {
     float acc = 0.f;
 #pragma unroll 8
-    for (int j = 0; j < ncol; j++) acc = fmaf(Q[(long long)j * ld + r], cs[j], acc);
+    for (int j = 0; j < ncol; j++) acc = fmaf(ld_stream(Q + (long long)j * ld + r), cs[j], acc);
     const double v = w[r] - double(acc);
     w[r] = v;
     ww += v * v;
