@@ -1427,6 +1427,9 @@ k_dot2_beta(long long n, const double *r, const double *z, const double *zo, dou
   DDLR_PDL_ENTRY();
   if (st->done) return;
   __shared__ double sm[NT / 32];
+  // zo == z (plain CG): r.zold is not needed, and neither its loads nor its
+  // FP64 products are spent
+  const bool two = zo != z;
   double a1 = 0, a2 = 0;
   const long long stp = (long long)gridDim.x * NT;
   for (long long i0 = (long long)blockIdx.x * NT + threadIdx.x; i0 < n; i0 += kStreamUnr * stp) {
@@ -1436,20 +1439,20 @@ k_dot2_beta(long long n, const double *r, const double *z, const double *zo, dou
       const long long i = i0 + u * stp;
       rv[u] = i < n ? r[i] : 0.0;
       zv[u] = i < n ? z[i] : 0.0;
-      ov[u] = i < n ? zo[i] : 0.0;
+      ov[u] = two && i < n ? zo[i] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < kStreamUnr; u++) {
-      a1 += rv[u] * zv[u];
-      a2 += rv[u] * ov[u];
-    }
+    for (int u = 0; u < kStreamUnr; u++) a1 += rv[u] * zv[u];
+    if (two)
+#pragma unroll
+      for (int u = 0; u < kStreamUnr; u++) a2 += rv[u] * ov[u];
   }
   a1 = block_sum<double, NT>(a1, sm);
-  a2 = block_sum<double, NT>(a2, sm);
+  if (two) a2 = block_sum<double, NT>(a2, sm);
   if (threadIdx.x == 0) { partials[blockIdx.x] = a1; partials[gridDim.x + blockIdx.x] = a2; }
   if (!pcg_last_cta(done)) return;
   const double rzn = pcg_sum_partials<NT>(partials, gridDim.x, sm);
-  const double rzo = pcg_sum_partials<NT>(partials + gridDim.x, gridDim.x, sm);
+  const double rzo = two ? pcg_sum_partials<NT>(partials + gridDim.x, gridDim.x, sm) : rzn;
   if (threadIdx.x == 0) {
     *done = 0u;
     double beta = st->flexible ? (rzn - rzo) / st->rz : rzn / st->rz;
