@@ -247,20 +247,6 @@ struct ddlr_ctx {
   // accounting
   long long launches = 0;
   bool timing = false;
-  // launches carry the dependent-launch attribute (DDLR_NO_PDL=1: plain launches)
-  // (not while a graph is captured: inside the per-iteration graphs the
-  // attribute measured slower, 128^3 PCG 68.3 -> 71.1 ms, while direct
-  // launches gain, 128^3 apply 0.259 -> 0.241 ms)
-  bool pdl = [] {
-    const char *e = getenv("DDLR_NO_PDL");
-    return !(e && e[0] == '1');
-  }();
-  bool capturing = false;
-  struct Capture {   // marks a graph capture on this handle for its scope
-    bool &f;
-    explicit Capture(bool &f_) : f(f_) { f = true; }
-    ~Capture() { f = false; }
-  };
   struct Rec { int fam; cudaEvent_t a, b; };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> evpool;
@@ -358,34 +344,10 @@ struct ddlr_ctx {
   };
 };
 
-// Kernel launch with the handle's family accounting.  With ctx->pdl the
-// launch carries the programmatic-stream-serialisation attribute (see
-// DDLR_PDL_ENTRY): the kernel may be scheduled while its predecessor in the
-// stream finishes, and waits for it on entry.
-template <typename... KArgs, typename... Args>
-void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-              Args &&...args) {
-  if (!pdl) {
-    kern<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
-    return;
-  }
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 #define KL(ctx, name, strm, kern, grid, block, smem, ...)                      \
   do {                                                                          \
     ddlr_ctx::Scope _sc((ctx), (name), (strm));                                 \
-    launch_k((ctx)->pdl && !(ctx)->capturing, kern, dim3(grid), dim3(block), size_t(smem), (strm), __VA_ARGS__); \
+    kern<<<(grid), (block), (smem), (strm)>>>(__VA_ARGS__);                     \
   } while (0)
 
 namespace {
@@ -1087,7 +1049,6 @@ ddlr_status run_lanczos(ddlr_ctx *c, bool resume = false) {
       if (!W.exec) {
         const long long l0 = c->launches;
         const std::vector<long long> f0 = c->fam_cnt;
-        ddlr_ctx::Capture cap_(c->capturing);
         ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
         lanczos_step(c, L);
         cudaGraph_t g = nullptr;
@@ -2122,7 +2083,6 @@ void pcg_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit,
       if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
       const long long l0 = c->launches;
       const std::vector<long long> f0 = c->fam_cnt;
-      ddlr_ctx::Capture cap_(c->capturing);
       ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
       pcg_iteration(c, b, x, flexible);
       cudaGraph_t g = nullptr;
@@ -2651,7 +2611,6 @@ void mr_graph(ddlr_ctx *c, int R, int flexible) {
   if (GR.exec) { cudaGraphExecDestroy(GR.exec); GR.exec = nullptr; }
   const long long l0 = c->launches;
   const std::vector<long long> f0 = c->fam_cnt;
-  ddlr_ctx::Capture cap_(c->capturing);
   ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
   pcg_mr_iteration(c, R, flexible);
   cudaGraph_t g = nullptr;

@@ -47,7 +47,6 @@ template <typename T>
 __global__ void k_sptrsv_chunks_mr(SolveLayout S, const int4 *chunks, int mode,
                                    const T *lval, const T *uval, const T *dinv,
                                    const T *X, T *Z, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int4 ch = chunks[blockIdx.x];
   const int lvl = ch.x, r0 = S.lvl_row0[lvl], s0 = S.lvl_slice0[lvl];
@@ -90,7 +89,6 @@ template <typename T>
 __global__ void k_sptrsv_desc_mr(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
                                  const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
                                  const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   constexpr int RR = kMrRowsPerThread;
   const int per = blockDim.x / R;
@@ -184,7 +182,6 @@ template <typename T>
 __global__ void k_sptrsv_desc_mr_v(const int4 *desc, int count, int mode, const int *l_col, const int *u_col,
                                    const T *lval, const T *uval, const T *dinv, const T *X, T *Z, int R,
                                    const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -279,7 +276,6 @@ template <typename T>
 __global__ void k_et_mr(int s, int m, const int *eht_rp, const int *eht_ci,
                         const T *eht_val, T ia, T a, const T *Z, T *Y, int R,
                         const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long j = row_of(idx, R);
@@ -295,7 +291,6 @@ template <typename T>
 __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
                                 const T *eh_val, T ia, const T *W, const T *X, T *RHS,
                                 int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long r = row_of(idx, R);
@@ -312,7 +307,6 @@ __global__ void k_e_interior_mr(int m, const int *eh_rp, const int *eh_ci,
 template <typename T>
 __global__ void k_et_mr_v(int s, int m, const int *eht_rp, const int *eht_ci, const T *eht_val, T ia, T a,
                           const T *Z, T *Y, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -341,7 +335,6 @@ __global__ void k_et_mr_v(int s, int m, const int *eht_rp, const int *eht_ci, co
 template <typename T>
 __global__ void k_e_interior_mr_v(int m, const int *eh_rp, const int *eh_ci, const T *eh_val, T ia, const T *W,
                                   const T *X, T *RHS, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   using VT = Vec16<T>;
   using V = typename VT::V;
@@ -373,7 +366,6 @@ template <typename T, typename TU>
 __global__ void __launch_bounds__(256)
 k_utx_mr_partial(long long nrows, int k, const TU *U, const T *Y, int R, T *partials,
                  const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T us[32 * 64];
   __shared__ T ys[32 * kMaxR];
@@ -411,7 +403,6 @@ k_utx_mr_partial(long long nrows, int k, const TU *U, const T *Y, int R, T *part
 template <typename T>
 __global__ void k_reduce_mr(int G, int k, int R, const T *partials, const T *coef,
                             const T *H, T *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T tmp[1024];
   const int no = k * R;
@@ -438,7 +429,6 @@ template <typename T, typename TU>
 __global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const T *Y,
                            const T *inv1mt, T a, const T *X, T *W, T *RHS, int R,
                            const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T ts[1024];
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = Tm[o];
@@ -459,7 +449,6 @@ __global__ void k_w_rhs_mr(int s, int m, int k, const TU *U, const T *Tm, const 
 template <typename T, typename TU>
 __global__ void k_u_add_mr(long long nrows, int k, const TU *U, const T *HT, T *Uo, int R,
                            const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T ts[1024];
   for (int o = threadIdx.x; o < k * R; o += blockDim.x) ts[o] = HT[o];
@@ -521,7 +510,6 @@ constexpr int kTcRows = 32, kTcUS = 68, kTcYS = 72;   // smem strides: conflict-
 template <typename TU>
 __global__ void __launch_bounds__(256)
 k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *partials, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float us[kTcRows * kTcUS];
   __shared__ float ys[kTcRows * kTcYS];
@@ -595,7 +583,6 @@ k_utx_mr_tc(long long nrows, int k, const TU *U, const float *Y, int R, float *p
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_reduce_cols_mr(int G, int no, int R, const T *partials, const T *coef, T *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T sm[8][32];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -660,7 +647,6 @@ template <typename TU>
 __global__ void __launch_bounds__(256)
 k_w_rhs_mr_tc(int s, int m, int k, const TU *U, const float *Tm, const float *Y, const float *inv1mt, float a,
               const float *X, float *W, float *RHS, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float ts[64 * 72];
   const int TS = tc_stage_small(Tm, k, R, ts);
@@ -693,7 +679,6 @@ k_w_rhs_mr_tc(int s, int m, int k, const TU *U, const float *Tm, const float *Y,
 template <typename TU>
 __global__ void __launch_bounds__(256)
 k_u_add_mr_tc(long long nrows, int k, const TU *U, const float *HT, float *Uo, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ float ts[64 * 72];
   const int TS = tc_stage_small(HT, k, R, ts);
@@ -721,7 +706,6 @@ k_u_add_mr_tc(long long nrows, int k, const TU *U, const float *HT, float *Uo, i
 template <typename T>
 __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
                           const T *val, const T *P, T *Q, int R, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long r = row_of(idx, R);
@@ -742,7 +726,6 @@ __global__ void k_spmv_mr(int n, const int *soff, const int *sw, const int *col,
 __global__ void __launch_bounds__(256)
 k_dot_mr_partial(long long n, int R, const double *A, const double *B,
                  const double *C, double *partials, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ double red[8][2 * kMaxR];
   const int w = threadIdx.x >> 5, q = threadIdx.x & 31;
@@ -812,7 +795,6 @@ __global__ void k_spmv_pq_mr(int n, const int *__restrict__ soff, const int *__r
                              const int *__restrict__ col, const double *__restrict__ val,
                              const double *__restrict__ P, double *__restrict__ Q, int R, double *bpart,
                              const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ double red[kFbMaxRed];
   const int gt = kFbLanes * R, gi = threadIdx.x / gt, tt = threadIdx.x % gt;
@@ -847,7 +829,6 @@ __global__ void k_spmv_pq_mr(int n, const int *__restrict__ soff, const int *__r
 // partials of Rr.Rr (all columns)
 __global__ void k_update_rr_mr(long long n, const PcgStateMR *st, const double *P, const double *Q, double *X,
                                double *Rr, double *bpart) {
-  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   __shared__ double red[kFbMaxRed];
   const int R = st->R;
@@ -886,7 +867,6 @@ __global__ void k_update_rr_mr(long long n, const PcgStateMR *st, const double *
 // order, of bpart[block][q]; grid kRedGrid, R threads
 __global__ void k_fused_partials_reduce(int nblocks, int R, const double *bpart, double *partials,
                                         const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int q = threadIdx.x;
   if (q >= R) return;
@@ -916,7 +896,6 @@ __device__ __forceinline__ void col_sums(const double *partials, int G, int R, i
 
 __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int R,
                              double tol, int maxit, int flexible) {
-  DDLR_PDL_ENTRY();
   const int q = threadIdx.x;
   __shared__ double sm[kMaxR];
   col_sums(partials, G, R, R, sm);
@@ -940,7 +919,6 @@ __global__ void k_pcgmr_init(PcgStateMR *st, const double *partials, int G, int 
 }
 
 __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[kMaxR];
@@ -953,7 +931,6 @@ __global__ void k_pcgmr_rz0(PcgStateMR *st, const double *partials, int G) {
 }
 
 __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[kMaxR];
@@ -972,7 +949,6 @@ __global__ void k_pcgmr_alpha(PcgStateMR *st, const double *partials, int G) {
 
 
 __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ int anyc;
@@ -998,7 +974,6 @@ __global__ void k_pcgmr_rr(PcgStateMR *st, const double *partials, int G) {
 __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, const int *sw,
                                  const int *col, const double *val, const double *B,
                                  const double *X, double *Tt) {
-  DDLR_PDL_ENTRY();
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * R;
@@ -1015,7 +990,6 @@ __global__ void k_pcgmr_true_res(int n, const PcgStateMR *st, const int *soff, c
 }
 
 __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   const int q = threadIdx.x, R = st->R;
   if (q == 0) st->no_check = 1;   // the check of this iteration is consumed here
   if (st->all_done || !st->any_check) return;
@@ -1035,7 +1009,6 @@ __global__ void k_pcgmr_true_dec(PcgStateMR *st, const double *partials, int G) 
 
 // (a restart is only ever set by a true-residual check of this iteration)
 __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *Tt, double *Rr) {
-  DDLR_PDL_ENTRY();
   if (st->all_done || !st->any_check) return;
   const int R = st->R;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n * R;
@@ -1046,7 +1019,6 @@ __global__ void k_pcgmr_copy_r(long long n, const PcgStateMR *st, const double *
 }
 
 __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->all_done) return;
   const int q = threadIdx.x, R = st->R;
   __shared__ double sm[2 * kMaxR];
@@ -1073,7 +1045,6 @@ __global__ void k_pcgmr_beta(PcgStateMR *st, const double *partials, int G) {
 // P = Z + beta P (and Zold = Z) for the columns still running
 __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, double *P,
                           double *Zold) {
-  DDLR_PDL_ENTRY();
   const int R = st->R;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
@@ -1096,20 +1067,17 @@ __global__ void k_pcgmr_p(long long n, const PcgStateMR *st, const double *Z, do
 
 // column q of a row-major n x R block <- a vector in original order
 __global__ void k_col_in(int n, int R, int q, const int *perm, const double *in, double *out) {
-  DDLR_PDL_ENTRY();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[(long long)g * R + q] = in[perm[g]];
 }
 // a vector in original order <- column q of a row-major n x R block
 __global__ void k_col_out(int n, int R, int q, const int *perm, const double *in, double *out) {
-  DDLR_PDL_ENTRY();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[perm[g]] = in[(long long)g * R + q];
 }
 // admitted columns (mask[q] != 0): X = 0, Rr = B, P = 0
 __global__ void k_slot_reset(long long n, int R, const int *mask, const double *B, double *X, double *Rr,
                              double *P) {
-  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R) return;
   const int q = col_of(idx, row_of(idx, R), R);
@@ -1121,7 +1089,6 @@ __global__ void k_slot_reset(long long n, int R, const int *mask, const double *
 // the per-column state of the admitted columns (partials: column sums of B.B)
 __global__ void k_slot_init(PcgStateMR *st, const double *partials, int G, const int *mask, int R, double tol,
                             int maxit, int flexible) {
-  DDLR_PDL_ENTRY();
   const int q = threadIdx.x;
   __shared__ double sm[kMaxR];
   col_sums(partials, G, R, R, sm);
@@ -1150,7 +1117,6 @@ __global__ void k_slot_init(PcgStateMR *st, const double *partials, int G, const
 // a block of R0 columns laid out again as R1 columns: column q of the new
 // block is column map[q] of the old one (map[q] < 0: a new, zero column)
 __global__ void k_relayout(long long n, int R0, int R1, const int *map, const double *in, double *out) {
-  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * R1) return;
   const long long r = row_of(idx, R1);
@@ -1161,7 +1127,6 @@ __global__ void k_relayout(long long n, int R0, int R1, const int *map, const do
 
 // Tt = B - Q (all columns)
 __global__ void k_sub_mr(long long cnt, const double *B, const double *Q, double *Tt) {
-  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < cnt) Tt[idx] = B[idx] - Q[idx];
 }
@@ -1170,7 +1135,6 @@ __global__ void k_sub_mr(long long cnt, const double *B, const double *Q, double
 // the batch layout (row-major, device order); optional row scaling
 __global__ void k_batch_in(int n, int R, const int *perm, const double *in, long long ld,
                            double *out) {
-  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
   const long long g = row_of(idx, R);
@@ -1179,7 +1143,6 @@ __global__ void k_batch_in(int n, int R, const int *perm, const double *in, long
 }
 __global__ void k_batch_out(int n, int R, const int *perm, const double *in, double *out,
                             long long ld) {
-  DDLR_PDL_ENTRY();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n * R) return;
   const long long g = row_of(idx, R);
@@ -1226,7 +1189,6 @@ __device__ __forceinline__ void from_f64(double x, double &o) { o = x; }
 // binary32 -> stored widened; dir 1: the binary32 reading of the low word
 // widened), compared with the hardware conversions by the caller
 __global__ void k_cvt_check(long long n, const double *in, double *out, int dir) {
-  DDLR_PDL_ENTRY();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (dir == 0) {
@@ -1246,7 +1208,6 @@ __global__ void k_cvt_check(long long n, const double *in, double *out, int dir)
 // the next by increment); launch with ceil(n R / 4) threads.
 template <typename TO, typename TI>
 __global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *in, TO *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long nR = n * R;
   const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -1270,7 +1231,6 @@ __global__ void k_scale_cast_mr(long long n, int R, const double *d, const TI *i
 
 __global__ void k_scale_rows_mr(long long n, int R, const double *d, const double *in,
                                 double *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < n * R) out[idx] = in[idx] * d[row_of(idx, R)];

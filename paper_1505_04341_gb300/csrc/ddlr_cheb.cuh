@@ -52,7 +52,6 @@ __device__ __forceinline__ void cheb_table(double lo, double hi, int t, double *
 
 // coefficients from a given interval
 __global__ void k_cheb_coef(double lo, double hi, int t, double *tab, float *tab32) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x == 0 && blockIdx.x == 0) cheb_table(lo, hi, t, tab, tab32);
 }
 
@@ -62,7 +61,6 @@ __global__ void k_cheb_coef(double lo, double hi, int t, double *tab, float *tab
 // zero or below falls back to the smallest Ritz value
 __global__ void k_cheb_bounds(int m, const double *vals, const double *Y, const double *be, int t,
                               double *tab, float *tab32) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double bm = be[m - 1];
   const double hi = vals[0] + bm * fabs(Y[m - 1]);
@@ -73,7 +71,6 @@ __global__ void k_cheb_bounds(int m, const double *vals, const double *Y, const 
 
 // a^2 on the diagonal of C_a
 __global__ void k_cc_add_diag(int s, const int *diag, double a2, double *val) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < s) val[diag[i]] += a2;
 }
@@ -81,7 +78,6 @@ __global__ void k_cc_add_diag(int s, const int *diag, double a2, double *val) {
 // start vector of the estimate: SplitMix64 stream seed + 2^32, drawn in the
 // order of rank[] (ascending original index of the interface nodes)
 __global__ void k_cheb_start(int s, int m, const int *rank, unsigned long long seed, double *r) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < s) r[m + i] = d_sm64_pm1(seed + 0x100000000ULL, (unsigned long long)rank[i]);
 }
@@ -89,7 +85,6 @@ __global__ void k_cheb_start(int s, int m, const int *rank, unsigned long long s
 // q = z / beta, pv = r / beta (interface rows)
 __global__ void k_cheb_lz_qp(int s, int m, const double *beta, const double *z, const double *r, double *q,
                              double *pv) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s) return;
   const double b = *beta;
@@ -100,7 +95,6 @@ __global__ void k_cheb_lz_qp(int s, int m, const double *beta, const double *z, 
 // w = C_a q - beta_prev pp   (beta_prev == nullptr: first step)
 __global__ void k_cheb_lz_w(int s, int m, const int *rp, const int *ci, const double *val, const double *q,
                             const double *pp, const double *beta_prev, double *w) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s) return;
   double acc = 0;
@@ -111,14 +105,12 @@ __global__ void k_cheb_lz_w(int s, int m, const int *rp, const int *ci, const do
 
 // w -= alpha pv
 __global__ void k_cheb_lz_sub(int s, int m, const double *alpha, const double *pv, double *w) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < s) w[m + i] -= *alpha * pv[m + i];
 }
 
 // *out = sqrt(max(sum of partials, 0)) (fixed order)
 __global__ void k_cheb_reduce_norm(int G, const double *partials, double *out) {
-  DDLR_PDL_ENTRY();
   const double v = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) *out = v > 0.0 ? sqrt(v) : 0.0;
 }
@@ -128,7 +120,6 @@ __global__ void k_cheb_reduce_norm(int G, const double *partials, double *out) {
 template <typename T>
 __global__ void k_cheb_first(int s, int m, int R, const int *rp, const int *ci, const T *cv, const T *tab, int t,
                              const T *y, T *z, T *d, T *xacc, T *r, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * R) return;
@@ -150,7 +141,6 @@ __global__ void k_cheb_first(int s, int m, int R, const int *rp, const int *ci, 
 template <typename T>
 __global__ void k_cheb_step(int s, int m, int R, const int *rp, const int *ci, const T *cv, const T *tab, int t,
                             int j, const T *zt, const T *dold, T *dnew, T *xacc, T *r, T *z, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * R) return;

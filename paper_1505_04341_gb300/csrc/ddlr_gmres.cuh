@@ -16,7 +16,6 @@ namespace ddlr {
 // c[col] = sum_g partials[g][col] (a warp per column, fixed order), and the
 // Hessenberg column hcol[col] = c[col] (first pass) or += c[col]
 __global__ void k_gm_reduce_acc(int G, int ncol, const double *partials, double *c, double *hcol, int first) {
-  DDLR_PDL_ENTRY();
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, l = threadIdx.x & 31;
   if (w >= ncol) return;
   double s = 0;
@@ -30,7 +29,6 @@ __global__ void k_gm_reduce_acc(int G, int ncol, const double *partials, double 
 
 // sqrt of the sum of G dot partials into *o1 and *o2 (a NaN stays a NaN)
 __global__ void k_gm_norm(int G, const double *partials, double *o1, double *o2) {
-  DDLR_PDL_ENTRY();
   const double v = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
     const double r = v >= 0.0 ? sqrt(v) : v;
@@ -41,7 +39,6 @@ __global__ void k_gm_norm(int G, const double *partials, double *o1, double *o2)
 
 // g = (beta, 0, ..., 0), m + 1 entries
 __global__ void k_gm_ginit(int m, const double *beta, double *g) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= m) g[i] = i == 0 ? *beta : 0.0;
 }
@@ -50,7 +47,6 @@ __global__ void k_gm_ginit(int m, const double *beta, double *g) {
 // then the rotation that zeroes h_{j+1,j}; g updated; *res = |g_{j+1}|, the
 // residual norm of the current iterate
 __global__ void k_gm_givens(int j, double *hcol, double *cs, double *sn, double *g, double *res) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = 0; i < j; i++) {
     const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
@@ -69,7 +65,6 @@ __global__ void k_gm_givens(int j, double *hcol, double *cs, double *sn, double 
 
 // R y = g, R the leading j x j upper triangle of H (one thread)
 __global__ void k_gm_backsolve(int j, const double *H, int ld, const double *g, double *y) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = j - 1; i >= 0; i--) {
     double t = g[i];
@@ -80,7 +75,6 @@ __global__ void k_gm_backsolve(int j, const double *H, int ld, const double *g, 
 
 // x += Z y (Z n x j column-major), a thread per row, y in shared memory
 __global__ void k_gm_update(long long n, int j, const double *Z, const double *y, double *x) {
-  DDLR_PDL_ENTRY();
   extern __shared__ double ys[];
   for (int l = threadIdx.x; l < j; l += blockDim.x) ys[l] = y[l];
   __syncthreads();
@@ -93,7 +87,6 @@ __global__ void k_gm_update(long long n, int j, const double *Z, const double *y
 
 // r = b - q
 __global__ void k_gm_resid(long long n, const double *b, const double *q, double *r) {
-  DDLR_PDL_ENTRY();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] = b[i] - q[i];
 }
@@ -103,7 +96,6 @@ __global__ void k_gm_resid(long long n, const double *b, const double *q, double
 // elimination with partial pivoting (one thread; work = k x k).  A pivot of
 // magnitude <= 1e-14 times the largest entry sets *singular.  Hk row-major.
 __global__ void k_hk_finalize_gj(int G, int k, const double *partials, double *work, double *Hk, int *singular) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double *M = work;
   double amax = 0.0;

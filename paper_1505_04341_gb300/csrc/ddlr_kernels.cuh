@@ -13,16 +13,6 @@
 
 namespace ddlr {
 
-// Programmatic dependent launch (sm_90 and later).  Every kernel first lets
-// the next kernel of its stream be scheduled, then waits until its own
-// predecessor has completed and that grid's writes are visible, before it
-// reads or writes anything: the next kernel's CTAs take the SMs this grid's
-// last wave leaves free, and its launch overlaps this grid's tail.  In a
-// kernel launched without the dependent-launch attribute, or after a stream
-// operation other than a kernel, both instructions do nothing.  (The
-// cooperative persistent kernels leave them out: their grid holds every SM.)
-#define DDLR_PDL_ENTRY() asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory")
-
 // Loads of data the persistent kernels stream once per step (the Lanczos
 // basis Q in the Gram-Schmidt passes, the factor entries and level
 // descriptors of the A0 solves), with the evict-first cache policy, so that
@@ -69,21 +59,18 @@ __device__ __forceinline__ T block_sum(T v, T *sm) {
 // =================================================================== setup
 __global__ void k_diag_scale(int n, const int *diag_pos, const double *val,
                              double *dsc) {
-  DDLR_PDL_ENTRY();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dsc[i] = 1.0 / sqrt(val[diag_pos[i]]);
 }
 
 __global__ void k_scale_vals(long long nnz, const int *orow, const int *ocol,
                              const double *val, const double *dsc, double *out) {
-  DDLR_PDL_ENTRY();
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < nnz) out[q] = val[q] * dsc[orow[q]] * dsc[ocol[q]];
 }
 
 template <typename T>
 __global__ void k_gather(long long cnt, const int *src, const double *in, T *out) {
-  DDLR_PDL_ENTRY();
   long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < cnt) { int s = src[q]; out[q] = s >= 0 ? T(in[s]) : T(0); }
 }
@@ -94,7 +81,6 @@ __global__ void k_gather(long long cnt, const int *src, const double *in, T *out
 // column: lx[slot] = l[slot] / L_cc (padding slots hold 0 and stay 0)
 template <typename T>
 __global__ void k_prescale_cols(long long nslot, const int *col, const T *l, const T *dinv, T *lx) {
-  DDLR_PDL_ENTRY();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nslot) lx[i] = l[i] * dinv[col[i]];
 }
@@ -103,7 +89,6 @@ __global__ void k_factor_init(int nf, const int *f_src, const int *f_prp,
                               const int *pa, const int *pb,
                               const unsigned char *cdiag, const double *as,
                               double ia2, double a2, double *fval) {
-  DDLR_PDL_ENTRY();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nf) return;
   double v = f_src[q] >= 0 ? as[f_src[q]] : 0.0;
@@ -123,7 +108,6 @@ __global__ void k_factor_init(int nf, const int *f_src, const int *f_prp,
 // l_ij is formed.  A non-positive pivot sets *err = 1 (BREAKDOWN).
 __global__ void k_ic_level(int cnt, const int *rows, const int *f_rp,
                            const int *f_ci, double *fval, int *err) {
-  DDLR_PDL_ENTRY();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
   const int i = rows[t];
@@ -153,7 +137,6 @@ __global__ void k_solve_layout(int nf, const int *f_row, const int *f_rp,
                                const int *map_l, const int *map_u,
                                const int *row_slot, const double *fval, T *lval,
                                T *uval, T *dinv, T *dinv_s) {
-  DDLR_PDL_ENTRY();
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nf) return;
   const int g = f_row[q];
@@ -198,7 +181,6 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks(SolveLayout S, const T *lval, const T *uval, const T *dinv,
                 const T *x, T *z, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int b = blockIdx.x;
   const int l0 = S.blk_lvl0[b], l1 = S.blk_lvl0[b + 1];
@@ -291,7 +273,6 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_tma(SolveLayout S, const T *lval, const T *uval, const T *dinv_s,
                     const T *x, T *z, const int *gate, TmaCfg cfg, int *err, unsigned long long limit_ns) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ int s_abort;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -452,7 +433,6 @@ __global__ void __launch_bounds__(NT)
 k_sptrsv_blocks_sf(const int *blk_row0, RowSpan rs, const int *l_col, const T *l_val,
                    const int *u_col, const T *u_val, const T *dinv, const T *x, T *z,
                    const int *gate, int *err, unsigned long long limit_ns) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -549,7 +529,6 @@ template <typename T, int R>
 __global__ void __launch_bounds__(kThreads / R)
 k_sptrsv_chunks(SolveLayout S, const int4 *chunks, int mode, const T *lval, const T *uval, const T *dinv,
                 const T *x, T *z, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   constexpr int NT = kThreads / R;
   const int4 ch = chunks[blockIdx.x];
@@ -623,7 +602,6 @@ template <typename T, int R, typename TX = T>
 __global__ void __launch_bounds__(kThreads / R)
 k_sptrsv_desc(const int4 *desc, int count, int mode, const int *l_col, const int *u_col, const T *lval,
               const T *uval, const T *dinv, const TX *x, T *z, const int *gate, double *z64 = nullptr) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   constexpr int NT = kThreads / R;
   const int base = blockIdx.x * kThreads + threadIdx.x;
@@ -652,7 +630,6 @@ template <typename T>
 __global__ void k_e_vec(int m, int s, const int *eh_rp, const int *eh_ci,
                         const T *eh_val, T ia, T a, const T *w, const T *xadd,
                         T *v, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m + s) return;
@@ -672,7 +649,6 @@ template <typename T, typename TX = T>
 __global__ void k_e_interior(int m, const int *eh_rp, const int *eh_ci,
                              const T *eh_val, T ia, const T *w, const TX *xadd,
                              T *v, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m) return;
@@ -686,7 +662,6 @@ template <typename T>
 __global__ void k_et(int s, int m, const int *eht_rp, const int *eht_ci,
                      const T *eht_val, T ia, T a, const T *z, T *y,
                      const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
@@ -702,7 +677,6 @@ template <typename T, typename TU, int NT>
 __global__ void __launch_bounds__(NT)
 k_utx_partial(int nrows, int k, const TU *U, const T *x, T *partials,
               const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T xs[NT];
   __shared__ T red[NT];
@@ -735,7 +709,6 @@ k_utx_partial(int nrows, int k, const TU *U, const T *x, T *partials,
 template <typename T>
 __global__ void k_reduce_cols(int G, int k, const T *partials, const T *coef,
                               const T *H, T *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ unsigned char smraw[];
   T *tmp = reinterpret_cast<T *>(smraw);
@@ -765,7 +738,6 @@ template <typename T, typename TU>
 __global__ void k_w_rhs(int s, int m, int k, const TU *U, const T *t,
                         const T *y, const T *inv1mt, T a, const T *x, T *w,
                         T *rhs, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ unsigned char smraw[];
   T *ts = reinterpret_cast<T *>(smraw);
@@ -785,7 +757,6 @@ __global__ void k_w_rhs(int s, int m, int k, const TU *U, const T *t,
 template <typename T, typename TU>
 __global__ void k_u_add(int nrows, int k, const TU *U, const T *h, T *u,
                         const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ unsigned char smraw[];
   T *hs = reinterpret_cast<T *>(smraw);
@@ -847,7 +818,6 @@ template <typename T, typename TU, int L, int NT, int UNR>
 __global__ void __launch_bounds__(NT, 2)   // two CTAs per SM: the fixed grid of 2 x 152 in one wave
 k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate, unsigned *done = nullptr,
           const T *coef = nullptr, const T *H = nullptr, T *out = nullptr) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   constexpr int E = Unpack16<TU>::E, K = L * E, RW = 32 / L, NW = NT / 32;
   __shared__ T red[NW][K];
@@ -922,8 +892,8 @@ k_utx_vec(long long nrows, const TU *U, const T *x, T *partials, const int *gate
 // thread; the epilogue gets (row, d_r) in lane cg == 0 of each row group:
 // DDLR-1 (rows = s): w_j = t_0 y_j + d_j, rhs_{m+j} = x_{m+j} - a w_j;
 // DDLR-2 (rows = n): u_r += d_r.
-template <typename T, typename TU, int L, int UNR, typename Epi>
-__device__ __forceinline__ void u_rows_dot(long long nrows, const TU *U, const T *t, Epi epi) {
+template <typename T, typename TU, int L, int UNR, typename Pre, typename Epi>
+__device__ __forceinline__ void u_rows_dot(long long nrows, const TU *U, const T *t, Pre pre, Epi epi) {
   constexpr int E = Unpack16<TU>::E, RW = 32 / L;
   const int lane = threadIdx.x & 31;
   const int cg = lane % L, ro = lane / L;
@@ -933,12 +903,15 @@ __device__ __forceinline__ void u_rows_dot(long long nrows, const TU *U, const T
 #pragma unroll
   for (int i = 0; i < E; i++) tv[i] = t[cg * E + i];
   const uint4 *U4 = reinterpret_cast<const uint4 *>(U);
+  using PV = decltype(pre(0LL));
   for (long long r0 = gw * RW; r0 < nrows; r0 += W * RW * UNR) {
     uint4 v[UNR];
+    PV pv[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
       const long long r = r0 + (long long)u * W * RW + ro;
       v[u] = r < nrows ? U4[r * L + cg] : make_uint4(0u, 0u, 0u, 0u);
+      if (cg == 0 && r < nrows) pv[u] = pre(r);
     }
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
@@ -950,7 +923,7 @@ __device__ __forceinline__ void u_rows_dot(long long nrows, const TU *U, const T
 #pragma unroll
       for (int o = 1; o < L; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       const long long r = r0 + (long long)u * W * RW + ro;
-      if (cg == 0 && r < nrows) epi(r, d);
+      if (cg == 0 && r < nrows) epi(r, d, pv[u]);
     }
   }
 }
@@ -992,7 +965,6 @@ __device__ __forceinline__ void u_rows_dot_smem(long long nrows, int k, const do
 __global__ void __launch_bounds__(kRowTile)
 k_w_rhs_smem(int s, int m, int k, const double *U, const double *t, const double *y, const double *inv1mt,
              double a, const double *x, double *w, double *rhs, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ double dsm[];
   const double it = *inv1mt;
@@ -1005,7 +977,6 @@ k_w_rhs_smem(int s, int m, int k, const double *U, const double *t, const double
 
 __global__ void __launch_bounds__(kRowTile)
 k_u_add_smem(long long nrows, int k, const double *U, const double *h, double *u, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   extern __shared__ double dsm[];
   u_rows_dot_smem(nrows, k, U, h, dsm + 64, dsm, [&](long long r, double d) { u[r] += d; });
@@ -1015,8 +986,9 @@ k_u_add_smem(long long nrows, int k, const double *U, const double *h, double *u
 // read as KV = k/2 16-byte loads issued back to back, at most 8 at a time (the
 // warp's loads cover 32 whole rows, so every sector fetched is used), then k
 // FMAs in two chains; t is read from shared memory (broadcast).
-template <int KV, typename Epi>
-__device__ __forceinline__ void u_rows_dot_direct(long long nrows, const double *U, const double *t, Epi epi) {
+template <int KV, typename Pre, typename Epi>
+__device__ __forceinline__ void u_rows_dot_direct(long long nrows, const double *U, const double *t, Pre pre,
+                                                  Epi epi) {
   constexpr int CH = KV < 8 ? KV : 8;
   __shared__ double ts[2 * KV];
   for (int c = threadIdx.x; c < 2 * KV; c += blockDim.x) ts[c] = t[c];
@@ -1024,6 +996,7 @@ __device__ __forceinline__ void u_rows_dot_direct(long long nrows, const double 
   const double2 *U2 = reinterpret_cast<const double2 *>(U);
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
        r += (long long)gridDim.x * blockDim.x) {
+    const auto pv = pre(r);
     double d0 = 0, d1 = 0;
 #pragma unroll 1
     for (int q0 = 0; q0 < KV; q0 += CH) {
@@ -1036,7 +1009,7 @@ __device__ __forceinline__ void u_rows_dot_direct(long long nrows, const double 
         d1 += v[q].y * ts[2 * (q0 + q) + 1];
       }
     }
-    epi(r, d0 + d1);
+    epi(r, d0 + d1, pv);
   }
 }
 
@@ -1044,41 +1017,44 @@ template <int KV>
 __global__ void __launch_bounds__(kThreads, 3) k_w_rhs_direct(int s, int m, const double *U, const double *t, const double *y,
                                const double *inv1mt, double a, const double *x, double *w, double *rhs,
                                const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const double it = *inv1mt;
-  u_rows_dot_direct<KV>(s, U, t, [&](long long j, double d) {
-    const double wj = it * y[j] + d;
-    w[j] = wj;
-    rhs[m + j] = x[m + j] - a * wj;
-  });
+  u_rows_dot_direct<KV>(
+      s, U, t, [&](long long j) { return make_double2(y[j], x[m + j]); },
+      [&](long long j, double d, double2 yx) {
+        const double wj = it * yx.x + d;
+        w[j] = wj;
+        rhs[m + j] = yx.y - a * wj;
+      });
 }
 
 template <int KV>
 __global__ void __launch_bounds__(kThreads, 3) k_u_add_direct(long long nrows, const double *U, const double *h, double *u, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
-  u_rows_dot_direct<KV>(nrows, U, h, [&](long long r, double d) { u[r] += d; });
+  u_rows_dot_direct<KV>(
+      nrows, U, h, [&](long long r) { return u[r]; }, [&](long long r, double d, double ur) { u[r] = ur + d; });
 }
 
 template <typename T, typename TU, int L, int UNR, typename TX = T>
 __global__ void k_w_rhs_vec(int s, int m, const TU *U, const T *t, const T *y, const T *inv1mt, T a,
                             const TX *x, T *w, T *rhs, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const T it = *inv1mt;
-  u_rows_dot<T, TU, L, UNR>(s, U, t, [&](long long j, T d) {
-    const T wj = it * y[j] + d;
-    w[j] = wj;
-    rhs[m + j] = T(x[m + j]) - a * wj;
-  });
+  struct YX { T y, x; };
+  u_rows_dot<T, TU, L, UNR>(
+      s, U, t, [&](long long j) { return YX{y[j], T(x[m + j])}; },
+      [&](long long j, T d, YX yx) {
+        const T wj = it * yx.y + d;
+        w[j] = wj;
+        rhs[m + j] = yx.x - a * wj;
+      });
 }
 
 template <typename T, typename TU, int L, int UNR>
 __global__ void k_u_add_vec(long long nrows, const TU *U, const T *h, T *u, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
-  u_rows_dot<T, TU, L, UNR>(nrows, U, h, [&](long long r, T d) { u[r] += d; });
+  u_rows_dot<T, TU, L, UNR>(
+      nrows, U, h, [&](long long r) { return u[r]; }, [&](long long r, T d, T ur) { u[r] = ur + d; });
 }
 
 // ===================================================== vectors and PCG
@@ -1086,7 +1062,6 @@ __global__ void k_u_add_vec(long long nrows, const TU *U, const T *h, T *u, cons
 template <typename T>
 __global__ void k_spmv(int n, const int *soff, const int *sw, const int *col,
                        const T *val, const T *x, T *y, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -1106,7 +1081,6 @@ constexpr int kStreamUnr = 4;
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_dot_partial(long long n, const T *a, const T *b, T *partials, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T sm[NT / 32];
   T acc = 0;
@@ -1132,7 +1106,6 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_dot2_partial(long long n, const T *a, const T *b, const T *c, T *partials,
                const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   __shared__ T sm[NT / 32];
   T acc = 0, acc2 = 0;
@@ -1157,7 +1130,6 @@ __device__ __forceinline__ double warp_sum_partials(const double *p, int G) {
 
 __global__ void k_reduce_scalar(int G, const double *partials, double *out,
                                 int do_sqrt, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   double s = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) *out = do_sqrt ? sqrt(s) : s;
@@ -1165,7 +1137,6 @@ __global__ void k_reduce_scalar(int G, const double *partials, double *out,
 
 template <typename T, typename S>
 __global__ void k_cast(long long n, const S *in, T *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = T(in[i]);
@@ -1174,14 +1145,12 @@ __global__ void k_cast(long long n, const S *in, T *out, const int *gate) {
 // out = a .* b
 template <typename T>
 __global__ void k_mulv_t(long long n, const T *a, const T *b, T *out, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a[i] * b[i];
 }
 
 __global__ void k_to_bf16(long long n, const double *in, __nv_bfloat16 *out) {
-  DDLR_PDL_ENTRY();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = __float2bfloat16_rn(float(in[i]));
 }
@@ -1189,13 +1158,11 @@ __global__ void k_to_bf16(long long n, const double *in, __nv_bfloat16 *out) {
 // out[g] = in[perm[g]] (original -> device order)
 template <typename T>
 __global__ void k_permute_in(int n, const int *perm, const T *in, T *out) {
-  DDLR_PDL_ENTRY();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = in[perm[g]];
 }
 template <typename T>
 __global__ void k_permute_out(int n, const int *perm, const T *in, T *out) {
-  DDLR_PDL_ENTRY();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[perm[g]] = in[g];
 }
@@ -1204,7 +1171,6 @@ __global__ void k_permute_out(int n, const int *perm, const T *in, T *out) {
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_resid2_partial(long long n, const double *b, const double *q, double *partials) {
-  DDLR_PDL_ENTRY();
   __shared__ double sm[NT / 32];
   double acc = 0;
   for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n;
@@ -1224,7 +1190,6 @@ struct PcgState {
 
 __global__ void k_pcg_init(PcgState *st, const double *partials, int G,
                            double tol, int maxit, int flexible) {
-  DDLR_PDL_ENTRY();
   double bb = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
     st->bb = bb;
@@ -1238,7 +1203,6 @@ __global__ void k_pcg_init(PcgState *st, const double *partials, int G,
 
 // rz = r.z after the first preconditioning
 __global__ void k_pcg_rz0(PcgState *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   double s = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
@@ -1249,7 +1213,6 @@ __global__ void k_pcg_rz0(PcgState *st, const double *partials, int G) {
 
 // alpha = rz / (p.q)
 __global__ void k_pcg_alpha(PcgState *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   double pq = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
@@ -1264,7 +1227,6 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
 k_pcg_update(long long n, PcgState *st, const double *p, const double *q,
              double *x, double *r, double *partials) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   __shared__ double sm[NT / 32];
   const double a = st->alpha;
@@ -1282,7 +1244,6 @@ k_pcg_update(long long n, PcgState *st, const double *p, const double *q,
 
 // recursive residual test; a pass schedules the true-residual check
 __global__ void k_pcg_rr(PcgState *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   double rr = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
@@ -1300,7 +1261,6 @@ __global__ void __launch_bounds__(NT)
 k_pcg_true_res(int n, const PcgState *st, const int *soff, const int *sw,
                const int *col, const double *val, const double *b,
                const double *x, double *t, double *partials) {
-  DDLR_PDL_ENTRY();
   if (st->done || !st->check_true) return;
   __shared__ double sm[NT / 32];
   double acc = 0;
@@ -1318,7 +1278,6 @@ k_pcg_true_res(int n, const PcgState *st, const int *soff, const int *sw,
 }
 
 __global__ void k_pcg_true_dec(PcgState *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->done || !st->check_true) return;
   double rt2 = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) {
@@ -1332,7 +1291,6 @@ __global__ void k_pcg_true_dec(PcgState *st, const double *partials, int G) {
 
 __global__ void k_pcg_copy_r(long long n, const PcgState *st, const double *t,
                              double *r) {
-  DDLR_PDL_ENTRY();
   if (st->done || !st->restart) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     r[i] = t[i];
@@ -1340,7 +1298,6 @@ __global__ void k_pcg_copy_r(long long n, const PcgState *st, const double *t,
 
 // beta = rz_new / rz (Hestenes-Stiefel) or (rz_new - r.z_old) / rz (flexible)
 __global__ void k_pcg_beta(PcgState *st, const double *partials, int G) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   double rzn = warp_sum_partials(partials, G);
   double rzo = warp_sum_partials(partials + G, G);
@@ -1381,7 +1338,6 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
 k_pcg_update_rr(long long n, PcgState *st, const double *p, const double *q, double *x, double *r,
                 double *partials, unsigned *done) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   __shared__ double sm[NT / 32];
   const double a = st->alpha;
@@ -1424,7 +1380,6 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
 k_dot2_beta(long long n, const double *r, const double *z, const double *zo, double *partials, PcgState *st,
             unsigned *done) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   __shared__ double sm[NT / 32];
   // zo == z (plain CG): r.zold is not needed, and neither its loads nor its
@@ -1467,7 +1422,6 @@ k_dot2_beta(long long n, const double *r, const double *z, const double *zo, dou
 // p = z + beta p (and z_old = z for flexible CG)
 __global__ void k_pcg_p(long long n, const PcgState *st, const double *z,
                         double *p, double *zold) {
-  DDLR_PDL_ENTRY();
   if (st->done) return;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1511,7 +1465,6 @@ __device__ __forceinline__ double d_sm64_pm1(unsigned long long seed, unsigned l
 // arr[st->j] = sum of G partials (sqrt when asked)
 __global__ void k_lz_reduce_at(int G, const double *partials, double *arr, const LzState *st,
                                int do_sqrt, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   double s = warp_sum_partials(partials, G);
   if (threadIdx.x == 0) arr[st->j] = do_sqrt ? sqrt(s) : s;
@@ -1520,7 +1473,6 @@ __global__ void k_lz_reduce_at(int G, const double *partials, double *arr, const
 // w -= alpha_j q_j + beta_{j-1} q_{j-1}
 __global__ void k_lz_three_term_d(int s, const double *al, const double *be, const LzState *st,
                                   const double *qcur, const double *qprev, double *w) {
-  DDLR_PDL_ENTRY();
   if (st->stop) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
@@ -1536,7 +1488,6 @@ template <int NT>
 __global__ void __launch_bounds__(NT)
 k_gemvT_partial_d(int s, const double *Q, long long ld, const double *w, double *partials,
                   const LzState *st, const int *gate, const int *gate_inv) {
-  DDLR_PDL_ENTRY();
   if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
   const int ncol = st->j + 1;
   const int nw = NT / 32, wi = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -1555,7 +1506,6 @@ k_gemvT_partial_d(int s, const double *Q, long long ld, const double *w, double 
 // c[j] = sum_g partials[g][j], j <= st->j (warp per column, fixed order)
 __global__ void k_reduce_cols_d(int G, const double *partials, double *c, const LzState *st,
                                 const int *gate, const int *gate_inv) {
-  DDLR_PDL_ENTRY();
   if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
   const int ncol = st->j + 1;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -1570,7 +1520,6 @@ __global__ void k_reduce_cols_d(int G, const double *partials, double *c, const 
 // w -= Q_{j+1} c
 __global__ void k_gemvN_sub_d(int s, const double *Q, long long ld, const double *c, double *w,
                               const LzState *st, const int *gate, const int *gate_inv) {
-  DDLR_PDL_ENTRY();
   if ((gate && *gate) || (gate_inv && !*gate_inv)) return;
   extern __shared__ unsigned char smraw[];
   double *cs = reinterpret_cast<double *>(smraw);
@@ -1588,14 +1537,12 @@ __global__ void k_gemvN_sub_d(int s, const double *Q, long long ld, const double
 // Second Gram-Schmidt pass of a Lanczos step: always when always2, else when
 // the first pass left less than half of ||w||^2 (nrm[0] before, nrm[1] after)
 __global__ void k_lz_dgks(LzState *st, const double *nrm, int always2) {
-  DDLR_PDL_ENTRY();
   if (st->stop || threadIdx.x != 0) return;
   st->pass2 = (always2 || nrm[1] < 0.5 * nrm[0]) ? 1 : 0;
   st->npass2 += st->pass2;
 }
 
 __global__ void k_lz_decide(LzState *st, const double *al, const double *be) {
-  DDLR_PDL_ENTRY();
   if (st->stop || threadIdx.x != 0) return;
   const int j = st->j;
   const double a = al[j], b = be[j];
@@ -1614,7 +1561,6 @@ __global__ void k_lz_decide(LzState *st, const double *al, const double *be) {
 // normal step: q_{j+1} = w / beta_j into Q, qprev <- qcur, qcur <- q_{j+1}
 __global__ void k_lz_normalize(int s, const double *w, const double *be, double *Q, long long ld,
                                double *qcur, double *qprev, const LzState *st) {
-  DDLR_PDL_ENTRY();
   if (st->stop || !st->no_break) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
@@ -1628,7 +1574,6 @@ __global__ void k_lz_normalize(int s, const double *w, const double *be, double 
 // breakdown: w = SplitMix64 stream (seed + restarts), drawn in the order of
 // rank[] (ascending original index of the interface nodes)
 __global__ void k_lz_randvec(int s, const int *rank, const LzState *st, double *w) {
-  DDLR_PDL_ENTRY();
   if (st->stop || st->no_break) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
@@ -1638,7 +1583,6 @@ __global__ void k_lz_randvec(int s, const int *rank, const LzState *st, double *
 // breakdown: q_{j+1} = w / ||w|| (w orthogonalised), beta_j = 0
 __global__ void k_lz_restart_norm(int s, const double *w, const double *nrm, double *Q, long long ld,
                                   double *qcur, double *qprev, double *be, const LzState *st) {
-  DDLR_PDL_ENTRY();
   if (st->stop || st->no_break) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
@@ -1652,7 +1596,6 @@ __global__ void k_lz_restart_norm(int s, const double *w, const double *nrm, dou
 
 // end of step j: j += 1; stop at m_max
 __global__ void k_lz_advance(LzState *st) {
-  DDLR_PDL_ENTRY();
   if (st->stop || threadIdx.x != 0) return;
   st->j += 1;
   st->no_break = 1;
@@ -1661,7 +1604,6 @@ __global__ void k_lz_advance(LzState *st) {
 
 // eq. converge on the sums of the k largest Ritz values of T_m and T_{m-1}
 __global__ void k_lz_converged(const double *esum, double eps, int m, LzState *st) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0 || st->conv_m > 0) return;
   if (fabs(esum[0] - esum[1]) < eps * fabs(esum[1])) { st->conv_m = m; st->stop = 1; }
 }
@@ -1763,7 +1705,6 @@ constexpr int kEigRounds = 9;     // 9 x log2(129) = 63 bits
 // shared memory: 2m + 2 doubles.
 __global__ void __launch_bounds__(kEigPoints) k_tridiag_values(int m, const double *al, const double *be,
                                                                 int nv, double *vals) {
-  DDLR_PDL_ENTRY();
   extern __shared__ double shm[];
   double *a = shm, *b2 = shm + m, *bc = shm + 2 * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -1779,7 +1720,6 @@ __global__ void __launch_bounds__(kEigPoints) k_tridiag_values(int m, const doub
 
 // *out = sum of the first k entries of v (fixed order)
 __global__ void k_sum_first(int k, const double *v, double *out) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x == 0) {
     double s = 0;
     for (int i = 0; i < k; i++) s += v[i];
@@ -1797,7 +1737,6 @@ __global__ void k_sum_first(int k, const double *v, double *out) {
 __global__ void k_tridiag_vectors(int m, const double *al, const double *be,
                                   int nv, const double *vals, double *Y,
                                   double *work) {
-  DDLR_PDL_ENTRY();
   __shared__ double red[32];
   __shared__ double s_tn;
   const int tid = threadIdx.x;
@@ -1913,7 +1852,6 @@ __global__ void k_tridiag_vectors(int m, const double *al, const double *be,
 template <int CH>
 __global__ void k_ritz_gemm(int s, int m, int k, const double *Q, long long ld,
                             const double *Y, double *U) {
-  DDLR_PDL_ENTRY();
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
   for (int c0 = 0; c0 < k; c0 += CH) {
@@ -1937,7 +1875,6 @@ __global__ void k_ritz_gemm(int s, int m, int k, const double *Q, long long ld,
 __global__ void k_ddlr1_coef(int m, int k, int theta_mode, const double *vals,
                              double *theta, double *inv1mt, double *coef,
                              int *notspd) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0) return;
   const double th = (theta_mode == 1 && k < m) ? vals[k] : 0.0;
   *theta = th;
@@ -1948,12 +1885,10 @@ __global__ void k_ddlr1_coef(int m, int k, int theta_mode, const double *vals,
 
 // column c of a row-major n x k matrix <-> contiguous vector
 __global__ void k_get_col(long long n, int k, int c, const double *M, double *v) {
-  DDLR_PDL_ENTRY();
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) v[r] = M[r * k + c];
 }
 __global__ void k_set_col(long long n, int k, int c, const double *v, double *M) {
-  DDLR_PDL_ENTRY();
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) M[r * k + c] = v[r];
 }
@@ -1961,7 +1896,6 @@ __global__ void k_set_col(long long n, int k, int c, const double *v, double *M)
 // partials of K = U^T EV over row chunks (U, EV row-major n x k)
 __global__ void k_utv_partial(long long n, int k, const double *U,
                               const double *EV, double *partials) {
-  DDLR_PDL_ENTRY();
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const long long r0 = (long long)blockIdx.x * chunk, r1 = min(n, r0 + chunk);
   for (int pr = threadIdx.x; pr < k * k; pr += blockDim.x) {
@@ -1976,7 +1910,6 @@ __global__ void k_utv_partial(long long n, int k, const double *U,
 // the Cholesky flags NOT_SPD.  One thread; k is small.
 __global__ void k_hk_finalize(int G, int k, const double *partials, double *work,
                               double *Hk, int *notspd) {
-  DDLR_PDL_ENTRY();
   if (threadIdx.x != 0) return;
   double *M = work;            // k x k
   double *e = work + k * k;    // k

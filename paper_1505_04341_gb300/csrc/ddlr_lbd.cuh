@@ -18,7 +18,6 @@ namespace ddlr {
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_cgs_partial(long long nrows, int ncol, const double *Q, long long ld, const double *w, double *partials) {
-  DDLR_PDL_ENTRY();
   const int nw = NT / 32, wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const long long chunk = (nrows + gridDim.x - 1) / gridDim.x;
   const long long r0 = (long long)blockIdx.x * chunk, r1 = min(nrows, r0 + chunk);
@@ -33,7 +32,6 @@ k_cgs_partial(long long nrows, int ncol, const double *Q, long long ld, const do
 
 // c[col] = sum_g partials[g][col], a warp per column
 __global__ void k_cgs_reduce(int G, int ncol, const double *partials, double *c) {
-  DDLR_PDL_ENTRY();
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, l = threadIdx.x & 31;
   if (w >= ncol) return;
   double s = 0;
@@ -44,7 +42,6 @@ __global__ void k_cgs_reduce(int G, int ncol, const double *partials, double *c)
 
 // w -= Q c (Q rows x ncol column-major, c in shared memory)
 __global__ void k_cgs_sub(long long nrows, int ncol, const double *Q, long long ld, const double *c, double *w) {
-  DDLR_PDL_ENTRY();
   extern __shared__ double cs[];
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) cs[j] = c[j];
   __syncthreads();
@@ -57,14 +54,12 @@ __global__ void k_cgs_sub(long long nrows, int ncol, const double *Q, long long 
 
 // y -= (*coef) x
 __global__ void k_lbd_axpy(long long n, const double *coef, const double *x, double *y) {
-  DDLR_PDL_ENTRY();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] -= *coef * x[i];
 }
 
 // out = x * (1 / *nrm)
 __global__ void k_lbd_scale(long long n, const double *x, const double *nrm, double *out) {
-  DDLR_PDL_ENTRY();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = x[i] * (1.0 / *nrm);
 }
@@ -72,7 +67,6 @@ __global__ void k_lbd_scale(long long n, const double *x, const double *nrm, dou
 // B_m^T B_m for the first m steps: td[i] = alpha_i^2 + beta_{i-1}^2,
 // te[i] = alpha_i beta_i
 __global__ void k_lbd_tri(int m, const double *al, const double *be, double *td, double *te) {
-  DDLR_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   td[i] = al[i] * al[i] + (i > 0 ? be[i - 1] * be[i - 1] : 0.0);
@@ -81,7 +75,6 @@ __global__ void k_lbd_tri(int m, const double *al, const double *be, double *td,
 
 // G = B_m Y (m x k, column-major): G[i][c] = alpha_i Y[i][c] + beta_i Y[i+1][c]
 __global__ void k_lbd_bmy(int m, int k, const double *al, const double *be, const double *Y, double *G) {
-  DDLR_PDL_ENTRY();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m * k) return;
   const int c = e / m, i = e - c * m;

@@ -22,7 +22,6 @@ constexpr int kChunkThreads = 256;   // rows of a level chunk (the plan's kChunk
 //   d_i  = a_ii - sum_t l_it^2 d_t.
 // No pivoting: a zero or non-finite pivot sets *err = 1 (BREAKDOWN).
 __global__ void k_ildl_level(int cnt, const int *rows, const int *f_rp, const int *f_ci, double *fval, int *err) {
-  DDLR_PDL_ENTRY();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
   const int i = rows[t];
@@ -63,7 +62,6 @@ template <typename T>
 __global__ void __launch_bounds__(kChunkThreads)
 k_ldl_sweep(SolveLayout S, const int4 *chunks, int fwd, const T *lval, const T *uval, const T *dinv, const T *x,
             T *z, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const int4 ch = chunks[blockIdx.x];
   const int t = threadIdx.x;

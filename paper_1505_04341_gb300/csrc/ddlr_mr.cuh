@@ -109,7 +109,6 @@ __device__ __forceinline__ void mr_merge(const MrX X, int nr, const int *rk, con
 
 // X_0 = diag(C_a)^-1
 __global__ void k_mr_init(int s, const int *cc_diag, const double *cc, MrX X) {
-  DDLR_PDL_ENTRY();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   X.cnt[j] = 1;
@@ -122,7 +121,6 @@ __global__ void k_mr_init(int s, const int *cc_diag, const double *cc, MrX X) {
 __global__ void __launch_bounds__(128)
 k_mr_column(int s, const int *rp, const int *ci, const double *cv, const MrX X, int lfil, double droptol,
             int *zcnt, int *zrow, double *zval, double *num, double *den) {
-  DDLR_PDL_ENTRY();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   int rk[kMrCand], hk[kMrCand], hl[kMrCand], hp[kMrCand];
@@ -186,7 +184,6 @@ k_mr_column(int s, const int *rp, const int *ci, const double *cv, const MrX X, 
 // beta = sum num / sum den (fixed order, one CTA of 256); beta = 0 when the
 // denominator vanishes (R = 0 after dropping: X is final)
 __global__ void k_mr_beta(int s, const double *num, const double *den, double *beta) {
-  DDLR_PDL_ENTRY();
   __shared__ double sm[8];
   double a = 0, b = 0;
   for (int j = threadIdx.x; j < s; j += 256) { a += num[j]; b += den[j]; }
@@ -197,7 +194,6 @@ __global__ void k_mr_beta(int s, const double *num, const double *den, double *b
 
 // x_j += beta z_j (merge of two row-sorted lists)
 __global__ void k_mr_update(int s, MrX X, const int *zcnt, const int *zrow, const double *zval, const double *beta) {
-  DDLR_PDL_ENTRY();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   const double bt = *beta;
@@ -219,7 +215,6 @@ __global__ void k_mr_update(int s, MrX X, const int *zcnt, const int *zrow, cons
 
 // symmetric part (X + X^T)/2 as row CSR: count, (scan), fill, sort + combine
 __global__ void k_mr_sym_count(int s, const MrX X, int *rcnt) {
-  DDLR_PDL_ENTRY();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   for (int t = 0; t < X.cnt[j]; t++) {
@@ -231,7 +226,6 @@ __global__ void k_mr_sym_count(int s, const MrX X, int *rcnt) {
 
 // exclusive scan of cnt[0..s) into ptr[0..s] by one CTA of 1024 threads
 __global__ void k_mr_scan(int s, const int *cnt, int *ptr) {
-  DDLR_PDL_ENTRY();
   __shared__ int part[1024];
   const int t = threadIdx.x;
   const long long chunk = (s + 1023) / 1024;
@@ -251,7 +245,6 @@ __global__ void k_mr_scan(int s, const int *cnt, int *ptr) {
 }
 
 __global__ void k_mr_sym_fill(int s, const MrX X, const int *ptr, int *cursor, int *col, double *val) {
-  DDLR_PDL_ENTRY();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   for (int t = 0; t < X.cnt[j]; t++) {
@@ -269,7 +262,6 @@ __global__ void k_mr_sym_fill(int s, const MrX X, const int *ptr, int *cursor, i
 // row r: sort by column and combine the (at most two) entries per column;
 // ucnt[r] = distinct entries, kept at the front of the row
 __global__ void k_mr_sym_sort(int s, const int *ptr, int *col, double *val, int *ucnt) {
-  DDLR_PDL_ENTRY();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= s) return;
   const int b = ptr[r], n = ptr[r + 1] - b;
@@ -298,7 +290,6 @@ __global__ void k_mr_sym_sort(int s, const int *ptr, int *col, double *val, int 
 template <typename T>
 __global__ void k_mr_apply(int s, int m, int R, const int *ptr, const int *ucnt, const int *col, const T *val,
                            const T *x, T *z, const int *gate) {
-  DDLR_PDL_ENTRY();
   if (gate && *gate) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * R) return;

@@ -23,7 +23,6 @@ constexpr int kRandMaxL = 64;
 
 // Omega: Y[r * L + c] = SplitMix64(seed + 2^33 + c)[rank[r]]
 __global__ void k_rand_omega(int s, int L, const int *rank, unsigned long long seed, double *Y) {
-  DDLR_PDL_ENTRY();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)s * L) return;
   const int r = int(unsigned(e) / unsigned(L)), c = int(e - (long long)r * L);
@@ -33,7 +32,6 @@ __global__ void k_rand_omega(int s, int L, const int *rank, unsigned long long s
 // V = E W = [a^-1 Ehat W ; -a W] for a block of L columns (W s x L, V n x L)
 __global__ void k_e_block(int m, int s, int L, const int *eh_rp, const int *eh_ci, const double *eh, double ia,
                           double a, const double *W, double *V) {
-  DDLR_PDL_ENTRY();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)(m + s) * L) return;
   const int r = int(unsigned(e) / unsigned(L)), c = int(e - (long long)r * L);
@@ -53,7 +51,6 @@ __global__ void k_e_block(int m, int s, int L, const int *eh_rp, const int *eh_c
 constexpr int kGramNT = 256, kGramTile = 32;
 __global__ void __launch_bounds__(kGramNT)
 k_gram_partial(long long s, int L, const double *X, const double *Y, double *partials) {
-  DDLR_PDL_ENTRY();
   __shared__ double xs[kGramTile * kRandMaxL], ys[kGramTile * kRandMaxL];
   constexpr int PER = kRandMaxL * kRandMaxL / kGramNT;   // pairs per thread (16)
   const int np = L * L;
@@ -90,7 +87,6 @@ k_gram_partial(long long s, int L, const double *X, const double *Y, double *par
 
 // out[o] = sum_g partials[g][o] in order (o < L*L)
 __global__ void k_gram_reduce(int G, int np, const double *partials, double *out) {
-  DDLR_PDL_ENTRY();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= np) return;
   double v = 0;
@@ -101,7 +97,6 @@ __global__ void k_gram_reduce(int G, int np, const double *partials, double *out
 // Cholesky G = L L^T (G symmetrised first) and Linv = L^-1, one CTA of
 // kRandMaxL threads; a pivot <= 0 or not finite sets *flag
 __global__ void k_chol_inv(int L, const double *G, double *Linv, int *flag) {
-  DDLR_PDL_ENTRY();
   __shared__ double A[kRandMaxL * kRandMaxL];
   __shared__ int bad;
   const int t = threadIdx.x;
@@ -140,7 +135,6 @@ __global__ void k_chol_inv(int L, const double *G, double *Linv, int *flag) {
 
 // Q = Y L^-T row by row: Q[r][c] = sum_{j <= c} Y[r][j] Linv[c][j]
 __global__ void k_apply_rinv(long long s, int L, const double *Y, const double *Linv, double *Q) {
-  DDLR_PDL_ENTRY();
   __shared__ double Li[kRandMaxL * kRandMaxL];
   for (int o = threadIdx.x; o < L * L; o += blockDim.x) Li[o] = Linv[o];
   __syncthreads();
@@ -158,7 +152,6 @@ __global__ void k_apply_rinv(long long s, int L, const double *Y, const double *
 // kRandMaxL threads: d (diagonal), e (off-diagonal, e[i] couples i, i+1) and
 // the unit reflection vectors Hv[j][*] (zero where the reflection is I)
 __global__ void k_sym_tridiag(int L, const double *B, double *d, double *e, double *Hv) {
-  DDLR_PDL_ENTRY();
   __shared__ double A[kRandMaxL * kRandMaxL];
   __shared__ double v[kRandMaxL], p[kRandMaxL], w[kRandMaxL];
   __shared__ double sc[2];
@@ -228,7 +221,6 @@ __global__ void k_sym_tridiag(int L, const double *B, double *d, double *e, doub
 // eigenvectors of B from those of the tridiagonal form: Y (L x k column-
 // major) <- P_0 P_1 ... P_{L-3} Y, one thread per vector
 __global__ void k_back_transform(int L, int k, const double *Hv, double *Y) {
-  DDLR_PDL_ENTRY();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= k) return;
   double *y = Y + (long long)c * L;
@@ -243,7 +235,6 @@ __global__ void k_back_transform(int L, int k, const double *Hv, double *Y) {
 
 // out (s x k row-major) = Q (s x L row-major) Y (L x k column-major)
 __global__ void k_rm_gemm(long long s, int L, int k, const double *Q, const double *Y, double *out) {
-  DDLR_PDL_ENTRY();
   __shared__ double Ys[kRandMaxL * kRandMaxL];
   for (int o = threadIdx.x; o < L * k; o += blockDim.x) Ys[o] = Y[o];
   __syncthreads();
