@@ -13,13 +13,13 @@
 
 namespace ddlr {
 
-// Loads of data the persistent kernels stream once per step (the Lanczos
-// basis Q in the Gram-Schmidt passes, the factor entries and level
-// descriptors of the A0 solves), with the evict-first cache policy, so that
-// the vectors they gather keep their place in L2 while the 0.8 GB basis
-// streams through (128^3 setup 54.0 -> 52.7 ms).  The per-phase kernels keep
-// plain loads: there the hint measured no faster, and slower for the FP32
-// sweeps, whose factor is reused from L2 by the apply's second solve.
+// Loads of the Lanczos basis Q in the persistent kernel's Gram-Schmidt
+// passes, with the evict-first cache policy, so that the factor and the
+// vectors of the next step's operator keep their place in L2 while the
+// 0.8 GB basis streams through.  Other loads keep the default policy: the
+// hint measured no faster on the per-phase kernels, slower for the FP32
+// sweeps (whose factor the apply's second solve reuses from L2), and slower
+// for the L2-resident 64^3 persistent PCG when it also covered the factor.
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) {
   return __ldcs(p);

@@ -218,19 +218,19 @@ __device__ __forceinline__ void pz_level(const PzOp<T, TU> &O, int L, int mode, 
                                          T *z, const double *racc, const double *zsc, double &acc, T *z2) {
   const int c0 = O.lvl_ptr[L], cnt = O.lvl_ptr[L + 1] - c0;
   for (int v = blockIdx.x * NT + threadIdx.x; v < cnt; v += gridDim.x * NT) {
-    const int4 d = ld_stream(O.desc + c0 + v);
+    const int4 d = ro(O.desc + c0 + v);
     const int r = d.x;
     T zr;
     const T dr = ro(O.dinv + r);
     if (mode == 1) {
       const int off = d.z, w = int(unsigned(d.w) >> 16);
       T t = z[r];
-      for (int kk = 0; kk < w; kk++) t -= ld_stream(O.uval + off + kk * 32) * z[ld_stream(O.u_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.uval + off + kk * 32) * z[ro(O.u_col + off + kk * 32)];
       zr = t * dr;
     } else {
       const int off = d.y, w = int(unsigned(d.w) & 0xffffu);
       T t = pz_in<T>(x, xsc, r);
-      for (int kk = 0; kk < w; kk++) t -= ld_stream(O.lval + off + kk * 32) * z[ld_stream(O.l_col + off + kk * 32)];
+      for (int kk = 0; kk < w; kk++) t -= ro(O.lval + off + kk * 32) * z[ro(O.l_col + off + kk * 32)];
       zr = t * dr;
       if (mode == 2) zr = zr * dr;
     }
