@@ -189,6 +189,19 @@ struct ddlr_ctx {
     int m = 0;
     double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr,
            *cpart = nullptr, *cvec = nullptr, *st = nullptr;
+    // Arnoldi step j of a cycle as one CUDA graph each (captured at first
+    // use; they hold the arrays above and the handle's wait limit)
+    std::vector<cudaGraphExec_t> step;
+    int step_m = 0;                   // the restart length they were captured for
+    std::vector<long long> nodes;
+    std::vector<std::vector<long long>> fam_nodes;
+    void free_graphs() {
+      for (auto &e : step)
+        if (e) cudaGraphExecDestroy(e);
+      step.clear();
+      nodes.clear();
+      fam_nodes.clear();
+    }
   } gm;
   int cheb_msteps = 0;
   // approximate inverse of C_a (c_solver 2): columns of X during the MR
@@ -2162,6 +2175,7 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
   auto &G = c->gm;
   if (G.m < m) {
     // grown arrays replace the old ones; the arena keeps the old until destroy
+    G.free_graphs();
     G.V = c->alloc<double>(size_t(n) * (m + 1));
     G.Z = c->alloc<double>(size_t(n) * m);
     G.H = c->alloc<double>(size_t(m + 1) * m);
@@ -2174,6 +2188,28 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
   }
   const int ld = m + 1;
   double *r = c->pv[1], *w = c->pv[3], *q = c->pv[4];
+  // unless per-kernel timing is on, every Arnoldi step runs as one CUDA graph
+  // (step j captured once per handle, on the internal stream ordered after
+  // the caller's): with deep factors a step is about a thousand launches
+  const char *ng = getenv("DDLR_NO_GRAPH");
+  const bool use_graph = !c->timing && !(ng && ng[0] == '1');
+  cudaStream_t user = c->stream;
+  struct Restore {
+    ddlr_ctx *c; cudaStream_t s;
+    ~Restore() { c->stream = s; }
+  } restore{c, user};
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_fork, user), "event");
+    ck(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0), "wait");
+    c->stream = c->gstream;
+    if (G.step_m != m) G.free_graphs();   // H's leading dimension is m + 1
+    G.step_m = m;
+    if (int(G.step.size()) < m) {
+      G.step.resize(m, nullptr);
+      G.nodes.resize(m, 0);
+      G.fam_nodes.resize(m);
+    }
+  }
   auto norm_to = [&](const double *v, double *o1, double *o2) {
     KL(c, "gmres", c->stream, (k_dot_partial<double, 256>), kRedGrid, 256, 0, (long long)n, v, v, c->part64,
        (const int *)nullptr);
@@ -2202,23 +2238,52 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
     int j = 0;
     bool nan = false;
     while (j < m && its < maxit) {
-      const double *vj = G.V + size_t(j) * n;
-      double *zj = G.Z + size_t(j) * n, *hcol = G.H + size_t(j) * ld;
-      precond(c, vj, zj, nullptr);                                                        // z_j = M^-1 v_j
-      KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, zj, w,
-         (const int *)nullptr);                                                           // w = A z_j
-      for (int pass = 0; pass < 2; pass++) {
-        KL(c, "gmres_cgs", c->stream, k_cgs_partial<256>, kRedGrid, 256, 0, (long long)n, j + 1, G.V, (long long)n, w,
-           G.cpart);
-        KL(c, "gmres_cgs", c->stream, k_gm_reduce_acc, ((j + 1) * 32 + 255) / 256, 256, 0, kRedGrid, j + 1, G.cpart,
-           G.cvec, hcol, pass == 0 ? 1 : 0);
-        KL(c, "gmres_cgs", c->stream, k_cgs_sub, nblk(n), kThreads, (j + 1) * sizeof(double), (long long)n, j + 1, G.V,
-           (long long)n, G.cvec, w);
+      // one Arnoldi step: z_j = M^-1 v_j, w = A z_j, two CGS passes against
+      // V_{j+1}, h_{j+1,j}, v_{j+1}, the Givens rotation of column j
+      auto arnoldi = [&](int jj) {
+        const double *vj = G.V + size_t(jj) * n;
+        double *zj = G.Z + size_t(jj) * n, *hcol = G.H + size_t(jj) * ld;
+        precond(c, vj, zj, nullptr);
+        KL(c, "spmv", c->stream, k_spmv<double>, nblk(n), kThreads, 0, n, c->a_soff, c->a_sw, c->a_col, c->a_val, zj,
+           w, (const int *)nullptr);
+        for (int pass = 0; pass < 2; pass++) {
+          KL(c, "gmres_cgs", c->stream, k_cgs_partial<256>, kRedGrid, 256, 0, (long long)n, jj + 1, G.V, (long long)n,
+             w, G.cpart);
+          KL(c, "gmres_cgs", c->stream, k_gm_reduce_acc, ((jj + 1) * 32 + 255) / 256, 256, 0, kRedGrid, jj + 1,
+             G.cpart, G.cvec, hcol, pass == 0 ? 1 : 0);
+          KL(c, "gmres_cgs", c->stream, k_cgs_sub, nblk(n), kThreads, (jj + 1) * sizeof(double), (long long)n, jj + 1,
+             G.V, (long long)n, G.cvec, w);
+        }
+        norm_to(w, hcol + jj + 1, G.st + 1);
+        KL(c, "gmres", c->stream, k_lbd_scale, nblk(n), kThreads, 0, (long long)n, w, G.st + 1,
+           G.V + size_t(jj + 1) * n);
+        KL(c, "gmres", c->stream, k_gm_givens, 1, 32, 0, jj, hcol, G.cs, G.sn, G.g, G.st);
+      };
+      if (use_graph) {
+        if (!G.step[j]) {
+          const long long l0 = c->launches;
+          const std::vector<long long> f0 = c->fam_cnt;
+          ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture");
+          arnoldi(j);
+          cudaGraph_t g = nullptr;
+          ck(cudaStreamEndCapture(c->stream, &g), "capture");
+          cudaError_t e = cudaGraphInstantiate(&G.step[j], g, 0);
+          cudaGraphDestroy(g);
+          ck(e, "cudaGraphInstantiate");
+          G.nodes[j] = c->launches - l0;
+          G.fam_nodes[j].assign(c->fam_cnt.size(), 0);
+          for (size_t i = 0; i < c->fam_cnt.size(); i++)
+            G.fam_nodes[j][i] = c->fam_cnt[i] - (i < f0.size() ? f0[i] : 0);
+          c->launches = l0;                  // captured, not yet executed
+          for (size_t i = 0; i < f0.size(); i++) c->fam_cnt[i] = f0[i];
+          for (size_t i = f0.size(); i < c->fam_cnt.size(); i++) c->fam_cnt[i] = 0;
+        }
+        ck(cudaGraphLaunch(G.step[j], c->stream), "cudaGraphLaunch");
+        c->launches += G.nodes[j];
+        for (size_t i = 0; i < G.fam_nodes[j].size(); i++) c->fam_cnt[i] += G.fam_nodes[j][i];
+      } else {
+        arnoldi(j);
       }
-      norm_to(w, hcol + j + 1, G.st + 1);                                                 // h_{j+1,j}
-      KL(c, "gmres", c->stream, k_lbd_scale, nblk(n), kThreads, 0, (long long)n, w, G.st + 1,
-         G.V + size_t(j + 1) * n);
-      KL(c, "gmres", c->stream, k_gm_givens, 1, 32, 0, j, hcol, G.cs, G.sn, G.g, G.st);
       read2(G.st, sc);
       its++;
       j++;
@@ -2234,6 +2299,10 @@ void gmres_dev(ddlr_ctx *c, const double *b, double *x, double tol, int maxit, i
     norm_to(r, G.st + 2, G.st + 3);
     read2(G.st + 2, sc);
     beta = sc[0];
+  }
+  if (use_graph) {
+    ck(cudaEventRecord(c->ev_join, c->stream), "event");
+    ck(cudaStreamWaitEvent(user, c->ev_join, 0), "wait");
   }
   int dfl[4];
   read_dev(c, dfl, c->dflag, sizeof(dfl));
@@ -3126,6 +3195,7 @@ ddlr_status ddlr_increase_rank(ddlr_handle c, int k_new) {
     // graphs hold the old arrays' addresses
     if (W.exec) { cudaGraphExecDestroy(W.exec); W.exec = nullptr; }
     if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+    c->gm.free_graphs();
     batch_free(c);
     // Lanczos workspace for m_new steps: the basis and T_j carried over (the
     // old arrays stay in the handle's arena until it is destroyed)
@@ -3674,6 +3744,7 @@ ddlr_status ddlr_set_wait_limit(ddlr_handle c, double seconds) {
     // captured graphs hold the old limit in their kernel arguments
     if (c->lw.exec) { cudaGraphExecDestroy(c->lw.exec); c->lw.exec = nullptr; }
     if (c->pcg_exec) { cudaGraphExecDestroy(c->pcg_exec); c->pcg_exec = nullptr; }
+    c->gm.free_graphs();
     for (auto &kv : c->bt.graphs)
       if (kv.second.exec) { cudaGraphExecDestroy(kv.second.exec); kv.second.exec = nullptr; }
     c->bt.graphs.clear();
@@ -3721,6 +3792,7 @@ ddlr_status ddlr_destroy(ddlr_handle c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+  c->gm.free_graphs();
   if (c->lw.exec) cudaGraphExecDestroy(c->lw.exec);
   if (c->lw.ev_chk) cudaEventDestroy(c->lw.ev_chk);
   if (c->lw.ev_done) cudaEventDestroy(c->lw.ev_done);

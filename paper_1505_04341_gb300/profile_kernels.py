@@ -1,8 +1,10 @@
 """Kernel driver for profiling and timing one operation of the library.
 
 Builds the preconditioner for a named workload and repeats one operation --
-an A0 solve, an M^-1 apply, a PCG solve or the device setup from resident
-values (factorisation and Lanczos, `setup`) -- with device-resident vectors,
+an A0 solve, an M^-1 apply, a PCG solve, a GMRES(40) solve (`gmres`, with
+--indefinite 1 for a preconditioner that is not SPD, --factor and
+--fill-level for the local factors) or the device setup from resident values
+(factorisation and Lanczos, `setup`) -- with device-resident vectors,
 printing the CUDA-event time per repetition and the algorithmic bytes.  Used
 as the command under ncu for the kernel summaries in profiles/:
 
@@ -29,7 +31,7 @@ if ROOT not in sys.path:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="lap3d_64_b4")
-    ap.add_argument("--op", default="a0", choices=["a0", "apply", "pcg", "setup"])
+    ap.add_argument("--op", default="a0", choices=["a0", "apply", "pcg", "setup", "gmres"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--variant", type=int, default=1)
     ap.add_argument("--k", type=int, default=16)
@@ -43,6 +45,10 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--scale-diag", type=int, default=0)
     ap.add_argument("--maxit", type=int, default=500)
+    ap.add_argument("--factor", type=int, default=0)
+    ap.add_argument("--fill-level", type=int, default=0)
+    ap.add_argument("--indefinite", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-8)
     args = ap.parse_args(argv)
 
     import torch
@@ -54,7 +60,8 @@ def main(argv=None):
     w = W.workload(args.workload)
     A, part, p = w["A"], w["part"], w["p"]
     n = A[0]
-    h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=0,
+    h = DDLR(A, part, p, variant=args.variant, rank_k=args.k, factor=args.factor, fill_level=args.fill_level,
+             indefinite=args.indefinite,
              c_order=args.c_order, b_order=args.b_order, precision=args.precision,
              uk_bf16=args.bf16, c_solver=args.c_solver, scale_diag=args.scale_diag,
              max_nrhs=args.nrhs, lanczos_max=args.lanczos_max)
@@ -73,6 +80,8 @@ def main(argv=None):
             h.apply(b, y)
         elif args.op == "setup":
             h.refactor()
+        elif args.op == "gmres":    # GMRES(40); a capped step count profiles the same kernels
+            h.gmres(b, y, tol=args.tol, maxit=args.maxit, check=False)
         else:
             try:
                 h.pcg(b, y, tol=1e-8, maxit=args.maxit)
